@@ -1,0 +1,199 @@
+"""FP64 CPU oracle for the coupled Stokes-Darcy step (arXiv 2108.13229, Sec. 2).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` use this module; the product library never
+imports it.  The arithmetic lives in ``sd_oracle.c`` (plain C, FP64,
+single-threaded); this file only builds it with gcc and marshals numpy
+arrays through ctypes.
+
+Vector layout of the whole system (the same order as the public C ABI uses
+for its host buffers): ``u`` ((n+1) x n faces, row j*(n+1)+i), ``v``
+(n x (n+1) faces, row j*n+i, j = 0 on the interface), ``p_ff`` (n x n),
+``p_pm`` (n x n); DoF = 4n^2 + 2n (Table 1).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sd_oracle.c")
+_SO = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (portable flags: it also builds on Arm)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = ctypes.CDLL(build())
+    lib.or_create.restype = ctypes.c_void_p
+    lib.or_create.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp]
+    lib.or_destroy.argtypes = [ctypes.c_void_p]
+    lib.or_ndof.restype = ctypes.c_int64
+    lib.or_ndof.argtypes = [ctypes.c_void_p]
+    lib.or_nnz.restype = ctypes.c_int64
+    lib.or_nnz.argtypes = [ctypes.c_void_p]
+    lib.or_dof_count.restype = ctypes.c_int64
+    lib.or_dof_count.argtypes = [ctypes.c_int]
+    lib.or_get_csr.argtypes = [ctypes.c_void_p, _i64p, _i32p, _dp]
+    lib.or_apply.argtypes = [ctypes.c_void_p, _dp, _dp]
+    lib.or_exact.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp]
+    lib.or_rhs.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, _dp]
+    lib.or_factor.restype = ctypes.c_int
+    lib.or_factor.argtypes = [ctypes.c_void_p]
+    lib.or_solve.restype = ctypes.c_int
+    lib.or_solve.argtypes = [ctypes.c_void_p, _dp, _dp]
+    lib.or_bandwidth.restype = ctypes.c_int
+    lib.or_bandwidth.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.or_residual.restype = ctypes.c_double
+    lib.or_residual.argtypes = [ctypes.c_void_p, _dp, _dp, _dp]
+    lib.or_run.restype = ctypes.c_int
+    lib.or_run.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, ctypes.c_int]
+    for name in ("or_mms_u", "or_mms_v", "or_mms_ppm"):
+        f = getattr(lib, name)
+        f.restype = ctypes.c_double
+        f.argtypes = [ctypes.c_double] * 3
+    for name in ("or_mms_pff", "or_mms_fx", "or_mms_fy"):
+        f = getattr(lib, name)
+        f.restype = ctypes.c_double
+        f.argtypes = [ctypes.c_double] * 4
+    _lib = lib
+    return lib
+
+
+def _ptr(a: np.ndarray, ctype=ctypes.c_double):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def dof_count(n: int) -> int:
+    return int(_load().or_dof_count(n))
+
+
+def offsets(n: int) -> dict:
+    """Start offset of each field in the whole-system vector."""
+    nu = n * (n + 1)
+    return {"u": 0, "v": nu, "p_ff": 2 * nu, "p_pm": 2 * nu + n * n, "end": 2 * nu + 2 * n * n}
+
+
+def split(x: np.ndarray, n: int) -> dict:
+    """Views of the four fields as 2-D arrays indexed [j, i]."""
+    o = offsets(n)
+    return {
+        "u": x[o["u"]:o["v"]].reshape(n, n + 1),
+        "v": x[o["v"]:o["p_ff"]].reshape(n + 1, n),
+        "p_ff": x[o["p_ff"]:o["p_pm"]].reshape(n, n),
+        "p_pm": x[o["p_pm"]:o["end"]].reshape(n, n),
+    }
+
+
+def exact(n: int, t: float, mu: float = 1.0) -> np.ndarray:
+    """Manufactured solution sampled at the DoF locations at time t."""
+    x = np.zeros(dof_count(n))
+    _load().or_exact(n, t, mu, _ptr(x))
+    return x
+
+
+def mms(name: str, *args) -> float:
+    """Evaluate one manufactured closed form: u, v, pff, ppm, fx, fy."""
+    return float(getattr(_load(), "or_mms_" + name)(*[float(a) for a in args]))
+
+
+class Oracle:
+    """Assembled FP64 system of one instance (n cells per side per subdomain)."""
+
+    def __init__(self, n: int, mu: float, alpha: float, dt: float, K):
+        K = _f64(K).reshape(n, n)
+        self.n, self.mu, self.alpha, self.dt = n, float(mu), float(alpha), float(dt)
+        self._lib = _load()
+        self._c = self._lib.or_create(n, self.mu, self.alpha, self.dt, _ptr(K))
+        if not self._c:
+            raise ValueError("oracle: invalid parameters")
+        self.ndof = int(self._lib.or_ndof(self._c))
+        self.nnz = int(self._lib.or_nnz(self._c))
+        self.factored = False
+
+    def __del__(self):
+        c = getattr(self, "_c", None)
+        if c:
+            self._lib.or_destroy(c)
+            self._c = None
+
+    def csr(self):
+        rowptr = np.zeros(self.ndof + 1, dtype=np.int64)
+        col = np.zeros(self.nnz, dtype=np.int32)
+        val = np.zeros(self.nnz)
+        self._lib.or_get_csr(self._c, _ptr(rowptr, ctypes.c_int64), _ptr(col, ctypes.c_int32), _ptr(val))
+        return rowptr, col, val
+
+    def scipy_csr(self):
+        import scipy.sparse as sp
+        rowptr, col, val = self.csr()
+        return sp.csr_matrix((val, col, rowptr), shape=(self.ndof, self.ndof))
+
+    def apply(self, x) -> np.ndarray:
+        x = _f64(x)
+        y = np.zeros(self.ndof)
+        self._lib.or_apply(self._c, _ptr(x), _ptr(y))
+        return y
+
+    def rhs(self, xprev, t: float) -> np.ndarray:
+        xprev = _f64(xprev)
+        b = np.zeros(self.ndof)
+        self._lib.or_rhs(self._c, _ptr(xprev), float(t), _ptr(b))
+        return b
+
+    def factor(self) -> None:
+        info = self._lib.or_factor(self._c)
+        if info != 0:
+            raise RuntimeError("oracle: banded LU failed (info=%d)" % info)
+        self.factored = True
+
+    def bandwidth(self):
+        kl, ku = ctypes.c_int(), ctypes.c_int()
+        self._lib.or_bandwidth(self._c, ctypes.byref(kl), ctypes.byref(ku))
+        return kl.value, ku.value
+
+    def solve(self, b) -> np.ndarray:
+        if not self.factored:
+            self.factor()
+        b = _f64(b)
+        x = np.zeros(self.ndof)
+        if self._lib.or_solve(self._c, _ptr(b), _ptr(x)) != 0:
+            raise RuntimeError("oracle: solve without factorisation")
+        return x
+
+    def residual(self, x, b):
+        x, b = _f64(x), _f64(b)
+        r = np.zeros(self.ndof)
+        nrm = self._lib.or_residual(self._c, _ptr(x), _ptr(b), _ptr(r))
+        return r, float(nrm)
+
+    def run(self, x0, t0: float, nsteps: int) -> np.ndarray:
+        """nsteps implicit-Euler steps from state x0 at time t0."""
+        if not self.factored:
+            self.factor()
+        x = _f64(x0).copy()
+        if self._lib.or_run(self._c, _ptr(x), float(t0), int(nsteps)) != 0:
+            raise RuntimeError("oracle: run failed")
+        return x

@@ -1,0 +1,220 @@
+"""Pins of the FP64 oracle against things other than itself (CPU only).
+
+* the manufactured solution, re-derived symbolically from its stream function
+  and the PDE (Eqs. (1)-(7)) with sympy;
+* Table 1 (Sec. 1): DoF counts exactly, matrix entries per DoF;
+* brute force: the banded LU against numpy's dense LAPACK solve;
+* structure: S*A symmetric (S = -1 on the pressure rows), identity
+  Dirichlet rows, B * const = 0 away from Gamma, Darcy row sums;
+* invariants of a solution: discrete divergence, global mass balance through
+  Gamma (Eq. (7)) on both sides;
+* second-order convergence to the manufactured solution, and loss of it when
+  a coupling parameter is planted inconsistently.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2108_13229_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _table1():
+    rows = []
+    with open(os.path.join(GOLDEN, "table1.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                n, dof, dens = line.split()
+                rows.append((int(n), int(dof), float(dens)))
+    return rows
+
+
+# ---------------------------------------------------------------------------
+# manufactured solution
+# ---------------------------------------------------------------------------
+def test_mms_symbolic():
+    sp = pytest.importorskip("sympy")
+    x, y, t, mu = sp.symbols("x y t mu", real=True)
+    A = sp.pi ** 2 + 2
+    phi = 1 + A * (y - 1) + (y - 1) ** 2
+    psi = sp.sin(sp.pi * x) * phi
+    s = 1 + t
+    u = sp.diff(psi, y) * s
+    v = -sp.diff(psi, x) * s
+    ppm = sp.cos(sp.pi * x) * sp.exp(sp.pi * (y - 1)) * s
+    # Eq. (5) on y = 1 fixes p_ff (taken constant in y): p - 2 mu dv/dy = p_pm
+    pff = sp.simplify((ppm + 2 * mu * sp.diff(v, y)).subs(y, 1))
+    # Eq. (2) and Darcy (Eqs. (3), (4) with K = mu = 1): div v = 0, lap p_pm = 0
+    assert sp.simplify(sp.diff(u, x) + sp.diff(v, y)) == 0
+    assert sp.simplify(sp.diff(ppm, x, 2) + sp.diff(ppm, y, 2)) == 0
+    # Eq. (6) with K = alpha = 1, n = (0,-1), t = (1,0): u = du/dy + dv/dx on y = 1
+    assert sp.simplify((u - (sp.diff(u, y) + sp.diff(v, x))).subs(y, 1)) == 0
+    # Eq. (7) with K = mu = 1: v_ff(y=1) = -dp_pm/dy(y=1)
+    assert sp.simplify((v + sp.diff(ppm, y)).subs(y, 1)) == 0
+    # no flow through the pm sides
+    assert sp.simplify(sp.diff(ppm, x).subs(x, 0)) == 0
+    assert sp.simplify(sp.diff(ppm, x).subs(x, 1)) == 0
+    # forcing of Eq. (1) from the full symmetric stress (rho = 1)
+    txx, tyy = 2 * mu * sp.diff(u, x), 2 * mu * sp.diff(v, y)
+    txy = mu * (sp.diff(u, y) + sp.diff(v, x))
+    fx = sp.diff(u, t) + sp.diff(-txx + pff, x) + sp.diff(-txy, y)
+    fy = sp.diff(v, t) + sp.diff(-txy, x) + sp.diff(-tyy + pff, y)
+    exprs = {"u": u, "v": v, "ppm": ppm}
+    exprs_mu = {"pff": pff, "fx": fx, "fy": fy}
+    rng = np.random.default_rng(1)
+    for name, e in exprs.items():
+        f = sp.lambdify((x, y, t), e, "math")
+        for _ in range(5):
+            px, py, pt = rng.uniform(0, 1), rng.uniform(0, 2), rng.uniform(0, 2)
+            assert O.mms(name, px, py, pt) == pytest.approx(f(px, py, pt), rel=1e-13, abs=1e-13)
+    for name, e in exprs_mu.items():
+        f = sp.lambdify((x, y, t, mu), e, "math")
+        for m in (1.0, 1e-3):
+            for _ in range(5):
+                px, py, pt = rng.uniform(0, 1), rng.uniform(0, 2), rng.uniform(0, 2)
+                assert O.mms(name, px, py, pt, m) == pytest.approx(f(px, py, pt, m), rel=1e-12, abs=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Table 1
+# ---------------------------------------------------------------------------
+def test_table1_dof_counts():
+    for n, dof, _ in _table1():
+        assert O.dof_count(n) == dof
+    for n, dof, _ in _table1()[:3]:
+        assert O.Oracle(n, 1.0, 1.0, 0.1, I.constant_K(n)).ndof == dof
+
+
+def test_table1_entries_per_dof():
+    # Table 1 prints one decimal; on the two finest grids the boundary rows no
+    # longer matter and the interior stencils (11-point momentum with the full
+    # stress, 4-point continuity, 5-point TPFA) fix the ratio.
+    for n, dof, dens in _table1():
+        if n < 160:
+            continue
+        o = O.Oracle(n, 1.0, 1.0, 0.1, I.constant_K(n))
+        assert round(o.nnz / o.ndof, 1) == dens
+    # the interior-only limit (2*11 + 4 + 5)/4 = 7.75 bounds the ratio from above
+    assert O.Oracle(500, 1.0, 1.0, 0.1, I.constant_K(500)).nnz / O.dof_count(500) < 7.75
+
+
+# ---------------------------------------------------------------------------
+# brute force: banded LU vs dense LAPACK
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [4, 5, 8])
+def test_banded_lu_vs_dense(n):
+    K = I.lognormal_K(n, -4.0, 1.5, 2.0, seed=n)
+    o = O.Oracle(n, 1e-3, 0.7, 0.05, K)
+    A = o.scipy_csr().toarray()
+    rng = np.random.default_rng(n)
+    b = rng.standard_normal(o.ndof)
+    x_band = o.solve(b)
+    x_dense = np.linalg.solve(A, b)
+    assert np.linalg.norm(x_band - x_dense) <= 1e-10 * np.linalg.norm(x_dense)
+    assert np.linalg.norm(A @ x_band - b) <= 1e-12 * np.linalg.norm(b) * max(1.0, np.abs(A).max())
+    kl, ku = o.bandwidth()
+    assert kl <= 3 * n + 2 and ku <= 3 * n + 2
+
+
+# ---------------------------------------------------------------------------
+# structure of A (Eq. (9))
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [5, 8])
+def test_structure(n):
+    K = I.lognormal_K(n, -4.0, 1.0, 3.0, seed=3)
+    mu = 1e-3
+    o = O.Oracle(n, mu, 1.3, 0.05, K)
+    A = o.scipy_csr().toarray()
+    off = O.offsets(n)
+    S = np.ones(o.ndof)
+    S[off["p_ff"]:] = -1.0
+    SA = S[:, None] * A
+    # symmetric saddle-point form: V = V^T, C = -B^T, C'_1 = -B'_1^T, D' = D'^T
+    assert np.abs(SA - SA.T).max() <= 1e-14 * np.abs(A).max()
+    # Dirichlet velocity faces: identity rows, eliminated from every other row
+    dirichlet = []
+    for j in range(n):
+        dirichlet += [off["u"] + j * (n + 1), off["u"] + j * (n + 1) + n]
+    dirichlet += [off["v"] + n * n + i for i in range(n)]
+    for k in dirichlet:
+        e = np.zeros(o.ndof)
+        e[k] = 1.0
+        assert np.array_equal(A[k], e) and np.array_equal(A[:, k], e)
+    # continuity rows have no diagonal; no pressure-pressure coupling in ff
+    assert np.all(A[off["p_ff"]:off["p_pm"], off["p_ff"]:off["p_pm"]] == 0)
+    # gradient of a constant ff pressure vanishes except on the v_Gamma rows
+    one = np.zeros(o.ndof)
+    one[off["p_ff"]:off["p_pm"]] = 1.0
+    y = A @ one
+    vg = slice(off["v"], off["v"] + n)
+    assert np.allclose(y[vg], 1.0 / n, rtol=1e-14)
+    y[vg] = 0.0
+    assert np.abs(y).max() == 0.0
+    # Darcy row sums: fluxes between cells cancel, only the Dirichlet bottom remains
+    onep = np.zeros(o.ndof)
+    onep[off["p_pm"]:] = 1.0
+    yp = (A @ onep)[off["p_pm"]:].reshape(n, n)
+    assert np.allclose(yp[0], 2.0 * K[0] / mu, rtol=1e-13)
+    assert np.abs(yp[1:]).max() <= 1e-12 * np.abs(yp[0]).max()
+
+
+# ---------------------------------------------------------------------------
+# invariants of a solution
+# ---------------------------------------------------------------------------
+def test_divergence_and_interface_mass_balance():
+    n, mu = 16, 1e-3
+    K = I.lognormal_K(n, -4.0, 1.0, 4.0, seed=7)
+    o = O.Oracle(n, mu, 1.0, 0.05, K)
+    x0 = O.exact(n, 0.0, mu)
+    x = o.run(x0, 0.0, 3)
+    f = O.split(x, n)
+    h = 1.0 / n
+    u, v, ppm = f["u"], f["v"], f["p_pm"]
+    div = h * (u[:, 1:] - u[:, :-1] + v[1:, :] - v[:-1, :])
+    assert np.abs(div).max() <= 1e-12 * h * np.abs(u).max()
+    # flux into the Darcy domain through Gamma (Eq. (7)) = flux leaving ff through Gamma
+    #   ff side: h*sum(v_Gamma) = h*sum(u_right - u_left) + h*sum(v_top)
+    q_gamma = h * v[0].sum()
+    q_ff = h * (u[:, n] - u[:, 0]).sum() + h * v[n].sum()
+    assert abs(q_gamma - q_ff) <= 1e-12 * h * np.abs(v).sum()
+    #   pm side: what enters through Gamma leaves through the Dirichlet bottom
+    t_end = 3 * 0.05
+    g = np.array([O.mms("ppm", (i + 0.5) * h, 0.0, t_end) for i in range(n)])
+    q_bottom = (2.0 * K[0] / mu * (ppm[0] - g)).sum()
+    assert abs(q_gamma + q_bottom) <= 1e-10 * abs(q_bottom) + 1e-13
+
+
+# ---------------------------------------------------------------------------
+# convergence to the manufactured solution
+# ---------------------------------------------------------------------------
+def _mms_errors(n, alpha=1.0, kval=1.0, steps=10, dt=0.1):
+    o = O.Oracle(n, 1.0, alpha, dt, I.constant_K(n, kval))
+    x = o.run(O.exact(n, 0.0, 1.0), 0.0, steps)
+    xe = O.exact(n, steps * dt, 1.0)
+    h = 1.0 / n
+    fs, fe = O.split(x, n), O.split(xe, n)
+    return {k: float(np.sqrt(h * h * np.sum((fs[k] - fe[k]) ** 2))) for k in fs}
+
+
+def test_mms_second_order():
+    ns = [16, 32, 64, 128]
+    errs = [_mms_errors(n) for n in ns]
+    orders = [{k: np.log2(a[k] / b[k]) for k in a} for a, b in zip(errs, errs[1:])]
+    for od in orders:
+        for k in ("u", "v", "p_pm"):
+            assert od[k] >= 1.9, (k, orders)
+    # the ff pressure carries a first-order error in the two top corner cells;
+    # its L2 order rises towards two
+    pf = [od["p_ff"] for od in orders]
+    assert pf[0] >= 1.5 and pf[-1] >= 1.8 and pf[0] < pf[1] < pf[2], orders
+
+
+@pytest.mark.parametrize("alpha,kval", [(2.0, 1.0), (1.0, 2.0)])
+def test_mms_detects_planted_inconsistency(alpha, kval):
+    # the manufactured solution needs alpha_BJ = 1 and K = mu = 1; planting
+    # another value in the oracle must stop convergence
+    e1, e2 = _mms_errors(32, alpha, kval), _mms_errors(64, alpha, kval)
+    assert max(np.log2(e1[k] / e2[k]) for k in e1) < 1.0

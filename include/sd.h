@@ -1,0 +1,208 @@
+/*
+ * sd.h -- C ABI of the GB300-native monolithic Stokes-Darcy solver.
+ *
+ * Method (arXiv 2108.13229): the time-dependent Stokes-Darcy problem of
+ * Sec. 2 (Eqs. (1)-(7)), discretised by backward Euler in time, MAC
+ * staggered finite volumes in the free flow and cell-centred TPFA in the
+ * porous medium, gives one linear system per time step, Eq. (8)/(9):
+ *
+ *     [ V    B   B'_1 ] [ v^ff ]   [ g ]
+ *     [ C    0   0    ] [ p^ff ] = [ 0 ]
+ *     [ C'_1 0   D'   ] [ p^pm ]   [ 0 ]
+ *
+ * solved monolithically by a flexible GMRES(m) with a block preconditioner
+ * of the kind built in Sec. 4 (the zero block replaced, V and D' handled by
+ * their own preconditioners -- here geometric multigrid V-cycles).
+ *
+ * Geometry: free flow [0,1]x[1,2] over porous medium [0,1]x[0,1], n x n
+ * cells each, interface y = 1.  Whole-system vectors use the layout
+ *     u    (n+1) x n  vertical ff faces, index j*(n+1)+i
+ *     v    n x (n+1)  horizontal ff faces, index j*n+i   (j = 0 on the interface)
+ *     p_ff n x n      ff cell centres, index j*n+i
+ *     p_pm n x n      pm cell centres, index j*n+i       (j = 0 at y = 0)
+ * concatenated in this order, 4n^2 + 2n doubles (the DoF count of Table 1).
+ *
+ * Conventions for every function:
+ *  - returns SD_OK (0) or a negative SD_E_* code; sd_strerror() names it;
+ *    no C++ exception crosses this interface;
+ *  - every array argument may be host memory or CUDA device memory of the
+ *    current device (the library inspects the pointer); it is owned by the
+ *    caller and is not retained after the call returns;
+ *  - a handle owns all device memory it allocates until sd_destroy();
+ *    calls on one handle are serialised by the handle; distinct handles may
+ *    be used from distinct threads at the same time.
+ */
+#ifndef SD_H
+#define SD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SD_OK 0
+#define SD_PENDING 1       /* sd_poll: the request is queued or running */
+#define SD_E_INVAL -1      /* invalid argument (grid, mu, K, alpha_BJ, dt, options) */
+#define SD_E_NOMEM -2      /* device memory (or the server's HBM budget) exhausted */
+#define SD_E_NOCONV -3     /* max_iters reached; the state holds the last iterate */
+#define SD_E_NUMERIC -4    /* NaN/Inf in the Krylov recurrence */
+#define SD_E_TIMEOUT -5    /* a bounded wait gave up */
+#define SD_E_CUDA -6       /* a CUDA runtime call failed */
+#define SD_E_STATE -7      /* unknown ticket, or call not valid in this state */
+
+/* precision of the multigrid V-cycles inside the preconditioner; the outer
+   FGMRES (residual, Gram-Schmidt, Hessenberg least squares) and the
+   coarsest-grid solves are always FP64 */
+#define SD_FP64 0
+#define SD_MIXED 1
+
+/* block preconditioner (Sec. 4):
+   SD_TRI_SCHUR  block upper-triangular on (v, p_ff) with the zero block
+                 replaced by a Schur approximation S^, S^-1 = (mu/(gamma h^2)) I
+                 + (1/dt) L_p^-1 (viscous plus mass-dominated parts of
+                 B^T V^-1 B), then the Darcy block after the velocity (C'_1
+                 coupling kept): z_pff, z_v, z_pm;
+   SD_PV_BJ_I    pressure-velocity block Jacobi P^pv_BJ(P_V, P_D') with the
+                 identity on the p_ff block (Sec. 4);
+   SD_PV_BGS_I   pressure-velocity block Gauss-Seidel P^pv_BGS(P_V, P_D')
+                 with the identity on the p_ff block (Sec. 4). */
+#define SD_TRI_SCHUR 0
+#define SD_PV_BJ_I 1
+#define SD_PV_BGS_I 2
+
+/* boundary data: manufactured solution (Dirichlet ff velocity on the top and
+   sides, Dirichlet pressure at the pm bottom, no flow through the pm sides) */
+#define SD_BC_MMS 0
+
+typedef struct sd_handle sd_handle;
+typedef struct sd_server sd_server;
+
+typedef struct {
+  int32_t nx, ny; /* cells per subdomain side; square subdomains: nx == ny == n,
+                     n = m * 2^k with m <= 16 so that multigrid reaches a small grid */
+} sd_grid;
+
+typedef struct {
+  int32_t restart;     /* FGMRES restart length m, 1..30 (default 30) */
+  double rtol;         /* stop when ||b - A x||_2 <= rtol ||b||_2 (default 1e-10) */
+  int32_t max_iters;   /* FGMRES iterations allowed per time step (default 600) */
+  int32_t precision;   /* SD_FP64 | SD_MIXED (default SD_MIXED) */
+  int32_t precond;     /* SD_TRI_SCHUR | SD_PV_BJ_I | SD_PV_BGS_I (default SD_TRI_SCHUR) */
+  int32_t bc;          /* SD_BC_MMS */
+  int32_t cheb_degree; /* Chebyshev smoothing steps before and after each coarse
+                          correction (default 2) */
+  int32_t coarsest;    /* coarsen while the grid has more than this many cells per
+                          side (default 8) */
+  double schur_gamma;  /* gamma of S^ (default 0.5) */
+  double cheb_ratio;   /* Chebyshev interval [lmax/ratio, 1.1 lmax] (default 8) */
+  int32_t schur_mass;  /* SD_TRI_SCHUR: add the mass-dominated part (1/dt) L_p^-1 of
+                          the Schur complement, L_p = B^T B / h^2 (default 1) */
+  void *stream;        /* cudaStream_t to run on; NULL: the handle creates one */
+} sd_options;
+
+typedef struct {
+  int32_t iters;    /* FGMRES iterations of this step */
+  int32_t restarts; /* restart cycles of this step */
+  int32_t status;   /* SD_OK | SD_E_NOCONV | SD_E_NUMERIC */
+  double relres;    /* final true ||b - A x||_2 / ||b||_2 (FP64, recomputed) */
+  double ms;        /* device time of the step (CUDA events) */
+} sd_step_info;
+
+/* Fill *opt with the defaults above. */
+void sd_options_default(sd_options *opt);
+
+/* 4 n^2 + 2 n: unknowns of one instance (Table 1). */
+int64_t sd_dof_count(int32_t n);
+
+/* Device bytes sd_create() will allocate for this grid and options. */
+int64_t sd_memory_estimate(const sd_grid *grid, const sd_options *opt);
+
+/* Create one instance of the coupled problem (Sec. 2) and its solver.
+ *   mu        dynamic viscosity (> 0), rho = 1;
+ *   K         n*n permeabilities of the pm cells (> 0, finite), index j*n+i,
+ *             host or device, copied before return;
+ *   alpha_bj  Beavers-Joseph coefficient of Eq. (6) (> 0);
+ *   dt        implicit-Euler step (> 0);
+ *   opt       NULL for defaults.
+ * Builds the multigrid hierarchy, coarsest-grid inverses and Chebyshev
+ * bounds, and sets the state to the manufactured solution at t = 0.
+ * Errors: SD_E_INVAL, SD_E_NOMEM, SD_E_CUDA. */
+int sd_create(const sd_grid *grid, double mu, const double *K, double alpha_bj, double dt, const sd_options *opt,
+              sd_handle **out);
+
+/* Advance nsteps implicit-Euler steps (Sec. 2): right-hand side from the
+ * previous velocities, then FGMRES to rtol, warm-started from the previous
+ * solution.  info: NULL or nsteps entries.  Returns the first non-OK step
+ * status (the state advances regardless). */
+int sd_step(sd_handle *h, int32_t nsteps, sd_step_info *info);
+
+/* Copy the current fields out (any of the four may be NULL). */
+int sd_get_fields(sd_handle *h, double *u, double *v, double *p_ff, double *p_pm);
+
+/* Read / replace the whole state: time, step count, whole-system vector x. */
+int sd_get_state(sd_handle *h, double *t, int64_t *step, double *x);
+int sd_set_state(sd_handle *h, double t, int64_t step, const double *x);
+
+/* y = A x with A the matrix of Eq. (9) (whole-system layout). */
+int sd_apply(sd_handle *h, const double *x, double *y);
+
+/* Right-hand side b of the implicit-Euler step to time t from the previous
+ * state xprev (Sec. 2). */
+int sd_rhs(sd_handle *h, const double *xprev, double t, double *b);
+
+/* Solve A x = b by preconditioned FGMRES; x holds the initial guess on entry
+ * and the solution on return.  info may be NULL. */
+int sd_solve(sd_handle *h, const double *b, double *x, sd_step_info *info);
+
+/* Wait for all work of the handle. */
+int sd_sync(sd_handle *h);
+
+/* Release the handle and its device memory. */
+void sd_destroy(sd_handle *h);
+
+/* Advance count independent instances concurrently (each on its own stream,
+ * one host thread per instance up to max_threads; 0 = one per instance).
+ * nsteps[k] steps for hs[k]; infos[k] NULL or nsteps[k] entries.  Each
+ * instance's result is identical to running it alone.  Returns the first
+ * non-OK status. */
+int sd_solve_batch(sd_handle *const *hs, int32_t count, const int32_t *nsteps, sd_step_info *const *infos,
+                   int32_t max_threads);
+
+/* Continuous-batching server: requests are admitted as slots and HBM budget
+ * free up and run concurrently; each run keeps its state on the device. */
+typedef struct {
+  sd_grid grid;
+  double mu, alpha_bj, dt;
+  const double *K;   /* host, n*n, copied by sd_submit */
+  int32_t nsteps;
+  int32_t keep_fields; /* 1: the result keeps the final whole-system vector */
+} sd_request;
+
+typedef struct {
+  int32_t status;      /* SD_OK or the first failing step's status */
+  int32_t steps_done;
+  int32_t total_iters;
+  double max_relres;
+  double queue_ms;     /* submit -> start */
+  double run_ms;       /* start -> finished */
+  double latency_ms;   /* submit -> finished */
+  int64_t dof;
+} sd_result;
+
+int sd_server_create(int64_t hbm_budget_bytes, int32_t max_running, const sd_options *opt, sd_server **out);
+int sd_submit(sd_server *s, const sd_request *req, uint64_t *ticket);
+/* SD_PENDING while queued or running; SD_OK (or the run's error) when done.
+ * x: NULL or 4n^2+2n doubles (host) receiving the final state if keep_fields. */
+int sd_poll(sd_server *s, uint64_t ticket, sd_result *out, double *x);
+/* Block until every submitted request has finished. */
+int sd_server_drain(sd_server *s);
+void sd_server_destroy(sd_server *s);
+
+const char *sd_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SD_H */

@@ -1,0 +1,170 @@
+// sd_internal.cuh -- device data layout and launch wrappers of the GB300
+// Stokes-Darcy solver (arXiv 2108.13229, Secs. 2 and 4).  Internal to the
+// library; the public interface is include/sd.h.
+//
+// Layout of one level with n x n cells per subdomain (all fields share the
+// row pitch P = roundup(n + 1, 8) elements, x fastest):
+//   u    n     rows x P   vertical ff faces, i = 0..n   (i = 0, n: Dirichlet)
+//   v    n + 1 rows x P   horizontal ff faces, i = 0..n-1 (j = 0: interface,
+//                         j = n: Dirichlet)
+//   p_ff n     rows x P   ff cell centres
+//   p_pm n     rows x P   pm cell centres
+// A whole-system vector is [u | v | p_ff | p_pm]; the velocity block V is the
+// contiguous prefix [u | v]; the Darcy block D' is the suffix p_pm.  Padding
+// entries are zero in every vector and no kernel writes them.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sdk {
+
+struct Geom {
+  int n;        // cells per side
+  int P;        // row pitch in elements
+  long long ou, ov, opf, opm, len;  // field offsets and whole-vector length
+  long long lenV;                   // length of the velocity block [u | v]
+  long long lenD;                   // length of the Darcy block
+  double h;
+};
+
+inline Geom make_geom(int n) {
+  Geom g;
+  g.n = n;
+  g.P = ((n + 1) + 7) / 8 * 8;
+  g.ou = 0;
+  g.ov = (long long)n * g.P;
+  g.opf = (long long)(2 * n + 1) * g.P;
+  g.opm = (long long)(3 * n + 1) * g.P;
+  g.len = (long long)(4 * n + 1) * g.P;
+  g.lenV = g.opf;
+  g.lenD = (long long)n * g.P;
+  g.h = 1.0 / n;
+  return g;
+}
+
+// Coefficients of one level in precision T (Sec. 2 discretisation):
+//   w[i]  = mu / (h + 2 beta_i), beta_i = mean sqrt(K) of the two pm cells
+//           below interface u face i, over alpha_BJ (Eq. (6)); i = 1..n-1
+//   rg[i] = mu h^2 / (2 K_i) of the pm cell below v_Gamma face i (Eq. (5))
+//   Tx    n rows x P: TPFA transmissibility of the pm face left of cell i
+//         (i = 0 and i = n: no-flow sides, 0)
+//   Ty    (n+1) rows x P: face below cell row j (j = 0: Dirichlet bottom,
+//         2K/mu; j = n: interface, 0 -- the flux there is h v_Gamma)
+template <typename T>
+struct Coef {
+  int n, P;
+  T h, mu, cm;  // cm = h^2 / dt
+  const T* w;
+  const T* rg;
+  const T* Tx;
+  const T* Ty;
+};
+
+// ---------------------------------------------------------------- sd_ops.cu
+// setup
+void launch_coarsen_K(const double* Kf, int nf, int Pf, double* Kc, int Pc, cudaStream_t s);
+void launch_pack_K(const double* Kdense, int n, double* Kp, int P, cudaStream_t s);
+void launch_fill_K(double* K, int n, int P, double v, cudaStream_t s);
+template <typename T>
+void launch_setup_coef(const double* Kp, int n, int P, double mu, double alpha, T* w, T* rg, T* Tx, T* Ty,
+                       cudaStream_t s);
+template <typename T>
+void launch_convert(const double* src, T* dst, long long len, cudaStream_t s);
+
+// whole-system operator (FP64): y = A x  or  y = b - A x
+void launch_apply_full(const Coef<double>& c, const double* x, const double* b, double* y, cudaStream_t s);
+
+// right-hand side: b = mass * xprev + B0 + s1 * B1; also writes the Dirichlet
+// values of b into x (so that the identity rows start exact)
+void launch_rhs(const Geom& g, double cm, const double* B0, const double* B1, double s1, const double* xprev,
+                double* b, double* x, cudaStream_t s);
+// manufactured-solution data: B0 (time-derivative part of the forcing),
+// B1 (everything proportional to 1 + t), and the exact state at time t
+void launch_mms_terms(const Coef<double>& c, const double* Kp, double* B0, double* B1, cudaStream_t s);
+void launch_mms_exact(const Geom& g, double mu, double t, double* x, cudaStream_t s);
+
+// dense canonical layout <-> padded layout (whole-system vector)
+void launch_pack(const Geom& g, const double* dense, double* padded, cudaStream_t s);
+void launch_unpack(const Geom& g, const double* padded, double* dense, cudaStream_t s);
+
+// block smoothers / residuals / transfers (T = float or double)
+//   block V: velocity rows (u, v), identity on Dirichlet faces
+//   block D: Darcy rows p_pm
+// Chebyshev step: d = a d + c D^-1 (b - A x_in); x_out = x_in + d.
+//   x_in == nullptr means x_in = 0;  a == 0 means d is not read.
+template <typename T>
+void launch_cheb_V(const Coef<T>& c, const T* x_in, const T* b, T* d, T* x_out, T a, T cc, int nbatch,
+                   long long bstride, cudaStream_t s);
+template <typename T>
+void launch_cheb_D(const Coef<T>& c, const T* x_in, const T* b, T* d, T* x_out, T a, T cc, int nbatch,
+                   long long bstride, cudaStream_t s);
+// mode 0: r = b - A x (b == nullptr: r = -A x); 1: r = D^-1 A x; 2: r = A x
+template <typename T>
+void launch_resid_V(const Coef<T>& c, const T* x, const T* b, T* r, int jac, int nbatch, long long bstride,
+                    cudaStream_t s);
+template <typename T>
+void launch_resid_D(const Coef<T>& c, const T* x, const T* b, T* r, int jac, int nbatch, long long bstride,
+                    cudaStream_t s);
+// coarse rhs = R r with R the transposed bilinear (V) / cell-sum (D) transfer
+template <typename T>
+void launch_restrict_V(int nf, int Pf, const T* r, int nc, int Pc, T* bc, cudaStream_t s);
+template <typename T>
+void launch_restrict_D(int nf, int Pf, const T* r, int nc, int Pc, T* bc, cudaStream_t s);
+// x += P e (bilinear, staggered for V, cell-centred for D)
+template <typename T>
+void launch_prolong_V(int nf, int Pf, T* x, int nc, int Pc, const T* e, cudaStream_t s);
+template <typename T>
+void launch_prolong_D(int nf, int Pf, T* x, int nc, int Pc, const T* e, cudaStream_t s);
+
+// preconditioner glue on the fine level (Sec. 4 block preconditioners):
+//  entry: zpf = schur * r_pf + cmass * eP (eP: pressure-Laplacian solve, may be
+//  null); rV = T(r_v - B zpf) (B omitted: use_B == 0)
+template <typename T>
+void launch_precond_entry(const Coef<double>& c, const double* r, double* z, double schur, const T* eP, double cmass,
+                          int use_B, T* rV, cudaStream_t s);
+//  mid: z_v = double(eV); rD = T(r_pm - C'_1 z_v) (C'_1 omitted: use_C == 0)
+template <typename T>
+void launch_precond_mid(const Coef<double>& c, const double* r, double* z, const T* eV, int use_C, T* rD,
+                        cudaStream_t s);
+//  block Gauss-Seidel with identity on p_ff: z_pf = r_pf - C z_v
+template <typename T>
+void launch_precond_bgs_pff(const Coef<double>& c, const double* r, double* z, const T* eV, cudaStream_t s);
+//  exit: z_pm = double(eD)
+template <typename T>
+void launch_precond_exit(const Coef<double>& c, double* z, const T* eD, cudaStream_t s);
+
+// ------------------------------------------------------------- sd_krylov.cu
+int reduce_blocks(long long len);
+// partial[blk * kmax + i] = sum over the block's range of V_i . w, i < k
+void launch_mdot(const double* V, long long vstride, int k, const double* w, long long len, double* partial,
+                 int kmax, int nblk, cudaStream_t s);
+// w -= sum_i coef[i] V_i, then partial dots of V_i . w (mode 1) or w . w (mode 2)
+void launch_mupdate(const double* V, long long vstride, int k, const double* coef, double* w, long long len,
+                    double* partial, int kmax, int nblk, int mode, cudaStream_t s);
+// out[i] = sum_b partial[b * kmax + i] (+ out[i] if accumulate), fixed order
+void launch_reduce(const double* partial, int nblk, int k, int kmax, double* out, int accumulate, cudaStream_t s);
+// generic dot of two vectors: partials then reduce -> out[0]
+void launch_dot(const double* a, const double* b, long long len, double* partial, int nblk, double* out,
+                cudaStream_t s);
+// y = alpha_dev[0]^p * x  (p = -1: divide by sqrt(alpha) ... see implementation)
+void launch_scale_by(const double* x, double* y, long long len, const double* sdev, int mode, cudaStream_t s);
+void launch_axpy_multi(double* x, const double* Z, long long zstride, const double* ycoef, int k, long long len,
+                       cudaStream_t s);
+
+void launch_givens(double* st, int j, int m, const double* hcol1, const double* hcol2, const double* nrm2,
+                   double* flag, cudaStream_t s);
+void launch_backsolve(double* st, int k, int m, double* y, cudaStream_t s);
+void launch_init_cycle(double* st, int m, const double* beta2, double* flag, cudaStream_t s);
+
+// dense coarse solve: x[idx[k]] = T(sum_l Ainv[k][l] * b[idx[l]])
+template <typename T>
+void launch_dense_solve(const double* Ainv, const int* idx, int m, const T* b, T* x, cudaStream_t s);
+// in-place Gauss-Jordan inverse with partial pivoting, one CTA (setup only)
+void launch_gj_inverse(double* A, double* work, int m, int* status, cudaStream_t s);
+// identity batch in a padded layout: X[k * stride + idx[k]] = 1
+void launch_identity_batch(double* X, long long stride, const int* idx, int m, cudaStream_t s);
+void launch_gather_dense(const double* Y, long long stride, const int* idx, int m, double* A, cudaStream_t s);
+void launch_fill(double* x, double v, long long len, cudaStream_t s);
+void launch_hash_fill(double* x, long long len, unsigned seed, cudaStream_t s);
+
+}  // namespace sdk

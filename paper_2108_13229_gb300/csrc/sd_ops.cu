@@ -1,0 +1,880 @@
+// sd_ops.cu -- stencil kernels of the monolithic Stokes-Darcy solve
+// (arXiv 2108.13229): the coupled operator of Eq. (9), the velocity block V
+// and Darcy block D' used by the block preconditioners of Sec. 4, grid
+// transfers of their geometric multigrid V-cycles, the preconditioner glue,
+// coefficient setup and the implicit-Euler right-hand side.
+//
+// Discrete rows (every row integrated over its control volume, h = 1/n):
+//  u face (i,j), 1<=i<=n-1:  (h^2/dt) u + 2mu(2u - uE - uW)          [normal stress]
+//      + top corner:    mu(u - uN) - mu(vN,i - vN,i-1)   (j < n-1)
+//                       2mu u                             (j = n-1, wall at h/2)
+//      + bottom corner: mu(u - uS) + mu(v_i - v_i-1)      (j > 0)
+//                       h w_i (2u + vG_i - vG_i-1)        (j = 0, BJS slip of Eq. (6)
+//                                                          eliminated, w = mu/(h+2beta))
+//      + h (p_i - p_i-1)                                  [block B]
+//  v face (i,j), 1<=j<=n-1: symmetric to u, walls at x = 0, 1 at h/2.
+//  v_Gamma face i (j = 0): half control volume [1, 1+h/2] (Eq. (5)):
+//      (h^2/2dt + 2mu + mu h^2/(2K)) vG - 2mu v_i,1 + h p_ff - h p_pm[top]
+//      + (h/2)(tau_W - tau_E), tau at interface corners from the BJS slip,
+//        mu-only wall corners at x = 0, 1
+//  p_ff cell: h (uE - uW + vN - vS)                       [Eq. (2), block C]
+//  p_pm cell: sum_f T_f (p - p_nb) + h vG (top row)       [Eqs. (3),(4),(7); C'_1]
+//  Dirichlet velocity faces: identity rows, eliminated from all other rows.
+#include "sd_internal.cuh"
+
+#include <math.h>
+
+namespace sdk {
+
+static const int BX = 32, BY = 8;
+
+static inline dim3 grid2(int nx, int ny) { return dim3((nx + BX - 1) / BX, (ny + BY - 1) / BY); }
+
+// ------------------------------------------------------------------ rows
+// Off-diagonal part and diagonal of the velocity-block row of interior u face (i, j).
+template <typename T>
+__device__ __forceinline__ void u_row(const Coef<T>& c, const T* __restrict__ u, const T* __restrict__ v, int i,
+                                      int j, bool read, T& off, T& diag) {
+  const int n = c.n, P = c.P;
+  const T mu = c.mu, h = c.h;
+  T dg = c.cm + T(4) * mu, of = T(0);
+  if (read) {
+    if (i - 1 >= 1) of -= T(2) * mu * u[j * P + i - 1];
+    if (i + 1 <= n - 1) of -= T(2) * mu * u[j * P + i + 1];
+  }
+  if (j < n - 1) {
+    dg += mu;
+    if (read) of += -mu * u[(j + 1) * P + i] - mu * v[(j + 1) * P + i] + mu * v[(j + 1) * P + i - 1];
+  } else {
+    dg += T(2) * mu;
+  }
+  if (j > 0) {
+    dg += mu;
+    if (read) of += -mu * u[(j - 1) * P + i] + mu * v[j * P + i] - mu * v[j * P + i - 1];
+  } else {
+    const T wh = c.w[i] * h;
+    dg += T(2) * wh;
+    if (read) of += wh * (v[i] - v[i - 1]);
+  }
+  off = of;
+  diag = dg;
+}
+
+// Same for the v face (i, j), 0 <= j <= n-1 (j = 0: interface half control volume).
+template <typename T>
+__device__ __forceinline__ void v_row(const Coef<T>& c, const T* __restrict__ u, const T* __restrict__ v, int i,
+                                      int j, bool read, T& off, T& diag) {
+  const int n = c.n, P = c.P;
+  const T mu = c.mu, h = c.h;
+  T dg, of = T(0);
+  if (j == 0) {
+    dg = T(0.5) * c.cm + T(2) * mu + c.rg[i];
+    if (read) of -= T(2) * mu * v[P + i];
+    if (i > 0) {
+      const T w = c.w[i];
+      dg += T(0.5) * h * w;
+      if (read) of += w * h * u[i] - T(0.5) * h * w * v[i - 1];
+    } else {
+      dg += mu;
+    }
+    if (i < n - 1) {
+      const T w = c.w[i + 1];
+      dg += T(0.5) * h * w;
+      if (read) of += -w * h * u[i + 1] - T(0.5) * h * w * v[i + 1];
+    } else {
+      dg += mu;
+    }
+  } else {
+    dg = c.cm + T(4) * mu;
+    if (read) {
+      of -= T(2) * mu * v[(j - 1) * P + i];
+      if (j + 1 <= n - 1) of -= T(2) * mu * v[(j + 1) * P + i];
+    }
+    if (i < n - 1) {
+      dg += mu;
+      if (read) of += -mu * v[j * P + i + 1] - mu * u[j * P + i + 1] + mu * u[(j - 1) * P + i + 1];
+    } else {
+      dg += T(2) * mu;
+    }
+    if (i > 0) {
+      dg += mu;
+      if (read) of += -mu * v[j * P + i - 1] + mu * u[j * P + i] - mu * u[(j - 1) * P + i];
+    } else {
+      dg += T(2) * mu;
+    }
+  }
+  off = of;
+  diag = dg;
+}
+
+// Darcy row of pm cell (i, j) (D' block only, no interface flux).
+template <typename T>
+__device__ __forceinline__ void d_row(const Coef<T>& c, const T* __restrict__ p, int i, int j, bool read, T& off,
+                                      T& diag) {
+  const int n = c.n, P = c.P;
+  const T tw = c.Tx[j * P + i], te = c.Tx[j * P + i + 1];
+  const T ts = c.Ty[j * P + i], tn = c.Ty[(j + 1) * P + i];
+  diag = tw + te + ts + tn;
+  T of = T(0);
+  if (read) {
+    if (i > 0) of -= tw * p[j * P + i - 1];
+    if (i < n - 1) of -= te * p[j * P + i + 1];
+    if (j > 0) of -= ts * p[(j - 1) * P + i];
+    if (j < n - 1) of -= tn * p[(j + 1) * P + i];
+  }
+  off = of;
+}
+
+// ------------------------------------------------------- whole operator (K1)
+__global__ void k_apply_full(Coef<double> c, const double* __restrict__ x, const double* __restrict__ b,
+                             double* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int n = c.n, P = c.P;
+  if (i > n || j > n) return;
+  const double h = c.h;
+  const double* u = x;
+  const double* v = x + (long long)n * P;
+  const double* pf = x + (long long)(2 * n + 1) * P;
+  const double* pm = x + (long long)(3 * n + 1) * P;
+  if (j < n) {
+    const long long k = (long long)j * P + i;
+    double val;
+    if (i == 0 || i == n) {
+      val = u[k];
+    } else {
+      double off, dg;
+      u_row(c, u, v, i, j, true, off, dg);
+      val = dg * u[k] + off + h * (pf[k] - pf[k - 1]);
+    }
+    y[k] = b ? b[k] - val : val;
+  }
+  if (i < n) {
+    const long long kv = (long long)j * P + i;
+    const long long k = (long long)n * P + kv;
+    double val;
+    if (j == n) {
+      val = v[kv];
+    } else {
+      double off, dg;
+      v_row(c, u, v, i, j, true, off, dg);
+      val = dg * v[kv] + off;
+      if (j > 0) val += h * (pf[kv] - pf[kv - P]);
+      else val += h * pf[i] - h * pm[(long long)(n - 1) * P + i];
+    }
+    y[k] = b ? b[k] - val : val;
+  }
+  if (i < n && j < n) {
+    const long long kc = (long long)j * P + i;
+    double s = -v[kc];
+    if (i + 1 <= n - 1) s += u[kc + 1];
+    if (i >= 1) s -= u[kc];
+    if (j + 1 <= n - 1) s += v[kc + P];
+    const long long kp = (long long)(2 * n + 1) * P + kc;
+    y[kp] = b ? b[kp] - h * s : h * s;
+    double off, dg;
+    d_row(c, pm, i, j, true, off, dg);
+    double val = dg * pm[kc] + off;
+    if (j == n - 1) val += h * v[i];
+    const long long km = (long long)(3 * n + 1) * P + kc;
+    y[km] = b ? b[km] - val : val;
+  }
+}
+
+void launch_apply_full(const Coef<double>& c, const double* x, const double* b, double* y, cudaStream_t s) {
+  k_apply_full<<<grid2(c.n + 1, c.n + 1), dim3(BX, BY), 0, s>>>(c, x, b, y);
+}
+
+// ------------------------------------------------------ block V smoothers
+template <typename T>
+__global__ void k_cheb_V(Coef<T> c, const T* __restrict__ xin, const T* __restrict__ b, T* __restrict__ d,
+                         T* __restrict__ xout, T a, T cc, long long bstride) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int n = c.n, P = c.P;
+  if (i > n || j > n) return;
+  const long long bo = (long long)blockIdx.z * bstride;
+  const T* u = xin ? xin + bo : nullptr;
+  const T* v = xin ? xin + bo + (long long)n * P : nullptr;
+  const bool rd = xin != nullptr;
+  if (j < n) {
+    const long long k = bo + (long long)j * P + i;
+    if (i == 0 || i == n) {
+      xout[k] = b[k];
+      d[k] = T(0);
+    } else {
+      T off, dg;
+      u_row(c, u, v, i, j, rd, off, dg);
+      const T xc = rd ? xin[k] : T(0);
+      const T r = b[k] - (dg * xc + off);
+      const T dn = (a != T(0) ? a * d[k] : T(0)) + cc * r / dg;
+      d[k] = dn;
+      xout[k] = xc + dn;
+    }
+  }
+  if (i < n) {
+    const long long k = bo + (long long)n * P + (long long)j * P + i;
+    if (j == n) {
+      xout[k] = b[k];
+      d[k] = T(0);
+    } else {
+      T off, dg;
+      v_row(c, u, v, i, j, rd, off, dg);
+      const T xc = rd ? xin[k] : T(0);
+      const T r = b[k] - (dg * xc + off);
+      const T dn = (a != T(0) ? a * d[k] : T(0)) + cc * r / dg;
+      d[k] = dn;
+      xout[k] = xc + dn;
+    }
+  }
+}
+
+template <typename T>
+void launch_cheb_V(const Coef<T>& c, const T* x_in, const T* b, T* d, T* x_out, T a, T cc, int nbatch,
+                   long long bstride, cudaStream_t s) {
+  dim3 g = grid2(c.n + 1, c.n + 1);
+  g.z = nbatch;
+  k_cheb_V<T><<<g, dim3(BX, BY), 0, s>>>(c, x_in, b, d, x_out, a, cc, bstride);
+}
+
+template <typename T>
+__global__ void k_resid_V(Coef<T> c, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, int jac,
+                          long long bstride) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int n = c.n, P = c.P;
+  if (i > n || j > n) return;
+  const long long bo = (long long)blockIdx.z * bstride;
+  const T* u = x + bo;
+  const T* v = x + bo + (long long)n * P;
+  if (j < n) {
+    const long long k = bo + (long long)j * P + i;
+    T ax, dg = T(1);
+    if (i == 0 || i == n) {
+      ax = x[k];
+    } else {
+      T off;
+      u_row(c, u, v, i, j, true, off, dg);
+      ax = dg * x[k] + off;
+    }
+    r[k] = jac == 1 ? ax / dg : (jac == 2 ? ax : (b ? b[k] - ax : -ax));
+  }
+  if (i < n) {
+    const long long k = bo + (long long)n * P + (long long)j * P + i;
+    T ax, dg = T(1);
+    if (j == n) {
+      ax = x[k];
+    } else {
+      T off;
+      v_row(c, u, v, i, j, true, off, dg);
+      ax = dg * x[k] + off;
+    }
+    r[k] = jac == 1 ? ax / dg : (jac == 2 ? ax : (b ? b[k] - ax : -ax));
+  }
+}
+
+template <typename T>
+void launch_resid_V(const Coef<T>& c, const T* x, const T* b, T* r, int jac, int nbatch, long long bstride,
+                    cudaStream_t s) {
+  dim3 g = grid2(c.n + 1, c.n + 1);
+  g.z = nbatch;
+  k_resid_V<T><<<g, dim3(BX, BY), 0, s>>>(c, x, b, r, jac, bstride);
+}
+
+// ------------------------------------------------------ block D' smoothers
+template <typename T>
+__global__ void k_cheb_D(Coef<T> c, const T* __restrict__ xin, const T* __restrict__ b, T* __restrict__ d,
+                         T* __restrict__ xout, T a, T cc, long long bstride) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int n = c.n, P = c.P;
+  if (i >= n || j >= n) return;
+  const long long bo = (long long)blockIdx.z * bstride;
+  const long long k = bo + (long long)j * P + i;
+  const bool rd = xin != nullptr;
+  T off, dg;
+  d_row(c, rd ? xin + bo : nullptr, i, j, rd, off, dg);
+  const T xc = rd ? xin[k] : T(0);
+  const T r = b[k] - (dg * xc + off);
+  const T dn = (a != T(0) ? a * d[k] : T(0)) + cc * r / dg;
+  d[k] = dn;
+  xout[k] = xc + dn;
+}
+
+template <typename T>
+void launch_cheb_D(const Coef<T>& c, const T* x_in, const T* b, T* d, T* x_out, T a, T cc, int nbatch,
+                   long long bstride, cudaStream_t s) {
+  dim3 g = grid2(c.n, c.n);
+  g.z = nbatch;
+  k_cheb_D<T><<<g, dim3(BX, BY), 0, s>>>(c, x_in, b, d, x_out, a, cc, bstride);
+}
+
+template <typename T>
+__global__ void k_resid_D(Coef<T> c, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, int jac,
+                          long long bstride) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int n = c.n, P = c.P;
+  if (i >= n || j >= n) return;
+  const long long bo = (long long)blockIdx.z * bstride;
+  const long long k = bo + (long long)j * P + i;
+  T off, dg;
+  d_row(c, x + bo, i, j, true, off, dg);
+  const T ax = dg * x[k] + off;
+  r[k] = jac == 1 ? ax / dg : (jac == 2 ? ax : (b ? b[k] - ax : -ax));
+}
+
+template <typename T>
+void launch_resid_D(const Coef<T>& c, const T* x, const T* b, T* r, int jac, int nbatch, long long bstride,
+                    cudaStream_t s) {
+  dim3 g = grid2(c.n, c.n);
+  g.z = nbatch;
+  k_resid_D<T><<<g, dim3(BX, BY), 0, s>>>(c, x, b, r, jac, bstride);
+}
+
+// ------------------------------------------------------------ transfers
+// Prolongation of the velocity block is bilinear on the staggered grid:
+//  u: linear in x between coarse faces (Dirichlet faces carry 0), cell-centred
+//     in y with weights 3/4, 1/4; below coarse row 0 (the interface) the
+//     ghost equals row 0, above the top row (wall) it is the negative.
+//  v: linear in y between coarse faces (the Dirichlet top carries 0),
+//     cell-centred in x with weights 3/4, 1/4 and negative ghosts at the walls.
+// Restriction is its transpose applied to the fine residual.
+template <typename T>
+__global__ void k_restrict_V(int nf, int Pf, const T* __restrict__ r, int nc, int Pc, T* __restrict__ bc) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I > nc || J > nc) return;
+  const T* ru = r;
+  const T* rv = r + (long long)nf * Pf;
+  if (J < nc) {
+    T s = T(0);
+    if (I > 0 && I < nc) {
+      int rows[4];
+      T wy[4];
+      rows[0] = 2 * J - 1; wy[0] = J >= 1 ? T(0.25) : T(0);
+      rows[1] = 2 * J;     wy[1] = J == 0 ? T(1) : T(0.75);
+      rows[2] = 2 * J + 1; wy[2] = J == nc - 1 ? T(0.5) : T(0.75);
+      rows[3] = 2 * J + 2; wy[3] = J <= nc - 2 ? T(0.25) : T(0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (wy[q] == T(0)) continue;
+        const T* row = ru + (long long)rows[q] * Pf;
+        s += wy[q] * (row[2 * I] + T(0.5) * (row[2 * I - 1] + row[2 * I + 1]));
+      }
+    }
+    bc[(long long)J * Pc + I] = s;
+  }
+  if (I < nc) {
+    T s = T(0);
+    if (J < nc) {
+      int cols[4];
+      T wx[4];
+      cols[0] = 2 * I - 1; wx[0] = I >= 1 ? T(0.25) : T(0);
+      cols[1] = 2 * I;     wx[1] = I == 0 ? T(0.5) : T(0.75);
+      cols[2] = 2 * I + 1; wx[2] = I == nc - 1 ? T(0.5) : T(0.75);
+      cols[3] = 2 * I + 2; wx[3] = I <= nc - 2 ? T(0.25) : T(0);
+      const T* r0 = rv + (long long)(2 * J) * Pf;
+      const T* r1 = rv + (long long)(2 * J + 1) * Pf;
+      const T* rm = J >= 1 ? rv + (long long)(2 * J - 1) * Pf : nullptr;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (wx[q] == T(0)) continue;
+        const int ci = cols[q];
+        T t = r0[ci] + T(0.5) * r1[ci];
+        if (rm) t += T(0.5) * rm[ci];
+        s += wx[q] * t;
+      }
+    }
+    bc[(long long)nc * Pc + (long long)J * Pc + I] = s;
+  }
+}
+
+template <typename T>
+void launch_restrict_V(int nf, int Pf, const T* r, int nc, int Pc, T* bc, cudaStream_t s) {
+  k_restrict_V<T><<<grid2(nc + 1, nc + 1), dim3(BX, BY), 0, s>>>(nf, Pf, r, nc, Pc, bc);
+}
+
+template <typename T>
+__global__ void k_restrict_D(int nf, int Pf, const T* __restrict__ r, int nc, int Pc, T* __restrict__ bc) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I >= nc || J >= nc) return;
+  const T* r0 = r + (long long)(2 * J) * Pf + 2 * I;
+  bc[(long long)J * Pc + I] = (r0[0] + r0[1]) + (r0[Pf] + r0[Pf + 1]);
+}
+
+template <typename T>
+void launch_restrict_D(int nf, int Pf, const T* r, int nc, int Pc, T* bc, cudaStream_t s) {
+  k_restrict_D<T><<<grid2(nc, nc), dim3(BX, BY), 0, s>>>(nf, Pf, r, nc, Pc, bc);
+}
+
+template <typename T>
+__device__ __forceinline__ T cu_at(const T* eu, int nc, int Pc, int I, int J) {
+  // coarse u with zero Dirichlet faces and the y ghosts described above
+  if (I <= 0 || I >= nc) return T(0);
+  if (J < 0) J = 0;
+  if (J > nc - 1) return -eu[(long long)(nc - 1) * Pc + I];
+  return eu[(long long)J * Pc + I];
+}
+template <typename T>
+__device__ __forceinline__ T cv_at(const T* ev, int nc, int Pc, int I, int J) {
+  if (J >= nc) return T(0);
+  if (I < 0) return -ev[(long long)J * Pc];
+  if (I > nc - 1) return -ev[(long long)J * Pc + nc - 1];
+  return ev[(long long)J * Pc + I];
+}
+
+template <typename T>
+__global__ void k_prolong_V(int nf, int Pf, T* __restrict__ x, int nc, int Pc, const T* __restrict__ e) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > nf || j > nf) return;
+  const T* eu = e;
+  const T* ev = e + (long long)nc * Pc;
+  if (j < nf && i > 0 && i < nf) {
+    const int J = j >> 1, Jn = (j & 1) ? J + 1 : J - 1;
+    T cy0, cy1;
+    if (i & 1) {
+      const int I = i >> 1;
+      cy0 = T(0.5) * (cu_at(eu, nc, Pc, I, J) + cu_at(eu, nc, Pc, I + 1, J));
+      cy1 = T(0.5) * (cu_at(eu, nc, Pc, I, Jn) + cu_at(eu, nc, Pc, I + 1, Jn));
+    } else {
+      const int I = i >> 1;
+      cy0 = cu_at(eu, nc, Pc, I, J);
+      cy1 = cu_at(eu, nc, Pc, I, Jn);
+    }
+    x[(long long)j * Pf + i] += T(0.75) * cy0 + T(0.25) * cy1;
+  }
+  if (i < nf && j < nf) {
+    const int I = i >> 1, In = (i & 1) ? I + 1 : I - 1;
+    T cx0, cx1;
+    if (j & 1) {
+      const int J = j >> 1;
+      cx0 = T(0.5) * (cv_at(ev, nc, Pc, I, J) + cv_at(ev, nc, Pc, I, J + 1));
+      cx1 = T(0.5) * (cv_at(ev, nc, Pc, In, J) + cv_at(ev, nc, Pc, In, J + 1));
+    } else {
+      const int J = j >> 1;
+      cx0 = cv_at(ev, nc, Pc, I, J);
+      cx1 = cv_at(ev, nc, Pc, In, J);
+    }
+    x[(long long)nf * Pf + (long long)j * Pf + i] += T(0.75) * cx0 + T(0.25) * cx1;
+  }
+}
+
+template <typename T>
+void launch_prolong_V(int nf, int Pf, T* x, int nc, int Pc, const T* e, cudaStream_t s) {
+  k_prolong_V<T><<<grid2(nf + 1, nf + 1), dim3(BX, BY), 0, s>>>(nf, Pf, x, nc, Pc, e);
+}
+
+template <typename T>
+__device__ __forceinline__ T cd_at(const T* e, int nc, int Pc, int I, int J) {
+  // lateral sides and top of D' are no-flow (mirror), the bottom is Dirichlet (negative mirror)
+  if (I < 0) I = 0;
+  if (I > nc - 1) I = nc - 1;
+  if (J < 0) return -e[I];
+  if (J > nc - 1) J = nc - 1;
+  return e[(long long)J * Pc + I];
+}
+
+template <typename T>
+__global__ void k_prolong_D(int nf, int Pf, T* __restrict__ x, int nc, int Pc, const T* __restrict__ e) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= nf || j >= nf) return;
+  const int I = i >> 1, J = j >> 1;
+  const int In = (i & 1) ? I + 1 : I - 1, Jn = (j & 1) ? J + 1 : J - 1;
+  const T val = T(0.5625) * cd_at(e, nc, Pc, I, J) + T(0.1875) * (cd_at(e, nc, Pc, In, J) + cd_at(e, nc, Pc, I, Jn)) +
+                T(0.0625) * cd_at(e, nc, Pc, In, Jn);
+  x[(long long)j * Pf + i] += val;
+}
+
+template <typename T>
+void launch_prolong_D(int nf, int Pf, T* x, int nc, int Pc, const T* e, cudaStream_t s) {
+  k_prolong_D<T><<<grid2(nf, nf), dim3(BX, BY), 0, s>>>(nf, Pf, x, nc, Pc, e);
+}
+
+// ------------------------------------------------------ preconditioner glue
+// Block upper-triangular Stokes part (Sec. 4, zero block replaced by the
+// Schur approximation S^ = h^2/(2 mu) I, or by I): z_pf = schur * r_pf,
+// then the velocity rhs r_v - B z_pf for the V-block multigrid.
+template <typename T>
+__global__ void k_precond_entry(Coef<double> c, const double* __restrict__ r, double* __restrict__ z, double schur,
+                                const T* __restrict__ eP, double cmass, int useB, T* __restrict__ rV) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int n = c.n, P = c.P;
+  if (i > n || j > n) return;
+  const double h = c.h;
+  const double* rpf = r + (long long)(2 * n + 1) * P;
+  // z_pf at cell kc: schur * r_pf (+ cmass * eP, the pressure-Laplacian part)
+  auto zp = [&](long long kc) { return schur * rpf[kc] + (eP ? cmass * (double)eP[kc] : 0.0); };
+  if (i < n && j < n) z[(long long)(2 * n + 1) * P + (long long)j * P + i] = zp((long long)j * P + i);
+  if (j < n) {
+    const long long k = (long long)j * P + i;
+    double val = r[k];
+    if (useB && i > 0 && i < n) val -= h * (zp(k) - zp(k - 1));
+    rV[k] = (T)val;
+  }
+  if (i < n) {
+    const long long kv = (long long)j * P + i;
+    const long long k = (long long)n * P + kv;
+    double val = r[k];
+    if (useB && j < n) {
+      if (j > 0) val -= h * (zp(kv) - zp(kv - P));
+      else val -= h * zp(i);
+    }
+    rV[k] = (T)val;
+  }
+}
+
+template <typename T>
+void launch_precond_entry(const Coef<double>& c, const double* r, double* z, double schur, const T* eP, double cmass,
+                          int use_B, T* rV, cudaStream_t s) {
+  k_precond_entry<T><<<grid2(c.n + 1, c.n + 1), dim3(BX, BY), 0, s>>>(c, r, z, schur, eP, cmass, use_B, rV);
+}
+
+template <typename T>
+__global__ void k_precond_mid(Coef<double> c, const double* __restrict__ r, double* __restrict__ z,
+                              const T* __restrict__ eV, int useC, T* __restrict__ rD) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int n = c.n, P = c.P;
+  if (i > n || j > n) return;
+  if (j < n) {
+    const long long k = (long long)j * P + i;
+    z[k] = (double)eV[k];
+  }
+  if (i < n) {
+    const long long k = (long long)n * P + (long long)j * P + i;
+    z[k] = (double)eV[k];
+  }
+  if (i < n && j < n) {
+    const long long kc = (long long)j * P + i;
+    double val = r[(long long)(3 * n + 1) * P + kc];
+    if (useC && j == n - 1) val -= c.h * (double)eV[(long long)n * P + i];
+    rD[kc] = (T)val;
+  }
+}
+
+template <typename T>
+void launch_precond_mid(const Coef<double>& c, const double* r, double* z, const T* eV, int use_C, T* rD,
+                        cudaStream_t s) {
+  k_precond_mid<T><<<grid2(c.n + 1, c.n + 1), dim3(BX, BY), 0, s>>>(c, r, z, eV, use_C, rD);
+}
+
+template <typename T>
+__global__ void k_precond_exit(int n, int P, double* __restrict__ z, const T* __restrict__ eD) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= n || j >= n) return;
+  const long long kc = (long long)j * P + i;
+  z[(long long)(3 * n + 1) * P + kc] = (double)eD[kc];
+}
+
+template <typename T>
+void launch_precond_exit(const Coef<double>& c, double* z, const T* eD, cudaStream_t s) {
+  k_precond_exit<T><<<grid2(c.n, c.n), dim3(BX, BY), 0, s>>>(c.n, c.P, z, eD);
+}
+
+// P^pv_BGS(P_V, P_D') of Sec. 4: after z_v = P_V r_v, the identity block
+// gives z_pf = r_pf - C z_v (C: the continuity rows of Eq. (2)).
+template <typename T>
+__global__ void k_precond_bgs_pff(Coef<double> c, const double* __restrict__ r, double* __restrict__ z,
+                                  const T* __restrict__ eV) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int n = c.n, P = c.P;
+  if (i >= n || j >= n) return;
+  const long long kc = (long long)j * P + i;
+  const T* u = eV;
+  const T* v = eV + (long long)n * P;
+  double s = -(double)v[kc];
+  if (i + 1 <= n - 1) s += (double)u[kc + 1];
+  if (i >= 1) s -= (double)u[kc];
+  if (j + 1 <= n - 1) s += (double)v[kc + P];
+  const long long kp = (long long)(2 * n + 1) * P + kc;
+  z[kp] = r[kp] - c.h * s;
+}
+
+template <typename T>
+void launch_precond_bgs_pff(const Coef<double>& c, const double* r, double* z, const T* eV, cudaStream_t s) {
+  k_precond_bgs_pff<T><<<grid2(c.n, c.n), dim3(BX, BY), 0, s>>>(c, r, z, eV);
+}
+
+// ------------------------------------------------------------------ setup
+__global__ void k_pack_K(const double* __restrict__ Kd, int n, double* __restrict__ Kp, int P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= n || j >= n) return;
+  Kp[(long long)j * P + i] = Kd[(long long)j * n + i];
+}
+void launch_pack_K(const double* Kdense, int n, double* Kp, int P, cudaStream_t s) {
+  k_pack_K<<<grid2(n, n), dim3(BX, BY), 0, s>>>(Kdense, n, Kp, P);
+}
+
+__global__ void k_fill_K(double* __restrict__ K, int n, int P, double v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= n || j >= n) return;
+  K[(long long)j * P + i] = v;
+}
+void launch_fill_K(double* K, int n, int P, double v, cudaStream_t s) {
+  k_fill_K<<<grid2(n, n), dim3(BX, BY), 0, s>>>(K, n, P, v);
+}
+
+// coarse permeability: geometric mean of the 2 x 2 children
+__global__ void k_coarsen_K(const double* __restrict__ Kf, int nf, int Pf, double* __restrict__ Kc, int Pc) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int nc = nf / 2;
+  if (I >= nc || J >= nc) return;
+  const double* k0 = Kf + (long long)(2 * J) * Pf + 2 * I;
+  Kc[(long long)J * Pc + I] = sqrt(sqrt(k0[0] * k0[1] * k0[Pf] * k0[Pf + 1]));
+}
+void launch_coarsen_K(const double* Kf, int nf, int Pf, double* Kc, int Pc, cudaStream_t s) {
+  k_coarsen_K<<<grid2(nf / 2, nf / 2), dim3(BX, BY), 0, s>>>(Kf, nf, Pf, Kc, Pc);
+}
+
+template <typename T>
+__global__ void k_setup_coef(const double* __restrict__ K, int n, int P, double mu, double alpha, T* w, T* rg, T* Tx,
+                             T* Ty) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > n || j > n) return;
+  const double h = 1.0 / n;
+  if (j < n) {  // x faces of pm row j
+    double t = 0.0;
+    if (i > 0 && i < n) {
+      const double ka = K[(long long)j * P + i - 1], kb = K[(long long)j * P + i];
+      t = 2.0 * ka * kb / (ka + kb) / mu;
+    }
+    Tx[(long long)j * P + i] = (T)t;
+  }
+  if (i < n) {  // y faces below pm row j
+    double t = 0.0;
+    if (j == 0) t = 2.0 * K[i] / mu;
+    else if (j < n) {
+      const double ka = K[(long long)(j - 1) * P + i], kb = K[(long long)j * P + i];
+      t = 2.0 * ka * kb / (ka + kb) / mu;
+    }
+    Ty[(long long)j * P + i] = (T)t;
+  }
+  if (j == 0) {
+    const double* top = K + (long long)(n - 1) * P;
+    if (i > 0 && i < n) {
+      const double beta = 0.5 * (sqrt(top[i - 1]) + sqrt(top[i])) / alpha;
+      w[i] = (T)(mu / (h + 2.0 * beta));
+    } else {
+      w[i] = (T)0;
+    }
+    if (i < n) rg[i] = (T)(mu * h * h / (2.0 * top[i]));
+  }
+}
+
+template <typename T>
+void launch_setup_coef(const double* Kp, int n, int P, double mu, double alpha, T* w, T* rg, T* Tx, T* Ty,
+                       cudaStream_t s) {
+  k_setup_coef<T><<<grid2(n + 1, n + 1), dim3(BX, BY), 0, s>>>(Kp, n, P, mu, alpha, w, rg, Tx, Ty);
+}
+
+template <typename T>
+__global__ void k_convert(const double* __restrict__ a, T* __restrict__ b, long long len) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < len; k += (long long)gridDim.x * blockDim.x)
+    b[k] = (T)a[k];
+}
+template <typename T>
+void launch_convert(const double* src, T* dst, long long len, cudaStream_t s) {
+  long long nb = (len + 255) / 256;
+  if (nb > 4096) nb = 4096;
+  if (nb < 1) nb = 1;
+  k_convert<T><<<(int)nb, 256, 0, s>>>(src, dst, len);
+}
+
+// ------------------------------------------------- manufactured solution
+// psi = sin(pi x) phi(y), phi = 1 + A(y-1) + (y-1)^2, A = pi^2 + 2;
+// u = psi_y, v = -psi_x, p_ff = cos(pi x)(1 - 2 mu pi A), p_pm = cos(pi x) e^{pi(y-1)},
+// every field times s = 1 + t.  The momentum source f = dv/dt - mu lap v + grad p
+// splits as f = f0 + s f1 with f0 = (U0, V0) (the time derivative) and
+// f1 = (mu pi^2 U0 - pi c0 sin(pi x), -mu pi cos(pi x)(pi^2 phi - 2)).
+#define SD_PI 3.14159265358979323846
+__device__ __forceinline__ double mm_A() { return SD_PI * SD_PI + 2.0; }
+__device__ __forceinline__ double mm_phi(double y) { const double s = y - 1.0; return 1.0 + mm_A() * s + s * s; }
+__device__ __forceinline__ double mm_U0(double x, double y) { return sin(SD_PI * x) * (mm_A() + 2.0 * (y - 1.0)); }
+__device__ __forceinline__ double mm_V0(double x, double y) { return -SD_PI * cos(SD_PI * x) * mm_phi(y); }
+__device__ __forceinline__ double mm_Pff0(double x, double mu) { return cos(SD_PI * x) * (1.0 - 2.0 * mu * SD_PI * mm_A()); }
+__device__ __forceinline__ double mm_Ppm0(double x, double y) { return cos(SD_PI * x) * exp(SD_PI * (y - 1.0)); }
+__device__ __forceinline__ double mm_f1x(double x, double y, double mu) {
+  return mu * SD_PI * SD_PI * mm_U0(x, y) - SD_PI * (1.0 - 2.0 * mu * SD_PI * mm_A()) * sin(SD_PI * x);
+}
+__device__ __forceinline__ double mm_f1y(double x, double y, double mu) {
+  return -mu * SD_PI * cos(SD_PI * x) * (SD_PI * SD_PI * mm_phi(y) - 2.0);
+}
+
+// B0: time-derivative part of the integrated source; B1: all terms proportional
+// to s = 1 + t (rest of the source, boundary data moved to the right-hand side,
+// Dirichlet values of the identity rows).
+__global__ void k_mms_terms(Coef<double> c, const double* __restrict__ K, double* __restrict__ B0,
+                            double* __restrict__ B1) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int n = c.n, P = c.P;
+  if (i > n || j > n) return;
+  const double h = c.h, mu = c.mu, h2 = h * h;
+  if (j < n) {  // u face (i, j)
+    const long long k = (long long)j * P + i;
+    const double x = i * h, y = 1.0 + (j + 0.5) * h;
+    double b0 = 0.0, b1;
+    if (i == 0 || i == n) {
+      b1 = mm_U0(x, y);
+    } else {
+      b0 = h2 * mm_U0(x, y);
+      b1 = h2 * mm_f1x(x, y, mu);
+      if (i == 1) b1 += 2.0 * mu * mm_U0(0.0, y);
+      if (i == n - 1) b1 += 2.0 * mu * mm_U0(1.0, y);
+      if (j == n - 1) b1 += 2.0 * mu * mm_U0(x, 2.0) + mu * (mm_V0(x + 0.5 * h, 2.0) - mm_V0(x - 0.5 * h, 2.0));
+    }
+    B0[k] = b0;
+    B1[k] = b1;
+  }
+  if (i < n) {  // v face (i, j)
+    const long long k = (long long)n * P + (long long)j * P + i;
+    const double x = (i + 0.5) * h, y = 1.0 + j * h;
+    double b0 = 0.0, b1;
+    if (j == n) {
+      b1 = mm_V0(x, 2.0);
+    } else if (j == 0) {
+      b0 = 0.5 * h2 * mm_V0(x, 1.0);
+      b1 = 0.5 * h2 * mm_f1y(x, 1.0, mu);
+      if (i == 0) b1 += -mu * (mm_U0(0.0, 1.0 + 0.5 * h) - mm_U0(0.0, 1.0)) + mu * mm_V0(0.0, 1.0);
+      if (i == n - 1) b1 += mu * (mm_U0(1.0, 1.0 + 0.5 * h) - mm_U0(1.0, 1.0)) + mu * mm_V0(1.0, 1.0);
+    } else {
+      b0 = h2 * mm_V0(x, y);
+      b1 = h2 * mm_f1y(x, y, mu);
+      if (j == n - 1) b1 += 2.0 * mu * mm_V0(x, 2.0);
+      if (i == 0) b1 += 2.0 * mu * mm_V0(0.0, y) - mu * (mm_U0(0.0, y + 0.5 * h) - mm_U0(0.0, y - 0.5 * h));
+      if (i == n - 1) b1 += 2.0 * mu * mm_V0(1.0, y) + mu * (mm_U0(1.0, y + 0.5 * h) - mm_U0(1.0, y - 0.5 * h));
+    }
+    B0[k] = b0;
+    B1[k] = b1;
+  }
+  if (i < n && j < n) {
+    const long long kc = (long long)j * P + i;
+    const double y = 1.0 + (j + 0.5) * h, x = (i + 0.5) * h;
+    double s = 0.0;
+    if (i == 0) s += h * mm_U0(0.0, y);
+    if (i == n - 1) s -= h * mm_U0(1.0, y);
+    if (j == n - 1) s -= h * mm_V0(x, 2.0);
+    B0[(long long)(2 * n + 1) * P + kc] = 0.0;
+    B1[(long long)(2 * n + 1) * P + kc] = s;
+    double sp = 0.0;
+    if (j == 0) sp = 2.0 * K[i] / mu * mm_Ppm0(x, 0.0);
+    B0[(long long)(3 * n + 1) * P + kc] = 0.0;
+    B1[(long long)(3 * n + 1) * P + kc] = sp;
+  }
+}
+
+void launch_mms_terms(const Coef<double>& c, const double* Kp, double* B0, double* B1, cudaStream_t s) {
+  k_mms_terms<<<grid2(c.n + 1, c.n + 1), dim3(BX, BY), 0, s>>>(c, Kp, B0, B1);
+}
+
+__global__ void k_mms_exact(int n, int P, double mu, double t, double* __restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > n || j > n) return;
+  const double h = 1.0 / n, s = 1.0 + t;
+  if (j < n) x[(long long)j * P + i] = s * mm_U0(i * h, 1.0 + (j + 0.5) * h);
+  if (i < n) x[(long long)n * P + (long long)j * P + i] = s * mm_V0((i + 0.5) * h, 1.0 + j * h);
+  if (i < n && j < n) {
+    const long long kc = (long long)j * P + i;
+    x[(long long)(2 * n + 1) * P + kc] = s * mm_Pff0((i + 0.5) * h, mu);
+    x[(long long)(3 * n + 1) * P + kc] = s * mm_Ppm0((i + 0.5) * h, (j + 0.5) * h);
+  }
+}
+
+void launch_mms_exact(const Geom& g, double mu, double t, double* x, cudaStream_t s) {
+  k_mms_exact<<<grid2(g.n + 1, g.n + 1), dim3(BX, BY), 0, s>>>(g.n, g.P, mu, t, x);
+}
+
+// b = mass * xprev + B0 + s1 * B1 (mass = h^2/dt on velocity rows, half on
+// v_Gamma, 0 elsewhere); Dirichlet rows of x take their new values.
+__global__ void k_rhs(int n, int P, double cm, const double* __restrict__ B0, const double* __restrict__ B1,
+                      double s1, const double* __restrict__ xprev, double* __restrict__ b, double* __restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > n || j > n) return;
+  if (j < n) {
+    const long long k = (long long)j * P + i;
+    const bool dir = (i == 0 || i == n);
+    const double val = (dir ? 0.0 : cm * xprev[k]) + B0[k] + s1 * B1[k];
+    b[k] = val;
+    if (dir) x[k] = val;
+  }
+  if (i < n) {
+    const long long k = (long long)n * P + (long long)j * P + i;
+    const bool dir = (j == n);
+    const double m = dir ? 0.0 : (j == 0 ? 0.5 * cm : cm);
+    const double val = m * xprev[k] + B0[k] + s1 * B1[k];
+    b[k] = val;
+    if (dir) x[k] = val;
+  }
+  if (i < n && j < n) {
+    const long long kc = (long long)j * P + i;
+    const long long kp = (long long)(2 * n + 1) * P + kc, km = (long long)(3 * n + 1) * P + kc;
+    b[kp] = B0[kp] + s1 * B1[kp];
+    b[km] = B0[km] + s1 * B1[km];
+  }
+}
+
+void launch_rhs(const Geom& g, double cm, const double* B0, const double* B1, double s1, const double* xprev,
+                double* b, double* x, cudaStream_t s) {
+  k_rhs<<<grid2(g.n + 1, g.n + 1), dim3(BX, BY), 0, s>>>(g.n, g.P, cm, B0, B1, s1, xprev, b, x);
+}
+
+// ------------------------------------------------------------ pack/unpack
+__global__ void k_pack2(int n, int P, const double* __restrict__ src, double* __restrict__ dst, int to_padded) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > n || j > n) return;
+  const long long nu = (long long)n * (n + 1), nn = (long long)n * n;
+  long long kd[4], kp[4];
+  bool ok[4];
+  ok[0] = j < n;          kd[0] = (long long)j * (n + 1) + i;              kp[0] = (long long)j * P + i;
+  ok[1] = i < n;          kd[1] = nu + (long long)j * n + i;               kp[1] = (long long)n * P + (long long)j * P + i;
+  ok[2] = i < n && j < n; kd[2] = 2 * nu + (long long)j * n + i;           kp[2] = (long long)(2 * n + 1) * P + (long long)j * P + i;
+  ok[3] = ok[2];          kd[3] = 2 * nu + nn + (long long)j * n + i;      kp[3] = (long long)(3 * n + 1) * P + (long long)j * P + i;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (!ok[q]) continue;
+    if (to_padded) dst[kp[q]] = src[kd[q]];
+    else dst[kd[q]] = src[kp[q]];
+  }
+}
+
+void launch_pack(const Geom& g, const double* dense, double* padded, cudaStream_t s) {
+  k_pack2<<<grid2(g.n + 1, g.n + 1), dim3(BX, BY), 0, s>>>(g.n, g.P, dense, padded, 1);
+}
+void launch_unpack(const Geom& g, const double* padded, double* dense, cudaStream_t s) {
+  k_pack2<<<grid2(g.n + 1, g.n + 1), dim3(BX, BY), 0, s>>>(g.n, g.P, padded, dense, 0);
+}
+
+// ------------------------------------------------------- instantiations
+#define SD_INST(T)                                                                                               \
+  template void launch_setup_coef<T>(const double*, int, int, double, double, T*, T*, T*, T*, cudaStream_t);    \
+  template void launch_convert<T>(const double*, T*, long long, cudaStream_t);                                   \
+  template void launch_cheb_V<T>(const Coef<T>&, const T*, const T*, T*, T*, T, T, int, long long, cudaStream_t); \
+  template void launch_cheb_D<T>(const Coef<T>&, const T*, const T*, T*, T*, T, T, int, long long, cudaStream_t); \
+  template void launch_resid_V<T>(const Coef<T>&, const T*, const T*, T*, int, int, long long, cudaStream_t);    \
+  template void launch_resid_D<T>(const Coef<T>&, const T*, const T*, T*, int, int, long long, cudaStream_t);    \
+  template void launch_restrict_V<T>(int, int, const T*, int, int, T*, cudaStream_t);            \
+  template void launch_restrict_D<T>(int, int, const T*, int, int, T*, cudaStream_t);            \
+  template void launch_prolong_V<T>(int, int, T*, int, int, const T*, cudaStream_t);                              \
+  template void launch_prolong_D<T>(int, int, T*, int, int, const T*, cudaStream_t);                              \
+  template void launch_precond_entry<T>(const Coef<double>&, const double*, double*, double, const T*, double, int, T*, cudaStream_t); \
+  template void launch_precond_mid<T>(const Coef<double>&, const double*, double*, const T*, int, T*, cudaStream_t); \
+  template void launch_precond_exit<T>(const Coef<double>&, double*, const T*, cudaStream_t);                     \
+  template void launch_precond_bgs_pff<T>(const Coef<double>&, const double*, double*, const T*, cudaStream_t);
+SD_INST(float)
+SD_INST(double)
+
+}  // namespace sdk

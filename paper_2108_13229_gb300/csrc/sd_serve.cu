@@ -1,0 +1,226 @@
+// sd_serve.cu -- many independent instances at once: sd_solve_batch (a
+// fixed set of handles advanced concurrently, each on its own stream) and
+// the continuous-batching server (requests admitted FIFO as running slots
+// and HBM budget free up, each run keeping its state on the device for all
+// its time steps).  Host code only, built on the public C ABI; instances
+// never share device memory, so every result equals the instance run alone.
+#include "../../include/sd.h"
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+namespace {
+
+using clk = std::chrono::steady_clock;
+
+double ms_between(clk::time_point a, clk::time_point b) {
+  return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+struct Job {
+  uint64_t id = 0;
+  sd_request req;
+  std::vector<double> K;
+  int64_t est = 0;
+  int status = SD_PENDING;
+  sd_result res;
+  std::vector<double> x;
+  clk::time_point t_submit, t_start, t_end;
+};
+
+}  // namespace
+
+struct sd_server {
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<uint64_t> queue;
+  std::map<uint64_t, std::unique_ptr<Job>> jobs;
+  int64_t budget = 0, used = 0;
+  int max_running = 1, running = 0;
+  bool stop = false;
+  sd_options opt;
+  uint64_t next_id = 1;
+  int device = 0;
+  std::vector<std::thread> workers;
+};
+
+namespace {
+
+void run_job(sd_server* S, Job* J) {
+  sd_options o = S->opt;
+  o.stream = nullptr;  // each run gets its own stream, so runs overlap on the device
+  sd_handle* h = nullptr;
+  int rc = sd_create(&J->req.grid, J->req.mu, J->K.data(), J->req.alpha_bj, J->req.dt, &o, &h);
+  std::memset(&J->res, 0, sizeof(J->res));
+  J->res.dof = sd_dof_count(J->req.grid.nx);
+  if (rc == SD_OK) {
+    std::vector<sd_step_info> info(J->req.nsteps > 0 ? J->req.nsteps : 1);
+    rc = sd_step(h, J->req.nsteps, info.data());
+    int done = 0, it = 0;
+    double mr = 0.0;
+    for (int k = 0; k < J->req.nsteps; ++k) {
+      ++done;
+      it += info[k].iters;
+      if (info[k].relres > mr) mr = info[k].relres;
+    }
+    J->res.steps_done = done;
+    J->res.total_iters = it;
+    J->res.max_relres = mr;
+    if (J->req.keep_fields) {
+      J->x.resize((size_t)sd_dof_count(J->req.grid.nx));
+      int r2 = sd_get_state(h, nullptr, nullptr, J->x.data());
+      if (rc == SD_OK) rc = r2;
+    }
+  }
+  if (h) sd_destroy(h);
+  J->status = rc;
+  J->res.status = rc;
+}
+
+void worker_loop(sd_server* S) {
+  cudaSetDevice(S->device);
+  for (;;) {
+    Job* J = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv.wait(lk, [&] {
+        if (S->stop) return true;
+        if (S->queue.empty()) return false;
+        Job* head = S->jobs[S->queue.front()].get();
+        return S->used + head->est <= S->budget;
+      });
+      if (S->stop) return;
+      J = S->jobs[S->queue.front()].get();
+      S->queue.pop_front();
+      S->used += J->est;
+      S->running += 1;
+      J->t_start = clk::now();
+    }
+    run_job(S, J);
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      J->t_end = clk::now();
+      J->res.queue_ms = ms_between(J->t_submit, J->t_start);
+      J->res.run_ms = ms_between(J->t_start, J->t_end);
+      J->res.latency_ms = ms_between(J->t_submit, J->t_end);
+      S->used -= J->est;
+      S->running -= 1;
+    }
+    S->cv.notify_all();
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int sd_solve_batch(sd_handle* const* hs, int32_t count, const int32_t* nsteps, sd_step_info* const* infos,
+                   int32_t max_threads) {
+  if (count < 0 || (count > 0 && (!hs || !nsteps))) return SD_E_INVAL;
+  if (count == 0) return SD_OK;
+  int nt = (max_threads > 0 && max_threads < count) ? max_threads : count;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::atomic<int> next(0);
+  std::vector<int> rcs(count, SD_OK);
+  auto body = [&]() {
+    cudaSetDevice(dev);
+    for (;;) {
+      const int k = next.fetch_add(1);
+      if (k >= count) return;
+      rcs[k] = sd_step(hs[k], nsteps[k], infos ? infos[k] : nullptr);
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t) th.emplace_back(body);
+  for (auto& t : th) t.join();
+  for (int k = 0; k < count; ++k)
+    if (rcs[k] != SD_OK) return rcs[k];
+  return SD_OK;
+}
+
+int sd_server_create(int64_t hbm_budget_bytes, int32_t max_running, const sd_options* opt, sd_server** out) {
+  if (!out || hbm_budget_bytes <= 0 || max_running < 1) return SD_E_INVAL;
+  sd_server* S = new sd_server();
+  sd_options_default(&S->opt);
+  if (opt) S->opt = *opt;
+  S->budget = hbm_budget_bytes;
+  S->max_running = max_running;
+  cudaGetDevice(&S->device);
+  for (int k = 0; k < max_running; ++k) S->workers.emplace_back(worker_loop, S);
+  *out = S;
+  return SD_OK;
+}
+
+int sd_submit(sd_server* S, const sd_request* req, uint64_t* ticket) {
+  if (!S || !req || !ticket || !req->K || req->nsteps < 0) return SD_E_INVAL;
+  const int64_t est = sd_memory_estimate(&req->grid, &S->opt);
+  if (est < 0) return SD_E_INVAL;
+  if (est > S->budget) return SD_E_NOMEM;
+  const int n = req->grid.nx;
+  std::unique_ptr<Job> J(new Job());
+  J->req = *req;
+  J->K.assign(req->K, req->K + (size_t)n * n);
+  J->req.K = nullptr;
+  J->est = est + (int64_t)(4 << 20);  // setup temporaries and stream resources
+  J->t_submit = clk::now();
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    J->id = S->next_id++;
+    *ticket = J->id;
+    S->queue.push_back(J->id);
+    S->jobs[J->id] = std::move(J);
+  }
+  S->cv.notify_all();
+  return SD_OK;
+}
+
+int sd_poll(sd_server* S, uint64_t ticket, sd_result* out, double* x) {
+  if (!S) return SD_E_INVAL;
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->jobs.find(ticket);
+  if (it == S->jobs.end()) return SD_E_STATE;
+  Job* J = it->second.get();
+  if (J->t_end == clk::time_point()) {
+    if (out) {
+      std::memset(out, 0, sizeof(*out));
+      out->status = SD_PENDING;
+    }
+    return SD_PENDING;
+  }
+  if (out) *out = J->res;
+  if (x && !J->x.empty()) std::memcpy(x, J->x.data(), sizeof(double) * J->x.size());
+  const int st = J->status;
+  S->jobs.erase(it);
+  return st;
+}
+
+int sd_server_drain(sd_server* S) {
+  if (!S) return SD_E_INVAL;
+  std::unique_lock<std::mutex> lk(S->mu);
+  S->cv.wait(lk, [&] { return S->queue.empty() && S->running == 0; });
+  return SD_OK;
+}
+
+void sd_server_destroy(sd_server* S) {
+  if (!S) return;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv.notify_all();
+  for (auto& t : S->workers) t.join();
+  delete S;
+}
+
+}  // extern "C"

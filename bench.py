@@ -1,0 +1,390 @@
+"""Benchmark of the monolithic block-preconditioned Stokes-Darcy solve on GB300.
+
+One step = one implicit-Euler step of the coupled problem (right-hand side,
+then block-preconditioned FGMRES to ||b - A x||_2 <= 1e-10 ||b||_2), the
+whole hot path.  Default workload: 1024 x 1024 cells per subdomain
+(4 196 352 unknowns), mu = 1e-3, alpha_BJ = 1, dt = 0.05, log-normal
+permeability (ln K ~ N(-4, 1), exponential covariance, correlation length 16
+cells, seed 0).  The headline runs the FP32 multigrid / FP64 outer form; the
+FP64-throughout form of the same workload is measured beside it.
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs an
+independent replica of the workload (the single-instance solve does not
+shard) and the value is the sum of units over the max time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n 1024]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "coupled DOF*steps/s at rel.res 1e-10 (FP32-MG vs FP64); p50/p99 solve latency"
+UNIT = "DOF*steps/s"
+HBM_FALLBACK_GBS = 6800.0
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def workload_desc(n: int, steps: int) -> str:
+    return ("stokes-darcy monolithic, %dx%d cells per subdomain (%d DoF), lognormal K ln K~N(-4,1) "
+            "corr 16 cells seed 0, mu=1e-3, alpha_BJ=1, dt=0.05, %d implicit-Euler steps, rtol 1e-10"
+            % (n, n, 4 * n * n + 2 * n, steps))
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def aggregate(units: float, seconds: float, ws: int):
+    """Whole-job (sum of units, max of seconds) over ranks; identity when ws == 1."""
+    if ws == 1:
+        return units, seconds
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
+    s = torch.tensor([seconds], dtype=torch.float64, device=dev)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(s, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(s.item())
+
+
+def _barrier():
+    try:
+        import torch.distributed as dist
+        if dist.is_available() and dist.is_initialized():
+            dist.barrier()
+    except Exception:
+        pass
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    p = [x.strip() for x in line.split(",")]
+                    if len(p) < 9:
+                        continue
+                    try:
+                        sm.append(float(p[1]))
+                        smax.append(float(p[2]))
+                    except ValueError:
+                        continue
+                    for nm, val in zip(names, p[5:9]):
+                        if val.lower() in ("active", "1"):
+                            reasons.add(nm)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+def run_form(sd, torch, n, K, precision, steps, warmup, stream, prof_kernel=None):
+    """Warm up, then time `steps` implicit-Euler steps with CUDA events on `stream`."""
+    opts = sd.sd_options_default()
+    opts.precision = precision
+    opts.stream = stream.cuda_stream
+    h = sd.sd_create(n, 1e-3, K, 1.0, 0.05, opts)
+    sd.sd_step(h, warmup)
+    if prof_kernel is not None:
+        sd.sd_profile(h, prof_kernel, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    _barrier()
+    torch.cuda.synchronize()
+    l0 = sd.sd_launch_count()
+    with torch.cuda.stream(stream):
+        torch.cuda.nvtx.range_push("timed")
+        ev0.record(stream)
+        infos = sd.sd_step(h, steps)
+        ev1.record(stream)
+        torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    _barrier()
+    launches = sd.sd_launch_count() - l0
+    ms = ev0.elapsed_time(ev1)
+    prof = sd.sd_profile_read(h) if prof_kernel is not None else None
+    sd.sd_destroy(h)
+    return ms, infos, launches, prof
+
+
+KERNELS = {0: ("k_apply_full", "sd_ops.cu", True), 1: ("k_cheb_V<float> fine level", "sd_ops.cu", False),
+           2: ("k_mupdate", "sd_krylov.cu", True), 3: ("k_mdot", "sd_krylov.cu", True)}
+
+
+def source_hash(fname: str) -> str:
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2108_13229_gb300", "csrc", fname), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def ncu_traffic(name: str, fname: str):
+    """DRAM bytes per algorithmic byte from the committed ncu summary, if the kernel is unchanged."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            tab = json.load(f)
+        e = tab[name]
+        if e.get("source_hash") != source_hash(fname):
+            return None
+        return e["dram_bytes_per_launch"] / e["algorithmic_bytes_per_launch"]
+    except Exception:
+        return None
+
+
+def roofline_entry(kid: int, prof, step_ms: float):
+    kms, klaunch, kbytes, kflops = prof
+    name, fname, fp64 = KERNELS[kid]
+    hbm_peak, hbm_src = read_peaks()
+    gbs = (kbytes / 1e9) / (kms / 1e3) if kms > 0 else 0.0
+    ratio = ncu_traffic(name, fname)
+    traffic = ratio * kbytes / max(klaunch, 1) if ratio is not None else None
+    e = {"kernel": name, "launches": klaunch, "avg_launch_us": 1e3 * kms / max(klaunch, 1),
+         "share_of_step_time": kms / step_ms if step_ms > 0 else None,
+         "bytes_per_launch": kbytes / max(klaunch, 1), "flops_per_launch": kflops / max(klaunch, 1),
+         "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak, "traffic": traffic}
+    if fp64:
+        tf = (kflops / 1e12) / (kms / 1e3) if kms > 0 else 0.0
+        e.update({"bound": "alu", "achieved": tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                  "frac": tf / FP64_NOMINAL_TFLOPS,
+                  "peak_source": "nominal FP64 rate of the part (1.25 TFLOP/s at 2070 MHz); FP64 is not in the "
+                                 "measured peaks file"})
+    else:
+        e.update({"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                  "peak_source": hbm_src})
+    return e
+
+
+def cpu_oracle_sample(n_sample: int, steps: int):
+    """Time the oracle on a bounded sample: same physics on an n_sample grid."""
+    import oracle as O
+    from paper_2108_13229_gb300 import inputs as I
+    K = I.lognormal_K(n_sample, -4.0, 1.0, 16.0, seed=0)
+    t0 = time.perf_counter()
+    o = O.Oracle(n_sample, 1e-3, 1.0, 0.05, K)
+    o.factor()
+    t1 = time.perf_counter()
+    o.run(O.exact(n_sample, 0.0, 1e-3), 0.0, steps)
+    t2 = time.perf_counter()
+    dof = 4 * n_sample * n_sample + 2 * n_sample
+    return {"value": dof * steps / (t2 - t0), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "same physics on %dx%d cells (%d DoF), %d steps; banded-LU factorisation %.2fs + steps %.2fs "
+                      "on one host core; the %s grid is beyond the banded LU's memory" %
+                      (n_sample, n_sample, dof, steps, t1 - t0, t2 - t1, "workload")}
+
+
+def bench_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    n_sample = 128
+    import oracle as O
+    from paper_2108_13229_gb300 import inputs as I
+    K = I.lognormal_K(n_sample, -4.0, 1.0, 16.0, seed=0)
+    o = O.Oracle(n_sample, 1e-3, 1.0, 0.05, K)
+    tf0 = time.perf_counter()
+    o.factor()
+    tf = time.perf_counter() - tf0
+    x = O.exact(n_sample, 0.0, 1e-3)
+    x = o.run(x, 0.0, args.warmup)
+    t0 = time.perf_counter()
+    x = o.run(x, args.warmup * 0.05, args.steps)
+    el = time.perf_counter() - t0
+    dof = 4 * n_sample * n_sample + 2 * n_sample
+    val = dof * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload_desc(args.n, args.steps),
+                                            "sample_grid": n_sample},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "each step: right-hand side + banded-LU triangular solves of the same "
+                                       "physics on %dx%d cells (%d DoF), one host core; factorisation %.2fs "
+                                       "outside the timed steps" % (n_sample, n_sample, dof, tf)},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def bench_ours(args, ws, rank, local):
+    import torch
+    from paper_2108_13229_gb300 import inputs as I
+    from paper_2108_13229_gb300 import sd
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    n, steps, warmup = args.n, args.steps, args.warmup
+    K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=rank)
+    dof = 4 * n * n + 2 * n
+    stream = torch.cuda.Stream()
+
+    # headline: FP32 multigrid inside FP64 FGMRES
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms, infos, launches, _ = run_form(sd, torch, n, K, sd.SD_MIXED, steps, warmup, stream)
+    clocks = sampler.stop()
+    units, secs = aggregate(dof * steps, ms / 1e3, ws)
+    value = units / secs
+    lat = [i["ms"] for i in infos]
+    iters = [i["iters"] for i in infos]
+    relres = max(i["relres"] for i in infos)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": steps, "warmup": warmup,
+            "ms_per_step": secs * 1e3 / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 outer / f32 multigrid", "data": "synthetic",
+            "config": {"workload": workload_desc(n, steps), "n": n, "dof": dof, "precision": "mixed",
+                       "parallelism": "replicas only" if ws > 1 else "single instance",
+                       "l2": "working set ~2.4 GB per instance, larger than L2 (no flush needed)"},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "iters_per_step": iters, "max_relres": relres, "gpu_launches": launches, "clocks": clocks}
+
+    if not args.quick:
+        # FP64 throughout, same workload
+        ms64, infos64, _, _ = run_form(sd, torch, n, K, sd.SD_FP64, steps, warmup, stream)
+        u64, s64 = aggregate(dof * steps, ms64 / 1e3, ws)
+        lat64 = [i["ms"] for i in infos64]
+        line["fp64"] = {"value": u64 / s64, "ms_per_step": s64 * 1e3 / steps,
+                        "latency_ms": {"p50": float(np.percentile(lat64, 50)), "p99": float(np.percentile(lat64, 99))},
+                        "iters_per_step": [i["iters"] for i in infos64]}
+        line["mixed_over_fp64"] = value / (u64 / s64)
+
+        # roofline: each candidate kernel class is timed live (CUDA events around
+        # every launch) during its own timed run; the largest share of the step
+        # time is the dominant kernel
+        cands = []
+        for kid in (sd.SD_PROF_MUPDATE, sd.SD_PROF_APPLY, sd.SD_PROF_MDOT, sd.SD_PROF_CHEB_V):
+            msk, _, _, prof = run_form(sd, torch, n, K, sd.SD_MIXED, steps, warmup, stream, prof_kernel=kid)
+            cands.append(roofline_entry(kid, prof, msk))
+        cands.sort(key=lambda e: -(e["share_of_step_time"] or 0.0))
+        line["roofline"] = cands[0]
+        line["roofline_kernels"] = cands[1:]
+
+        # end to end through the public API with host buffers: create from host K,
+        # then every step read the fields back into pinned host memory
+        pinned = torch.empty(dof, dtype=torch.float64, pin_memory=True)
+        Kh = torch.from_numpy(np.ascontiguousarray(K)).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        opts = sd.sd_options_default()
+        h = sd.sd_create(n, 1e-3, Kh, 1.0, 0.05, opts)
+        for _ in range(steps):
+            sd.sd_step(h, 1)
+            sd.sd_get_state(h, pinned)
+        sd.sd_destroy(h)
+        el = time.perf_counter() - t0
+        ue, se = aggregate(dof * steps, el, ws)
+        line["e2e"] = {"value": ue / se, "unit": UNIT, "h2d_bytes_per_step": n * n * 8 / steps,
+                       "d2h_bytes_per_step": dof * 8,
+                       "note": "setup (sd_create from host K, hierarchy, coarse inverses) inside the timed region"}
+
+        if rank == 0 and ws >= 1 and not args.no_cpu:
+            line["cpu_baseline"] = cpu_oracle_sample(args.cpu_n, 20)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def peak_probe() -> int:
+    """Compile and run paper_2108_13229_gb300/peak_probe.cu; prints its JSON line."""
+    src = os.path.join(ROOT, "paper_2108_13229_gb300", "peak_probe.cu")
+    exe = os.path.join(tempfile.gettempdir(), "sd_peak_probe")
+    subprocess.check_call(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src])
+    return subprocess.call([exe])
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--cpu-n", type=int, default=128)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="headline form only")
+    ap.add_argument("--peak-probe", action="store_true", help="measure FP64/FP32 FMA rates and copy bandwidth")
+    args = ap.parse_args()
+    if args.peak_probe:
+        return peak_probe()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if (args.impl == "ours" and torch.cuda.is_available()) else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+        dist.barrier()
+    try:
+        if args.impl == "reference":
+            return bench_reference(args, ws, rank)
+        return bench_ours(args, ws, rank, local)
+    finally:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -92,13 +92,20 @@ typedef struct {
   int32_t precond;     /* SD_TRI_SCHUR | SD_PV_BJ_I | SD_PV_BGS_I (default SD_TRI_SCHUR) */
   int32_t bc;          /* SD_BC_MMS */
   int32_t cheb_degree; /* Chebyshev smoothing steps before and after each coarse
-                          correction (default 2) */
+                          correction (default 3) */
   int32_t coarsest;    /* coarsen while the grid has more than this many cells per
-                          side (default 8) */
+                          side (default 4) */
   double schur_gamma;  /* gamma of S^ (default 0.5) */
   double cheb_ratio;   /* Chebyshev interval [lmax/ratio, 1.1 lmax] (default 8) */
   int32_t schur_mass;  /* SD_TRI_SCHUR: add the mass-dominated part (1/dt) L_p^-1 of
                           the Schur complement, L_p = B^T B / h^2 (default 1) */
+  int32_t fuse_coarse; /* run all levels with <= 32 cells per side in one single-CTA
+                          kernel (default 1) */
+  int32_t orth;        /* 0: classical Gram-Schmidt twice (CGS2, default); 1: second
+                          pass only when ||w'|| < reorth_eta ||w|| */
+  double reorth_eta;   /* default 1/sqrt(2) */
+  int32_t extrapolate; /* initial guess of step n+1: 2 x^n - x^{n-1} (1, default)
+                          or x^n (0) */
   void *stream;        /* cudaStream_t to run on; NULL: the handle creates one */
 } sd_options;
 
@@ -108,6 +115,7 @@ typedef struct {
   int32_t status;   /* SD_OK | SD_E_NOCONV | SD_E_NUMERIC */
   double relres;    /* final true ||b - A x||_2 / ||b||_2 (FP64, recomputed) */
   double ms;        /* device time of the step (CUDA events) */
+  int32_t reorths;  /* Arnoldi steps that took the second Gram-Schmidt pass */
 } sd_step_info;
 
 /* Fill *opt with the defaults above. */
@@ -141,9 +149,14 @@ int sd_step(sd_handle *h, int32_t nsteps, sd_step_info *info);
 /* Copy the current fields out (any of the four may be NULL). */
 int sd_get_fields(sd_handle *h, double *u, double *v, double *p_ff, double *p_pm);
 
-/* Read / replace the whole state: time, step count, whole-system vector x. */
-int sd_get_state(sd_handle *h, double *t, int64_t *step, double *x);
-int sd_set_state(sd_handle *h, double t, int64_t step, const double *x);
+/* Read / replace the whole state (checkpoint / resume): time, step count,
+ * whole-system vector x^n and the previous time level x^{n-1} used by the
+ * extrapolated initial guess (any output may be NULL; a NULL xprev in
+ * sd_set_state clears the history, so the next step starts from x^n).
+ * Resuming from a saved (t, step, x, xprev) reproduces the uninterrupted run
+ * bit for bit. */
+int sd_get_state(sd_handle *h, double *t, int64_t *step, double *x, double *xprev);
+int sd_set_state(sd_handle *h, double t, int64_t step, const double *x, const double *xprev);
 
 /* y = A x with A the matrix of Eq. (9) (whole-system layout). */
 int sd_apply(sd_handle *h, const double *x, double *y);
@@ -199,6 +212,22 @@ int sd_poll(sd_server *s, uint64_t ticket, sd_result *out, double *x);
 /* Block until every submitted request has finished. */
 int sd_server_drain(sd_server *s);
 void sd_server_destroy(sd_server *s);
+
+/* Kernel timing for roofline reports.  While enabled, every launch of the
+ * selected kernel class is bracketed by CUDA events on the handle's stream;
+ * sd_profile_read() returns the summed device time, the number of launches,
+ * and the summed algorithmic bytes (compulsory traffic: every input and
+ * output array counted once) and floating-point operations of those
+ * launches. */
+#define SD_PROF_APPLY 0   /* whole-system FP64 operator y = A x (Eq. (9)) */
+#define SD_PROF_CHEB_V 1  /* fine-level velocity-block Chebyshev step */
+#define SD_PROF_MUPDATE 2 /* Gram-Schmidt update fused with the next dots */
+#define SD_PROF_MDOT 3    /* Gram-Schmidt multi-dot */
+int sd_profile(sd_handle *h, int32_t kernel, int32_t enable);
+int sd_profile_read(sd_handle *h, double *total_ms, int64_t *launches, double *bytes, double *flops);
+
+/* Kernel launches made by this library in this process so far. */
+int64_t sd_launch_count(void);
 
 const char *sd_strerror(int code);
 

@@ -95,7 +95,11 @@ struct MG {
   double *AinvV = nullptr, *AinvD = nullptr, *AinvP = nullptr;
   int *idxV = nullptr, *idxD = nullptr;
   int mV = 0, mD = 0;
+  int fuse_from = -1;  // first level handled by the fused single-CTA coarse cycle
+  CoarseCycle<T> cycV, cycD, cycP;
 };
+
+const int FUSE_N = 32;  // grids with at most this many cells per side run fused
 
 int level_count(int n, int coarsest) {
   int L = 1;
@@ -126,14 +130,22 @@ struct sd_handle {
   std::vector<LevelCoef<double>> c64;  // FP64 coefficients of every level
   MG<float> mg32;
   MG<double> mg64;
-  double *stage = nullptr, *x = nullptr, *b = nullptr, *B0 = nullptr, *B1 = nullptr;
+  double *stage = nullptr, *x = nullptr, *xm = nullptr, *b = nullptr, *B0 = nullptr, *B1 = nullptr;
   double *V = nullptr, *Z = nullptr, *partial = nullptr, *scal = nullptr, *st = nullptr, *flag = nullptr;
   double* hflag = nullptr;  // pinned
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   double t = 0.0;
   long long step = 0;
+  bool have_prev = false;  // x_m holds the state of the previous time level
+  // kernel timing (sd_profile): event pairs around launches of one kernel class
+  int prof_id = -1;
+  std::vector<cudaEvent_t> prof_ev;
+  std::vector<double> prof_bytes_pending, prof_flops_pending;
+  int prof_used = 0;
+  double prof_ms = 0.0, prof_bytes = 0.0, prof_flops = 0.0;
+  long long prof_launches = 0;
   // scalar slots in scal[]
-  static const int S_H1 = 0, S_H2 = 32, S_N2 = 64, S_B2 = 65, S_BN = 66, S_Y = 96;
+  static const int S_H1 = 0, S_H2 = 32, S_N2 = 64, S_B2 = 65, S_BN = 66, S_N2B = 67, S_REO = 68, S_Y = 96;
 };
 
 namespace {
@@ -196,6 +208,7 @@ void plan_all(sd_handle* h) {
   }
   const long long len = h->g.len;
   h->x = a.take<double>(len);
+  h->xm = a.take<double>(len);
   h->b = a.take<double>(len);
   h->B0 = a.take<double>(len);
   h->B1 = a.take<double>(len);
@@ -366,7 +379,95 @@ int setup_mg(sd_handle* h, MG<T>& M) {
     cheb_coeffs<T>(ld, h->opt.cheb_ratio, deg, M.L[l].D.cha, M.L[l].D.chc);
     cheb_coeffs<T>(lp, h->opt.cheb_ratio, deg, M.L[l].Pb.cha, M.L[l].Pb.chc);
   }
+  M.fuse_from = -1;
+  if (h->opt.fuse_coarse) {
+    int f = 0;
+    while (f < h->nlev && h->geo[f].n > FUSE_N) ++f;
+    if (f < h->nlev && h->nlev - f <= SD_CYC_MAXL) {
+      auto fill = [&](CoarseCycle<T>& q, int kind, int which) {
+        std::memset(&q, 0, sizeof(q));
+        q.nlev = h->nlev - f;
+        q.kind = kind;
+        q.deg = deg;
+        for (int l = f; l < h->nlev; ++l) {
+          MGLevel<T>& L = M.L[l];
+          q.c[l - f] = which == 2 ? L.cP : L.c;
+          Block<T>& B = which == 0 ? L.V : (which == 1 ? L.D : L.Pb);
+          for (int k = 0; k < deg && k < 8 && l + 1 < h->nlev; ++k) {
+            q.cha[l - f][k] = B.cha[k];
+            q.chc[l - f][k] = B.chc[k];
+          }
+        }
+        Block<T>& B0 = which == 0 ? M.L[f].V : (which == 1 ? M.L[f].D : M.L[f].Pb);
+        q.b_in = B0.b;
+        q.x_out = B0.x;
+        q.Ainv = which == 0 ? M.AinvV : (which == 1 ? M.AinvD : M.AinvP);
+        q.idx = which == 0 ? M.idxV : M.idxD;
+        q.m = which == 0 ? M.mV : M.mD;
+      };
+      fill(M.cycV, 0, 0);
+      fill(M.cycD, 1, 1);
+      fill(M.cycP, 1, 2);
+      if (coarse_cycle_smem(M.cycV) <= 200 * 1024 && coarse_cycle_smem(M.cycD) <= 200 * 1024) M.fuse_from = f;
+    }
+  }
   return SD_OK;
+}
+
+// ------------------------------------------------------ kernel timing
+// Accumulate the elapsed time of the recorded event pairs (the stream has
+// been synchronised by the caller, so every event has completed).
+void prof_flush(sd_handle* h) {
+  for (int k = 0; k + 1 < h->prof_used; k += 2) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->prof_ev[k], h->prof_ev[k + 1]) == cudaSuccess) {
+      h->prof_ms += ms;
+      h->prof_bytes += h->prof_bytes_pending[k / 2];
+      h->prof_flops += h->prof_flops_pending[k / 2];
+      h->prof_launches += 1;
+    }
+  }
+  h->prof_used = 0;
+}
+
+struct ProfScope {
+  sd_handle* h;
+  bool on;
+  ProfScope(sd_handle* hh, int id, double bytes, double flops = 0.0) : h(hh), on(hh->prof_id == id) {
+    if (!on) return;
+    if (h->prof_used + 2 > (int)h->prof_ev.size()) {
+      cudaStreamSynchronize(h->s);
+      prof_flush(h);
+    }
+    h->prof_bytes_pending[h->prof_used / 2] = bytes;
+    h->prof_flops_pending[h->prof_used / 2] = flops;
+    cudaEventRecord(h->prof_ev[h->prof_used++], h->s);
+  }
+  ~ProfScope() {
+    if (on) cudaEventRecord(h->prof_ev[h->prof_used++], h->s);
+  }
+};
+
+// Algorithmic bytes of one launch (compulsory traffic, each array once):
+//  fine velocity-block Chebyshev step: read x_in (if any), b, d (if a != 0);
+//  write d and x_out, over the 2n(n+1) velocity faces.
+double cheb_bytes_V(const Geom& g, size_t es, bool has_x, bool has_d) {
+  const double nv = 2.0 * g.n * (g.n + 1);
+  return nv * es * (1.0 + (has_x ? 1 : 0) + (has_d ? 1 : 0) + 2.0);
+}
+//  whole-system FP64 operator, algorithmic flops: one multiply-add per stored
+//  matrix entry, nnz = 2 * 11 (u, v rows) + 4 (continuity) + 5 (Darcy) per
+//  cell minus the eliminated boundary couplings, about 31 per cell.
+double apply_flops(const Geom& g) {
+  const double n = g.n;
+  const double nnz = 31.0 * n * n - 6.0 * n;
+  return 2.0 * nnz;
+}
+//  whole-system FP64 operator: read x (4n^2+2n), the transmissibilities
+//  (2n(n+1)) and interface coefficients (2n), read b if residual, write y.
+double apply_bytes(const Geom& g, bool resid) {
+  const double nd = 4.0 * g.n * g.n + 2.0 * g.n;
+  return 8.0 * (nd * (resid ? 3 : 2) + 2.0 * g.n * (g.n + 1) + 2.0 * g.n);
 }
 
 // ----------------------------------------------------------- V-cycles
@@ -374,9 +475,13 @@ int setup_mg(sd_handle* h, MG<T>& M) {
 // bilinear restriction, coarse correction, bilinear prolongation,
 // Chebyshev post-smoothing; dense FP64 solve on the coarsest grid.
 template <typename T>
-void vcycle_V(MG<T>& M, int l, int deg, cudaStream_t s) {
+void vcycle_V(MG<T>& M, int l, int deg, cudaStream_t s, sd_handle* prof_owner) {
   MGLevel<T>& L = M.L[l];
   Block<T>& B = L.V;
+  if (l == M.fuse_from && launch_coarse_cycle<T>(M.cycV, s) == 0) {
+    B.res = B.x;
+    return;
+  }
   if (l + 1 == (int)M.L.size()) {
     launch_dense_solve<T>(M.AinvV, M.idxV, M.mV, B.b, B.x, s);
     B.res = B.x;
@@ -385,17 +490,23 @@ void vcycle_V(MG<T>& M, int l, int deg, cudaStream_t s) {
   T* cur = nullptr;
   for (int k = 0; k < deg; ++k) {
     T* out = (cur == B.x) ? B.x2 : B.x;
-    launch_cheb_V<T>(L.c, cur, B.b, B.d, out, B.cha[k], B.chc[k], 1, 0, s);
+    {
+      ProfScope ps(prof_owner, l == 0 ? SD_PROF_CHEB_V : -2, cheb_bytes_V(L.g, sizeof(T), cur != nullptr, k > 0));
+      launch_cheb_V<T>(L.c, cur, B.b, B.d, out, B.cha[k], B.chc[k], 1, 0, s);
+    }
     cur = out;
   }
   MGLevel<T>& C = M.L[l + 1];
   launch_resid_V<T>(L.c, cur, B.b, B.r, 0, 1, 0, s);
   launch_restrict_V<T>(L.g.n, L.g.P, B.r, C.g.n, C.g.P, C.V.b, s);
-  vcycle_V(M, l + 1, deg, s);
+  vcycle_V(M, l + 1, deg, s, prof_owner);
   launch_prolong_V<T>(L.g.n, L.g.P, cur, C.g.n, C.g.P, C.V.res, s);
   for (int k = 0; k < deg; ++k) {
     T* out = (cur == B.x) ? B.x2 : B.x;
-    launch_cheb_V<T>(L.c, cur, B.b, B.d, out, B.cha[k], B.chc[k], 1, 0, s);
+    {
+      ProfScope ps(prof_owner, l == 0 ? SD_PROF_CHEB_V : -2, cheb_bytes_V(L.g, sizeof(T), true, k > 0));
+      launch_cheb_V<T>(L.c, cur, B.b, B.d, out, B.cha[k], B.chc[k], 1, 0, s);
+    }
     cur = out;
   }
   B.res = cur;
@@ -408,6 +519,10 @@ void vcycle_cell(MG<T>& M, int l, int deg, bool poisson, cudaStream_t s) {
   MGLevel<T>& L = M.L[l];
   Block<T>& B = poisson ? L.Pb : L.D;
   const Coef<T>& c = poisson ? L.cP : L.c;
+  if (l == M.fuse_from && launch_coarse_cycle<T>(poisson ? M.cycP : M.cycD, s) == 0) {
+    B.res = B.x;
+    return;
+  }
   if (l + 1 == (int)M.L.size()) {
     launch_dense_solve<T>(poisson ? M.AinvP : M.AinvD, M.idxD, M.mD, B.b, B.x, s);
     B.res = B.x;
@@ -452,7 +567,7 @@ void precond(sd_handle* h, MG<T>& M, const double* r, double* z) {
     eP = M.L[0].Pb.res;
   }
   launch_precond_entry<T>(c, r, z, schur, eP, 1.0 / h->dt, tri, M.L[0].V.b, s);
-  vcycle_V<T>(M, 0, deg, s);
+  vcycle_V<T>(M, 0, deg, s, h);
   if (mode == SD_PV_BGS_I) launch_precond_bgs_pff<T>(c, r, z, M.L[0].V.res, s);
   launch_precond_mid<T>(c, r, z, M.L[0].V.res, mode != SD_PV_BJ_I, M.L[0].D.b, s);
   vcycle_cell<T>(M, 0, deg, false, s);
@@ -462,6 +577,63 @@ void precond(sd_handle* h, MG<T>& M, const double* r, double* z) {
 void apply_precond(sd_handle* h, const double* r, double* z) {
   if (h->opt.precision == SD_MIXED) precond<float>(h, h->mg32, r, z);
   else precond<double>(h, h->mg64, r, z);
+}
+
+// ----------------------------------------------------------- Arnoldi step
+// z_j = P^-1 v_j, w = A z_j, then w orthogonalised against v_0..v_j and the
+// new Hessenberg column rotated (Givens).  Orthogonalisation:
+//   orth 0: classical Gram-Schmidt with one re-orthogonalisation (CGS2);
+//   orth 1: the second pass only when the first removed most of w
+//           (||w'|| < eta ||w||, decided on the device).
+void arnoldi_orth(sd_handle* h, int j, const double* vj, double* zj, double* w) {
+  cudaStream_t s = h->s;
+  const long long len = h->g.len, vs = h->lenA;
+  const int nb = h->nblk, m = h->m, k = j + 1;
+  double* sc = h->scal;
+  apply_precond(h, vj, zj);
+  {
+    ProfScope ps(h, SD_PROF_APPLY, apply_bytes(h->g, false), apply_flops(h->g));
+    launch_apply_full(coef64(h, 0), zj, nullptr, w, s);
+  }
+  if (h->opt.orth == 0) {
+    {
+      ProfScope ps(h, SD_PROF_MDOT, 8.0 * (k + 1) * (double)len, 2.0 * k * (double)len);
+      launch_mdot(h->V, vs, k, w, len, h->partial, nb, nb, 0, nullptr, s);
+    }
+    launch_reduce(h->partial, nb, k, nb, sc + sd_handle::S_H1, 0, nullptr, s);
+    {
+      ProfScope ps(h, SD_PROF_MUPDATE, 8.0 * (k + 2) * (double)len, 4.0 * k * (double)len);
+      launch_mupdate(h->V, vs, k, sc + sd_handle::S_H1, w, len, h->partial, nb, nb, 1, nullptr, s);
+    }
+    launch_reduce(h->partial, nb, k, nb, sc + sd_handle::S_H2, 0, nullptr, s);
+    {
+      ProfScope ps(h, SD_PROF_MUPDATE, 8.0 * (k + 2) * (double)len, 2.0 * (k + 1) * (double)len);
+      launch_mupdate(h->V, vs, k, sc + sd_handle::S_H2, w, len, h->partial, nb, nb, 2, nullptr, s);
+    }
+    launch_reduce(h->partial, nb, 1, nb, sc + sd_handle::S_N2B, 0, nullptr, s);
+    launch_givens(h->st, j, m, sc + sd_handle::S_H1, sc + sd_handle::S_H2, sc + sd_handle::S_N2,
+                  sc + sd_handle::S_N2B, nullptr, h->flag, s);
+  } else {
+    const double* reo = sc + sd_handle::S_REO;
+    {
+      ProfScope ps(h, SD_PROF_MDOT, 8.0 * (k + 1) * (double)len, 2.0 * (k + 1) * (double)len);
+      launch_mdot(h->V, vs, k, w, len, h->partial, nb, nb, 1, nullptr, s);
+    }
+    launch_reduce(h->partial, nb, k + 1, nb, sc + sd_handle::S_H1, 0, nullptr, s);
+    {
+      ProfScope ps(h, SD_PROF_MUPDATE, 8.0 * (k + 2) * (double)len, 2.0 * (k + 1) * (double)len);
+      launch_mupdate(h->V, vs, k, sc + sd_handle::S_H1, w, len, h->partial, nb, nb, 2, nullptr, s);
+    }
+    launch_reduce(h->partial, nb, 1, nb, sc + sd_handle::S_N2, 0, nullptr, s);
+    const double eta = h->opt.reorth_eta;
+    launch_reorth_decide(sc + sd_handle::S_H1 + k, sc + sd_handle::S_N2, eta * eta, sc + sd_handle::S_REO, s);
+    launch_mdot(h->V, vs, k, w, len, h->partial, nb, nb, 0, reo, s);
+    launch_reduce(h->partial, nb, k, nb, sc + sd_handle::S_H2, 0, reo, s);
+    launch_mupdate(h->V, vs, k, sc + sd_handle::S_H2, w, len, h->partial, nb, nb, 2, reo, s);
+    launch_reduce(h->partial, nb, 1, nb, sc + sd_handle::S_N2B, 0, reo, s);
+    launch_givens(h->st, j, m, sc + sd_handle::S_H1, sc + sd_handle::S_H2, sc + sd_handle::S_N2,
+                  sc + sd_handle::S_N2B, reo, h->flag, s);
+  }
 }
 
 // --------------------------------------------------------------- FGMRES
@@ -479,7 +651,7 @@ int fgmres(sd_handle* h, const double* b, double* x, sd_step_info* info) {
   CK(cudaStreamSynchronize(s));
   const double bnorm = std::sqrt(h->hflag[4]);
   const double tol = h->opt.rtol * (bnorm > 0 ? bnorm : 1.0);
-  int iters = 0, restarts = 0, status = SD_OK;
+  int iters = 0, restarts = 0, status = SD_OK, reorths = 0;
   double relres = 0.0;
   for (;;) {
     launch_apply_full(c, x, b, h->V, s);  // V_0 = b - A x
@@ -500,19 +672,13 @@ int fgmres(sd_handle* h, const double* b, double* x, sd_step_info* info) {
       double* vj = h->V + (long long)j * vs;
       double* zj = h->Z + (long long)j * vs;
       double* w = h->V + (long long)(j + 1) * vs;
-      apply_precond(h, vj, zj);
-      launch_apply_full(c, zj, nullptr, w, s);
-      launch_mdot(h->V, vs, j + 1, w, len, h->partial, 32, nb, s);
-      launch_reduce(h->partial, nb, j + 1, 32, sc + sd_handle::S_H1, 0, s);
-      launch_mupdate(h->V, vs, j + 1, sc + sd_handle::S_H1, w, len, h->partial, 32, nb, 1, s);
-      launch_reduce(h->partial, nb, j + 1, 32, sc + sd_handle::S_H2, 0, s);
-      launch_mupdate(h->V, vs, j + 1, sc + sd_handle::S_H2, w, len, h->partial, 32, nb, 2, s);
-      launch_reduce(h->partial, nb, 1, 32, sc + sd_handle::S_N2, 0, s);
-      launch_givens(h->st, j, m, sc + sd_handle::S_H1, sc + sd_handle::S_H2, sc + sd_handle::S_N2, h->flag, s);
+      arnoldi_orth(h, j, vj, zj, w);
       launch_scale_by(w, w, len, h->flag + 1, 0, s);
-      CK(cudaMemcpyAsync(h->hflag, h->flag, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(h->hflag, h->flag, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
+      if (h->prof_used) prof_flush(h);
       ++iters;
+      reorths += h->hflag[4] != 0.0 ? 1 : 0;
       k = j + 1;
       if (h->hflag[2] != 0.0) { numeric = true; break; }
       if (h->hflag[0] <= tol || h->hflag[3] != 0.0 || iters >= h->opt.max_iters) break;
@@ -527,6 +693,7 @@ int fgmres(sd_handle* h, const double* b, double* x, sd_step_info* info) {
     info->restarts = restarts;
     info->relres = relres;
     info->status = status;
+    info->reorths = reorths;
   }
   return status;
 }
@@ -552,6 +719,7 @@ int validate(const sd_grid* grid, double mu, double alpha, double dt, const sd_o
   if (o->precond < SD_TRI_SCHUR || o->precond > SD_PV_BGS_I || o->bc != SD_BC_MMS) return SD_E_INVAL;
   if (o->cheb_degree < 1 || o->cheb_degree > 8 || o->coarsest < 2 || !(o->schur_gamma > 0) || !(o->cheb_ratio > 1))
     return SD_E_INVAL;
+  if (o->orth < 0 || o->orth > 1 || !(o->reorth_eta > 0) || o->reorth_eta > 1) return SD_E_INVAL;
   int n = grid->nx, L = level_count(n, o->coarsest);
   for (int l = 1; l < L; ++l) n /= 2;
   if (n > 16) return SD_E_INVAL;  // coarsest grid must stay small for the dense solve
@@ -656,8 +824,12 @@ void sd_options_default(sd_options* o) {
   o->precision = SD_MIXED;
   o->precond = SD_TRI_SCHUR;
   o->bc = SD_BC_MMS;
-  o->cheb_degree = 2;
-  o->coarsest = 8;
+  o->cheb_degree = 3;
+  o->coarsest = 4;
+  o->fuse_coarse = 1;
+  o->orth = 0;
+  o->reorth_eta = 0.70710678118654752;
+  o->extrapolate = 1;
   o->schur_gamma = 0.5;
   o->cheb_ratio = 8.0;
   o->schur_mass = 1;
@@ -694,8 +866,16 @@ int sd_step(sd_handle* h, int32_t nsteps, sd_step_info* info) {
   for (int k = 0; k < nsteps; ++k) {
     const double tn = h->t + h->dt;
     CK(cudaEventRecord(h->e0, h->s));
-    // the previous state is both the mass term source and the initial guess
-    launch_rhs(h->g, cm, h->B0, h->B1, 1.0 + tn, h->x, h->b, h->x, h->s);
+    if (h->opt.extrapolate && h->have_prev) {
+      // initial guess 2 x^n - x^{n-1}; x_m then holds x^n, the mass-term source
+      launch_extrapolate(h->x, h->xm, h->g.len, h->s);
+      launch_rhs(h->g, cm, h->B0, h->B1, 1.0 + tn, h->xm, h->b, h->x, h->s);
+    } else {
+      // the previous state is both the mass-term source and the initial guess
+      CK(cudaMemcpyAsync(h->xm, h->x, sizeof(double) * h->g.len, cudaMemcpyDeviceToDevice, h->s));
+      launch_rhs(h->g, cm, h->B0, h->B1, 1.0 + tn, h->x, h->b, h->x, h->s);
+    }
+    h->have_prev = true;
     sd_step_info si;
     std::memset(&si, 0, sizeof(si));
     const int rc = fgmres(h, h->b, h->x, &si);
@@ -710,6 +890,7 @@ int sd_step(sd_handle* h, int32_t nsteps, sd_step_info* info) {
     if (info) info[k] = si;
     if (rc != SD_OK && first == SD_OK) first = rc;
   }
+  if (h->prof_used) prof_flush(h);
   return first;
 }
 
@@ -727,7 +908,7 @@ int sd_get_fields(sd_handle* h, double* u, double* v, double* p_ff, double* p_pm
   return SD_OK;
 }
 
-int sd_get_state(sd_handle* h, double* t, int64_t* step, double* x) {
+int sd_get_state(sd_handle* h, double* t, int64_t* step, double* x, double* xprev) {
   if (!h) return SD_E_INVAL;
   std::lock_guard<std::mutex> lk(h->mtx);
   if (t) *t = h->t;
@@ -736,16 +917,28 @@ int sd_get_state(sd_handle* h, double* t, int64_t* step, double* x) {
     launch_unpack(h->g, h->x, h->stage, h->s);
     CKR(copy_out(h, x, h->stage, sd_dof_count(h->n)));
   }
+  if (xprev) {
+    CK(cudaStreamSynchronize(h->s));
+    launch_unpack(h->g, h->have_prev ? h->xm : h->x, h->stage, h->s);
+    CKR(copy_out(h, xprev, h->stage, sd_dof_count(h->n)));
+  }
   CK(cudaStreamSynchronize(h->s));
   return SD_OK;
 }
 
-int sd_set_state(sd_handle* h, double t, int64_t step, const double* x) {
+int sd_set_state(sd_handle* h, double t, int64_t step, const double* x, const double* xprev) {
   if (!h || !x) return SD_E_INVAL;
   std::lock_guard<std::mutex> lk(h->mtx);
   CKR(copy_in_dense(h, x, sd_dof_count(h->n)));
   launch_pack(h->g, h->stage, h->x, h->s);
   CK(cudaStreamSynchronize(h->s));
+  h->have_prev = false;
+  if (xprev) {
+    CKR(copy_in_dense(h, xprev, sd_dof_count(h->n)));
+    launch_pack(h->g, h->stage, h->xm, h->s);
+    CK(cudaStreamSynchronize(h->s));
+    h->have_prev = true;
+  }
   h->t = t;
   h->step = step;
   return SD_OK;
@@ -819,6 +1012,8 @@ int sd_sync(sd_handle* h) {
 void sd_destroy(sd_handle* h) {
   if (!h) return;
   if (h->s) cudaStreamSynchronize(h->s);
+  for (auto& e : h->prof_ev)
+    if (e) cudaEventDestroy(e);
   if (h->ar.base) cudaFree(h->ar.base);
   if (h->hflag) cudaFreeHost(h->hflag);
   if (h->e0) cudaEventDestroy(h->e0);
@@ -826,6 +1021,39 @@ void sd_destroy(sd_handle* h) {
   if (h->own_stream && h->s) cudaStreamDestroy(h->s);
   delete h;
 }
+
+int sd_profile(sd_handle* h, int32_t kernel, int32_t enable) {
+  if (!h) return SD_E_INVAL;
+  std::lock_guard<std::mutex> lk(h->mtx);
+  CK(cudaStreamSynchronize(h->s));
+  prof_flush(h);
+  if (h->prof_ev.empty()) {
+    h->prof_ev.resize(4096);
+    h->prof_bytes_pending.resize(2048);
+    h->prof_flops_pending.resize(2048);
+    for (auto& e : h->prof_ev) CK(cudaEventCreate(&e));
+  }
+  h->prof_id = enable ? kernel : -1;
+  h->prof_ms = 0.0;
+  h->prof_bytes = 0.0;
+  h->prof_flops = 0.0;
+  h->prof_launches = 0;
+  return SD_OK;
+}
+
+int sd_profile_read(sd_handle* h, double* total_ms, int64_t* launches, double* bytes, double* flops) {
+  if (!h) return SD_E_INVAL;
+  std::lock_guard<std::mutex> lk(h->mtx);
+  CK(cudaStreamSynchronize(h->s));
+  prof_flush(h);
+  if (total_ms) *total_ms = h->prof_ms;
+  if (launches) *launches = h->prof_launches;
+  if (bytes) *bytes = h->prof_bytes;
+  if (flops) *flops = h->prof_flops;
+  return SD_OK;
+}
+
+int64_t sd_launch_count(void) { return (int64_t)sdk::g_launch_count.load(); }
 
 const char* sd_strerror(int code) {
   switch (code) {

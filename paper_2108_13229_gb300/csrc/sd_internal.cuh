@@ -16,7 +16,13 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace sdk {
+
+// process-wide count of kernel launches made by this library
+extern std::atomic<long long> g_launch_count;
+#define SD_COUNT(k) ::sdk::g_launch_count.fetch_add((k), std::memory_order_relaxed)
 
 struct Geom {
   int n;        // cells per side
@@ -116,6 +122,25 @@ void launch_prolong_V(int nf, int Pf, T* x, int nc, int Pc, const T* e, cudaStre
 template <typename T>
 void launch_prolong_D(int nf, int Pf, T* x, int nc, int Pc, const T* e, cudaStream_t s);
 
+// Fused coarse V-cycle: levels c[0] (entry) .. c[nlev-1] (coarsest) in one
+// CTA with shared-memory work vectors.  kind 0: velocity block, 1: cell block.
+#define SD_CYC_MAXL 6
+template <typename T>
+struct CoarseCycle {
+  int nlev, kind, deg, m;
+  Coef<T> c[SD_CYC_MAXL];
+  T cha[SD_CYC_MAXL][8], chc[SD_CYC_MAXL][8];
+  const double* Ainv;
+  const int* idx;
+  const T* b_in;  // entry-level right-hand side (global, padded layout)
+  T* x_out;       // entry-level result (global; valid entries written)
+};
+template <typename T>
+size_t coarse_cycle_smem(const CoarseCycle<T>& q);
+// returns -1 (nothing launched) if the levels need more shared memory than allowed
+template <typename T>
+int launch_coarse_cycle(const CoarseCycle<T>& q, cudaStream_t s);
+
 // preconditioner glue on the fine level (Sec. 4 block preconditioners):
 //  entry: zpf = schur * r_pf + cmass * eP (eP: pressure-Laplacian solve, may be
 //  null); rV = T(r_v - B zpf) (B omitted: use_B == 0)
@@ -134,15 +159,21 @@ template <typename T>
 void launch_precond_exit(const Coef<double>& c, double* z, const T* eD, cudaStream_t s);
 
 // ------------------------------------------------------------- sd_krylov.cu
+// number of blocks (= partial sums per dot product) for a vector of length len
 int reduce_blocks(long long len);
-// partial[blk * kmax + i] = sum over the block's range of V_i . w, i < k
+// partial[i * ps + blk] = sum over the block's elements of V_i . w, i < k
+//   self != 0: also w . w as entry k; cond (may be null): skipped when cond[0] == 0
 void launch_mdot(const double* V, long long vstride, int k, const double* w, long long len, double* partial,
-                 int kmax, int nblk, cudaStream_t s);
+                 int ps, int nblk, int self, const double* cond, cudaStream_t s);
 // w -= sum_i coef[i] V_i, then partial dots of V_i . w (mode 1) or w . w (mode 2)
 void launch_mupdate(const double* V, long long vstride, int k, const double* coef, double* w, long long len,
-                    double* partial, int kmax, int nblk, int mode, cudaStream_t s);
-// out[i] = sum_b partial[b * kmax + i] (+ out[i] if accumulate), fixed order
-void launch_reduce(const double* partial, int nblk, int k, int kmax, double* out, int accumulate, cudaStream_t s);
+                    double* partial, int ps, int nblk, int mode, const double* cond, cudaStream_t s);
+// out[i] = sum_b partial[i * ps + b] (+ out[i] if accumulate), fixed order
+//   cond (may be null): when cond[0] == 0 the outputs are set to zero
+void launch_reduce(const double* partial, int nblk, int k, int ps, double* out, int accumulate, const double* cond,
+                   cudaStream_t s);
+void launch_reorth_decide(const double* nw2, const double* n2a, double eta2, double* flag, cudaStream_t s);
+void launch_extrapolate(double* x, double* xm, long long len, cudaStream_t s);
 // generic dot of two vectors: partials then reduce -> out[0]
 void launch_dot(const double* a, const double* b, long long len, double* partial, int nblk, double* out,
                 cudaStream_t s);
@@ -151,8 +182,10 @@ void launch_scale_by(const double* x, double* y, long long len, const double* sd
 void launch_axpy_multi(double* x, const double* Z, long long zstride, const double* ycoef, int k, long long len,
                        cudaStream_t s);
 
-void launch_givens(double* st, int j, int m, const double* hcol1, const double* hcol2, const double* nrm2,
-                   double* flag, cudaStream_t s);
+//   the new column is hcol1 + hcol2; its sub-diagonal is sqrt(nrm2b) if reo is null
+//   or reo[0] != 0 (second Gram-Schmidt pass done), else sqrt(nrm2a)
+void launch_givens(double* st, int j, int m, const double* hcol1, const double* hcol2, const double* nrm2a,
+                   const double* nrm2b, const double* reo, double* flag, cudaStream_t s);
 void launch_backsolve(double* st, int k, int m, double* y, cudaStream_t s);
 void launch_init_cycle(double* st, int m, const double* beta2, double* flag, cudaStream_t s);
 

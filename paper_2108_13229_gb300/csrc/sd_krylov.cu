@@ -17,113 +17,185 @@
 
 namespace sdk {
 
+std::atomic<long long> g_launch_count{0};
+
 static const int RT = 256;      // threads per reduction block
+static const int KE = 4;        // vector elements owned by one thread
 static const int KMAX_REG = 32;  // max dot products per pass
 
+// Blocks of the Krylov kernels for a vector of length len: each block owns
+// RT * KE consecutive elements (fixed for a given len, so every reduction
+// sums its partials in the same order on every call).
 int reduce_blocks(long long len) {
-  long long nb = (len + RT * 4 - 1) / (RT * 4);
-  if (nb > 152 * 4) nb = 152 * 4;
-  if (nb < 1) nb = 1;
-  return (int)nb;
+  long long nb = (len + (long long)RT * KE - 1) / ((long long)RT * KE);
+  return (int)(nb < 1 ? 1 : nb);
 }
 
-// block-wide sum of acc[q] for q < k; result of q in partial[blockIdx.x*kmax+q]
-__device__ __forceinline__ void block_sum_store(double* acc, int k, double* partial, int kmax) {
-  __shared__ double sm[RT / 32][KMAX_REG];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Warp-sum v and store it in red[warp][q] (lane 0).
+__device__ __forceinline__ void warp_store(double v, double (*red)[KMAX_REG], int q) {
 #pragma unroll
-  for (int q = 0; q < KMAX_REG; ++q) {
-    if (q < k) {
-      double v = acc[q];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if (lane == 0) sm[warp][q] = v;
-    }
-  }
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][q] = v;
+}
+
+// Sum red[.][q] over the block's warps for q < k into partial[q * ps + block].
+__device__ __forceinline__ void block_store(double (*red)[KMAX_REG], int k, double* partial, int ps) {
   __syncthreads();
   if (threadIdx.x < k) {
     double s = 0.0;
 #pragma unroll
-    for (int w = 0; w < RT / 32; ++w) s += sm[w][threadIdx.x];
-    partial[(long long)blockIdx.x * kmax + threadIdx.x] = s;
+    for (int w = 0; w < RT / 32; ++w) s += red[w][threadIdx.x];
+    partial[(long long)threadIdx.x * ps + blockIdx.x] = s;
   }
 }
 
+// partial[q * ps + blk] = sum over the block's elements of V_q . w, q < k;
+// with self != 0 also w . w as entry k.  cond (may be null): skip when 0.
 __global__ void __launch_bounds__(RT) k_mdot(const double* __restrict__ V, long long vs, int k,
                                              const double* __restrict__ w, long long len, double* __restrict__ partial,
-                                             int kmax) {
-  double acc[KMAX_REG];
+                                             int ps, int self, const double* __restrict__ cond) {
+  if (cond && cond[0] == 0.0) return;
+  __shared__ double red[RT / 32][KMAX_REG];
+  const long long base = (long long)blockIdx.x * RT * KE + threadIdx.x;
+  double we[KE];
 #pragma unroll
-  for (int q = 0; q < KMAX_REG; ++q) acc[q] = 0.0;
-  const long long stride = (long long)gridDim.x * RT;
-  for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < len; e += stride) {
-    const double we = w[e];
-#pragma unroll
-    for (int q = 0; q < KMAX_REG; ++q)
-      if (q < k) acc[q] = fma(V[q * vs + e], we, acc[q]);
+  for (int t = 0; t < KE; ++t) {
+    const long long e = base + (long long)t * RT;
+    we[t] = e < len ? w[e] : 0.0;
   }
-  block_sum_store(acc, k, partial, kmax);
+  for (int q = 0; q < k; ++q) {
+    const double* vq = V + (long long)q * vs;
+    double s = 0.0;
+#pragma unroll
+    for (int t = 0; t < KE; ++t) {
+      const long long e = base + (long long)t * RT;
+      if (e < len) s = fma(vq[e], we[t], s);
+    }
+    warp_store(s, red, q);
+  }
+  if (self) {
+    double s = 0.0;
+#pragma unroll
+    for (int t = 0; t < KE; ++t) s = fma(we[t], we[t], s);
+    warp_store(s, red, k);
+  }
+  block_store(red, k + (self ? 1 : 0), partial, ps);
 }
 
-void launch_mdot(const double* V, long long vstride, int k, const double* w, long long len, double* partial, int kmax,
-                 int nblk, cudaStream_t s) {
-  k_mdot<<<nblk, RT, 0, s>>>(V, vstride, k, w, len, partial, kmax);
+void launch_mdot(const double* V, long long vstride, int k, const double* w, long long len, double* partial, int ps,
+                 int nblk, int self, const double* cond, cudaStream_t s) {
+  SD_COUNT(1);
+  k_mdot<<<nblk, RT, 0, s>>>(V, vstride, k, w, len, partial, ps, self, cond);
 }
 
-// mode 1: w -= sum coef_q V_q, partial dots V_q . w   (second CGS pass)
-// mode 2: w -= sum coef_q V_q, partial dot w . w      (norm of the new vector)
+// w -= sum_q coef_q V_q, then
+//   mode 1: partial dots V_q . w (second Gram-Schmidt pass),
+//   mode 2: partial w . w (norm of the new basis vector).
 __global__ void __launch_bounds__(RT) k_mupdate(const double* __restrict__ V, long long vs, int k,
                                                 const double* __restrict__ coef, double* __restrict__ w,
-                                                long long len, double* __restrict__ partial, int kmax, int mode) {
+                                                long long len, double* __restrict__ partial, int ps, int mode,
+                                                const double* __restrict__ cond) {
+  if (cond && cond[0] == 0.0) return;
   __shared__ double cf[KMAX_REG];
+  __shared__ double red[RT / 32][KMAX_REG];
   if (threadIdx.x < KMAX_REG) cf[threadIdx.x] = threadIdx.x < k ? coef[threadIdx.x] : 0.0;
   __syncthreads();
-  double acc[KMAX_REG];
+  const long long base = (long long)blockIdx.x * RT * KE + threadIdx.x;
+  double we[KE];
 #pragma unroll
-  for (int q = 0; q < KMAX_REG; ++q) acc[q] = 0.0;
-  const long long stride = (long long)gridDim.x * RT;
-  for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < len; e += stride) {
-    double we = w[e];
+  for (int t = 0; t < KE; ++t) {
+    const long long e = base + (long long)t * RT;
+    we[t] = e < len ? w[e] : 0.0;
+  }
+  for (int q = 0; q < k; ++q) {
+    const double* vq = V + (long long)q * vs;
+    const double c = cf[q];
 #pragma unroll
-    for (int q = 0; q < KMAX_REG; ++q)
-      if (q < k) we = fma(-cf[q], V[q * vs + e], we);
-    w[e] = we;
-    if (mode == 1) {
-#pragma unroll
-      for (int q = 0; q < KMAX_REG; ++q)
-        if (q < k) acc[q] = fma(V[q * vs + e], we, acc[q]);
-    } else {
-      acc[0] = fma(we, we, acc[0]);
+    for (int t = 0; t < KE; ++t) {
+      const long long e = base + (long long)t * RT;
+      if (e < len) we[t] = fma(-c, vq[e], we[t]);
     }
   }
-  block_sum_store(acc, mode == 1 ? k : 1, partial, kmax);
+#pragma unroll
+  for (int t = 0; t < KE; ++t) {
+    const long long e = base + (long long)t * RT;
+    if (e < len) w[e] = we[t];
+  }
+  if (mode == 1) {
+    for (int q = 0; q < k; ++q) {
+      const double* vq = V + (long long)q * vs;
+      double s = 0.0;
+#pragma unroll
+      for (int t = 0; t < KE; ++t) {
+        const long long e = base + (long long)t * RT;
+        if (e < len) s = fma(vq[e], we[t], s);
+      }
+      warp_store(s, red, q);
+    }
+    block_store(red, k, partial, ps);
+  } else {
+    double s = 0.0;
+#pragma unroll
+    for (int t = 0; t < KE; ++t) s = fma(we[t], we[t], s);
+    warp_store(s, red, 0);
+    block_store(red, 1, partial, ps);
+  }
 }
 
 void launch_mupdate(const double* V, long long vstride, int k, const double* coef, double* w, long long len,
-                    double* partial, int kmax, int nblk, int mode, cudaStream_t s) {
-  k_mupdate<<<nblk, RT, 0, s>>>(V, vstride, k, coef, w, len, partial, kmax, mode);
+                    double* partial, int ps, int nblk, int mode, const double* cond, cudaStream_t s) {
+  SD_COUNT(1);
+  k_mupdate<<<nblk, RT, 0, s>>>(V, vstride, k, coef, w, len, partial, ps, mode, cond);
 }
 
-__global__ void k_reduce(const double* __restrict__ partial, int nblk, int k, int kmax, double* __restrict__ out,
-                         int accumulate) {
-  // one warp per output; lanes sum strided partials, then a fixed shuffle tree
+// out[q] = sum_b partial[q * ps + b] (+ out[q] if accumulate), fixed-order tree
+__global__ void k_reduce(const double* __restrict__ partial, int nblk, int k, int ps, double* __restrict__ out,
+                         int accumulate, const double* __restrict__ cond) {
+  __shared__ double sm[RT / 32];
   const int q = blockIdx.x;
   if (q >= k) return;
+  if (cond && cond[0] == 0.0) {  // skipped pass: its coefficients are zero
+    if (threadIdx.x == 0 && !accumulate) out[q] = 0.0;
+    return;
+  }
+  const double* p = partial + (long long)q * ps;
   double s = 0.0;
-  for (int b = threadIdx.x; b < nblk; b += 32) s += partial[(long long)b * kmax + q];
+  for (int b = threadIdx.x; b < nblk; b += RT) s += p[b];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (threadIdx.x == 0) out[q] = accumulate ? out[q] + s : s;
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < RT / 32; ++w) t += sm[w];
+    out[q] = accumulate ? out[q] + t : t;
+  }
 }
 
-void launch_reduce(const double* partial, int nblk, int k, int kmax, double* out, int accumulate, cudaStream_t s) {
-  k_reduce<<<k, 32, 0, s>>>(partial, nblk, k, kmax, out, accumulate);
+void launch_reduce(const double* partial, int nblk, int k, int ps, double* out, int accumulate, const double* cond,
+                   cudaStream_t s) {
+  SD_COUNT(1);
+  k_reduce<<<k, RT, 0, s>>>(partial, nblk, k, ps, out, accumulate, cond);
+}
+
+// Selective re-orthogonalisation (Daniel-Gragg-Kaufman-Stewart test): a second
+// Gram-Schmidt pass is needed when the projection removed most of w,
+// ||w'||^2 < eta^2 ||w||^2.  flag[0] = 1 (pass needed) or 0.
+__global__ void k_reorth_decide(const double* nw2, const double* n2a, double eta2, double* flag) {
+  if (threadIdx.x == 0) flag[0] = (n2a[0] < eta2 * nw2[0]) ? 1.0 : 0.0;
+}
+
+void launch_reorth_decide(const double* nw2, const double* n2a, double eta2, double* flag, cudaStream_t s) {
+  SD_COUNT(1);
+  k_reorth_decide<<<1, 32, 0, s>>>(nw2, n2a, eta2, flag);
 }
 
 void launch_dot(const double* a, const double* b, long long len, double* partial, int nblk, double* out,
                 cudaStream_t s) {
-  k_mdot<<<nblk, RT, 0, s>>>(a, 0, 1, b, len, partial, 1);
-  k_reduce<<<1, 32, 0, s>>>(partial, nblk, 1, 1, out, 0);
+  SD_COUNT(2);
+  k_mdot<<<nblk, RT, 0, s>>>(a, 0, 1, b, len, partial, nblk, 0, nullptr);
+  k_reduce<<<1, RT, 0, s>>>(partial, nblk, 1, nblk, out, 0, nullptr);
 }
 
 // mode 0: y = sdev[0] * x ; mode 1: y = x / sqrt(sdev[0])
@@ -135,25 +207,43 @@ __global__ void k_scale_by(const double* __restrict__ x, double* __restrict__ y,
 }
 
 void launch_scale_by(const double* x, double* y, long long len, const double* sdev, int mode, cudaStream_t s) {
-  k_scale_by<<<reduce_blocks(len), RT, 0, s>>>(x, y, len, sdev, mode);
+  SD_COUNT(1);
+  const long long nb = (len + RT - 1) / RT;
+  k_scale_by<<<(int)(nb < 152 * 16 ? nb : 152 * 16), RT, 0, s>>>(x, y, len, sdev, mode);
 }
 
+// x += sum_q y_q Z_q
 __global__ void __launch_bounds__(RT) k_axpy_multi(double* __restrict__ x, const double* __restrict__ Z, long long zs,
                                                    const double* __restrict__ y, int k, long long len) {
   __shared__ double cf[KMAX_REG];
   if (threadIdx.x < KMAX_REG) cf[threadIdx.x] = threadIdx.x < k ? y[threadIdx.x] : 0.0;
   __syncthreads();
-  for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < len; e += (long long)gridDim.x * RT) {
-    double xe = x[e];
+  const long long base = (long long)blockIdx.x * RT * KE + threadIdx.x;
+  double xe[KE];
 #pragma unroll
-    for (int q = 0; q < KMAX_REG; ++q)
-      if (q < k) xe = fma(cf[q], Z[q * zs + e], xe);
-    x[e] = xe;
+  for (int t = 0; t < KE; ++t) {
+    const long long e = base + (long long)t * RT;
+    xe[t] = e < len ? x[e] : 0.0;
+  }
+  for (int q = 0; q < k; ++q) {
+    const double* zq = Z + (long long)q * zs;
+    const double c = cf[q];
+#pragma unroll
+    for (int t = 0; t < KE; ++t) {
+      const long long e = base + (long long)t * RT;
+      if (e < len) xe[t] = fma(c, zq[e], xe[t]);
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < KE; ++t) {
+    const long long e = base + (long long)t * RT;
+    if (e < len) x[e] = xe[t];
   }
 }
 
 void launch_axpy_multi(double* x, const double* Z, long long zstride, const double* ycoef, int k, long long len,
                        cudaStream_t s) {
+  SD_COUNT(1);
   k_axpy_multi<<<reduce_blocks(len), RT, 0, s>>>(x, Z, zstride, ycoef, k, len);
 }
 
@@ -175,12 +265,15 @@ __global__ void k_init_cycle(double* st, int m, const double* beta2, double* fla
 }
 
 void launch_init_cycle(double* st, int m, const double* beta2, double* flag, cudaStream_t s) {
+  SD_COUNT(1);
   k_init_cycle<<<1, 32, 0, s>>>(st, m, beta2, flag);
 }
 
-__global__ void k_givens(double* st, int j, int m, const double* h1, const double* h2, const double* nrm2,
-                         double* flag) {
+__global__ void k_givens(double* st, int j, int m, const double* h1, const double* h2, const double* nrm2a,
+                         const double* nrm2b, const double* reo, double* flag) {
   if (threadIdx.x != 0) return;
+  const bool second = reo == nullptr || reo[0] != 0.0;
+  const double* nrm2 = second ? nrm2b : nrm2a;
   double* R = st;
   double* cs = st + (m + 1) * m;
   double* sn = cs + m;
@@ -208,11 +301,28 @@ __global__ void k_givens(double* st, int j, int m, const double* h1, const doubl
   flag[1] = hn > 0.0 ? 1.0 / hn : 0.0;
   flag[2] = (isfinite(r) && isfinite(g[j + 1])) ? 0.0 : 1.0;
   flag[3] = hn > 0.0 ? 0.0 : 1.0;
+  flag[4] = second ? 1.0 : 0.0;
 }
 
-void launch_givens(double* st, int j, int m, const double* hcol1, const double* hcol2, const double* nrm2,
-                   double* flag, cudaStream_t s) {
-  k_givens<<<1, 32, 0, s>>>(st, j, m, hcol1, hcol2, nrm2, flag);
+void launch_givens(double* st, int j, int m, const double* hcol1, const double* hcol2, const double* nrm2a,
+                   const double* nrm2b, const double* reo, double* flag, cudaStream_t s) {
+  SD_COUNT(1);
+  k_givens<<<1, 32, 0, s>>>(st, j, m, hcol1, hcol2, nrm2a, nrm2b, reo, flag);
+}
+
+// x_m <- x, x <- 2 x - x_m (linear extrapolation in time of the initial guess)
+__global__ void k_extrapolate(double* __restrict__ x, double* __restrict__ xm, long long len) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len; e += (long long)gridDim.x * blockDim.x) {
+    const double t = x[e];
+    x[e] = 2.0 * t - xm[e];
+    xm[e] = t;
+  }
+}
+
+void launch_extrapolate(double* x, double* xm, long long len, cudaStream_t s) {
+  SD_COUNT(1);
+  const long long nb = (len + RT - 1) / RT;
+  k_extrapolate<<<(int)(nb < 152 * 16 ? nb : 152 * 16), RT, 0, s>>>(x, xm, len);
 }
 
 __global__ void k_backsolve(const double* st, int k, int m, double* y) {
@@ -226,7 +336,8 @@ __global__ void k_backsolve(const double* st, int k, int m, double* y) {
   }
 }
 
-void launch_backsolve(double* st, int k, int m, double* y, cudaStream_t s) { k_backsolve<<<1, 32, 0, s>>>(st, k, m, y); }
+void launch_backsolve(double* st, int k, int m, double* y, cudaStream_t s) {
+  SD_COUNT(1); k_backsolve<<<1, 32, 0, s>>>(st, k, m, y); }
 
 // ------------------------------------------------------ dense coarse solve
 template <typename T>
@@ -248,6 +359,7 @@ __global__ void k_dense_solve(const double* __restrict__ Ainv, const int* __rest
 
 template <typename T>
 void launch_dense_solve(const double* Ainv, const int* idx, int m, const T* b, T* x, cudaStream_t s) {
+  SD_COUNT(1);
   k_dense_solve<T><<<1, 512, sizeof(double) * m, s>>>(Ainv, idx, m, b, x);
 }
 
@@ -303,6 +415,7 @@ __global__ void k_gj_inverse(double* A, double* W, int m, int* status) {
 }
 
 void launch_gj_inverse(double* A, double* work, int m, int* status, cudaStream_t s) {
+  SD_COUNT(1);
   k_gj_inverse<<<1, 1024, sizeof(double) * m, s>>>(A, work, m, status);
 }
 
@@ -311,6 +424,7 @@ __global__ void k_identity_batch(double* X, long long stride, const int* idx, in
   if (k < m) X[(long long)k * stride + idx[k]] = 1.0;
 }
 void launch_identity_batch(double* X, long long stride, const int* idx, int m, cudaStream_t s) {
+  SD_COUNT(1);
   k_identity_batch<<<(m + 127) / 128, 128, 0, s>>>(X, stride, idx, m);
 }
 
@@ -322,6 +436,7 @@ __global__ void k_gather_dense(const double* Y, long long stride, const int* idx
   A[e] = Y[(long long)k * stride + idx[r]];
 }
 void launch_gather_dense(const double* Y, long long stride, const int* idx, int m, double* A, cudaStream_t s) {
+  SD_COUNT(1);
   const long long tot = (long long)m * m;
   k_gather_dense<<<(int)((tot + 255) / 256), 256, 0, s>>>(Y, stride, idx, m, A);
 }
@@ -330,7 +445,8 @@ __global__ void k_fill(double* x, double v, long long len) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len; e += (long long)gridDim.x * blockDim.x)
     x[e] = v;
 }
-void launch_fill(double* x, double v, long long len, cudaStream_t s) { k_fill<<<reduce_blocks(len), RT, 0, s>>>(x, v, len); }
+void launch_fill(double* x, double v, long long len, cudaStream_t s) {
+  SD_COUNT(1); k_fill<<<reduce_blocks(len), RT, 0, s>>>(x, v, len); }
 
 // deterministic pseudo-random fill in [-1, 1] (start vector of the power iteration)
 __global__ void k_hash_fill(double* x, long long len, unsigned seed) {
@@ -343,6 +459,7 @@ __global__ void k_hash_fill(double* x, long long len, unsigned seed) {
   }
 }
 void launch_hash_fill(double* x, long long len, unsigned seed, cudaStream_t s) {
+  SD_COUNT(1);
   k_hash_fill<<<reduce_blocks(len), RT, 0, s>>>(x, len, seed);
 }
 

@@ -182,23 +182,22 @@ __global__ void k_apply_full(Coef<double> c, const double* __restrict__ x, const
 }
 
 void launch_apply_full(const Coef<double>& c, const double* x, const double* b, double* y, cudaStream_t s) {
+  SD_COUNT(1);
   k_apply_full<<<grid2(c.n + 1, c.n + 1), dim3(BX, BY), 0, s>>>(c, x, b, y);
 }
 
 // ------------------------------------------------------ block V smoothers
+// One Chebyshev step at position (i, j) of the velocity block (u face (i,j)
+// if j < n, v face (i,j) if i < n).  Dirichlet faces take x = b exactly.
 template <typename T>
-__global__ void k_cheb_V(Coef<T> c, const T* __restrict__ xin, const T* __restrict__ b, T* __restrict__ d,
-                         T* __restrict__ xout, T a, T cc, long long bstride) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void cheb_V_at(const Coef<T>& c, const T* __restrict__ xin, const T* __restrict__ b,
+                                          T* __restrict__ d, T* __restrict__ xout, T a, T cc, int i, int j) {
   const int n = c.n, P = c.P;
-  if (i > n || j > n) return;
-  const long long bo = (long long)blockIdx.z * bstride;
-  const T* u = xin ? xin + bo : nullptr;
-  const T* v = xin ? xin + bo + (long long)n * P : nullptr;
+  const T* u = xin;
+  const T* v = xin ? xin + (long long)n * P : nullptr;
   const bool rd = xin != nullptr;
   if (j < n) {
-    const long long k = bo + (long long)j * P + i;
+    const long long k = (long long)j * P + i;
     if (i == 0 || i == n) {
       xout[k] = b[k];
       d[k] = T(0);
@@ -213,7 +212,7 @@ __global__ void k_cheb_V(Coef<T> c, const T* __restrict__ xin, const T* __restri
     }
   }
   if (i < n) {
-    const long long k = bo + (long long)n * P + (long long)j * P + i;
+    const long long k = (long long)n * P + (long long)j * P + i;
     if (j == n) {
       xout[k] = b[k];
       d[k] = T(0);
@@ -230,25 +229,33 @@ __global__ void k_cheb_V(Coef<T> c, const T* __restrict__ xin, const T* __restri
 }
 
 template <typename T>
+__global__ void k_cheb_V(Coef<T> c, const T* __restrict__ xin, const T* __restrict__ b, T* __restrict__ d,
+                         T* __restrict__ xout, T a, T cc, long long bstride) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > c.n || j > c.n) return;
+  const long long bo = (long long)blockIdx.z * bstride;
+  cheb_V_at(c, xin ? xin + bo : nullptr, b + bo, d + bo, xout + bo, a, cc, i, j);
+}
+
+template <typename T>
 void launch_cheb_V(const Coef<T>& c, const T* x_in, const T* b, T* d, T* x_out, T a, T cc, int nbatch,
                    long long bstride, cudaStream_t s) {
+  SD_COUNT(1);
   dim3 g = grid2(c.n + 1, c.n + 1);
   g.z = nbatch;
   k_cheb_V<T><<<g, dim3(BX, BY), 0, s>>>(c, x_in, b, d, x_out, a, cc, bstride);
 }
 
+// r = b - V x (mode 0; b == nullptr: -V x), D^-1 V x (mode 1), V x (mode 2)
 template <typename T>
-__global__ void k_resid_V(Coef<T> c, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, int jac,
-                          long long bstride) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void resid_V_at(const Coef<T>& c, const T* __restrict__ x, const T* __restrict__ b,
+                                           T* __restrict__ r, int jac, int i, int j) {
   const int n = c.n, P = c.P;
-  if (i > n || j > n) return;
-  const long long bo = (long long)blockIdx.z * bstride;
-  const T* u = x + bo;
-  const T* v = x + bo + (long long)n * P;
+  const T* u = x;
+  const T* v = x + (long long)n * P;
   if (j < n) {
-    const long long k = bo + (long long)j * P + i;
+    const long long k = (long long)j * P + i;
     T ax, dg = T(1);
     if (i == 0 || i == n) {
       ax = x[k];
@@ -260,7 +267,7 @@ __global__ void k_resid_V(Coef<T> c, const T* __restrict__ x, const T* __restric
     r[k] = jac == 1 ? ax / dg : (jac == 2 ? ax : (b ? b[k] - ax : -ax));
   }
   if (i < n) {
-    const long long k = bo + (long long)n * P + (long long)j * P + i;
+    const long long k = (long long)n * P + (long long)j * P + i;
     T ax, dg = T(1);
     if (j == n) {
       ax = x[k];
@@ -274,8 +281,19 @@ __global__ void k_resid_V(Coef<T> c, const T* __restrict__ x, const T* __restric
 }
 
 template <typename T>
+__global__ void k_resid_V(Coef<T> c, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, int jac,
+                          long long bstride) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > c.n || j > c.n) return;
+  const long long bo = (long long)blockIdx.z * bstride;
+  resid_V_at(c, x + bo, b ? b + bo : nullptr, r + bo, jac, i, j);
+}
+
+template <typename T>
 void launch_resid_V(const Coef<T>& c, const T* x, const T* b, T* r, int jac, int nbatch, long long bstride,
                     cudaStream_t s) {
+  SD_COUNT(1);
   dim3 g = grid2(c.n + 1, c.n + 1);
   g.z = nbatch;
   k_resid_V<T><<<g, dim3(BX, BY), 0, s>>>(c, x, b, r, jac, bstride);
@@ -283,17 +301,12 @@ void launch_resid_V(const Coef<T>& c, const T* x, const T* b, T* r, int jac, int
 
 // ------------------------------------------------------ block D' smoothers
 template <typename T>
-__global__ void k_cheb_D(Coef<T> c, const T* __restrict__ xin, const T* __restrict__ b, T* __restrict__ d,
-                         T* __restrict__ xout, T a, T cc, long long bstride) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int n = c.n, P = c.P;
-  if (i >= n || j >= n) return;
-  const long long bo = (long long)blockIdx.z * bstride;
-  const long long k = bo + (long long)j * P + i;
+__device__ __forceinline__ void cheb_D_at(const Coef<T>& c, const T* __restrict__ xin, const T* __restrict__ b,
+                                          T* __restrict__ d, T* __restrict__ xout, T a, T cc, int i, int j) {
+  const long long k = (long long)j * c.P + i;
   const bool rd = xin != nullptr;
   T off, dg;
-  d_row(c, rd ? xin + bo : nullptr, i, j, rd, off, dg);
+  d_row(c, xin, i, j, rd, off, dg);
   const T xc = rd ? xin[k] : T(0);
   const T r = b[k] - (dg * xc + off);
   const T dn = (a != T(0) ? a * d[k] : T(0)) + cc * r / dg;
@@ -302,11 +315,32 @@ __global__ void k_cheb_D(Coef<T> c, const T* __restrict__ xin, const T* __restri
 }
 
 template <typename T>
+__global__ void k_cheb_D(Coef<T> c, const T* __restrict__ xin, const T* __restrict__ b, T* __restrict__ d,
+                         T* __restrict__ xout, T a, T cc, long long bstride) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= c.n || j >= c.n) return;
+  const long long bo = (long long)blockIdx.z * bstride;
+  cheb_D_at(c, xin ? xin + bo : nullptr, b + bo, d + bo, xout + bo, a, cc, i, j);
+}
+
+template <typename T>
 void launch_cheb_D(const Coef<T>& c, const T* x_in, const T* b, T* d, T* x_out, T a, T cc, int nbatch,
                    long long bstride, cudaStream_t s) {
+  SD_COUNT(1);
   dim3 g = grid2(c.n, c.n);
   g.z = nbatch;
   k_cheb_D<T><<<g, dim3(BX, BY), 0, s>>>(c, x_in, b, d, x_out, a, cc, bstride);
+}
+
+template <typename T>
+__device__ __forceinline__ void resid_D_at(const Coef<T>& c, const T* __restrict__ x, const T* __restrict__ b,
+                                           T* __restrict__ r, int jac, int i, int j) {
+  const long long k = (long long)j * c.P + i;
+  T off, dg;
+  d_row(c, x, i, j, true, off, dg);
+  const T ax = dg * x[k] + off;
+  r[k] = jac == 1 ? ax / dg : (jac == 2 ? ax : (b ? b[k] - ax : -ax));
 }
 
 template <typename T>
@@ -314,19 +348,15 @@ __global__ void k_resid_D(Coef<T> c, const T* __restrict__ x, const T* __restric
                           long long bstride) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int n = c.n, P = c.P;
-  if (i >= n || j >= n) return;
+  if (i >= c.n || j >= c.n) return;
   const long long bo = (long long)blockIdx.z * bstride;
-  const long long k = bo + (long long)j * P + i;
-  T off, dg;
-  d_row(c, x + bo, i, j, true, off, dg);
-  const T ax = dg * x[k] + off;
-  r[k] = jac == 1 ? ax / dg : (jac == 2 ? ax : (b ? b[k] - ax : -ax));
+  resid_D_at(c, x + bo, b ? b + bo : nullptr, r + bo, jac, i, j);
 }
 
 template <typename T>
 void launch_resid_D(const Coef<T>& c, const T* x, const T* b, T* r, int jac, int nbatch, long long bstride,
                     cudaStream_t s) {
+  SD_COUNT(1);
   dim3 g = grid2(c.n, c.n);
   g.z = nbatch;
   k_resid_D<T><<<g, dim3(BX, BY), 0, s>>>(c, x, b, r, jac, bstride);
@@ -341,10 +371,8 @@ void launch_resid_D(const Coef<T>& c, const T* x, const T* b, T* r, int jac, int
 //     cell-centred in x with weights 3/4, 1/4 and negative ghosts at the walls.
 // Restriction is its transpose applied to the fine residual.
 template <typename T>
-__global__ void k_restrict_V(int nf, int Pf, const T* __restrict__ r, int nc, int Pc, T* __restrict__ bc) {
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
-  const int J = blockIdx.y * blockDim.y + threadIdx.y;
-  if (I > nc || J > nc) return;
+__device__ __forceinline__ void restrict_V_at(int nf, int Pf, const T* __restrict__ r, int nc, int Pc,
+                                              T* __restrict__ bc, int I, int J) {
   const T* ru = r;
   const T* rv = r + (long long)nf * Pf;
   if (J < nc) {
@@ -391,8 +419,24 @@ __global__ void k_restrict_V(int nf, int Pf, const T* __restrict__ r, int nc, in
 }
 
 template <typename T>
+__global__ void k_restrict_V(int nf, int Pf, const T* __restrict__ r, int nc, int Pc, T* __restrict__ bc) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I > nc || J > nc) return;
+  restrict_V_at(nf, Pf, r, nc, Pc, bc, I, J);
+}
+
+template <typename T>
 void launch_restrict_V(int nf, int Pf, const T* r, int nc, int Pc, T* bc, cudaStream_t s) {
+  SD_COUNT(1);
   k_restrict_V<T><<<grid2(nc + 1, nc + 1), dim3(BX, BY), 0, s>>>(nf, Pf, r, nc, Pc, bc);
+}
+
+template <typename T>
+__device__ __forceinline__ void restrict_D_at(int Pf, const T* __restrict__ r, int Pc, T* __restrict__ bc, int I,
+                                              int J) {
+  const T* r0 = r + (long long)(2 * J) * Pf + 2 * I;
+  bc[(long long)J * Pc + I] = (r0[0] + r0[1]) + (r0[Pf] + r0[Pf + 1]);
 }
 
 template <typename T>
@@ -400,12 +444,12 @@ __global__ void k_restrict_D(int nf, int Pf, const T* __restrict__ r, int nc, in
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= nc || J >= nc) return;
-  const T* r0 = r + (long long)(2 * J) * Pf + 2 * I;
-  bc[(long long)J * Pc + I] = (r0[0] + r0[1]) + (r0[Pf] + r0[Pf + 1]);
+  restrict_D_at(Pf, r, Pc, bc, I, J);
 }
 
 template <typename T>
 void launch_restrict_D(int nf, int Pf, const T* r, int nc, int Pc, T* bc, cudaStream_t s) {
+  SD_COUNT(1);
   k_restrict_D<T><<<grid2(nc, nc), dim3(BX, BY), 0, s>>>(nf, Pf, r, nc, Pc, bc);
 }
 
@@ -426,10 +470,8 @@ __device__ __forceinline__ T cv_at(const T* ev, int nc, int Pc, int I, int J) {
 }
 
 template <typename T>
-__global__ void k_prolong_V(int nf, int Pf, T* __restrict__ x, int nc, int Pc, const T* __restrict__ e) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i > nf || j > nf) return;
+__device__ __forceinline__ void prolong_V_at(int nf, int Pf, T* __restrict__ x, int nc, int Pc,
+                                             const T* __restrict__ e, int i, int j) {
   const T* eu = e;
   const T* ev = e + (long long)nc * Pc;
   if (j < nf && i > 0 && i < nf) {
@@ -463,7 +505,16 @@ __global__ void k_prolong_V(int nf, int Pf, T* __restrict__ x, int nc, int Pc, c
 }
 
 template <typename T>
+__global__ void k_prolong_V(int nf, int Pf, T* __restrict__ x, int nc, int Pc, const T* __restrict__ e) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > nf || j > nf) return;
+  prolong_V_at(nf, Pf, x, nc, Pc, e, i, j);
+}
+
+template <typename T>
 void launch_prolong_V(int nf, int Pf, T* x, int nc, int Pc, const T* e, cudaStream_t s) {
+  SD_COUNT(1);
   k_prolong_V<T><<<grid2(nf + 1, nf + 1), dim3(BX, BY), 0, s>>>(nf, Pf, x, nc, Pc, e);
 }
 
@@ -478,10 +529,8 @@ __device__ __forceinline__ T cd_at(const T* e, int nc, int Pc, int I, int J) {
 }
 
 template <typename T>
-__global__ void k_prolong_D(int nf, int Pf, T* __restrict__ x, int nc, int Pc, const T* __restrict__ e) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= nf || j >= nf) return;
+__device__ __forceinline__ void prolong_D_at(int Pf, T* __restrict__ x, int nc, int Pc, const T* __restrict__ e,
+                                             int i, int j) {
   const int I = i >> 1, J = j >> 1;
   const int In = (i & 1) ? I + 1 : I - 1, Jn = (j & 1) ? J + 1 : J - 1;
   const T val = T(0.5625) * cd_at(e, nc, Pc, I, J) + T(0.1875) * (cd_at(e, nc, Pc, In, J) + cd_at(e, nc, Pc, I, Jn)) +
@@ -490,8 +539,151 @@ __global__ void k_prolong_D(int nf, int Pf, T* __restrict__ x, int nc, int Pc, c
 }
 
 template <typename T>
+__global__ void k_prolong_D(int nf, int Pf, T* __restrict__ x, int nc, int Pc, const T* __restrict__ e) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= nf || j >= nf) return;
+  prolong_D_at(Pf, x, nc, Pc, e, i, j);
+}
+
+template <typename T>
 void launch_prolong_D(int nf, int Pf, T* x, int nc, int Pc, const T* e, cudaStream_t s) {
+  SD_COUNT(1);
   k_prolong_D<T><<<grid2(nf, nf), dim3(BX, BY), 0, s>>>(nf, Pf, x, nc, Pc, e);
+}
+
+// ------------------------------------------------ fused coarse V-cycle
+// All levels from `first` down to the coarsest (n <= 32 cells per side) in
+// one CTA: every work vector lives in shared memory, the sweeps of the
+// smoother, residual, transfers and the dense coarsest solve are separated
+// by __syncthreads.  Same arithmetic, in the same order per point, as the
+// per-level kernels; it only removes the launches of the small grids.
+static __host__ __device__ inline int cyc_pitch(int n) { return ((n + 1) + 7) / 8 * 8; }
+static __host__ __device__ inline int cyc_len(int n, int kind) {
+  return kind == 0 ? (2 * n + 1) * cyc_pitch(n) : n * cyc_pitch(n);
+}
+
+template <typename T>
+__device__ void cyc_sweep(const CoarseCycle<T>& q, int l, int op, const T* xin, const T* b, T* d, T* xout, T a, T cc,
+                          T* r, const T* bnext, T* bcoarse, const T* ecoarse) {
+  const Coef<T>& c = q.c[l];
+  const int n = c.n;
+  const int w = q.kind == 0 ? n + 1 : n;
+  for (int p = threadIdx.x; p < w * w; p += blockDim.x) {
+    const int i = p % w, j = p / w;
+    if (op == 0) {
+      if (q.kind == 0) cheb_V_at(c, xin, b, d, xout, a, cc, i, j);
+      else cheb_D_at(c, xin, b, d, xout, a, cc, i, j);
+    } else if (op == 1) {
+      if (q.kind == 0) resid_V_at(c, xin, b, r, 0, i, j);
+      else resid_D_at(c, xin, b, r, 0, i, j);
+    } else if (op == 2) {  // restriction to level l + 1 (p runs over the coarse grid)
+      const int nc = q.c[l + 1].n, wc = q.kind == 0 ? nc + 1 : nc;
+      if (p < wc * wc) {
+        const int I = p % wc, J = p / wc;
+        if (q.kind == 0) restrict_V_at(n, c.P, bnext, nc, q.c[l + 1].P, bcoarse, I, J);
+        else restrict_D_at(c.P, bnext, q.c[l + 1].P, bcoarse, I, J);
+      }
+    } else {  // prolongation of level l + 1 into xout
+      const int nc = q.c[l + 1].n;
+      if (q.kind == 0) prolong_V_at(n, c.P, xout, nc, q.c[l + 1].P, ecoarse, i, j);
+      else prolong_D_at(c.P, xout, nc, q.c[l + 1].P, ecoarse, i, j);
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_coarse_cycle(CoarseCycle<T> q) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  T* B[SD_CYC_MAXL];
+  T* X[SD_CYC_MAXL];
+  T* X2[SD_CYC_MAXL];
+  T* Dd[SD_CYC_MAXL];
+  T* R[SD_CYC_MAXL];
+  T* cur[SD_CYC_MAXL];
+  int off = 0;
+  for (int l = 0; l < q.nlev; ++l) {
+    const int len = cyc_len(q.c[l].n, q.kind);
+    B[l] = sm + off; off += len;
+    X[l] = sm + off; off += len;
+    X2[l] = sm + off; off += len;
+    Dd[l] = sm + off; off += len;
+    R[l] = sm + off; off += len;
+  }
+  const int len0 = cyc_len(q.c[0].n, q.kind);
+  for (int p = threadIdx.x; p < len0; p += blockDim.x) B[0][p] = q.b_in[p];
+  __syncthreads();
+  const int L = q.nlev;
+  for (int l = 0; l + 1 < L; ++l) {
+    T* c0 = nullptr;
+    for (int k = 0; k < q.deg; ++k) {
+      T* o = (c0 == X[l]) ? X2[l] : X[l];
+      cyc_sweep<T>(q, l, 0, c0, B[l], Dd[l], o, q.cha[l][k], q.chc[l][k], nullptr, nullptr, nullptr, nullptr);
+      c0 = o;
+    }
+    cur[l] = c0;
+    cyc_sweep<T>(q, l, 1, c0, B[l], nullptr, nullptr, T(0), T(0), R[l], nullptr, nullptr, nullptr);
+    cyc_sweep<T>(q, l, 2, nullptr, nullptr, nullptr, nullptr, T(0), T(0), nullptr, R[l], B[l + 1], nullptr);
+  }
+  {  // coarsest grid: x = A^-1 b with the FP64 inverse
+    const int m = q.m;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int r = warp; r < m; r += nw) {
+      const double* row = q.Ainv + (long long)r * m;
+      double s = 0.0;
+      for (int l2 = lane; l2 < m; l2 += 32) s = fma(row[l2], (double)B[L - 1][q.idx[l2]], s);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      if (lane == 0) X[L - 1][q.idx[r]] = (T)s;
+    }
+    cur[L - 1] = X[L - 1];
+    __syncthreads();
+  }
+  for (int l = L - 2; l >= 0; --l) {
+    cyc_sweep<T>(q, l, 3, nullptr, nullptr, nullptr, cur[l], T(0), T(0), nullptr, nullptr, nullptr, cur[l + 1]);
+    T* c0 = cur[l];
+    for (int k = 0; k < q.deg; ++k) {
+      T* o = (c0 == X[l]) ? X2[l] : X[l];
+      cyc_sweep<T>(q, l, 0, c0, B[l], Dd[l], o, q.cha[l][k], q.chc[l][k], nullptr, nullptr, nullptr, nullptr);
+      c0 = o;
+    }
+    cur[l] = c0;
+  }
+  // write the valid entries of the first level's result
+  const Coef<T>& c = q.c[0];
+  const int n = c.n, w = q.kind == 0 ? n + 1 : n;
+  for (int p = threadIdx.x; p < w * w; p += blockDim.x) {
+    const int i = p % w, j = p / w;
+    if (q.kind == 0) {
+      if (j < n) q.x_out[(long long)j * c.P + i] = cur[0][j * c.P + i];
+      if (i < n) q.x_out[(long long)(n + j) * c.P + i] = cur[0][(n + j) * c.P + i];
+    } else {
+      q.x_out[(long long)j * c.P + i] = cur[0][j * c.P + i];
+    }
+  }
+}
+
+template <typename T>
+size_t coarse_cycle_smem(const CoarseCycle<T>& q) {
+  size_t tot = 0;
+  for (int l = 0; l < q.nlev; ++l) tot += 5 * (size_t)cyc_len(q.c[l].n, q.kind);
+  return tot * sizeof(T);
+}
+
+template <typename T>
+int launch_coarse_cycle(const CoarseCycle<T>& q, cudaStream_t s) {
+  const size_t sm = coarse_cycle_smem(q);
+  if (sm > 200 * 1024) return -1;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_coarse_cycle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  SD_COUNT(1);
+  k_coarse_cycle<T><<<1, 1024, sm, s>>>(q);
+  return 0;
 }
 
 // ------------------------------------------------------ preconditioner glue
@@ -505,32 +697,35 @@ __global__ void k_precond_entry(Coef<double> c, const double* __restrict__ r, do
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int n = c.n, P = c.P;
   if (i > n || j > n) return;
-  const double h = c.h;
+  const T h = (T)c.h;
   const double* rpf = r + (long long)(2 * n + 1) * P;
-  // z_pf at cell kc: schur * r_pf (+ cmass * eP, the pressure-Laplacian part)
-  auto zp = [&](long long kc) { return schur * rpf[kc] + (eP ? cmass * (double)eP[kc] : 0.0); };
-  if (i < n && j < n) z[(long long)(2 * n + 1) * P + (long long)j * P + i] = zp((long long)j * P + i);
+  // z_pf at cell kc: schur * r_pf (+ cmass * eP, the pressure-Laplacian part),
+  // evaluated in the multigrid precision T
+  const T ts = (T)schur, tm = (T)cmass;
+  auto zp = [&](long long kc) -> T { return ts * (T)rpf[kc] + (eP ? tm * eP[kc] : T(0)); };
+  if (i < n && j < n) z[(long long)(2 * n + 1) * P + (long long)j * P + i] = (double)zp((long long)j * P + i);
   if (j < n) {
     const long long k = (long long)j * P + i;
-    double val = r[k];
+    T val = (T)r[k];
     if (useB && i > 0 && i < n) val -= h * (zp(k) - zp(k - 1));
-    rV[k] = (T)val;
+    rV[k] = val;
   }
   if (i < n) {
     const long long kv = (long long)j * P + i;
     const long long k = (long long)n * P + kv;
-    double val = r[k];
+    T val = (T)r[k];
     if (useB && j < n) {
       if (j > 0) val -= h * (zp(kv) - zp(kv - P));
       else val -= h * zp(i);
     }
-    rV[k] = (T)val;
+    rV[k] = val;
   }
 }
 
 template <typename T>
 void launch_precond_entry(const Coef<double>& c, const double* r, double* z, double schur, const T* eP, double cmass,
                           int use_B, T* rV, cudaStream_t s) {
+  SD_COUNT(1);
   k_precond_entry<T><<<grid2(c.n + 1, c.n + 1), dim3(BX, BY), 0, s>>>(c, r, z, schur, eP, cmass, use_B, rV);
 }
 
@@ -551,15 +746,16 @@ __global__ void k_precond_mid(Coef<double> c, const double* __restrict__ r, doub
   }
   if (i < n && j < n) {
     const long long kc = (long long)j * P + i;
-    double val = r[(long long)(3 * n + 1) * P + kc];
-    if (useC && j == n - 1) val -= c.h * (double)eV[(long long)n * P + i];
-    rD[kc] = (T)val;
+    T val = (T)r[(long long)(3 * n + 1) * P + kc];
+    if (useC && j == n - 1) val -= (T)c.h * eV[(long long)n * P + i];
+    rD[kc] = val;
   }
 }
 
 template <typename T>
 void launch_precond_mid(const Coef<double>& c, const double* r, double* z, const T* eV, int use_C, T* rD,
                         cudaStream_t s) {
+  SD_COUNT(1);
   k_precond_mid<T><<<grid2(c.n + 1, c.n + 1), dim3(BX, BY), 0, s>>>(c, r, z, eV, use_C, rD);
 }
 
@@ -574,6 +770,7 @@ __global__ void k_precond_exit(int n, int P, double* __restrict__ z, const T* __
 
 template <typename T>
 void launch_precond_exit(const Coef<double>& c, double* z, const T* eD, cudaStream_t s) {
+  SD_COUNT(1);
   k_precond_exit<T><<<grid2(c.n, c.n), dim3(BX, BY), 0, s>>>(c.n, c.P, z, eD);
 }
 
@@ -599,6 +796,7 @@ __global__ void k_precond_bgs_pff(Coef<double> c, const double* __restrict__ r, 
 
 template <typename T>
 void launch_precond_bgs_pff(const Coef<double>& c, const double* r, double* z, const T* eV, cudaStream_t s) {
+  SD_COUNT(1);
   k_precond_bgs_pff<T><<<grid2(c.n, c.n), dim3(BX, BY), 0, s>>>(c, r, z, eV);
 }
 
@@ -610,6 +808,7 @@ __global__ void k_pack_K(const double* __restrict__ Kd, int n, double* __restric
   Kp[(long long)j * P + i] = Kd[(long long)j * n + i];
 }
 void launch_pack_K(const double* Kdense, int n, double* Kp, int P, cudaStream_t s) {
+  SD_COUNT(1);
   k_pack_K<<<grid2(n, n), dim3(BX, BY), 0, s>>>(Kdense, n, Kp, P);
 }
 
@@ -620,6 +819,7 @@ __global__ void k_fill_K(double* __restrict__ K, int n, int P, double v) {
   K[(long long)j * P + i] = v;
 }
 void launch_fill_K(double* K, int n, int P, double v, cudaStream_t s) {
+  SD_COUNT(1);
   k_fill_K<<<grid2(n, n), dim3(BX, BY), 0, s>>>(K, n, P, v);
 }
 
@@ -633,6 +833,7 @@ __global__ void k_coarsen_K(const double* __restrict__ Kf, int nf, int Pf, doubl
   Kc[(long long)J * Pc + I] = sqrt(sqrt(k0[0] * k0[1] * k0[Pf] * k0[Pf + 1]));
 }
 void launch_coarsen_K(const double* Kf, int nf, int Pf, double* Kc, int Pc, cudaStream_t s) {
+  SD_COUNT(1);
   k_coarsen_K<<<grid2(nf / 2, nf / 2), dim3(BX, BY), 0, s>>>(Kf, nf, Pf, Kc, Pc);
 }
 
@@ -675,6 +876,7 @@ __global__ void k_setup_coef(const double* __restrict__ K, int n, int P, double 
 template <typename T>
 void launch_setup_coef(const double* Kp, int n, int P, double mu, double alpha, T* w, T* rg, T* Tx, T* Ty,
                        cudaStream_t s) {
+  SD_COUNT(1);
   k_setup_coef<T><<<grid2(n + 1, n + 1), dim3(BX, BY), 0, s>>>(Kp, n, P, mu, alpha, w, rg, Tx, Ty);
 }
 
@@ -685,6 +887,7 @@ __global__ void k_convert(const double* __restrict__ a, T* __restrict__ b, long 
 }
 template <typename T>
 void launch_convert(const double* src, T* dst, long long len, cudaStream_t s) {
+  SD_COUNT(1);
   long long nb = (len + 255) / 256;
   if (nb > 4096) nb = 4096;
   if (nb < 1) nb = 1;
@@ -775,6 +978,7 @@ __global__ void k_mms_terms(Coef<double> c, const double* __restrict__ K, double
 }
 
 void launch_mms_terms(const Coef<double>& c, const double* Kp, double* B0, double* B1, cudaStream_t s) {
+  SD_COUNT(1);
   k_mms_terms<<<grid2(c.n + 1, c.n + 1), dim3(BX, BY), 0, s>>>(c, Kp, B0, B1);
 }
 
@@ -793,6 +997,7 @@ __global__ void k_mms_exact(int n, int P, double mu, double t, double* __restric
 }
 
 void launch_mms_exact(const Geom& g, double mu, double t, double* x, cudaStream_t s) {
+  SD_COUNT(1);
   k_mms_exact<<<grid2(g.n + 1, g.n + 1), dim3(BX, BY), 0, s>>>(g.n, g.P, mu, t, x);
 }
 
@@ -828,6 +1033,7 @@ __global__ void k_rhs(int n, int P, double cm, const double* __restrict__ B0, co
 
 void launch_rhs(const Geom& g, double cm, const double* B0, const double* B1, double s1, const double* xprev,
                 double* b, double* x, cudaStream_t s) {
+  SD_COUNT(1);
   k_rhs<<<grid2(g.n + 1, g.n + 1), dim3(BX, BY), 0, s>>>(g.n, g.P, cm, B0, B1, s1, xprev, b, x);
 }
 
@@ -852,9 +1058,11 @@ __global__ void k_pack2(int n, int P, const double* __restrict__ src, double* __
 }
 
 void launch_pack(const Geom& g, const double* dense, double* padded, cudaStream_t s) {
+  SD_COUNT(1);
   k_pack2<<<grid2(g.n + 1, g.n + 1), dim3(BX, BY), 0, s>>>(g.n, g.P, dense, padded, 1);
 }
 void launch_unpack(const Geom& g, const double* padded, double* dense, cudaStream_t s) {
+  SD_COUNT(1);
   k_pack2<<<grid2(g.n + 1, g.n + 1), dim3(BX, BY), 0, s>>>(g.n, g.P, padded, dense, 0);
 }
 
@@ -876,5 +1084,9 @@ void launch_unpack(const Geom& g, const double* padded, double* dense, cudaStrea
   template void launch_precond_bgs_pff<T>(const Coef<double>&, const double*, double*, const T*, cudaStream_t);
 SD_INST(float)
 SD_INST(double)
+template int launch_coarse_cycle<float>(const CoarseCycle<float>&, cudaStream_t);
+template int launch_coarse_cycle<double>(const CoarseCycle<double>&, cudaStream_t);
+template size_t coarse_cycle_smem<float>(const CoarseCycle<float>&);
+template size_t coarse_cycle_smem<double>(const CoarseCycle<double>&);
 
 }  // namespace sdk

@@ -78,7 +78,7 @@ void run_job(sd_server* S, Job* J) {
     J->res.max_relres = mr;
     if (J->req.keep_fields) {
       J->x.resize((size_t)sd_dof_count(J->req.grid.nx));
-      int r2 = sd_get_state(h, nullptr, nullptr, J->x.data());
+      int r2 = sd_get_state(h, nullptr, nullptr, J->x.data(), nullptr);
       if (rc == SD_OK) rc = r2;
     }
   }

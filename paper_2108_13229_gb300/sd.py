@@ -21,6 +21,7 @@ SD_E_INVAL, SD_E_NOMEM, SD_E_NOCONV, SD_E_NUMERIC, SD_E_TIMEOUT, SD_E_CUDA, SD_E
 SD_FP64, SD_MIXED = 0, 1
 SD_TRI_SCHUR, SD_PV_BJ_I, SD_PV_BGS_I = 0, 1, 2
 SD_BC_MMS = 0
+SD_PROF_APPLY, SD_PROF_CHEB_V, SD_PROF_MUPDATE, SD_PROF_MDOT = 0, 1, 2, 3
 
 
 class SdError(RuntimeError):
@@ -37,12 +38,14 @@ class sd_options(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int32), ("rtol", ctypes.c_double), ("max_iters", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("precond", ctypes.c_int32), ("bc", ctypes.c_int32),
                 ("cheb_degree", ctypes.c_int32), ("coarsest", ctypes.c_int32), ("schur_gamma", ctypes.c_double),
-                ("cheb_ratio", ctypes.c_double), ("schur_mass", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("cheb_ratio", ctypes.c_double), ("schur_mass", ctypes.c_int32), ("fuse_coarse", ctypes.c_int32),
+                ("orth", ctypes.c_int32), ("reorth_eta", ctypes.c_double), ("extrapolate", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
 
 
 class sd_step_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("restarts", ctypes.c_int32), ("status", ctypes.c_int32),
-                ("relres", ctypes.c_double), ("ms", ctypes.c_double)]
+                ("relres", ctypes.c_double), ("ms", ctypes.c_double), ("reorths", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -71,8 +74,8 @@ _SIGS = {
                                  ctypes.POINTER(sd_options), ctypes.POINTER(_vp)]),
     "sd_step": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(sd_step_info)]),
     "sd_get_fields": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
-    "sd_get_state": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), _vp]),
-    "sd_set_state": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int64, _vp]),
+    "sd_get_state": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), _vp, _vp]),
+    "sd_set_state": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int64, _vp, _vp]),
     "sd_apply": (ctypes.c_int, [_vp, _vp, _vp]),
     "sd_rhs": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp]),
     "sd_solve": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(sd_step_info)]),
@@ -86,6 +89,10 @@ _SIGS = {
     "sd_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(sd_result), _vp]),
     "sd_server_drain": (ctypes.c_int, [_vp]),
     "sd_server_destroy": (None, [_vp]),
+    "sd_profile": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
+    "sd_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "sd_launch_count": (ctypes.c_int64, []),
     "sd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
 
@@ -206,16 +213,23 @@ def sd_get_fields(h: Handle, u=None, v=None, p_ff=None, p_pm=None):
     return {"u": u, "v": v, "p_ff": p_ff, "p_pm": p_pm}
 
 
-def sd_get_state(h: Handle, x=None):
+def sd_get_state(h: Handle, x=None, xprev=None, with_prev: bool = False):
+    """(t, step, x) or, with_prev=True, (t, step, x, xprev)."""
     x = np.empty(h.dof) if x is None else x
+    if with_prev and xprev is None:
+        xprev = np.empty(h.dof)
     t = ctypes.c_double()
     st = ctypes.c_int64()
-    _check(_load().sd_get_state(h.ptr, ctypes.byref(t), ctypes.byref(st), _ptr(x, h.dof)), "sd_get_state")
+    _check(_load().sd_get_state(h.ptr, ctypes.byref(t), ctypes.byref(st), _ptr(x, h.dof),
+                                _ptr(xprev, h.dof) if xprev is not None else None), "sd_get_state")
+    if with_prev or xprev is not None:
+        return t.value, st.value, x, xprev
     return t.value, st.value, x
 
 
-def sd_set_state(h: Handle, t: float, step: int, x) -> None:
-    _check(_load().sd_set_state(h.ptr, float(t), int(step), _ptr(x, h.dof)), "sd_set_state")
+def sd_set_state(h: Handle, t: float, step: int, x, xprev=None) -> None:
+    _check(_load().sd_set_state(h.ptr, float(t), int(step), _ptr(x, h.dof),
+                                _ptr(xprev, h.dof) if xprev is not None else None), "sd_set_state")
 
 
 def sd_apply(h: Handle, x, y=None):
@@ -313,3 +327,22 @@ def sd_server_destroy(server: Server) -> None:
     if server.ptr:
         _load().sd_server_destroy(server.ptr)
         server.ptr = None
+
+
+def sd_profile(h: Handle, kernel: int, enable: bool = True) -> None:
+    _check(_load().sd_profile(h.ptr, int(kernel), int(bool(enable))), "sd_profile")
+
+
+def sd_profile_read(h: Handle):
+    """(total device ms, launches, algorithmic bytes, algorithmic flops) of the profiled kernel class."""
+    ms = ctypes.c_double()
+    cnt = ctypes.c_int64()
+    by = ctypes.c_double()
+    fl = ctypes.c_double()
+    _check(_load().sd_profile_read(h.ptr, ctypes.byref(ms), ctypes.byref(cnt), ctypes.byref(by), ctypes.byref(fl)),
+           "sd_profile_read")
+    return ms.value, cnt.value, by.value, fl.value
+
+
+def sd_launch_count() -> int:
+    return int(_load().sd_launch_count())

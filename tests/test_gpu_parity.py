@@ -1,0 +1,236 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances:
+ * operator and right-hand side: the same FP64 rows summed in another order,
+   relative L2 <= 1e-13 (a few ulps times the row length);
+ * solves at rtol = 1e-12: per-field relative L2 <= 1e-8 against the
+   oracle's direct solve (forward error <= cond * 1e-12 with cond <~ 1e4);
+ * at the workload size the oracle cannot factor; there it recomputes the
+   residual of the GPU solution with its own CSR matrix.
+Grids span several 32 x 8 thread tiles with ragged tails (n = 40: 41 faces
+per row) and odd coarsest grids (n = 5, 12, 40).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2108_13229_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sd():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2108_13229_gb300 import sd as S
+    S._load()
+    return S
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def fields_rel(x, xr, n):
+    fs, fr = O.split(x, n), O.split(xr, n)
+    return {k: rel(fs[k], fr[k]) for k in fs}
+
+
+def make(sd, n, mu, K, alpha, dt, precision=1, rtol=1e-10, **kw):
+    o = sd.sd_options_default()
+    o.precision = precision
+    o.rtol = rtol
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return sd.sd_create(n, mu, K, alpha, dt, o)
+
+
+@pytest.mark.parametrize("n", [4, 5, 12, 40, 72])
+def test_operator_parity(sd, n):
+    K = I.lognormal_K(n, -4.0, 1.5, 4.0, seed=n)
+    o = O.Oracle(n, 1e-3, 1.3, 0.05, K)
+    h = make(sd, n, 1e-3, K, 1.3, 0.05)
+    rng = np.random.default_rng(n)
+    for _ in range(3):
+        x = rng.standard_normal(o.ndof)
+        assert rel(sd.sd_apply(h, x), o.apply(x)) <= 1e-13
+
+
+def test_operator_columns(sd):
+    # apply to every unit vector of a 4 x 4 grid: each column of the CSR matrix
+    n = 4
+    K = I.lognormal_K(n, -4.0, 1.0, 2.0, seed=1)
+    o = O.Oracle(n, 0.7, 0.9, 0.2, K)
+    A = o.scipy_csr().toarray()
+    h = make(sd, n, 0.7, K, 0.9, 0.2)
+    scale = np.abs(A).max()
+    for k in range(o.ndof):
+        e = np.zeros(o.ndof)
+        e[k] = 1.0
+        assert np.abs(sd.sd_apply(h, e) - A[:, k]).max() <= 1e-14 * scale
+
+
+@pytest.mark.parametrize("n", [5, 40])
+def test_rhs_parity(sd, n):
+    K = I.lognormal_K(n, -4.0, 1.0, 4.0, seed=2)
+    o = O.Oracle(n, 1e-3, 1.0, 0.05, K)
+    h = make(sd, n, 1e-3, K, 1.0, 0.05)
+    rng = np.random.default_rng(3)
+    for t in (0.05, 0.73):
+        xp = rng.standard_normal(o.ndof)
+        assert rel(sd.sd_rhs(h, xp, t), o.rhs(xp, t)) <= 1e-13
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("n", [4, 8, 12, 40])
+def test_solve_parity(sd, n, precision):
+    K = I.lognormal_K(n, -4.0, 1.0, 4.0, seed=n)
+    o = O.Oracle(n, 1e-3, 1.3, 0.05, K)
+    h = make(sd, n, 1e-3, K, 1.3, 0.05, precision, rtol=1e-12)
+    rng = np.random.default_rng(10 + n)
+    b = rng.standard_normal(o.ndof)
+    x = np.zeros(o.ndof)
+    info = sd.sd_solve(h, b, x)
+    assert info["status"] == 0 and info["relres"] <= 1e-12
+    for k, e in fields_rel(x, o.solve(b), n).items():
+        assert e <= 1e-8, (k, e)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_mms_time_stepping(sd, precision):
+    # manufactured-solution case: 32 x 32 cells, mu = K = alpha = 1, dt = 0.1, 10 steps
+    n = 32
+    K = np.ones((n, n))
+    o = O.Oracle(n, 1.0, 1.0, 0.1, K)
+    xr = o.run(O.exact(n, 0.0, 1.0), 0.0, 10)
+    h = make(sd, n, 1.0, K, 1.0, 0.1, precision, rtol=1e-12)
+    infos = sd.sd_step(h, 10)
+    assert all(i["status"] == 0 for i in infos)
+    t, step, x = sd.sd_get_state(h)
+    assert step == 10 and abs(t - 1.0) < 1e-12
+    for k, e in fields_rel(x, xr, n).items():
+        assert e <= 1e-8, (k, e)
+    # at the default rtol = 1e-10 the result stays within the forward-error bound
+    h2 = make(sd, n, 1.0, K, 1.0, 0.1, precision)
+    infos = sd.sd_step(h2, 10)
+    assert max(i["relres"] for i in infos) <= 1e-10
+    _, _, x2 = sd.sd_get_state(h2)
+    for k, e in fields_rel(x2, xr, n).items():
+        assert e <= 1e-6, (k, e)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("n", [64, 128])
+def test_lognormal_time_stepping(sd, n, precision):
+    # the workload's physics (mu = 1e-3, ln K ~ N(-4, 1), corr. 16 cells) on grids the oracle factors
+    K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=0)
+    o = O.Oracle(n, 1e-3, 1.0, 0.05, K)
+    xr = o.run(O.exact(n, 0.0, 1e-3), 0.0, 3)
+    h = make(sd, n, 1e-3, K, 1.0, 0.05, precision, rtol=1e-12)
+    infos = sd.sd_step(h, 3)
+    assert all(i["status"] == 0 for i in infos)
+    _, _, x = sd.sd_get_state(h)
+    for k, e in fields_rel(x, xr, n).items():
+        assert e <= 1e-8, (k, e)
+
+
+def test_workload_size_residual(sd):
+    # 1024 x 1024 cells, the benchmark's launch configuration (mixed precision, rtol 1e-10):
+    # the oracle recomputes ||b - A x|| / ||b|| of the GPU state with its own CSR matrix
+    n = 1024
+    K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=0)
+    o = O.Oracle(n, 1e-3, 1.0, 0.05, K)
+    h = make(sd, n, 1e-3, K, 1.0, 0.05, 1)
+    sd.sd_step(h, 1)
+    _, _, x1 = sd.sd_get_state(h)
+    info = sd.sd_step(h, 1)[0]
+    _, _, x2 = sd.sd_get_state(h)
+    b = o.rhs(x1, 0.1)
+    _, r = o.residual(x2, b)
+    assert r / np.linalg.norm(b) <= 1.05e-10 and info["relres"] <= 1e-10
+    # operator parity at full size on a random vector
+    rng = np.random.default_rng(0)
+    xv = rng.standard_normal(o.ndof)
+    assert rel(sd.sd_apply(h, xv), o.apply(xv)) <= 1e-13
+
+
+def test_determinism_and_state_roundtrip(sd):
+    n = 64
+    K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=4)
+    h1 = make(sd, n, 1e-3, K, 1.0, 0.05)
+    h2 = make(sd, n, 1e-3, K, 1.0, 0.05)
+    sd.sd_step(h1, 4)
+    sd.sd_step(h2, 2)
+    t, st, x, xp = sd.sd_get_state(h2, with_prev=True)
+    h3 = make(sd, n, 1e-3, K, 1.0, 0.05)
+    sd.sd_set_state(h3, t, st, x, xp)
+    sd.sd_step(h2, 2)
+    sd.sd_step(h3, 2)
+    a, b, c = sd.sd_get_state(h1)[2], sd.sd_get_state(h2)[2], sd.sd_get_state(h3)[2]
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+
+
+def test_batch_alone_vs_mixed(sd):
+    cases = [(32, 1), (64, 2), (128, 3), (64, 4)]
+    alone = []
+    for n, seed in cases:
+        h = make(sd, n, 1e-3, I.lognormal_K(n, -4.0, 1.5, 16.0, seed=seed), 0.5 + seed, 0.1)
+        sd.sd_step(h, 3)
+        alone.append(sd.sd_get_state(h)[2])
+    hs = [make(sd, n, 1e-3, I.lognormal_K(n, -4.0, 1.5, 16.0, seed=seed), 0.5 + seed, 0.1) for n, seed in cases]
+    infos = sd.sd_solve_batch(hs, [3] * len(cases))
+    assert all(i["status"] == 0 for inf in infos for i in inf)
+    for h, xa in zip(hs, alone):
+        assert np.array_equal(sd.sd_get_state(h)[2], xa)
+
+
+def test_server_results_match_alone(sd):
+    reqs = [(32, 5, 1), (64, 7, 2), (128, 4, 3), (32, 9, 4), (96, 6, 5), (64, 5, 6)]
+    srv = sd.sd_server_create(8 << 30, 3)
+    tickets = []
+    for n, steps, seed in reqs:
+        K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=seed)
+        tickets.append(sd.sd_submit(srv, n, 1e-3, K, 1.0, 0.1, steps, keep_fields=True))
+    sd.sd_server_drain(srv)
+    for (n, steps, seed), tk in zip(reqs, tickets):
+        rc, res, x = sd.sd_poll(srv, tk, want_x=True)
+        assert rc == 0 and res["steps_done"] == steps and res["latency_ms"] >= res["run_ms"] > 0
+        K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=seed)
+        h = make(sd, n, 1e-3, K, 1.0, 0.1)
+        sd.sd_step(h, steps)
+        assert np.array_equal(sd.sd_get_state(h)[2], x)
+    sd.sd_server_destroy(srv)
+
+
+def test_error_paths(sd):
+    n = 32
+    K = np.ones((n, n))
+    h = make(sd, n, 1.0, K, 1.0, 0.1, max_iters=2)
+    infos = sd.sd_step(h, 1, raise_on_error=False)
+    assert infos[0]["status"] == sd.SD_E_NOCONV
+    t, st, _ = sd.sd_get_state(h)
+    assert st == 1 and abs(t - 0.1) < 1e-15
+    srv = sd.sd_server_create(1 << 20, 1)
+    with pytest.raises(sd.SdError) as e:
+        sd.sd_submit(srv, 256, 1e-3, np.ones((256, 256)), 1.0, 0.1, 2)
+    assert e.value.code == sd.SD_E_NOMEM
+    assert sd.sd_poll(srv, 12345)[0] == sd.SD_E_STATE
+    sd.sd_server_destroy(srv)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_paper_block_preconditioners(sd, mode):
+    # P^pv_BJ and P^pv_BGS with the identity on the p_ff block (Sec. 4) on the
+    # manufactured-solution case: same solution as the oracle
+    n = 16
+    K = np.ones((n, n))
+    o = O.Oracle(n, 1.0, 1.0, 0.1, K)
+    xr = o.run(O.exact(n, 0.0, 1.0), 0.0, 1)
+    h = make(sd, n, 1.0, K, 1.0, 0.1, 0, rtol=1e-12, precond=mode, max_iters=3000)
+    info = sd.sd_step(h, 1)[0]
+    assert info["status"] == 0
+    _, _, x = sd.sd_get_state(h)
+    for k, e in fields_rel(x, xr, n).items():
+        assert e <= 1e-8, (k, e)

@@ -22,6 +22,7 @@ SD_FP64, SD_MIXED = 0, 1
 SD_TRI_SCHUR, SD_PV_BJ_I, SD_PV_BGS_I = 0, 1, 2
 SD_BC_MMS = 0
 SD_PROF_APPLY, SD_PROF_CHEB_V, SD_PROF_MUPDATE, SD_PROF_MDOT = 0, 1, 2, 3
+SD_NOALLOC_MAX_N = 256
 
 
 class SdError(RuntimeError):
@@ -93,6 +94,8 @@ _SIGS = {
     "sd_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "sd_launch_count": (ctypes.c_int64, []),
+    "sd_apply_noalloc": (ctypes.c_int, [ctypes.POINTER(sd_grid), ctypes.c_double, _vp, ctypes.c_double,
+                                        ctypes.c_double, _vp, _vp, _vp]),
     "sd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
 
@@ -346,3 +349,10 @@ def sd_profile_read(h: Handle):
 
 def sd_launch_count() -> int:
     return int(_load().sd_launch_count())
+
+
+def sd_apply_noalloc(n: int, mu: float, K, alpha_bj: float, dt: float, x, y, stream=None) -> None:
+    """y = A x without allocating (all arrays: CUDA float64 tensors; see include/sd.h)."""
+    g = sd_grid(n, n)
+    _check(_load().sd_apply_noalloc(ctypes.byref(g), float(mu), _ptr(K, n * n), float(alpha_bj), float(dt),
+                                    _ptr(x), _ptr(y), stream), "sd_apply_noalloc")

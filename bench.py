@@ -213,6 +213,57 @@ def roofline_entry(kid: int, prof, step_ms: float):
     return e
 
 
+def bench_batch(sd, count: int, steps: int, threads: int, seed: int = 0):
+    """Independent instances with uneven grids advanced together by sd_solve_batch."""
+    from paper_2108_13229_gb300 import inputs as I
+    wls = I.batch_instances(count, seed=seed, steps=steps)
+    hs = []
+    for wl in wls:
+        o = sd.sd_options_default()
+        hs.append(sd.sd_create(wl.n, wl.mu, wl.K(), wl.alpha, wl.dt, o))
+    t0 = time.perf_counter()
+    infos = sd.sd_solve_batch(hs, [steps] * count, max_threads=threads)
+    el = time.perf_counter() - t0
+    dof = sum(wl.dof for wl in wls)
+    its = [i["iters"] for inf in infos for i in inf]
+    for h in hs:
+        sd.sd_destroy(h)
+    return {"value": dof * steps / el, "unit": UNIT, "instances": count, "steps_each": steps, "threads": threads,
+            "seconds": el, "total_dof": dof, "grids": sorted(set(wl.n for wl in wls)),
+            "iters_per_step_mean": float(np.mean(its)), "max_relres": max(i["relres"] for inf in infos for i in inf)}
+
+
+def bench_serve(sd, rate: float, count: int, max_running: int, budget_gb: float = 120.0, seed: int = 0):
+    """Poisson arrivals of time-dependent runs submitted to the continuous-batching server."""
+    from paper_2108_13229_gb300 import inputs as I
+    reqs = I.serving_requests(count, rate, seed=seed)
+    Ks = [wl.K() for _, wl in reqs]
+    srv = sd.sd_server_create(int(budget_gb * (1 << 30)), max_running)
+    t0 = time.perf_counter()
+    tickets = []
+    for (ta, wl), K in zip(reqs, Ks):
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        tickets.append((sd.sd_submit(srv, wl.n, wl.mu, K, wl.alpha, wl.dt, wl.steps), wl))
+    sd.sd_server_drain(srv)
+    el = time.perf_counter() - t0
+    lat, work, its = [], 0, 0
+    for tk, wl in tickets:
+        rc, res, _ = sd.sd_poll(srv, tk)
+        if rc != 0:
+            raise RuntimeError("request failed: %d" % rc)
+        lat.append(res["latency_ms"])
+        work += res["dof"] * res["steps_done"]
+        its += res["total_iters"]
+    sd.sd_server_destroy(srv)
+    return {"rate_per_s": rate, "requests": count, "max_running": max_running, "hbm_budget_gb": budget_gb,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "mean": float(np.mean(lat))},
+            "value": work / el, "unit": UNIT, "makespan_s": el,
+            "grids": [int(x) for x in np.percentile([wl.n for _, wl in reqs], [0, 50, 100])]}
+
+
 def cpu_oracle_sample(n_sample: int, steps: int):
     """Time the oracle on a bounded sample: same physics on an n_sample grid."""
     import oracle as O
@@ -335,6 +386,11 @@ def bench_ours(args, ws, rank, local):
                        "d2h_bytes_per_step": dof * 8,
                        "note": "setup (sd_create from host K, hierarchy, coarse inverses) inside the timed region"}
 
+        # independent instances (uneven grids) and the serving loop, smaller
+        # versions of the batched and serving workloads
+        line["batch"] = bench_batch(sd, 64, 10, 16, seed=rank)
+        line["serving"] = bench_serve(sd, 50.0, 40, 8)
+
         if rank == 0 and ws >= 1 and not args.no_cpu:
             line["cpu_baseline"] = cpu_oracle_sample(args.cpu_n, 20)
     if rank == 0:
@@ -361,9 +417,28 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="headline form only")
     ap.add_argument("--peak-probe", action="store_true", help="measure FP64/FP32 FMA rates and copy bandwidth")
+    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"])
+    ap.add_argument("--count", type=int, default=256, help="batch instances / serving requests")
+    ap.add_argument("--threads", type=int, default=32, help="host threads (batch) / running slots (serve)")
+    ap.add_argument("--rates", type=float, nargs="*", default=[10.0, 50.0, 200.0])
     args = ap.parse_args()
     if args.peak_probe:
         return peak_probe()
+    if args.mode in ("batch", "serve"):
+        import torch
+        from paper_2108_13229_gb300 import sd
+        torch.cuda.set_device(dist_env()[2])
+        if args.mode == "batch":
+            r = bench_batch(sd, args.count, args.steps if args.steps != 20 else 10, args.threads)
+            r.update({"metric": "batched coupled DOF*steps/s, independent instances of uneven grids", "mode": "batch"})
+            print(json.dumps(r), flush=True)
+        else:
+            for rate in args.rates:
+                r = bench_serve(sd, rate, args.count, args.threads)
+                r.update({"metric": "serving: p50/p99 request latency and DOF*steps/s under Poisson arrivals",
+                          "mode": "serve"})
+                print(json.dumps(r), flush=True)
+        return 0
     if args.warmup < 3:
         args.warmup = 3
     ws, rank, local = dist_env()

@@ -106,6 +106,11 @@ typedef struct {
   double reorth_eta;   /* default 1/sqrt(2) */
   int32_t extrapolate; /* initial guess of step n+1: 2 x^n - x^{n-1} (1, default)
                           or x^n (0) */
+  int32_t graph;       /* replay each Arnoldi step from a captured CUDA graph (default 1;
+                          ignored on the legacy default stream and while profiling) */
+  int32_t darcy_coupled; /* SD_TRI_SCHUR: 1 (default) keeps C'_1, the Darcy block follows
+                          the velocity; 0 drops it and overlaps the Darcy V-cycle with
+                          the Stokes part on a second stream */
   void *stream;        /* cudaStream_t to run on; NULL: the handle creates one */
 } sd_options;
 
@@ -252,7 +257,8 @@ int sd_profile_read(sd_handle *h, double *total_ms, int64_t *launches, double *b
 int sd_apply_noalloc(const sd_grid *grid, double mu, const double *K, double alpha_bj, double dt, const double *x,
                      double *y, void *stream);
 
-/* Kernel launches made by this library in this process so far. */
+/* Kernel launches made by this library in this process so far (kernels replayed
+ * from captured CUDA graphs included). */
 int64_t sd_launch_count(void);
 
 const char *sd_strerror(int code);

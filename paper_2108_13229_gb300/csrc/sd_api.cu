@@ -119,6 +119,10 @@ struct sd_handle {
   sd_options opt;
   cudaStream_t s = nullptr;
   bool own_stream = false;
+  cudaStream_t s2 = nullptr;                   // second stream (Darcy V-cycle overlap)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  std::vector<cudaGraphExec_t> gexec;          // one captured Arnoldi step per basis index
+  std::vector<long long> gcount;               // kernels in each captured step
   Geom g;
   int nlev = 1;
   int m = 30;
@@ -536,8 +540,7 @@ void vcycle_cell(MG<T>& M, int l, int deg, bool poisson, cudaStream_t s) {
   }
   MGLevel<T>& C = M.L[l + 1];
   Block<T>& BC = poisson ? C.Pb : C.D;
-  launch_resid_D<T>(c, cur, B.b, B.r, 0, 1, 0, s);
-  launch_restrict_D<T>(L.g.n, L.g.P, B.r, C.g.n, C.g.P, BC.b, s);
+  launch_resid_restrict_D<T>(c, cur, B.b, C.g.n, C.g.P, BC.b, s);
   vcycle_cell(M, l + 1, deg, poisson, s);
   launch_prolong_D<T>(L.g.n, L.g.P, cur, C.g.n, C.g.P, BC.res, s);
   for (int k = 0; k < deg; ++k) {
@@ -560,6 +563,17 @@ void precond(sd_handle* h, MG<T>& M, const double* r, double* z) {
   const int deg = h->opt.cheb_degree;
   const bool tri = mode == SD_TRI_SCHUR;
   const double schur = tri ? h->mu / (h->opt.schur_gamma * h->g.h * h->g.h) : 1.0;
+  // block-diagonal Darcy part (no C'_1 coupling): its V-cycle runs on the
+  // second stream, overlapping the pressure and velocity cycles
+  const bool overlap = tri && !h->opt.darcy_coupled;
+  if (overlap) {
+    cudaEventRecord(h->ev_fork, s);
+    cudaStreamWaitEvent(h->s2, h->ev_fork, 0);
+    launch_convert<T>(r + h->g.opm, M.L[0].D.b, h->g.lenD, h->s2);
+    vcycle_cell<T>(M, 0, deg, false, h->s2);
+    launch_precond_exit<T>(c, z, M.L[0].D.res, h->s2);
+    cudaEventRecord(h->ev_join, h->s2);
+  }
   const T* eP = nullptr;
   if (tri && h->opt.schur_mass) {
     launch_convert<T>(r + h->g.opf, M.L[0].Pb.b, h->g.lenD, s);
@@ -569,6 +583,11 @@ void precond(sd_handle* h, MG<T>& M, const double* r, double* z) {
   launch_precond_entry<T>(c, r, z, schur, eP, 1.0 / h->dt, tri, M.L[0].V.b, s);
   vcycle_V<T>(M, 0, deg, s, h);
   if (mode == SD_PV_BGS_I) launch_precond_bgs_pff<T>(c, r, z, M.L[0].V.res, s);
+  if (overlap) {
+    launch_precond_mid<T>(c, r, z, M.L[0].V.res, 0, (T*)nullptr, s);
+    cudaStreamWaitEvent(s, h->ev_join, 0);
+    return;
+  }
   launch_precond_mid<T>(c, r, z, M.L[0].V.res, mode != SD_PV_BJ_I, M.L[0].D.b, s);
   vcycle_cell<T>(M, 0, deg, false, s);
   launch_precond_exit<T>(c, z, M.L[0].D.res, s);
@@ -672,8 +691,28 @@ int fgmres(sd_handle* h, const double* b, double* x, sd_step_info* info) {
       double* vj = h->V + (long long)j * vs;
       double* zj = h->Z + (long long)j * vs;
       double* w = h->V + (long long)(j + 1) * vs;
-      arnoldi_orth(h, j, vj, zj, w);
-      launch_scale_by(w, w, len, h->flag + 1, 0, s);
+      if (h->opt.graph && h->prof_id < 0 && h->s != nullptr) {
+        if (!h->gexec[j]) {
+          cudaGraph_t gr = nullptr;
+          const long long l0 = t_launch_count;
+          CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+          arnoldi_orth(h, j, vj, zj, w);
+          launch_scale_by(w, w, len, h->flag + 1, 0, s);
+          CK(cudaStreamEndCapture(s, &gr));
+          const cudaError_t ie = cudaGraphInstantiate(&h->gexec[j], gr, 0);
+          cudaGraphDestroy(gr);
+          CK(ie);
+          // the capture went through the counting launch wrappers; replays are
+          // credited with the same number of kernels
+          h->gcount[j] = t_launch_count - l0;
+          g_launch_count.fetch_sub(h->gcount[j]);
+        }
+        CK(cudaGraphLaunch(h->gexec[j], s));
+        g_launch_count.fetch_add(h->gcount[j]);
+      } else {
+        arnoldi_orth(h, j, vj, zj, w);
+        launch_scale_by(w, w, len, h->flag + 1, 0, s);
+      }
       CK(cudaMemcpyAsync(h->hflag, h->flag, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       if (h->prof_used) prof_flush(h);
@@ -775,6 +814,13 @@ int create_impl(const sd_grid* grid, double mu, const double* K, double alpha, d
   if (cudaMemsetAsync(h->ar.base, 0, bytes, h->s) != cudaSuccess) return fail(SD_E_CUDA);
   plan_all(h);
   if (cudaHostAlloc(&h->hflag, 16 * sizeof(double), cudaHostAllocDefault) != cudaSuccess) return fail(SD_E_CUDA);
+  if (cudaStreamCreateWithFlags(&h->s2, cudaStreamNonBlocking) != cudaSuccess) return fail(SD_E_CUDA);
+  if (cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess)
+    return fail(SD_E_CUDA);
+  h->gexec.assign(h->m, nullptr);
+  h->gcount.assign(h->m, 0);
+  if (prepare_coarse_cycle<float>() != 0 || prepare_coarse_cycle<double>() != 0) return fail(SD_E_CUDA);
   if (cudaEventCreate(&h->e0) != cudaSuccess || cudaEventCreate(&h->e1) != cudaSuccess) return fail(SD_E_CUDA);
   cudaStream_t s = h->s;
   // permeability hierarchy (geometric means of 2 x 2 children)
@@ -830,6 +876,8 @@ void sd_options_default(sd_options* o) {
   o->orth = 0;
   o->reorth_eta = 0.70710678118654752;
   o->extrapolate = 1;
+  o->graph = 1;
+  o->darcy_coupled = 1;
   o->schur_gamma = 0.5;
   o->cheb_ratio = 8.0;
   o->schur_mass = 1;
@@ -1014,6 +1062,14 @@ void sd_destroy(sd_handle* h) {
   if (h->s) cudaStreamSynchronize(h->s);
   for (auto& e : h->prof_ev)
     if (e) cudaEventDestroy(e);
+  for (auto& ge : h->gexec)
+    if (ge) cudaGraphExecDestroy(ge);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->s2) {
+    cudaStreamSynchronize(h->s2);
+    cudaStreamDestroy(h->s2);
+  }
   if (h->ar.base) cudaFree(h->ar.base);
   if (h->hflag) cudaFreeHost(h->hflag);
   if (h->e0) cudaEventDestroy(h->e0);

@@ -20,9 +20,12 @@
 
 namespace sdk {
 
-// process-wide count of kernel launches made by this library
+// process-wide count of kernel launches made by this library (and the same
+// count per host thread, used to size captured graphs)
 extern std::atomic<long long> g_launch_count;
-#define SD_COUNT(k) ::sdk::g_launch_count.fetch_add((k), std::memory_order_relaxed)
+extern thread_local long long t_launch_count;
+#define SD_COUNT(k) \
+  (::sdk::t_launch_count += (k), ::sdk::g_launch_count.fetch_add((k), std::memory_order_relaxed))
 
 struct Geom {
   int n;        // cells per side
@@ -116,6 +119,9 @@ template <typename T>
 void launch_restrict_V(int nf, int Pf, const T* r, int nc, int Pc, T* bc, cudaStream_t s);
 template <typename T>
 void launch_restrict_D(int nf, int Pf, const T* r, int nc, int Pc, T* bc, cudaStream_t s);
+// cell blocks: bc = R (b - A x) with the cell-sum restriction, one pass
+template <typename T>
+void launch_resid_restrict_D(const Coef<T>& c, const T* x, const T* b, int nc, int Pc, T* bc, cudaStream_t s);
 // x += P e (bilinear, staggered for V, cell-centred for D)
 template <typename T>
 void launch_prolong_V(int nf, int Pf, T* x, int nc, int Pc, const T* e, cudaStream_t s);
@@ -140,6 +146,9 @@ size_t coarse_cycle_smem(const CoarseCycle<T>& q);
 // returns -1 (nothing launched) if the levels need more shared memory than allowed
 template <typename T>
 int launch_coarse_cycle(const CoarseCycle<T>& q, cudaStream_t s);
+// opt the kernel in to the large dynamic shared memory (once per device, before any capture)
+template <typename T>
+int prepare_coarse_cycle();
 
 // preconditioner glue on the fine level (Sec. 4 block preconditioners):
 //  entry: zpf = schur * r_pf + cmass * eP (eP: pressure-Laplacian solve, may be
@@ -147,7 +156,7 @@ int launch_coarse_cycle(const CoarseCycle<T>& q, cudaStream_t s);
 template <typename T>
 void launch_precond_entry(const Coef<double>& c, const double* r, double* z, double schur, const T* eP, double cmass,
                           int use_B, T* rV, cudaStream_t s);
-//  mid: z_v = double(eV); rD = T(r_pm - C'_1 z_v) (C'_1 omitted: use_C == 0)
+//  mid: z_v = double(eV); rD = T(r_pm - C'_1 z_v) (C'_1 omitted: use_C == 0; rD null: not written)
 template <typename T>
 void launch_precond_mid(const Coef<double>& c, const double* r, double* z, const T* eV, int use_C, T* rD,
                         cudaStream_t s);

@@ -18,134 +18,161 @@
 namespace sdk {
 
 std::atomic<long long> g_launch_count{0};
+thread_local long long t_launch_count = 0;
 
-static const int RT = 256;      // threads per reduction block
-static const int KE = 4;        // vector elements owned by one thread
+static const int RT = 256;       // threads per reduction / update block
+static const int KT = 128;       // threads per Gram-Schmidt block
+static const int KE = 16;        // vector elements owned by one Gram-Schmidt thread
 static const int KMAX_REG = 32;  // max dot products per pass
 
-// Blocks of the Krylov kernels for a vector of length len: each block owns
-// RT * KE consecutive elements (fixed for a given len, so every reduction
-// sums its partials in the same order on every call).
+// Blocks of the Gram-Schmidt kernels for a vector of length len: each block
+// owns KT * KE consecutive elements (fixed for a given len, so every
+// reduction sums its partials in the same order on every call).
 int reduce_blocks(long long len) {
-  long long nb = (len + (long long)RT * KE - 1) / ((long long)RT * KE);
+  long long nb = (len + (long long)KT * KE - 1) / ((long long)KT * KE);
   return (int)(nb < 1 ? 1 : nb);
 }
 
-// Warp-sum v and store it in red[warp][q] (lane 0).
-__device__ __forceinline__ void warp_store(double v, double (*red)[KMAX_REG], int q) {
+// Per-thread dot of its KE elements: four interleaved partial sums.
+__device__ __forceinline__ double own_dot(const double* __restrict__ v, const double* we, long long base,
+                                          long long len) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][q] = v;
+  for (int t = 0; t < KE; t += 4) {
+    const long long e = base + (long long)t * KT;
+    if (e < len) s0 = fma(v[e], we[t], s0);
+    if (e + KT < len) s1 = fma(v[e + KT], we[t + 1], s1);
+    if (e + 2 * KT < len) s2 = fma(v[e + 2 * KT], we[t + 2], s2);
+    if (e + 3 * KT < len) s3 = fma(v[e + 3 * KT], we[t + 3], s3);
+  }
+  return (s0 + s1) + (s2 + s3);
 }
 
-// Sum red[.][q] over the block's warps for q < k into partial[q * ps + block].
-__device__ __forceinline__ void block_store(double (*red)[KMAX_REG], int k, double* partial, int ps) {
+// red[q][tid] holds every thread's partial of dot q (q < kk); a fixed binary
+// tree over tid (all q at once) leaves the block sum in red[q][0], written to
+// partial[q * ps + block].
+__device__ __forceinline__ void block_tree(double (*red)[KT], int kk, double* partial, int ps) {
   __syncthreads();
-  if (threadIdx.x < k) {
-    double s = 0.0;
+  for (int st = KT / 2; st > 0; st >>= 1) {
+    for (int p = threadIdx.x; p < kk * st; p += KT) {
+      const int q = p / st, t = p - q * st;
+      red[q][t] += red[q][t + st];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < kk) partial[(long long)threadIdx.x * ps + blockIdx.x] = red[threadIdx.x][0];
+}
+
+__device__ __forceinline__ void load_own(const double* __restrict__ w, double* we, long long base, long long len) {
 #pragma unroll
-    for (int w = 0; w < RT / 32; ++w) s += red[w][threadIdx.x];
-    partial[(long long)threadIdx.x * ps + blockIdx.x] = s;
+  for (int t = 0; t < KE; ++t) {
+    const long long e = base + (long long)t * KT;
+    we[t] = e < len ? w[e] : 0.0;
   }
 }
 
 // partial[q * ps + blk] = sum over the block's elements of V_q . w, q < k;
 // with self != 0 also w . w as entry k.  cond (may be null): skip when 0.
-__global__ void __launch_bounds__(RT) k_mdot(const double* __restrict__ V, long long vs, int k,
+__global__ void __launch_bounds__(KT) k_mdot(const double* __restrict__ V, long long vs, int k,
                                              const double* __restrict__ w, long long len, double* __restrict__ partial,
                                              int ps, int self, const double* __restrict__ cond) {
   if (cond && cond[0] == 0.0) return;
-  __shared__ double red[RT / 32][KMAX_REG];
-  const long long base = (long long)blockIdx.x * RT * KE + threadIdx.x;
+  __shared__ double red[KMAX_REG][KT];
+  const long long base = (long long)blockIdx.x * KT * KE + threadIdx.x;
   double we[KE];
-#pragma unroll
-  for (int t = 0; t < KE; ++t) {
-    const long long e = base + (long long)t * RT;
-    we[t] = e < len ? w[e] : 0.0;
+  load_own(w, we, base, len);
+  int q = 0;
+  for (; q + 1 < k; q += 2) {
+    const double a0 = own_dot(V + (long long)q * vs, we, base, len);
+    const double a1 = own_dot(V + (long long)(q + 1) * vs, we, base, len);
+    red[q][threadIdx.x] = a0;
+    red[q + 1][threadIdx.x] = a1;
   }
-  for (int q = 0; q < k; ++q) {
-    const double* vq = V + (long long)q * vs;
-    double s = 0.0;
-#pragma unroll
-    for (int t = 0; t < KE; ++t) {
-      const long long e = base + (long long)t * RT;
-      if (e < len) s = fma(vq[e], we[t], s);
-    }
-    warp_store(s, red, q);
-  }
+  if (q < k) red[q][threadIdx.x] = own_dot(V + (long long)q * vs, we, base, len);
   if (self) {
-    double s = 0.0;
+    double s0 = 0.0, s1 = 0.0;
 #pragma unroll
-    for (int t = 0; t < KE; ++t) s = fma(we[t], we[t], s);
-    warp_store(s, red, k);
+    for (int t = 0; t < KE; t += 2) {
+      s0 = fma(we[t], we[t], s0);
+      s1 = fma(we[t + 1], we[t + 1], s1);
+    }
+    red[k][threadIdx.x] = s0 + s1;
   }
-  block_store(red, k + (self ? 1 : 0), partial, ps);
+  block_tree(red, k + (self ? 1 : 0), partial, ps);
 }
 
 void launch_mdot(const double* V, long long vstride, int k, const double* w, long long len, double* partial, int ps,
                  int nblk, int self, const double* cond, cudaStream_t s) {
   SD_COUNT(1);
-  k_mdot<<<nblk, RT, 0, s>>>(V, vstride, k, w, len, partial, ps, self, cond);
+  k_mdot<<<nblk, KT, 0, s>>>(V, vstride, k, w, len, partial, ps, self, cond);
 }
 
 // w -= sum_q coef_q V_q, then
 //   mode 1: partial dots V_q . w (second Gram-Schmidt pass),
 //   mode 2: partial w . w (norm of the new basis vector).
-__global__ void __launch_bounds__(RT) k_mupdate(const double* __restrict__ V, long long vs, int k,
+__global__ void __launch_bounds__(KT) k_mupdate(const double* __restrict__ V, long long vs, int k,
                                                 const double* __restrict__ coef, double* __restrict__ w,
                                                 long long len, double* __restrict__ partial, int ps, int mode,
                                                 const double* __restrict__ cond) {
   if (cond && cond[0] == 0.0) return;
   __shared__ double cf[KMAX_REG];
-  __shared__ double red[RT / 32][KMAX_REG];
+  __shared__ double red[KMAX_REG][KT];
   if (threadIdx.x < KMAX_REG) cf[threadIdx.x] = threadIdx.x < k ? coef[threadIdx.x] : 0.0;
   __syncthreads();
-  const long long base = (long long)blockIdx.x * RT * KE + threadIdx.x;
+  const long long base = (long long)blockIdx.x * KT * KE + threadIdx.x;
   double we[KE];
-#pragma unroll
-  for (int t = 0; t < KE; ++t) {
-    const long long e = base + (long long)t * RT;
-    we[t] = e < len ? w[e] : 0.0;
-  }
-  for (int q = 0; q < k; ++q) {
-    const double* vq = V + (long long)q * vs;
-    const double c = cf[q];
+  load_own(w, we, base, len);
+  int q = 0;
+  for (; q + 1 < k; q += 2) {
+    const double* v0 = V + (long long)q * vs;
+    const double* v1 = V + (long long)(q + 1) * vs;
+    const double c0 = cf[q], c1 = cf[q + 1];
 #pragma unroll
     for (int t = 0; t < KE; ++t) {
-      const long long e = base + (long long)t * RT;
-      if (e < len) we[t] = fma(-c, vq[e], we[t]);
+      const long long e = base + (long long)t * KT;
+      if (e < len) we[t] = fma(-c1, v1[e], fma(-c0, v0[e], we[t]));
+    }
+  }
+  if (q < k) {
+    const double* v0 = V + (long long)q * vs;
+    const double c0 = cf[q];
+#pragma unroll
+    for (int t = 0; t < KE; ++t) {
+      const long long e = base + (long long)t * KT;
+      if (e < len) we[t] = fma(-c0, v0[e], we[t]);
     }
   }
 #pragma unroll
   for (int t = 0; t < KE; ++t) {
-    const long long e = base + (long long)t * RT;
+    const long long e = base + (long long)t * KT;
     if (e < len) w[e] = we[t];
   }
   if (mode == 1) {
-    for (int q = 0; q < k; ++q) {
-      const double* vq = V + (long long)q * vs;
-      double s = 0.0;
-#pragma unroll
-      for (int t = 0; t < KE; ++t) {
-        const long long e = base + (long long)t * RT;
-        if (e < len) s = fma(vq[e], we[t], s);
-      }
-      warp_store(s, red, q);
+    q = 0;
+    for (; q + 1 < k; q += 2) {
+      const double a0 = own_dot(V + (long long)q * vs, we, base, len);
+      const double a1 = own_dot(V + (long long)(q + 1) * vs, we, base, len);
+      red[q][threadIdx.x] = a0;
+      red[q + 1][threadIdx.x] = a1;
     }
-    block_store(red, k, partial, ps);
+    if (q < k) red[q][threadIdx.x] = own_dot(V + (long long)q * vs, we, base, len);
+    block_tree(red, k, partial, ps);
   } else {
-    double s = 0.0;
+    double s0 = 0.0, s1 = 0.0;
 #pragma unroll
-    for (int t = 0; t < KE; ++t) s = fma(we[t], we[t], s);
-    warp_store(s, red, 0);
-    block_store(red, 1, partial, ps);
+    for (int t = 0; t < KE; t += 2) {
+      s0 = fma(we[t], we[t], s0);
+      s1 = fma(we[t + 1], we[t + 1], s1);
+    }
+    red[0][threadIdx.x] = s0 + s1;
+    block_tree(red, 1, partial, ps);
   }
 }
 
 void launch_mupdate(const double* V, long long vstride, int k, const double* coef, double* w, long long len,
                     double* partial, int ps, int nblk, int mode, const double* cond, cudaStream_t s) {
   SD_COUNT(1);
-  k_mupdate<<<nblk, RT, 0, s>>>(V, vstride, k, coef, w, len, partial, ps, mode, cond);
+  k_mupdate<<<nblk, KT, 0, s>>>(V, vstride, k, coef, w, len, partial, ps, mode, cond);
 }
 
 // out[q] = sum_b partial[q * ps + b] (+ out[q] if accumulate), fixed-order tree
@@ -194,7 +221,7 @@ void launch_reorth_decide(const double* nw2, const double* n2a, double eta2, dou
 void launch_dot(const double* a, const double* b, long long len, double* partial, int nblk, double* out,
                 cudaStream_t s) {
   SD_COUNT(2);
-  k_mdot<<<nblk, RT, 0, s>>>(a, 0, 1, b, len, partial, nblk, 0, nullptr);
+  k_mdot<<<nblk, KT, 0, s>>>(a, 0, 1, b, len, partial, nblk, 0, nullptr);
   k_reduce<<<1, RT, 0, s>>>(partial, nblk, 1, nblk, out, 0, nullptr);
 }
 
@@ -213,30 +240,37 @@ void launch_scale_by(const double* x, double* y, long long len, const double* sd
 }
 
 // x += sum_q y_q Z_q
-__global__ void __launch_bounds__(RT) k_axpy_multi(double* __restrict__ x, const double* __restrict__ Z, long long zs,
+__global__ void __launch_bounds__(KT) k_axpy_multi(double* __restrict__ x, const double* __restrict__ Z, long long zs,
                                                    const double* __restrict__ y, int k, long long len) {
   __shared__ double cf[KMAX_REG];
   if (threadIdx.x < KMAX_REG) cf[threadIdx.x] = threadIdx.x < k ? y[threadIdx.x] : 0.0;
   __syncthreads();
-  const long long base = (long long)blockIdx.x * RT * KE + threadIdx.x;
+  const long long base = (long long)blockIdx.x * KT * KE + threadIdx.x;
   double xe[KE];
-#pragma unroll
-  for (int t = 0; t < KE; ++t) {
-    const long long e = base + (long long)t * RT;
-    xe[t] = e < len ? x[e] : 0.0;
-  }
-  for (int q = 0; q < k; ++q) {
-    const double* zq = Z + (long long)q * zs;
-    const double c = cf[q];
+  load_own(x, xe, base, len);
+  int q = 0;
+  for (; q + 1 < k; q += 2) {
+    const double* z0 = Z + (long long)q * zs;
+    const double* z1 = Z + (long long)(q + 1) * zs;
+    const double c0 = cf[q], c1 = cf[q + 1];
 #pragma unroll
     for (int t = 0; t < KE; ++t) {
-      const long long e = base + (long long)t * RT;
-      if (e < len) xe[t] = fma(c, zq[e], xe[t]);
+      const long long e = base + (long long)t * KT;
+      if (e < len) xe[t] = fma(c1, z1[e], fma(c0, z0[e], xe[t]));
+    }
+  }
+  if (q < k) {
+    const double* z0 = Z + (long long)q * zs;
+    const double c0 = cf[q];
+#pragma unroll
+    for (int t = 0; t < KE; ++t) {
+      const long long e = base + (long long)t * KT;
+      if (e < len) xe[t] = fma(c0, z0[e], xe[t]);
     }
   }
 #pragma unroll
   for (int t = 0; t < KE; ++t) {
-    const long long e = base + (long long)t * RT;
+    const long long e = base + (long long)t * KT;
     if (e < len) x[e] = xe[t];
   }
 }
@@ -244,7 +278,7 @@ __global__ void __launch_bounds__(RT) k_axpy_multi(double* __restrict__ x, const
 void launch_axpy_multi(double* x, const double* Z, long long zstride, const double* ycoef, int k, long long len,
                        cudaStream_t s) {
   SD_COUNT(1);
-  k_axpy_multi<<<reduce_blocks(len), RT, 0, s>>>(x, Z, zstride, ycoef, k, len);
+  k_axpy_multi<<<reduce_blocks(len), KT, 0, s>>>(x, Z, zstride, ycoef, k, len);
 }
 
 // ----------------------------------------------------- Hessenberg / Givens

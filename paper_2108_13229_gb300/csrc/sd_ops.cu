@@ -29,35 +29,46 @@ namespace sdk {
 static const int BX = 32, BY = 8;
 
 static inline dim3 grid2(int nx, int ny) { return dim3((nx + BX - 1) / BX, (ny + BY - 1) / BY); }
+// rows marched by one thread (measured on GB300): four consecutive rows help
+// the FP64 operator from n = 512 and the cell-block kernels from n = 1024;
+// the velocity-block kernels keep one row per thread (more blocks in flight)
+static inline int rows_apply(int n) { return n >= 512 ? 4 : 1; }
+static inline int rows_cell(int n) { return n >= 1024 ? 4 : 1; }
+static inline int rows_vel(int) { return 1; }
+static inline dim3 grid2R(int nx, int ny, int R) { return dim3((nx + BX - 1) / BX, (ny + BY * R - 1) / (BY * R)); }
 
 // ------------------------------------------------------------------ rows
+// Each row function loads every neighbour it may need from an in-range
+// (clamped) address first and masks the terms that do not exist at a
+// boundary with selects, so the loads of a row can be issued together.
+// Terms are accumulated in a fixed order.
+//
 // Off-diagonal part and diagonal of the velocity-block row of interior u face (i, j).
 template <typename T>
 __device__ __forceinline__ void u_row(const Coef<T>& c, const T* __restrict__ u, const T* __restrict__ v, int i,
                                       int j, bool read, T& off, T& diag) {
   const int n = c.n, P = c.P;
   const T mu = c.mu, h = c.h;
-  T dg = c.cm + T(4) * mu, of = T(0);
-  if (read) {
-    if (i - 1 >= 1) of -= T(2) * mu * u[j * P + i - 1];
-    if (i + 1 <= n - 1) of -= T(2) * mu * u[j * P + i + 1];
-  }
-  if (j < n - 1) {
-    dg += mu;
-    if (read) of += -mu * u[(j + 1) * P + i] - mu * v[(j + 1) * P + i] + mu * v[(j + 1) * P + i - 1];
-  } else {
-    dg += T(2) * mu;
-  }
-  if (j > 0) {
-    dg += mu;
-    if (read) of += -mu * u[(j - 1) * P + i] + mu * v[j * P + i] - mu * v[j * P + i - 1];
-  } else {
-    const T wh = c.w[i] * h;
-    dg += T(2) * wh;
-    if (read) of += wh * (v[i] - v[i - 1]);
-  }
-  off = of;
+  const bool top = j == n - 1, bot = j == 0;
+  const T wh = bot ? c.w[i] * h : T(0);
+  T dg = c.cm + T(4) * mu;
+  dg += top ? T(2) * mu : mu;
+  dg += bot ? T(2) * wh : mu;
   diag = dg;
+  if (!read) {
+    off = T(0);
+    return;
+  }
+  const long long r0 = (long long)j * P, rN = (long long)(top ? j : j + 1) * P, rS = (long long)(bot ? j : j - 1) * P;
+  const long long rv1 = (long long)(j + 1) * P;
+  const T uW = u[r0 + i - 1], uE = u[r0 + i + 1], uN = u[rN + i], uS = u[rS + i];
+  const T vN = v[rv1 + i], vNW = v[rv1 + i - 1], vS = v[r0 + i], vSW = v[r0 + i - 1];
+  T of = T(0);
+  of -= (i - 1 >= 1) ? T(2) * mu * uW : T(0);
+  of -= (i + 1 <= n - 1) ? T(2) * mu * uE : T(0);
+  of += top ? T(0) : (-mu * uN - mu * vN + mu * vNW);
+  of += bot ? wh * (vS - vSW) : (-mu * uS + mu * vS - mu * vSW);
+  off = of;
 }
 
 // Same for the v face (i, j), 0 <= j <= n-1 (j = 0: interface half control volume).
@@ -66,45 +77,42 @@ __device__ __forceinline__ void v_row(const Coef<T>& c, const T* __restrict__ u,
                                       int j, bool read, T& off, T& diag) {
   const int n = c.n, P = c.P;
   const T mu = c.mu, h = c.h;
-  T dg, of = T(0);
+  const bool left = i == 0, right = i == n - 1;
   if (j == 0) {
-    dg = T(0.5) * c.cm + T(2) * mu + c.rg[i];
-    if (read) of -= T(2) * mu * v[P + i];
-    if (i > 0) {
-      const T w = c.w[i];
-      dg += T(0.5) * h * w;
-      if (read) of += w * h * u[i] - T(0.5) * h * w * v[i - 1];
-    } else {
-      dg += mu;
+    const T wl = left ? T(0) : c.w[i], wr = right ? T(0) : c.w[i + 1];
+    T dg = T(0.5) * c.cm + T(2) * mu + c.rg[i];
+    dg += left ? mu : T(0.5) * h * wl;
+    dg += right ? mu : T(0.5) * h * wr;
+    diag = dg;
+    if (!read) {
+      off = T(0);
+      return;
     }
-    if (i < n - 1) {
-      const T w = c.w[i + 1];
-      dg += T(0.5) * h * w;
-      if (read) of += -w * h * u[i + 1] - T(0.5) * h * w * v[i + 1];
-    } else {
-      dg += mu;
-    }
-  } else {
-    dg = c.cm + T(4) * mu;
-    if (read) {
-      of -= T(2) * mu * v[(j - 1) * P + i];
-      if (j + 1 <= n - 1) of -= T(2) * mu * v[(j + 1) * P + i];
-    }
-    if (i < n - 1) {
-      dg += mu;
-      if (read) of += -mu * v[j * P + i + 1] - mu * u[j * P + i + 1] + mu * u[(j - 1) * P + i + 1];
-    } else {
-      dg += T(2) * mu;
-    }
-    if (i > 0) {
-      dg += mu;
-      if (read) of += -mu * v[j * P + i - 1] + mu * u[j * P + i] - mu * u[(j - 1) * P + i];
-    } else {
-      dg += T(2) * mu;
-    }
+    const T v1 = v[P + i], uL = u[i], uR = u[i + 1];
+    const T vL = v[left ? i : i - 1], vR = v[right ? i : i + 1];
+    T of = -(T(2) * mu * v1);
+    of += left ? T(0) : (wl * h * uL - T(0.5) * h * wl * vL);
+    of += right ? T(0) : (-wr * h * uR - T(0.5) * h * wr * vR);
+    off = of;
+    return;
   }
-  off = of;
+  T dg = c.cm + T(4) * mu;
+  dg += right ? T(2) * mu : mu;
+  dg += left ? T(2) * mu : mu;
   diag = dg;
+  if (!read) {
+    off = T(0);
+    return;
+  }
+  const long long r0 = (long long)j * P, rm = (long long)(j - 1) * P, rp = (long long)(j + 1) * P;
+  const int iE = right ? i : i + 1, iW = left ? i : i - 1;
+  const T vS = v[rm + i], vN = v[rp + i], vE = v[r0 + iE], vW = v[r0 + iW];
+  const T uE = u[r0 + i + 1], uES = u[rm + i + 1], uW = u[r0 + i], uWS = u[rm + i];
+  T of = -(T(2) * mu * vS);
+  of -= (j + 1 <= n - 1) ? T(2) * mu * vN : T(0);
+  of += right ? T(0) : (-mu * vE - mu * uE + mu * uES);
+  of += left ? T(0) : (-mu * vW + mu * uW - mu * uWS);
+  off = of;
 }
 
 // Darcy row of pm cell (i, j) (D' block only, no interface flux).
@@ -112,78 +120,91 @@ template <typename T>
 __device__ __forceinline__ void d_row(const Coef<T>& c, const T* __restrict__ p, int i, int j, bool read, T& off,
                                       T& diag) {
   const int n = c.n, P = c.P;
-  const T tw = c.Tx[j * P + i], te = c.Tx[j * P + i + 1];
-  const T ts = c.Ty[j * P + i], tn = c.Ty[(j + 1) * P + i];
+  const long long r0 = (long long)j * P;
+  const T tw = c.Tx[r0 + i], te = c.Tx[r0 + i + 1];
+  const T ts = c.Ty[r0 + i], tn = c.Ty[r0 + P + i];
   diag = tw + te + ts + tn;
-  T of = T(0);
-  if (read) {
-    if (i > 0) of -= tw * p[j * P + i - 1];
-    if (i < n - 1) of -= te * p[j * P + i + 1];
-    if (j > 0) of -= ts * p[(j - 1) * P + i];
-    if (j < n - 1) of -= tn * p[(j + 1) * P + i];
+  if (!read) {
+    off = T(0);
+    return;
   }
+  const T pW = p[r0 + (i > 0 ? i - 1 : i)], pE = p[r0 + (i < n - 1 ? i + 1 : i)];
+  const T pS = p[(j > 0 ? r0 - P : r0) + i], pN = p[(j < n - 1 ? r0 + P : r0) + i];
+  T of = T(0);
+  of -= i > 0 ? tw * pW : T(0);
+  of -= i < n - 1 ? te * pE : T(0);
+  of -= j > 0 ? ts * pS : T(0);
+  of -= j < n - 1 ? tn * pN : T(0);
   off = of;
 }
 
 // ------------------------------------------------------- whole operator (K1)
+template <int R>
 __global__ void k_apply_full(Coef<double> c, const double* __restrict__ x, const double* __restrict__ b,
                              double* __restrict__ y) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
   const int n = c.n, P = c.P;
-  if (i > n || j > n) return;
-  const double h = c.h;
-  const double* u = x;
-  const double* v = x + (long long)n * P;
-  const double* pf = x + (long long)(2 * n + 1) * P;
-  const double* pm = x + (long long)(3 * n + 1) * P;
-  if (j < n) {
-    const long long k = (long long)j * P + i;
-    double val;
-    if (i == 0 || i == n) {
-      val = u[k];
-    } else {
-      double off, dg;
-      u_row(c, u, v, i, j, true, off, dg);
-      val = dg * u[k] + off + h * (pf[k] - pf[k - 1]);
+  if (i > c.n) return;
+#pragma unroll
+  for (int rr = 0; rr < R; ++rr) {
+    const int j = j0 + rr;
+    if (j > c.n) break;
+    const double h = c.h;
+    const double* u = x;
+    const double* v = x + (long long)n * P;
+    const double* pf = x + (long long)(2 * n + 1) * P;
+    const double* pm = x + (long long)(3 * n + 1) * P;
+    if (j < n) {
+      const long long k = (long long)j * P + i;
+      double val;
+      if (i == 0 || i == n) {
+        val = u[k];
+      } else {
+        double off, dg;
+        u_row(c, u, v, i, j, true, off, dg);
+        val = dg * u[k] + off + h * (pf[k] - pf[k - 1]);
+      }
+      y[k] = b ? b[k] - val : val;
     }
-    y[k] = b ? b[k] - val : val;
-  }
-  if (i < n) {
-    const long long kv = (long long)j * P + i;
-    const long long k = (long long)n * P + kv;
-    double val;
-    if (j == n) {
-      val = v[kv];
-    } else {
-      double off, dg;
-      v_row(c, u, v, i, j, true, off, dg);
-      val = dg * v[kv] + off;
-      if (j > 0) val += h * (pf[kv] - pf[kv - P]);
-      else val += h * pf[i] - h * pm[(long long)(n - 1) * P + i];
+    if (i < n) {
+      const long long kv = (long long)j * P + i;
+      const long long k = (long long)n * P + kv;
+      double val;
+      if (j == n) {
+        val = v[kv];
+      } else {
+        double off, dg;
+        v_row(c, u, v, i, j, true, off, dg);
+        val = dg * v[kv] + off;
+        if (j > 0) val += h * (pf[kv] - pf[kv - P]);
+        else val += h * pf[i] - h * pm[(long long)(n - 1) * P + i];
+      }
+      y[k] = b ? b[k] - val : val;
     }
-    y[k] = b ? b[k] - val : val;
-  }
-  if (i < n && j < n) {
-    const long long kc = (long long)j * P + i;
-    double s = -v[kc];
-    if (i + 1 <= n - 1) s += u[kc + 1];
-    if (i >= 1) s -= u[kc];
-    if (j + 1 <= n - 1) s += v[kc + P];
-    const long long kp = (long long)(2 * n + 1) * P + kc;
-    y[kp] = b ? b[kp] - h * s : h * s;
-    double off, dg;
-    d_row(c, pm, i, j, true, off, dg);
-    double val = dg * pm[kc] + off;
-    if (j == n - 1) val += h * v[i];
-    const long long km = (long long)(3 * n + 1) * P + kc;
-    y[km] = b ? b[km] - val : val;
+    if (i < n && j < n) {
+      const long long kc = (long long)j * P + i;
+      double s = -v[kc];
+      if (i + 1 <= n - 1) s += u[kc + 1];
+      if (i >= 1) s -= u[kc];
+      if (j + 1 <= n - 1) s += v[kc + P];
+      const long long kp = (long long)(2 * n + 1) * P + kc;
+      y[kp] = b ? b[kp] - h * s : h * s;
+      double off, dg;
+      d_row(c, pm, i, j, true, off, dg);
+      double val = dg * pm[kc] + off;
+      if (j == n - 1) val += h * v[i];
+      const long long km = (long long)(3 * n + 1) * P + kc;
+      y[km] = b ? b[km] - val : val;
+    }
   }
 }
 
 void launch_apply_full(const Coef<double>& c, const double* x, const double* b, double* y, cudaStream_t s) {
   SD_COUNT(1);
-  k_apply_full<<<grid2(c.n + 1, c.n + 1), dim3(BX, BY), 0, s>>>(c, x, b, y);
+  const int R = rows_apply(c.n);
+  if (R == 4) k_apply_full<4><<<grid2R(c.n + 1, c.n + 1, 4), dim3(BX, BY), 0, s>>>(c, x, b, y);
+  else k_apply_full<1><<<grid2R(c.n + 1, c.n + 1, 1), dim3(BX, BY), 0, s>>>(c, x, b, y);
 }
 
 // ------------------------------------------------------ block V smoothers
@@ -228,23 +249,30 @@ __device__ __forceinline__ void cheb_V_at(const Coef<T>& c, const T* __restrict_
   }
 }
 
-template <typename T>
+template <typename T, int R>
 __global__ void k_cheb_V(Coef<T> c, const T* __restrict__ xin, const T* __restrict__ b, T* __restrict__ d,
                          T* __restrict__ xout, T a, T cc, long long bstride) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i > c.n || j > c.n) return;
-  const long long bo = (long long)blockIdx.z * bstride;
-  cheb_V_at(c, xin ? xin + bo : nullptr, b + bo, d + bo, xout + bo, a, cc, i, j);
+  const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
+  if (i > c.n) return;
+#pragma unroll
+  for (int rr = 0; rr < R; ++rr) {
+    const int j = j0 + rr;
+    if (j > c.n) break;
+    const long long bo = (long long)blockIdx.z * bstride;
+    cheb_V_at(c, xin ? xin + bo : nullptr, b + bo, d + bo, xout + bo, a, cc, i, j);
+  }
 }
 
 template <typename T>
 void launch_cheb_V(const Coef<T>& c, const T* x_in, const T* b, T* d, T* x_out, T a, T cc, int nbatch,
                    long long bstride, cudaStream_t s) {
   SD_COUNT(1);
-  dim3 g = grid2(c.n + 1, c.n + 1);
+  const int R = rows_vel(c.n);
+  dim3 g = grid2R(c.n + 1, c.n + 1, R);
   g.z = nbatch;
-  k_cheb_V<T><<<g, dim3(BX, BY), 0, s>>>(c, x_in, b, d, x_out, a, cc, bstride);
+  if (R == 4) k_cheb_V<T, 4><<<g, dim3(BX, BY), 0, s>>>(c, x_in, b, d, x_out, a, cc, bstride);
+  else k_cheb_V<T, 1><<<g, dim3(BX, BY), 0, s>>>(c, x_in, b, d, x_out, a, cc, bstride);
 }
 
 // r = b - V x (mode 0; b == nullptr: -V x), D^-1 V x (mode 1), V x (mode 2)
@@ -280,23 +308,30 @@ __device__ __forceinline__ void resid_V_at(const Coef<T>& c, const T* __restrict
   }
 }
 
-template <typename T>
+template <typename T, int R>
 __global__ void k_resid_V(Coef<T> c, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, int jac,
                           long long bstride) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i > c.n || j > c.n) return;
-  const long long bo = (long long)blockIdx.z * bstride;
-  resid_V_at(c, x + bo, b ? b + bo : nullptr, r + bo, jac, i, j);
+  const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
+  if (i > c.n) return;
+#pragma unroll
+  for (int rr = 0; rr < R; ++rr) {
+    const int j = j0 + rr;
+    if (j > c.n) break;
+    const long long bo = (long long)blockIdx.z * bstride;
+    resid_V_at(c, x + bo, b ? b + bo : nullptr, r + bo, jac, i, j);
+  }
 }
 
 template <typename T>
 void launch_resid_V(const Coef<T>& c, const T* x, const T* b, T* r, int jac, int nbatch, long long bstride,
                     cudaStream_t s) {
   SD_COUNT(1);
-  dim3 g = grid2(c.n + 1, c.n + 1);
+  const int R = rows_vel(c.n);
+  dim3 g = grid2R(c.n + 1, c.n + 1, R);
   g.z = nbatch;
-  k_resid_V<T><<<g, dim3(BX, BY), 0, s>>>(c, x, b, r, jac, bstride);
+  if (R == 4) k_resid_V<T, 4><<<g, dim3(BX, BY), 0, s>>>(c, x, b, r, jac, bstride);
+  else k_resid_V<T, 1><<<g, dim3(BX, BY), 0, s>>>(c, x, b, r, jac, bstride);
 }
 
 // ------------------------------------------------------ block D' smoothers
@@ -314,23 +349,30 @@ __device__ __forceinline__ void cheb_D_at(const Coef<T>& c, const T* __restrict_
   xout[k] = xc + dn;
 }
 
-template <typename T>
+template <typename T, int R>
 __global__ void k_cheb_D(Coef<T> c, const T* __restrict__ xin, const T* __restrict__ b, T* __restrict__ d,
                          T* __restrict__ xout, T a, T cc, long long bstride) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= c.n || j >= c.n) return;
-  const long long bo = (long long)blockIdx.z * bstride;
-  cheb_D_at(c, xin ? xin + bo : nullptr, b + bo, d + bo, xout + bo, a, cc, i, j);
+  const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
+  if (i >= c.n) return;
+#pragma unroll
+  for (int rr = 0; rr < R; ++rr) {
+    const int j = j0 + rr;
+    if (j >= c.n) break;
+    const long long bo = (long long)blockIdx.z * bstride;
+    cheb_D_at(c, xin ? xin + bo : nullptr, b + bo, d + bo, xout + bo, a, cc, i, j);
+  }
 }
 
 template <typename T>
 void launch_cheb_D(const Coef<T>& c, const T* x_in, const T* b, T* d, T* x_out, T a, T cc, int nbatch,
                    long long bstride, cudaStream_t s) {
   SD_COUNT(1);
-  dim3 g = grid2(c.n, c.n);
+  const int R = rows_cell(c.n);
+  dim3 g = grid2R(c.n, c.n, R);
   g.z = nbatch;
-  k_cheb_D<T><<<g, dim3(BX, BY), 0, s>>>(c, x_in, b, d, x_out, a, cc, bstride);
+  if (R == 4) k_cheb_D<T, 4><<<g, dim3(BX, BY), 0, s>>>(c, x_in, b, d, x_out, a, cc, bstride);
+  else k_cheb_D<T, 1><<<g, dim3(BX, BY), 0, s>>>(c, x_in, b, d, x_out, a, cc, bstride);
 }
 
 template <typename T>
@@ -343,23 +385,30 @@ __device__ __forceinline__ void resid_D_at(const Coef<T>& c, const T* __restrict
   r[k] = jac == 1 ? ax / dg : (jac == 2 ? ax : (b ? b[k] - ax : -ax));
 }
 
-template <typename T>
+template <typename T, int R>
 __global__ void k_resid_D(Coef<T> c, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, int jac,
                           long long bstride) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= c.n || j >= c.n) return;
-  const long long bo = (long long)blockIdx.z * bstride;
-  resid_D_at(c, x + bo, b ? b + bo : nullptr, r + bo, jac, i, j);
+  const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
+  if (i >= c.n) return;
+#pragma unroll
+  for (int rr = 0; rr < R; ++rr) {
+    const int j = j0 + rr;
+    if (j >= c.n) break;
+    const long long bo = (long long)blockIdx.z * bstride;
+    resid_D_at(c, x + bo, b ? b + bo : nullptr, r + bo, jac, i, j);
+  }
 }
 
 template <typename T>
 void launch_resid_D(const Coef<T>& c, const T* x, const T* b, T* r, int jac, int nbatch, long long bstride,
                     cudaStream_t s) {
   SD_COUNT(1);
-  dim3 g = grid2(c.n, c.n);
+  const int R = rows_cell(c.n);
+  dim3 g = grid2R(c.n, c.n, R);
   g.z = nbatch;
-  k_resid_D<T><<<g, dim3(BX, BY), 0, s>>>(c, x, b, r, jac, bstride);
+  if (R == 4) k_resid_D<T, 4><<<g, dim3(BX, BY), 0, s>>>(c, x, b, r, jac, bstride);
+  else k_resid_D<T, 1><<<g, dim3(BX, BY), 0, s>>>(c, x, b, r, jac, bstride);
 }
 
 // ------------------------------------------------------------ transfers
@@ -453,6 +502,32 @@ void launch_restrict_D(int nf, int Pf, const T* r, int nc, int Pc, T* bc, cudaSt
   k_restrict_D<T><<<grid2(nc, nc), dim3(BX, BY), 0, s>>>(nf, Pf, r, nc, Pc, bc);
 }
 
+// Cell blocks: b_c(I, J) = sum of the residuals b - A x of the four fine
+// cells of coarse cell (I, J) (residual and cell-sum restriction in one pass).
+template <typename T>
+__global__ void k_resid_restrict_D(Coef<T> c, const T* __restrict__ x, const T* __restrict__ b, int nc, int Pc,
+                                   T* __restrict__ bc) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I >= nc || J >= nc) return;
+  T r[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = 2 * I + (q & 1), j = 2 * J + (q >> 1);
+    const long long k = (long long)j * c.P + i;
+    T off, dg;
+    d_row(c, x, i, j, true, off, dg);
+    r[q] = b[k] - (dg * x[k] + off);
+  }
+  bc[(long long)J * Pc + I] = (r[0] + r[1]) + (r[2] + r[3]);
+}
+
+template <typename T>
+void launch_resid_restrict_D(const Coef<T>& c, const T* x, const T* b, int nc, int Pc, T* bc, cudaStream_t s) {
+  SD_COUNT(1);
+  k_resid_restrict_D<T><<<grid2(nc, nc), dim3(BX, BY), 0, s>>>(c, x, b, nc, Pc, bc);
+}
+
 template <typename T>
 __device__ __forceinline__ T cu_at(const T* eu, int nc, int Pc, int I, int J) {
   // coarse u with zero Dirichlet faces and the y ghosts described above
@@ -504,18 +579,25 @@ __device__ __forceinline__ void prolong_V_at(int nf, int Pf, T* __restrict__ x, 
   }
 }
 
-template <typename T>
+template <typename T, int R>
 __global__ void k_prolong_V(int nf, int Pf, T* __restrict__ x, int nc, int Pc, const T* __restrict__ e) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i > nf || j > nf) return;
-  prolong_V_at(nf, Pf, x, nc, Pc, e, i, j);
+  const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
+  if (i > nf) return;
+#pragma unroll
+  for (int rr = 0; rr < R; ++rr) {
+    const int j = j0 + rr;
+    if (j > nf) break;
+    prolong_V_at(nf, Pf, x, nc, Pc, e, i, j);
+  }
 }
 
 template <typename T>
 void launch_prolong_V(int nf, int Pf, T* x, int nc, int Pc, const T* e, cudaStream_t s) {
   SD_COUNT(1);
-  k_prolong_V<T><<<grid2(nf + 1, nf + 1), dim3(BX, BY), 0, s>>>(nf, Pf, x, nc, Pc, e);
+  const int R = rows_vel(nf);
+  if (R == 4) k_prolong_V<T, 4><<<grid2R(nf + 1, nf + 1, 4), dim3(BX, BY), 0, s>>>(nf, Pf, x, nc, Pc, e);
+  else k_prolong_V<T, 1><<<grid2R(nf + 1, nf + 1, 1), dim3(BX, BY), 0, s>>>(nf, Pf, x, nc, Pc, e);
 }
 
 template <typename T>
@@ -538,18 +620,25 @@ __device__ __forceinline__ void prolong_D_at(int Pf, T* __restrict__ x, int nc, 
   x[(long long)j * Pf + i] += val;
 }
 
-template <typename T>
+template <typename T, int R>
 __global__ void k_prolong_D(int nf, int Pf, T* __restrict__ x, int nc, int Pc, const T* __restrict__ e) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= nf || j >= nf) return;
-  prolong_D_at(Pf, x, nc, Pc, e, i, j);
+  const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
+  if (i >= nf) return;
+#pragma unroll
+  for (int rr = 0; rr < R; ++rr) {
+    const int j = j0 + rr;
+    if (j >= nf) break;
+    prolong_D_at(Pf, x, nc, Pc, e, i, j);
+  }
 }
 
 template <typename T>
 void launch_prolong_D(int nf, int Pf, T* x, int nc, int Pc, const T* e, cudaStream_t s) {
   SD_COUNT(1);
-  k_prolong_D<T><<<grid2(nf, nf), dim3(BX, BY), 0, s>>>(nf, Pf, x, nc, Pc, e);
+  const int R = rows_cell(nf);
+  if (R == 4) k_prolong_D<T, 4><<<grid2R(nf, nf, 4), dim3(BX, BY), 0, s>>>(nf, Pf, x, nc, Pc, e);
+  else k_prolong_D<T, 1><<<grid2R(nf, nf, 1), dim3(BX, BY), 0, s>>>(nf, Pf, x, nc, Pc, e);
 }
 
 // ------------------------------------------------ fused coarse V-cycle
@@ -673,14 +762,17 @@ size_t coarse_cycle_smem(const CoarseCycle<T>& q) {
 }
 
 template <typename T>
+int prepare_coarse_cycle() {
+  return cudaFuncSetAttribute(k_coarse_cycle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) ==
+                 cudaSuccess
+             ? 0
+             : -1;
+}
+
+template <typename T>
 int launch_coarse_cycle(const CoarseCycle<T>& q, cudaStream_t s) {
   const size_t sm = coarse_cycle_smem(q);
   if (sm > 200 * 1024) return -1;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_coarse_cycle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
   SD_COUNT(1);
   k_coarse_cycle<T><<<1, 1024, sm, s>>>(q);
   return 0;
@@ -744,7 +836,7 @@ __global__ void k_precond_mid(Coef<double> c, const double* __restrict__ r, doub
     const long long k = (long long)n * P + (long long)j * P + i;
     z[k] = (double)eV[k];
   }
-  if (i < n && j < n) {
+  if (rD && i < n && j < n) {
     const long long kc = (long long)j * P + i;
     T val = (T)r[(long long)(3 * n + 1) * P + kc];
     if (useC && j == n - 1) val -= (T)c.h * eV[(long long)n * P + i];
@@ -1078,6 +1170,7 @@ void launch_unpack(const Geom& g, const double* padded, double* dense, cudaStrea
   template void launch_restrict_D<T>(int, int, const T*, int, int, T*, cudaStream_t);            \
   template void launch_prolong_V<T>(int, int, T*, int, int, const T*, cudaStream_t);                              \
   template void launch_prolong_D<T>(int, int, T*, int, int, const T*, cudaStream_t);                              \
+  template void launch_resid_restrict_D<T>(const Coef<T>&, const T*, const T*, int, int, T*, cudaStream_t);                              \
   template void launch_precond_entry<T>(const Coef<double>&, const double*, double*, double, const T*, double, int, T*, cudaStream_t); \
   template void launch_precond_mid<T>(const Coef<double>&, const double*, double*, const T*, int, T*, cudaStream_t); \
   template void launch_precond_exit<T>(const Coef<double>&, double*, const T*, cudaStream_t);                     \
@@ -1085,6 +1178,8 @@ void launch_unpack(const Geom& g, const double* padded, double* dense, cudaStrea
 SD_INST(float)
 SD_INST(double)
 template int launch_coarse_cycle<float>(const CoarseCycle<float>&, cudaStream_t);
+template int prepare_coarse_cycle<float>();
+template int prepare_coarse_cycle<double>();
 template int launch_coarse_cycle<double>(const CoarseCycle<double>&, cudaStream_t);
 template size_t coarse_cycle_smem<float>(const CoarseCycle<float>&);
 template size_t coarse_cycle_smem<double>(const CoarseCycle<double>&);

@@ -41,7 +41,7 @@ class sd_options(ctypes.Structure):
                 ("cheb_degree", ctypes.c_int32), ("coarsest", ctypes.c_int32), ("schur_gamma", ctypes.c_double),
                 ("cheb_ratio", ctypes.c_double), ("schur_mass", ctypes.c_int32), ("fuse_coarse", ctypes.c_int32),
                 ("orth", ctypes.c_int32), ("reorth_eta", ctypes.c_double), ("extrapolate", ctypes.c_int32),
-                ("stream", ctypes.c_void_p)]
+                ("graph", ctypes.c_int32), ("darcy_coupled", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
 
 class sd_step_info(ctypes.Structure):

@@ -234,3 +234,30 @@ def test_paper_block_preconditioners(sd, mode):
     _, _, x = sd.sd_get_state(h)
     for k, e in fields_rel(x, xr, n).items():
         assert e <= 1e-8, (k, e)
+
+
+def test_graph_replay_bitwise(sd):
+    # the captured Arnoldi step launches exactly the kernels of the direct path
+    n = 64
+    K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=9)
+    xs = []
+    for graph in (0, 1):
+        h = make(sd, n, 1e-3, K, 1.0, 0.05, graph=graph)
+        sd.sd_step(h, 4)
+        xs.append(sd.sd_get_state(h)[2])
+    assert np.array_equal(xs[0], xs[1])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_darcy_overlap_parity(sd, precision):
+    # block-diagonal Darcy part on a second stream: same solution as the oracle
+    n = 64
+    K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=0)
+    o = O.Oracle(n, 1e-3, 1.0, 0.05, K)
+    xr = o.run(O.exact(n, 0.0, 1e-3), 0.0, 3)
+    h = make(sd, n, 1e-3, K, 1.0, 0.05, precision, rtol=1e-12, darcy_coupled=0)
+    infos = sd.sd_step(h, 3)
+    assert all(i["status"] == 0 for i in infos)
+    _, _, x = sd.sd_get_state(h)
+    for k, e in fields_rel(x, xr, n).items():
+        assert e <= 1e-8, (k, e)

@@ -93,6 +93,9 @@ typedef struct {
   int32_t bc;          /* SD_BC_MMS */
   int32_t cheb_degree; /* Chebyshev smoothing steps before and after each coarse
                           correction (default 3) */
+  int32_t cheb_degree_coarse; /* the same below the finest level (0: cheb_degree) */
+  int32_t schur_degree;       /* the same in the pressure-Laplacian block (0: as above;
+                                 default 1, one damped-Jacobi step) */
   int32_t coarsest;    /* coarsen while the grid has more than this many cells per
                           side (default 4) */
   double schur_gamma;  /* gamma of S^ (default 0.5) */
@@ -108,9 +111,14 @@ typedef struct {
                           or x^n (0) */
   int32_t graph;       /* replay each Arnoldi step from a captured CUDA graph (default 1;
                           ignored on the legacy default stream and while profiling) */
+  int32_t pdl;         /* programmatic dependent launch between consecutive kernels
+                          of sd_step / sd_solve (default 1) */
+  int32_t tile;        /* FP32 V-cycles: all Chebyshev steps of one smoothing in one
+                          shared-memory-tiled kernel, prolongation folded in (default 1) */
   int32_t darcy_coupled; /* SD_TRI_SCHUR: 1 (default) keeps C'_1, the Darcy block follows
                           the velocity; 0 drops it and overlaps the Darcy V-cycle with
-                          the Stokes part on a second stream */
+                          the Stokes part on a second stream; 2 solves the Darcy block
+                          first (B'_1 kept), concurrently with the pressure block */
   void *stream;        /* cudaStream_t to run on; NULL: the handle creates one */
 } sd_options;
 
@@ -260,6 +268,10 @@ int sd_apply_noalloc(const sd_grid *grid, double mu, const double *K, double alp
 /* Kernel launches made by this library in this process so far (kernels replayed
  * from captured CUDA graphs included). */
 int64_t sd_launch_count(void);
+
+/* sizeof of the public structs, for bindings that check their layout:
+ * 0 sd_grid, 1 sd_options, 2 sd_step_info, 3 sd_request, 4 sd_result; -1 otherwise. */
+int64_t sd_struct_size(int32_t which);
 
 const char *sd_strerror(int code);
 

@@ -17,6 +17,7 @@
 #include <mutex>
 #include <new>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 using namespace sdk;
@@ -235,6 +236,7 @@ Coef<double> coef64(sd_handle* h, int l, bool poisson = false) {
   c.rg = poisson ? C.rgP : C.rg;
   c.Tx = poisson ? C.TxP : C.Tx;
   c.Ty = poisson ? C.TyP : C.Ty;
+  finish_coef(c);
   return c;
 }
 
@@ -247,6 +249,8 @@ void bind_coef(sd_handle* h, MG<T>& M) {
     L.cP = L.c;
     L.c.w = L.own.w; L.c.rg = L.own.rg; L.c.Tx = L.own.Tx; L.c.Ty = L.own.Ty;
     L.cP.w = L.own.wP; L.cP.rg = L.own.rgP; L.cP.Tx = L.own.TxP; L.cP.Ty = L.own.TyP;
+    finish_coef(L.c);
+    finish_coef(L.cP);
   }
 }
 template <>
@@ -379,40 +383,45 @@ int setup_mg(sd_handle* h, MG<T>& M) {
     CKR(power_lmax(h, l, 0, &lv));
     CKR(power_lmax(h, l, 1, &ld));
     CKR(power_lmax(h, l, 2, &lp));
-    cheb_coeffs<T>(lv, h->opt.cheb_ratio, deg, M.L[l].V.cha, M.L[l].V.chc);
-    cheb_coeffs<T>(ld, h->opt.cheb_ratio, deg, M.L[l].D.cha, M.L[l].D.chc);
-    cheb_coeffs<T>(lp, h->opt.cheb_ratio, deg, M.L[l].Pb.cha, M.L[l].Pb.chc);
+    const int dl = (l > 0 && h->opt.cheb_degree_coarse > 0) ? h->opt.cheb_degree_coarse : deg;
+    const int dp = h->opt.schur_degree > 0 ? h->opt.schur_degree : dl;
+    cheb_coeffs<T>(lv, h->opt.cheb_ratio, dl, M.L[l].V.cha, M.L[l].V.chc);
+    cheb_coeffs<T>(ld, h->opt.cheb_ratio, dl, M.L[l].D.cha, M.L[l].D.chc);
+    cheb_coeffs<T>(lp, h->opt.cheb_ratio, dp, M.L[l].Pb.cha, M.L[l].Pb.chc);
   }
   M.fuse_from = -1;
   if (h->opt.fuse_coarse) {
-    int f = 0;
-    while (f < h->nlev && h->geo[f].n > FUSE_N) ++f;
-    if (f < h->nlev && h->nlev - f <= SD_CYC_MAXL) {
-      auto fill = [&](CoarseCycle<T>& q, int kind, int which) {
-        std::memset(&q, 0, sizeof(q));
-        q.nlev = h->nlev - f;
-        q.kind = kind;
-        q.deg = deg;
-        for (int l = f; l < h->nlev; ++l) {
-          MGLevel<T>& L = M.L[l];
-          q.c[l - f] = which == 2 ? L.cP : L.c;
-          Block<T>& B = which == 0 ? L.V : (which == 1 ? L.D : L.Pb);
-          for (int k = 0; k < deg && k < 8 && l + 1 < h->nlev; ++k) {
-            q.cha[l - f][k] = B.cha[k];
-            q.chc[l - f][k] = B.chc[k];
-          }
+    auto fill = [&](CoarseCycle<T>& q, int kind, int which, int f) {
+      std::memset(&q, 0, sizeof(q));
+      q.nlev = h->nlev - f;
+      q.kind = kind;
+      for (int l = f; l < h->nlev; ++l) {
+        MGLevel<T>& L = M.L[l];
+        q.c[l - f] = which == 2 ? L.cP : L.c;
+        Block<T>& B = which == 0 ? L.V : (which == 1 ? L.D : L.Pb);
+        q.deg[l - f] = (int)B.cha.size();
+        for (int k = 0; k < (int)B.cha.size() && k < 8 && l + 1 < h->nlev; ++k) {
+          q.cha[l - f][k] = B.cha[k];
+          q.chc[l - f][k] = B.chc[k];
         }
-        Block<T>& B0 = which == 0 ? M.L[f].V : (which == 1 ? M.L[f].D : M.L[f].Pb);
-        q.b_in = B0.b;
-        q.x_out = B0.x;
-        q.Ainv = which == 0 ? M.AinvV : (which == 1 ? M.AinvD : M.AinvP);
-        q.idx = which == 0 ? M.idxV : M.idxD;
-        q.m = which == 0 ? M.mV : M.mD;
-      };
-      fill(M.cycV, 0, 0);
-      fill(M.cycD, 1, 1);
-      fill(M.cycP, 1, 2);
-      if (coarse_cycle_smem(M.cycV) <= 200 * 1024 && coarse_cycle_smem(M.cycD) <= 200 * 1024) M.fuse_from = f;
+      }
+      Block<T>& B0 = which == 0 ? M.L[f].V : (which == 1 ? M.L[f].D : M.L[f].Pb);
+      q.b_in = B0.b;
+      q.x_out = B0.x;
+      q.Ainv = which == 0 ? M.AinvV : (which == 1 ? M.AinvD : M.AinvP);
+      q.idx = which == 0 ? M.idxV : M.idxD;
+      q.m = which == 0 ? M.mV : M.mD;
+    };
+    // the largest entry grid (at most FUSE_N cells per side) whose levels fit in shared memory
+    for (int f = 0; f < h->nlev; ++f) {
+      if (h->geo[f].n > FUSE_N || h->nlev - f > SD_CYC_MAXL) continue;
+      fill(M.cycV, 0, 0, f);
+      fill(M.cycD, 1, 1, f);
+      fill(M.cycP, 1, 2, f);
+      if (coarse_cycle_smem(M.cycV) <= 200 * 1024 && coarse_cycle_smem(M.cycD) <= 200 * 1024) {
+        M.fuse_from = f;
+        break;
+      }
     }
   }
   return SD_OK;
@@ -459,6 +468,12 @@ double cheb_bytes_V(const Geom& g, size_t es, bool has_x, bool has_d) {
   const double nv = 2.0 * g.n * (g.n + 1);
   return nv * es * (1.0 + (has_x ? 1 : 0) + (has_d ? 1 : 0) + 2.0);
 }
+//  tiled velocity smoothing: read b (and x_in), write x_out over the faces
+//  (the small coarse correction read by the post-smoothing is not counted)
+double tile_bytes_V(const Geom& g, size_t es, bool has_x) {
+  const double nv = 2.0 * g.n * (g.n + 1);
+  return nv * es * (has_x ? 3.0 : 2.0);
+}
 //  whole-system FP64 operator, algorithmic flops: one multiply-add per stored
 //  matrix entry, nnz = 2 * 11 (u, v rows) + 4 (continuity) + 5 (Darcy) per
 //  cell minus the eliminated boundary couplings, about 31 per cell.
@@ -475,11 +490,30 @@ double apply_bytes(const Geom& g, bool resid) {
 }
 
 // ----------------------------------------------------------- V-cycles
+template <typename T>
+ChebSteps<T> steps_of(const Block<T>& B) {
+  ChebSteps<T> cs;
+  std::memset(&cs, 0, sizeof(cs));
+  cs.ns = (int)B.cha.size();
+  for (int k = 0; k < cs.ns && k < 8; ++k) {
+    cs.a[k] = B.cha[k];
+    cs.c[k] = B.chc[k];
+  }
+  return cs;
+}
+
+// tiled smoothing (all steps of one smoothing in one kernel) is used for the
+// FP32 hierarchy with at most four Chebyshev steps
+template <typename T>
+bool use_tiles(const sd_handle* h, const Block<T>& B) {
+  return std::is_same<T, float>::value && h->opt.tile && B.cha.size() >= 1 && B.cha.size() <= 4;
+}
+
 // Velocity block: Chebyshev pre-smoothing from zero, residual, transposed
 // bilinear restriction, coarse correction, bilinear prolongation,
 // Chebyshev post-smoothing; dense FP64 solve on the coarsest grid.
 template <typename T>
-void vcycle_V(MG<T>& M, int l, int deg, cudaStream_t s, sd_handle* prof_owner) {
+void vcycle_V(MG<T>& M, int l, cudaStream_t s, sd_handle* prof_owner) {
   MGLevel<T>& L = M.L[l];
   Block<T>& B = L.V;
   if (l == M.fuse_from && launch_coarse_cycle<T>(M.cycV, s) == 0) {
@@ -491,27 +525,43 @@ void vcycle_V(MG<T>& M, int l, int deg, cudaStream_t s, sd_handle* prof_owner) {
     B.res = B.x;
     return;
   }
-  T* cur = nullptr;
-  for (int k = 0; k < deg; ++k) {
-    T* out = (cur == B.x) ? B.x2 : B.x;
-    {
-      ProfScope ps(prof_owner, l == 0 ? SD_PROF_CHEB_V : -2, cheb_bytes_V(L.g, sizeof(T), cur != nullptr, k > 0));
-      launch_cheb_V<T>(L.c, cur, B.b, B.d, out, B.cha[k], B.chc[k], 1, 0, s);
-    }
-    cur = out;
-  }
   MGLevel<T>& C = M.L[l + 1];
+  T* cur = nullptr;
+  const bool tiles = use_tiles(prof_owner, B);
+  if (tiles) {
+    ProfScope ps(prof_owner, l == 0 ? SD_PROF_CHEB_V : -2, tile_bytes_V(L.g, sizeof(T), false));
+    if constexpr (std::is_same<T, float>::value)
+      launch_smooth_tile_V<T>(L.c, nullptr, B.b, B.x, steps_of(B), nullptr, 0, 0, s);
+    cur = B.x;
+  } else {
+    for (int k = 0; k < (int)B.cha.size(); ++k) {
+      T* out = (cur == B.x) ? B.x2 : B.x;
+      {
+        ProfScope ps(prof_owner, l == 0 ? SD_PROF_CHEB_V : -2, cheb_bytes_V(L.g, sizeof(T), cur != nullptr, k > 0));
+        launch_cheb_V<T>(L.c, cur, B.b, B.d, out, B.cha[k], B.chc[k], 1, 0, s);
+      }
+      cur = out;
+    }
+  }
   launch_resid_V<T>(L.c, cur, B.b, B.r, 0, 1, 0, s);
   launch_restrict_V<T>(L.g.n, L.g.P, B.r, C.g.n, C.g.P, C.V.b, s);
-  vcycle_V(M, l + 1, deg, s, prof_owner);
-  launch_prolong_V<T>(L.g.n, L.g.P, cur, C.g.n, C.g.P, C.V.res, s);
-  for (int k = 0; k < deg; ++k) {
+  vcycle_V(M, l + 1, s, prof_owner);
+  if (tiles) {  // prolongation folded into the post-smoothing tile load
     T* out = (cur == B.x) ? B.x2 : B.x;
-    {
-      ProfScope ps(prof_owner, l == 0 ? SD_PROF_CHEB_V : -2, cheb_bytes_V(L.g, sizeof(T), true, k > 0));
-      launch_cheb_V<T>(L.c, cur, B.b, B.d, out, B.cha[k], B.chc[k], 1, 0, s);
-    }
+    ProfScope ps(prof_owner, l == 0 ? SD_PROF_CHEB_V : -2, tile_bytes_V(L.g, sizeof(T), true));
+    if constexpr (std::is_same<T, float>::value)
+      launch_smooth_tile_V<T>(L.c, cur, B.b, out, steps_of(B), C.V.res, C.g.n, C.g.P, s);
     cur = out;
+  } else {
+    launch_prolong_V<T>(L.g.n, L.g.P, cur, C.g.n, C.g.P, C.V.res, s);
+    for (int k = 0; k < (int)B.cha.size(); ++k) {
+      T* out = (cur == B.x) ? B.x2 : B.x;
+      {
+        ProfScope ps(prof_owner, l == 0 ? SD_PROF_CHEB_V : -2, cheb_bytes_V(L.g, sizeof(T), true, k > 0));
+        launch_cheb_V<T>(L.c, cur, B.b, B.d, out, B.cha[k], B.chc[k], 1, 0, s);
+      }
+      cur = out;
+    }
   }
   B.res = cur;
 }
@@ -519,7 +569,7 @@ void vcycle_V(MG<T>& M, int l, int deg, cudaStream_t s, sd_handle* prof_owner) {
 // Cell-centred block (Darcy D' with its TPFA coefficients, or the pressure
 // Laplacian P): same cycle with cell-sum restriction and bilinear prolongation.
 template <typename T>
-void vcycle_cell(MG<T>& M, int l, int deg, bool poisson, cudaStream_t s) {
+void vcycle_cell(MG<T>& M, int l, bool poisson, cudaStream_t s, const sd_handle* h) {
   MGLevel<T>& L = M.L[l];
   Block<T>& B = poisson ? L.Pb : L.D;
   const Coef<T>& c = poisson ? L.cP : L.c;
@@ -532,21 +582,35 @@ void vcycle_cell(MG<T>& M, int l, int deg, bool poisson, cudaStream_t s) {
     B.res = B.x;
     return;
   }
-  T* cur = nullptr;
-  for (int k = 0; k < deg; ++k) {
-    T* out = (cur == B.x) ? B.x2 : B.x;
-    launch_cheb_D<T>(c, cur, B.b, B.d, out, B.cha[k], B.chc[k], 1, 0, s);
-    cur = out;
-  }
   MGLevel<T>& C = M.L[l + 1];
   Block<T>& BC = poisson ? C.Pb : C.D;
+  T* cur = nullptr;
+  const bool tiles = use_tiles(h, B);
+  if (tiles) {
+    if constexpr (std::is_same<T, float>::value)
+      launch_smooth_tile_D<T>(c, nullptr, B.b, B.x, steps_of(B), nullptr, 0, 0, s);
+    cur = B.x;
+  } else {
+    for (int k = 0; k < (int)B.cha.size(); ++k) {
+      T* out = (cur == B.x) ? B.x2 : B.x;
+      launch_cheb_D<T>(c, cur, B.b, B.d, out, B.cha[k], B.chc[k], 1, 0, s);
+      cur = out;
+    }
+  }
   launch_resid_restrict_D<T>(c, cur, B.b, C.g.n, C.g.P, BC.b, s);
-  vcycle_cell(M, l + 1, deg, poisson, s);
-  launch_prolong_D<T>(L.g.n, L.g.P, cur, C.g.n, C.g.P, BC.res, s);
-  for (int k = 0; k < deg; ++k) {
+  vcycle_cell(M, l + 1, poisson, s, h);
+  if (tiles) {  // prolongation folded into the post-smoothing tile load
     T* out = (cur == B.x) ? B.x2 : B.x;
-    launch_cheb_D<T>(c, cur, B.b, B.d, out, B.cha[k], B.chc[k], 1, 0, s);
+    if constexpr (std::is_same<T, float>::value)
+      launch_smooth_tile_D<T>(c, cur, B.b, out, steps_of(B), BC.res, C.g.n, C.g.P, s);
     cur = out;
+  } else {
+    launch_prolong_D<T>(L.g.n, L.g.P, cur, C.g.n, C.g.P, BC.res, s);
+    for (int k = 0; k < (int)B.cha.size(); ++k) {
+      T* out = (cur == B.x) ? B.x2 : B.x;
+      launch_cheb_D<T>(c, cur, B.b, B.d, out, B.cha[k], B.chc[k], 1, 0, s);
+      cur = out;
+    }
   }
   B.res = cur;
 }
@@ -560,28 +624,50 @@ void precond(sd_handle* h, MG<T>& M, const double* r, double* z) {
   cudaStream_t s = h->s;
   const Coef<double> c = coef64(h, 0);
   const int mode = h->opt.precond;
-  const int deg = h->opt.cheb_degree;
   const bool tri = mode == SD_TRI_SCHUR;
   const double schur = tri ? h->mu / (h->opt.schur_gamma * h->g.h * h->g.h) : 1.0;
+  if (tri && h->opt.darcy_coupled == 2) {
+    // Darcy first (block lower-triangular in the order p_pm, p_ff -> v): the
+    // Darcy and pressure-Laplacian cycles depend only on r and run
+    // concurrently on two streams; the velocity cycle then sees B z_pff and
+    // B'_1 z_pm
+    cudaEventRecord(h->ev_fork, s);
+    cudaStreamWaitEvent(h->s2, h->ev_fork, 0);
+    launch_convert<T>(r + h->g.opm, M.L[0].D.b, h->g.lenD, h->s2);
+    vcycle_cell<T>(M, 0, false, h->s2, h);
+    launch_precond_exit<T>(c, z, M.L[0].D.res, h->s2);
+    cudaEventRecord(h->ev_join, h->s2);
+    const T* eP = nullptr;
+    if (h->opt.schur_mass) {
+      launch_convert<T>(r + h->g.opf, M.L[0].Pb.b, h->g.lenD, s);
+      vcycle_cell<T>(M, 0, true, s, h);
+      eP = M.L[0].Pb.res;
+    }
+    cudaStreamWaitEvent(s, h->ev_join, 0);
+    launch_precond_entry<T>(c, r, z, schur, eP, 1.0 / h->dt, 1, 1, M.L[0].V.b, s);
+    vcycle_V<T>(M, 0, s, h);
+    launch_precond_mid<T>(c, r, z, M.L[0].V.res, 0, (T*)nullptr, s);
+    return;
+  }
   // block-diagonal Darcy part (no C'_1 coupling): its V-cycle runs on the
   // second stream, overlapping the pressure and velocity cycles
-  const bool overlap = tri && !h->opt.darcy_coupled;
+  const bool overlap = tri && h->opt.darcy_coupled == 0;
   if (overlap) {
     cudaEventRecord(h->ev_fork, s);
     cudaStreamWaitEvent(h->s2, h->ev_fork, 0);
     launch_convert<T>(r + h->g.opm, M.L[0].D.b, h->g.lenD, h->s2);
-    vcycle_cell<T>(M, 0, deg, false, h->s2);
+    vcycle_cell<T>(M, 0, false, h->s2, h);
     launch_precond_exit<T>(c, z, M.L[0].D.res, h->s2);
     cudaEventRecord(h->ev_join, h->s2);
   }
   const T* eP = nullptr;
   if (tri && h->opt.schur_mass) {
     launch_convert<T>(r + h->g.opf, M.L[0].Pb.b, h->g.lenD, s);
-    vcycle_cell<T>(M, 0, deg, true, s);
+    vcycle_cell<T>(M, 0, true, s, h);
     eP = M.L[0].Pb.res;
   }
-  launch_precond_entry<T>(c, r, z, schur, eP, 1.0 / h->dt, tri, M.L[0].V.b, s);
-  vcycle_V<T>(M, 0, deg, s, h);
+  launch_precond_entry<T>(c, r, z, schur, eP, 1.0 / h->dt, tri, 0, M.L[0].V.b, s);
+  vcycle_V<T>(M, 0, s, h);
   if (mode == SD_PV_BGS_I) launch_precond_bgs_pff<T>(c, r, z, M.L[0].V.res, s);
   if (overlap) {
     launch_precond_mid<T>(c, r, z, M.L[0].V.res, 0, (T*)nullptr, s);
@@ -589,7 +675,7 @@ void precond(sd_handle* h, MG<T>& M, const double* r, double* z) {
     return;
   }
   launch_precond_mid<T>(c, r, z, M.L[0].V.res, mode != SD_PV_BJ_I, M.L[0].D.b, s);
-  vcycle_cell<T>(M, 0, deg, false, s);
+  vcycle_cell<T>(M, 0, false, s, h);
   launch_precond_exit<T>(c, z, M.L[0].D.res, s);
 }
 
@@ -759,6 +845,9 @@ int validate(const sd_grid* grid, double mu, double alpha, double dt, const sd_o
   if (o->cheb_degree < 1 || o->cheb_degree > 8 || o->coarsest < 2 || !(o->schur_gamma > 0) || !(o->cheb_ratio > 1))
     return SD_E_INVAL;
   if (o->orth < 0 || o->orth > 1 || !(o->reorth_eta > 0) || o->reorth_eta > 1) return SD_E_INVAL;
+  if (o->darcy_coupled < 0 || o->darcy_coupled > 2) return SD_E_INVAL;
+  if (o->cheb_degree_coarse < 0 || o->cheb_degree_coarse > 8 || o->schur_degree < 0 || o->schur_degree > 8)
+    return SD_E_INVAL;
   int n = grid->nx, L = level_count(n, o->coarsest);
   for (int l = 1; l < L; ++l) n /= 2;
   if (n > 16) return SD_E_INVAL;  // coarsest grid must stay small for the dense solve
@@ -871,12 +960,16 @@ void sd_options_default(sd_options* o) {
   o->precond = SD_TRI_SCHUR;
   o->bc = SD_BC_MMS;
   o->cheb_degree = 3;
+  o->cheb_degree_coarse = 0;
+  o->schur_degree = 1;
   o->coarsest = 4;
   o->fuse_coarse = 1;
   o->orth = 0;
   o->reorth_eta = 0.70710678118654752;
   o->extrapolate = 1;
   o->graph = 1;
+  o->pdl = 1;
+  o->tile = 1;
   o->darcy_coupled = 1;
   o->schur_gamma = 0.5;
   o->cheb_ratio = 8.0;
@@ -909,6 +1002,7 @@ int sd_create(const sd_grid* grid, double mu, const double* K, double alpha_bj, 
 int sd_step(sd_handle* h, int32_t nsteps, sd_step_info* info) {
   if (!h || nsteps < 0) return SD_E_INVAL;
   std::lock_guard<std::mutex> lk(h->mtx);
+  t_pdl = h->opt.pdl;
   int first = SD_OK;
   const double cm = h->g.h * h->g.h / h->dt;
   for (int k = 0; k < nsteps; ++k) {
@@ -1025,6 +1119,7 @@ int sd_rhs(sd_handle* h, const double* xprev, double t, double* bout) {
 int sd_solve(sd_handle* h, const double* b, double* x, sd_step_info* info) {
   if (!h || !b || !x) return SD_E_INVAL;
   std::lock_guard<std::mutex> lk(h->mtx);
+  t_pdl = h->opt.pdl;
   const long long nd = sd_dof_count(h->n);
   // b and the iterate use the handle's b and a separate padded copy of x
   CKR(copy_in_dense(h, b, nd));
@@ -1110,6 +1205,17 @@ int sd_profile_read(sd_handle* h, double* total_ms, int64_t* launches, double* b
 }
 
 int64_t sd_launch_count(void) { return (int64_t)sdk::g_launch_count.load(); }
+
+int64_t sd_struct_size(int32_t which) {
+  switch (which) {
+    case 0: return (int64_t)sizeof(sd_grid);
+    case 1: return (int64_t)sizeof(sd_options);
+    case 2: return (int64_t)sizeof(sd_step_info);
+    case 3: return (int64_t)sizeof(sd_request);
+    case 4: return (int64_t)sizeof(sd_result);
+    default: return -1;
+  }
+}
 
 const char* sd_strerror(int code) {
   switch (code) {

@@ -20,6 +20,31 @@
 
 namespace sdk {
 
+// Programmatic dependent launch: when enabled for the calling host thread,
+// kernels are launched with programmatic stream serialisation, so a grid's
+// launch overlaps the drain of the previous grid.  Every kernel of this
+// library starts with griddep_wait(), which returns once the previous grid
+// has completed and its memory operations are visible, before the kernel
+// touches global memory.  (An explicit early trigger for the next grid was
+// measured and gave no gain.)
+extern thread_local int t_pdl;
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*kern)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = g;
+  cfg.blockDim = b;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = t_pdl ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // process-wide count of kernel launches made by this library (and the same
 // count per host thread, used to size captured graphs)
 extern std::atomic<long long> g_launch_count;
@@ -67,7 +92,16 @@ struct Coef {
   const T* rg;
   const T* Tx;
   const T* Ty;
+  T d6, m1, m2;  // derived: cm + 6 mu (interior velocity diagonal), -mu, -2 mu
 };
+
+// fill the derived constants of a Coef from cm and mu
+template <typename T>
+inline void finish_coef(Coef<T>& c) {
+  c.d6 = c.cm + T(6) * c.mu;
+  c.m1 = -c.mu;
+  c.m2 = T(-2) * c.mu;
+}
 
 // ---------------------------------------------------------------- sd_ops.cu
 // setup
@@ -133,7 +167,8 @@ void launch_prolong_D(int nf, int Pf, T* x, int nc, int Pc, const T* e, cudaStre
 #define SD_CYC_MAXL 6
 template <typename T>
 struct CoarseCycle {
-  int nlev, kind, deg, m;
+  int nlev, kind, m;
+  int deg[SD_CYC_MAXL];  // Chebyshev steps per smoothing on each level
   Coef<T> c[SD_CYC_MAXL];
   T cha[SD_CYC_MAXL][8], chc[SD_CYC_MAXL][8];
   const double* Ainv;
@@ -150,12 +185,29 @@ int launch_coarse_cycle(const CoarseCycle<T>& q, cudaStream_t s);
 template <typename T>
 int prepare_coarse_cycle();
 
+// Chebyshev step coefficients of one smoothing (ns <= 8 steps)
+template <typename T>
+struct ChebSteps {
+  int ns;
+  T a[8], c[8];
+};
+// Tiled smoothing: ns Chebyshev steps in one kernel, x_out = S(x_in + P ec)
+// (x_in null: from zero; ec null: no prolongation).  FP32 only; returns -1
+// (nothing launched) for ns > 4.
+template <typename T>
+int launch_smooth_tile_D(const Coef<T>& c, const T* x_in, const T* b, T* x_out, const ChebSteps<T>& cs, const T* ec,
+                         int nc, int Pc, cudaStream_t s);
+template <typename T>
+int launch_smooth_tile_V(const Coef<T>& c, const T* x_in, const T* b, T* x_out, const ChebSteps<T>& cs, const T* ec,
+                         int nc, int Pc, cudaStream_t s);
+
 // preconditioner glue on the fine level (Sec. 4 block preconditioners):
 //  entry: zpf = schur * r_pf + cmass * eP (eP: pressure-Laplacian solve, may be
-//  null); rV = T(r_v - B zpf) (B omitted: use_B == 0)
+//  null); rV = T(r_v - B zpf - B'_1 z_pm) (B omitted: use_B == 0; B'_1 only with
+//  use_B1, reading the z_pm already in z)
 template <typename T>
 void launch_precond_entry(const Coef<double>& c, const double* r, double* z, double schur, const T* eP, double cmass,
-                          int use_B, T* rV, cudaStream_t s);
+                          int use_B, int use_B1, T* rV, cudaStream_t s);
 //  mid: z_v = double(eV); rD = T(r_pm - C'_1 z_v) (C'_1 omitted: use_C == 0; rD null: not written)
 template <typename T>
 void launch_precond_mid(const Coef<double>& c, const double* r, double* z, const T* eV, int use_C, T* rD,

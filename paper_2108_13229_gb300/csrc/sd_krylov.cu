@@ -19,6 +19,7 @@ namespace sdk {
 
 std::atomic<long long> g_launch_count{0};
 thread_local long long t_launch_count = 0;
+thread_local int t_pdl = 0;
 
 static const int RT = 256;       // threads per reduction / update block
 static const int KT = 128;       // threads per Gram-Schmidt block
@@ -76,6 +77,7 @@ __device__ __forceinline__ void load_own(const double* __restrict__ w, double* w
 __global__ void __launch_bounds__(KT) k_mdot(const double* __restrict__ V, long long vs, int k,
                                              const double* __restrict__ w, long long len, double* __restrict__ partial,
                                              int ps, int self, const double* __restrict__ cond) {
+  griddep_wait();
   if (cond && cond[0] == 0.0) return;
   __shared__ double red[KMAX_REG][KT];
   const long long base = (long long)blockIdx.x * KT * KE + threadIdx.x;
@@ -104,7 +106,7 @@ __global__ void __launch_bounds__(KT) k_mdot(const double* __restrict__ V, long 
 void launch_mdot(const double* V, long long vstride, int k, const double* w, long long len, double* partial, int ps,
                  int nblk, int self, const double* cond, cudaStream_t s) {
   SD_COUNT(1);
-  k_mdot<<<nblk, KT, 0, s>>>(V, vstride, k, w, len, partial, ps, self, cond);
+  launch_k(k_mdot, dim3(nblk), dim3(KT), 0, s, V, vstride, k, w, len, partial, ps, self, cond);
 }
 
 // w -= sum_q coef_q V_q, then
@@ -114,6 +116,7 @@ __global__ void __launch_bounds__(KT) k_mupdate(const double* __restrict__ V, lo
                                                 const double* __restrict__ coef, double* __restrict__ w,
                                                 long long len, double* __restrict__ partial, int ps, int mode,
                                                 const double* __restrict__ cond) {
+  griddep_wait();
   if (cond && cond[0] == 0.0) return;
   __shared__ double cf[KMAX_REG];
   __shared__ double red[KMAX_REG][KT];
@@ -172,12 +175,13 @@ __global__ void __launch_bounds__(KT) k_mupdate(const double* __restrict__ V, lo
 void launch_mupdate(const double* V, long long vstride, int k, const double* coef, double* w, long long len,
                     double* partial, int ps, int nblk, int mode, const double* cond, cudaStream_t s) {
   SD_COUNT(1);
-  k_mupdate<<<nblk, KT, 0, s>>>(V, vstride, k, coef, w, len, partial, ps, mode, cond);
+  launch_k(k_mupdate, dim3(nblk), dim3(KT), 0, s, V, vstride, k, coef, w, len, partial, ps, mode, cond);
 }
 
 // out[q] = sum_b partial[q * ps + b] (+ out[q] if accumulate), fixed-order tree
 __global__ void k_reduce(const double* __restrict__ partial, int nblk, int k, int ps, double* __restrict__ out,
                          int accumulate, const double* __restrict__ cond) {
+  griddep_wait();
   __shared__ double sm[RT / 32];
   const int q = blockIdx.x;
   if (q >= k) return;
@@ -203,31 +207,33 @@ __global__ void k_reduce(const double* __restrict__ partial, int nblk, int k, in
 void launch_reduce(const double* partial, int nblk, int k, int ps, double* out, int accumulate, const double* cond,
                    cudaStream_t s) {
   SD_COUNT(1);
-  k_reduce<<<k, RT, 0, s>>>(partial, nblk, k, ps, out, accumulate, cond);
+  launch_k(k_reduce, dim3(k), dim3(RT), 0, s, partial, nblk, k, ps, out, accumulate, cond);
 }
 
 // Selective re-orthogonalisation (Daniel-Gragg-Kaufman-Stewart test): a second
 // Gram-Schmidt pass is needed when the projection removed most of w,
 // ||w'||^2 < eta^2 ||w||^2.  flag[0] = 1 (pass needed) or 0.
 __global__ void k_reorth_decide(const double* nw2, const double* n2a, double eta2, double* flag) {
+  griddep_wait();
   if (threadIdx.x == 0) flag[0] = (n2a[0] < eta2 * nw2[0]) ? 1.0 : 0.0;
 }
 
 void launch_reorth_decide(const double* nw2, const double* n2a, double eta2, double* flag, cudaStream_t s) {
   SD_COUNT(1);
-  k_reorth_decide<<<1, 32, 0, s>>>(nw2, n2a, eta2, flag);
+  launch_k(k_reorth_decide, dim3(1), dim3(32), 0, s, nw2, n2a, eta2, flag);
 }
 
 void launch_dot(const double* a, const double* b, long long len, double* partial, int nblk, double* out,
                 cudaStream_t s) {
   SD_COUNT(2);
-  k_mdot<<<nblk, KT, 0, s>>>(a, 0, 1, b, len, partial, nblk, 0, nullptr);
-  k_reduce<<<1, RT, 0, s>>>(partial, nblk, 1, nblk, out, 0, nullptr);
+  launch_k(k_mdot, dim3(nblk), dim3(KT), 0, s, a, 0, 1, b, len, partial, nblk, 0, nullptr);
+  launch_k(k_reduce, dim3(1), dim3(RT), 0, s, partial, nblk, 1, nblk, out, 0, nullptr);
 }
 
 // mode 0: y = sdev[0] * x ; mode 1: y = x / sqrt(sdev[0])
 __global__ void k_scale_by(const double* __restrict__ x, double* __restrict__ y, long long len,
                            const double* __restrict__ sdev, int mode) {
+  griddep_wait();
   const double f = mode == 0 ? sdev[0] : 1.0 / sqrt(sdev[0]);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len; e += (long long)gridDim.x * blockDim.x)
     y[e] = f * x[e];
@@ -236,12 +242,13 @@ __global__ void k_scale_by(const double* __restrict__ x, double* __restrict__ y,
 void launch_scale_by(const double* x, double* y, long long len, const double* sdev, int mode, cudaStream_t s) {
   SD_COUNT(1);
   const long long nb = (len + RT - 1) / RT;
-  k_scale_by<<<(int)(nb < 152 * 16 ? nb : 152 * 16), RT, 0, s>>>(x, y, len, sdev, mode);
+  launch_k(k_scale_by, dim3((int)(nb < 152 * 16 ? nb : 152 * 16)), dim3(RT), 0, s, x, y, len, sdev, mode);
 }
 
 // x += sum_q y_q Z_q
 __global__ void __launch_bounds__(KT) k_axpy_multi(double* __restrict__ x, const double* __restrict__ Z, long long zs,
                                                    const double* __restrict__ y, int k, long long len) {
+  griddep_wait();
   __shared__ double cf[KMAX_REG];
   if (threadIdx.x < KMAX_REG) cf[threadIdx.x] = threadIdx.x < k ? y[threadIdx.x] : 0.0;
   __syncthreads();
@@ -278,7 +285,7 @@ __global__ void __launch_bounds__(KT) k_axpy_multi(double* __restrict__ x, const
 void launch_axpy_multi(double* x, const double* Z, long long zstride, const double* ycoef, int k, long long len,
                        cudaStream_t s) {
   SD_COUNT(1);
-  k_axpy_multi<<<reduce_blocks(len), KT, 0, s>>>(x, Z, zstride, ycoef, k, len);
+  launch_k(k_axpy_multi, dim3(reduce_blocks(len)), dim3(KT), 0, s, x, Z, zstride, ycoef, k, len);
 }
 
 // ----------------------------------------------------- Hessenberg / Givens
@@ -287,6 +294,7 @@ void launch_axpy_multi(double* x, const double* Z, long long zstride, const doub
 // flag[1] = 1 / h_{j+1,j} (scale of the next basis vector), flag[2] = 1 on
 // NaN/Inf, flag[3] = 1 on breakdown (h_{j+1,j} == 0).
 __global__ void k_init_cycle(double* st, int m, const double* beta2, double* flag) {
+  griddep_wait();
   if (threadIdx.x != 0) return;
   double* g = st + (m + 1) * m + 2 * m;
   const double beta = sqrt(beta2[0]);
@@ -300,11 +308,12 @@ __global__ void k_init_cycle(double* st, int m, const double* beta2, double* fla
 
 void launch_init_cycle(double* st, int m, const double* beta2, double* flag, cudaStream_t s) {
   SD_COUNT(1);
-  k_init_cycle<<<1, 32, 0, s>>>(st, m, beta2, flag);
+  launch_k(k_init_cycle, dim3(1), dim3(32), 0, s, st, m, beta2, flag);
 }
 
 __global__ void k_givens(double* st, int j, int m, const double* h1, const double* h2, const double* nrm2a,
                          const double* nrm2b, const double* reo, double* flag) {
+  griddep_wait();
   if (threadIdx.x != 0) return;
   const bool second = reo == nullptr || reo[0] != 0.0;
   const double* nrm2 = second ? nrm2b : nrm2a;
@@ -341,11 +350,12 @@ __global__ void k_givens(double* st, int j, int m, const double* h1, const doubl
 void launch_givens(double* st, int j, int m, const double* hcol1, const double* hcol2, const double* nrm2a,
                    const double* nrm2b, const double* reo, double* flag, cudaStream_t s) {
   SD_COUNT(1);
-  k_givens<<<1, 32, 0, s>>>(st, j, m, hcol1, hcol2, nrm2a, nrm2b, reo, flag);
+  launch_k(k_givens, dim3(1), dim3(32), 0, s, st, j, m, hcol1, hcol2, nrm2a, nrm2b, reo, flag);
 }
 
 // x_m <- x, x <- 2 x - x_m (linear extrapolation in time of the initial guess)
 __global__ void k_extrapolate(double* __restrict__ x, double* __restrict__ xm, long long len) {
+  griddep_wait();
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len; e += (long long)gridDim.x * blockDim.x) {
     const double t = x[e];
     x[e] = 2.0 * t - xm[e];
@@ -356,10 +366,11 @@ __global__ void k_extrapolate(double* __restrict__ x, double* __restrict__ xm, l
 void launch_extrapolate(double* x, double* xm, long long len, cudaStream_t s) {
   SD_COUNT(1);
   const long long nb = (len + RT - 1) / RT;
-  k_extrapolate<<<(int)(nb < 152 * 16 ? nb : 152 * 16), RT, 0, s>>>(x, xm, len);
+  launch_k(k_extrapolate, dim3((int)(nb < 152 * 16 ? nb : 152 * 16)), dim3(RT), 0, s, x, xm, len);
 }
 
 __global__ void k_backsolve(const double* st, int k, int m, double* y) {
+  griddep_wait();
   if (threadIdx.x != 0) return;
   const double* R = st;
   const double* g = st + (m + 1) * m + 2 * m;
@@ -371,12 +382,13 @@ __global__ void k_backsolve(const double* st, int k, int m, double* y) {
 }
 
 void launch_backsolve(double* st, int k, int m, double* y, cudaStream_t s) {
-  SD_COUNT(1); k_backsolve<<<1, 32, 0, s>>>(st, k, m, y); }
+  SD_COUNT(1); launch_k(k_backsolve, dim3(1), dim3(32), 0, s, st, k, m, y); }
 
 // ------------------------------------------------------ dense coarse solve
 template <typename T>
 __global__ void k_dense_solve(const double* __restrict__ Ainv, const int* __restrict__ idx, int m,
                               const T* __restrict__ b, T* __restrict__ x) {
+  griddep_wait();
   extern __shared__ double bs[];
   for (int l = threadIdx.x; l < m; l += blockDim.x) bs[l] = (double)b[idx[l]];
   __syncthreads();
@@ -394,11 +406,12 @@ __global__ void k_dense_solve(const double* __restrict__ Ainv, const int* __rest
 template <typename T>
 void launch_dense_solve(const double* Ainv, const int* idx, int m, const T* b, T* x, cudaStream_t s) {
   SD_COUNT(1);
-  k_dense_solve<T><<<1, 512, sizeof(double) * m, s>>>(Ainv, idx, m, b, x);
+  launch_k(k_dense_solve<T>, dim3(1), dim3(512), sizeof(double) * m, s, Ainv, idx, m, b, x);
 }
 
 // Gauss-Jordan with partial pivoting on [A | I], one CTA; the inverse ends in W.
 __global__ void k_gj_inverse(double* A, double* W, int m, int* status) {
+  griddep_wait();
   extern __shared__ double fcol[];
   __shared__ int piv;
   __shared__ double pval;
@@ -450,20 +463,22 @@ __global__ void k_gj_inverse(double* A, double* W, int m, int* status) {
 
 void launch_gj_inverse(double* A, double* work, int m, int* status, cudaStream_t s) {
   SD_COUNT(1);
-  k_gj_inverse<<<1, 1024, sizeof(double) * m, s>>>(A, work, m, status);
+  launch_k(k_gj_inverse, dim3(1), dim3(1024), sizeof(double) * m, s, A, work, m, status);
 }
 
 __global__ void k_identity_batch(double* X, long long stride, const int* idx, int m) {
+  griddep_wait();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < m) X[(long long)k * stride + idx[k]] = 1.0;
 }
 void launch_identity_batch(double* X, long long stride, const int* idx, int m, cudaStream_t s) {
   SD_COUNT(1);
-  k_identity_batch<<<(m + 127) / 128, 128, 0, s>>>(X, stride, idx, m);
+  launch_k(k_identity_batch, dim3((m + 127) / 128), dim3(128), 0, s, X, stride, idx, m);
 }
 
 // A[r][k] = Y[k * stride + idx[r]]  (column k = operator applied to unit vector k)
 __global__ void k_gather_dense(const double* Y, long long stride, const int* idx, int m, double* A) {
+  griddep_wait();
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= (long long)m * m) return;
   const int r = (int)(e / m), k = (int)(e % m);
@@ -472,18 +487,20 @@ __global__ void k_gather_dense(const double* Y, long long stride, const int* idx
 void launch_gather_dense(const double* Y, long long stride, const int* idx, int m, double* A, cudaStream_t s) {
   SD_COUNT(1);
   const long long tot = (long long)m * m;
-  k_gather_dense<<<(int)((tot + 255) / 256), 256, 0, s>>>(Y, stride, idx, m, A);
+  launch_k(k_gather_dense, dim3((int)((tot + 255) / 256)), dim3(256), 0, s, Y, stride, idx, m, A);
 }
 
 __global__ void k_fill(double* x, double v, long long len) {
+  griddep_wait();
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len; e += (long long)gridDim.x * blockDim.x)
     x[e] = v;
 }
 void launch_fill(double* x, double v, long long len, cudaStream_t s) {
-  SD_COUNT(1); k_fill<<<reduce_blocks(len), RT, 0, s>>>(x, v, len); }
+  SD_COUNT(1); launch_k(k_fill, dim3(reduce_blocks(len)), dim3(RT), 0, s, x, v, len); }
 
 // deterministic pseudo-random fill in [-1, 1] (start vector of the power iteration)
 __global__ void k_hash_fill(double* x, long long len, unsigned seed) {
+  griddep_wait();
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len; e += (long long)gridDim.x * blockDim.x) {
     unsigned long long z = (unsigned long long)e * 0x9E3779B97F4A7C15ull + seed;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -494,7 +511,7 @@ __global__ void k_hash_fill(double* x, long long len, unsigned seed) {
 }
 void launch_hash_fill(double* x, long long len, unsigned seed, cudaStream_t s) {
   SD_COUNT(1);
-  k_hash_fill<<<reduce_blocks(len), RT, 0, s>>>(x, len, seed);
+  launch_k(k_hash_fill, dim3(reduce_blocks(len)), dim3(RT), 0, s, x, len, seed);
 }
 
 template void launch_dense_solve<float>(const double*, const int*, int, const float*, float*, cudaStream_t);

@@ -99,6 +99,7 @@ extern "C" int sd_apply_noalloc(const sd_grid* grid, double mu, const double* K,
   c.rg = base + org;
   c.Tx = base + oTx;
   c.Ty = base + oTy;
+  finish_coef(c);
   launch_apply_full(c, base + ox, nullptr, base + oy, s);
   launch_unpack(g, base + oy, y, s);
   return cudaGetLastError() == cudaSuccess ? SD_OK : SD_E_CUDA;

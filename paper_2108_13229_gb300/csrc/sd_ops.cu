@@ -48,12 +48,15 @@ template <typename T>
 __device__ __forceinline__ void u_row(const Coef<T>& c, const T* __restrict__ u, const T* __restrict__ v, int i,
                                       int j, bool read, T& off, T& diag) {
   const int n = c.n, P = c.P;
-  const T mu = c.mu, h = c.h;
+  const T mu = c.mu;
   const bool top = j == n - 1, bot = j == 0;
-  const T wh = bot ? c.w[i] * h : T(0);
-  T dg = c.cm + T(4) * mu;
-  dg += top ? T(2) * mu : mu;
-  dg += bot ? T(2) * wh : mu;
+  T dg = c.d6;  // interior: h^2/dt + 4 mu (normal stress) + mu + mu (shear)
+  T wh = T(0);
+  if (top) dg += mu;  // wall at half distance above: 2 mu instead of mu
+  if (bot) {          // Gamma below: BJS shear instead of mu
+    wh = c.w[i] * c.h;
+    dg += T(2) * wh - mu;
+  }
   diag = dg;
   if (!read) {
     off = T(0);
@@ -63,11 +66,21 @@ __device__ __forceinline__ void u_row(const Coef<T>& c, const T* __restrict__ u,
   const long long rv1 = (long long)(j + 1) * P;
   const T uW = u[r0 + i - 1], uE = u[r0 + i + 1], uN = u[rN + i], uS = u[rS + i];
   const T vN = v[rv1 + i], vNW = v[rv1 + i - 1], vS = v[r0 + i], vSW = v[r0 + i - 1];
-  T of = T(0);
-  of -= (i - 1 >= 1) ? T(2) * mu * uW : T(0);
-  of -= (i + 1 <= n - 1) ? T(2) * mu * uE : T(0);
-  of += top ? T(0) : (-mu * uN - mu * vN + mu * vNW);
-  of += bot ? wh * (vS - vSW) : (-mu * uS + mu * vS - mu * vSW);
+  const T cW = (i - 1 >= 1) ? c.m2 : T(0), cE = (i + 1 <= n - 1) ? c.m2 : T(0);
+  T of = cW * uW;
+  of = fma(cE, uE, of);
+  if (!top) {
+    of = fma(c.m1, uN, of);
+    of = fma(c.m1, vN, of);
+    of = fma(mu, vNW, of);
+  }
+  if (!bot) {
+    of = fma(c.m1, uS, of);
+    of = fma(mu, vS, of);
+    of = fma(c.m1, vSW, of);
+  } else {
+    of = fma(wh, vS - vSW, of);
+  }
   off = of;
 }
 
@@ -90,15 +103,21 @@ __device__ __forceinline__ void v_row(const Coef<T>& c, const T* __restrict__ u,
     }
     const T v1 = v[P + i], uL = u[i], uR = u[i + 1];
     const T vL = v[left ? i : i - 1], vR = v[right ? i : i + 1];
-    T of = -(T(2) * mu * v1);
-    of += left ? T(0) : (wl * h * uL - T(0.5) * h * wl * vL);
-    of += right ? T(0) : (-wr * h * uR - T(0.5) * h * wr * vR);
+    T of = c.m2 * v1;
+    if (!left) {
+      of = fma(wl * h, uL, of);
+      of = fma(T(-0.5) * h * wl, vL, of);
+    }
+    if (!right) {
+      of = fma(-wr * h, uR, of);
+      of = fma(T(-0.5) * h * wr, vR, of);
+    }
     off = of;
     return;
   }
-  T dg = c.cm + T(4) * mu;
-  dg += right ? T(2) * mu : mu;
-  dg += left ? T(2) * mu : mu;
+  T dg = c.d6;
+  if (right) dg += mu;
+  if (left) dg += mu;
   diag = dg;
   if (!read) {
     off = T(0);
@@ -108,10 +127,19 @@ __device__ __forceinline__ void v_row(const Coef<T>& c, const T* __restrict__ u,
   const int iE = right ? i : i + 1, iW = left ? i : i - 1;
   const T vS = v[rm + i], vN = v[rp + i], vE = v[r0 + iE], vW = v[r0 + iW];
   const T uE = u[r0 + i + 1], uES = u[rm + i + 1], uW = u[r0 + i], uWS = u[rm + i];
-  T of = -(T(2) * mu * vS);
-  of -= (j + 1 <= n - 1) ? T(2) * mu * vN : T(0);
-  of += right ? T(0) : (-mu * vE - mu * uE + mu * uES);
-  of += left ? T(0) : (-mu * vW + mu * uW - mu * uWS);
+  const T cN = (j + 1 <= n - 1) ? c.m2 : T(0);
+  T of = c.m2 * vS;
+  of = fma(cN, vN, of);
+  if (!right) {
+    of = fma(c.m1, vE, of);
+    of = fma(c.m1, uE, of);
+    of = fma(mu, uES, of);
+  }
+  if (!left) {
+    of = fma(c.m1, vW, of);
+    of = fma(mu, uW, of);
+    of = fma(c.m1, uWS, of);
+  }
   off = of;
 }
 
@@ -123,25 +151,27 @@ __device__ __forceinline__ void d_row(const Coef<T>& c, const T* __restrict__ p,
   const long long r0 = (long long)j * P;
   const T tw = c.Tx[r0 + i], te = c.Tx[r0 + i + 1];
   const T ts = c.Ty[r0 + i], tn = c.Ty[r0 + P + i];
-  diag = tw + te + ts + tn;
+  diag = (tw + te) + (ts + tn);
   if (!read) {
     off = T(0);
     return;
   }
   const T pW = p[r0 + (i > 0 ? i - 1 : i)], pE = p[r0 + (i < n - 1 ? i + 1 : i)];
   const T pS = p[(j > 0 ? r0 - P : r0) + i], pN = p[(j < n - 1 ? r0 + P : r0) + i];
-  T of = T(0);
-  of -= i > 0 ? tw * pW : T(0);
-  of -= i < n - 1 ? te * pE : T(0);
-  of -= j > 0 ? ts * pS : T(0);
-  of -= j < n - 1 ? tn * pN : T(0);
-  off = of;
+  const T cW = i > 0 ? tw : T(0), cE = i < n - 1 ? te : T(0);
+  const T cS = j > 0 ? ts : T(0), cN = j < n - 1 ? tn : T(0);
+  T of = cW * pW;
+  of = fma(cE, pE, of);
+  of = fma(cS, pS, of);
+  of = fma(cN, pN, of);
+  off = -of;
 }
 
 // ------------------------------------------------------- whole operator (K1)
 template <int R>
 __global__ void k_apply_full(Coef<double> c, const double* __restrict__ x, const double* __restrict__ b,
                              double* __restrict__ y) {
+  griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
   const int n = c.n, P = c.P;
@@ -203,55 +233,63 @@ __global__ void k_apply_full(Coef<double> c, const double* __restrict__ x, const
 void launch_apply_full(const Coef<double>& c, const double* x, const double* b, double* y, cudaStream_t s) {
   SD_COUNT(1);
   const int R = rows_apply(c.n);
-  if (R == 4) k_apply_full<4><<<grid2R(c.n + 1, c.n + 1, 4), dim3(BX, BY), 0, s>>>(c, x, b, y);
-  else k_apply_full<1><<<grid2R(c.n + 1, c.n + 1, 1), dim3(BX, BY), 0, s>>>(c, x, b, y);
+  if (R == 4) launch_k(k_apply_full<4>, dim3(grid2R(c.n + 1, c.n + 1, 4)), dim3(dim3(BX, BY)), 0, s, c, x, b, y);
+  else launch_k(k_apply_full<1>, dim3(grid2R(c.n + 1, c.n + 1, 1)), dim3(dim3(BX, BY)), 0, s, c, x, b, y);
 }
 
 // ------------------------------------------------------ block V smoothers
 // One Chebyshev step at position (i, j) of the velocity block (u face (i,j)
 // if j < n, v face (i,j) if i < n).  Dirichlet faces take x = b exactly.
 template <typename T>
-__device__ __forceinline__ void cheb_V_at(const Coef<T>& c, const T* __restrict__ xin, const T* __restrict__ b,
-                                          T* __restrict__ d, T* __restrict__ xout, T a, T cc, int i, int j) {
+__device__ __forceinline__ void cheb_V_at2(const Coef<T>& c, const T* __restrict__ uin, const T* __restrict__ vin,
+                                           const T* __restrict__ bu, const T* __restrict__ bv, T* __restrict__ du,
+                                           T* __restrict__ dv, T* __restrict__ uout, T* __restrict__ vout, T a, T cc,
+                                           int i, int j) {
   const int n = c.n, P = c.P;
-  const T* u = xin;
-  const T* v = xin ? xin + (long long)n * P : nullptr;
-  const bool rd = xin != nullptr;
+  const bool rd = uin != nullptr;
   if (j < n) {
     const long long k = (long long)j * P + i;
     if (i == 0 || i == n) {
-      xout[k] = b[k];
-      d[k] = T(0);
+      uout[k] = bu[k];
+      du[k] = T(0);
     } else {
       T off, dg;
-      u_row(c, u, v, i, j, rd, off, dg);
-      const T xc = rd ? xin[k] : T(0);
-      const T r = b[k] - (dg * xc + off);
-      const T dn = (a != T(0) ? a * d[k] : T(0)) + cc * r / dg;
-      d[k] = dn;
-      xout[k] = xc + dn;
+      u_row(c, uin, vin, i, j, rd, off, dg);
+      const T xc = rd ? uin[k] : T(0);
+      const T r = bu[k] - (dg * xc + off);
+      const T dn = (a != T(0) ? a * du[k] : T(0)) + cc * r / dg;
+      du[k] = dn;
+      uout[k] = xc + dn;
     }
   }
   if (i < n) {
-    const long long k = (long long)n * P + (long long)j * P + i;
+    const long long k = (long long)j * P + i;
     if (j == n) {
-      xout[k] = b[k];
-      d[k] = T(0);
+      vout[k] = bv[k];
+      dv[k] = T(0);
     } else {
       T off, dg;
-      v_row(c, u, v, i, j, rd, off, dg);
-      const T xc = rd ? xin[k] : T(0);
-      const T r = b[k] - (dg * xc + off);
-      const T dn = (a != T(0) ? a * d[k] : T(0)) + cc * r / dg;
-      d[k] = dn;
-      xout[k] = xc + dn;
+      v_row(c, uin, vin, i, j, rd, off, dg);
+      const T xc = rd ? vin[k] : T(0);
+      const T r = bv[k] - (dg * xc + off);
+      const T dn = (a != T(0) ? a * dv[k] : T(0)) + cc * r / dg;
+      dv[k] = dn;
+      vout[k] = xc + dn;
     }
   }
+}
+
+template <typename T>
+__device__ __forceinline__ void cheb_V_at(const Coef<T>& c, const T* __restrict__ xin, const T* __restrict__ b,
+                                          T* __restrict__ d, T* __restrict__ xout, T a, T cc, int i, int j) {
+  const long long nv = (long long)c.n * c.P;
+  cheb_V_at2(c, xin, xin ? xin + nv : nullptr, b, b + nv, d, d + nv, xout, xout + nv, a, cc, i, j);
 }
 
 template <typename T, int R>
 __global__ void k_cheb_V(Coef<T> c, const T* __restrict__ xin, const T* __restrict__ b, T* __restrict__ d,
                          T* __restrict__ xout, T a, T cc, long long bstride) {
+  griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
   if (i > c.n) return;
@@ -271,8 +309,8 @@ void launch_cheb_V(const Coef<T>& c, const T* x_in, const T* b, T* d, T* x_out, 
   const int R = rows_vel(c.n);
   dim3 g = grid2R(c.n + 1, c.n + 1, R);
   g.z = nbatch;
-  if (R == 4) k_cheb_V<T, 4><<<g, dim3(BX, BY), 0, s>>>(c, x_in, b, d, x_out, a, cc, bstride);
-  else k_cheb_V<T, 1><<<g, dim3(BX, BY), 0, s>>>(c, x_in, b, d, x_out, a, cc, bstride);
+  if (R == 4) launch_k(k_cheb_V<T, 4>, dim3(g), dim3(dim3(BX, BY)), 0, s, c, x_in, b, d, x_out, a, cc, bstride);
+  else launch_k(k_cheb_V<T, 1>, dim3(g), dim3(dim3(BX, BY)), 0, s, c, x_in, b, d, x_out, a, cc, bstride);
 }
 
 // r = b - V x (mode 0; b == nullptr: -V x), D^-1 V x (mode 1), V x (mode 2)
@@ -311,6 +349,7 @@ __device__ __forceinline__ void resid_V_at(const Coef<T>& c, const T* __restrict
 template <typename T, int R>
 __global__ void k_resid_V(Coef<T> c, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, int jac,
                           long long bstride) {
+  griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
   if (i > c.n) return;
@@ -330,8 +369,8 @@ void launch_resid_V(const Coef<T>& c, const T* x, const T* b, T* r, int jac, int
   const int R = rows_vel(c.n);
   dim3 g = grid2R(c.n + 1, c.n + 1, R);
   g.z = nbatch;
-  if (R == 4) k_resid_V<T, 4><<<g, dim3(BX, BY), 0, s>>>(c, x, b, r, jac, bstride);
-  else k_resid_V<T, 1><<<g, dim3(BX, BY), 0, s>>>(c, x, b, r, jac, bstride);
+  if (R == 4) launch_k(k_resid_V<T, 4>, dim3(g), dim3(dim3(BX, BY)), 0, s, c, x, b, r, jac, bstride);
+  else launch_k(k_resid_V<T, 1>, dim3(g), dim3(dim3(BX, BY)), 0, s, c, x, b, r, jac, bstride);
 }
 
 // ------------------------------------------------------ block D' smoothers
@@ -352,6 +391,7 @@ __device__ __forceinline__ void cheb_D_at(const Coef<T>& c, const T* __restrict_
 template <typename T, int R>
 __global__ void k_cheb_D(Coef<T> c, const T* __restrict__ xin, const T* __restrict__ b, T* __restrict__ d,
                          T* __restrict__ xout, T a, T cc, long long bstride) {
+  griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
   if (i >= c.n) return;
@@ -371,8 +411,8 @@ void launch_cheb_D(const Coef<T>& c, const T* x_in, const T* b, T* d, T* x_out, 
   const int R = rows_cell(c.n);
   dim3 g = grid2R(c.n, c.n, R);
   g.z = nbatch;
-  if (R == 4) k_cheb_D<T, 4><<<g, dim3(BX, BY), 0, s>>>(c, x_in, b, d, x_out, a, cc, bstride);
-  else k_cheb_D<T, 1><<<g, dim3(BX, BY), 0, s>>>(c, x_in, b, d, x_out, a, cc, bstride);
+  if (R == 4) launch_k(k_cheb_D<T, 4>, dim3(g), dim3(dim3(BX, BY)), 0, s, c, x_in, b, d, x_out, a, cc, bstride);
+  else launch_k(k_cheb_D<T, 1>, dim3(g), dim3(dim3(BX, BY)), 0, s, c, x_in, b, d, x_out, a, cc, bstride);
 }
 
 template <typename T>
@@ -388,6 +428,7 @@ __device__ __forceinline__ void resid_D_at(const Coef<T>& c, const T* __restrict
 template <typename T, int R>
 __global__ void k_resid_D(Coef<T> c, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, int jac,
                           long long bstride) {
+  griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
   if (i >= c.n) return;
@@ -407,8 +448,8 @@ void launch_resid_D(const Coef<T>& c, const T* x, const T* b, T* r, int jac, int
   const int R = rows_cell(c.n);
   dim3 g = grid2R(c.n, c.n, R);
   g.z = nbatch;
-  if (R == 4) k_resid_D<T, 4><<<g, dim3(BX, BY), 0, s>>>(c, x, b, r, jac, bstride);
-  else k_resid_D<T, 1><<<g, dim3(BX, BY), 0, s>>>(c, x, b, r, jac, bstride);
+  if (R == 4) launch_k(k_resid_D<T, 4>, dim3(g), dim3(dim3(BX, BY)), 0, s, c, x, b, r, jac, bstride);
+  else launch_k(k_resid_D<T, 1>, dim3(g), dim3(dim3(BX, BY)), 0, s, c, x, b, r, jac, bstride);
 }
 
 // ------------------------------------------------------------ transfers
@@ -469,6 +510,7 @@ __device__ __forceinline__ void restrict_V_at(int nf, int Pf, const T* __restric
 
 template <typename T>
 __global__ void k_restrict_V(int nf, int Pf, const T* __restrict__ r, int nc, int Pc, T* __restrict__ bc) {
+  griddep_wait();
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I > nc || J > nc) return;
@@ -478,7 +520,7 @@ __global__ void k_restrict_V(int nf, int Pf, const T* __restrict__ r, int nc, in
 template <typename T>
 void launch_restrict_V(int nf, int Pf, const T* r, int nc, int Pc, T* bc, cudaStream_t s) {
   SD_COUNT(1);
-  k_restrict_V<T><<<grid2(nc + 1, nc + 1), dim3(BX, BY), 0, s>>>(nf, Pf, r, nc, Pc, bc);
+  launch_k(k_restrict_V<T>, dim3(grid2(nc + 1, nc + 1)), dim3(dim3(BX, BY)), 0, s, nf, Pf, r, nc, Pc, bc);
 }
 
 template <typename T>
@@ -490,6 +532,7 @@ __device__ __forceinline__ void restrict_D_at(int Pf, const T* __restrict__ r, i
 
 template <typename T>
 __global__ void k_restrict_D(int nf, int Pf, const T* __restrict__ r, int nc, int Pc, T* __restrict__ bc) {
+  griddep_wait();
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= nc || J >= nc) return;
@@ -499,7 +542,7 @@ __global__ void k_restrict_D(int nf, int Pf, const T* __restrict__ r, int nc, in
 template <typename T>
 void launch_restrict_D(int nf, int Pf, const T* r, int nc, int Pc, T* bc, cudaStream_t s) {
   SD_COUNT(1);
-  k_restrict_D<T><<<grid2(nc, nc), dim3(BX, BY), 0, s>>>(nf, Pf, r, nc, Pc, bc);
+  launch_k(k_restrict_D<T>, dim3(grid2(nc, nc)), dim3(dim3(BX, BY)), 0, s, nf, Pf, r, nc, Pc, bc);
 }
 
 // Cell blocks: b_c(I, J) = sum of the residuals b - A x of the four fine
@@ -507,6 +550,7 @@ void launch_restrict_D(int nf, int Pf, const T* r, int nc, int Pc, T* bc, cudaSt
 template <typename T>
 __global__ void k_resid_restrict_D(Coef<T> c, const T* __restrict__ x, const T* __restrict__ b, int nc, int Pc,
                                    T* __restrict__ bc) {
+  griddep_wait();
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= nc || J >= nc) return;
@@ -525,7 +569,7 @@ __global__ void k_resid_restrict_D(Coef<T> c, const T* __restrict__ x, const T* 
 template <typename T>
 void launch_resid_restrict_D(const Coef<T>& c, const T* x, const T* b, int nc, int Pc, T* bc, cudaStream_t s) {
   SD_COUNT(1);
-  k_resid_restrict_D<T><<<grid2(nc, nc), dim3(BX, BY), 0, s>>>(c, x, b, nc, Pc, bc);
+  launch_k(k_resid_restrict_D<T>, dim3(grid2(nc, nc)), dim3(dim3(BX, BY)), 0, s, c, x, b, nc, Pc, bc);
 }
 
 template <typename T>
@@ -544,43 +588,52 @@ __device__ __forceinline__ T cv_at(const T* ev, int nc, int Pc, int I, int J) {
   return ev[(long long)J * Pc + I];
 }
 
+// increment of fine u face (i, j), 0 < i < nf, j < nf
+template <typename T>
+__device__ __forceinline__ T prolong_u_val(const T* __restrict__ eu, int nc, int Pc, int i, int j) {
+  const int J = j >> 1, Jn = (j & 1) ? J + 1 : J - 1;
+  T cy0, cy1;
+  if (i & 1) {
+    const int I = i >> 1;
+    cy0 = T(0.5) * (cu_at(eu, nc, Pc, I, J) + cu_at(eu, nc, Pc, I + 1, J));
+    cy1 = T(0.5) * (cu_at(eu, nc, Pc, I, Jn) + cu_at(eu, nc, Pc, I + 1, Jn));
+  } else {
+    const int I = i >> 1;
+    cy0 = cu_at(eu, nc, Pc, I, J);
+    cy1 = cu_at(eu, nc, Pc, I, Jn);
+  }
+  return T(0.75) * cy0 + T(0.25) * cy1;
+}
+
+// increment of fine v face (i, j), i < nf, j < nf
+template <typename T>
+__device__ __forceinline__ T prolong_v_val(const T* __restrict__ ev, int nc, int Pc, int i, int j) {
+  const int I = i >> 1, In = (i & 1) ? I + 1 : I - 1;
+  T cx0, cx1;
+  if (j & 1) {
+    const int J = j >> 1;
+    cx0 = T(0.5) * (cv_at(ev, nc, Pc, I, J) + cv_at(ev, nc, Pc, I, J + 1));
+    cx1 = T(0.5) * (cv_at(ev, nc, Pc, In, J) + cv_at(ev, nc, Pc, In, J + 1));
+  } else {
+    const int J = j >> 1;
+    cx0 = cv_at(ev, nc, Pc, I, J);
+    cx1 = cv_at(ev, nc, Pc, In, J);
+  }
+  return T(0.75) * cx0 + T(0.25) * cx1;
+}
+
 template <typename T>
 __device__ __forceinline__ void prolong_V_at(int nf, int Pf, T* __restrict__ x, int nc, int Pc,
                                              const T* __restrict__ e, int i, int j) {
   const T* eu = e;
   const T* ev = e + (long long)nc * Pc;
-  if (j < nf && i > 0 && i < nf) {
-    const int J = j >> 1, Jn = (j & 1) ? J + 1 : J - 1;
-    T cy0, cy1;
-    if (i & 1) {
-      const int I = i >> 1;
-      cy0 = T(0.5) * (cu_at(eu, nc, Pc, I, J) + cu_at(eu, nc, Pc, I + 1, J));
-      cy1 = T(0.5) * (cu_at(eu, nc, Pc, I, Jn) + cu_at(eu, nc, Pc, I + 1, Jn));
-    } else {
-      const int I = i >> 1;
-      cy0 = cu_at(eu, nc, Pc, I, J);
-      cy1 = cu_at(eu, nc, Pc, I, Jn);
-    }
-    x[(long long)j * Pf + i] += T(0.75) * cy0 + T(0.25) * cy1;
-  }
-  if (i < nf && j < nf) {
-    const int I = i >> 1, In = (i & 1) ? I + 1 : I - 1;
-    T cx0, cx1;
-    if (j & 1) {
-      const int J = j >> 1;
-      cx0 = T(0.5) * (cv_at(ev, nc, Pc, I, J) + cv_at(ev, nc, Pc, I, J + 1));
-      cx1 = T(0.5) * (cv_at(ev, nc, Pc, In, J) + cv_at(ev, nc, Pc, In, J + 1));
-    } else {
-      const int J = j >> 1;
-      cx0 = cv_at(ev, nc, Pc, I, J);
-      cx1 = cv_at(ev, nc, Pc, In, J);
-    }
-    x[(long long)nf * Pf + (long long)j * Pf + i] += T(0.75) * cx0 + T(0.25) * cx1;
-  }
+  if (j < nf && i > 0 && i < nf) x[(long long)j * Pf + i] += prolong_u_val(eu, nc, Pc, i, j);
+  if (i < nf && j < nf) x[(long long)nf * Pf + (long long)j * Pf + i] += prolong_v_val(ev, nc, Pc, i, j);
 }
 
 template <typename T, int R>
 __global__ void k_prolong_V(int nf, int Pf, T* __restrict__ x, int nc, int Pc, const T* __restrict__ e) {
+  griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
   if (i > nf) return;
@@ -596,8 +649,8 @@ template <typename T>
 void launch_prolong_V(int nf, int Pf, T* x, int nc, int Pc, const T* e, cudaStream_t s) {
   SD_COUNT(1);
   const int R = rows_vel(nf);
-  if (R == 4) k_prolong_V<T, 4><<<grid2R(nf + 1, nf + 1, 4), dim3(BX, BY), 0, s>>>(nf, Pf, x, nc, Pc, e);
-  else k_prolong_V<T, 1><<<grid2R(nf + 1, nf + 1, 1), dim3(BX, BY), 0, s>>>(nf, Pf, x, nc, Pc, e);
+  if (R == 4) launch_k(k_prolong_V<T, 4>, dim3(grid2R(nf + 1, nf + 1, 4)), dim3(dim3(BX, BY)), 0, s, nf, Pf, x, nc, Pc, e);
+  else launch_k(k_prolong_V<T, 1>, dim3(grid2R(nf + 1, nf + 1, 1)), dim3(dim3(BX, BY)), 0, s, nf, Pf, x, nc, Pc, e);
 }
 
 template <typename T>
@@ -611,17 +664,22 @@ __device__ __forceinline__ T cd_at(const T* e, int nc, int Pc, int I, int J) {
 }
 
 template <typename T>
-__device__ __forceinline__ void prolong_D_at(int Pf, T* __restrict__ x, int nc, int Pc, const T* __restrict__ e,
-                                             int i, int j) {
+__device__ __forceinline__ T prolong_D_val(const T* __restrict__ e, int nc, int Pc, int i, int j) {
   const int I = i >> 1, J = j >> 1;
   const int In = (i & 1) ? I + 1 : I - 1, Jn = (j & 1) ? J + 1 : J - 1;
-  const T val = T(0.5625) * cd_at(e, nc, Pc, I, J) + T(0.1875) * (cd_at(e, nc, Pc, In, J) + cd_at(e, nc, Pc, I, Jn)) +
-                T(0.0625) * cd_at(e, nc, Pc, In, Jn);
-  x[(long long)j * Pf + i] += val;
+  return T(0.5625) * cd_at(e, nc, Pc, I, J) + T(0.1875) * (cd_at(e, nc, Pc, In, J) + cd_at(e, nc, Pc, I, Jn)) +
+         T(0.0625) * cd_at(e, nc, Pc, In, Jn);
+}
+
+template <typename T>
+__device__ __forceinline__ void prolong_D_at(int Pf, T* __restrict__ x, int nc, int Pc, const T* __restrict__ e,
+                                             int i, int j) {
+  x[(long long)j * Pf + i] += prolong_D_val(e, nc, Pc, i, j);
 }
 
 template <typename T, int R>
 __global__ void k_prolong_D(int nf, int Pf, T* __restrict__ x, int nc, int Pc, const T* __restrict__ e) {
+  griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
   if (i >= nf) return;
@@ -637,46 +695,284 @@ template <typename T>
 void launch_prolong_D(int nf, int Pf, T* x, int nc, int Pc, const T* e, cudaStream_t s) {
   SD_COUNT(1);
   const int R = rows_cell(nf);
-  if (R == 4) k_prolong_D<T, 4><<<grid2R(nf, nf, 4), dim3(BX, BY), 0, s>>>(nf, Pf, x, nc, Pc, e);
-  else k_prolong_D<T, 1><<<grid2R(nf, nf, 1), dim3(BX, BY), 0, s>>>(nf, Pf, x, nc, Pc, e);
+  if (R == 4) launch_k(k_prolong_D<T, 4>, dim3(grid2R(nf, nf, 4)), dim3(dim3(BX, BY)), 0, s, nf, Pf, x, nc, Pc, e);
+  else launch_k(k_prolong_D<T, 1>, dim3(grid2R(nf, nf, 1)), dim3(dim3(BX, BY)), 0, s, nf, Pf, x, nc, Pc, e);
+}
+
+// ------------------------------------------- tiled (temporally blocked) smoothing
+// NS Chebyshev steps in one kernel.  Each block loads an output tile of
+// TLX x TLY positions plus a halo of NS (one per step: every step reaches one
+// neighbour) into shared memory, with x_in optionally increased by the
+// prolongation of a coarse correction, runs the NS steps there (the computed
+// region shrinks by one per step), and writes only its output tile.  Each
+// point's arithmetic is that of the per-step kernels, in the same order, so
+// the result is bitwise the same; only the global traffic and the launches
+// of the intermediate steps disappear.
+static const int TLX = 32, TLY = 16, TLT = 256;
+
+template <typename T, int NS>
+__global__ void __launch_bounds__(TLT) k_smooth_tile_D(Coef<T> c, const T* __restrict__ xin,
+                                                       const T* __restrict__ b, T* __restrict__ xout,
+                                                       ChebSteps<T> cs, const T* __restrict__ ec, int nc, int Pc) {
+  griddep_wait();
+  constexpr int H = NS, EX = TLX + 2 * H, EY = TLY + 2 * H, SP = EX + 1, SR = EY + 1;
+  __shared__ T sb[SR * SP], sx0[SR * SP], sx1[SR * SP], sd[SR * SP], sTx[SR * SP], sTy[SR * SP];
+  const int n = c.n, P = c.P;
+  const int ilo = blockIdx.x * TLX - H, jlo = blockIdx.y * TLY - H;
+  for (int p = threadIdx.x; p < SR * SP; p += TLT) {
+    const int gi = ilo + p % SP, gj = jlo + p / SP;
+    T vb = T(0), vx = T(0), vtx = T(0), vty = T(0);
+    if (gi >= 0 && gj >= 0) {
+      const long long gk = (long long)gj * P + gi;
+      if (gi < n && gj < n) {
+        vb = b[gk];
+        if (xin) {
+          vx = xin[gk];
+          if (ec) vx += prolong_D_val(ec, nc, Pc, gi, gj);
+        }
+      }
+      if (gi <= n && gj < n) vtx = c.Tx[gk];
+      if (gi < n && gj <= n) vty = c.Ty[gk];
+    }
+    sb[p] = vb;
+    sx0[p] = vx;
+    sTx[p] = vtx;
+    sTy[p] = vty;
+  }
+  __syncthreads();
+  // shared view: global (i, j) -> (j - jlo) * SP + (i - ilo)
+  const long long sh = (long long)jlo * SP + ilo;
+  Coef<T> tc = c;
+  tc.P = SP;
+  tc.Tx = sTx - sh;
+  tc.Ty = sTy - sh;
+  const T* bq = sb - sh;
+  T* dq = sd - sh;
+  T* xa = sx0 - sh;
+  T* xb = sx1 - sh;
+  const T* cur = xin ? xa : nullptr;
+  T* nxt = xb;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const int lo = s + 1, w = EX - 2 * lo, hgt = EY - 2 * lo;
+    for (int p = threadIdx.x; p < w * hgt; p += TLT) {
+      const int gi = ilo + lo + p % w, gj = jlo + lo + p / w;
+      if (gi >= 0 && gj >= 0 && gi < n && gj < n) cheb_D_at(tc, cur, bq, dq, nxt, cs.a[s], cs.c[s], gi, gj);
+    }
+    __syncthreads();
+    cur = nxt;
+    nxt = (nxt == xb) ? xa : xb;
+  }
+  for (int p = threadIdx.x; p < TLX * TLY; p += TLT) {
+    const int gi = ilo + H + p % TLX, gj = jlo + H + p / TLX;
+    if (gi < n && gj < n) xout[(long long)gj * P + gi] = cur[(long long)gj * SP + gi];
+  }
+}
+
+template <typename T, int NS>
+__global__ void __launch_bounds__(TLT) k_smooth_tile_V(Coef<T> c, const T* __restrict__ xin,
+                                                       const T* __restrict__ b, T* __restrict__ xout,
+                                                       ChebSteps<T> cs, const T* __restrict__ ec, int nc, int Pc) {
+  griddep_wait();
+  constexpr int H = NS, EX = TLX + 2 * H, EY = TLY + 2 * H, SP = EX + 1, SR = EY + 1;
+  __shared__ T sbu[SR * SP], sbv[SR * SP], sau[SR * SP], sav[SR * SP], sbu2[SR * SP], sbv2[SR * SP];
+  __shared__ T sdu[SR * SP], sdv[SR * SP], sw[SP], srg[SP];
+  const int n = c.n, P = c.P;
+  const long long nv = (long long)n * P;
+  const int ilo = blockIdx.x * TLX - H, jlo = blockIdx.y * TLY - H;
+  const T* ecu = ec;
+  const T* ecv = ec ? ec + (long long)nc * Pc : nullptr;
+  for (int p = threadIdx.x; p < SR * SP; p += TLT) {
+    const int gi = ilo + p % SP, gj = jlo + p / SP;
+    T bu = T(0), bv = T(0), xu = T(0), xv = T(0);
+    if (gi >= 0 && gj >= 0) {
+      const long long gk = (long long)gj * P + gi;
+      if (gi <= n && gj < n) {  // u face
+        bu = b[gk];
+        if (xin) {
+          xu = xin[gk];
+          if (ec && gi > 0 && gi < n) xu += prolong_u_val(ecu, nc, Pc, gi, gj);
+        }
+      }
+      if (gi < n && gj <= n) {  // v face
+        bv = b[nv + gk];
+        if (xin) {
+          xv = xin[nv + gk];
+          if (ec && gj < n) xv += prolong_v_val(ecv, nc, Pc, gi, gj);
+        }
+      }
+    }
+    sbu[p] = bu;
+    sbv[p] = bv;
+    sau[p] = xu;
+    sav[p] = xv;
+  }
+  for (int p = threadIdx.x; p < SP; p += TLT) {
+    const int gi = ilo + p;
+    sw[p] = (gi >= 0 && gi <= n) ? c.w[gi] : T(0);
+    srg[p] = (gi >= 0 && gi < n) ? c.rg[gi] : T(0);
+  }
+  __syncthreads();
+  const long long sh = (long long)jlo * SP + ilo;
+  Coef<T> tc = c;
+  tc.P = SP;
+  tc.w = sw - ilo;
+  tc.rg = srg - ilo;
+  const T* bu = sbu - sh;
+  const T* bv = sbv - sh;
+  T* du = sdu - sh;
+  T* dv = sdv - sh;
+  T* au = sau - sh;
+  T* av = sav - sh;
+  T* cu2 = sbu2 - sh;
+  T* cv2 = sbv2 - sh;
+  const T* curu = xin ? au : nullptr;
+  const T* curv = xin ? av : nullptr;
+  T* nxu = cu2;
+  T* nxv = cv2;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const int lo = s + 1, w = EX - 2 * lo, hgt = EY - 2 * lo;
+    for (int p = threadIdx.x; p < w * hgt; p += TLT) {
+      const int gi = ilo + lo + p % w, gj = jlo + lo + p / w;
+      if (gi >= 0 && gj >= 0 && gi <= n && gj <= n)
+        cheb_V_at2(tc, curu, curv, bu, bv, du, dv, nxu, nxv, cs.a[s], cs.c[s], gi, gj);
+    }
+    __syncthreads();
+    curu = nxu;
+    curv = nxv;
+    nxu = (nxu == cu2) ? au : cu2;
+    nxv = (nxv == cv2) ? av : cv2;
+  }
+  for (int p = threadIdx.x; p < TLX * TLY; p += TLT) {
+    const int gi = ilo + H + p % TLX, gj = jlo + H + p / TLX;
+    const long long gk = (long long)gj * P + gi, sk = (long long)gj * SP + gi;
+    if (gi <= n && gj < n) xout[gk] = curu[sk];
+    if (gi < n && gj <= n) xout[nv + gk] = curv[sk];
+  }
+}
+
+template <typename T>
+int launch_smooth_tile_D(const Coef<T>& c, const T* x_in, const T* b, T* x_out, const ChebSteps<T>& cs,
+                         const T* ec, int nc, int Pc, cudaStream_t s) {
+  const dim3 g((c.n + TLX - 1) / TLX, (c.n + TLY - 1) / TLY);
+  switch (cs.ns) {
+    case 1: launch_k(k_smooth_tile_D<T, 1>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ec, nc, Pc); break;
+    case 2: launch_k(k_smooth_tile_D<T, 2>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ec, nc, Pc); break;
+    case 3: launch_k(k_smooth_tile_D<T, 3>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ec, nc, Pc); break;
+    case 4: launch_k(k_smooth_tile_D<T, 4>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ec, nc, Pc); break;
+    default: return -1;
+  }
+  SD_COUNT(1);
+  return 0;
+}
+
+template <typename T>
+int launch_smooth_tile_V(const Coef<T>& c, const T* x_in, const T* b, T* x_out, const ChebSteps<T>& cs,
+                         const T* ec, int nc, int Pc, cudaStream_t s) {
+  const dim3 g((c.n + 1 + TLX - 1) / TLX, (c.n + 1 + TLY - 1) / TLY);
+  switch (cs.ns) {
+    case 1: launch_k(k_smooth_tile_V<T, 1>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ec, nc, Pc); break;
+    case 2: launch_k(k_smooth_tile_V<T, 2>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ec, nc, Pc); break;
+    case 3: launch_k(k_smooth_tile_V<T, 3>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ec, nc, Pc); break;
+    case 4: launch_k(k_smooth_tile_V<T, 4>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ec, nc, Pc); break;
+    default: return -1;
+  }
+  SD_COUNT(1);
+  return 0;
 }
 
 // ------------------------------------------------ fused coarse V-cycle
-// All levels from `first` down to the coarsest (n <= 32 cells per side) in
-// one CTA: every work vector lives in shared memory, the sweeps of the
-// smoother, residual, transfers and the dense coarsest solve are separated
-// by __syncthreads.  Same arithmetic, in the same order per point, as the
-// per-level kernels; it only removes the launches of the small grids.
+// All levels from `first` (at most 32 x 32 cells) down to the coarsest in one
+// CTA: every work vector lives in shared memory (four per level: b, two
+// iterates and d, which also holds the residual), the sweeps of the smoother,
+// residual, transfers and the dense coarsest solve are separated by
+// __syncthreads.  Same arithmetic, in the same order per point, as the
+// per-level kernels; it only removes the launches of the small grids.  (Entry
+// at 64 x 64 was measured slower than the per-level kernels it replaced.)
 static __host__ __device__ inline int cyc_pitch(int n) { return ((n + 1) + 7) / 8 * 8; }
 static __host__ __device__ inline int cyc_len(int n, int kind) {
   return kind == 0 ? (2 * n + 1) * cyc_pitch(n) : n * cyc_pitch(n);
 }
 
+// d = a d + c D^-1 (b - A x) at (i, j) of the velocity block (Dirichlet faces: d = 0)
 template <typename T>
-__device__ void cyc_sweep(const CoarseCycle<T>& q, int l, int op, const T* xin, const T* b, T* d, T* xout, T a, T cc,
-                          T* r, const T* bnext, T* bcoarse, const T* ecoarse) {
+__device__ __forceinline__ void cheb_d_V_at(const Coef<T>& c, const T* __restrict__ x, const T* __restrict__ b,
+                                            T* __restrict__ d, T a, T cc, int i, int j) {
+  const int n = c.n, P = c.P;
+  const T* u = x;
+  const T* v = x + (long long)n * P;
+  if (j < n) {
+    const long long k = (long long)j * P + i;
+    if (i == 0 || i == n) {
+      d[k] = T(0);
+    } else {
+      T off, dg;
+      u_row(c, u, v, i, j, true, off, dg);
+      const T r = b[k] - (dg * x[k] + off);
+      d[k] = (a != T(0) ? a * d[k] : T(0)) + cc * r / dg;
+    }
+  }
+  if (i < n) {
+    const long long k = (long long)n * P + (long long)j * P + i;
+    if (j == n) {
+      d[k] = T(0);
+    } else {
+      T off, dg;
+      v_row(c, u, v, i, j, true, off, dg);
+      const T r = b[k] - (dg * x[k] + off);
+      d[k] = (a != T(0) ? a * d[k] : T(0)) + cc * r / dg;
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void cheb_d_D_at(const Coef<T>& c, const T* __restrict__ x, const T* __restrict__ b,
+                                            T* __restrict__ d, T a, T cc, int i, int j) {
+  const long long k = (long long)j * c.P + i;
+  T off, dg;
+  d_row(c, x, i, j, true, off, dg);
+  const T r = b[k] - (dg * x[k] + off);
+  d[k] = (a != T(0) ? a * d[k] : T(0)) + cc * r / dg;
+}
+
+// ops: 0 Chebyshev step (writes d and x_out from x_in), 1 d-update only,
+//      2 x += d, 3 residual into d, 4 restriction of d to level l + 1,
+//      5 prolongation of level l + 1 into x
+template <typename T>
+__device__ void cyc_sweep(const CoarseCycle<T>& q, int l, int op, T* X, const T* B, T* D, T a, T cc, T* Bc,
+                          const T* Xc) {
   const Coef<T>& c = q.c[l];
   const int n = c.n;
   const int w = q.kind == 0 ? n + 1 : n;
-  for (int p = threadIdx.x; p < w * w; p += blockDim.x) {
-    const int i = p % w, j = p / w;
-    if (op == 0) {
-      if (q.kind == 0) cheb_V_at(c, xin, b, d, xout, a, cc, i, j);
-      else cheb_D_at(c, xin, b, d, xout, a, cc, i, j);
+  const int nc = (op >= 4) ? q.c[l + 1].n : 0;
+  const int wc = q.kind == 0 ? nc + 1 : nc;
+  const int npts = op == 4 ? wc * wc : w * w;
+  for (int p = threadIdx.x; p < npts; p += blockDim.x) {
+    const int ww = op == 4 ? wc : w;
+    const int i = p % ww, j = p / ww;
+    if (op == 0) {  // Chebyshev step x_out (X) = x_in (Xc, null: zero) + d
+      if (q.kind == 0) cheb_V_at(c, Xc, B, D, X, a, cc, i, j);
+      else cheb_D_at(c, Xc, B, D, X, a, cc, i, j);
     } else if (op == 1) {
-      if (q.kind == 0) resid_V_at(c, xin, b, r, 0, i, j);
-      else resid_D_at(c, xin, b, r, 0, i, j);
-    } else if (op == 2) {  // restriction to level l + 1 (p runs over the coarse grid)
-      const int nc = q.c[l + 1].n, wc = q.kind == 0 ? nc + 1 : nc;
-      if (p < wc * wc) {
-        const int I = p % wc, J = p / wc;
-        if (q.kind == 0) restrict_V_at(n, c.P, bnext, nc, q.c[l + 1].P, bcoarse, I, J);
-        else restrict_D_at(c.P, bnext, q.c[l + 1].P, bcoarse, I, J);
+      if (q.kind == 0) cheb_d_V_at(c, X, B, D, a, cc, i, j);
+      else cheb_d_D_at(c, X, B, D, a, cc, i, j);
+    } else if (op == 2) {
+      if (q.kind == 0) {
+        if (j < n) X[j * c.P + i] += D[j * c.P + i];
+        if (i < n) X[(n + j) * c.P + i] += D[(n + j) * c.P + i];
+      } else {
+        X[j * c.P + i] += D[j * c.P + i];
       }
-    } else {  // prolongation of level l + 1 into xout
-      const int nc = q.c[l + 1].n;
-      if (q.kind == 0) prolong_V_at(n, c.P, xout, nc, q.c[l + 1].P, ecoarse, i, j);
-      else prolong_D_at(c.P, xout, nc, q.c[l + 1].P, ecoarse, i, j);
+    } else if (op == 3) {
+      if (q.kind == 0) resid_V_at(c, X, B, D, 0, i, j);
+      else resid_D_at(c, X, B, D, 0, i, j);
+    } else if (op == 4) {
+      if (q.kind == 0) restrict_V_at(n, c.P, D, nc, q.c[l + 1].P, Bc, i, j);
+      else restrict_D_at(c.P, D, q.c[l + 1].P, Bc, i, j);
+    } else {
+      if (q.kind == 0) prolong_V_at(n, c.P, X, nc, q.c[l + 1].P, Xc, i, j);
+      else prolong_D_at(c.P, X, nc, q.c[l + 1].P, Xc, i, j);
     }
   }
   __syncthreads();
@@ -684,13 +980,13 @@ __device__ void cyc_sweep(const CoarseCycle<T>& q, int l, int op, const T* xin, 
 
 template <typename T>
 __global__ void __launch_bounds__(1024) k_coarse_cycle(CoarseCycle<T> q) {
+  griddep_wait();
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   T* B[SD_CYC_MAXL];
   T* X[SD_CYC_MAXL];
   T* X2[SD_CYC_MAXL];
-  T* Dd[SD_CYC_MAXL];
-  T* R[SD_CYC_MAXL];
+  T* D[SD_CYC_MAXL];
   T* cur[SD_CYC_MAXL];
   int off = 0;
   for (int l = 0; l < q.nlev; ++l) {
@@ -698,8 +994,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(CoarseCycle<T> q) {
     B[l] = sm + off; off += len;
     X[l] = sm + off; off += len;
     X2[l] = sm + off; off += len;
-    Dd[l] = sm + off; off += len;
-    R[l] = sm + off; off += len;
+    D[l] = sm + off; off += len;
   }
   const int len0 = cyc_len(q.c[0].n, q.kind);
   for (int p = threadIdx.x; p < len0; p += blockDim.x) B[0][p] = q.b_in[p];
@@ -707,14 +1002,14 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(CoarseCycle<T> q) {
   const int L = q.nlev;
   for (int l = 0; l + 1 < L; ++l) {
     T* c0 = nullptr;
-    for (int k = 0; k < q.deg; ++k) {
+    for (int k = 0; k < q.deg[l]; ++k) {
       T* o = (c0 == X[l]) ? X2[l] : X[l];
-      cyc_sweep<T>(q, l, 0, c0, B[l], Dd[l], o, q.cha[l][k], q.chc[l][k], nullptr, nullptr, nullptr, nullptr);
+      cyc_sweep<T>(q, l, 0, o, B[l], D[l], q.cha[l][k], q.chc[l][k], nullptr, c0);
       c0 = o;
     }
     cur[l] = c0;
-    cyc_sweep<T>(q, l, 1, c0, B[l], nullptr, nullptr, T(0), T(0), R[l], nullptr, nullptr, nullptr);
-    cyc_sweep<T>(q, l, 2, nullptr, nullptr, nullptr, nullptr, T(0), T(0), nullptr, R[l], B[l + 1], nullptr);
+    cyc_sweep<T>(q, l, 3, c0, B[l], D[l], T(0), T(0), nullptr, nullptr);
+    cyc_sweep<T>(q, l, 4, c0, B[l], D[l], T(0), T(0), B[l + 1], nullptr);
   }
   {  // coarsest grid: x = A^-1 b with the FP64 inverse
     const int m = q.m;
@@ -731,11 +1026,11 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(CoarseCycle<T> q) {
     __syncthreads();
   }
   for (int l = L - 2; l >= 0; --l) {
-    cyc_sweep<T>(q, l, 3, nullptr, nullptr, nullptr, cur[l], T(0), T(0), nullptr, nullptr, nullptr, cur[l + 1]);
+    cyc_sweep<T>(q, l, 5, cur[l], B[l], D[l], T(0), T(0), nullptr, cur[l + 1]);
     T* c0 = cur[l];
-    for (int k = 0; k < q.deg; ++k) {
+    for (int k = 0; k < q.deg[l]; ++k) {
       T* o = (c0 == X[l]) ? X2[l] : X[l];
-      cyc_sweep<T>(q, l, 0, c0, B[l], Dd[l], o, q.cha[l][k], q.chc[l][k], nullptr, nullptr, nullptr, nullptr);
+      cyc_sweep<T>(q, l, 0, o, B[l], D[l], q.cha[l][k], q.chc[l][k], nullptr, c0);
       c0 = o;
     }
     cur[l] = c0;
@@ -757,7 +1052,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(CoarseCycle<T> q) {
 template <typename T>
 size_t coarse_cycle_smem(const CoarseCycle<T>& q) {
   size_t tot = 0;
-  for (int l = 0; l < q.nlev; ++l) tot += 5 * (size_t)cyc_len(q.c[l].n, q.kind);
+  for (int l = 0; l < q.nlev; ++l) tot += 4 * (size_t)cyc_len(q.c[l].n, q.kind);
   return tot * sizeof(T);
 }
 
@@ -774,7 +1069,7 @@ int launch_coarse_cycle(const CoarseCycle<T>& q, cudaStream_t s) {
   const size_t sm = coarse_cycle_smem(q);
   if (sm > 200 * 1024) return -1;
   SD_COUNT(1);
-  k_coarse_cycle<T><<<1, 1024, sm, s>>>(q);
+  launch_k(k_coarse_cycle<T>, dim3(1), dim3(1024), sm, s, q);
   return 0;
 }
 
@@ -784,7 +1079,8 @@ int launch_coarse_cycle(const CoarseCycle<T>& q, cudaStream_t s) {
 // then the velocity rhs r_v - B z_pf for the V-block multigrid.
 template <typename T>
 __global__ void k_precond_entry(Coef<double> c, const double* __restrict__ r, double* __restrict__ z, double schur,
-                                const T* __restrict__ eP, double cmass, int useB, T* __restrict__ rV) {
+                                const T* __restrict__ eP, double cmass, int useB, int useB1, T* __restrict__ rV) {
+  griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int n = c.n, P = c.P;
@@ -810,20 +1106,23 @@ __global__ void k_precond_entry(Coef<double> c, const double* __restrict__ r, do
       if (j > 0) val -= h * (zp(kv) - zp(kv - P));
       else val -= h * zp(i);
     }
+    // Darcy solved first: r_v - B'_1 z_pm on the interface rows (B'_1 = -h)
+    if (useB1 && j == 0) val += h * (T)z[(long long)(3 * n + 1) * P + (long long)(n - 1) * P + i];
     rV[k] = val;
   }
 }
 
 template <typename T>
 void launch_precond_entry(const Coef<double>& c, const double* r, double* z, double schur, const T* eP, double cmass,
-                          int use_B, T* rV, cudaStream_t s) {
+                          int use_B, int use_B1, T* rV, cudaStream_t s) {
   SD_COUNT(1);
-  k_precond_entry<T><<<grid2(c.n + 1, c.n + 1), dim3(BX, BY), 0, s>>>(c, r, z, schur, eP, cmass, use_B, rV);
+  launch_k(k_precond_entry<T>, dim3(grid2(c.n + 1, c.n + 1)), dim3(dim3(BX, BY)), 0, s, c, r, z, schur, eP, cmass, use_B, use_B1, rV);
 }
 
 template <typename T>
 __global__ void k_precond_mid(Coef<double> c, const double* __restrict__ r, double* __restrict__ z,
                               const T* __restrict__ eV, int useC, T* __restrict__ rD) {
+  griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int n = c.n, P = c.P;
@@ -848,11 +1147,12 @@ template <typename T>
 void launch_precond_mid(const Coef<double>& c, const double* r, double* z, const T* eV, int use_C, T* rD,
                         cudaStream_t s) {
   SD_COUNT(1);
-  k_precond_mid<T><<<grid2(c.n + 1, c.n + 1), dim3(BX, BY), 0, s>>>(c, r, z, eV, use_C, rD);
+  launch_k(k_precond_mid<T>, dim3(grid2(c.n + 1, c.n + 1)), dim3(dim3(BX, BY)), 0, s, c, r, z, eV, use_C, rD);
 }
 
 template <typename T>
 __global__ void k_precond_exit(int n, int P, double* __restrict__ z, const T* __restrict__ eD) {
+  griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= n || j >= n) return;
@@ -863,7 +1163,7 @@ __global__ void k_precond_exit(int n, int P, double* __restrict__ z, const T* __
 template <typename T>
 void launch_precond_exit(const Coef<double>& c, double* z, const T* eD, cudaStream_t s) {
   SD_COUNT(1);
-  k_precond_exit<T><<<grid2(c.n, c.n), dim3(BX, BY), 0, s>>>(c.n, c.P, z, eD);
+  launch_k(k_precond_exit<T>, dim3(grid2(c.n, c.n)), dim3(dim3(BX, BY)), 0, s, c.n, c.P, z, eD);
 }
 
 // P^pv_BGS(P_V, P_D') of Sec. 4: after z_v = P_V r_v, the identity block
@@ -871,6 +1171,7 @@ void launch_precond_exit(const Coef<double>& c, double* z, const T* eD, cudaStre
 template <typename T>
 __global__ void k_precond_bgs_pff(Coef<double> c, const double* __restrict__ r, double* __restrict__ z,
                                   const T* __restrict__ eV) {
+  griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int n = c.n, P = c.P;
@@ -889,11 +1190,12 @@ __global__ void k_precond_bgs_pff(Coef<double> c, const double* __restrict__ r, 
 template <typename T>
 void launch_precond_bgs_pff(const Coef<double>& c, const double* r, double* z, const T* eV, cudaStream_t s) {
   SD_COUNT(1);
-  k_precond_bgs_pff<T><<<grid2(c.n, c.n), dim3(BX, BY), 0, s>>>(c, r, z, eV);
+  launch_k(k_precond_bgs_pff<T>, dim3(grid2(c.n, c.n)), dim3(dim3(BX, BY)), 0, s, c, r, z, eV);
 }
 
 // ------------------------------------------------------------------ setup
 __global__ void k_pack_K(const double* __restrict__ Kd, int n, double* __restrict__ Kp, int P) {
+  griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= n || j >= n) return;
@@ -901,10 +1203,11 @@ __global__ void k_pack_K(const double* __restrict__ Kd, int n, double* __restric
 }
 void launch_pack_K(const double* Kdense, int n, double* Kp, int P, cudaStream_t s) {
   SD_COUNT(1);
-  k_pack_K<<<grid2(n, n), dim3(BX, BY), 0, s>>>(Kdense, n, Kp, P);
+  launch_k(k_pack_K, dim3(grid2(n, n)), dim3(dim3(BX, BY)), 0, s, Kdense, n, Kp, P);
 }
 
 __global__ void k_fill_K(double* __restrict__ K, int n, int P, double v) {
+  griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= n || j >= n) return;
@@ -912,11 +1215,12 @@ __global__ void k_fill_K(double* __restrict__ K, int n, int P, double v) {
 }
 void launch_fill_K(double* K, int n, int P, double v, cudaStream_t s) {
   SD_COUNT(1);
-  k_fill_K<<<grid2(n, n), dim3(BX, BY), 0, s>>>(K, n, P, v);
+  launch_k(k_fill_K, dim3(grid2(n, n)), dim3(dim3(BX, BY)), 0, s, K, n, P, v);
 }
 
 // coarse permeability: geometric mean of the 2 x 2 children
 __global__ void k_coarsen_K(const double* __restrict__ Kf, int nf, int Pf, double* __restrict__ Kc, int Pc) {
+  griddep_wait();
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   const int nc = nf / 2;
@@ -926,12 +1230,13 @@ __global__ void k_coarsen_K(const double* __restrict__ Kf, int nf, int Pf, doubl
 }
 void launch_coarsen_K(const double* Kf, int nf, int Pf, double* Kc, int Pc, cudaStream_t s) {
   SD_COUNT(1);
-  k_coarsen_K<<<grid2(nf / 2, nf / 2), dim3(BX, BY), 0, s>>>(Kf, nf, Pf, Kc, Pc);
+  launch_k(k_coarsen_K, dim3(grid2(nf / 2, nf / 2)), dim3(dim3(BX, BY)), 0, s, Kf, nf, Pf, Kc, Pc);
 }
 
 template <typename T>
 __global__ void k_setup_coef(const double* __restrict__ K, int n, int P, double mu, double alpha, T* w, T* rg, T* Tx,
                              T* Ty) {
+  griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i > n || j > n) return;
@@ -969,11 +1274,12 @@ template <typename T>
 void launch_setup_coef(const double* Kp, int n, int P, double mu, double alpha, T* w, T* rg, T* Tx, T* Ty,
                        cudaStream_t s) {
   SD_COUNT(1);
-  k_setup_coef<T><<<grid2(n + 1, n + 1), dim3(BX, BY), 0, s>>>(Kp, n, P, mu, alpha, w, rg, Tx, Ty);
+  launch_k(k_setup_coef<T>, dim3(grid2(n + 1, n + 1)), dim3(dim3(BX, BY)), 0, s, Kp, n, P, mu, alpha, w, rg, Tx, Ty);
 }
 
 template <typename T>
 __global__ void k_convert(const double* __restrict__ a, T* __restrict__ b, long long len) {
+  griddep_wait();
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < len; k += (long long)gridDim.x * blockDim.x)
     b[k] = (T)a[k];
 }
@@ -983,7 +1289,7 @@ void launch_convert(const double* src, T* dst, long long len, cudaStream_t s) {
   long long nb = (len + 255) / 256;
   if (nb > 4096) nb = 4096;
   if (nb < 1) nb = 1;
-  k_convert<T><<<(int)nb, 256, 0, s>>>(src, dst, len);
+  launch_k(k_convert<T>, dim3((int)nb), dim3(256), 0, s, src, dst, len);
 }
 
 // ------------------------------------------------- manufactured solution
@@ -1011,6 +1317,7 @@ __device__ __forceinline__ double mm_f1y(double x, double y, double mu) {
 // Dirichlet values of the identity rows).
 __global__ void k_mms_terms(Coef<double> c, const double* __restrict__ K, double* __restrict__ B0,
                             double* __restrict__ B1) {
+  griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int n = c.n, P = c.P;
@@ -1071,10 +1378,11 @@ __global__ void k_mms_terms(Coef<double> c, const double* __restrict__ K, double
 
 void launch_mms_terms(const Coef<double>& c, const double* Kp, double* B0, double* B1, cudaStream_t s) {
   SD_COUNT(1);
-  k_mms_terms<<<grid2(c.n + 1, c.n + 1), dim3(BX, BY), 0, s>>>(c, Kp, B0, B1);
+  launch_k(k_mms_terms, dim3(grid2(c.n + 1, c.n + 1)), dim3(dim3(BX, BY)), 0, s, c, Kp, B0, B1);
 }
 
 __global__ void k_mms_exact(int n, int P, double mu, double t, double* __restrict__ x) {
+  griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i > n || j > n) return;
@@ -1090,13 +1398,14 @@ __global__ void k_mms_exact(int n, int P, double mu, double t, double* __restric
 
 void launch_mms_exact(const Geom& g, double mu, double t, double* x, cudaStream_t s) {
   SD_COUNT(1);
-  k_mms_exact<<<grid2(g.n + 1, g.n + 1), dim3(BX, BY), 0, s>>>(g.n, g.P, mu, t, x);
+  launch_k(k_mms_exact, dim3(grid2(g.n + 1, g.n + 1)), dim3(dim3(BX, BY)), 0, s, g.n, g.P, mu, t, x);
 }
 
 // b = mass * xprev + B0 + s1 * B1 (mass = h^2/dt on velocity rows, half on
 // v_Gamma, 0 elsewhere); Dirichlet rows of x take their new values.
 __global__ void k_rhs(int n, int P, double cm, const double* __restrict__ B0, const double* __restrict__ B1,
                       double s1, const double* __restrict__ xprev, double* __restrict__ b, double* __restrict__ x) {
+  griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i > n || j > n) return;
@@ -1126,11 +1435,12 @@ __global__ void k_rhs(int n, int P, double cm, const double* __restrict__ B0, co
 void launch_rhs(const Geom& g, double cm, const double* B0, const double* B1, double s1, const double* xprev,
                 double* b, double* x, cudaStream_t s) {
   SD_COUNT(1);
-  k_rhs<<<grid2(g.n + 1, g.n + 1), dim3(BX, BY), 0, s>>>(g.n, g.P, cm, B0, B1, s1, xprev, b, x);
+  launch_k(k_rhs, dim3(grid2(g.n + 1, g.n + 1)), dim3(dim3(BX, BY)), 0, s, g.n, g.P, cm, B0, B1, s1, xprev, b, x);
 }
 
 // ------------------------------------------------------------ pack/unpack
 __global__ void k_pack2(int n, int P, const double* __restrict__ src, double* __restrict__ dst, int to_padded) {
+  griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i > n || j > n) return;
@@ -1151,11 +1461,11 @@ __global__ void k_pack2(int n, int P, const double* __restrict__ src, double* __
 
 void launch_pack(const Geom& g, const double* dense, double* padded, cudaStream_t s) {
   SD_COUNT(1);
-  k_pack2<<<grid2(g.n + 1, g.n + 1), dim3(BX, BY), 0, s>>>(g.n, g.P, dense, padded, 1);
+  launch_k(k_pack2, dim3(grid2(g.n + 1, g.n + 1)), dim3(dim3(BX, BY)), 0, s, g.n, g.P, dense, padded, 1);
 }
 void launch_unpack(const Geom& g, const double* padded, double* dense, cudaStream_t s) {
   SD_COUNT(1);
-  k_pack2<<<grid2(g.n + 1, g.n + 1), dim3(BX, BY), 0, s>>>(g.n, g.P, padded, dense, 0);
+  launch_k(k_pack2, dim3(grid2(g.n + 1, g.n + 1)), dim3(dim3(BX, BY)), 0, s, g.n, g.P, padded, dense, 0);
 }
 
 // ------------------------------------------------------- instantiations
@@ -1171,7 +1481,7 @@ void launch_unpack(const Geom& g, const double* padded, double* dense, cudaStrea
   template void launch_prolong_V<T>(int, int, T*, int, int, const T*, cudaStream_t);                              \
   template void launch_prolong_D<T>(int, int, T*, int, int, const T*, cudaStream_t);                              \
   template void launch_resid_restrict_D<T>(const Coef<T>&, const T*, const T*, int, int, T*, cudaStream_t);                              \
-  template void launch_precond_entry<T>(const Coef<double>&, const double*, double*, double, const T*, double, int, T*, cudaStream_t); \
+  template void launch_precond_entry<T>(const Coef<double>&, const double*, double*, double, const T*, double, int, int, T*, cudaStream_t); \
   template void launch_precond_mid<T>(const Coef<double>&, const double*, double*, const T*, int, T*, cudaStream_t); \
   template void launch_precond_exit<T>(const Coef<double>&, double*, const T*, cudaStream_t);                     \
   template void launch_precond_bgs_pff<T>(const Coef<double>&, const double*, double*, const T*, cudaStream_t);
@@ -1179,6 +1489,10 @@ SD_INST(float)
 SD_INST(double)
 template int launch_coarse_cycle<float>(const CoarseCycle<float>&, cudaStream_t);
 template int prepare_coarse_cycle<float>();
+template int launch_smooth_tile_D<float>(const Coef<float>&, const float*, const float*, float*, const ChebSteps<float>&,
+                                         const float*, int, int, cudaStream_t);
+template int launch_smooth_tile_V<float>(const Coef<float>&, const float*, const float*, float*, const ChebSteps<float>&,
+                                         const float*, int, int, cudaStream_t);
 template int prepare_coarse_cycle<double>();
 template int launch_coarse_cycle<double>(const CoarseCycle<double>&, cudaStream_t);
 template size_t coarse_cycle_smem<float>(const CoarseCycle<float>&);

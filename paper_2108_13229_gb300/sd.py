@@ -38,10 +38,13 @@ class sd_grid(ctypes.Structure):
 class sd_options(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int32), ("rtol", ctypes.c_double), ("max_iters", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("precond", ctypes.c_int32), ("bc", ctypes.c_int32),
-                ("cheb_degree", ctypes.c_int32), ("coarsest", ctypes.c_int32), ("schur_gamma", ctypes.c_double),
+                ("cheb_degree", ctypes.c_int32), ("cheb_degree_coarse", ctypes.c_int32),
+                ("schur_degree", ctypes.c_int32), ("coarsest", ctypes.c_int32), ("schur_gamma", ctypes.c_double),
                 ("cheb_ratio", ctypes.c_double), ("schur_mass", ctypes.c_int32), ("fuse_coarse", ctypes.c_int32),
                 ("orth", ctypes.c_int32), ("reorth_eta", ctypes.c_double), ("extrapolate", ctypes.c_int32),
-                ("graph", ctypes.c_int32), ("darcy_coupled", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("graph", ctypes.c_int32), ("pdl", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("darcy_coupled", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
 
 
 class sd_step_info(ctypes.Structure):
@@ -94,6 +97,7 @@ _SIGS = {
     "sd_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "sd_launch_count": (ctypes.c_int64, []),
+    "sd_struct_size": (ctypes.c_int64, [ctypes.c_int32]),
     "sd_apply_noalloc": (ctypes.c_int, [ctypes.POINTER(sd_grid), ctypes.c_double, _vp, ctypes.c_double,
                                         ctypes.c_double, _vp, _vp, _vp]),
     "sd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -356,3 +360,7 @@ def sd_apply_noalloc(n: int, mu: float, K, alpha_bj: float, dt: float, x, y, str
     g = sd_grid(n, n)
     _check(_load().sd_apply_noalloc(ctypes.byref(g), float(mu), _ptr(K, n * n), float(alpha_bj), float(dt),
                                     _ptr(x), _ptr(y), stream), "sd_apply_noalloc")
+
+
+def sd_struct_size(which: int) -> int:
+    return int(_load().sd_struct_size(int(which)))

@@ -81,3 +81,9 @@ def test_validation_without_gpu(sd):
     with pytest.raises(sd.SdError):
         sd.sd_create(n, 1.0, K, 1.0, 0.1, o)
     assert sd.sd_strerror(sd.SD_E_NOCONV).startswith("FGMRES")
+
+
+def test_struct_layout_matches_binding(sd):
+    import ctypes
+    for k, cls in enumerate([sd.sd_grid, sd.sd_options, sd.sd_step_info, sd.sd_request, sd.sd_result]):
+        assert sd.sd_struct_size(k) == ctypes.sizeof(cls), cls.__name__

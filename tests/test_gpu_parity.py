@@ -261,3 +261,43 @@ def test_darcy_overlap_parity(sd, precision):
     _, _, x = sd.sd_get_state(h)
     for k, e in fields_rel(x, xr, n).items():
         assert e <= 1e-8, (k, e)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_darcy_first_parity(sd, precision):
+    # Darcy block first (B'_1 kept), concurrent with the pressure block: same solution
+    n = 64
+    K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=0)
+    o = O.Oracle(n, 1e-3, 1.0, 0.05, K)
+    xr = o.run(O.exact(n, 0.0, 1e-3), 0.0, 3)
+    h = make(sd, n, 1e-3, K, 1.0, 0.05, precision, rtol=1e-12, darcy_coupled=2)
+    infos = sd.sd_step(h, 3)
+    assert all(i["status"] == 0 for i in infos)
+    _, _, x = sd.sd_get_state(h)
+    for k, e in fields_rel(x, xr, n).items():
+        assert e <= 1e-8, (k, e)
+
+
+def test_pdl_bitwise(sd):
+    # programmatic dependent launch only changes when grids start, not what they compute
+    n = 64
+    K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=10)
+    xs = []
+    for pdl in (0, 1):
+        h = make(sd, n, 1e-3, K, 1.0, 0.05, pdl=pdl)
+        sd.sd_step(h, 3)
+        xs.append(sd.sd_get_state(h)[2])
+    assert np.array_equal(xs[0], xs[1])
+
+
+@pytest.mark.parametrize("n", [64, 256])
+def test_tiled_smoothing_bitwise(sd, n):
+    # all Chebyshev steps of a smoothing in one tiled kernel, prolongation folded
+    # in: the same arithmetic per point as the per-step kernels
+    K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=11)
+    xs = []
+    for tile in (0, 1):
+        h = make(sd, n, 1e-3, K, 1.0, 0.05, 1, tile=tile)
+        sd.sd_step(h, 3)
+        xs.append(sd.sd_get_state(h)[2])
+    assert np.array_equal(xs[0], xs[1])

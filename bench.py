@@ -139,11 +139,32 @@ class ClockSampler:
         return out
 
 
-def run_form(sd, torch, n, K, precision, steps, warmup, stream, prof_kernel=None):
+TUNED = ("tile_rows", "coarsest", "cheb_degree")
+
+
+def tune_form(sd, n, K, precision, stream, enabled: bool):
+    """Autotuned (tile_rows, coarsest, cheb_degree) for this grid and precision, outside any timed region."""
+    base = sd.sd_options_default()
+    base.precision = precision
+    base.stream = stream.cuda_stream
+    if not enabled:
+        return {k: getattr(base, k) for k in TUNED}, None
+    cache = os.environ.get("SD_TUNE_CACHE", os.path.join(tempfile.gettempdir(), "sd_tune.txt"))
+    t0 = time.perf_counter()
+    best, ms = sd.sd_autotune(n, 1e-3, K, 1.0, 0.05, base, 3, cache)
+    tuned = {k: getattr(best, k) for k in TUNED}
+    return tuned, {"choice": tuned, "tuned_ms_per_step": ms, "seconds": time.perf_counter() - t0,
+                   "candidates": "tile_rows {16,8} x coarsest {4,8,16} x cheb_degree {3,2,4}; 2+3 steps each; "
+                                 "cache " + os.path.basename(cache)}
+
+
+def run_form(sd, torch, n, K, precision, steps, warmup, stream, prof_kernel=None, tuned=None):
     """Warm up, then time `steps` implicit-Euler steps with CUDA events on `stream`."""
     opts = sd.sd_options_default()
     opts.precision = precision
     opts.stream = stream.cuda_stream
+    for k, v in (tuned or {}).items():
+        setattr(opts, k, v)
     h = sd.sd_create(n, 1e-3, K, 1.0, 0.05, opts)
     sd.sd_step(h, warmup)
     if prof_kernel is not None:
@@ -213,23 +234,27 @@ def roofline_entry(kid: int, prof, step_ms: float):
     return e
 
 
-def bench_batch(sd, count: int, steps: int, threads: int, seed: int = 0):
-    """Independent instances with uneven grids advanced together by sd_solve_batch."""
+def bench_batch(sd, count: int, steps: int, threads: int, seed: int = 0, lockstep: bool = True):
+    """Independent instances with uneven grids advanced together by sd_solve_batch: instances of one grid size
+    run in lockstep (one launch serves the whole group), groups concurrently on their own streams."""
     from paper_2108_13229_gb300 import inputs as I
     wls = I.batch_instances(count, seed=seed, steps=steps)
     hs = []
     for wl in wls:
         o = sd.sd_options_default()
         hs.append(sd.sd_create(wl.n, wl.mu, wl.K(), wl.alpha, wl.dt, o))
+    l0 = sd.sd_launch_count()
     t0 = time.perf_counter()
-    infos = sd.sd_solve_batch(hs, [steps] * count, max_threads=threads)
+    infos = sd.sd_solve_batch(hs, [steps] * count, max_threads=threads, lockstep=lockstep)
     el = time.perf_counter() - t0
+    launches = sd.sd_launch_count() - l0
     dof = sum(wl.dof for wl in wls)
     its = [i["iters"] for inf in infos for i in inf]
     for h in hs:
         sd.sd_destroy(h)
     return {"value": dof * steps / el, "unit": UNIT, "instances": count, "steps_each": steps, "threads": threads,
-            "seconds": el, "total_dof": dof, "grids": sorted(set(wl.n for wl in wls)),
+            "mode": "lockstep groups by grid size" if lockstep else "one stream and host thread per instance",
+            "seconds": el, "total_dof": dof, "grids": sorted(set(wl.n for wl in wls)), "gpu_launches": launches,
             "iters_per_step_mean": float(np.mean(its)), "max_relres": max(i["relres"] for inf in infos for i in inf)}
 
 
@@ -327,10 +352,11 @@ def bench_ours(args, ws, rank, local):
     dof = 4 * n * n + 2 * n
     stream = torch.cuda.Stream()
 
-    # headline: FP32 multigrid inside FP64 FGMRES
+    # headline: FP32 multigrid inside FP64 FGMRES, launch shape and hierarchy autotuned
+    tuned, tune_info = tune_form(sd, n, K, sd.SD_MIXED, stream, not args.no_autotune)
     sampler = ClockSampler(local)
     sampler.start()
-    ms, infos, launches, _ = run_form(sd, torch, n, K, sd.SD_MIXED, steps, warmup, stream)
+    ms, infos, launches, _ = run_form(sd, torch, n, K, sd.SD_MIXED, steps, warmup, stream, tuned=tuned)
     clocks = sampler.stop()
     units, secs = aggregate(dof * steps, ms / 1e3, ws)
     value = units / secs
@@ -345,16 +371,18 @@ def bench_ours(args, ws, rank, local):
                        "parallelism": "replicas only" if ws > 1 else "single instance",
                        "l2": "working set ~2.4 GB per instance, larger than L2 (no flush needed)"},
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-            "iters_per_step": iters, "max_relres": relres, "gpu_launches": launches, "clocks": clocks}
+            "iters_per_step": iters, "max_relres": relres, "gpu_launches": launches, "clocks": clocks,
+            "autotune": tune_info}
 
     if not args.quick:
         # FP64 throughout, same workload
-        ms64, infos64, _, _ = run_form(sd, torch, n, K, sd.SD_FP64, steps, warmup, stream)
+        tuned64, tune64 = tune_form(sd, n, K, sd.SD_FP64, stream, not args.no_autotune)
+        ms64, infos64, _, _ = run_form(sd, torch, n, K, sd.SD_FP64, steps, warmup, stream, tuned=tuned64)
         u64, s64 = aggregate(dof * steps, ms64 / 1e3, ws)
         lat64 = [i["ms"] for i in infos64]
         line["fp64"] = {"value": u64 / s64, "ms_per_step": s64 * 1e3 / steps,
                         "latency_ms": {"p50": float(np.percentile(lat64, 50)), "p99": float(np.percentile(lat64, 99))},
-                        "iters_per_step": [i["iters"] for i in infos64]}
+                        "iters_per_step": [i["iters"] for i in infos64], "autotune": tune64}
         line["mixed_over_fp64"] = value / (u64 / s64)
 
         # roofline: each candidate kernel class is timed live (CUDA events around
@@ -362,7 +390,8 @@ def bench_ours(args, ws, rank, local):
         # time is the dominant kernel
         cands = []
         for kid in (sd.SD_PROF_MUPDATE, sd.SD_PROF_APPLY, sd.SD_PROF_MDOT, sd.SD_PROF_CHEB_V):
-            msk, _, _, prof = run_form(sd, torch, n, K, sd.SD_MIXED, steps, warmup, stream, prof_kernel=kid)
+            msk, _, _, prof = run_form(sd, torch, n, K, sd.SD_MIXED, steps, warmup, stream, prof_kernel=kid,
+                                       tuned=tuned)
             cands.append(roofline_entry(kid, prof, msk))
         cands.sort(key=lambda e: -(e["share_of_step_time"] or 0.0))
         line["roofline"] = cands[0]
@@ -375,6 +404,8 @@ def bench_ours(args, ws, rank, local):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         opts = sd.sd_options_default()
+        for k, v in tuned.items():
+            setattr(opts, k, v)
         h = sd.sd_create(n, 1e-3, Kh, 1.0, 0.05, opts)
         for _ in range(steps):
             sd.sd_step(h, 1)
@@ -389,6 +420,7 @@ def bench_ours(args, ws, rank, local):
         # independent instances (uneven grids) and the serving loop, smaller
         # versions of the batched and serving workloads
         line["batch"] = bench_batch(sd, 64, 10, 16, seed=rank)
+        line["batch"]["per_instance_streams"] = bench_batch(sd, 64, 10, 16, seed=rank, lockstep=False)
         line["serving"] = bench_serve(sd, 50.0, 40, 8)
 
         if rank == 0 and ws >= 1 and not args.no_cpu:
@@ -396,6 +428,88 @@ def bench_ours(args, ws, rank, local):
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
+
+
+def bench_configs(sd, torch, steps_small: int = 10, steps_big: int = 5):
+    """One JSON line per workload that is not the headline: the manufactured case (32^2, FP64, mu = K = alpha = 1,
+    dt = 0.1, 10 steps) and the 2048^2 log-normal case in both precisions with the per-field difference of the
+    mixed-precision solution from the FP64 one."""
+    from paper_2108_13229_gb300 import inputs as I
+    out = []
+    # manufactured solution, FP64 throughout
+    n = 32
+    o = sd.sd_options_default()
+    o.precision = sd.SD_FP64
+    h = sd.sd_create(n, 1.0, np.ones(n * n), 1.0, 0.1, o)
+    sd.sd_step(h, 3)
+    infos = sd.sd_step(h, steps_small)
+    lat = [i["ms"] for i in infos]
+    dof = 4 * n * n + 2 * n
+    out.append({"workload": "manufactured solution 32x32 (4160 DoF), FP64, mu=K=alpha=1, dt=0.1",
+                "value": dof * len(lat) / (sum(lat) / 1e3), "unit": UNIT, "ms_per_step": float(np.mean(lat)),
+                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+                "iters_per_step": [i["iters"] for i in infos], "max_relres": max(i["relres"] for i in infos),
+                "note": "L2-resident and launch-latency bound; parity with the oracle is in tests/"})
+    sd.sd_destroy(h)
+    # 2048^2: mixed vs FP64 from the same initial state
+    n = 2048
+    K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=0)
+    dof = 4 * n * n + 2 * n
+    res, xs = {}, {}
+    for name, prec in (("mixed", sd.SD_MIXED), ("fp64", sd.SD_FP64)):
+        o = sd.sd_options_default()
+        o.precision = prec
+        h = sd.sd_create(n, 1e-3, K, 1.0, 0.05, o)
+        infos = sd.sd_step(h, steps_big)
+        lat = [i["ms"] for i in infos[1:]]
+        res[name] = {"value": dof * len(lat) / (sum(lat) / 1e3), "ms_per_step": float(np.mean(lat)),
+                     "iters_per_step": [i["iters"] for i in infos], "max_relres": max(i["relres"] for i in infos)}
+        xs[name] = sd.sd_get_fields(h)
+        sd.sd_destroy(h)
+    err = {k: float(np.linalg.norm(xs["mixed"][k] - xs["fp64"][k]) / np.linalg.norm(xs["fp64"][k]))
+           for k in xs["fp64"]}
+    out.append({"workload": "lognormal 2048x2048 (%d DoF), mu=1e-3, dt=0.05, %d steps from the initial state, "
+                            "rtol 1e-10" % (dof, steps_big),
+                "unit": UNIT, "mixed": res["mixed"], "fp64": res["fp64"],
+                "mixed_over_fp64": res["mixed"]["value"] / res["fp64"]["value"],
+                "rel_l2_mixed_vs_fp64": err,
+                "note": "first step excluded from the rates (unextrapolated start); both solves reach rtol 1e-10, "
+                        "so the per-field difference is bounded by the conditioning times 1e-10"})
+    return out
+
+
+def oracle_scan(sizes=(32, 64, 128), steps: int = 5, resid_sizes=(1024,)):
+    """The oracle on one host core: banded-LU factorisation and per-step solves at small grids, and the CSR
+    residual evaluator (assembly + one residual) at workload sizes the LU cannot hold."""
+    import oracle as O
+    from paper_2108_13229_gb300 import inputs as I
+    rows = []
+    for n in sizes:
+        K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=0)
+        t0 = time.perf_counter()
+        o = O.Oracle(n, 1e-3, 1.0, 0.05, K)
+        o.factor()
+        t1 = time.perf_counter()
+        o.run(O.exact(n, 0.0, 1e-3), 0.0, steps)
+        t2 = time.perf_counter()
+        dof = 4 * n * n + 2 * n
+        rows.append({"n": n, "dof": dof, "factor_s": t1 - t0, "step_s": (t2 - t1) / steps,
+                     "dof_steps_per_s_steps_only": dof * steps / (t2 - t1),
+                     "dof_steps_per_s_with_factor": dof * steps / (t2 - t0)})
+    for n in resid_sizes:
+        K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=0)
+        t0 = time.perf_counter()
+        o = O.Oracle(n, 1e-3, 1.0, 0.05, K)
+        x = O.exact(n, 0.0, 1e-3)
+        b = o.rhs(x, 0.05)
+        t1 = time.perf_counter()
+        o.residual(x, b)
+        t2 = time.perf_counter()
+        rows.append({"n": n, "dof": 4 * n * n + 2 * n, "assemble_and_rhs_s": t1 - t0, "residual_s": t2 - t1,
+                     "note": "banded LU infeasible (memory); residual evaluator only"})
+    import platform
+    return {"metric": "oracle timing on one host core", "cpu": platform.processor() or platform.machine(),
+            "cores_used": 1, "rows": rows}
 
 
 def peak_probe() -> int:
@@ -416,22 +530,37 @@ def main():
     ap.add_argument("--cpu-n", type=int, default=128)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="headline form only")
+    ap.add_argument("--no-autotune", action="store_true", help="library defaults instead of autotuned options")
     ap.add_argument("--peak-probe", action="store_true", help="measure FP64/FP32 FMA rates and copy bandwidth")
-    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"])
+    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve", "configs", "oracle"])
     ap.add_argument("--count", type=int, default=256, help="batch instances / serving requests")
     ap.add_argument("--threads", type=int, default=32, help="host threads (batch) / running slots (serve)")
     ap.add_argument("--rates", type=float, nargs="*", default=[10.0, 50.0, 200.0])
     args = ap.parse_args()
     if args.peak_probe:
         return peak_probe()
+    if args.mode == "oracle":
+        print(json.dumps(oracle_scan()), flush=True)
+        return 0
+    if args.mode == "configs":
+        import torch
+        from paper_2108_13229_gb300 import sd
+        torch.cuda.set_device(dist_env()[2])
+        for r in bench_configs(sd, torch):
+            r["bench_mode"] = "configs"
+            print(json.dumps(r), flush=True)
+        return 0
     if args.mode in ("batch", "serve"):
         import torch
         from paper_2108_13229_gb300 import sd
         torch.cuda.set_device(dist_env()[2])
         if args.mode == "batch":
-            r = bench_batch(sd, args.count, args.steps if args.steps != 20 else 10, args.threads)
-            r.update({"metric": "batched coupled DOF*steps/s, independent instances of uneven grids", "mode": "batch"})
-            print(json.dumps(r), flush=True)
+            for lockstep in (True, False):
+                r = bench_batch(sd, args.count, args.steps if args.steps != 20 else 10, args.threads,
+                                lockstep=lockstep)
+                r.update({"metric": "batched coupled DOF*steps/s, independent instances of uneven grids",
+                          "bench_mode": "batch"})
+                print(json.dumps(r), flush=True)
         else:
             for rate in args.rates:
                 r = bench_serve(sd, rate, args.count, args.threads)

@@ -115,6 +115,9 @@ typedef struct {
                           of sd_step / sd_solve (default 1) */
   int32_t tile;        /* FP32 V-cycles: all Chebyshev steps of one smoothing in one
                           shared-memory-tiled kernel, prolongation folded in (default 1) */
+  int32_t tile_rows;   /* output rows of one smoothing tile, 8 or 16; 0 (default):
+                          8 on levels up to 1024 cells per side, 16 above;
+                          tiles are 32 faces or cells wide */
   int32_t darcy_coupled; /* SD_TRI_SCHUR: 1 (default) keeps C'_1, the Darcy block follows
                           the velocity; 0 drops it and overlaps the Darcy V-cycle with
                           the Stokes part on a second stream; 2 solves the Darcy block
@@ -188,13 +191,28 @@ int sd_sync(sd_handle *h);
 /* Release the handle and its device memory. */
 void sd_destroy(sd_handle *h);
 
-/* Advance count independent instances concurrently (each on its own stream,
- * one host thread per instance up to max_threads; 0 = one per instance).
- * nsteps[k] steps for hs[k]; infos[k] NULL or nsteps[k] entries.  Each
- * instance's result is identical to running it alone.  Returns the first
- * non-OK status. */
+/* Advance count independent instances (many instances of uneven grid sizes,
+ * permeability fields and alpha_BJ; the batched workload has no counterpart
+ * in the paper, whose solver runs one instance).  nsteps[k] steps for hs[k];
+ * infos[k] NULL or nsteps[k] entries (ms: the step time of hs[k]'s group).
+ *
+ * Handles with the same grid size, mu, dt and options (the stream aside) and
+ * the same nsteps form a lockstep group: every kernel launch of the group
+ * serves all its instances (one instance per blockIdx.z, each instance's
+ * buffers addressed from its own allocation), the Arnoldi steps of the
+ * group are captured as one CUDA graph per basis index, and an instance
+ * that has converged sits idle while the others iterate.  Groups and
+ * single instances run concurrently, each on its own stream, from up to
+ * max_threads host threads (0 = one per group).  Each instance does exactly
+ * the arithmetic of its single-instance sd_step, so its result is bitwise
+ * identical to running it alone.  Returns the first non-OK status.
+ * sd_solve_batch_ex with flags = 0 runs every instance on its own stream
+ * and host thread instead (no lockstep groups). */
+#define SD_BATCH_LOCKSTEP 1
 int sd_solve_batch(sd_handle *const *hs, int32_t count, const int32_t *nsteps, sd_step_info *const *infos,
                    int32_t max_threads);
+int sd_solve_batch_ex(sd_handle *const *hs, int32_t count, const int32_t *nsteps, sd_step_info *const *infos,
+                      int32_t max_threads, int32_t flags);
 
 /* Continuous-batching server: requests are admitted as slots and HBM budget
  * free up and run concurrently; each run keeps its state on the device. */
@@ -264,6 +282,26 @@ int sd_profile_read(sd_handle *h, double *total_ms, int64_t *launches, double *b
 #define SD_NOALLOC_MAX_N 256
 int sd_apply_noalloc(const sd_grid *grid, double mu, const double *K, double alpha_bj, double dt, const double *x,
                      double *y, void *stream);
+
+/* Autotuner: pick tile_rows, coarsest (V-cycle depth) and cheb_degree for
+ * this grid size on the current device by timing.  Each candidate of the
+ * grid {16, 8} rows (FP32 tiled smoothing only) x coarsest {4, 8, 16} x
+ * cheb_degree {3, 2, 4} builds a fresh instance from (grid, mu, K,
+ * alpha_bj, dt) with *base (NULL: defaults) and those three fields, runs 2
+ * untimed and then `nsteps` timed implicit-Euler steps, and is scored by its
+ * mean device time per step; candidates whose steps do not all converge are
+ * dropped.  The tuned choice does not change what is solved: every step
+ * still reaches base->rtol.
+ *   K          host or device permeability as in sd_create;
+ *   cache_path text file (NULL or "": no cache).  A line matching this device,
+ *              n, precision, precond, darcy_coupled, restart and rtol is
+ *              returned without timing; otherwise the winner is appended;
+ *   best       receives *base with the three tuned fields;
+ *   best_ms    (may be NULL) mean device ms per step of the winner.
+ * Costs about 18 instance setups plus 18 (nsteps + 2) steps on a cache miss.
+ * Errors: SD_E_INVAL, SD_E_NOCONV (no candidate converged). */
+int sd_autotune(const sd_grid *grid, double mu, const double *K, double alpha_bj, double dt, const sd_options *base,
+                int32_t nsteps, const char *cache_path, sd_options *best, double *best_ms);
 
 /* Kernel launches made by this library in this process so far (kernels replayed
  * from captured CUDA graphs included). */

@@ -6,6 +6,7 @@
 #include "../../include/sd.h"
 #include "sd_internal.cuh"
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -72,6 +73,7 @@ struct Block {
   T *b = nullptr, *x = nullptr, *x2 = nullptr, *d = nullptr, *r = nullptr;
   T* res = nullptr;          // where the last V-cycle left its result
   std::vector<T> cha, chc;   // Chebyshev step coefficients
+  T* cht = nullptr;          // the same in device memory: a at cht[0..7], c at cht[8..15]
 };
 
 // Coefficient arrays of one level (the Darcy set from K, the pressure
@@ -96,6 +98,7 @@ struct MG {
   double *AinvV = nullptr, *AinvD = nullptr, *AinvP = nullptr;
   int *idxV = nullptr, *idxD = nullptr;
   int mV = 0, mD = 0;
+  T* chtab = nullptr;  // Chebyshev coefficients, 16 per (level, block): a[0..7], c[8..15]
   int fuse_from = -1;  // first level handled by the fused single-CTA coarse cycle
   CoarseCycle<T> cycV, cycD, cycP;
 };
@@ -198,6 +201,7 @@ void plan_mg(sd_handle* h, MG<T>& M, bool own_coef) {
   M.AinvP = a.take<double>((long long)M.mD * M.mD);
   M.idxV = a.take<int>(M.mV);
   M.idxD = a.take<int>(M.mD);
+  M.chtab = a.take<T>((long long)h->nlev * 3 * 16);
 }
 
 void plan_all(sd_handle* h) {
@@ -389,6 +393,24 @@ int setup_mg(sd_handle* h, MG<T>& M) {
     cheb_coeffs<T>(ld, h->opt.cheb_ratio, dl, M.L[l].D.cha, M.L[l].D.chc);
     cheb_coeffs<T>(lp, h->opt.cheb_ratio, dp, M.L[l].Pb.cha, M.L[l].Pb.chc);
   }
+  // the same coefficients in device memory: a lockstep batch reads each
+  // instance's own (they differ with the spectrum of its operator)
+  {
+    std::vector<T> tab((size_t)h->nlev * 3 * 16, T(0));
+    for (int l = 0; l + 1 < h->nlev; ++l) {
+      Block<T>* bl[3] = {&M.L[l].V, &M.L[l].D, &M.L[l].Pb};
+      for (int q = 0; q < 3; ++q) {
+        T* row = tab.data() + ((size_t)l * 3 + q) * 16;
+        for (int k = 0; k < (int)bl[q]->cha.size() && k < 8; ++k) {
+          row[k] = bl[q]->cha[k];
+          row[8 + k] = bl[q]->chc[k];
+        }
+        bl[q]->cht = M.chtab + ((size_t)l * 3 + q) * 16;
+      }
+    }
+    CK(cudaMemcpyAsync(M.chtab, tab.data(), sizeof(T) * tab.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  }
   M.fuse_from = -1;
   if (h->opt.fuse_coarse) {
     auto fill = [&](CoarseCycle<T>& q, int kind, int which, int f) {
@@ -400,6 +422,7 @@ int setup_mg(sd_handle* h, MG<T>& M) {
         q.c[l - f] = which == 2 ? L.cP : L.c;
         Block<T>& B = which == 0 ? L.V : (which == 1 ? L.D : L.Pb);
         q.deg[l - f] = (int)B.cha.size();
+        q.cht[l - f] = l + 1 < h->nlev ? B.cht : nullptr;
         for (int k = 0; k < (int)B.cha.size() && k < 8 && l + 1 < h->nlev; ++k) {
           q.cha[l - f][k] = B.cha[k];
           q.chc[l - f][k] = B.chc[k];
@@ -491,15 +514,23 @@ double apply_bytes(const Geom& g, bool resid) {
 
 // ----------------------------------------------------------- V-cycles
 template <typename T>
-ChebSteps<T> steps_of(const Block<T>& B) {
+ChebSteps<T> steps_of(const Block<T>& B, int rows) {
   ChebSteps<T> cs;
   std::memset(&cs, 0, sizeof(cs));
   cs.ns = (int)B.cha.size();
+  cs.rows = rows;
   for (int k = 0; k < cs.ns && k < 8; ++k) {
     cs.a[k] = B.cha[k];
     cs.c[k] = B.chc[k];
   }
   return cs;
+}
+
+// smoothing tile height of a level with n cells per side: the option, or by
+// default 8 rows up to n = 1024 (more CTAs in flight) and 16 above (less halo)
+int tile_rows_of(const sd_handle* h, int n) {
+  if (h->opt.tile_rows) return h->opt.tile_rows;
+  return n <= 1024 ? 8 : 16;
 }
 
 // tiled smoothing (all steps of one smoothing in one kernel) is used for the
@@ -528,17 +559,18 @@ void vcycle_V(MG<T>& M, int l, cudaStream_t s, sd_handle* prof_owner) {
   MGLevel<T>& C = M.L[l + 1];
   T* cur = nullptr;
   const bool tiles = use_tiles(prof_owner, B);
+  const int h_tile_rows = tile_rows_of(prof_owner, L.g.n);
   if (tiles) {
     ProfScope ps(prof_owner, l == 0 ? SD_PROF_CHEB_V : -2, tile_bytes_V(L.g, sizeof(T), false));
     if constexpr (std::is_same<T, float>::value)
-      launch_smooth_tile_V<T>(L.c, nullptr, B.b, B.x, steps_of(B), nullptr, 0, 0, s);
+      launch_smooth_tile_V<T>(L.c, nullptr, B.b, B.x, steps_of(B, h_tile_rows), B.cht, nullptr, 0, 0, s);
     cur = B.x;
   } else {
     for (int k = 0; k < (int)B.cha.size(); ++k) {
       T* out = (cur == B.x) ? B.x2 : B.x;
       {
         ProfScope ps(prof_owner, l == 0 ? SD_PROF_CHEB_V : -2, cheb_bytes_V(L.g, sizeof(T), cur != nullptr, k > 0));
-        launch_cheb_V<T>(L.c, cur, B.b, B.d, out, B.cha[k], B.chc[k], 1, 0, s);
+        launch_cheb_V<T>(L.c, cur, B.b, B.d, out, B.cha[k], B.chc[k], B.cht ? B.cht + k : nullptr, 1, 0, s);
       }
       cur = out;
     }
@@ -550,7 +582,7 @@ void vcycle_V(MG<T>& M, int l, cudaStream_t s, sd_handle* prof_owner) {
     T* out = (cur == B.x) ? B.x2 : B.x;
     ProfScope ps(prof_owner, l == 0 ? SD_PROF_CHEB_V : -2, tile_bytes_V(L.g, sizeof(T), true));
     if constexpr (std::is_same<T, float>::value)
-      launch_smooth_tile_V<T>(L.c, cur, B.b, out, steps_of(B), C.V.res, C.g.n, C.g.P, s);
+      launch_smooth_tile_V<T>(L.c, cur, B.b, out, steps_of(B, h_tile_rows), B.cht, C.V.res, C.g.n, C.g.P, s);
     cur = out;
   } else {
     launch_prolong_V<T>(L.g.n, L.g.P, cur, C.g.n, C.g.P, C.V.res, s);
@@ -558,7 +590,7 @@ void vcycle_V(MG<T>& M, int l, cudaStream_t s, sd_handle* prof_owner) {
       T* out = (cur == B.x) ? B.x2 : B.x;
       {
         ProfScope ps(prof_owner, l == 0 ? SD_PROF_CHEB_V : -2, cheb_bytes_V(L.g, sizeof(T), true, k > 0));
-        launch_cheb_V<T>(L.c, cur, B.b, B.d, out, B.cha[k], B.chc[k], 1, 0, s);
+        launch_cheb_V<T>(L.c, cur, B.b, B.d, out, B.cha[k], B.chc[k], B.cht ? B.cht + k : nullptr, 1, 0, s);
       }
       cur = out;
     }
@@ -586,14 +618,15 @@ void vcycle_cell(MG<T>& M, int l, bool poisson, cudaStream_t s, const sd_handle*
   Block<T>& BC = poisson ? C.Pb : C.D;
   T* cur = nullptr;
   const bool tiles = use_tiles(h, B);
+  const int h_tile_rows = tile_rows_of(h, L.g.n);
   if (tiles) {
     if constexpr (std::is_same<T, float>::value)
-      launch_smooth_tile_D<T>(c, nullptr, B.b, B.x, steps_of(B), nullptr, 0, 0, s);
+      launch_smooth_tile_D<T>(c, nullptr, B.b, B.x, steps_of(B, h_tile_rows), B.cht, nullptr, 0, 0, s);
     cur = B.x;
   } else {
     for (int k = 0; k < (int)B.cha.size(); ++k) {
       T* out = (cur == B.x) ? B.x2 : B.x;
-      launch_cheb_D<T>(c, cur, B.b, B.d, out, B.cha[k], B.chc[k], 1, 0, s);
+      launch_cheb_D<T>(c, cur, B.b, B.d, out, B.cha[k], B.chc[k], B.cht ? B.cht + k : nullptr, 1, 0, s);
       cur = out;
     }
   }
@@ -602,13 +635,13 @@ void vcycle_cell(MG<T>& M, int l, bool poisson, cudaStream_t s, const sd_handle*
   if (tiles) {  // prolongation folded into the post-smoothing tile load
     T* out = (cur == B.x) ? B.x2 : B.x;
     if constexpr (std::is_same<T, float>::value)
-      launch_smooth_tile_D<T>(c, cur, B.b, out, steps_of(B), BC.res, C.g.n, C.g.P, s);
+      launch_smooth_tile_D<T>(c, cur, B.b, out, steps_of(B, h_tile_rows), B.cht, BC.res, C.g.n, C.g.P, s);
     cur = out;
   } else {
     launch_prolong_D<T>(L.g.n, L.g.P, cur, C.g.n, C.g.P, BC.res, s);
     for (int k = 0; k < (int)B.cha.size(); ++k) {
       T* out = (cur == B.x) ? B.x2 : B.x;
-      launch_cheb_D<T>(c, cur, B.b, B.d, out, B.cha[k], B.chc[k], 1, 0, s);
+      launch_cheb_D<T>(c, cur, B.b, B.d, out, B.cha[k], B.chc[k], B.cht ? B.cht + k : nullptr, 1, 0, s);
       cur = out;
     }
   }
@@ -809,8 +842,8 @@ int fgmres(sd_handle* h, const double* b, double* x, sd_step_info* info) {
       if (h->hflag[0] <= tol || h->hflag[3] != 0.0 || iters >= h->opt.max_iters) break;
     }
     if (numeric) { status = SD_E_NUMERIC; break; }
-    launch_backsolve(h->st, k, m, sc + sd_handle::S_Y, s);
-    launch_axpy_multi(x, h->Z, vs, sc + sd_handle::S_Y, k, len, s);
+    launch_backsolve(h->st, k, m, sc + sd_handle::S_Y, nullptr, s);
+    launch_axpy_multi(x, h->Z, vs, sc + sd_handle::S_Y, k, len, nullptr, s);
   }
   CK(cudaGetLastError());
   if (info) {
@@ -821,6 +854,23 @@ int fgmres(sd_handle* h, const double* b, double* x, sd_step_info* info) {
     info->reorths = reorths;
   }
   return status;
+}
+
+// Right-hand side and initial guess of the next implicit-Euler step, queued on s.
+int step_rhs(sd_handle* h, cudaStream_t s) {
+  const double cm = h->g.h * h->g.h / h->dt;
+  const double tn = h->t + h->dt;
+  if (h->opt.extrapolate && h->have_prev) {
+    // initial guess 2 x^n - x^{n-1}; x_m then holds x^n, the mass-term source
+    launch_extrapolate(h->x, h->xm, h->g.len, s);
+    launch_rhs(h->g, cm, h->B0, h->B1, 1.0 + tn, h->xm, h->b, h->x, s);
+  } else {
+    // the previous state is both the mass-term source and the initial guess
+    CK(cudaMemcpyAsync(h->xm, h->x, sizeof(double) * h->g.len, cudaMemcpyDeviceToDevice, s));
+    launch_rhs(h->g, cm, h->B0, h->B1, 1.0 + tn, h->x, h->b, h->x, s);
+  }
+  h->have_prev = true;
+  return SD_OK;
 }
 
 int copy_in_dense(sd_handle* h, const double* src, long long count) {
@@ -846,6 +896,7 @@ int validate(const sd_grid* grid, double mu, double alpha, double dt, const sd_o
     return SD_E_INVAL;
   if (o->orth < 0 || o->orth > 1 || !(o->reorth_eta > 0) || o->reorth_eta > 1) return SD_E_INVAL;
   if (o->darcy_coupled < 0 || o->darcy_coupled > 2) return SD_E_INVAL;
+  if (o->tile_rows != 0 && o->tile_rows != 8 && o->tile_rows != 16) return SD_E_INVAL;
   if (o->cheb_degree_coarse < 0 || o->cheb_degree_coarse > 8 || o->schur_degree < 0 || o->schur_degree > 8)
     return SD_E_INVAL;
   int n = grid->nx, L = level_count(n, o->coarsest);
@@ -947,6 +998,260 @@ int create_impl(const sd_grid* grid, double mu, const double* K, double alpha, d
 
 }  // namespace
 
+// ====================================================== lockstep batches
+// Instances with the same grid, viscosity, time step and options have
+// buffers at the same offsets inside their allocations, so one launch can
+// serve all of them (Bat in sd_internal.cuh): blockIdx.z picks the instance
+// and every pointer of instance 0 is moved by that instance's offset.  The
+// FGMRES iterations run in lockstep: each Arnoldi step is one captured graph
+// for the whole batch, and an instance that has met its own stopping test
+// is made idle (its blocks return at once) while the others go on.  Every
+// instance does exactly the arithmetic of its single-instance solve (same
+// per-instance reductions, same coefficients), so its result is bitwise the
+// same.
+namespace sdk {
+
+bool can_lockstep(const sd_handle* a, const sd_handle* b) {
+  const sd_options& x = a->opt;
+  const sd_options& y = b->opt;
+  const bool same_opt = x.restart == y.restart && x.rtol == y.rtol && x.max_iters == y.max_iters &&
+                        x.precision == y.precision && x.precond == y.precond && x.bc == y.bc &&
+                        x.cheb_degree == y.cheb_degree && x.cheb_degree_coarse == y.cheb_degree_coarse &&
+                        x.schur_degree == y.schur_degree && x.coarsest == y.coarsest &&
+                        x.schur_gamma == y.schur_gamma && x.cheb_ratio == y.cheb_ratio &&
+                        x.schur_mass == y.schur_mass && x.fuse_coarse == y.fuse_coarse && x.orth == y.orth &&
+                        x.reorth_eta == y.reorth_eta && x.extrapolate == y.extrapolate && x.graph == y.graph &&
+                        x.pdl == y.pdl && x.tile == y.tile && x.tile_rows == y.tile_rows &&
+                        x.darcy_coupled == y.darcy_coupled;
+  return same_opt && a->n == b->n && a->mu == b->mu && a->dt == b->dt && a->ar.off == b->ar.off &&
+         a->nlev == b->nlev && a->prof_id < 0 && b->prof_id < 0;
+}
+
+namespace {
+
+struct Lockstep {
+  std::vector<sd_handle*> hs;
+  int B = 0;
+  long long* off_dev = nullptr;
+  int* act_dev = nullptr;
+  double* gat_dev = nullptr;
+  double* gat_host = nullptr;  // pinned
+  std::vector<int> act;
+  std::vector<cudaGraphExec_t> gexec;
+  std::vector<long long> gcount;
+  ~Lockstep() {
+    for (auto& g : gexec)
+      if (g) cudaGraphExecDestroy(g);
+    if (off_dev) cudaFree(off_dev);
+    if (act_dev) cudaFree(act_dev);
+    if (gat_dev) cudaFree(gat_dev);
+    if (gat_host) cudaFreeHost(gat_host);
+  }
+};
+
+// makes the calling thread's launches serve the whole batch
+struct BatScope {
+  Bat saved;
+  int saved_n;
+  BatScope(const Lockstep& L) : saved(t_bat), saved_n(t_bat_n) {
+    t_bat.off = L.off_dev;
+    t_bat.act = L.act_dev;
+    t_bat_n = L.B;
+  }
+  ~BatScope() {
+    t_bat = saved;
+    t_bat_n = saved_n;
+  }
+};
+
+// upload the idle mask (from pageable memory: the copy has taken the data
+// when the call returns)
+int set_act(Lockstep& L, cudaStream_t s) {
+  CK(cudaMemcpyAsync(L.act_dev, L.act.data(), sizeof(int) * L.B, cudaMemcpyHostToDevice, s));
+  return SD_OK;
+}
+
+// every instance's src[0..count) into L.gat_host[z * count + t]
+int gather(Lockstep& L, const double* src, int count, cudaStream_t s) {
+  launch_gather_inst(src, count, L.gat_dev, s);
+  CK(cudaMemcpyAsync(L.gat_host, L.gat_dev, sizeof(double) * count * L.B, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return SD_OK;
+}
+
+int fgmres_lockstep(Lockstep& L, std::vector<sd_step_info>& si) {
+  sd_handle* h = L.hs[0];
+  cudaStream_t s = h->s;
+  const int B = L.B;
+  const long long len = h->g.len, vs = h->lenA;
+  const int m = h->m, nb = h->nblk;
+  const Coef<double> c = coef64(h, 0);
+  double* sc = h->scal;
+  BatScope bs(L);
+  std::vector<int> iters(B, 0), restarts(B, 0), reorths(B, 0), status(B, SD_OK);
+  std::vector<double> relres(B, 0.0), bnorm(B), tol(B);
+  std::vector<char> live(B, 1), cyc(B, 0), numeric(B, 0);
+  L.act.assign(B, 1);
+  CKR(set_act(L, s));
+  launch_dot(h->b, h->b, len, h->partial, nb, sc + sd_handle::S_BN, s);
+  CKR(gather(L, sc + sd_handle::S_BN, 1, s));
+  for (int i = 0; i < B; ++i) {
+    bnorm[i] = std::sqrt(L.gat_host[i]);
+    tol[i] = h->opt.rtol * (bnorm[i] > 0 ? bnorm[i] : 1.0);
+  }
+  for (;;) {
+    for (int i = 0; i < B; ++i) L.act[i] = live[i];
+    CKR(set_act(L, s));
+    launch_apply_full(c, h->x, h->b, h->V, s);  // V_0 = b - A x
+    launch_dot(h->V, h->V, len, h->partial, nb, sc + sd_handle::S_B2, s);
+    CKR(gather(L, sc + sd_handle::S_B2, 1, s));
+    bool any = false;
+    for (int i = 0; i < B; ++i) {
+      cyc[i] = 0;
+      if (!live[i]) continue;
+      const double beta = std::sqrt(L.gat_host[i]);
+      relres[i] = bnorm[i] > 0 ? beta / bnorm[i] : beta;
+      if (!std::isfinite(beta)) { status[i] = SD_E_NUMERIC; live[i] = 0; continue; }
+      if (beta <= tol[i]) { live[i] = 0; continue; }
+      if (iters[i] >= h->opt.max_iters) { status[i] = SD_E_NOCONV; live[i] = 0; continue; }
+      cyc[i] = 1;
+      restarts[i] += 1;
+      any = true;
+    }
+    if (!any) break;
+    for (int i = 0; i < B; ++i) L.act[i] = cyc[i];
+    CKR(set_act(L, s));
+    launch_init_cycle(h->st, m, sc + sd_handle::S_B2, h->flag, s);
+    launch_scale_by(h->V, h->V, len, h->flag + 1, 0, s);
+    for (int j = 0; j < m; ++j) {
+      double* vj = h->V + (long long)j * vs;
+      double* zj = h->Z + (long long)j * vs;
+      double* w = h->V + (long long)(j + 1) * vs;
+      if (h->opt.graph) {
+        if (!L.gexec[j]) {
+          cudaGraph_t gr = nullptr;
+          const long long l0 = t_launch_count;
+          CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+          arnoldi_orth(h, j, vj, zj, w);
+          launch_scale_by(w, w, len, h->flag + 1, 0, s);
+          CK(cudaStreamEndCapture(s, &gr));
+          const cudaError_t ie = cudaGraphInstantiate(&L.gexec[j], gr, 0);
+          cudaGraphDestroy(gr);
+          CK(ie);
+          L.gcount[j] = t_launch_count - l0;
+          g_launch_count.fetch_sub(L.gcount[j]);
+        }
+        CK(cudaGraphLaunch(L.gexec[j], s));
+        g_launch_count.fetch_add(L.gcount[j]);
+      } else {
+        arnoldi_orth(h, j, vj, zj, w);
+        launch_scale_by(w, w, len, h->flag + 1, 0, s);
+      }
+      CKR(gather(L, h->flag, 6, s));
+      bool running = false;
+      for (int i = 0; i < B; ++i) {
+        if (!L.act[i]) continue;
+        const double* f = L.gat_host + (size_t)i * 6;
+        iters[i] += 1;
+        reorths[i] += f[4] != 0.0 ? 1 : 0;
+        if (f[2] != 0.0) {
+          numeric[i] = 1;
+          L.act[i] = 0;
+        } else if (f[0] <= tol[i] || f[3] != 0.0 || iters[i] >= h->opt.max_iters) {
+          L.act[i] = 0;
+        } else {
+          running = true;
+        }
+      }
+      if (!running) break;
+      CKR(set_act(L, s));
+    }
+    // solution update of every instance that took part in the cycle, each
+    // with its own number of basis vectors (flag[5], written by k_givens)
+    for (int i = 0; i < B; ++i) {
+      if (numeric[i]) {
+        status[i] = SD_E_NUMERIC;
+        live[i] = 0;
+        cyc[i] = 0;
+      }
+      L.act[i] = cyc[i];
+    }
+    CKR(set_act(L, s));
+    launch_backsolve(h->st, m, m, sc + sd_handle::S_Y, h->flag + 5, s);
+    launch_axpy_multi(h->x, h->Z, vs, sc + sd_handle::S_Y, m, len, h->flag + 5, s);
+  }
+  CK(cudaGetLastError());
+  for (int i = 0; i < B; ++i) {
+    si[i].iters = iters[i];
+    si[i].restarts = restarts[i];
+    si[i].relres = relres[i];
+    si[i].status = status[i];
+    si[i].reorths = reorths[i];
+  }
+  return SD_OK;
+}
+
+}  // namespace
+
+int step_lockstep(sd_handle* const* hs, int count, int nsteps, sd_step_info* const* infos) {
+  if (count < 1 || nsteps < 0) return SD_E_INVAL;
+  for (int i = 1; i < count; ++i)
+    if (!can_lockstep(hs[0], hs[i])) return SD_E_INVAL;
+  std::vector<sd_handle*> order(hs, hs + count);
+  std::sort(order.begin(), order.end());
+  if (std::adjacent_find(order.begin(), order.end()) != order.end()) return SD_E_INVAL;  // no handle twice
+  std::vector<std::unique_lock<std::mutex>> locks;
+  for (sd_handle* h : order) locks.emplace_back(h->mtx);
+  Lockstep L;
+  L.hs.assign(hs, hs + count);
+  L.B = count;
+  sd_handle* h0 = hs[0];
+  cudaStream_t s = h0->s;
+  t_pdl = h0->opt.pdl;
+  std::vector<long long> off(count);
+  for (int i = 0; i < count; ++i) {
+    off[i] = (long long)(reinterpret_cast<uintptr_t>(hs[i]->ar.base) - reinterpret_cast<uintptr_t>(h0->ar.base));
+    CK(cudaStreamSynchronize(hs[i]->s));  // nothing of an instance may still run on its own stream
+  }
+  CK(cudaMalloc(&L.off_dev, sizeof(long long) * count));
+  CK(cudaMalloc(&L.act_dev, sizeof(int) * count));
+  CK(cudaMalloc(&L.gat_dev, sizeof(double) * 8 * count));
+  CK(cudaHostAlloc(&L.gat_host, sizeof(double) * 8 * count, cudaHostAllocDefault));
+  CK(cudaMemcpyAsync(L.off_dev, off.data(), sizeof(long long) * count, cudaMemcpyHostToDevice, s));
+  L.gexec.assign(h0->m, nullptr);
+  L.gcount.assign(h0->m, 0);
+  int first = SD_OK;
+  std::vector<sd_step_info> si(count);
+  t_bat_misuse = 0;
+  for (int k = 0; k < nsteps; ++k) {
+    CK(cudaEventRecord(h0->e0, s));
+    for (int i = 0; i < count; ++i) CKR(step_rhs(hs[i], s));  // single-instance launches on the batch stream
+    std::memset(si.data(), 0, sizeof(sd_step_info) * count);
+    const int rc = fgmres_lockstep(L, si);
+    if (rc != SD_OK) return rc;
+    if (t_bat_misuse) {
+      snprintf(g_errmsg, sizeof(g_errmsg), "a kernel without batch support was launched in a lockstep batch");
+      return SD_E_STATE;
+    }
+    CK(cudaEventRecord(h0->e1, s));
+    CK(cudaEventSynchronize(h0->e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h0->e0, h0->e1));
+    for (int i = 0; i < count; ++i) {
+      sd_handle* h = hs[i];
+      h->t += h->dt;
+      h->step += 1;
+      si[i].ms = ms;
+      if (infos && infos[i]) infos[i][k] = si[i];
+      if (si[i].status != SD_OK && first == SD_OK) first = si[i].status;
+    }
+  }
+  CK(cudaStreamSynchronize(s));
+  return first;
+}
+
+}  // namespace sdk
+
 // ================================================================ C ABI
 extern "C" {
 
@@ -970,6 +1275,7 @@ void sd_options_default(sd_options* o) {
   o->graph = 1;
   o->pdl = 1;
   o->tile = 1;
+  o->tile_rows = 0;
   o->darcy_coupled = 1;
   o->schur_gamma = 0.5;
   o->cheb_ratio = 8.0;
@@ -1004,20 +1310,10 @@ int sd_step(sd_handle* h, int32_t nsteps, sd_step_info* info) {
   std::lock_guard<std::mutex> lk(h->mtx);
   t_pdl = h->opt.pdl;
   int first = SD_OK;
-  const double cm = h->g.h * h->g.h / h->dt;
   for (int k = 0; k < nsteps; ++k) {
     const double tn = h->t + h->dt;
     CK(cudaEventRecord(h->e0, h->s));
-    if (h->opt.extrapolate && h->have_prev) {
-      // initial guess 2 x^n - x^{n-1}; x_m then holds x^n, the mass-term source
-      launch_extrapolate(h->x, h->xm, h->g.len, h->s);
-      launch_rhs(h->g, cm, h->B0, h->B1, 1.0 + tn, h->xm, h->b, h->x, h->s);
-    } else {
-      // the previous state is both the mass-term source and the initial guess
-      CK(cudaMemcpyAsync(h->xm, h->x, sizeof(double) * h->g.len, cudaMemcpyDeviceToDevice, h->s));
-      launch_rhs(h->g, cm, h->B0, h->B1, 1.0 + tn, h->x, h->b, h->x, h->s);
-    }
-    h->have_prev = true;
+    CKR(step_rhs(h, h->s));
     sd_step_info si;
     std::memset(&si, 0, sizeof(si));
     const int rc = fgmres(h, h->b, h->x, &si);

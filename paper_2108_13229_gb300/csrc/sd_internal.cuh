@@ -17,6 +17,8 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <type_traits>
+#include <utility>
 
 namespace sdk {
 
@@ -30,6 +32,48 @@ namespace sdk {
 extern thread_local int t_pdl;
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Lockstep batches (sd_solve_batch): instances whose buffers have identical
+// layouts run in the same launches, one instance per blockIdx.z.  Every
+// buffer of instance z is the same buffer of instance 0 moved by off[z]
+// bytes (each instance's buffers come from one allocation laid out by the
+// same plan), and act[z] == 0 makes the blocks of instance z return at once
+// (instances that have converged wait for the others).  Kernels that take a
+// Bat as their last parameter get it from launch_k: the calling host
+// thread's t_bat, with the grid's z extent multiplied by t_bat_n.  With
+// off == null (a single instance) nothing moves and blockIdx.z keeps any
+// meaning the kernel gives it.
+struct Bat {
+  const long long* off;
+  const int* act;
+};
+extern thread_local Bat t_bat;
+extern thread_local int t_bat_n;
+// set when a kernel without batch support is launched while t_bat is active
+// (it would serve instance 0 only); the batch driver reports it
+extern thread_local int t_bat_misuse;
+
+// Byte offset of this block's instance; false if the instance is idle.
+// Call after griddep_wait() (act is written by the host between launches).
+__device__ __forceinline__ bool bat_enter(const Bat& b, long long& o) {
+  o = 0;
+  if (!b.off) return true;
+  const int z = blockIdx.z;
+  if (b.act && b.act[z] == 0) return false;
+  o = b.off[z];
+  return true;
+}
+template <typename P>
+__device__ __forceinline__ P bsh(P p, long long o) {
+  return p ? reinterpret_cast<P>(reinterpret_cast<uintptr_t>(p) + o) : p;
+}
+
+template <typename... Ts>
+struct last_is_bat : std::false_type {};
+template <typename T>
+struct last_is_bat<T> : std::is_same<typename std::decay<T>::type, Bat> {};
+template <typename T, typename U, typename... Ts>
+struct last_is_bat<T, U, Ts...> : last_is_bat<U, Ts...> {};
+
 template <typename... KArgs, typename... Args>
 inline void launch_k(void (*kern)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t s, Args&&... args) {
   cudaLaunchConfig_t cfg = {};
@@ -42,7 +86,13 @@ inline void launch_k(void (*kern)(KArgs...), dim3 g, dim3 b, size_t smem, cudaSt
   attr[0].val.programmaticStreamSerializationAllowed = t_pdl ? 1 : 0;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+  if constexpr (last_is_bat<KArgs...>::value) {
+    if (t_bat.off) cfg.gridDim.z *= (unsigned)t_bat_n;
+    cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)..., t_bat);
+  } else {
+    if (t_bat.off) t_bat_misuse = 1;
+    cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+  }
 }
 
 // process-wide count of kernel launches made by this library (and the same
@@ -103,6 +153,15 @@ inline void finish_coef(Coef<T>& c) {
   c.m2 = T(-2) * c.mu;
 }
 
+// the coefficient arrays of a Coef moved to another instance of a batch
+template <typename T>
+__device__ __forceinline__ void bsh_coef(Coef<T>& c, long long o) {
+  c.w = bsh(c.w, o);
+  c.rg = bsh(c.rg, o);
+  c.Tx = bsh(c.Tx, o);
+  c.Ty = bsh(c.Ty, o);
+}
+
 // ---------------------------------------------------------------- sd_ops.cu
 // setup
 void launch_coarsen_K(const double* Kf, int nf, int Pf, double* Kc, int Pc, cudaStream_t s);
@@ -135,11 +194,13 @@ void launch_unpack(const Geom& g, const double* padded, double* dense, cudaStrea
 //   block D: Darcy rows p_pm
 // Chebyshev step: d = a d + c D^-1 (b - A x_in); x_out = x_in + d.
 //   x_in == nullptr means x_in = 0;  a == 0 means d is not read.
+//   ck (may be null): the same a, c in device memory (a = ck[0], c = ck[8]),
+//   read instead in a lockstep batch, where they differ per instance.
 template <typename T>
-void launch_cheb_V(const Coef<T>& c, const T* x_in, const T* b, T* d, T* x_out, T a, T cc, int nbatch,
+void launch_cheb_V(const Coef<T>& c, const T* x_in, const T* b, T* d, T* x_out, T a, T cc, const T* ck, int nbatch,
                    long long bstride, cudaStream_t s);
 template <typename T>
-void launch_cheb_D(const Coef<T>& c, const T* x_in, const T* b, T* d, T* x_out, T a, T cc, int nbatch,
+void launch_cheb_D(const Coef<T>& c, const T* x_in, const T* b, T* d, T* x_out, T a, T cc, const T* ck, int nbatch,
                    long long bstride, cudaStream_t s);
 // mode 0: r = b - A x (b == nullptr: r = -A x); 1: r = D^-1 A x; 2: r = A x
 template <typename T>
@@ -171,6 +232,7 @@ struct CoarseCycle {
   int deg[SD_CYC_MAXL];  // Chebyshev steps per smoothing on each level
   Coef<T> c[SD_CYC_MAXL];
   T cha[SD_CYC_MAXL][8], chc[SD_CYC_MAXL][8];
+  const T* cht[SD_CYC_MAXL];  // the same coefficients in device memory (a at 0..7, c at 8..15)
   const double* Ainv;
   const int* idx;
   const T* b_in;  // entry-level right-hand side (global, padded layout)
@@ -189,17 +251,19 @@ int prepare_coarse_cycle();
 template <typename T>
 struct ChebSteps {
   int ns;
+  int rows;  // tiled smoothing: output rows per tile (8 or 16)
   T a[8], c[8];
 };
 // Tiled smoothing: ns Chebyshev steps in one kernel, x_out = S(x_in + P ec)
 // (x_in null: from zero; ec null: no prolongation).  FP32 only; returns -1
-// (nothing launched) for ns > 4.
+// (nothing launched) for ns > 4.  ct: the coefficients of cs in device
+// memory (a at 0..7, c at 8..15), read instead in a lockstep batch.
 template <typename T>
-int launch_smooth_tile_D(const Coef<T>& c, const T* x_in, const T* b, T* x_out, const ChebSteps<T>& cs, const T* ec,
-                         int nc, int Pc, cudaStream_t s);
+int launch_smooth_tile_D(const Coef<T>& c, const T* x_in, const T* b, T* x_out, const ChebSteps<T>& cs, const T* ct,
+                         const T* ec, int nc, int Pc, cudaStream_t s);
 template <typename T>
-int launch_smooth_tile_V(const Coef<T>& c, const T* x_in, const T* b, T* x_out, const ChebSteps<T>& cs, const T* ec,
-                         int nc, int Pc, cudaStream_t s);
+int launch_smooth_tile_V(const Coef<T>& c, const T* x_in, const T* b, T* x_out, const ChebSteps<T>& cs, const T* ct,
+                         const T* ec, int nc, int Pc, cudaStream_t s);
 
 // preconditioner glue on the fine level (Sec. 4 block preconditioners):
 //  entry: zpf = schur * r_pf + cmass * eP (eP: pressure-Laplacian solve, may be
@@ -240,14 +304,18 @@ void launch_dot(const double* a, const double* b, long long len, double* partial
                 cudaStream_t s);
 // y = alpha_dev[0]^p * x  (p = -1: divide by sqrt(alpha) ... see implementation)
 void launch_scale_by(const double* x, double* y, long long len, const double* sdev, int mode, cudaStream_t s);
+// (kdev, may be null: in a lockstep batch each instance's k is kdev[0])
 void launch_axpy_multi(double* x, const double* Z, long long zstride, const double* ycoef, int k, long long len,
-                       cudaStream_t s);
+                       const double* kdev, cudaStream_t s);
 
 //   the new column is hcol1 + hcol2; its sub-diagonal is sqrt(nrm2b) if reo is null
-//   or reo[0] != 0 (second Gram-Schmidt pass done), else sqrt(nrm2a)
+//   or reo[0] != 0 (second Gram-Schmidt pass done), else sqrt(nrm2a);
+//   flag[5] = j + 1, the basis vectors of the cycle so far
 void launch_givens(double* st, int j, int m, const double* hcol1, const double* hcol2, const double* nrm2a,
                    const double* nrm2b, const double* reo, double* flag, cudaStream_t s);
-void launch_backsolve(double* st, int k, int m, double* y, cudaStream_t s);
+void launch_backsolve(double* st, int k, int m, double* y, const double* kdev, cudaStream_t s);
+// lockstep batches: out[z * count + t] = instance z's src[t]
+void launch_gather_inst(const double* src, int count, double* out, cudaStream_t s);
 void launch_init_cycle(double* st, int m, const double* beta2, double* flag, cudaStream_t s);
 
 // dense coarse solve: x[idx[k]] = T(sum_l Ainv[k][l] * b[idx[l]])
@@ -260,5 +328,16 @@ void launch_identity_batch(double* X, long long stride, const int* idx, int m, c
 void launch_gather_dense(const double* Y, long long stride, const int* idx, int m, double* A, cudaStream_t s);
 void launch_fill(double* x, double v, long long len, cudaStream_t s);
 void launch_hash_fill(double* x, long long len, unsigned seed, cudaStream_t s);
+
+#ifdef SD_H
+// ------------------------------------------------- lockstep batches (sd_api.cu)
+// true if b can run in the same launches as a (same grid, mu, dt, options and
+// buffer layout; no kernel timing active)
+bool can_lockstep(const sd_handle* a, const sd_handle* b);
+// nsteps implicit-Euler steps of count mutually compatible handles in lockstep
+// on the first handle's stream; infos[i] (may be null) receives instance i's
+// per-step information.  Returns the first non-OK step status.
+int step_lockstep(sd_handle* const* hs, int count, int nsteps, sd_step_info* const* infos);
+#endif
 
 }  // namespace sdk

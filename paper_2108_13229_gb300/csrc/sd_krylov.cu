@@ -20,6 +20,9 @@ namespace sdk {
 std::atomic<long long> g_launch_count{0};
 thread_local long long t_launch_count = 0;
 thread_local int t_pdl = 0;
+thread_local Bat t_bat = {nullptr, nullptr};
+thread_local int t_bat_n = 1;
+thread_local int t_bat_misuse = 0;
 
 static const int RT = 256;       // threads per reduction / update block
 static const int KT = 128;       // threads per Gram-Schmidt block
@@ -76,8 +79,16 @@ __device__ __forceinline__ void load_own(const double* __restrict__ w, double* w
 // with self != 0 also w . w as entry k.  cond (may be null): skip when 0.
 __global__ void __launch_bounds__(KT) k_mdot(const double* __restrict__ V, long long vs, int k,
                                              const double* __restrict__ w, long long len, double* __restrict__ partial,
-                                             int ps, int self, const double* __restrict__ cond) {
+                                             int ps, int self, const double* __restrict__ cond, Bat bt) {
   griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  if (bt.off) {
+    V = bsh(V, o);
+    w = bsh(w, o);
+    partial = bsh(partial, o);
+    cond = bsh(cond, o);
+  }
   if (cond && cond[0] == 0.0) return;
   __shared__ double red[KMAX_REG][KT];
   const long long base = (long long)blockIdx.x * KT * KE + threadIdx.x;
@@ -115,8 +126,17 @@ void launch_mdot(const double* V, long long vstride, int k, const double* w, lon
 __global__ void __launch_bounds__(KT) k_mupdate(const double* __restrict__ V, long long vs, int k,
                                                 const double* __restrict__ coef, double* __restrict__ w,
                                                 long long len, double* __restrict__ partial, int ps, int mode,
-                                                const double* __restrict__ cond) {
+                                                const double* __restrict__ cond, Bat bt) {
   griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  if (bt.off) {
+    V = bsh(V, o);
+    coef = bsh(coef, o);
+    w = bsh(w, o);
+    partial = bsh(partial, o);
+    cond = bsh(cond, o);
+  }
   if (cond && cond[0] == 0.0) return;
   __shared__ double cf[KMAX_REG];
   __shared__ double red[KMAX_REG][KT];
@@ -180,8 +200,15 @@ void launch_mupdate(const double* V, long long vstride, int k, const double* coe
 
 // out[q] = sum_b partial[q * ps + b] (+ out[q] if accumulate), fixed-order tree
 __global__ void k_reduce(const double* __restrict__ partial, int nblk, int k, int ps, double* __restrict__ out,
-                         int accumulate, const double* __restrict__ cond) {
+                         int accumulate, const double* __restrict__ cond, Bat bt) {
   griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  if (bt.off) {
+    partial = bsh(partial, o);
+    out = bsh(out, o);
+    cond = bsh(cond, o);
+  }
   __shared__ double sm[RT / 32];
   const int q = blockIdx.x;
   if (q >= k) return;
@@ -213,8 +240,13 @@ void launch_reduce(const double* partial, int nblk, int k, int ps, double* out, 
 // Selective re-orthogonalisation (Daniel-Gragg-Kaufman-Stewart test): a second
 // Gram-Schmidt pass is needed when the projection removed most of w,
 // ||w'||^2 < eta^2 ||w||^2.  flag[0] = 1 (pass needed) or 0.
-__global__ void k_reorth_decide(const double* nw2, const double* n2a, double eta2, double* flag) {
+__global__ void k_reorth_decide(const double* nw2, const double* n2a, double eta2, double* flag, Bat bt) {
   griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  nw2 = bsh(nw2, o);
+  n2a = bsh(n2a, o);
+  flag = bsh(flag, o);
   if (threadIdx.x == 0) flag[0] = (n2a[0] < eta2 * nw2[0]) ? 1.0 : 0.0;
 }
 
@@ -232,8 +264,15 @@ void launch_dot(const double* a, const double* b, long long len, double* partial
 
 // mode 0: y = sdev[0] * x ; mode 1: y = x / sqrt(sdev[0])
 __global__ void k_scale_by(const double* __restrict__ x, double* __restrict__ y, long long len,
-                           const double* __restrict__ sdev, int mode) {
+                           const double* __restrict__ sdev, int mode, Bat bt) {
   griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  if (bt.off) {
+    x = bsh(x, o);
+    y = bsh(y, o);
+    sdev = bsh(sdev, o);
+  }
   const double f = mode == 0 ? sdev[0] : 1.0 / sqrt(sdev[0]);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len; e += (long long)gridDim.x * blockDim.x)
     y[e] = f * x[e];
@@ -247,8 +286,17 @@ void launch_scale_by(const double* x, double* y, long long len, const double* sd
 
 // x += sum_q y_q Z_q
 __global__ void __launch_bounds__(KT) k_axpy_multi(double* __restrict__ x, const double* __restrict__ Z, long long zs,
-                                                   const double* __restrict__ y, int k, long long len) {
+                                                   const double* __restrict__ y, int k, long long len,
+                                                   const double* __restrict__ kdev, Bat bt) {
   griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  if (bt.off) {
+    x = bsh(x, o);
+    Z = bsh(Z, o);
+    y = bsh(y, o);
+    if (kdev) k = (int)bsh(kdev, o)[0];
+  }
   __shared__ double cf[KMAX_REG];
   if (threadIdx.x < KMAX_REG) cf[threadIdx.x] = threadIdx.x < k ? y[threadIdx.x] : 0.0;
   __syncthreads();
@@ -283,9 +331,9 @@ __global__ void __launch_bounds__(KT) k_axpy_multi(double* __restrict__ x, const
 }
 
 void launch_axpy_multi(double* x, const double* Z, long long zstride, const double* ycoef, int k, long long len,
-                       cudaStream_t s) {
+                       const double* kdev, cudaStream_t s) {
   SD_COUNT(1);
-  launch_k(k_axpy_multi, dim3(reduce_blocks(len)), dim3(KT), 0, s, x, Z, zstride, ycoef, k, len);
+  launch_k(k_axpy_multi, dim3(reduce_blocks(len)), dim3(KT), 0, s, x, Z, zstride, ycoef, k, len, kdev);
 }
 
 // ----------------------------------------------------- Hessenberg / Givens
@@ -293,8 +341,13 @@ void launch_axpy_multi(double* x, const double* Z, long long zstride, const doub
 // cs[m], sn[m], g[m+1].  flag[0] = |g_{j+1}| (residual estimate),
 // flag[1] = 1 / h_{j+1,j} (scale of the next basis vector), flag[2] = 1 on
 // NaN/Inf, flag[3] = 1 on breakdown (h_{j+1,j} == 0).
-__global__ void k_init_cycle(double* st, int m, const double* beta2, double* flag) {
+__global__ void k_init_cycle(double* st, int m, const double* beta2, double* flag, Bat bt) {
   griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  st = bsh(st, o);
+  beta2 = bsh(beta2, o);
+  flag = bsh(flag, o);
   if (threadIdx.x != 0) return;
   double* g = st + (m + 1) * m + 2 * m;
   const double beta = sqrt(beta2[0]);
@@ -304,6 +357,7 @@ __global__ void k_init_cycle(double* st, int m, const double* beta2, double* fla
   flag[1] = beta > 0.0 ? 1.0 / beta : 0.0;
   flag[2] = isfinite(beta) ? 0.0 : 1.0;
   flag[3] = 0.0;
+  flag[5] = 0.0;
 }
 
 void launch_init_cycle(double* st, int m, const double* beta2, double* flag, cudaStream_t s) {
@@ -312,9 +366,20 @@ void launch_init_cycle(double* st, int m, const double* beta2, double* flag, cud
 }
 
 __global__ void k_givens(double* st, int j, int m, const double* h1, const double* h2, const double* nrm2a,
-                         const double* nrm2b, const double* reo, double* flag) {
+                         const double* nrm2b, const double* reo, double* flag, Bat bt) {
   griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
   if (threadIdx.x != 0) return;
+  if (bt.off) {
+    st = bsh(st, o);
+    h1 = bsh(h1, o);
+    h2 = bsh(h2, o);
+    nrm2a = bsh(nrm2a, o);
+    nrm2b = bsh(nrm2b, o);
+    reo = bsh(reo, o);
+    flag = bsh(flag, o);
+  }
   const bool second = reo == nullptr || reo[0] != 0.0;
   const double* nrm2 = second ? nrm2b : nrm2a;
   double* R = st;
@@ -345,6 +410,7 @@ __global__ void k_givens(double* st, int j, int m, const double* h1, const doubl
   flag[2] = (isfinite(r) && isfinite(g[j + 1])) ? 0.0 : 1.0;
   flag[3] = hn > 0.0 ? 0.0 : 1.0;
   flag[4] = second ? 1.0 : 0.0;
+  flag[5] = (double)(j + 1);
 }
 
 void launch_givens(double* st, int j, int m, const double* hcol1, const double* hcol2, const double* nrm2a,
@@ -369,9 +435,16 @@ void launch_extrapolate(double* x, double* xm, long long len, cudaStream_t s) {
   launch_k(k_extrapolate, dim3((int)(nb < 152 * 16 ? nb : 152 * 16)), dim3(RT), 0, s, x, xm, len);
 }
 
-__global__ void k_backsolve(const double* st, int k, int m, double* y) {
+__global__ void k_backsolve(const double* st, int k, int m, double* y, const double* kdev, Bat bt) {
   griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
   if (threadIdx.x != 0) return;
+  if (bt.off) {
+    st = bsh(st, o);
+    y = bsh(y, o);
+    if (kdev) k = (int)bsh(kdev, o)[0];
+  }
   const double* R = st;
   const double* g = st + (m + 1) * m + 2 * m;
   for (int i = k - 1; i >= 0; --i) {
@@ -381,14 +454,38 @@ __global__ void k_backsolve(const double* st, int k, int m, double* y) {
   }
 }
 
-void launch_backsolve(double* st, int k, int m, double* y, cudaStream_t s) {
-  SD_COUNT(1); launch_k(k_backsolve, dim3(1), dim3(32), 0, s, st, k, m, y); }
+void launch_backsolve(double* st, int k, int m, double* y, const double* kdev, cudaStream_t s) {
+  SD_COUNT(1);
+  launch_k(k_backsolve, dim3(1), dim3(32), 0, s, st, k, m, y, kdev);
+}
+
+// out[z * count + t] = src_z[t] for every instance z of a lockstep batch
+// (src moved to instance z; out is not), idle instances included
+__global__ void k_gather_inst(const double* __restrict__ src, int count, double* __restrict__ out, Bat bt) {
+  griddep_wait();
+  const long long o = bt.off ? bt.off[blockIdx.z] : 0;
+  const double* p = bsh(src, o);
+  for (int t = threadIdx.x; t < count; t += blockDim.x) out[(long long)blockIdx.z * count + t] = p[t];
+}
+
+void launch_gather_inst(const double* src, int count, double* out, cudaStream_t s) {
+  SD_COUNT(1);
+  launch_k(k_gather_inst, dim3(1), dim3(32), 0, s, src, count, out);
+}
 
 // ------------------------------------------------------ dense coarse solve
 template <typename T>
 __global__ void k_dense_solve(const double* __restrict__ Ainv, const int* __restrict__ idx, int m,
-                              const T* __restrict__ b, T* __restrict__ x) {
+                              const T* __restrict__ b, T* __restrict__ x, Bat bt) {
   griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  if (bt.off) {
+    Ainv = bsh(Ainv, o);
+    idx = bsh(idx, o);
+    b = bsh(b, o);
+    x = bsh(x, o);
+  }
   extern __shared__ double bs[];
   for (int l = threadIdx.x; l < m; l += blockDim.x) bs[l] = (double)b[idx[l]];
   __syncthreads();

@@ -37,6 +37,12 @@ static inline int rows_cell(int n) { return n >= 1024 ? 4 : 1; }
 static inline int rows_vel(int) { return 1; }
 static inline dim3 grid2R(int nx, int ny, int R) { return dim3((nx + BX - 1) / BX, (ny + BY * R - 1) / (BY * R)); }
 
+// Jacobi-scaled update term r / diag of the smoothers: the fast FP32
+// division in the FP32 hierarchy (a smoother needs no correctly rounded
+// quotient), the IEEE division in FP64
+__device__ __forceinline__ float sdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double sdiv(double a, double b) { return a / b; }
+
 // ------------------------------------------------------------------ rows
 // Each row function loads every neighbour it may need from an in-range
 // (clamped) address first and masks the terms that do not exist at a
@@ -62,8 +68,8 @@ __device__ __forceinline__ void u_row(const Coef<T>& c, const T* __restrict__ u,
     off = T(0);
     return;
   }
-  const long long r0 = (long long)j * P, rN = (long long)(top ? j : j + 1) * P, rS = (long long)(bot ? j : j - 1) * P;
-  const long long rv1 = (long long)(j + 1) * P;
+  const int r0 = j * P, rN = (top ? j : j + 1) * P, rS = (bot ? j : j - 1) * P;
+  const int rv1 = (j + 1) * P;
   const T uW = u[r0 + i - 1], uE = u[r0 + i + 1], uN = u[rN + i], uS = u[rS + i];
   const T vN = v[rv1 + i], vNW = v[rv1 + i - 1], vS = v[r0 + i], vSW = v[r0 + i - 1];
   const T cW = (i - 1 >= 1) ? c.m2 : T(0), cE = (i + 1 <= n - 1) ? c.m2 : T(0);
@@ -123,7 +129,7 @@ __device__ __forceinline__ void v_row(const Coef<T>& c, const T* __restrict__ u,
     off = T(0);
     return;
   }
-  const long long r0 = (long long)j * P, rm = (long long)(j - 1) * P, rp = (long long)(j + 1) * P;
+  const int r0 = j * P, rm = (j - 1) * P, rp = (j + 1) * P;
   const int iE = right ? i : i + 1, iW = left ? i : i - 1;
   const T vS = v[rm + i], vN = v[rp + i], vE = v[r0 + iE], vW = v[r0 + iW];
   const T uE = u[r0 + i + 1], uES = u[rm + i + 1], uW = u[r0 + i], uWS = u[rm + i];
@@ -148,7 +154,7 @@ template <typename T>
 __device__ __forceinline__ void d_row(const Coef<T>& c, const T* __restrict__ p, int i, int j, bool read, T& off,
                                       T& diag) {
   const int n = c.n, P = c.P;
-  const long long r0 = (long long)j * P;
+  const int r0 = j * P;
   const T tw = c.Tx[r0 + i], te = c.Tx[r0 + i + 1];
   const T ts = c.Ty[r0 + i], tn = c.Ty[r0 + P + i];
   diag = (tw + te) + (ts + tn);
@@ -170,8 +176,16 @@ __device__ __forceinline__ void d_row(const Coef<T>& c, const T* __restrict__ p,
 // ------------------------------------------------------- whole operator (K1)
 template <int R>
 __global__ void k_apply_full(Coef<double> c, const double* __restrict__ x, const double* __restrict__ b,
-                             double* __restrict__ y) {
+                             double* __restrict__ y, Bat bt) {
   griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  if (bt.off) {
+    bsh_coef(c, o);
+    x = bsh(x, o);
+    b = bsh(b, o);
+    y = bsh(y, o);
+  }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
   const int n = c.n, P = c.P;
@@ -248,7 +262,7 @@ __device__ __forceinline__ void cheb_V_at2(const Coef<T>& c, const T* __restrict
   const int n = c.n, P = c.P;
   const bool rd = uin != nullptr;
   if (j < n) {
-    const long long k = (long long)j * P + i;
+    const int k = j * P + i;
     if (i == 0 || i == n) {
       uout[k] = bu[k];
       du[k] = T(0);
@@ -257,13 +271,13 @@ __device__ __forceinline__ void cheb_V_at2(const Coef<T>& c, const T* __restrict
       u_row(c, uin, vin, i, j, rd, off, dg);
       const T xc = rd ? uin[k] : T(0);
       const T r = bu[k] - (dg * xc + off);
-      const T dn = (a != T(0) ? a * du[k] : T(0)) + cc * r / dg;
+      const T dn = (a != T(0) ? a * du[k] : T(0)) + sdiv(cc * r, dg);
       du[k] = dn;
       uout[k] = xc + dn;
     }
   }
   if (i < n) {
-    const long long k = (long long)j * P + i;
+    const int k = j * P + i;
     if (j == n) {
       vout[k] = bv[k];
       dv[k] = T(0);
@@ -272,7 +286,7 @@ __device__ __forceinline__ void cheb_V_at2(const Coef<T>& c, const T* __restrict
       v_row(c, uin, vin, i, j, rd, off, dg);
       const T xc = rd ? vin[k] : T(0);
       const T r = bv[k] - (dg * xc + off);
-      const T dn = (a != T(0) ? a * dv[k] : T(0)) + cc * r / dg;
+      const T dn = (a != T(0) ? a * dv[k] : T(0)) + sdiv(cc * r, dg);
       dv[k] = dn;
       vout[k] = xc + dn;
     }
@@ -288,8 +302,21 @@ __device__ __forceinline__ void cheb_V_at(const Coef<T>& c, const T* __restrict_
 
 template <typename T, int R>
 __global__ void k_cheb_V(Coef<T> c, const T* __restrict__ xin, const T* __restrict__ b, T* __restrict__ d,
-                         T* __restrict__ xout, T a, T cc, long long bstride) {
+                         T* __restrict__ xout, T a, T cc, const T* __restrict__ ck, long long bstride, Bat bt) {
   griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  if (bt.off) {
+    bsh_coef(c, o);
+    xin = bsh(xin, o);
+    b = bsh(b, o);
+    d = bsh(d, o);
+    xout = bsh(xout, o);
+    if (ck) {
+      a = bsh(ck, o)[0];
+      cc = bsh(ck, o)[8];
+    }
+  }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
   if (i > c.n) return;
@@ -303,14 +330,14 @@ __global__ void k_cheb_V(Coef<T> c, const T* __restrict__ xin, const T* __restri
 }
 
 template <typename T>
-void launch_cheb_V(const Coef<T>& c, const T* x_in, const T* b, T* d, T* x_out, T a, T cc, int nbatch,
+void launch_cheb_V(const Coef<T>& c, const T* x_in, const T* b, T* d, T* x_out, T a, T cc, const T* ck, int nbatch,
                    long long bstride, cudaStream_t s) {
   SD_COUNT(1);
   const int R = rows_vel(c.n);
   dim3 g = grid2R(c.n + 1, c.n + 1, R);
   g.z = nbatch;
-  if (R == 4) launch_k(k_cheb_V<T, 4>, dim3(g), dim3(dim3(BX, BY)), 0, s, c, x_in, b, d, x_out, a, cc, bstride);
-  else launch_k(k_cheb_V<T, 1>, dim3(g), dim3(dim3(BX, BY)), 0, s, c, x_in, b, d, x_out, a, cc, bstride);
+  if (R == 4) launch_k(k_cheb_V<T, 4>, dim3(g), dim3(dim3(BX, BY)), 0, s, c, x_in, b, d, x_out, a, cc, ck, bstride);
+  else launch_k(k_cheb_V<T, 1>, dim3(g), dim3(dim3(BX, BY)), 0, s, c, x_in, b, d, x_out, a, cc, ck, bstride);
 }
 
 // r = b - V x (mode 0; b == nullptr: -V x), D^-1 V x (mode 1), V x (mode 2)
@@ -321,7 +348,7 @@ __device__ __forceinline__ void resid_V_at(const Coef<T>& c, const T* __restrict
   const T* u = x;
   const T* v = x + (long long)n * P;
   if (j < n) {
-    const long long k = (long long)j * P + i;
+    const int k = j * P + i;
     T ax, dg = T(1);
     if (i == 0 || i == n) {
       ax = x[k];
@@ -333,7 +360,7 @@ __device__ __forceinline__ void resid_V_at(const Coef<T>& c, const T* __restrict
     r[k] = jac == 1 ? ax / dg : (jac == 2 ? ax : (b ? b[k] - ax : -ax));
   }
   if (i < n) {
-    const long long k = (long long)n * P + (long long)j * P + i;
+    const int k = n * P + j * P + i;
     T ax, dg = T(1);
     if (j == n) {
       ax = x[k];
@@ -348,8 +375,16 @@ __device__ __forceinline__ void resid_V_at(const Coef<T>& c, const T* __restrict
 
 template <typename T, int R>
 __global__ void k_resid_V(Coef<T> c, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, int jac,
-                          long long bstride) {
+                          long long bstride, Bat bt) {
   griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  if (bt.off) {
+    bsh_coef(c, o);
+    x = bsh(x, o);
+    b = bsh(b, o);
+    r = bsh(r, o);
+  }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
   if (i > c.n) return;
@@ -377,21 +412,34 @@ void launch_resid_V(const Coef<T>& c, const T* x, const T* b, T* r, int jac, int
 template <typename T>
 __device__ __forceinline__ void cheb_D_at(const Coef<T>& c, const T* __restrict__ xin, const T* __restrict__ b,
                                           T* __restrict__ d, T* __restrict__ xout, T a, T cc, int i, int j) {
-  const long long k = (long long)j * c.P + i;
+  const int k = j * c.P + i;
   const bool rd = xin != nullptr;
   T off, dg;
   d_row(c, xin, i, j, rd, off, dg);
   const T xc = rd ? xin[k] : T(0);
   const T r = b[k] - (dg * xc + off);
-  const T dn = (a != T(0) ? a * d[k] : T(0)) + cc * r / dg;
+  const T dn = (a != T(0) ? a * d[k] : T(0)) + sdiv(cc * r, dg);
   d[k] = dn;
   xout[k] = xc + dn;
 }
 
 template <typename T, int R>
 __global__ void k_cheb_D(Coef<T> c, const T* __restrict__ xin, const T* __restrict__ b, T* __restrict__ d,
-                         T* __restrict__ xout, T a, T cc, long long bstride) {
+                         T* __restrict__ xout, T a, T cc, const T* __restrict__ ck, long long bstride, Bat bt) {
   griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  if (bt.off) {
+    bsh_coef(c, o);
+    xin = bsh(xin, o);
+    b = bsh(b, o);
+    d = bsh(d, o);
+    xout = bsh(xout, o);
+    if (ck) {
+      a = bsh(ck, o)[0];
+      cc = bsh(ck, o)[8];
+    }
+  }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
   if (i >= c.n) return;
@@ -405,20 +453,20 @@ __global__ void k_cheb_D(Coef<T> c, const T* __restrict__ xin, const T* __restri
 }
 
 template <typename T>
-void launch_cheb_D(const Coef<T>& c, const T* x_in, const T* b, T* d, T* x_out, T a, T cc, int nbatch,
+void launch_cheb_D(const Coef<T>& c, const T* x_in, const T* b, T* d, T* x_out, T a, T cc, const T* ck, int nbatch,
                    long long bstride, cudaStream_t s) {
   SD_COUNT(1);
   const int R = rows_cell(c.n);
   dim3 g = grid2R(c.n, c.n, R);
   g.z = nbatch;
-  if (R == 4) launch_k(k_cheb_D<T, 4>, dim3(g), dim3(dim3(BX, BY)), 0, s, c, x_in, b, d, x_out, a, cc, bstride);
-  else launch_k(k_cheb_D<T, 1>, dim3(g), dim3(dim3(BX, BY)), 0, s, c, x_in, b, d, x_out, a, cc, bstride);
+  if (R == 4) launch_k(k_cheb_D<T, 4>, dim3(g), dim3(dim3(BX, BY)), 0, s, c, x_in, b, d, x_out, a, cc, ck, bstride);
+  else launch_k(k_cheb_D<T, 1>, dim3(g), dim3(dim3(BX, BY)), 0, s, c, x_in, b, d, x_out, a, cc, ck, bstride);
 }
 
 template <typename T>
 __device__ __forceinline__ void resid_D_at(const Coef<T>& c, const T* __restrict__ x, const T* __restrict__ b,
                                            T* __restrict__ r, int jac, int i, int j) {
-  const long long k = (long long)j * c.P + i;
+  const int k = j * c.P + i;
   T off, dg;
   d_row(c, x, i, j, true, off, dg);
   const T ax = dg * x[k] + off;
@@ -427,8 +475,16 @@ __device__ __forceinline__ void resid_D_at(const Coef<T>& c, const T* __restrict
 
 template <typename T, int R>
 __global__ void k_resid_D(Coef<T> c, const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r, int jac,
-                          long long bstride) {
+                          long long bstride, Bat bt) {
   griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  if (bt.off) {
+    bsh_coef(c, o);
+    x = bsh(x, o);
+    b = bsh(b, o);
+    r = bsh(r, o);
+  }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
   if (i >= c.n) return;
@@ -509,8 +565,14 @@ __device__ __forceinline__ void restrict_V_at(int nf, int Pf, const T* __restric
 }
 
 template <typename T>
-__global__ void k_restrict_V(int nf, int Pf, const T* __restrict__ r, int nc, int Pc, T* __restrict__ bc) {
+__global__ void k_restrict_V(int nf, int Pf, const T* __restrict__ r, int nc, int Pc, T* __restrict__ bc, Bat bt) {
   griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  if (bt.off) {
+    r = bsh(r, o);
+    bc = bsh(bc, o);
+  }
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I > nc || J > nc) return;
@@ -531,8 +593,14 @@ __device__ __forceinline__ void restrict_D_at(int Pf, const T* __restrict__ r, i
 }
 
 template <typename T>
-__global__ void k_restrict_D(int nf, int Pf, const T* __restrict__ r, int nc, int Pc, T* __restrict__ bc) {
+__global__ void k_restrict_D(int nf, int Pf, const T* __restrict__ r, int nc, int Pc, T* __restrict__ bc, Bat bt) {
   griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  if (bt.off) {
+    r = bsh(r, o);
+    bc = bsh(bc, o);
+  }
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= nc || J >= nc) return;
@@ -549,8 +617,16 @@ void launch_restrict_D(int nf, int Pf, const T* r, int nc, int Pc, T* bc, cudaSt
 // cells of coarse cell (I, J) (residual and cell-sum restriction in one pass).
 template <typename T>
 __global__ void k_resid_restrict_D(Coef<T> c, const T* __restrict__ x, const T* __restrict__ b, int nc, int Pc,
-                                   T* __restrict__ bc) {
+                                   T* __restrict__ bc, Bat bt) {
   griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  if (bt.off) {
+    bsh_coef(c, o);
+    x = bsh(x, o);
+    b = bsh(b, o);
+    bc = bsh(bc, o);
+  }
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= nc || J >= nc) return;
@@ -632,8 +708,14 @@ __device__ __forceinline__ void prolong_V_at(int nf, int Pf, T* __restrict__ x, 
 }
 
 template <typename T, int R>
-__global__ void k_prolong_V(int nf, int Pf, T* __restrict__ x, int nc, int Pc, const T* __restrict__ e) {
+__global__ void k_prolong_V(int nf, int Pf, T* __restrict__ x, int nc, int Pc, const T* __restrict__ e, Bat bt) {
   griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  if (bt.off) {
+    x = bsh(x, o);
+    e = bsh(e, o);
+  }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
   if (i > nf) return;
@@ -678,8 +760,14 @@ __device__ __forceinline__ void prolong_D_at(int Pf, T* __restrict__ x, int nc, 
 }
 
 template <typename T, int R>
-__global__ void k_prolong_D(int nf, int Pf, T* __restrict__ x, int nc, int Pc, const T* __restrict__ e) {
+__global__ void k_prolong_D(int nf, int Pf, T* __restrict__ x, int nc, int Pc, const T* __restrict__ e, Bat bt) {
   griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  if (bt.off) {
+    x = bsh(x, o);
+    e = bsh(e, o);
+  }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
   if (i >= nf) return;
@@ -708,13 +796,33 @@ void launch_prolong_D(int nf, int Pf, T* x, int nc, int Pc, const T* e, cudaStre
 // point's arithmetic is that of the per-step kernels, in the same order, so
 // the result is bitwise the same; only the global traffic and the launches
 // of the intermediate steps disappear.
-static const int TLX = 32, TLY = 16, TLT = 256;
+static const int TLX = 32, TLT = 256;  // tile width and threads; the height TLY is a template parameter
 
-template <typename T, int NS>
+template <typename T, int NS, int TLY, bool BT>
 __global__ void __launch_bounds__(TLT) k_smooth_tile_D(Coef<T> c, const T* __restrict__ xin,
                                                        const T* __restrict__ b, T* __restrict__ xout,
-                                                       ChebSteps<T> cs, const T* __restrict__ ec, int nc, int Pc) {
+                                                       ChebSteps<T> cs, const T* __restrict__ ct,
+                                                       const T* __restrict__ ec, int nc, int Pc, Bat bt) {
   griddep_wait();
+  // a separate instantiation for lockstep batches keeps the single-instance
+  // kernel's coefficients in the parameter space
+  if constexpr (BT) {
+    long long o;
+    if (!bat_enter(bt, o)) return;
+    bsh_coef(c, o);
+    xin = bsh(xin, o);
+    b = bsh(b, o);
+    xout = bsh(xout, o);
+    ec = bsh(ec, o);
+    if (ct) {
+      const T* q = bsh(ct, o);
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        cs.a[s] = q[s];
+        cs.c[s] = q[8 + s];
+      }
+    }
+  }
   constexpr int H = NS, EX = TLX + 2 * H, EY = TLY + 2 * H, SP = EX + 1, SR = EY + 1;
   __shared__ T sb[SR * SP], sx0[SR * SP], sx1[SR * SP], sd[SR * SP], sTx[SR * SP], sTy[SR * SP];
   const int n = c.n, P = c.P;
@@ -769,11 +877,31 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_D(Coef<T> c, const T* __res
   }
 }
 
-template <typename T, int NS>
+template <typename T, int NS, int TLY, bool BT>
 __global__ void __launch_bounds__(TLT) k_smooth_tile_V(Coef<T> c, const T* __restrict__ xin,
                                                        const T* __restrict__ b, T* __restrict__ xout,
-                                                       ChebSteps<T> cs, const T* __restrict__ ec, int nc, int Pc) {
+                                                       ChebSteps<T> cs, const T* __restrict__ ct,
+                                                       const T* __restrict__ ec, int nc, int Pc, Bat bt) {
   griddep_wait();
+  // a separate instantiation for lockstep batches keeps the single-instance
+  // kernel's coefficients in the parameter space
+  if constexpr (BT) {
+    long long o;
+    if (!bat_enter(bt, o)) return;
+    bsh_coef(c, o);
+    xin = bsh(xin, o);
+    b = bsh(b, o);
+    xout = bsh(xout, o);
+    ec = bsh(ec, o);
+    if (ct) {
+      const T* q = bsh(ct, o);
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        cs.a[s] = q[s];
+        cs.c[s] = q[8 + s];
+      }
+    }
+  }
   constexpr int H = NS, EX = TLX + 2 * H, EY = TLY + 2 * H, SP = EX + 1, SR = EY + 1;
   __shared__ T sbu[SR * SP], sbv[SR * SP], sau[SR * SP], sav[SR * SP], sbu2[SR * SP], sbv2[SR * SP];
   __shared__ T sdu[SR * SP], sdv[SR * SP], sw[SP], srg[SP];
@@ -852,15 +980,61 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_V(Coef<T> c, const T* __res
   }
 }
 
-template <typename T>
-int launch_smooth_tile_D(const Coef<T>& c, const T* x_in, const T* b, T* x_out, const ChebSteps<T>& cs,
-                         const T* ec, int nc, int Pc, cudaStream_t s) {
+template <typename T, int TLY>
+int launch_tile_D_rows(const Coef<T>& c, const T* x_in, const T* b, T* x_out, const ChebSteps<T>& cs, const T* ct,
+                       const T* ec, int nc, int Pc, cudaStream_t s) {
   const dim3 g((c.n + TLX - 1) / TLX, (c.n + TLY - 1) / TLY);
   switch (cs.ns) {
-    case 1: launch_k(k_smooth_tile_D<T, 1>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ec, nc, Pc); break;
-    case 2: launch_k(k_smooth_tile_D<T, 2>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ec, nc, Pc); break;
-    case 3: launch_k(k_smooth_tile_D<T, 3>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ec, nc, Pc); break;
-    case 4: launch_k(k_smooth_tile_D<T, 4>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ec, nc, Pc); break;
+    case 1:
+      if (t_bat.off) launch_k(k_smooth_tile_D<T, 1, TLY, true>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
+      else launch_k(k_smooth_tile_D<T, 1, TLY, false>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
+      break;
+    case 2:
+      if (t_bat.off) launch_k(k_smooth_tile_D<T, 2, TLY, true>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
+      else launch_k(k_smooth_tile_D<T, 2, TLY, false>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
+      break;
+    case 3:
+      if (t_bat.off) launch_k(k_smooth_tile_D<T, 3, TLY, true>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
+      else launch_k(k_smooth_tile_D<T, 3, TLY, false>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
+      break;
+    case 4:
+      if (t_bat.off) launch_k(k_smooth_tile_D<T, 4, TLY, true>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
+      else launch_k(k_smooth_tile_D<T, 4, TLY, false>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
+      break;
+    default: return -1;
+  }
+  SD_COUNT(1);
+  return 0;
+}
+
+template <typename T>
+int launch_smooth_tile_D(const Coef<T>& c, const T* x_in, const T* b, T* x_out, const ChebSteps<T>& cs,
+                         const T* ct, const T* ec, int nc, int Pc, cudaStream_t s) {
+  return cs.rows == 8 ? launch_tile_D_rows<T, 8>(c, x_in, b, x_out, cs, ct, ec, nc, Pc, s)
+                      : launch_tile_D_rows<T, 16>(c, x_in, b, x_out, cs, ct, ec, nc, Pc, s);
+}
+
+template <typename T, int TLY>
+int launch_tile_V_rows(const Coef<T>& c, const T* x_in, const T* b, T* x_out, const ChebSteps<T>& cs, const T* ct,
+                       const T* ec, int nc, int Pc, cudaStream_t s) {
+  const dim3 g((c.n + 1 + TLX - 1) / TLX, (c.n + 1 + TLY - 1) / TLY);
+  switch (cs.ns) {
+    case 1:
+      if (t_bat.off) launch_k(k_smooth_tile_V<T, 1, TLY, true>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
+      else launch_k(k_smooth_tile_V<T, 1, TLY, false>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
+      break;
+    case 2:
+      if (t_bat.off) launch_k(k_smooth_tile_V<T, 2, TLY, true>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
+      else launch_k(k_smooth_tile_V<T, 2, TLY, false>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
+      break;
+    case 3:
+      if (t_bat.off) launch_k(k_smooth_tile_V<T, 3, TLY, true>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
+      else launch_k(k_smooth_tile_V<T, 3, TLY, false>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
+      break;
+    case 4:
+      if (t_bat.off) launch_k(k_smooth_tile_V<T, 4, TLY, true>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
+      else launch_k(k_smooth_tile_V<T, 4, TLY, false>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
+      break;
     default: return -1;
   }
   SD_COUNT(1);
@@ -869,17 +1043,9 @@ int launch_smooth_tile_D(const Coef<T>& c, const T* x_in, const T* b, T* x_out, 
 
 template <typename T>
 int launch_smooth_tile_V(const Coef<T>& c, const T* x_in, const T* b, T* x_out, const ChebSteps<T>& cs,
-                         const T* ec, int nc, int Pc, cudaStream_t s) {
-  const dim3 g((c.n + 1 + TLX - 1) / TLX, (c.n + 1 + TLY - 1) / TLY);
-  switch (cs.ns) {
-    case 1: launch_k(k_smooth_tile_V<T, 1>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ec, nc, Pc); break;
-    case 2: launch_k(k_smooth_tile_V<T, 2>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ec, nc, Pc); break;
-    case 3: launch_k(k_smooth_tile_V<T, 3>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ec, nc, Pc); break;
-    case 4: launch_k(k_smooth_tile_V<T, 4>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ec, nc, Pc); break;
-    default: return -1;
-  }
-  SD_COUNT(1);
-  return 0;
+                         const T* ct, const T* ec, int nc, int Pc, cudaStream_t s) {
+  return cs.rows == 8 ? launch_tile_V_rows<T, 8>(c, x_in, b, x_out, cs, ct, ec, nc, Pc, s)
+                      : launch_tile_V_rows<T, 16>(c, x_in, b, x_out, cs, ct, ec, nc, Pc, s);
 }
 
 // ------------------------------------------------ fused coarse V-cycle
@@ -903,25 +1069,25 @@ __device__ __forceinline__ void cheb_d_V_at(const Coef<T>& c, const T* __restric
   const T* u = x;
   const T* v = x + (long long)n * P;
   if (j < n) {
-    const long long k = (long long)j * P + i;
+    const int k = j * P + i;
     if (i == 0 || i == n) {
       d[k] = T(0);
     } else {
       T off, dg;
       u_row(c, u, v, i, j, true, off, dg);
       const T r = b[k] - (dg * x[k] + off);
-      d[k] = (a != T(0) ? a * d[k] : T(0)) + cc * r / dg;
+      d[k] = (a != T(0) ? a * d[k] : T(0)) + sdiv(cc * r, dg);
     }
   }
   if (i < n) {
-    const long long k = (long long)n * P + (long long)j * P + i;
+    const int k = n * P + j * P + i;
     if (j == n) {
       d[k] = T(0);
     } else {
       T off, dg;
       v_row(c, u, v, i, j, true, off, dg);
       const T r = b[k] - (dg * x[k] + off);
-      d[k] = (a != T(0) ? a * d[k] : T(0)) + cc * r / dg;
+      d[k] = (a != T(0) ? a * d[k] : T(0)) + sdiv(cc * r, dg);
     }
   }
 }
@@ -929,11 +1095,11 @@ __device__ __forceinline__ void cheb_d_V_at(const Coef<T>& c, const T* __restric
 template <typename T>
 __device__ __forceinline__ void cheb_d_D_at(const Coef<T>& c, const T* __restrict__ x, const T* __restrict__ b,
                                             T* __restrict__ d, T a, T cc, int i, int j) {
-  const long long k = (long long)j * c.P + i;
+  const int k = j * c.P + i;
   T off, dg;
   d_row(c, x, i, j, true, off, dg);
   const T r = b[k] - (dg * x[k] + off);
-  d[k] = (a != T(0) ? a * d[k] : T(0)) + cc * r / dg;
+  d[k] = (a != T(0) ? a * d[k] : T(0)) + sdiv(cc * r, dg);
 }
 
 // ops: 0 Chebyshev step (writes d and x_out from x_in), 1 d-update only,
@@ -979,8 +1145,7 @@ __device__ void cyc_sweep(const CoarseCycle<T>& q, int l, int op, T* X, const T*
 }
 
 template <typename T>
-__global__ void __launch_bounds__(1024) k_coarse_cycle(CoarseCycle<T> q) {
-  griddep_wait();
+__device__ __forceinline__ void coarse_cycle_body(const CoarseCycle<T>& q) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   T* B[SD_CYC_MAXL];
@@ -1049,6 +1214,45 @@ __global__ void __launch_bounds__(1024) k_coarse_cycle(CoarseCycle<T> q) {
   }
 }
 
+// The descriptor is copied to shared memory first; in a lockstep batch it is
+// then moved to this block's instance (its arrays by the instance offset,
+// its Chebyshev coefficients read from the instance's own table).  A single
+// instance runs the same code on the unmoved copy, so both compile to the
+// same arithmetic and give bitwise the same result.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_coarse_cycle(const __grid_constant__ CoarseCycle<T> q, Bat bt) {
+  griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  __shared__ CoarseCycle<T> sq;
+  {
+    const int* src = reinterpret_cast<const int*>(&q);
+    int* dst = reinterpret_cast<int*>(&sq);
+    for (int w = threadIdx.x; w < (int)(sizeof(CoarseCycle<T>) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+  }
+  __syncthreads();
+  if (bt.off) {  // uniform over the block
+    const int tid = threadIdx.x;
+    if (tid < q.nlev) bsh_coef(sq.c[tid], o);
+    if (tid >= 32 && tid < 32 + 8 * q.nlev) {
+      const int l = (tid - 32) >> 3, k = (tid - 32) & 7;
+      if (q.cht[l] && k < q.deg[l]) {
+        const T* row = bsh(q.cht[l], o);
+        sq.cha[l][k] = row[k];
+        sq.chc[l][k] = row[8 + k];
+      }
+    }
+    if (tid == 96) {
+      sq.Ainv = bsh(q.Ainv, o);
+      sq.idx = bsh(q.idx, o);
+      sq.b_in = bsh(q.b_in, o);
+      sq.x_out = bsh(q.x_out, o);
+    }
+    __syncthreads();
+  }
+  coarse_cycle_body(sq);
+}
+
 template <typename T>
 size_t coarse_cycle_smem(const CoarseCycle<T>& q) {
   size_t tot = 0;
@@ -1079,8 +1283,18 @@ int launch_coarse_cycle(const CoarseCycle<T>& q, cudaStream_t s) {
 // then the velocity rhs r_v - B z_pf for the V-block multigrid.
 template <typename T>
 __global__ void k_precond_entry(Coef<double> c, const double* __restrict__ r, double* __restrict__ z, double schur,
-                                const T* __restrict__ eP, double cmass, int useB, int useB1, T* __restrict__ rV) {
+                                const T* __restrict__ eP, double cmass, int useB, int useB1, T* __restrict__ rV,
+                                Bat bt) {
   griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  if (bt.off) {
+    bsh_coef(c, o);
+    r = bsh(r, o);
+    z = bsh(z, o);
+    eP = bsh(eP, o);
+    rV = bsh(rV, o);
+  }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int n = c.n, P = c.P;
@@ -1121,8 +1335,17 @@ void launch_precond_entry(const Coef<double>& c, const double* r, double* z, dou
 
 template <typename T>
 __global__ void k_precond_mid(Coef<double> c, const double* __restrict__ r, double* __restrict__ z,
-                              const T* __restrict__ eV, int useC, T* __restrict__ rD) {
+                              const T* __restrict__ eV, int useC, T* __restrict__ rD, Bat bt) {
   griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  if (bt.off) {
+    bsh_coef(c, o);
+    r = bsh(r, o);
+    z = bsh(z, o);
+    eV = bsh(eV, o);
+    rD = bsh(rD, o);
+  }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int n = c.n, P = c.P;
@@ -1151,8 +1374,14 @@ void launch_precond_mid(const Coef<double>& c, const double* r, double* z, const
 }
 
 template <typename T>
-__global__ void k_precond_exit(int n, int P, double* __restrict__ z, const T* __restrict__ eD) {
+__global__ void k_precond_exit(int n, int P, double* __restrict__ z, const T* __restrict__ eD, Bat bt) {
   griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  if (bt.off) {
+    z = bsh(z, o);
+    eD = bsh(eD, o);
+  }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= n || j >= n) return;
@@ -1170,8 +1399,16 @@ void launch_precond_exit(const Coef<double>& c, double* z, const T* eD, cudaStre
 // gives z_pf = r_pf - C z_v (C: the continuity rows of Eq. (2)).
 template <typename T>
 __global__ void k_precond_bgs_pff(Coef<double> c, const double* __restrict__ r, double* __restrict__ z,
-                                  const T* __restrict__ eV) {
+                                  const T* __restrict__ eV, Bat bt) {
   griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  if (bt.off) {
+    bsh_coef(c, o);
+    r = bsh(r, o);
+    z = bsh(z, o);
+    eV = bsh(eV, o);
+  }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int n = c.n, P = c.P;
@@ -1278,8 +1515,14 @@ void launch_setup_coef(const double* Kp, int n, int P, double mu, double alpha, 
 }
 
 template <typename T>
-__global__ void k_convert(const double* __restrict__ a, T* __restrict__ b, long long len) {
+__global__ void k_convert(const double* __restrict__ a, T* __restrict__ b, long long len, Bat bt) {
   griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  if (bt.off) {
+    a = bsh(a, o);
+    b = bsh(b, o);
+  }
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < len; k += (long long)gridDim.x * blockDim.x)
     b[k] = (T)a[k];
 }
@@ -1472,8 +1715,8 @@ void launch_unpack(const Geom& g, const double* padded, double* dense, cudaStrea
 #define SD_INST(T)                                                                                               \
   template void launch_setup_coef<T>(const double*, int, int, double, double, T*, T*, T*, T*, cudaStream_t);    \
   template void launch_convert<T>(const double*, T*, long long, cudaStream_t);                                   \
-  template void launch_cheb_V<T>(const Coef<T>&, const T*, const T*, T*, T*, T, T, int, long long, cudaStream_t); \
-  template void launch_cheb_D<T>(const Coef<T>&, const T*, const T*, T*, T*, T, T, int, long long, cudaStream_t); \
+  template void launch_cheb_V<T>(const Coef<T>&, const T*, const T*, T*, T*, T, T, const T*, int, long long, cudaStream_t); \
+  template void launch_cheb_D<T>(const Coef<T>&, const T*, const T*, T*, T*, T, T, const T*, int, long long, cudaStream_t); \
   template void launch_resid_V<T>(const Coef<T>&, const T*, const T*, T*, int, int, long long, cudaStream_t);    \
   template void launch_resid_D<T>(const Coef<T>&, const T*, const T*, T*, int, int, long long, cudaStream_t);    \
   template void launch_restrict_V<T>(int, int, const T*, int, int, T*, cudaStream_t);            \
@@ -1490,9 +1733,9 @@ SD_INST(double)
 template int launch_coarse_cycle<float>(const CoarseCycle<float>&, cudaStream_t);
 template int prepare_coarse_cycle<float>();
 template int launch_smooth_tile_D<float>(const Coef<float>&, const float*, const float*, float*, const ChebSteps<float>&,
-                                         const float*, int, int, cudaStream_t);
+                                         const float*, const float*, int, int, cudaStream_t);
 template int launch_smooth_tile_V<float>(const Coef<float>&, const float*, const float*, float*, const ChebSteps<float>&,
-                                         const float*, int, int, cudaStream_t);
+                                         const float*, const float*, int, int, cudaStream_t);
 template int prepare_coarse_cycle<double>();
 template int launch_coarse_cycle<double>(const CoarseCycle<double>&, cudaStream_t);
 template size_t coarse_cycle_smem<float>(const CoarseCycle<float>&);

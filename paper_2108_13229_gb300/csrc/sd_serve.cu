@@ -1,10 +1,13 @@
 // sd_serve.cu -- many independent instances at once: sd_solve_batch (a
-// fixed set of handles advanced concurrently, each on its own stream) and
+// fixed set of handles advanced together: compatible handles in lockstep
+// groups that share every launch, the rest each on its own stream) and
 // the continuous-batching server (requests admitted FIFO as running slots
 // and HBM budget free up, each run keeping its state on the device for all
-// its time steps).  Host code only, built on the public C ABI; instances
-// never share device memory, so every result equals the instance run alone.
+// its time steps).  Host code on the public C ABI and the lockstep driver;
+// instances never share device memory, so every result equals the instance
+// run alone.
 #include "../../include/sd.h"
+#include "sd_internal.cuh"
 
 #include <cuda_runtime.h>
 
@@ -124,29 +127,66 @@ void worker_loop(sd_server* S) {
 
 extern "C" {
 
-int sd_solve_batch(sd_handle* const* hs, int32_t count, const int32_t* nsteps, sd_step_info* const* infos,
-                   int32_t max_threads) {
+int sd_solve_batch_ex(sd_handle* const* hs, int32_t count, const int32_t* nsteps, sd_step_info* const* infos,
+                      int32_t max_threads, int32_t flags) {
   if (count < 0 || (count > 0 && (!hs || !nsteps))) return SD_E_INVAL;
   if (count == 0) return SD_OK;
-  int nt = (max_threads > 0 && max_threads < count) ? max_threads : count;
+  for (int k = 0; k < count; ++k)
+    if (!hs[k] || nsteps[k] < 0) return SD_E_INVAL;
+  // work items: lockstep groups of compatible handles (same nsteps), or
+  // single handles
+  std::vector<std::vector<int>> items;
+  for (int k = 0; k < count; ++k) {
+    bool placed = false;
+    if (flags & SD_BATCH_LOCKSTEP) {
+      for (auto& it : items) {
+        const int a = it[0];
+        if (nsteps[a] == nsteps[k] && sdk::can_lockstep(hs[a], hs[k])) {
+          it.push_back(k);
+          placed = true;
+          break;
+        }
+      }
+    }
+    if (!placed) items.push_back(std::vector<int>(1, k));
+  }
+  const int ni = (int)items.size();
+  const int nt = (max_threads > 0 && max_threads < ni) ? max_threads : ni;
   int dev = 0;
   cudaGetDevice(&dev);
   std::atomic<int> next(0);
-  std::vector<int> rcs(count, SD_OK);
+  std::vector<int> rcs(ni, SD_OK);
   auto body = [&]() {
     cudaSetDevice(dev);
     for (;;) {
-      const int k = next.fetch_add(1);
-      if (k >= count) return;
-      rcs[k] = sd_step(hs[k], nsteps[k], infos ? infos[k] : nullptr);
+      const int w = next.fetch_add(1);
+      if (w >= ni) return;
+      const std::vector<int>& it = items[w];
+      if (it.size() == 1) {
+        const int k = it[0];
+        rcs[w] = sd_step(hs[k], nsteps[k], infos ? infos[k] : nullptr);
+      } else {
+        std::vector<sd_handle*> g;
+        std::vector<sd_step_info*> gi;
+        for (int k : it) {
+          g.push_back(hs[k]);
+          gi.push_back(infos ? infos[k] : nullptr);
+        }
+        rcs[w] = sdk::step_lockstep(g.data(), (int)g.size(), nsteps[it[0]], gi.data());
+      }
     }
   };
   std::vector<std::thread> th;
   for (int t = 0; t < nt; ++t) th.emplace_back(body);
   for (auto& t : th) t.join();
-  for (int k = 0; k < count; ++k)
-    if (rcs[k] != SD_OK) return rcs[k];
+  for (int w = 0; w < ni; ++w)
+    if (rcs[w] != SD_OK) return rcs[w];
   return SD_OK;
+}
+
+int sd_solve_batch(sd_handle* const* hs, int32_t count, const int32_t* nsteps, sd_step_info* const* infos,
+                   int32_t max_threads) {
+  return sd_solve_batch_ex(hs, count, nsteps, infos, max_threads, SD_BATCH_LOCKSTEP);
 }
 
 int sd_server_create(int64_t hbm_budget_bytes, int32_t max_running, const sd_options* opt, sd_server** out) {

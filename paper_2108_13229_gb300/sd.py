@@ -23,6 +23,7 @@ SD_TRI_SCHUR, SD_PV_BJ_I, SD_PV_BGS_I = 0, 1, 2
 SD_BC_MMS = 0
 SD_PROF_APPLY, SD_PROF_CHEB_V, SD_PROF_MUPDATE, SD_PROF_MDOT = 0, 1, 2, 3
 SD_NOALLOC_MAX_N = 256
+SD_BATCH_LOCKSTEP = 1
 
 
 class SdError(RuntimeError):
@@ -43,6 +44,7 @@ class sd_options(ctypes.Structure):
                 ("cheb_ratio", ctypes.c_double), ("schur_mass", ctypes.c_int32), ("fuse_coarse", ctypes.c_int32),
                 ("orth", ctypes.c_int32), ("reorth_eta", ctypes.c_double), ("extrapolate", ctypes.c_int32),
                 ("graph", ctypes.c_int32), ("pdl", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("tile_rows", ctypes.c_int32),
                 ("darcy_coupled", ctypes.c_int32),
                 ("stream", ctypes.c_void_p)]
 
@@ -87,6 +89,8 @@ _SIGS = {
     "sd_destroy": (None, [_vp]),
     "sd_solve_batch": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(ctypes.POINTER(sd_step_info)), ctypes.c_int32]),
+    "sd_solve_batch_ex": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.POINTER(sd_step_info)), ctypes.c_int32, ctypes.c_int32]),
     "sd_server_create": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(sd_options),
                                         ctypes.POINTER(_vp)]),
     "sd_submit": (ctypes.c_int, [_vp, ctypes.POINTER(sd_request), ctypes.POINTER(ctypes.c_uint64)]),
@@ -100,6 +104,9 @@ _SIGS = {
     "sd_struct_size": (ctypes.c_int64, [ctypes.c_int32]),
     "sd_apply_noalloc": (ctypes.c_int, [ctypes.POINTER(sd_grid), ctypes.c_double, _vp, ctypes.c_double,
                                         ctypes.c_double, _vp, _vp, _vp]),
+    "sd_autotune": (ctypes.c_int, [ctypes.POINTER(sd_grid), ctypes.c_double, _vp, ctypes.c_double, ctypes.c_double,
+                                   ctypes.POINTER(sd_options), ctypes.c_int32, ctypes.c_char_p,
+                                   ctypes.POINTER(sd_options), ctypes.POINTER(ctypes.c_double)]),
     "sd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
 
@@ -270,16 +277,22 @@ def sd_destroy(h: Handle) -> None:
         h.ptr = None
 
 
-def sd_solve_batch(handles, nsteps, max_threads: int = 0, raise_on_error: bool = True):
+def sd_solve_batch(handles, nsteps, max_threads: int = 0, raise_on_error: bool = True, lockstep: bool = True):
+    """Advance the handles together; lockstep=False: every instance on its own stream (sd_solve_batch_ex flags 0)."""
     cnt = len(handles)
     hs = (ctypes.c_void_p * cnt)(*[h.ptr for h in handles])
     ns = (ctypes.c_int32 * cnt)(*[int(k) for k in nsteps])
     bufs = [(sd_step_info * max(1, int(k)))() for k in nsteps]
     infos = (ctypes.POINTER(sd_step_info) * cnt)(*[ctypes.cast(b, ctypes.POINTER(sd_step_info)) for b in bufs])
-    rc = _load().sd_solve_batch(hs, cnt, ns, infos, int(max_threads))
+    rc = _load().sd_solve_batch_ex(hs, cnt, ns, infos, int(max_threads), SD_BATCH_LOCKSTEP if lockstep else 0)
     if raise_on_error:
         _check(rc, "sd_solve_batch")
     return [[bufs[k][q].as_dict() for q in range(int(nsteps[k]))] for k in range(cnt)]
+
+
+def sd_solve_batch_ex(handles, nsteps, max_threads: int = 0, flags: int = SD_BATCH_LOCKSTEP,
+                      raise_on_error: bool = True):
+    return sd_solve_batch(handles, nsteps, max_threads, raise_on_error, lockstep=bool(flags & SD_BATCH_LOCKSTEP))
 
 
 class Server:
@@ -360,6 +373,21 @@ def sd_apply_noalloc(n: int, mu: float, K, alpha_bj: float, dt: float, x, y, str
     g = sd_grid(n, n)
     _check(_load().sd_apply_noalloc(ctypes.byref(g), float(mu), _ptr(K, n * n), float(alpha_bj), float(dt),
                                     _ptr(x), _ptr(y), stream), "sd_apply_noalloc")
+
+
+def sd_autotune(n: int, mu: float, K, alpha_bj: float, dt: float, base: sd_options | None = None,
+                nsteps: int = 3, cache_path: str | None = None):
+    """(tuned sd_options, mean device ms per step of the winner); see include/sd.h."""
+    if isinstance(K, np.ndarray):
+        K = np.ascontiguousarray(K, dtype=np.float64)
+    g = sd_grid(n, n)
+    best = sd_options()
+    ms = ctypes.c_double()
+    rc = _load().sd_autotune(ctypes.byref(g), float(mu), _ptr(K, n * n), float(alpha_bj), float(dt),
+                             ctypes.byref(base) if base is not None else None, int(nsteps),
+                             cache_path.encode() if cache_path else None, ctypes.byref(best), ctypes.byref(ms))
+    _check(rc, "sd_autotune")
+    return best, ms.value
 
 
 def sd_struct_size(which: int) -> int:

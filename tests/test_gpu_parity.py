@@ -186,6 +186,38 @@ def test_batch_alone_vs_mixed(sd):
         assert np.array_equal(sd.sd_get_state(h)[2], xa)
 
 
+@pytest.mark.parametrize("precision", [1, 0])
+def test_lockstep_batch_bitwise(sd, precision):
+    # lockstep groups (same n): instances with their own K field, alpha_BJ
+    # and iteration counts share every launch; converged instances sit idle.
+    # Each result equals its solo run bit for bit, as does the
+    # one-stream-per-instance mode.  n = 48 (one group of three, 49 faces per
+    # row), n = 16 (fused coarse cycle from the fine level), one n = 40 alone.
+    cases = [(48, 1, 0.1), (48, 2, 3.0), (48, 3, 10.0), (16, 4, 0.3), (16, 5, 7.0), (40, 6, 1.0)]
+    def mk(n, seed, alpha):
+        K = I.lognormal_K(n, -4.0, 0.5 + 0.3 * seed, 16.0, seed=seed)
+        return make(sd, n, 1e-3, K, alpha, 0.1, precision)
+    alone, its_alone = [], []
+    for n, seed, alpha in cases:
+        h = mk(n, seed, alpha)
+        infos = sd.sd_step(h, 4)
+        alone.append(sd.sd_get_state(h)[2])
+        its_alone.append([i["iters"] for i in infos])
+    for lockstep in (True, False):
+        hs = [mk(n, seed, alpha) for n, seed, alpha in cases]
+        l0 = sd.sd_launch_count()
+        infos = sd.sd_solve_batch(hs, [4] * len(cases), lockstep=lockstep)
+        launches = sd.sd_launch_count() - l0
+        for h, xa, inf, ia in zip(hs, alone, infos, its_alone):
+            assert [i["iters"] for i in inf] == ia
+            assert all(i["status"] == 0 for i in inf)
+            assert np.array_equal(sd.sd_get_state(h)[2], xa)
+        if lockstep:
+            launches_lockstep = launches
+        else:
+            assert launches_lockstep < launches  # the groups share their launches
+
+
 def test_server_results_match_alone(sd):
     reqs = [(32, 5, 1), (64, 7, 2), (128, 4, 3), (32, 9, 4), (96, 6, 5), (64, 5, 6)]
     srv = sd.sd_server_create(8 << 30, 3)
@@ -290,14 +322,41 @@ def test_pdl_bitwise(sd):
     assert np.array_equal(xs[0], xs[1])
 
 
-@pytest.mark.parametrize("n", [64, 256])
+@pytest.mark.parametrize("n", [64, 96, 256])
 def test_tiled_smoothing_bitwise(sd, n):
     # all Chebyshev steps of a smoothing in one tiled kernel, prolongation folded
-    # in: the same arithmetic per point as the per-step kernels
+    # in, with 16- or 8-row tiles: the same arithmetic per point as the per-step
+    # kernels (n = 96: 97 faces per row, a one-face ragged tile column)
     K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=11)
     xs = []
-    for tile in (0, 1):
-        h = make(sd, n, 1e-3, K, 1.0, 0.05, 1, tile=tile)
+    for tile, rows in ((0, 16), (1, 16), (1, 8)):
+        h = make(sd, n, 1e-3, K, 1.0, 0.05, 1, tile=tile, tile_rows=rows)
         sd.sd_step(h, 3)
         xs.append(sd.sd_get_state(h)[2])
     assert np.array_equal(xs[0], xs[1])
+    assert np.array_equal(xs[0], xs[2])
+
+
+def test_autotune(sd, tmp_path):
+    # the tuner returns a candidate of its grid, caches it, and the tuned
+    # solver still matches the oracle's direct solves
+    n = 48
+    K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=12)
+    base = sd.sd_options_default()
+    base.rtol = 1e-12
+    cache = str(tmp_path / "tune.txt")
+    best, ms = sd.sd_autotune(n, 1e-3, K, 1.0, 0.05, base, 1, cache)
+    assert ms > 0
+    assert best.tile_rows in (8, 16) and best.coarsest in (4, 8, 16) and best.cheb_degree in (2, 3, 4)
+    assert best.rtol == base.rtol and best.restart == base.restart
+    lines = open(cache).read().splitlines()
+    assert len(lines) == 1 and lines[0].startswith("sdtune1 ")
+    again, ms2 = sd.sd_autotune(n, 1e-3, K, 1.0, 0.05, base, 1, cache)
+    assert (again.tile_rows, again.coarsest, again.cheb_degree) == (best.tile_rows, best.coarsest, best.cheb_degree)
+    assert abs(ms2 - ms) <= 1e-6 * ms and len(open(cache).read().splitlines()) == 1
+    o = O.Oracle(n, 1e-3, 1.0, 0.05, K)
+    xr = o.run(O.exact(n, 0.0, 1e-3), 0.0, 2)
+    h = sd.sd_create(n, 1e-3, K, 1.0, 0.05, best)
+    sd.sd_step(h, 2)
+    for k, e in fields_rel(sd.sd_get_state(h)[2], xr, n).items():
+        assert e <= 1e-8, (k, e)

@@ -76,6 +76,31 @@ extern "C" {
    sides, Dirichlet pressure at the pm bottom, no flow through the pm sides) */
 #define SD_BC_MMS 0
 
+/* coupling of the two subdomains in a time step:
+   SD_MONOLITHIC  one block-preconditioned FGMRES solve of Eq. (9) (Sec. 4);
+   SD_PARTITIONED the partitioned iteration of Sec. 3: the porous-medium
+                  solver takes the interface normal velocity as flux data
+                  (Eq. (7)) and passes on the pressure of the cells below the
+                  interface; the free-flow solver takes that pressure into the
+                  normal-stress balance of the interface faces (Eq. (5)) and
+                  passes on the new interface velocity; the fixed-point
+                  residual R(v) = S_ff(S_pm(v)) - v is driven to zero by
+                  IQN-ILS post-processing (relaxed first step, least-squares
+                  inverse-Jacobian model from the differences of the time
+                  step's earlier iterations), stopping when the exchanged
+                  pressure and velocity both change by less than coupling_eps
+                  relative (the test of Sec. 3).  Each subdomain solve is an
+                  FGMRES on that subdomain's rows of Eq. (9) with the other
+                  side held fixed, preconditioned by the same V-cycles (V and
+                  Schur blocks / D' block), to rtol.  The converged state is
+                  the monolithic solution.  Sec. 3 solves the free flow first
+                  with the velocity as its data; that order needs a pressure
+                  boundary in the free flow, which the SD_BC_MMS problem lacks
+                  (its free-flow block with a prescribed interface velocity is
+                  singular), so the porous medium goes first. */
+#define SD_MONOLITHIC 0
+#define SD_PARTITIONED 1
+
 typedef struct sd_handle sd_handle;
 typedef struct sd_server sd_server;
 
@@ -122,6 +147,14 @@ typedef struct {
                           the velocity; 0 drops it and overlaps the Darcy V-cycle with
                           the Stokes part on a second stream; 2 solves the Darcy block
                           first (B'_1 kept), concurrently with the pressure block */
+  int32_t coupling;    /* SD_MONOLITHIC (default) | SD_PARTITIONED */
+  int32_t coupling_max;     /* SD_PARTITIONED: coupling iterations per step (default 100) */
+  int32_t coupling_columns; /* SD_PARTITIONED: IQN-ILS difference columns kept, 1..30
+                               (default 30; the oldest is dropped) */
+  double coupling_eps;      /* SD_PARTITIONED: relative change of the exchanged pressure and
+                               velocity that ends the iteration (default 1e-9) */
+  double coupling_omega;    /* SD_PARTITIONED: relaxation of the first iteration of a step
+                               (default 0.1) */
   void *stream;        /* cudaStream_t to run on; NULL: the handle creates one */
 } sd_options;
 
@@ -132,6 +165,9 @@ typedef struct {
   double relres;    /* final true ||b - A x||_2 / ||b||_2 (FP64, recomputed) */
   double ms;        /* device time of the step (CUDA events) */
   int32_t reorths;  /* Arnoldi steps that took the second Gram-Schmidt pass */
+  int32_t coupling_iters; /* SD_PARTITIONED: subdomain-solve pairs of this step (0 otherwise);
+                             iters then counts the FGMRES iterations of all subdomain solves
+                             and relres is the monolithic residual of the coupled state */
 } sd_step_info;
 
 /* Fill *opt with the defaults above. */

@@ -125,8 +125,10 @@ struct sd_handle {
   bool own_stream = false;
   cudaStream_t s2 = nullptr;                   // second stream (Darcy V-cycle overlap)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  std::vector<cudaGraphExec_t> gexec;          // one captured Arnoldi step per basis index
-  std::vector<long long> gcount;               // kernels in each captured step
+  // one captured Arnoldi step per basis index, per solve mode (monolithic, and the
+  // free-flow and porous-medium subdomain solves of the partitioned coupling)
+  std::vector<cudaGraphExec_t> gexec[3];
+  std::vector<long long> gcount[3];            // kernels in each captured step
   Geom g;
   int nlev = 1;
   int m = 30;
@@ -140,6 +142,9 @@ struct sd_handle {
   MG<double> mg64;
   double *stage = nullptr, *x = nullptr, *xm = nullptr, *b = nullptr, *B0 = nullptr, *B1 = nullptr;
   double *V = nullptr, *Z = nullptr, *partial = nullptr, *scal = nullptr, *st = nullptr, *flag = nullptr;
+  // partitioned coupling: subdomain right-hand side and the IQN-ILS state
+  double* bsub = nullptr;
+  IqnState iqn;
   double* hflag = nullptr;  // pinned
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   double t = 0.0;
@@ -227,6 +232,25 @@ void plan_all(sd_handle* h) {
   h->scal = a.take<double>(256);
   h->st = a.take<double>((long long)(h->m + 1) * h->m + 3 * h->m + 1);
   h->flag = a.take<double>(8);
+  if (h->opt.coupling == SD_PARTITIONED) {
+    const int n = h->n, qm = h->opt.coupling_columns;
+    const long long ld = (n + 31) / 32 * 32;
+    h->bsub = a.take<double>(len);
+    IqnState& q = h->iqn;
+    q.n = n;
+    q.qmax = qm;
+    q.omega0 = h->opt.coupling_omega;
+    q.ld = ld;
+    q.v = a.take<double>(ld);
+    q.p_prev = a.take<double>(ld);
+    q.vt_prev = a.take<double>(ld);
+    q.r_prev = a.take<double>(ld);
+    q.Vc = a.take<double>(ld * qm);
+    q.Wc = a.take<double>(ld * qm);
+    q.Q = a.take<double>(ld * qm);
+    q.R = a.take<double>((long long)qm * qm);
+    q.scal = a.take<double>(8);
+  }
   if (h->opt.precision == SD_MIXED) plan_mg<float>(h, h->mg32, true);
   else plan_mg<double>(h, h->mg64, false);
 }
@@ -717,36 +741,106 @@ void apply_precond(sd_handle* h, const double* r, double* z) {
   else precond<double>(h, h->mg64, r, z);
 }
 
+// ------------------------------------------------ solve modes
+// FGMRES runs on the whole system (MODE_MONO) or, for the partitioned
+// coupling, on one subdomain's rows of Eq. (9) with the other subdomain's
+// unknowns held fixed: MODE_FF on the prefix [u | v | p_ff] of the
+// whole-system layout, MODE_PM on the suffix p_pm.  Vectors keep the
+// whole-system layout; a mode reads and writes only its own range.
+enum { MODE_MONO = 0, MODE_FF = 1, MODE_PM = 2 };
+
+struct Range {
+  long long off, len;
+};
+Range mode_range(const sd_handle* h, int mode) {
+  if (mode == MODE_FF) return {0, h->g.opm};
+  if (mode == MODE_PM) return {h->g.opm, h->g.lenD};
+  return {0, h->g.len};
+}
+
+// y = A_mode x, or y = b - A_mode x
+void apply_op(sd_handle* h, int mode, const double* x, const double* b, double* y) {
+  const Coef<double> c = coef64(h, 0);
+  if (mode == MODE_FF) {
+    launch_apply_ff(c, x, b, y, h->s);
+  } else if (mode == MODE_PM) {
+    const long long o = h->g.opm;
+    launch_resid_D<double>(c, x + o, b ? b + o : nullptr, y + o, b ? 0 : 2, 1, 0, h->s);
+  } else {
+    launch_apply_full(c, x, b, y, h->s);
+  }
+}
+
+// Subdomain preconditioners: the free-flow part of the block preconditioner
+// (Schur block and velocity V-cycle, no Darcy block) and the D' V-cycle.
+template <typename T>
+void precond_sub(sd_handle* h, MG<T>& M, int mode, const double* r, double* z) {
+  cudaStream_t s = h->s;
+  const Coef<double> c = coef64(h, 0);
+  if (mode == MODE_PM) {
+    launch_convert<T>(r + h->g.opm, M.L[0].D.b, h->g.lenD, s);
+    vcycle_cell<T>(M, 0, false, s, h);
+    launch_precond_exit<T>(c, z, M.L[0].D.res, s);
+    return;
+  }
+  const int pmode = h->opt.precond;
+  const bool tri = pmode == SD_TRI_SCHUR;
+  const double schur = tri ? h->mu / (h->opt.schur_gamma * h->g.h * h->g.h) : 1.0;
+  const T* eP = nullptr;
+  if (tri && h->opt.schur_mass) {
+    launch_convert<T>(r + h->g.opf, M.L[0].Pb.b, h->g.lenD, s);
+    vcycle_cell<T>(M, 0, true, s, h);
+    eP = M.L[0].Pb.res;
+  }
+  launch_precond_entry<T>(c, r, z, schur, eP, 1.0 / h->dt, tri, 0, M.L[0].V.b, s);
+  vcycle_V<T>(M, 0, s, h);
+  if (pmode == SD_PV_BGS_I) launch_precond_bgs_pff<T>(c, r, z, M.L[0].V.res, s);
+  launch_precond_mid<T>(c, r, z, M.L[0].V.res, 0, (T*)nullptr, s);
+}
+
+void apply_precond_mode(sd_handle* h, int mode, const double* r, double* z) {
+  if (mode == MODE_MONO) {
+    apply_precond(h, r, z);
+  } else if (h->opt.precision == SD_MIXED) {
+    precond_sub<float>(h, h->mg32, mode, r, z);
+  } else {
+    precond_sub<double>(h, h->mg64, mode, r, z);
+  }
+}
+
 // ----------------------------------------------------------- Arnoldi step
 // z_j = P^-1 v_j, w = A z_j, then w orthogonalised against v_0..v_j and the
 // new Hessenberg column rotated (Givens).  Orthogonalisation:
 //   orth 0: classical Gram-Schmidt with one re-orthogonalisation (CGS2);
 //   orth 1: the second pass only when the first removed most of w
 //           (||w'|| < eta ||w||, decided on the device).
-void arnoldi_orth(sd_handle* h, int j, const double* vj, double* zj, double* w) {
+void arnoldi_orth(sd_handle* h, int j, const double* vj, double* zj, double* w, int mode = MODE_MONO) {
   cudaStream_t s = h->s;
-  const long long len = h->g.len, vs = h->lenA;
-  const int nb = h->nblk, m = h->m, k = j + 1;
+  const Range rg = mode_range(h, mode);
+  const long long len = rg.len, vs = h->lenA;
+  const int nb = reduce_blocks(len), m = h->m, k = j + 1;
   double* sc = h->scal;
-  apply_precond(h, vj, zj);
+  apply_precond_mode(h, mode, vj, zj);
   {
-    ProfScope ps(h, SD_PROF_APPLY, apply_bytes(h->g, false), apply_flops(h->g));
-    launch_apply_full(coef64(h, 0), zj, nullptr, w, s);
+    ProfScope ps(h, mode == MODE_MONO ? SD_PROF_APPLY : -2, apply_bytes(h->g, false), apply_flops(h->g));
+    apply_op(h, mode, zj, nullptr, w);
   }
+  const double* Vb = h->V + rg.off;
+  w += rg.off;
   if (h->opt.orth == 0) {
     {
       ProfScope ps(h, SD_PROF_MDOT, 8.0 * (k + 1) * (double)len, 2.0 * k * (double)len);
-      launch_mdot(h->V, vs, k, w, len, h->partial, nb, nb, 0, nullptr, s);
+      launch_mdot(Vb, vs, k, w, len, h->partial, nb, nb, 0, nullptr, s);
     }
     launch_reduce(h->partial, nb, k, nb, sc + sd_handle::S_H1, 0, nullptr, s);
     {
       ProfScope ps(h, SD_PROF_MUPDATE, 8.0 * (k + 2) * (double)len, 4.0 * k * (double)len);
-      launch_mupdate(h->V, vs, k, sc + sd_handle::S_H1, w, len, h->partial, nb, nb, 1, nullptr, s);
+      launch_mupdate(Vb, vs, k, sc + sd_handle::S_H1, w, len, h->partial, nb, nb, 1, nullptr, s);
     }
     launch_reduce(h->partial, nb, k, nb, sc + sd_handle::S_H2, 0, nullptr, s);
     {
       ProfScope ps(h, SD_PROF_MUPDATE, 8.0 * (k + 2) * (double)len, 2.0 * (k + 1) * (double)len);
-      launch_mupdate(h->V, vs, k, sc + sd_handle::S_H2, w, len, h->partial, nb, nb, 2, nullptr, s);
+      launch_mupdate(Vb, vs, k, sc + sd_handle::S_H2, w, len, h->partial, nb, nb, 2, nullptr, s);
     }
     launch_reduce(h->partial, nb, 1, nb, sc + sd_handle::S_N2B, 0, nullptr, s);
     launch_givens(h->st, j, m, sc + sd_handle::S_H1, sc + sd_handle::S_H2, sc + sd_handle::S_N2,
@@ -755,19 +849,19 @@ void arnoldi_orth(sd_handle* h, int j, const double* vj, double* zj, double* w) 
     const double* reo = sc + sd_handle::S_REO;
     {
       ProfScope ps(h, SD_PROF_MDOT, 8.0 * (k + 1) * (double)len, 2.0 * (k + 1) * (double)len);
-      launch_mdot(h->V, vs, k, w, len, h->partial, nb, nb, 1, nullptr, s);
+      launch_mdot(Vb, vs, k, w, len, h->partial, nb, nb, 1, nullptr, s);
     }
     launch_reduce(h->partial, nb, k + 1, nb, sc + sd_handle::S_H1, 0, nullptr, s);
     {
       ProfScope ps(h, SD_PROF_MUPDATE, 8.0 * (k + 2) * (double)len, 2.0 * (k + 1) * (double)len);
-      launch_mupdate(h->V, vs, k, sc + sd_handle::S_H1, w, len, h->partial, nb, nb, 2, nullptr, s);
+      launch_mupdate(Vb, vs, k, sc + sd_handle::S_H1, w, len, h->partial, nb, nb, 2, nullptr, s);
     }
     launch_reduce(h->partial, nb, 1, nb, sc + sd_handle::S_N2, 0, nullptr, s);
     const double eta = h->opt.reorth_eta;
     launch_reorth_decide(sc + sd_handle::S_H1 + k, sc + sd_handle::S_N2, eta * eta, sc + sd_handle::S_REO, s);
-    launch_mdot(h->V, vs, k, w, len, h->partial, nb, nb, 0, reo, s);
+    launch_mdot(Vb, vs, k, w, len, h->partial, nb, nb, 0, reo, s);
     launch_reduce(h->partial, nb, k, nb, sc + sd_handle::S_H2, 0, reo, s);
-    launch_mupdate(h->V, vs, k, sc + sd_handle::S_H2, w, len, h->partial, nb, nb, 2, reo, s);
+    launch_mupdate(Vb, vs, k, sc + sd_handle::S_H2, w, len, h->partial, nb, nb, 2, reo, s);
     launch_reduce(h->partial, nb, 1, nb, sc + sd_handle::S_N2B, 0, reo, s);
     launch_givens(h->st, j, m, sc + sd_handle::S_H1, sc + sd_handle::S_H2, sc + sd_handle::S_N2,
                   sc + sd_handle::S_N2B, reo, h->flag, s);
@@ -778,13 +872,13 @@ void arnoldi_orth(sd_handle* h, int j, const double* vj, double* zj, double* w) 
 // Flexible GMRES(m) with CGS2 orthogonalisation, all FP64.  x holds the
 // initial guess.  The stopping test is the FP64 true residual
 // ||b - A x||_2 <= rtol ||b||_2, checked at every restart and at the end.
-int fgmres(sd_handle* h, const double* b, double* x, sd_step_info* info) {
+int fgmres(sd_handle* h, const double* b, double* x, sd_step_info* info, int mode = MODE_MONO) {
   cudaStream_t s = h->s;
-  const long long len = h->g.len, vs = h->lenA;
-  const int m = h->m, nb = h->nblk;
-  const Coef<double> c = coef64(h, 0);
+  const Range rg = mode_range(h, mode);
+  const long long len = rg.len, vs = h->lenA, o = rg.off;
+  const int m = h->m, nb = reduce_blocks(len);
   double* sc = h->scal;
-  launch_dot(b, b, len, h->partial, nb, sc + sd_handle::S_BN, s);
+  launch_dot(b + o, b + o, len, h->partial, nb, sc + sd_handle::S_BN, s);
   CK(cudaMemcpyAsync(h->hflag + 4, sc + sd_handle::S_BN, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   const double bnorm = std::sqrt(h->hflag[4]);
@@ -792,8 +886,8 @@ int fgmres(sd_handle* h, const double* b, double* x, sd_step_info* info) {
   int iters = 0, restarts = 0, status = SD_OK, reorths = 0;
   double relres = 0.0;
   for (;;) {
-    launch_apply_full(c, x, b, h->V, s);  // V_0 = b - A x
-    launch_dot(h->V, h->V, len, h->partial, nb, sc + sd_handle::S_B2, s);
+    apply_op(h, mode, x, b, h->V);  // V_0 = b - A x
+    launch_dot(h->V + o, h->V + o, len, h->partial, nb, sc + sd_handle::S_B2, s);
     CK(cudaMemcpyAsync(h->hflag + 5, sc + sd_handle::S_B2, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     const double beta = std::sqrt(h->hflag[5]);
@@ -803,34 +897,36 @@ int fgmres(sd_handle* h, const double* b, double* x, sd_step_info* info) {
     if (iters >= h->opt.max_iters) { status = SD_E_NOCONV; break; }
     ++restarts;
     launch_init_cycle(h->st, m, sc + sd_handle::S_B2, h->flag, s);
-    launch_scale_by(h->V, h->V, len, h->flag + 1, 0, s);
+    launch_scale_by(h->V + o, h->V + o, len, h->flag + 1, 0, s);
     int k = 0;
     bool numeric = false;
     for (int j = 0; j < m; ++j) {
       double* vj = h->V + (long long)j * vs;
       double* zj = h->Z + (long long)j * vs;
       double* w = h->V + (long long)(j + 1) * vs;
+      std::vector<cudaGraphExec_t>& gx = h->gexec[mode];
+      std::vector<long long>& gc = h->gcount[mode];
       if (h->opt.graph && h->prof_id < 0 && h->s != nullptr) {
-        if (!h->gexec[j]) {
+        if (!gx[j]) {
           cudaGraph_t gr = nullptr;
           const long long l0 = t_launch_count;
           CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-          arnoldi_orth(h, j, vj, zj, w);
-          launch_scale_by(w, w, len, h->flag + 1, 0, s);
+          arnoldi_orth(h, j, vj, zj, w, mode);
+          launch_scale_by(w + o, w + o, len, h->flag + 1, 0, s);
           CK(cudaStreamEndCapture(s, &gr));
-          const cudaError_t ie = cudaGraphInstantiate(&h->gexec[j], gr, 0);
+          const cudaError_t ie = cudaGraphInstantiate(&gx[j], gr, 0);
           cudaGraphDestroy(gr);
           CK(ie);
           // the capture went through the counting launch wrappers; replays are
           // credited with the same number of kernels
-          h->gcount[j] = t_launch_count - l0;
-          g_launch_count.fetch_sub(h->gcount[j]);
+          gc[j] = t_launch_count - l0;
+          g_launch_count.fetch_sub(gc[j]);
         }
-        CK(cudaGraphLaunch(h->gexec[j], s));
-        g_launch_count.fetch_add(h->gcount[j]);
+        CK(cudaGraphLaunch(gx[j], s));
+        g_launch_count.fetch_add(gc[j]);
       } else {
-        arnoldi_orth(h, j, vj, zj, w);
-        launch_scale_by(w, w, len, h->flag + 1, 0, s);
+        arnoldi_orth(h, j, vj, zj, w, mode);
+        launch_scale_by(w + o, w + o, len, h->flag + 1, 0, s);
       }
       CK(cudaMemcpyAsync(h->hflag, h->flag, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
@@ -843,7 +939,7 @@ int fgmres(sd_handle* h, const double* b, double* x, sd_step_info* info) {
     }
     if (numeric) { status = SD_E_NUMERIC; break; }
     launch_backsolve(h->st, k, m, sc + sd_handle::S_Y, nullptr, s);
-    launch_axpy_multi(x, h->Z, vs, sc + sd_handle::S_Y, k, len, nullptr, s);
+    launch_axpy_multi(x + o, h->Z + o, vs, sc + sd_handle::S_Y, k, len, nullptr, s);
   }
   CK(cudaGetLastError());
   if (info) {
@@ -852,6 +948,74 @@ int fgmres(sd_handle* h, const double* b, double* x, sd_step_info* info) {
     info->relres = relres;
     info->status = status;
     info->reorths = reorths;
+  }
+  return status;
+}
+
+// Partitioned coupling of Sec. 3 for one time step (include/sd.h,
+// SD_PARTITIONED): the Darcy solve with the interface flux given, the
+// free-flow solve with the pressure below the interface given, and the
+// IQN-ILS update of the interface velocity, until the exchanged pressure and
+// velocity both settle.  Both subdomain iterates live in the state vector x
+// (disjoint ranges), so the converged x is the coupled state.
+int step_partitioned(sd_handle* h, sd_step_info* info) {
+  cudaStream_t s = h->s;
+  const Geom& g = h->g;
+  IqnState& q = h->iqn;
+  const int n = h->n;
+  double* vG = h->x + g.ov;                                       // interface faces of the state
+  const double* pTop = h->x + g.opm + (long long)(n - 1) * g.P;  // pm cells below the interface
+  CK(cudaMemcpyAsync(q.v, vG, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemsetAsync(q.scal, 0, sizeof(double) * 8, s));
+  int iters = 0, it = 0, status = SD_OK, reorths = 0;
+  bool conv = false;
+  const double eps2 = h->opt.coupling_eps * h->opt.coupling_eps;
+  while (it < h->opt.coupling_max) {
+    ++it;
+    sd_step_info sp, sf;
+    std::memset(&sp, 0, sizeof(sp));
+    std::memset(&sf, 0, sizeof(sf));
+    launch_dn_rhs_pm(g, h->b, q.v, h->bsub, s);
+    int rc = fgmres(h, h->bsub, h->x, &sp, MODE_PM);
+    iters += sp.iters;
+    reorths += sp.reorths;
+    if (rc == SD_E_CUDA || rc == SD_E_NOMEM) return rc;
+    if (rc != SD_OK) { status = rc; break; }
+    launch_dn_rhs_ff(g, h->b, pTop, h->bsub, s);
+    rc = fgmres(h, h->bsub, h->x, &sf, MODE_FF);
+    iters += sf.iters;
+    reorths += sf.reorths;
+    if (rc == SD_E_CUDA || rc == SD_E_NOMEM) return rc;
+    if (rc != SD_OK) { status = rc; break; }
+    launch_iqn(q, vG, pTop, s);
+    CK(cudaMemcpyAsync(h->hflag + 8, q.scal + 2, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double* f = h->hflag + 8;  // |dp|^2 (negative: first evaluation), |p|^2, |dv|^2, |v~|^2
+    if (!std::isfinite(f[0]) || !std::isfinite(f[1]) || !std::isfinite(f[2]) || !std::isfinite(f[3])) {
+      status = SD_E_NUMERIC;
+      break;
+    }
+    if (f[0] >= 0.0 && f[0] <= eps2 * f[1] && f[2] <= eps2 * f[3]) {
+      conv = true;
+      break;
+    }
+  }
+  if (status == SD_OK && !conv) status = SD_E_NOCONV;
+  // residual of the coupled state in the monolithic system
+  double* sc = h->scal;
+  apply_op(h, MODE_MONO, h->x, h->b, h->V);
+  launch_dot(h->V, h->V, g.len, h->partial, h->nblk, sc + sd_handle::S_B2, s);
+  launch_dot(h->b, h->b, g.len, h->partial, h->nblk, sc + sd_handle::S_BN, s);
+  CK(cudaMemcpyAsync(h->hflag + 12, sc + sd_handle::S_B2, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h->hflag + 13, sc + sd_handle::S_BN, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (info) {
+    info->iters = iters;
+    info->restarts = 0;
+    info->relres = h->hflag[13] > 0 ? std::sqrt(h->hflag[12] / h->hflag[13]) : std::sqrt(h->hflag[12]);
+    info->status = status;
+    info->reorths = reorths;
+    info->coupling_iters = it;
   }
   return status;
 }
@@ -897,6 +1061,11 @@ int validate(const sd_grid* grid, double mu, double alpha, double dt, const sd_o
   if (o->orth < 0 || o->orth > 1 || !(o->reorth_eta > 0) || o->reorth_eta > 1) return SD_E_INVAL;
   if (o->darcy_coupled < 0 || o->darcy_coupled > 2) return SD_E_INVAL;
   if (o->tile_rows != 0 && o->tile_rows != 8 && o->tile_rows != 16) return SD_E_INVAL;
+  if (o->coupling != SD_MONOLITHIC && o->coupling != SD_PARTITIONED) return SD_E_INVAL;
+  if (o->coupling == SD_PARTITIONED &&
+      (o->coupling_max < 1 || o->coupling_columns < 1 || o->coupling_columns > 30 || !(o->coupling_eps > 0) ||
+       !(o->coupling_omega > 0) || !(o->coupling_omega <= 2)))
+    return SD_E_INVAL;
   if (o->cheb_degree_coarse < 0 || o->cheb_degree_coarse > 8 || o->schur_degree < 0 || o->schur_degree > 8)
     return SD_E_INVAL;
   int n = grid->nx, L = level_count(n, o->coarsest);
@@ -958,8 +1127,10 @@ int create_impl(const sd_grid* grid, double mu, const double* K, double alpha, d
   if (cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess)
     return fail(SD_E_CUDA);
-  h->gexec.assign(h->m, nullptr);
-  h->gcount.assign(h->m, 0);
+  for (int q = 0; q < 3; ++q) {
+    h->gexec[q].assign(h->m, nullptr);
+    h->gcount[q].assign(h->m, 0);
+  }
   if (prepare_coarse_cycle<float>() != 0 || prepare_coarse_cycle<double>() != 0) return fail(SD_E_CUDA);
   if (cudaEventCreate(&h->e0) != cudaSuccess || cudaEventCreate(&h->e1) != cudaSuccess) return fail(SD_E_CUDA);
   cudaStream_t s = h->s;
@@ -1022,7 +1193,8 @@ bool can_lockstep(const sd_handle* a, const sd_handle* b) {
                         x.schur_mass == y.schur_mass && x.fuse_coarse == y.fuse_coarse && x.orth == y.orth &&
                         x.reorth_eta == y.reorth_eta && x.extrapolate == y.extrapolate && x.graph == y.graph &&
                         x.pdl == y.pdl && x.tile == y.tile && x.tile_rows == y.tile_rows &&
-                        x.darcy_coupled == y.darcy_coupled;
+                        x.darcy_coupled == y.darcy_coupled && x.coupling == SD_MONOLITHIC &&
+                        y.coupling == SD_MONOLITHIC;
   return same_opt && a->n == b->n && a->mu == b->mu && a->dt == b->dt && a->ar.off == b->ar.off &&
          a->nlev == b->nlev && a->prof_id < 0 && b->prof_id < 0;
 }
@@ -1277,6 +1449,11 @@ void sd_options_default(sd_options* o) {
   o->tile = 1;
   o->tile_rows = 0;
   o->darcy_coupled = 1;
+  o->coupling = SD_MONOLITHIC;
+  o->coupling_max = 100;
+  o->coupling_columns = 30;
+  o->coupling_eps = 1e-9;
+  o->coupling_omega = 0.1;
   o->schur_gamma = 0.5;
   o->cheb_ratio = 8.0;
   o->schur_mass = 1;
@@ -1316,7 +1493,7 @@ int sd_step(sd_handle* h, int32_t nsteps, sd_step_info* info) {
     CKR(step_rhs(h, h->s));
     sd_step_info si;
     std::memset(&si, 0, sizeof(si));
-    const int rc = fgmres(h, h->b, h->x, &si);
+    const int rc = h->opt.coupling == SD_PARTITIONED ? step_partitioned(h, &si) : fgmres(h, h->b, h->x, &si);
     if (rc == SD_E_CUDA || rc == SD_E_NOMEM) return rc;
     CK(cudaEventRecord(h->e1, h->s));
     CK(cudaEventSynchronize(h->e1));
@@ -1453,8 +1630,9 @@ void sd_destroy(sd_handle* h) {
   if (h->s) cudaStreamSynchronize(h->s);
   for (auto& e : h->prof_ev)
     if (e) cudaEventDestroy(e);
-  for (auto& ge : h->gexec)
-    if (ge) cudaGraphExecDestroy(ge);
+  for (auto& gv : h->gexec)
+    for (auto& ge : gv)
+      if (ge) cudaGraphExecDestroy(ge);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->s2) {

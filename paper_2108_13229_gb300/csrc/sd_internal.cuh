@@ -175,6 +175,30 @@ void launch_convert(const double* src, T* dst, long long len, cudaStream_t s);
 
 // whole-system operator (FP64): y = A x  or  y = b - A x
 void launch_apply_full(const Coef<double>& c, const double* x, const double* b, double* y, cudaStream_t s);
+// the free-flow rows of it (u, v, p_ff) with the porous-medium unknowns taken as zero;
+// the Darcy rows of y are not written
+void launch_apply_ff(const Coef<double>& c, const double* x, const double* b, double* y, cudaStream_t s);
+// partitioned coupling: subdomain right-hand sides from the monolithic b.
+//   pm: bs[p_pm] = b[p_pm] - h v on the cells below the interface (v: n values)
+//   ff: bs[u, v, p_ff] = b + h p on the interface faces (p: n values, the pressure below)
+void launch_dn_rhs_pm(const Geom& g, const double* b, const double* v, double* bs, cudaStream_t s);
+void launch_dn_rhs_ff(const Geom& g, const double* b, const double* p, double* bs, cudaStream_t s);
+// IQN-ILS update of the interface velocity (one CTA; see sd_krylov.cu)
+struct IqnState {
+  int n, qmax;
+  double omega0;
+  double* v;        // current input v_k, replaced by v_{k+1}
+  double* p_prev;   // pressure and v~ of the previous evaluation, r_{k-1}
+  double* vt_prev;
+  double* r_prev;
+  double* Vc;       // difference columns dr (qmax x ld), oldest first
+  double* Wc;       // difference columns dv~
+  double* Q;        // orthonormal basis of the Vc columns (modified Gram-Schmidt)
+  double* R;        // upper triangle, column j at j * qmax
+  double* scal;     // [0] k, [1] q, [2..5] |p - p_prev|^2, |p|^2, |v~ - v|^2, |v~|^2
+  long long ld;     // column stride
+};
+void launch_iqn(const IqnState& st, const double* vt, const double* p, cudaStream_t s);
 
 // right-hand side: b = mass * xprev + B0 + s1 * B1; also writes the Dirichlet
 // values of b into x (so that the identity rows start exact)

@@ -473,6 +473,159 @@ void launch_gather_inst(const double* src, int count, double* out, cudaStream_t 
   launch_k(k_gather_inst, dim3(1), dim3(32), 0, s, src, count, out);
 }
 
+// ------------------------------------------------- IQN-ILS (partitioned, Sec. 3)
+// One CTA updates the interface velocity of the partitioned coupling: the
+// interface vectors have n entries (one per interface face), far too few to
+// fill the GPU, and every step depends on the one before.  Sums use a fixed
+// reduction order (warp shuffles, then the warps in order).
+
+// sum over the block of one value per thread; red holds 33 doubles
+__device__ double cta_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    red[32] = t;
+  }
+  __syncthreads();
+  const double t = red[32];
+  __syncthreads();
+  return t;
+}
+
+__device__ double cta_dot(const double* a, const double* b, int n, double* red) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s = fma(a[i], b[i], s);
+  return cta_sum(s, red);
+}
+
+// Orthogonalise difference column c of st.Vc (copied to Q column q) against
+// Q columns 0..q-1 (two Gram-Schmidt passes, projections added into R column
+// q); keeps it as Q column q when it is not numerically dependent.  Returns
+// the new column count.
+__device__ int iqn_append(const IqnState& st, int c, int q, double* red) {
+  const int n = st.n;
+  double* Vq = st.Vc + (long long)q * st.ld;
+  double* Wq = st.Wc + (long long)q * st.ld;
+  double* qq = st.Q + (long long)q * st.ld;
+  if (c != q) {
+    const double* Vs = st.Vc + (long long)c * st.ld;
+    const double* Ws = st.Wc + (long long)c * st.ld;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      Vq[i] = Vs[i];
+      Wq[i] = Ws[i];
+    }
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) qq[i] = Vq[i];
+  double* Rc = st.R + (long long)q * st.qmax;
+  for (int l = threadIdx.x; l <= q; l += blockDim.x) Rc[l] = 0.0;
+  __syncthreads();
+  const double n0 = sqrt(cta_dot(qq, qq, n, red));
+  for (int pass = 0; pass < 2; ++pass)
+    for (int l = 0; l < q; ++l) {
+      const double* ql = st.Q + (long long)l * st.ld;
+      const double cl = cta_dot(ql, qq, n, red);
+      for (int i = threadIdx.x; i < n; i += blockDim.x) qq[i] -= cl * ql[i];
+      if (threadIdx.x == 0) Rc[l] += cl;
+      __syncthreads();
+    }
+  const double nr = sqrt(cta_dot(qq, qq, n, red));
+  if (!(nr > 1e-13 * n0)) return q;  // dependent on the kept columns (or zero): dropped
+  const double inv = 1.0 / nr;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) qq[i] *= inv;
+  if (threadIdx.x == 0) Rc[q] = nr;
+  __syncthreads();
+  return q + 1;
+}
+
+__global__ void __launch_bounds__(1024) k_iqn(IqnState st, const double* __restrict__ vt, const double* __restrict__ p) {
+  griddep_wait();
+  __shared__ double red[33];
+  __shared__ double alpha[32];
+  const int n = st.n;
+  const int k = (int)st.scal[0];
+  int q = (int)st.scal[1];
+  double* v = st.v;
+  // stopping test of Sec. 3: changes of the exchanged pressure and velocity
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double dp = p[i] - st.p_prev[i], dv = vt[i] - v[i];
+    a0 = fma(dp, dp, a0);
+    a1 = fma(p[i], p[i], a1);
+    a2 = fma(dv, dv, a2);
+    a3 = fma(vt[i], vt[i], a3);
+  }
+  const double s0 = cta_sum(a0, red), s1 = cta_sum(a1, red), s2 = cta_sum(a2, red), s3 = cta_sum(a3, red);
+  if (threadIdx.x == 0) {
+    st.scal[2] = k == 0 ? -1.0 : s0;  // no previous pressure yet
+    st.scal[3] = s1;
+    st.scal[4] = s2;
+    st.scal[5] = s3;
+  }
+  if (k == 0) {  // relaxed first step
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double r = vt[i] - v[i];
+      st.r_prev[i] = r;
+      st.vt_prev[i] = vt[i];
+      st.p_prev[i] = p[i];
+      v[i] = fma(st.omega0, r, v[i]);
+    }
+  } else {
+    if (q == st.qmax) {  // drop the oldest difference and rebuild the factorisation
+      int kept = 0;
+      for (int c = 1; c < q; ++c) kept = iqn_append(st, c, kept, red);
+      q = kept;
+    }
+    // new differences dr = r_k - r_{k-1}, dv~ = v~_k - v~_{k-1} as column q
+    double* Vq = st.Vc + (long long)q * st.ld;
+    double* Wq = st.Wc + (long long)q * st.ld;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      Vq[i] = (vt[i] - v[i]) - st.r_prev[i];
+      Wq[i] = vt[i] - st.vt_prev[i];
+    }
+    __syncthreads();
+    q = iqn_append(st, q, q, red);
+    // alpha = argmin ||V alpha + r_k||: R alpha = -Q^T r_k
+    for (int l = 0; l < q; ++l) {
+      const double* ql = st.Q + (long long)l * st.ld;
+      double s = 0.0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) s = fma(ql[i], vt[i] - v[i], s);
+      s = cta_sum(s, red);
+      if (threadIdx.x == 0) alpha[l] = -s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int i = q - 1; i >= 0; --i) {
+        double s = alpha[i];
+        for (int l = i + 1; l < q; ++l) s -= st.R[(long long)l * st.qmax + i] * alpha[l];
+        alpha[i] = s / st.R[(long long)i * st.qmax + i];
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      double vn = vt[i];
+      for (int l = 0; l < q; ++l) vn = fma(alpha[l], st.Wc[(long long)l * st.ld + i], vn);
+      st.r_prev[i] = vt[i] - v[i];
+      st.vt_prev[i] = vt[i];
+      st.p_prev[i] = p[i];
+      v[i] = vn;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st.scal[0] = (double)(k + 1);
+    st.scal[1] = (double)q;
+  }
+}
+
+void launch_iqn(const IqnState& st, const double* vt, const double* p, cudaStream_t s) {
+  SD_COUNT(1);
+  launch_k(k_iqn, dim3(1), dim3(1024), 0, s, st, vt, p);
+}
+
 // ------------------------------------------------------ dense coarse solve
 template <typename T>
 __global__ void k_dense_solve(const double* __restrict__ Ainv, const int* __restrict__ idx, int m,

@@ -174,7 +174,10 @@ __device__ __forceinline__ void d_row(const Coef<T>& c, const T* __restrict__ p,
 }
 
 // ------------------------------------------------------- whole operator (K1)
-template <int R>
+// FF: the free-flow rows only (u, v, p_ff), with the porous-medium unknowns
+// taken as zero and the Darcy rows not written (subdomain solve of the
+// partitioned coupling).
+template <int R, bool FF>
 __global__ void k_apply_full(Coef<double> c, const double* __restrict__ x, const double* __restrict__ b,
                              double* __restrict__ y, Bat bt) {
   griddep_wait();
@@ -222,6 +225,7 @@ __global__ void k_apply_full(Coef<double> c, const double* __restrict__ x, const
         v_row(c, u, v, i, j, true, off, dg);
         val = dg * v[kv] + off;
         if (j > 0) val += h * (pf[kv] - pf[kv - P]);
+        else if (FF) val += h * pf[i];
         else val += h * pf[i] - h * pm[(long long)(n - 1) * P + i];
       }
       y[k] = b ? b[k] - val : val;
@@ -234,6 +238,7 @@ __global__ void k_apply_full(Coef<double> c, const double* __restrict__ x, const
       if (j + 1 <= n - 1) s += v[kc + P];
       const long long kp = (long long)(2 * n + 1) * P + kc;
       y[kp] = b ? b[kp] - h * s : h * s;
+      if (FF) continue;
       double off, dg;
       d_row(c, pm, i, j, true, off, dg);
       double val = dg * pm[kc] + off;
@@ -247,8 +252,54 @@ __global__ void k_apply_full(Coef<double> c, const double* __restrict__ x, const
 void launch_apply_full(const Coef<double>& c, const double* x, const double* b, double* y, cudaStream_t s) {
   SD_COUNT(1);
   const int R = rows_apply(c.n);
-  if (R == 4) launch_k(k_apply_full<4>, dim3(grid2R(c.n + 1, c.n + 1, 4)), dim3(dim3(BX, BY)), 0, s, c, x, b, y);
-  else launch_k(k_apply_full<1>, dim3(grid2R(c.n + 1, c.n + 1, 1)), dim3(dim3(BX, BY)), 0, s, c, x, b, y);
+  if (R == 4)
+    launch_k(k_apply_full<4, false>, dim3(grid2R(c.n + 1, c.n + 1, 4)), dim3(dim3(BX, BY)), 0, s, c, x, b, y);
+  else launch_k(k_apply_full<1, false>, dim3(grid2R(c.n + 1, c.n + 1, 1)), dim3(dim3(BX, BY)), 0, s, c, x, b, y);
+}
+
+void launch_apply_ff(const Coef<double>& c, const double* x, const double* b, double* y, cudaStream_t s) {
+  SD_COUNT(1);
+  const int R = rows_apply(c.n);
+  if (R == 4)
+    launch_k(k_apply_full<4, true>, dim3(grid2R(c.n + 1, c.n + 1, 4)), dim3(dim3(BX, BY)), 0, s, c, x, b, y);
+  else launch_k(k_apply_full<1, true>, dim3(grid2R(c.n + 1, c.n + 1, 1)), dim3(dim3(BX, BY)), 0, s, c, x, b, y);
+}
+
+// --------------------------------------------- partitioned coupling (Sec. 3)
+// Right-hand sides of the subdomain solves: the monolithic b with the other
+// subdomain's unknowns moved over.  Darcy: the top cells' outflow h v_Gamma
+// (block C'_1) with v_Gamma given.  Free flow: the -h p_pm term of the
+// v_Gamma rows (block B'_1) with the pressure below the interface given.
+__global__ void k_dn_rhs_pm(int n, int P, double h, const double* __restrict__ b, const double* __restrict__ v,
+                            double* __restrict__ bs) {
+  griddep_wait();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= n || j >= n) return;
+  const long long k = (long long)(3 * n + 1) * P + (long long)j * P + i;
+  bs[k] = j == n - 1 ? b[k] - h * v[i] : b[k];
+}
+
+__global__ void k_dn_rhs_ff(int n, int P, double h, const double* __restrict__ b, const double* __restrict__ p,
+                            double* __restrict__ bs) {
+  griddep_wait();
+  const long long len = (long long)(3 * n + 1) * P, ov = (long long)n * P;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len; e += (long long)gridDim.x * blockDim.x) {
+    const long long q = e - ov;
+    bs[e] = (q >= 0 && q < n) ? b[e] + h * p[q] : b[e];
+  }
+}
+
+void launch_dn_rhs_pm(const Geom& g, const double* b, const double* v, double* bs, cudaStream_t s) {
+  SD_COUNT(1);
+  launch_k(k_dn_rhs_pm, dim3(grid2(g.n, g.n)), dim3(dim3(BX, BY)), 0, s, g.n, g.P, g.h, b, v, bs);
+}
+
+void launch_dn_rhs_ff(const Geom& g, const double* b, const double* p, double* bs, cudaStream_t s) {
+  SD_COUNT(1);
+  const long long len = (long long)(3 * g.n + 1) * g.P;
+  const long long nb = (len + 255) / 256;
+  launch_k(k_dn_rhs_ff, dim3((int)(nb < 152 * 16 ? nb : 152 * 16)), dim3(256), 0, s, g.n, g.P, g.h, b, p, bs);
 }
 
 // ------------------------------------------------------ block V smoothers

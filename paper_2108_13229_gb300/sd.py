@@ -24,6 +24,7 @@ SD_BC_MMS = 0
 SD_PROF_APPLY, SD_PROF_CHEB_V, SD_PROF_MUPDATE, SD_PROF_MDOT = 0, 1, 2, 3
 SD_NOALLOC_MAX_N = 256
 SD_BATCH_LOCKSTEP = 1
+SD_MONOLITHIC, SD_PARTITIONED = 0, 1
 
 
 class SdError(RuntimeError):
@@ -45,13 +46,16 @@ class sd_options(ctypes.Structure):
                 ("orth", ctypes.c_int32), ("reorth_eta", ctypes.c_double), ("extrapolate", ctypes.c_int32),
                 ("graph", ctypes.c_int32), ("pdl", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("tile_rows", ctypes.c_int32),
-                ("darcy_coupled", ctypes.c_int32),
+                ("darcy_coupled", ctypes.c_int32), ("coupling", ctypes.c_int32),
+                ("coupling_max", ctypes.c_int32), ("coupling_columns", ctypes.c_int32),
+                ("coupling_eps", ctypes.c_double), ("coupling_omega", ctypes.c_double),
                 ("stream", ctypes.c_void_p)]
 
 
 class sd_step_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("restarts", ctypes.c_int32), ("status", ctypes.c_int32),
-                ("relres", ctypes.c_double), ("ms", ctypes.c_double), ("reorths", ctypes.c_int32)]
+                ("relres", ctypes.c_double), ("ms", ctypes.c_double), ("reorths", ctypes.c_int32),
+                ("coupling_iters", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -360,3 +360,42 @@ def test_autotune(sd, tmp_path):
     sd.sd_step(h, 2)
     for k, e in fields_rel(sd.sd_get_state(h)[2], xr, n).items():
         assert e <= 1e-8, (k, e)
+
+
+@pytest.mark.parametrize("n,precision", [(24, 1), (40, 0), (64, 1)])
+def test_partitioned_coupling_parity(sd, n, precision):
+    # Sec. 3 coupling (Darcy solve with the interface flux, free-flow solve with the
+    # pressure below, IQN-ILS on the interface velocity) against the oracle's
+    # monolithic direct solves: the coupled state is the monolithic solution, to the
+    # coupling tolerance; the number of coupling iterations matches the oracle's own
+    # partitioned iteration with exact subdomain solves within one
+    from oracle.partitioned import DNOracle
+    K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=20 + n)
+    o = O.Oracle(n, 1e-3, 1.0, 0.05, K)
+    x0 = O.exact(n, 0.0, 1e-3)
+    xr = o.run(x0, 0.0, 2)
+    h = make(sd, n, 1e-3, K, 1.0, 0.05, precision, rtol=1e-12, coupling=sd.SD_PARTITIONED, coupling_eps=1e-10)
+    infos = sd.sd_step(h, 2)
+    assert all(i["status"] == 0 and i["coupling_iters"] >= 2 for i in infos)
+    assert all(i["relres"] <= 1e-9 for i in infos)
+    for k, e in fields_rel(sd.sd_get_state(h)[2], xr, n).items():
+        assert e <= 1e-7, (k, e)
+    # first step from the same initial state: coupling iterations vs the oracle's
+    d = DNOracle(o, K)
+    b = o.rhs(x0, 0.05)
+    _, evals = d.solve(b, O.split(x0, n)["v"][0].copy(), eps=1e-10)
+    assert abs(infos[0]["coupling_iters"] - evals) <= 1, (infos[0]["coupling_iters"], evals)
+
+
+def test_partitioned_manufactured_solution(sd):
+    # the manufactured case through the partitioned coupling matches the oracle's
+    # monolithic run (mu = K = alpha = 1, dt = 0.1)
+    n = 32
+    K = np.ones(n * n)
+    o = O.Oracle(n, 1.0, 1.0, 0.1, K)
+    xr = o.run(O.exact(n, 0.0, 1.0), 0.0, 3)
+    h = make(sd, n, 1.0, K, 1.0, 0.1, 0, rtol=1e-12, coupling=sd.SD_PARTITIONED, coupling_eps=1e-10)
+    infos = sd.sd_step(h, 3)
+    assert all(i["status"] == 0 for i in infos)
+    for k, e in fields_rel(sd.sd_get_state(h)[2], xr, n).items():
+        assert e <= 1e-7, (k, e)

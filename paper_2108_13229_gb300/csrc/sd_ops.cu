@@ -50,12 +50,14 @@ __device__ __forceinline__ double sdiv(double a, double b) { return a / b; }
 // Terms are accumulated in a fixed order.
 //
 // Off-diagonal part and diagonal of the velocity-block row of interior u face (i, j).
-template <typename T>
+// IN: the caller guarantees 2 <= i <= n-2 and 1 <= j <= n-2 (no boundary term
+// applies); the same operations in the same order, without the masks.
+template <typename T, bool IN = false>
 __device__ __forceinline__ void u_row(const Coef<T>& c, const T* __restrict__ u, const T* __restrict__ v, int i,
                                       int j, bool read, T& off, T& diag) {
   const int n = c.n, P = c.P;
   const T mu = c.mu;
-  const bool top = j == n - 1, bot = j == 0;
+  const bool top = !IN && j == n - 1, bot = !IN && j == 0;
   T dg = c.d6;  // interior: h^2/dt + 4 mu (normal stress) + mu + mu (shear)
   T wh = T(0);
   if (top) dg += mu;  // wall at half distance above: 2 mu instead of mu
@@ -72,7 +74,7 @@ __device__ __forceinline__ void u_row(const Coef<T>& c, const T* __restrict__ u,
   const int rv1 = (j + 1) * P;
   const T uW = u[r0 + i - 1], uE = u[r0 + i + 1], uN = u[rN + i], uS = u[rS + i];
   const T vN = v[rv1 + i], vNW = v[rv1 + i - 1], vS = v[r0 + i], vSW = v[r0 + i - 1];
-  const T cW = (i - 1 >= 1) ? c.m2 : T(0), cE = (i + 1 <= n - 1) ? c.m2 : T(0);
+  const T cW = (IN || i - 1 >= 1) ? c.m2 : T(0), cE = (IN || i + 1 <= n - 1) ? c.m2 : T(0);
   T of = cW * uW;
   of = fma(cE, uE, of);
   if (!top) {
@@ -91,13 +93,14 @@ __device__ __forceinline__ void u_row(const Coef<T>& c, const T* __restrict__ u,
 }
 
 // Same for the v face (i, j), 0 <= j <= n-1 (j = 0: interface half control volume).
-template <typename T>
+// IN: 1 <= i <= n-2 and 1 <= j <= n-2.
+template <typename T, bool IN = false>
 __device__ __forceinline__ void v_row(const Coef<T>& c, const T* __restrict__ u, const T* __restrict__ v, int i,
                                       int j, bool read, T& off, T& diag) {
   const int n = c.n, P = c.P;
   const T mu = c.mu, h = c.h;
-  const bool left = i == 0, right = i == n - 1;
-  if (j == 0) {
+  const bool left = !IN && i == 0, right = !IN && i == n - 1;
+  if (!IN && j == 0) {
     const T wl = left ? T(0) : c.w[i], wr = right ? T(0) : c.w[i + 1];
     T dg = T(0.5) * c.cm + T(2) * mu + c.rg[i];
     dg += left ? mu : T(0.5) * h * wl;
@@ -133,7 +136,7 @@ __device__ __forceinline__ void v_row(const Coef<T>& c, const T* __restrict__ u,
   const int iE = right ? i : i + 1, iW = left ? i : i - 1;
   const T vS = v[rm + i], vN = v[rp + i], vE = v[r0 + iE], vW = v[r0 + iW];
   const T uE = u[r0 + i + 1], uES = u[rm + i + 1], uW = u[r0 + i], uWS = u[rm + i];
-  const T cN = (j + 1 <= n - 1) ? c.m2 : T(0);
+  const T cN = (IN || j + 1 <= n - 1) ? c.m2 : T(0);
   T of = c.m2 * vS;
   of = fma(cN, vN, of);
   if (!right) {
@@ -150,7 +153,8 @@ __device__ __forceinline__ void v_row(const Coef<T>& c, const T* __restrict__ u,
 }
 
 // Darcy row of pm cell (i, j) (D' block only, no interface flux).
-template <typename T>
+// IN: 1 <= i <= n-2 and 1 <= j <= n-2.
+template <typename T, bool IN = false>
 __device__ __forceinline__ void d_row(const Coef<T>& c, const T* __restrict__ p, int i, int j, bool read, T& off,
                                       T& diag) {
   const int n = c.n, P = c.P;
@@ -162,10 +166,10 @@ __device__ __forceinline__ void d_row(const Coef<T>& c, const T* __restrict__ p,
     off = T(0);
     return;
   }
-  const T pW = p[r0 + (i > 0 ? i - 1 : i)], pE = p[r0 + (i < n - 1 ? i + 1 : i)];
-  const T pS = p[(j > 0 ? r0 - P : r0) + i], pN = p[(j < n - 1 ? r0 + P : r0) + i];
-  const T cW = i > 0 ? tw : T(0), cE = i < n - 1 ? te : T(0);
-  const T cS = j > 0 ? ts : T(0), cN = j < n - 1 ? tn : T(0);
+  const T pW = p[r0 + ((IN || i > 0) ? i - 1 : i)], pE = p[r0 + ((IN || i < n - 1) ? i + 1 : i)];
+  const T pS = p[((IN || j > 0) ? r0 - P : r0) + i], pN = p[((IN || j < n - 1) ? r0 + P : r0) + i];
+  const T cW = (IN || i > 0) ? tw : T(0), cE = (IN || i < n - 1) ? te : T(0);
+  const T cS = (IN || j > 0) ? ts : T(0), cN = (IN || j < n - 1) ? tn : T(0);
   T of = cW * pW;
   of = fma(cE, pE, of);
   of = fma(cS, pS, of);
@@ -305,21 +309,21 @@ void launch_dn_rhs_ff(const Geom& g, const double* b, const double* p, double* b
 // ------------------------------------------------------ block V smoothers
 // One Chebyshev step at position (i, j) of the velocity block (u face (i,j)
 // if j < n, v face (i,j) if i < n).  Dirichlet faces take x = b exactly.
-template <typename T>
+template <typename T, bool IN = false>
 __device__ __forceinline__ void cheb_V_at2(const Coef<T>& c, const T* __restrict__ uin, const T* __restrict__ vin,
                                            const T* __restrict__ bu, const T* __restrict__ bv, T* __restrict__ du,
                                            T* __restrict__ dv, T* __restrict__ uout, T* __restrict__ vout, T a, T cc,
                                            int i, int j) {
   const int n = c.n, P = c.P;
   const bool rd = uin != nullptr;
-  if (j < n) {
+  if (IN || j < n) {
     const int k = j * P + i;
-    if (i == 0 || i == n) {
+    if (!IN && (i == 0 || i == n)) {
       uout[k] = bu[k];
       du[k] = T(0);
     } else {
       T off, dg;
-      u_row(c, uin, vin, i, j, rd, off, dg);
+      u_row<T, IN>(c, uin, vin, i, j, rd, off, dg);
       const T xc = rd ? uin[k] : T(0);
       const T r = bu[k] - (dg * xc + off);
       const T dn = (a != T(0) ? a * du[k] : T(0)) + sdiv(cc * r, dg);
@@ -327,14 +331,14 @@ __device__ __forceinline__ void cheb_V_at2(const Coef<T>& c, const T* __restrict
       uout[k] = xc + dn;
     }
   }
-  if (i < n) {
+  if (IN || i < n) {
     const int k = j * P + i;
-    if (j == n) {
+    if (!IN && j == n) {
       vout[k] = bv[k];
       dv[k] = T(0);
     } else {
       T off, dg;
-      v_row(c, uin, vin, i, j, rd, off, dg);
+      v_row<T, IN>(c, uin, vin, i, j, rd, off, dg);
       const T xc = rd ? vin[k] : T(0);
       const T r = bv[k] - (dg * xc + off);
       const T dn = (a != T(0) ? a * dv[k] : T(0)) + sdiv(cc * r, dg);
@@ -460,13 +464,13 @@ void launch_resid_V(const Coef<T>& c, const T* x, const T* b, T* r, int jac, int
 }
 
 // ------------------------------------------------------ block D' smoothers
-template <typename T>
+template <typename T, bool IN = false>
 __device__ __forceinline__ void cheb_D_at(const Coef<T>& c, const T* __restrict__ xin, const T* __restrict__ b,
                                           T* __restrict__ d, T* __restrict__ xout, T a, T cc, int i, int j) {
   const int k = j * c.P + i;
   const bool rd = xin != nullptr;
   T off, dg;
-  d_row(c, xin, i, j, rd, off, dg);
+  d_row<T, IN>(c, xin, i, j, rd, off, dg);
   const T xc = rd ? xin[k] : T(0);
   const T r = b[k] - (dg * xc + off);
   const T dn = (a != T(0) ? a * d[k] : T(0)) + sdiv(cc * r, dg);
@@ -911,12 +915,21 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_D(Coef<T> c, const T* __res
   T* xb = sx1 - sh;
   const T* cur = xin ? xa : nullptr;
   T* nxt = xb;
+  // every point the first step computes is an interior cell: no boundary term anywhere
+  const bool inner = ilo + 1 >= 1 && ilo + EX - 2 <= n - 2 && jlo + 1 >= 1 && jlo + EY - 2 <= n - 2;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     const int lo = s + 1, w = EX - 2 * lo, hgt = EY - 2 * lo;
-    for (int p = threadIdx.x; p < w * hgt; p += TLT) {
-      const int gi = ilo + lo + p % w, gj = jlo + lo + p / w;
-      if (gi >= 0 && gj >= 0 && gi < n && gj < n) cheb_D_at(tc, cur, bq, dq, nxt, cs.a[s], cs.c[s], gi, gj);
+    if (inner) {
+      for (int p = threadIdx.x; p < w * hgt; p += TLT) {
+        const int gi = ilo + lo + p % w, gj = jlo + lo + p / w;
+        cheb_D_at<T, true>(tc, cur, bq, dq, nxt, cs.a[s], cs.c[s], gi, gj);
+      }
+    } else {
+      for (int p = threadIdx.x; p < w * hgt; p += TLT) {
+        const int gi = ilo + lo + p % w, gj = jlo + lo + p / w;
+        if (gi >= 0 && gj >= 0 && gi < n && gj < n) cheb_D_at(tc, cur, bq, dq, nxt, cs.a[s], cs.c[s], gi, gj);
+      }
     }
     __syncthreads();
     cur = nxt;
@@ -1009,13 +1022,22 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_V(Coef<T> c, const T* __res
   const T* curv = xin ? av : nullptr;
   T* nxu = cu2;
   T* nxv = cv2;
+  // every point the first step computes has interior u and v faces: no boundary term anywhere
+  const bool inner = ilo + 1 >= 2 && ilo + EX - 2 <= n - 2 && jlo + 1 >= 1 && jlo + EY - 2 <= n - 2;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     const int lo = s + 1, w = EX - 2 * lo, hgt = EY - 2 * lo;
-    for (int p = threadIdx.x; p < w * hgt; p += TLT) {
-      const int gi = ilo + lo + p % w, gj = jlo + lo + p / w;
-      if (gi >= 0 && gj >= 0 && gi <= n && gj <= n)
-        cheb_V_at2(tc, curu, curv, bu, bv, du, dv, nxu, nxv, cs.a[s], cs.c[s], gi, gj);
+    if (inner) {
+      for (int p = threadIdx.x; p < w * hgt; p += TLT) {
+        const int gi = ilo + lo + p % w, gj = jlo + lo + p / w;
+        cheb_V_at2<T, true>(tc, curu, curv, bu, bv, du, dv, nxu, nxv, cs.a[s], cs.c[s], gi, gj);
+      }
+    } else {
+      for (int p = threadIdx.x; p < w * hgt; p += TLT) {
+        const int gi = ilo + lo + p % w, gj = jlo + lo + p / w;
+        if (gi >= 0 && gj >= 0 && gi <= n && gj <= n)
+          cheb_V_at2(tc, curu, curv, bu, bv, du, dv, nxu, nxv, cs.a[s], cs.c[s], gi, gj);
+      }
     }
     __syncthreads();
     curu = nxu;

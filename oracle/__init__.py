@@ -45,6 +45,11 @@ def _load():
     lib = ctypes.CDLL(build())
     lib.or_create.restype = ctypes.c_void_p
     lib.or_create.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp]
+    lib.or_create_bc.restype = ctypes.c_void_p
+    lib.or_create_bc.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, ctypes.c_int,
+                                 ctypes.c_double, ctypes.c_double]
+    lib.or_p_in.restype = ctypes.c_double
+    lib.or_p_in.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
     lib.or_destroy.argtypes = [ctypes.c_void_p]
     lib.or_ndof.restype = ctypes.c_int64
     lib.or_ndof.argtypes = [ctypes.c_void_p]
@@ -119,14 +124,27 @@ def mms(name: str, *args) -> float:
     return float(getattr(_load(), "or_mms_" + name)(*[float(a) for a in args]))
 
 
-class Oracle:
-    """Assembled FP64 system of one instance (n cells per side per subdomain)."""
+def p_in(dp: float, t_end: float, t: float) -> float:
+    """Inflow pressure of the paper's pressure-driven problem (bc 2): half cosine from 0 to dp over [0, t_end]."""
+    return float(_load().or_p_in(float(dp), float(t_end), float(t)))
 
-    def __init__(self, n: int, mu: float, alpha: float, dt: float, K):
+
+class Oracle:
+    """Assembled FP64 system of one instance (n cells per side per subdomain).
+
+    bc 0: manufactured solution, Dirichlet velocity on the free-flow sides;
+    bc 1: manufactured solution with traction free-flow sides;
+    bc 2: the paper's pressure-driven problem (inflow pressure p_in(t) with
+    amplitude dp and ramp time t_end on the left, zero on the right).
+    """
+
+    def __init__(self, n: int, mu: float, alpha: float, dt: float, K, bc: int = 0, dp: float = 1.0,
+                 t_end: float = 1.0):
         K = _f64(K).reshape(n, n)
         self.n, self.mu, self.alpha, self.dt = n, float(mu), float(alpha), float(dt)
+        self.bc, self.dp, self.t_end = int(bc), float(dp), float(t_end)
         self._lib = _load()
-        self._c = self._lib.or_create(n, self.mu, self.alpha, self.dt, _ptr(K))
+        self._c = self._lib.or_create_bc(n, self.mu, self.alpha, self.dt, _ptr(K), self.bc, self.dp, self.t_end)
         if not self._c:
             raise ValueError("oracle: invalid parameters")
         self.ndof = int(self._lib.or_ndof(self._c))

@@ -34,12 +34,25 @@
  *                is eliminated from the shear flux of the bottom u rows.
  *   time         backward Euler (Sec. 2), mass h^2/dt on velocity rows
  *                (h^2/(2 dt) on the half control volume of v_Gamma).
- *   boundaries   the manufactured solution (below) gives Dirichlet velocity
- *                on the ff top, left and right sides, Dirichlet pressure on
- *                the pm bottom, no flow through the pm sides.  Dirichlet
- *                velocity faces are kept as DoFs with identity rows; their
- *                values are moved into the right-hand side of every row that
- *                touches them.
+ *   boundaries   bc 0: the manufactured solution (below) gives Dirichlet
+ *                velocity on the ff top, left and right sides, Dirichlet
+ *                pressure on the pm bottom, no flow through the pm sides.
+ *                Dirichlet velocity faces are kept as DoFs with identity rows;
+ *                their values are moved into the right-hand side of every row
+ *                that touches them.
+ *                bc 1 and 2: the ff left and right sides are traction
+ *                boundaries instead: the normal stress -p + 2 mu du/dx equals
+ *                -P_b and the tangential velocity is V_b there.  The u faces
+ *                on them are unknowns whose rows are the x-momentum balance of
+ *                the half control volume inside the domain (as for v_Gamma),
+ *                the corner shear taken at half distance from V_b and, at the
+ *                interface corner, through the eliminated BJS slip.
+ *                bc 1: P_b, V_b, top and pm data from the manufactured
+ *                solution (a test of the traction rows).
+ *                bc 2: the paper's pressure-driven problem (Sec. 5): P_b =
+ *                p_in(t) = dp (1 - cos(pi min(t, t_end)/t_end))/2 on the left,
+ *                0 on the right, V_b = 0, no slip on the top, p = 0 on the pm
+ *                bottom, no flow through the pm sides, no sources.
  *
  * Manufactured solution (constructed for testing; the paper has none):
  *   psi = sin(pi x) phi(y),  phi(y) = 1 + A (y-1) + (y-1)^2,  A = pi^2 + 2,
@@ -86,6 +99,8 @@ double or_mms_fy(double x, double y, double t, double mu) {
 typedef struct {
   int n;
   double h, mu, alpha, dt;
+  int bc;                    /* 0, 1, 2: see the header */
+  double dp, tend;           /* bc 2: inflow pressure amplitude and ramp time */
   double *K;                 /* n*n, row j*n+i, j = 0 at y = 0 */
   int64_t ndof, nnz;
   int64_t *rowptr;
@@ -119,6 +134,13 @@ static double bjs_w(const or_ctx *c, int i) {
   double beta = sk / c->alpha;
   return c->mu / (c->h + 2.0 * beta);
 }
+/* BJS shear coefficient at a traction side's u face above Gamma (i = 0 or n):
+   only one pm cell below it */
+static double bjs_w_side(const or_ctx *c, int i) {
+  int n = c->n, ic = i == 0 ? 0 : n - 1;
+  double beta = sqrt(kc(c, ic, n - 1)) / c->alpha;
+  return c->mu / (c->h + 2.0 * beta);
+}
 /* TPFA reconstruction of p_pm on Gamma adds mu h^2/(2 K_c) to the v_Gamma row */
 static double gam_r(const or_ctx *c, int i) { return c->mu * c->h * c->h / (2.0 * kc(c, i, c->n - 1)); }
 
@@ -145,12 +167,39 @@ static void build_row(const or_ctx *c, int64_t row, row_t *r) {
   const double h = c->h, mu = c->mu, cm = h * h / c->dt;
   r->cnt = 0;
   const int64_t nu = (int64_t)n * (n + 1), nv = nu, np = (int64_t)n * n;
+  const int lat = c->bc != 0;  /* traction sides */
   if (row < nu) { /* u row */
     int j = (int)(row / (n + 1)), i = (int)(row % (n + 1));
-    if (i == 0 || i == n) { radd(r, row, 1.0); return; }
+    if ((i == 0 || i == n) && !lat) { radd(r, row, 1.0); return; }
+    if (i == 0 || i == n) {                      /* traction side: half control volume */
+      const double sg = i == 0 ? 1.0 : -1.0;     /* mirror for the right side */
+      const int ii = i == 0 ? 1 : n - 1;         /* inner u neighbour */
+      const int ic = i == 0 ? 0 : n - 1;         /* adjacent ff cell column */
+      double diag = 0.5 * cm + 2.0 * mu;
+      radd(r, ix_u(n, ii, j), -2.0 * mu);
+      radd(r, ix_pf(n, ic, j), sg * h);
+      if (j < n - 1) {
+        diag += 0.5 * mu;
+        radd(r, ix_u(n, i, j + 1), -0.5 * mu);
+        radd(r, ix_v(n, ic, j + 1), -sg * mu);
+      } else {
+        diag += mu;                              /* wall at y = 2, half distance */
+      }
+      if (j > 0) {
+        diag += 0.5 * mu;
+        radd(r, ix_u(n, i, j - 1), -0.5 * mu);
+        radd(r, ix_v(n, ic, j), sg * mu);
+      } else {                                   /* interface corner: BJS slip eliminated */
+        double w = bjs_w_side(c, i);
+        diag += h * w;
+        radd(r, ix_v(n, ic, 0), sg * h * w);
+      }
+      radd(r, row, diag);
+      return;
+    }
     double diag = cm + 4.0 * mu;                 /* BE mass + normal stress 2mu d2u/dx2 */
-    if (i - 1 >= 1) radd(r, ix_u(n, i - 1, j), -2.0 * mu);
-    if (i + 1 <= n - 1) radd(r, ix_u(n, i + 1, j), -2.0 * mu);
+    if (i - 1 >= 1 || lat) radd(r, ix_u(n, i - 1, j), -2.0 * mu);
+    if (i + 1 <= n - 1 || lat) radd(r, ix_u(n, i + 1, j), -2.0 * mu);
     if (j < n - 1) {                             /* shear through the top corner */
       diag += mu;
       radd(r, ix_u(n, i, j + 1), -mu);
@@ -190,6 +239,10 @@ static void build_row(const or_ctx *c, int64_t row, row_t *r) {
         radd(r, ix_u(n, i, 0), w * h);
         radd(r, ix_v(n, i - 1, 0), -0.5 * h * w);
         diag += 0.5 * h * w;
+      } else if (lat) {                          /* traction side corner, BJS */
+        double w = bjs_w_side(c, 0);
+        radd(r, ix_u(n, 0, 0), w * h);
+        diag += h * w;
       } else {
         diag += mu;
       }
@@ -198,6 +251,10 @@ static void build_row(const or_ctx *c, int64_t row, row_t *r) {
         radd(r, ix_u(n, i + 1, 0), -w * h);
         radd(r, ix_v(n, i + 1, 0), -0.5 * h * w);
         diag += 0.5 * h * w;
+      } else if (lat) {
+        double w = bjs_w_side(c, n);
+        radd(r, ix_u(n, n, 0), -w * h);
+        diag += h * w;
       } else {
         diag += mu;
       }
@@ -213,7 +270,11 @@ static void build_row(const or_ctx *c, int64_t row, row_t *r) {
       radd(r, ix_u(n, i + 1, j), -mu);
       radd(r, ix_u(n, i + 1, j - 1), mu);
     } else {
-      diag += 2.0 * mu;
+      diag += 2.0 * mu;                          /* tangential velocity given at half distance */
+      if (lat) {
+        radd(r, ix_u(n, n, j), -mu);
+        radd(r, ix_u(n, n, j - 1), mu);
+      }
     }
     if (i > 0) {
       diag += mu;
@@ -222,6 +283,10 @@ static void build_row(const or_ctx *c, int64_t row, row_t *r) {
       radd(r, ix_u(n, i, j - 1), -mu);
     } else {
       diag += 2.0 * mu;
+      if (lat) {
+        radd(r, ix_u(n, 0, j), mu);
+        radd(r, ix_u(n, 0, j - 1), -mu);
+      }
     }
     radd(r, ix_pf(n, i, j), h);
     radd(r, ix_pf(n, i, j - 1), -h);
@@ -231,8 +296,8 @@ static void build_row(const or_ctx *c, int64_t row, row_t *r) {
   row -= nv;
   if (row < np) { /* continuity of ff cell (i, j), Eq. (2) */
     int j = (int)(row / n), i = (int)(row % n);
-    if (i + 1 <= n - 1) radd(r, ix_u(n, i + 1, j), h);
-    if (i >= 1) radd(r, ix_u(n, i, j), -h);
+    if (i + 1 <= n - 1 || lat) radd(r, ix_u(n, i + 1, j), h);
+    if (i >= 1 || lat) radd(r, ix_u(n, i, j), -h);
     if (j + 1 <= n - 1) radd(r, ix_v(n, i, j + 1), h);
     radd(r, ix_v(n, i, j), -h);
     return;
@@ -252,10 +317,11 @@ static void build_row(const or_ctx *c, int64_t row, row_t *r) {
   }
 }
 
-or_ctx *or_create(int n, double mu, double alpha, double dt, const double *K) {
-  if (n < 2 || !(mu > 0) || !(alpha > 0) || !(dt > 0) || !K) return NULL;
+or_ctx *or_create_bc(int n, double mu, double alpha, double dt, const double *K, int bc, double dp, double tend) {
+  if (n < 2 || !(mu > 0) || !(alpha > 0) || !(dt > 0) || !K || bc < 0 || bc > 2 || !(tend > 0)) return NULL;
   or_ctx *c = (or_ctx *)calloc(1, sizeof(or_ctx));
   c->n = n; c->h = 1.0 / n; c->mu = mu; c->alpha = alpha; c->dt = dt;
+  c->bc = bc; c->dp = dp; c->tend = tend;
   c->K = (double *)malloc(sizeof(double) * (size_t)n * n);
   memcpy(c->K, K, sizeof(double) * (size_t)n * n);
   c->ndof = or_dof_count(n);
@@ -274,6 +340,10 @@ or_ctx *or_create(int n, double mu, double alpha, double dt, const double *K) {
   }
   c->nnz = nz;
   return c;
+}
+
+or_ctx *or_create(int n, double mu, double alpha, double dt, const double *K) {
+  return or_create_bc(n, mu, alpha, dt, K, 0, 0.0, 1.0);
 }
 
 void or_destroy(or_ctx *c) {
@@ -320,8 +390,35 @@ void or_exact(int n, double t, double mu, double *x) {
 /* Right-hand side of the implicit-Euler step to time t (Sec. 2)             */
 /* xprev: solution at the previous time level (only its velocities enter)    */
 /* ------------------------------------------------------------------------ */
+/* inflow pressure of the paper's problem (bc 2): half cosine from 0 to dp over [0, t_end] */
+double or_p_in(double dp, double tend, double t) {
+  double s = t < tend ? t : tend;
+  return dp * 0.5 * (1.0 - cos(OR_PI * s / tend));
+}
+
+/* traction-side data: P_b (minus the prescribed normal stress) and V_b (tangential velocity) */
+static double side_p(const or_ctx *c, int right, double y, double t) {
+  if (c->bc == 2) return right ? 0.0 : or_p_in(c->dp, c->tend, t);
+  double x = right ? 1.0 : 0.0;
+  double ux = OR_PI * cos(OR_PI * x) * mms_dphi(y) * (1.0 + t);  /* du/dx of the manufactured u */
+  return or_mms_pff(x, y, t, c->mu) - 2.0 * c->mu * ux;
+}
+static double side_v(const or_ctx *c, int right, double y, double t) {
+  return c->bc == 2 ? 0.0 : or_mms_v(right ? 1.0 : 0.0, y, t);
+}
+/* boundary data of the other sides and the sources: manufactured (bc 0, 1) or zero (bc 2) */
+static double dat_u(const or_ctx *c, double x, double y, double t) { return c->bc == 2 ? 0.0 : or_mms_u(x, y, t); }
+static double dat_v(const or_ctx *c, double x, double y, double t) { return c->bc == 2 ? 0.0 : or_mms_v(x, y, t); }
+static double dat_ppm(const or_ctx *c, double x, double y, double t) { return c->bc == 2 ? 0.0 : or_mms_ppm(x, y, t); }
+static double dat_fx(const or_ctx *c, double x, double y, double t) {
+  return c->bc == 2 ? 0.0 : or_mms_fx(x, y, t, c->mu);
+}
+static double dat_fy(const or_ctx *c, double x, double y, double t) {
+  return c->bc == 2 ? 0.0 : or_mms_fy(x, y, t, c->mu);
+}
+
 void or_rhs(const or_ctx *c, const double *xprev, double t, double *b) {
-  const int n = c->n;
+  const int n = c->n, lat = c->bc != 0;
   const double h = c->h, mu = c->mu, cm = h * h / c->dt;
   /* u rows */
   for (int j = 0; j < n; ++j) {
@@ -329,12 +426,23 @@ void or_rhs(const or_ctx *c, const double *xprev, double t, double *b) {
     for (int i = 0; i <= n; ++i) {
       int64_t k = ix_u(n, i, j);
       double x = i * h;
-      if (i == 0 || i == n) { b[k] = or_mms_u(x, y, t); continue; }
-      double s = cm * xprev[k] + h * h * or_mms_fx(x, y, t, mu);
-      if (i == 1) s += 2.0 * mu * or_mms_u(0.0, y, t);
-      if (i == n - 1) s += 2.0 * mu * or_mms_u(1.0, y, t);
+      if ((i == 0 || i == n) && !lat) { b[k] = dat_u(c, x, y, t); continue; }
+      if (i == 0 || i == n) {                   /* traction side, half control volume */
+        const int rt = i == n;
+        const double sg = rt ? -1.0 : 1.0;
+        double s = 0.5 * cm * xprev[k] + 0.5 * h * h * dat_fx(c, x, y, t) + sg * h * side_p(c, rt, y, t);
+        if (j < n - 1) s -= sg * mu * side_v(c, rt, 1.0 + (j + 1) * h, t);
+        else s += mu * dat_u(c, x, 2.0, t) + sg * mu * (dat_v(c, x + sg * 0.5 * h, 2.0, t) - dat_v(c, x, 2.0, t));
+        if (j > 0) s += sg * mu * side_v(c, rt, 1.0 + j * h, t);
+        else s += sg * h * bjs_w_side(c, i) * side_v(c, rt, 1.0, t);
+        b[k] = s;
+        continue;
+      }
+      double s = cm * xprev[k] + h * h * dat_fx(c, x, y, t);
+      if (i == 1 && !lat) s += 2.0 * mu * dat_u(c, 0.0, y, t);
+      if (i == n - 1 && !lat) s += 2.0 * mu * dat_u(c, 1.0, y, t);
       if (j == n - 1)
-        s += 2.0 * mu * or_mms_u(x, 2.0, t) + mu * (or_mms_v(x + 0.5 * h, 2.0, t) - or_mms_v(x - 0.5 * h, 2.0, t));
+        s += 2.0 * mu * dat_u(c, x, 2.0, t) + mu * (dat_v(c, x + 0.5 * h, 2.0, t) - dat_v(c, x - 0.5 * h, 2.0, t));
       b[k] = s;
     }
   }
@@ -344,18 +452,30 @@ void or_rhs(const or_ctx *c, const double *xprev, double t, double *b) {
     for (int i = 0; i < n; ++i) {
       int64_t k = ix_v(n, i, j);
       double x = (i + 0.5) * h;
-      if (j == n) { b[k] = or_mms_v(x, 2.0, t); continue; }
+      if (j == n) { b[k] = dat_v(c, x, 2.0, t); continue; }
       if (j == 0) {
-        double s = 0.5 * cm * xprev[k] + 0.5 * h * h * or_mms_fy(x, 1.0, t, mu);
-        if (i == 0) s += -mu * (or_mms_u(0.0, 1.0 + 0.5 * h, t) - or_mms_u(0.0, 1.0, t)) + mu * or_mms_v(0.0, 1.0, t);
-        if (i == n - 1) s += mu * (or_mms_u(1.0, 1.0 + 0.5 * h, t) - or_mms_u(1.0, 1.0, t)) + mu * or_mms_v(1.0, 1.0, t);
+        double s = 0.5 * cm * xprev[k] + 0.5 * h * h * dat_fy(c, x, 1.0, t);
+        if (i == 0) {
+          if (lat) s += h * bjs_w_side(c, 0) * side_v(c, 0, 1.0, t);
+          else s += -mu * (dat_u(c, 0.0, 1.0 + 0.5 * h, t) - dat_u(c, 0.0, 1.0, t)) + mu * dat_v(c, 0.0, 1.0, t);
+        }
+        if (i == n - 1) {
+          if (lat) s += h * bjs_w_side(c, n) * side_v(c, 1, 1.0, t);
+          else s += mu * (dat_u(c, 1.0, 1.0 + 0.5 * h, t) - dat_u(c, 1.0, 1.0, t)) + mu * dat_v(c, 1.0, 1.0, t);
+        }
         b[k] = s;
         continue;
       }
-      double s = cm * xprev[k] + h * h * or_mms_fy(x, y, t, mu);
-      if (j == n - 1) s += 2.0 * mu * or_mms_v(x, 2.0, t);
-      if (i == 0) s += 2.0 * mu * or_mms_v(0.0, y, t) - mu * (or_mms_u(0.0, y + 0.5 * h, t) - or_mms_u(0.0, y - 0.5 * h, t));
-      if (i == n - 1) s += 2.0 * mu * or_mms_v(1.0, y, t) + mu * (or_mms_u(1.0, y + 0.5 * h, t) - or_mms_u(1.0, y - 0.5 * h, t));
+      double s = cm * xprev[k] + h * h * dat_fy(c, x, y, t);
+      if (j == n - 1) s += 2.0 * mu * dat_v(c, x, 2.0, t);
+      if (i == 0) {
+        if (lat) s += 2.0 * mu * side_v(c, 0, y, t);
+        else s += 2.0 * mu * dat_v(c, 0.0, y, t) - mu * (dat_u(c, 0.0, y + 0.5 * h, t) - dat_u(c, 0.0, y - 0.5 * h, t));
+      }
+      if (i == n - 1) {
+        if (lat) s += 2.0 * mu * side_v(c, 1, y, t);
+        else s += 2.0 * mu * dat_v(c, 1.0, y, t) + mu * (dat_u(c, 1.0, y + 0.5 * h, t) - dat_u(c, 1.0, y - 0.5 * h, t));
+      }
       b[k] = s;
     }
   }
@@ -364,9 +484,9 @@ void or_rhs(const or_ctx *c, const double *xprev, double t, double *b) {
     double y = 1.0 + (j + 0.5) * h;
     for (int i = 0; i < n; ++i) {
       double s = 0.0;
-      if (i == 0) s += h * or_mms_u(0.0, y, t);
-      if (i == n - 1) s -= h * or_mms_u(1.0, y, t);
-      if (j == n - 1) s -= h * or_mms_v((i + 0.5) * h, 2.0, t);
+      if (i == 0 && !lat) s += h * dat_u(c, 0.0, y, t);
+      if (i == n - 1 && !lat) s -= h * dat_u(c, 1.0, y, t);
+      if (j == n - 1) s -= h * dat_v(c, (i + 0.5) * h, 2.0, t);
       b[ix_pf(n, i, j)] = s;
     }
   }
@@ -374,7 +494,7 @@ void or_rhs(const or_ctx *c, const double *xprev, double t, double *b) {
   for (int j = 0; j < n; ++j)
     for (int i = 0; i < n; ++i) {
       double s = 0.0;
-      if (j == 0) s += 2.0 * kc(c, i, 0) / c->mu * or_mms_ppm((i + 0.5) * h, 0.0, t);
+      if (j == 0) s += 2.0 * kc(c, i, 0) / c->mu * dat_ppm(c, (i + 0.5) * h, 0.0, t);
       b[ix_pm(n, i, j)] = s;
     }
 }

@@ -218,3 +218,82 @@ def test_mms_detects_planted_inconsistency(alpha, kval):
     # another value in the oracle must stop convergence
     e1, e2 = _mms_errors(32, alpha, kval), _mms_errors(64, alpha, kval)
     assert max(np.log2(e1[k] / e2[k]) for k in e1) < 1.0
+
+
+# ---------------------------------------------------------------------------
+# traction free-flow sides (bc 1: manufactured data; bc 2: the paper's
+# pressure-driven problem)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("bc", [1, 2])
+def test_traction_sides_structure(bc):
+    # the half-control-volume rows of the side u faces keep the symmetric
+    # saddle-point form (V = V^T, C = -B^T); no identity rows remain on the sides
+    n = 6
+    K = I.lognormal_K(n, -4.0, 1.0, 3.0, seed=4)
+    o = O.Oracle(n, 1e-3, 0.8, 0.05, K, bc=bc)
+    A = o.scipy_csr().toarray()
+    off = O.offsets(n)
+    S = np.ones(o.ndof)
+    S[off["p_ff"]:] = -1.0
+    SA = S[:, None] * A
+    assert np.abs(SA - SA.T).max() <= 1e-14 * np.abs(A).max()
+    for j in range(n):
+        for i in (0, n):
+            k = off["u"] + j * (n + 1) + i
+            assert np.count_nonzero(A[k]) >= 5  # a momentum row, not an identity
+    # the same DoF count (Table 1)
+    assert o.ndof == 4 * n * n + 2 * n
+    # the gradient of a constant ff pressure now also acts on the side faces
+    one = np.zeros(o.ndof)
+    one[off["p_ff"]:off["p_pm"]] = 1.0
+    y = (A @ one)[off["u"]:off["v"]].reshape(n, n + 1)
+    assert np.allclose(y[:, 0], 1.0 / n) and np.allclose(y[:, n], -1.0 / n)
+    assert np.abs(y[:, 1:n]).max() == 0.0
+
+
+def test_traction_sides_second_order():
+    # manufactured solution with traction sides (P_b = p - 2 mu du/dx, V_b = v)
+    def errs(n, steps=10, dt=0.1):
+        o = O.Oracle(n, 1.0, 1.0, dt, I.constant_K(n), bc=1)
+        x = o.run(O.exact(n, 0.0, 1.0), 0.0, steps)
+        xe = O.exact(n, steps * dt, 1.0)
+        h = 1.0 / n
+        fs, fe = O.split(x, n), O.split(xe, n)
+        return {k: float(np.sqrt(h * h * np.sum((fs[k] - fe[k]) ** 2))) for k in fs}
+    e = [errs(n) for n in (16, 32, 64, 128)]
+    orders = [{k: np.log2(a[k] / b[k]) for k in a} for a, b in zip(e, e[1:])]
+    for k in ("u", "v", "p_pm", "p_ff"):
+        assert orders[-1][k] >= 1.8, (k, orders)
+
+
+def test_inflow_pressure_half_cosine():
+    assert O.p_in(2.0, 10.0, 0.0) == 0.0
+    assert abs(O.p_in(2.0, 10.0, 5.0) - 1.0) <= 1e-15
+    assert abs(O.p_in(2.0, 10.0, 10.0) - 2.0) <= 1e-15
+    assert O.p_in(2.0, 10.0, 30.0) == O.p_in(2.0, 10.0, 10.0)
+    assert O.p_in(2.0, 10.0, 2.5) < O.p_in(2.0, 10.0, 7.5)
+
+
+def test_pressure_driven_problem_mass_balance():
+    # the paper's problem: flow enters on the left, leaves on the right and
+    # through the porous medium; every cell conserves mass, the interface flux
+    # is the same on both sides, and the pm passes it on to its bottom
+    n, mu, dt, t_end = 16, 1e-3, 0.2, 2.0
+    K = I.lognormal_K(n, -4.0, 1.0, 4.0, seed=5)
+    o = O.Oracle(n, mu, 1.0, dt, K, bc=2, dp=1.0, t_end=t_end)
+    x = o.run(np.zeros(o.ndof), 0.0, 5)
+    f = O.split(x, n)
+    h = 1.0 / n
+    u, v, ppm = f["u"], f["v"], f["p_pm"]
+    div = h * (u[:, 1:] - u[:, :-1] + v[1:, :] - v[:-1, :])
+    assert np.abs(div).max() <= 1e-12 * h * np.abs(u).max()
+    assert np.abs(v[n]).max() == 0.0  # no slip on the top
+    q_in, q_out = h * u[:, 0].sum(), h * u[:, n].sum()
+    q_gamma = -h * v[0].sum()  # downward into the porous medium
+    assert q_in > 0 and q_out > 0 and q_gamma > 0
+    assert abs(q_in - q_out - q_gamma) <= 1e-12 * q_in
+    q_bottom = (2.0 * K[0] / mu * ppm[0]).sum()  # out through p = 0 at y = 0
+    assert abs(q_gamma - q_bottom) <= 1e-10 * q_gamma
+    # with the pressure drop still rising the flow accelerates
+    x1 = o.run(x, 5 * dt, 1)
+    assert h * O.split(x1, n)["u"][:, 0].sum() > q_in

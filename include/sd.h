@@ -72,9 +72,30 @@ extern "C" {
 #define SD_PV_BJ_I 1
 #define SD_PV_BGS_I 2
 
-/* boundary data: manufactured solution (Dirichlet ff velocity on the top and
-   sides, Dirichlet pressure at the pm bottom, no flow through the pm sides) */
+/* boundary conditions and data:
+   SD_BC_MMS           manufactured solution: Dirichlet ff velocity on the top
+                       and the sides x = 0, 1, Dirichlet pressure at the pm
+                       bottom, no flow through the pm sides; the state starts
+                       at the exact solution of t = 0;
+   SD_BC_MMS_TRACTION  the same solution with traction ff sides: on x = 0, 1
+                       the normal stress -p + 2 mu du/dx and the tangential
+                       velocity are prescribed (from the solution), and the
+                       side u faces are unknowns whose rows are the x-momentum
+                       balance of the half control volume inside the domain
+                       (corner shear at half distance from the side's
+                       tangential velocity, the interface corner through the
+                       eliminated BJS slip of Eq. (6));
+   SD_BC_PAPER         the pressure-driven problem of Sec. 5 on the square
+                       geometry of Table 1: traction sides with the inflow
+                       pressure p_in(t) = bc_dp (1 - cos(pi min(t, T)/T)) / 2
+                       on the left (a half-cosine rise over [0, T], T =
+                       bc_tend or 25 time steps when 0) and 0 on the right,
+                       no tangential velocity on the sides, no slip on the
+                       top, p = 0 at the pm bottom, no flow through the pm
+                       sides, no sources; the state starts at rest. */
 #define SD_BC_MMS 0
+#define SD_BC_MMS_TRACTION 1
+#define SD_BC_PAPER 2
 
 /* coupling of the two subdomains in a time step:
    SD_MONOLITHIC  one block-preconditioned FGMRES solve of Eq. (9) (Sec. 4);
@@ -115,7 +136,7 @@ typedef struct {
   int32_t max_iters;   /* FGMRES iterations allowed per time step (default 600) */
   int32_t precision;   /* SD_FP64 | SD_MIXED (default SD_MIXED) */
   int32_t precond;     /* SD_TRI_SCHUR | SD_PV_BJ_I | SD_PV_BGS_I (default SD_TRI_SCHUR) */
-  int32_t bc;          /* SD_BC_MMS */
+  int32_t bc;          /* SD_BC_MMS (default) | SD_BC_MMS_TRACTION | SD_BC_PAPER */
   int32_t cheb_degree; /* Chebyshev smoothing steps before and after each coarse
                           correction (default 3) */
   int32_t cheb_degree_coarse; /* the same below the finest level (0: cheb_degree) */
@@ -155,6 +176,9 @@ typedef struct {
                                velocity that ends the iteration (default 1e-9) */
   double coupling_omega;    /* SD_PARTITIONED: relaxation of the first iteration of a step
                                (default 0.1) */
+  double bc_dp;        /* SD_BC_PAPER: amplitude of the inflow pressure (default 1) */
+  double bc_tend;      /* SD_BC_PAPER: rise time T of the inflow pressure (default 0:
+                          25 time steps) */
   void *stream;        /* cudaStream_t to run on; NULL: the handle creates one */
 } sd_options;
 

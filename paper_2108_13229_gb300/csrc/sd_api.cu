@@ -260,6 +260,7 @@ Coef<double> coef64(sd_handle* h, int l, bool poisson = false) {
   LevelCoef<double>& C = h->c64[l];
   Coef<double> c;
   c.n = g.n; c.P = g.P; c.h = g.h; c.mu = h->mu; c.cm = g.h * g.h / h->dt;
+  c.lat = h->opt.bc != SD_BC_MMS;
   c.w = poisson ? C.wP : C.w;
   c.rg = poisson ? C.rgP : C.rg;
   c.Tx = poisson ? C.TxP : C.Tx;
@@ -274,6 +275,7 @@ void bind_coef(sd_handle* h, MG<T>& M) {
     MGLevel<T>& L = M.L[l];
     const Geom& g = h->geo[l];
     L.c.n = g.n; L.c.P = g.P; L.c.h = (T)g.h; L.c.mu = (T)h->mu; L.c.cm = (T)(g.h * g.h / h->dt);
+    L.c.lat = h->opt.bc != SD_BC_MMS;
     L.cP = L.c;
     L.c.w = L.own.w; L.c.rg = L.own.rg; L.c.Tx = L.own.Tx; L.c.Ty = L.own.Ty;
     L.cP.w = L.own.wP; L.cP.rg = L.own.rgP; L.cP.Tx = L.own.TxP; L.cP.Ty = L.own.TyP;
@@ -600,7 +602,7 @@ void vcycle_V(MG<T>& M, int l, cudaStream_t s, sd_handle* prof_owner) {
     }
   }
   launch_resid_V<T>(L.c, cur, B.b, B.r, 0, 1, 0, s);
-  launch_restrict_V<T>(L.g.n, L.g.P, B.r, C.g.n, C.g.P, C.V.b, s);
+  launch_restrict_V<T>(L.g.n, L.g.P, B.r, C.g.n, C.g.P, C.V.b, L.c.lat, s);
   vcycle_V(M, l + 1, s, prof_owner);
   if (tiles) {  // prolongation folded into the post-smoothing tile load
     T* out = (cur == B.x) ? B.x2 : B.x;
@@ -609,7 +611,7 @@ void vcycle_V(MG<T>& M, int l, cudaStream_t s, sd_handle* prof_owner) {
       launch_smooth_tile_V<T>(L.c, cur, B.b, out, steps_of(B, h_tile_rows), B.cht, C.V.res, C.g.n, C.g.P, s);
     cur = out;
   } else {
-    launch_prolong_V<T>(L.g.n, L.g.P, cur, C.g.n, C.g.P, C.V.res, s);
+    launch_prolong_V<T>(L.g.n, L.g.P, cur, C.g.n, C.g.P, C.V.res, L.c.lat, s);
     for (int k = 0; k < (int)B.cha.size(); ++k) {
       T* out = (cur == B.x) ? B.x2 : B.x;
       {
@@ -1020,18 +1022,30 @@ int step_partitioned(sd_handle* h, sd_step_info* info) {
   return status;
 }
 
+// Time function of the boundary and source data B1: 1 + t for the
+// manufactured cases; for the pressure-driven problem (Sec. 5) the inflow
+// pressure, a half cosine from 0 to bc_dp over [0, t_end] (t_end = bc_tend,
+// or 25 steps when 0), constant afterwards.
+double data_scale(const sd_handle* h, double t) {
+  if (h->opt.bc != SD_BC_PAPER) return 1.0 + t;
+  const double te = h->opt.bc_tend > 0 ? h->opt.bc_tend : 25.0 * h->dt;
+  const double s = t < te ? t : te;
+  return h->opt.bc_dp * 0.5 * (1.0 - std::cos(3.14159265358979323846 * s / te));
+}
+
 // Right-hand side and initial guess of the next implicit-Euler step, queued on s.
 int step_rhs(sd_handle* h, cudaStream_t s) {
   const double cm = h->g.h * h->g.h / h->dt;
   const double tn = h->t + h->dt;
+  const int lat = h->opt.bc != SD_BC_MMS;
   if (h->opt.extrapolate && h->have_prev) {
     // initial guess 2 x^n - x^{n-1}; x_m then holds x^n, the mass-term source
     launch_extrapolate(h->x, h->xm, h->g.len, s);
-    launch_rhs(h->g, cm, h->B0, h->B1, 1.0 + tn, h->xm, h->b, h->x, s);
+    launch_rhs(h->g, lat, cm, h->B0, h->B1, data_scale(h, tn), h->xm, h->b, h->x, s);
   } else {
     // the previous state is both the mass-term source and the initial guess
     CK(cudaMemcpyAsync(h->xm, h->x, sizeof(double) * h->g.len, cudaMemcpyDeviceToDevice, s));
-    launch_rhs(h->g, cm, h->B0, h->B1, 1.0 + tn, h->x, h->b, h->x, s);
+    launch_rhs(h->g, lat, cm, h->B0, h->B1, data_scale(h, tn), h->x, h->b, h->x, s);
   }
   h->have_prev = true;
   return SD_OK;
@@ -1055,7 +1069,9 @@ int validate(const sd_grid* grid, double mu, double alpha, double dt, const sd_o
     return SD_E_INVAL;
   if (o->restart < 1 || o->restart > 30 || !(o->rtol > 0) || o->max_iters < 1) return SD_E_INVAL;
   if (o->precision != SD_FP64 && o->precision != SD_MIXED) return SD_E_INVAL;
-  if (o->precond < SD_TRI_SCHUR || o->precond > SD_PV_BGS_I || o->bc != SD_BC_MMS) return SD_E_INVAL;
+  if (o->precond < SD_TRI_SCHUR || o->precond > SD_PV_BGS_I) return SD_E_INVAL;
+  if (o->bc != SD_BC_MMS && o->bc != SD_BC_MMS_TRACTION && o->bc != SD_BC_PAPER) return SD_E_INVAL;
+  if (!std::isfinite(o->bc_dp) || !(o->bc_tend >= 0) || !std::isfinite(o->bc_tend)) return SD_E_INVAL;
   if (o->cheb_degree < 1 || o->cheb_degree > 8 || o->coarsest < 2 || !(o->schur_gamma > 0) || !(o->cheb_ratio > 1))
     return SD_E_INVAL;
   if (o->orth < 0 || o->orth > 1 || !(o->reorth_eta > 0) || o->reorth_eta > 1) return SD_E_INVAL;
@@ -1143,7 +1159,7 @@ int create_impl(const sd_grid* grid, double mu, const double* K, double alpha, d
   for (int l = 0; l < h->nlev; ++l) {
     LevelCoef<double>& C = h->c64[l];
     const Geom& g = h->geo[l];
-    launch_setup_coef<double>(h->Klev[l], g.n, g.P, mu, alpha, C.w, C.rg, C.Tx, C.Ty, s);
+    launch_setup_coef<double>(h->Klev[l], g.n, g.P, mu, alpha, o.bc != SD_BC_MMS, C.w, C.rg, C.Tx, C.Ty, s);
   }
   // pressure Laplacian B^T B / h^2: TPFA with K / mu = 1 (the staging buffer
   // holds the unit permeability, the Krylov slots are free during setup)
@@ -1151,11 +1167,15 @@ int create_impl(const sd_grid* grid, double mu, const double* K, double alpha, d
     LevelCoef<double>& C = h->c64[l];
     const Geom& g = h->geo[l];
     launch_fill_K(h->V, g.n, g.P, mu, s);
-    launch_setup_coef<double>(h->V, g.n, g.P, mu, alpha, C.wP, C.rgP, C.TxP, C.TyP, s);
+    launch_setup_coef<double>(h->V, g.n, g.P, mu, alpha, o.bc != SD_BC_MMS, C.wP, C.rgP, C.TxP, C.TyP, s);
   }
   const Coef<double> c0 = coef64(h, 0);
-  launch_mms_terms(c0, h->Klev[0], h->B0, h->B1, s);
-  launch_mms_exact(h->g, mu, 0.0, h->x, s);
+  launch_mms_terms(c0, o.bc, h->Klev[0], h->B0, h->B1, s);
+  if (o.bc == SD_BC_PAPER) {  // the pressure-driven problem starts from rest
+    if (cudaMemsetAsync(h->x, 0, sizeof(double) * h->g.len, s) != cudaSuccess) return fail(SD_E_CUDA);
+  } else {
+    launch_mms_exact(h->g, mu, 0.0, h->x, s);
+  }
   int rc = (h->opt.precision == SD_MIXED) ? setup_mg<float>(h, h->mg32) : setup_mg<double>(h, h->mg64);
   if (rc != SD_OK) return fail(rc);
   // the setup used the Krylov slots as scratch: clear them (padding must be zero)
@@ -1193,7 +1213,8 @@ bool can_lockstep(const sd_handle* a, const sd_handle* b) {
                         x.schur_mass == y.schur_mass && x.fuse_coarse == y.fuse_coarse && x.orth == y.orth &&
                         x.reorth_eta == y.reorth_eta && x.extrapolate == y.extrapolate && x.graph == y.graph &&
                         x.pdl == y.pdl && x.tile == y.tile && x.tile_rows == y.tile_rows &&
-                        x.darcy_coupled == y.darcy_coupled && x.coupling == SD_MONOLITHIC &&
+                        x.darcy_coupled == y.darcy_coupled && x.bc_dp == y.bc_dp && x.bc_tend == y.bc_tend &&
+                        x.coupling == SD_MONOLITHIC &&
                         y.coupling == SD_MONOLITHIC;
   return same_opt && a->n == b->n && a->mu == b->mu && a->dt == b->dt && a->ar.off == b->ar.off &&
          a->nlev == b->nlev && a->prof_id < 0 && b->prof_id < 0;
@@ -1454,6 +1475,8 @@ void sd_options_default(sd_options* o) {
   o->coupling_columns = 30;
   o->coupling_eps = 1e-9;
   o->coupling_omega = 0.1;
+  o->bc_dp = 1.0;
+  o->bc_tend = 0.0;
   o->schur_gamma = 0.5;
   o->cheb_ratio = 8.0;
   o->schur_mass = 1;
@@ -1582,7 +1605,7 @@ int sd_rhs(sd_handle* h, const double* xprev, double t, double* bout) {
   double* bb = h->V + h->lenA;
   CKR(copy_in_dense(h, xprev, nd));
   launch_pack(h->g, h->stage, xp, h->s);
-  launch_rhs(h->g, h->g.h * h->g.h / h->dt, h->B0, h->B1, 1.0 + t, xp, bb, xp, h->s);
+  launch_rhs(h->g, h->opt.bc != SD_BC_MMS, h->g.h * h->g.h / h->dt, h->B0, h->B1, data_scale(h, t), xp, bb, xp, h->s);
   launch_unpack(h->g, bb, h->stage, h->s);
   CKR(copy_out(h, bout, h->stage, nd));
   CK(cudaStreamSynchronize(h->s));
@@ -1613,7 +1636,7 @@ int sd_solve(sd_handle* h, const double* b, double* x, sd_step_info* info) {
   CK(cudaEventElapsedTime(&ms, h->e0, h->e1));
   si.ms = ms;
   // restore the manufactured-solution data that B0 held
-  launch_mms_terms(coef64(h, 0), h->Klev[0], h->B0, h->B1, h->s);
+  launch_mms_terms(coef64(h, 0), h->opt.bc, h->Klev[0], h->B0, h->B1, h->s);
   CK(cudaStreamSynchronize(h->s));
   if (info) *info = si;
   return rc;

@@ -134,9 +134,13 @@ inline Geom make_geom(int n) {
 //         (i = 0 and i = n: no-flow sides, 0)
 //   Ty    (n+1) rows x P: face below cell row j (j = 0: Dirichlet bottom,
 //         2K/mu; j = n: interface, 0 -- the flux there is h v_Gamma)
+//   lat   1: the free-flow sides x = 0, 1 are traction sides (their u faces
+//         are unknowns with half-control-volume rows; w[0] and w[n] are the
+//         BJS coefficients of their interface corners); 0: Dirichlet sides
 template <typename T>
 struct Coef {
   int n, P;
+  int lat;
   T h, mu, cm;  // cm = h^2 / dt
   const T* w;
   const T* rg;
@@ -168,7 +172,7 @@ void launch_coarsen_K(const double* Kf, int nf, int Pf, double* Kc, int Pc, cuda
 void launch_pack_K(const double* Kdense, int n, double* Kp, int P, cudaStream_t s);
 void launch_fill_K(double* K, int n, int P, double v, cudaStream_t s);
 template <typename T>
-void launch_setup_coef(const double* Kp, int n, int P, double mu, double alpha, T* w, T* rg, T* Tx, T* Ty,
+void launch_setup_coef(const double* Kp, int n, int P, double mu, double alpha, int lat, T* w, T* rg, T* Tx, T* Ty,
                        cudaStream_t s);
 template <typename T>
 void launch_convert(const double* src, T* dst, long long len, cudaStream_t s);
@@ -201,12 +205,14 @@ struct IqnState {
 void launch_iqn(const IqnState& st, const double* vt, const double* p, cudaStream_t s);
 
 // right-hand side: b = mass * xprev + B0 + s1 * B1; also writes the Dirichlet
-// values of b into x (so that the identity rows start exact)
-void launch_rhs(const Geom& g, double cm, const double* B0, const double* B1, double s1, const double* xprev,
-                double* b, double* x, cudaStream_t s);
-// manufactured-solution data: B0 (time-derivative part of the forcing),
-// B1 (everything proportional to 1 + t), and the exact state at time t
-void launch_mms_terms(const Coef<double>& c, const double* Kp, double* B0, double* B1, cudaStream_t s);
+// values of b into x (so that the identity rows start exact); lat: traction sides
+void launch_rhs(const Geom& g, int lat, double cm, const double* B0, const double* B1, double s1,
+                const double* xprev, double* b, double* x, cudaStream_t s);
+// boundary and source data: B0 (time-derivative part of the manufactured
+// forcing), B1 (everything proportional to the time function s1 of
+// launch_rhs: 1 + t for the manufactured cases bc 0, 1; the inflow pressure
+// p_in(t) for the pressure-driven problem bc 2), and the exact state at time t
+void launch_mms_terms(const Coef<double>& c, int bc, const double* Kp, double* B0, double* B1, cudaStream_t s);
 void launch_mms_exact(const Geom& g, double mu, double t, double* x, cudaStream_t s);
 
 // dense canonical layout <-> padded layout (whole-system vector)
@@ -235,7 +241,7 @@ void launch_resid_D(const Coef<T>& c, const T* x, const T* b, T* r, int jac, int
                     cudaStream_t s);
 // coarse rhs = R r with R the transposed bilinear (V) / cell-sum (D) transfer
 template <typename T>
-void launch_restrict_V(int nf, int Pf, const T* r, int nc, int Pc, T* bc, cudaStream_t s);
+void launch_restrict_V(int nf, int Pf, const T* r, int nc, int Pc, T* bc, int lat, cudaStream_t s);
 template <typename T>
 void launch_restrict_D(int nf, int Pf, const T* r, int nc, int Pc, T* bc, cudaStream_t s);
 // cell blocks: bc = R (b - A x) with the cell-sum restriction, one pass
@@ -243,7 +249,7 @@ template <typename T>
 void launch_resid_restrict_D(const Coef<T>& c, const T* x, const T* b, int nc, int Pc, T* bc, cudaStream_t s);
 // x += P e (bilinear, staggered for V, cell-centred for D)
 template <typename T>
-void launch_prolong_V(int nf, int Pf, T* x, int nc, int Pc, const T* e, cudaStream_t s);
+void launch_prolong_V(int nf, int Pf, T* x, int nc, int Pc, const T* e, int lat, cudaStream_t s);
 template <typename T>
 void launch_prolong_D(int nf, int Pf, T* x, int nc, int Pc, const T* e, cudaStream_t s);
 

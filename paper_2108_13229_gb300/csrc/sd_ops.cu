@@ -74,7 +74,7 @@ __device__ __forceinline__ void u_row(const Coef<T>& c, const T* __restrict__ u,
   const int rv1 = (j + 1) * P;
   const T uW = u[r0 + i - 1], uE = u[r0 + i + 1], uN = u[rN + i], uS = u[rS + i];
   const T vN = v[rv1 + i], vNW = v[rv1 + i - 1], vS = v[r0 + i], vSW = v[r0 + i - 1];
-  const T cW = (IN || i - 1 >= 1) ? c.m2 : T(0), cE = (IN || i + 1 <= n - 1) ? c.m2 : T(0);
+  const T cW = (IN || c.lat || i - 1 >= 1) ? c.m2 : T(0), cE = (IN || c.lat || i + 1 <= n - 1) ? c.m2 : T(0);
   T of = cW * uW;
   of = fma(cE, uE, of);
   if (!top) {
@@ -101,10 +101,12 @@ __device__ __forceinline__ void v_row(const Coef<T>& c, const T* __restrict__ u,
   const T mu = c.mu, h = c.h;
   const bool left = !IN && i == 0, right = !IN && i == n - 1;
   if (!IN && j == 0) {
-    const T wl = left ? T(0) : c.w[i], wr = right ? T(0) : c.w[i + 1];
+    // corners: BJS (interior, or a traction side's corner at half distance)
+    // or a Dirichlet side at half distance
+    const T wl = (left && !c.lat) ? T(0) : c.w[i], wr = (right && !c.lat) ? T(0) : c.w[i + 1];
     T dg = T(0.5) * c.cm + T(2) * mu + c.rg[i];
-    dg += left ? mu : T(0.5) * h * wl;
-    dg += right ? mu : T(0.5) * h * wr;
+    dg += left ? (c.lat ? h * wl : mu) : T(0.5) * h * wl;
+    dg += right ? (c.lat ? h * wr : mu) : T(0.5) * h * wr;
     diag = dg;
     if (!read) {
       off = T(0);
@@ -116,10 +118,14 @@ __device__ __forceinline__ void v_row(const Coef<T>& c, const T* __restrict__ u,
     if (!left) {
       of = fma(wl * h, uL, of);
       of = fma(T(-0.5) * h * wl, vL, of);
+    } else if (c.lat) {
+      of = fma(wl * h, uL, of);
     }
     if (!right) {
       of = fma(-wr * h, uR, of);
       of = fma(T(-0.5) * h * wr, vR, of);
+    } else if (c.lat) {
+      of = fma(-wr * h, uR, of);
     }
     off = of;
     return;
@@ -143,11 +149,56 @@ __device__ __forceinline__ void v_row(const Coef<T>& c, const T* __restrict__ u,
     of = fma(c.m1, vE, of);
     of = fma(c.m1, uE, of);
     of = fma(mu, uES, of);
+  } else if (c.lat) {  // traction side: its u faces are unknowns
+    of = fma(c.m1, uE, of);
+    of = fma(mu, uES, of);
   }
   if (!left) {
     of = fma(c.m1, vW, of);
     of = fma(mu, uW, of);
     of = fma(c.m1, uWS, of);
+  } else if (c.lat) {
+    of = fma(mu, uW, of);
+    of = fma(c.m1, uWS, of);
+  }
+  off = of;
+}
+
+// Side u face (i = 0 or n) of a traction side: x-momentum balance of the
+// half control volume inside the domain (as v_Gamma for the interface):
+// normal stress through the adjacent cell centre (the side's traction goes
+// to the right-hand side), shear through its top and bottom at the side,
+// from the side's tangential velocity at half distance, the wall above the
+// top row at half distance, and at the interface corner the eliminated BJS
+// slip of Eq. (6).  The pressure term is added by the caller.
+template <typename T>
+__device__ __forceinline__ void ub_row(const Coef<T>& c, const T* __restrict__ u, const T* __restrict__ v, int i,
+                                       int j, bool read, T& off, T& diag) {
+  const int n = c.n, P = c.P;
+  const T mu = c.mu;
+  const bool rt = i == n, top = j == n - 1, bot = j == 0;
+  const T wh = bot ? c.w[i] * c.h : T(0);
+  T dg = T(0.5) * c.cm + T(2) * mu;
+  dg += top ? mu : T(0.5) * mu;
+  dg += bot ? wh : T(0.5) * mu;
+  diag = dg;
+  if (!read) {
+    off = T(0);
+    return;
+  }
+  const int r0 = j * P;
+  const int ii = rt ? n - 1 : 1, ic = rt ? n - 1 : 0;
+  const T sg = rt ? T(-1) : T(1);
+  T of = c.m2 * u[r0 + ii];
+  if (!top) {
+    of = fma(T(-0.5) * mu, u[r0 + P + i], of);
+    of = fma(-sg * mu, v[r0 + P + ic], of);
+  }
+  if (!bot) {
+    of = fma(T(-0.5) * mu, u[r0 - P + i], of);
+    of = fma(sg * mu, v[r0 + ic], of);
+  } else {
+    of = fma(sg * wh, v[ic], of);
   }
   off = of;
 }
@@ -209,8 +260,12 @@ __global__ void k_apply_full(Coef<double> c, const double* __restrict__ x, const
     if (j < n) {
       const long long k = (long long)j * P + i;
       double val;
-      if (i == 0 || i == n) {
+      if ((i == 0 || i == n) && !c.lat) {
         val = u[k];
+      } else if (i == 0 || i == n) {
+        double off, dg;
+        ub_row(c, u, v, i, j, true, off, dg);
+        val = dg * u[k] + off + (i == 0 ? h * pf[k] : -h * pf[k - 1]);
       } else {
         double off, dg;
         u_row(c, u, v, i, j, true, off, dg);
@@ -237,8 +292,8 @@ __global__ void k_apply_full(Coef<double> c, const double* __restrict__ x, const
     if (i < n && j < n) {
       const long long kc = (long long)j * P + i;
       double s = -v[kc];
-      if (i + 1 <= n - 1) s += u[kc + 1];
-      if (i >= 1) s -= u[kc];
+      if (c.lat || i + 1 <= n - 1) s += u[kc + 1];
+      if (c.lat || i >= 1) s -= u[kc];
       if (j + 1 <= n - 1) s += v[kc + P];
       const long long kp = (long long)(2 * n + 1) * P + kc;
       y[kp] = b ? b[kp] - h * s : h * s;
@@ -318,12 +373,14 @@ __device__ __forceinline__ void cheb_V_at2(const Coef<T>& c, const T* __restrict
   const bool rd = uin != nullptr;
   if (IN || j < n) {
     const int k = j * P + i;
-    if (!IN && (i == 0 || i == n)) {
+    const bool side = !IN && (i == 0 || i == n);
+    if (side && !c.lat) {
       uout[k] = bu[k];
       du[k] = T(0);
     } else {
       T off, dg;
-      u_row<T, IN>(c, uin, vin, i, j, rd, off, dg);
+      if (side) ub_row(c, uin, vin, i, j, rd, off, dg);
+      else u_row<T, IN>(c, uin, vin, i, j, rd, off, dg);
       const T xc = rd ? uin[k] : T(0);
       const T r = bu[k] - (dg * xc + off);
       const T dn = (a != T(0) ? a * du[k] : T(0)) + sdiv(cc * r, dg);
@@ -405,11 +462,12 @@ __device__ __forceinline__ void resid_V_at(const Coef<T>& c, const T* __restrict
   if (j < n) {
     const int k = j * P + i;
     T ax, dg = T(1);
-    if (i == 0 || i == n) {
+    if ((i == 0 || i == n) && !c.lat) {
       ax = x[k];
     } else {
       T off;
-      u_row(c, u, v, i, j, true, off, dg);
+      if (i == 0 || i == n) ub_row(c, u, v, i, j, true, off, dg);
+      else u_row(c, u, v, i, j, true, off, dg);
       ax = dg * x[k] + off;
     }
     r[k] = jac == 1 ? ax / dg : (jac == 2 ? ax : (b ? b[k] - ax : -ax));
@@ -573,12 +631,26 @@ void launch_resid_D(const Coef<T>& c, const T* x, const T* b, T* r, int jac, int
 // Restriction is its transpose applied to the fine residual.
 template <typename T>
 __device__ __forceinline__ void restrict_V_at(int nf, int Pf, const T* __restrict__ r, int nc, int Pc,
-                                              T* __restrict__ bc, int I, int J) {
+                                              T* __restrict__ bc, int I, int J, int lat = 0) {
   const T* ru = r;
   const T* rv = r + (long long)nf * Pf;
   if (J < nc) {
     T s = T(0);
-    if (I > 0 && I < nc) {
+    if (lat && (I == 0 || I == nc)) {  // traction side face: the one-sided transpose of the prolongation
+      int rows[4];
+      T wy[4];
+      rows[0] = 2 * J - 1; wy[0] = J >= 1 ? T(0.25) : T(0);
+      rows[1] = 2 * J;     wy[1] = J == 0 ? T(1) : T(0.75);
+      rows[2] = 2 * J + 1; wy[2] = J == nc - 1 ? T(0.5) : T(0.75);
+      rows[3] = 2 * J + 2; wy[3] = J <= nc - 2 ? T(0.25) : T(0);
+      const int ii = 2 * I, in = I == 0 ? 1 : 2 * I - 1;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (wy[q] == T(0)) continue;
+        const T* row = ru + (long long)rows[q] * Pf;
+        s += wy[q] * (row[ii] + T(0.5) * row[in]);
+      }
+    } else if (I > 0 && I < nc) {
       int rows[4];
       T wy[4];
       rows[0] = 2 * J - 1; wy[0] = J >= 1 ? T(0.25) : T(0);
@@ -620,7 +692,8 @@ __device__ __forceinline__ void restrict_V_at(int nf, int Pf, const T* __restric
 }
 
 template <typename T>
-__global__ void k_restrict_V(int nf, int Pf, const T* __restrict__ r, int nc, int Pc, T* __restrict__ bc, Bat bt) {
+__global__ void k_restrict_V(int nf, int Pf, const T* __restrict__ r, int nc, int Pc, T* __restrict__ bc, int lat,
+                             Bat bt) {
   griddep_wait();
   long long o;
   if (!bat_enter(bt, o)) return;
@@ -631,13 +704,13 @@ __global__ void k_restrict_V(int nf, int Pf, const T* __restrict__ r, int nc, in
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I > nc || J > nc) return;
-  restrict_V_at(nf, Pf, r, nc, Pc, bc, I, J);
+  restrict_V_at(nf, Pf, r, nc, Pc, bc, I, J, lat);
 }
 
 template <typename T>
-void launch_restrict_V(int nf, int Pf, const T* r, int nc, int Pc, T* bc, cudaStream_t s) {
+void launch_restrict_V(int nf, int Pf, const T* r, int nc, int Pc, T* bc, int lat, cudaStream_t s) {
   SD_COUNT(1);
-  launch_k(k_restrict_V<T>, dim3(grid2(nc + 1, nc + 1)), dim3(dim3(BX, BY)), 0, s, nf, Pf, r, nc, Pc, bc);
+  launch_k(k_restrict_V<T>, dim3(grid2(nc + 1, nc + 1)), dim3(dim3(BX, BY)), 0, s, nf, Pf, r, nc, Pc, bc, lat);
 }
 
 template <typename T>
@@ -704,9 +777,10 @@ void launch_resid_restrict_D(const Coef<T>& c, const T* x, const T* b, int nc, i
 }
 
 template <typename T>
-__device__ __forceinline__ T cu_at(const T* eu, int nc, int Pc, int I, int J) {
-  // coarse u with zero Dirichlet faces and the y ghosts described above
-  if (I <= 0 || I >= nc) return T(0);
+__device__ __forceinline__ T cu_at(const T* eu, int nc, int Pc, int I, int J, int lat) {
+  // coarse u with zero Dirichlet faces (traction sides: the side faces' own
+  // values) and the y ghosts described above
+  if (!lat && (I <= 0 || I >= nc)) return T(0);
   if (J < 0) J = 0;
   if (J > nc - 1) return -eu[(long long)(nc - 1) * Pc + I];
   return eu[(long long)J * Pc + I];
@@ -721,17 +795,17 @@ __device__ __forceinline__ T cv_at(const T* ev, int nc, int Pc, int I, int J) {
 
 // increment of fine u face (i, j), 0 < i < nf, j < nf
 template <typename T>
-__device__ __forceinline__ T prolong_u_val(const T* __restrict__ eu, int nc, int Pc, int i, int j) {
+__device__ __forceinline__ T prolong_u_val(const T* __restrict__ eu, int nc, int Pc, int i, int j, int lat = 0) {
   const int J = j >> 1, Jn = (j & 1) ? J + 1 : J - 1;
   T cy0, cy1;
   if (i & 1) {
     const int I = i >> 1;
-    cy0 = T(0.5) * (cu_at(eu, nc, Pc, I, J) + cu_at(eu, nc, Pc, I + 1, J));
-    cy1 = T(0.5) * (cu_at(eu, nc, Pc, I, Jn) + cu_at(eu, nc, Pc, I + 1, Jn));
+    cy0 = T(0.5) * (cu_at(eu, nc, Pc, I, J, lat) + cu_at(eu, nc, Pc, I + 1, J, lat));
+    cy1 = T(0.5) * (cu_at(eu, nc, Pc, I, Jn, lat) + cu_at(eu, nc, Pc, I + 1, Jn, lat));
   } else {
     const int I = i >> 1;
-    cy0 = cu_at(eu, nc, Pc, I, J);
-    cy1 = cu_at(eu, nc, Pc, I, Jn);
+    cy0 = cu_at(eu, nc, Pc, I, J, lat);
+    cy1 = cu_at(eu, nc, Pc, I, Jn, lat);
   }
   return T(0.75) * cy0 + T(0.25) * cy1;
 }
@@ -755,15 +829,16 @@ __device__ __forceinline__ T prolong_v_val(const T* __restrict__ ev, int nc, int
 
 template <typename T>
 __device__ __forceinline__ void prolong_V_at(int nf, int Pf, T* __restrict__ x, int nc, int Pc,
-                                             const T* __restrict__ e, int i, int j) {
+                                             const T* __restrict__ e, int i, int j, int lat = 0) {
   const T* eu = e;
   const T* ev = e + (long long)nc * Pc;
-  if (j < nf && i > 0 && i < nf) x[(long long)j * Pf + i] += prolong_u_val(eu, nc, Pc, i, j);
+  if (j < nf && (lat || (i > 0 && i < nf))) x[(long long)j * Pf + i] += prolong_u_val(eu, nc, Pc, i, j, lat);
   if (i < nf && j < nf) x[(long long)nf * Pf + (long long)j * Pf + i] += prolong_v_val(ev, nc, Pc, i, j);
 }
 
 template <typename T, int R>
-__global__ void k_prolong_V(int nf, int Pf, T* __restrict__ x, int nc, int Pc, const T* __restrict__ e, Bat bt) {
+__global__ void k_prolong_V(int nf, int Pf, T* __restrict__ x, int nc, int Pc, const T* __restrict__ e, int lat,
+                            Bat bt) {
   griddep_wait();
   long long o;
   if (!bat_enter(bt, o)) return;
@@ -778,16 +853,18 @@ __global__ void k_prolong_V(int nf, int Pf, T* __restrict__ x, int nc, int Pc, c
   for (int rr = 0; rr < R; ++rr) {
     const int j = j0 + rr;
     if (j > nf) break;
-    prolong_V_at(nf, Pf, x, nc, Pc, e, i, j);
+    prolong_V_at(nf, Pf, x, nc, Pc, e, i, j, lat);
   }
 }
 
 template <typename T>
-void launch_prolong_V(int nf, int Pf, T* x, int nc, int Pc, const T* e, cudaStream_t s) {
+void launch_prolong_V(int nf, int Pf, T* x, int nc, int Pc, const T* e, int lat, cudaStream_t s) {
   SD_COUNT(1);
   const int R = rows_vel(nf);
-  if (R == 4) launch_k(k_prolong_V<T, 4>, dim3(grid2R(nf + 1, nf + 1, 4)), dim3(dim3(BX, BY)), 0, s, nf, Pf, x, nc, Pc, e);
-  else launch_k(k_prolong_V<T, 1>, dim3(grid2R(nf + 1, nf + 1, 1)), dim3(dim3(BX, BY)), 0, s, nf, Pf, x, nc, Pc, e);
+  if (R == 4)
+    launch_k(k_prolong_V<T, 4>, dim3(grid2R(nf + 1, nf + 1, 4)), dim3(dim3(BX, BY)), 0, s, nf, Pf, x, nc, Pc, e, lat);
+  else
+    launch_k(k_prolong_V<T, 1>, dim3(grid2R(nf + 1, nf + 1, 1)), dim3(dim3(BX, BY)), 0, s, nf, Pf, x, nc, Pc, e, lat);
 }
 
 template <typename T>
@@ -983,7 +1060,7 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_V(Coef<T> c, const T* __res
         bu = b[gk];
         if (xin) {
           xu = xin[gk];
-          if (ec && gi > 0 && gi < n) xu += prolong_u_val(ecu, nc, Pc, gi, gj);
+          if (ec && (c.lat || (gi > 0 && gi < n))) xu += prolong_u_val(ecu, nc, Pc, gi, gj, c.lat);
         }
       }
       if (gi < n && gj <= n) {  // v face
@@ -1143,11 +1220,12 @@ __device__ __forceinline__ void cheb_d_V_at(const Coef<T>& c, const T* __restric
   const T* v = x + (long long)n * P;
   if (j < n) {
     const int k = j * P + i;
-    if (i == 0 || i == n) {
+    if ((i == 0 || i == n) && !c.lat) {
       d[k] = T(0);
     } else {
       T off, dg;
-      u_row(c, u, v, i, j, true, off, dg);
+      if (i == 0 || i == n) ub_row(c, u, v, i, j, true, off, dg);
+      else u_row(c, u, v, i, j, true, off, dg);
       const T r = b[k] - (dg * x[k] + off);
       d[k] = (a != T(0) ? a * d[k] : T(0)) + sdiv(cc * r, dg);
     }
@@ -1207,10 +1285,10 @@ __device__ void cyc_sweep(const CoarseCycle<T>& q, int l, int op, T* X, const T*
       if (q.kind == 0) resid_V_at(c, X, B, D, 0, i, j);
       else resid_D_at(c, X, B, D, 0, i, j);
     } else if (op == 4) {
-      if (q.kind == 0) restrict_V_at(n, c.P, D, nc, q.c[l + 1].P, Bc, i, j);
+      if (q.kind == 0) restrict_V_at(n, c.P, D, nc, q.c[l + 1].P, Bc, i, j, c.lat);
       else restrict_D_at(c.P, D, q.c[l + 1].P, Bc, i, j);
     } else {
-      if (q.kind == 0) prolong_V_at(n, c.P, X, nc, q.c[l + 1].P, Xc, i, j);
+      if (q.kind == 0) prolong_V_at(n, c.P, X, nc, q.c[l + 1].P, Xc, i, j, c.lat);
       else prolong_D_at(c.P, X, nc, q.c[l + 1].P, Xc, i, j);
     }
   }
@@ -1383,6 +1461,7 @@ __global__ void k_precond_entry(Coef<double> c, const double* __restrict__ r, do
     const long long k = (long long)j * P + i;
     T val = (T)r[k];
     if (useB && i > 0 && i < n) val -= h * (zp(k) - zp(k - 1));
+    else if (useB && c.lat) val -= i == 0 ? h * zp(k) : -h * zp(k - 1);  // traction side
     rV[k] = val;
   }
   if (i < n) {
@@ -1490,8 +1569,8 @@ __global__ void k_precond_bgs_pff(Coef<double> c, const double* __restrict__ r, 
   const T* u = eV;
   const T* v = eV + (long long)n * P;
   double s = -(double)v[kc];
-  if (i + 1 <= n - 1) s += (double)u[kc + 1];
-  if (i >= 1) s -= (double)u[kc];
+  if (c.lat || i + 1 <= n - 1) s += (double)u[kc + 1];
+  if (c.lat || i >= 1) s -= (double)u[kc];
   if (j + 1 <= n - 1) s += (double)v[kc + P];
   const long long kp = (long long)(2 * n + 1) * P + kc;
   z[kp] = r[kp] - c.h * s;
@@ -1544,8 +1623,8 @@ void launch_coarsen_K(const double* Kf, int nf, int Pf, double* Kc, int Pc, cuda
 }
 
 template <typename T>
-__global__ void k_setup_coef(const double* __restrict__ K, int n, int P, double mu, double alpha, T* w, T* rg, T* Tx,
-                             T* Ty) {
+__global__ void k_setup_coef(const double* __restrict__ K, int n, int P, double mu, double alpha, int lat, T* w,
+                             T* rg, T* Tx, T* Ty) {
   griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -1573,6 +1652,9 @@ __global__ void k_setup_coef(const double* __restrict__ K, int n, int P, double 
     if (i > 0 && i < n) {
       const double beta = 0.5 * (sqrt(top[i - 1]) + sqrt(top[i])) / alpha;
       w[i] = (T)(mu / (h + 2.0 * beta));
+    } else if (lat) {  // traction side's interface corner: the one pm cell below
+      const double beta = sqrt(top[i == 0 ? 0 : n - 1]) / alpha;
+      w[i] = (T)(mu / (h + 2.0 * beta));
     } else {
       w[i] = (T)0;
     }
@@ -1581,10 +1663,11 @@ __global__ void k_setup_coef(const double* __restrict__ K, int n, int P, double 
 }
 
 template <typename T>
-void launch_setup_coef(const double* Kp, int n, int P, double mu, double alpha, T* w, T* rg, T* Tx, T* Ty,
+void launch_setup_coef(const double* Kp, int n, int P, double mu, double alpha, int lat, T* w, T* rg, T* Tx, T* Ty,
                        cudaStream_t s) {
   SD_COUNT(1);
-  launch_k(k_setup_coef<T>, dim3(grid2(n + 1, n + 1)), dim3(dim3(BX, BY)), 0, s, Kp, n, P, mu, alpha, w, rg, Tx, Ty);
+  launch_k(k_setup_coef<T>, dim3(grid2(n + 1, n + 1)), dim3(dim3(BX, BY)), 0, s, Kp, n, P, mu, alpha, lat, w, rg, Tx,
+           Ty);
 }
 
 template <typename T>
@@ -1629,9 +1712,18 @@ __device__ __forceinline__ double mm_f1y(double x, double y, double mu) {
 }
 
 // B0: time-derivative part of the integrated source; B1: all terms proportional
-// to s = 1 + t (rest of the source, boundary data moved to the right-hand side,
-// Dirichlet values of the identity rows).
-__global__ void k_mms_terms(Coef<double> c, const double* __restrict__ K, double* __restrict__ B0,
+// to the time function s1 (1 + t for the manufactured cases: the rest of the
+// source, boundary data moved to the right-hand side, Dirichlet values of the
+// identity rows; p_in(t) for the pressure-driven problem: the inflow traction).
+//   bc 0: Dirichlet free-flow sides; bc 1: traction sides with the
+//   manufactured data (P_b = p - 2 mu du/dx, V_b = v on x = 0, 1);
+//   bc 2: the pressure-driven problem (unit inflow traction on the left
+//   side, all other data and sources zero).
+__device__ __forceinline__ double mm_Pside(double x, double y, double mu) {  // p - 2 mu du/dx at s = 1
+  return mm_Pff0(x, mu) - 2.0 * mu * SD_PI * cos(SD_PI * x) * (mm_A() + 2.0 * (y - 1.0));
+}
+
+__global__ void k_mms_terms(Coef<double> c, int bc, const double* __restrict__ K, double* __restrict__ B0,
                             double* __restrict__ B1) {
   griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1639,17 +1731,30 @@ __global__ void k_mms_terms(Coef<double> c, const double* __restrict__ K, double
   const int n = c.n, P = c.P;
   if (i > n || j > n) return;
   const double h = c.h, mu = c.mu, h2 = h * h;
+  const bool lat = bc != 0, mms = bc != 2;
   if (j < n) {  // u face (i, j)
     const long long k = (long long)j * P + i;
     const double x = i * h, y = 1.0 + (j + 0.5) * h;
-    double b0 = 0.0, b1;
-    if (i == 0 || i == n) {
+    double b0 = 0.0, b1 = 0.0;
+    if ((i == 0 || i == n) && !lat) {
       b1 = mm_U0(x, y);
-    } else {
+    } else if (i == 0 || i == n) {  // traction side, half control volume
+      const double sg = i == 0 ? 1.0 : -1.0;
+      if (mms) {
+        b0 = 0.5 * h2 * mm_U0(x, y);
+        b1 = 0.5 * h2 * mm_f1x(x, y, mu) + sg * h * mm_Pside(x, y, mu);
+        if (j < n - 1) b1 -= sg * mu * mm_V0(x, 1.0 + (j + 1) * h);
+        else b1 += mu * mm_U0(x, 2.0) + sg * mu * (mm_V0(x + sg * 0.5 * h, 2.0) - mm_V0(x, 2.0));
+        if (j > 0) b1 += sg * mu * mm_V0(x, 1.0 + j * h);
+        else b1 += sg * h * c.w[i] * mm_V0(x, 1.0);
+      } else if (i == 0) {
+        b1 = h;  // inflow traction p_in(t) enters as s1
+      }
+    } else if (mms) {
       b0 = h2 * mm_U0(x, y);
       b1 = h2 * mm_f1x(x, y, mu);
-      if (i == 1) b1 += 2.0 * mu * mm_U0(0.0, y);
-      if (i == n - 1) b1 += 2.0 * mu * mm_U0(1.0, y);
+      if (i == 1 && !lat) b1 += 2.0 * mu * mm_U0(0.0, y);
+      if (i == n - 1 && !lat) b1 += 2.0 * mu * mm_U0(1.0, y);
       if (j == n - 1) b1 += 2.0 * mu * mm_U0(x, 2.0) + mu * (mm_V0(x + 0.5 * h, 2.0) - mm_V0(x - 0.5 * h, 2.0));
     }
     B0[k] = b0;
@@ -1658,20 +1763,33 @@ __global__ void k_mms_terms(Coef<double> c, const double* __restrict__ K, double
   if (i < n) {  // v face (i, j)
     const long long k = (long long)n * P + (long long)j * P + i;
     const double x = (i + 0.5) * h, y = 1.0 + j * h;
-    double b0 = 0.0, b1;
-    if (j == n) {
+    double b0 = 0.0, b1 = 0.0;
+    if (!mms) {
+    } else if (j == n) {
       b1 = mm_V0(x, 2.0);
     } else if (j == 0) {
       b0 = 0.5 * h2 * mm_V0(x, 1.0);
       b1 = 0.5 * h2 * mm_f1y(x, 1.0, mu);
-      if (i == 0) b1 += -mu * (mm_U0(0.0, 1.0 + 0.5 * h) - mm_U0(0.0, 1.0)) + mu * mm_V0(0.0, 1.0);
-      if (i == n - 1) b1 += mu * (mm_U0(1.0, 1.0 + 0.5 * h) - mm_U0(1.0, 1.0)) + mu * mm_V0(1.0, 1.0);
+      if (i == 0) {
+        if (lat) b1 += h * c.w[0] * mm_V0(0.0, 1.0);
+        else b1 += -mu * (mm_U0(0.0, 1.0 + 0.5 * h) - mm_U0(0.0, 1.0)) + mu * mm_V0(0.0, 1.0);
+      }
+      if (i == n - 1) {
+        if (lat) b1 += h * c.w[n] * mm_V0(1.0, 1.0);
+        else b1 += mu * (mm_U0(1.0, 1.0 + 0.5 * h) - mm_U0(1.0, 1.0)) + mu * mm_V0(1.0, 1.0);
+      }
     } else {
       b0 = h2 * mm_V0(x, y);
       b1 = h2 * mm_f1y(x, y, mu);
       if (j == n - 1) b1 += 2.0 * mu * mm_V0(x, 2.0);
-      if (i == 0) b1 += 2.0 * mu * mm_V0(0.0, y) - mu * (mm_U0(0.0, y + 0.5 * h) - mm_U0(0.0, y - 0.5 * h));
-      if (i == n - 1) b1 += 2.0 * mu * mm_V0(1.0, y) + mu * (mm_U0(1.0, y + 0.5 * h) - mm_U0(1.0, y - 0.5 * h));
+      if (i == 0) {
+        if (lat) b1 += 2.0 * mu * mm_V0(0.0, y);
+        else b1 += 2.0 * mu * mm_V0(0.0, y) - mu * (mm_U0(0.0, y + 0.5 * h) - mm_U0(0.0, y - 0.5 * h));
+      }
+      if (i == n - 1) {
+        if (lat) b1 += 2.0 * mu * mm_V0(1.0, y);
+        else b1 += 2.0 * mu * mm_V0(1.0, y) + mu * (mm_U0(1.0, y + 0.5 * h) - mm_U0(1.0, y - 0.5 * h));
+      }
     }
     B0[k] = b0;
     B1[k] = b1;
@@ -1680,21 +1798,23 @@ __global__ void k_mms_terms(Coef<double> c, const double* __restrict__ K, double
     const long long kc = (long long)j * P + i;
     const double y = 1.0 + (j + 0.5) * h, x = (i + 0.5) * h;
     double s = 0.0;
-    if (i == 0) s += h * mm_U0(0.0, y);
-    if (i == n - 1) s -= h * mm_U0(1.0, y);
-    if (j == n - 1) s -= h * mm_V0(x, 2.0);
+    if (mms) {
+      if (i == 0 && !lat) s += h * mm_U0(0.0, y);
+      if (i == n - 1 && !lat) s -= h * mm_U0(1.0, y);
+      if (j == n - 1) s -= h * mm_V0(x, 2.0);
+    }
     B0[(long long)(2 * n + 1) * P + kc] = 0.0;
     B1[(long long)(2 * n + 1) * P + kc] = s;
     double sp = 0.0;
-    if (j == 0) sp = 2.0 * K[i] / mu * mm_Ppm0(x, 0.0);
+    if (j == 0 && mms) sp = 2.0 * K[i] / mu * mm_Ppm0(x, 0.0);
     B0[(long long)(3 * n + 1) * P + kc] = 0.0;
     B1[(long long)(3 * n + 1) * P + kc] = sp;
   }
 }
 
-void launch_mms_terms(const Coef<double>& c, const double* Kp, double* B0, double* B1, cudaStream_t s) {
+void launch_mms_terms(const Coef<double>& c, int bc, const double* Kp, double* B0, double* B1, cudaStream_t s) {
   SD_COUNT(1);
-  launch_k(k_mms_terms, dim3(grid2(c.n + 1, c.n + 1)), dim3(dim3(BX, BY)), 0, s, c, Kp, B0, B1);
+  launch_k(k_mms_terms, dim3(grid2(c.n + 1, c.n + 1)), dim3(dim3(BX, BY)), 0, s, c, bc, Kp, B0, B1);
 }
 
 __global__ void k_mms_exact(int n, int P, double mu, double t, double* __restrict__ x) {
@@ -1718,8 +1838,9 @@ void launch_mms_exact(const Geom& g, double mu, double t, double* x, cudaStream_
 }
 
 // b = mass * xprev + B0 + s1 * B1 (mass = h^2/dt on velocity rows, half on
-// v_Gamma, 0 elsewhere); Dirichlet rows of x take their new values.
-__global__ void k_rhs(int n, int P, double cm, const double* __restrict__ B0, const double* __restrict__ B1,
+// v_Gamma and on traction-side u faces, 0 elsewhere); Dirichlet rows of x
+// take their new values.
+__global__ void k_rhs(int n, int P, int lat, double cm, const double* __restrict__ B0, const double* __restrict__ B1,
                       double s1, const double* __restrict__ xprev, double* __restrict__ b, double* __restrict__ x) {
   griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1727,8 +1848,9 @@ __global__ void k_rhs(int n, int P, double cm, const double* __restrict__ B0, co
   if (i > n || j > n) return;
   if (j < n) {
     const long long k = (long long)j * P + i;
-    const bool dir = (i == 0 || i == n);
-    const double val = (dir ? 0.0 : cm * xprev[k]) + B0[k] + s1 * B1[k];
+    const bool side = (i == 0 || i == n), dir = side && !lat;
+    const double m = dir ? 0.0 : (side ? 0.5 * cm : cm);
+    const double val = m * xprev[k] + B0[k] + s1 * B1[k];
     b[k] = val;
     if (dir) x[k] = val;
   }
@@ -1748,10 +1870,11 @@ __global__ void k_rhs(int n, int P, double cm, const double* __restrict__ B0, co
   }
 }
 
-void launch_rhs(const Geom& g, double cm, const double* B0, const double* B1, double s1, const double* xprev,
-                double* b, double* x, cudaStream_t s) {
+void launch_rhs(const Geom& g, int lat, double cm, const double* B0, const double* B1, double s1,
+                const double* xprev, double* b, double* x, cudaStream_t s) {
   SD_COUNT(1);
-  launch_k(k_rhs, dim3(grid2(g.n + 1, g.n + 1)), dim3(dim3(BX, BY)), 0, s, g.n, g.P, cm, B0, B1, s1, xprev, b, x);
+  launch_k(k_rhs, dim3(grid2(g.n + 1, g.n + 1)), dim3(dim3(BX, BY)), 0, s, g.n, g.P, lat, cm, B0, B1, s1, xprev, b,
+           x);
 }
 
 // ------------------------------------------------------------ pack/unpack
@@ -1786,15 +1909,15 @@ void launch_unpack(const Geom& g, const double* padded, double* dense, cudaStrea
 
 // ------------------------------------------------------- instantiations
 #define SD_INST(T)                                                                                               \
-  template void launch_setup_coef<T>(const double*, int, int, double, double, T*, T*, T*, T*, cudaStream_t);    \
+  template void launch_setup_coef<T>(const double*, int, int, double, double, int, T*, T*, T*, T*, cudaStream_t); \
   template void launch_convert<T>(const double*, T*, long long, cudaStream_t);                                   \
   template void launch_cheb_V<T>(const Coef<T>&, const T*, const T*, T*, T*, T, T, const T*, int, long long, cudaStream_t); \
   template void launch_cheb_D<T>(const Coef<T>&, const T*, const T*, T*, T*, T, T, const T*, int, long long, cudaStream_t); \
   template void launch_resid_V<T>(const Coef<T>&, const T*, const T*, T*, int, int, long long, cudaStream_t);    \
   template void launch_resid_D<T>(const Coef<T>&, const T*, const T*, T*, int, int, long long, cudaStream_t);    \
-  template void launch_restrict_V<T>(int, int, const T*, int, int, T*, cudaStream_t);            \
+  template void launch_restrict_V<T>(int, int, const T*, int, int, T*, int, cudaStream_t);       \
   template void launch_restrict_D<T>(int, int, const T*, int, int, T*, cudaStream_t);            \
-  template void launch_prolong_V<T>(int, int, T*, int, int, const T*, cudaStream_t);                              \
+  template void launch_prolong_V<T>(int, int, T*, int, int, const T*, int, cudaStream_t);                         \
   template void launch_prolong_D<T>(int, int, T*, int, int, const T*, cudaStream_t);                              \
   template void launch_resid_restrict_D<T>(const Coef<T>&, const T*, const T*, int, int, T*, cudaStream_t);                              \
   template void launch_precond_entry<T>(const Coef<double>&, const double*, double*, double, const T*, double, int, int, T*, cudaStream_t); \

@@ -20,7 +20,7 @@ SD_OK, SD_PENDING = 0, 1
 SD_E_INVAL, SD_E_NOMEM, SD_E_NOCONV, SD_E_NUMERIC, SD_E_TIMEOUT, SD_E_CUDA, SD_E_STATE = -1, -2, -3, -4, -5, -6, -7
 SD_FP64, SD_MIXED = 0, 1
 SD_TRI_SCHUR, SD_PV_BJ_I, SD_PV_BGS_I = 0, 1, 2
-SD_BC_MMS = 0
+SD_BC_MMS, SD_BC_MMS_TRACTION, SD_BC_PAPER = 0, 1, 2
 SD_PROF_APPLY, SD_PROF_CHEB_V, SD_PROF_MUPDATE, SD_PROF_MDOT = 0, 1, 2, 3
 SD_NOALLOC_MAX_N = 256
 SD_BATCH_LOCKSTEP = 1
@@ -49,6 +49,7 @@ class sd_options(ctypes.Structure):
                 ("darcy_coupled", ctypes.c_int32), ("coupling", ctypes.c_int32),
                 ("coupling_max", ctypes.c_int32), ("coupling_columns", ctypes.c_int32),
                 ("coupling_eps", ctypes.c_double), ("coupling_omega", ctypes.c_double),
+                ("bc_dp", ctypes.c_double), ("bc_tend", ctypes.c_double),
                 ("stream", ctypes.c_void_p)]
 
 

@@ -399,3 +399,79 @@ def test_partitioned_manufactured_solution(sd):
     assert all(i["status"] == 0 for i in infos)
     for k, e in fields_rel(sd.sd_get_state(h)[2], xr, n).items():
         assert e <= 1e-7, (k, e)
+
+
+# --------------------------------------------------------------- traction sides
+# bc 1: manufactured solution with traction free-flow sides; bc 2: the paper's
+# pressure-driven problem (Sec. 5)
+@pytest.mark.parametrize("bc", [1, 2])
+@pytest.mark.parametrize("n", [4, 5, 12, 40])
+def test_traction_operator_parity(sd, n, bc):
+    K = I.lognormal_K(n, -4.0, 1.5, 4.0, seed=30 + n)
+    o = O.Oracle(n, 1e-3, 1.3, 0.05, K, bc=bc)
+    h = make(sd, n, 1e-3, K, 1.3, 0.05, bc=bc)
+    rng = np.random.default_rng(n)
+    for _ in range(3):
+        x = rng.standard_normal(o.ndof)
+        assert rel(sd.sd_apply(h, x), o.apply(x)) <= 1e-13
+    if n == 4:  # every column
+        A = o.scipy_csr().toarray()
+        scale = np.abs(A).max()
+        for k in range(o.ndof):
+            e = np.zeros(o.ndof)
+            e[k] = 1.0
+            assert np.abs(sd.sd_apply(h, e) - A[:, k]).max() <= 1e-14 * scale
+
+
+@pytest.mark.parametrize("bc", [1, 2])
+def test_traction_rhs_parity(sd, bc):
+    n = 24
+    K = I.lognormal_K(n, -4.0, 1.0, 4.0, seed=33)
+    o = O.Oracle(n, 1e-3, 0.9, 0.05, K, bc=bc, dp=2.0, t_end=0.5)
+    h = make(sd, n, 1e-3, K, 0.9, 0.05, bc=bc, bc_dp=2.0, bc_tend=0.5)
+    rng = np.random.default_rng(4)
+    for t in (0.05, 0.3, 0.73):
+        xp = rng.standard_normal(o.ndof)
+        assert rel(sd.sd_rhs(h, xp, t), o.rhs(xp, t)) <= 1e-13
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_traction_mms_time_stepping(sd, precision):
+    n = 32
+    K = np.ones((n, n))
+    o = O.Oracle(n, 1.0, 1.0, 0.1, K, bc=1)
+    xr = o.run(O.exact(n, 0.0, 1.0), 0.0, 5)
+    h = make(sd, n, 1.0, K, 1.0, 0.1, precision, rtol=1e-12, bc=1)
+    infos = sd.sd_step(h, 5)
+    assert all(i["status"] == 0 for i in infos)
+    for k, e in fields_rel(sd.sd_get_state(h)[2], xr, n).items():
+        assert e <= 1e-8, (k, e)
+
+
+@pytest.mark.parametrize("precision,n", [(0, 24), (1, 40), (1, 64)])
+def test_pressure_driven_problem(sd, precision, n):
+    # from rest, the inflow pressure rising over 10 steps; lognormal K
+    K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=34)
+    dt = 0.05
+    o = O.Oracle(n, 1e-3, 1.0, dt, K, bc=2, dp=1.0, t_end=10 * dt)
+    xr = o.run(np.zeros(o.ndof), 0.0, 6)
+    h = make(sd, n, 1e-3, K, 1.0, dt, precision, rtol=1e-12, bc=2, bc_dp=1.0, bc_tend=10 * dt)
+    infos = sd.sd_step(h, 6)
+    assert all(i["status"] == 0 for i in infos)
+    for k, e in fields_rel(sd.sd_get_state(h)[2], xr, n).items():
+        assert e <= 1e-8, (k, e)
+
+
+def test_pressure_driven_partitioned(sd):
+    # the partitioned coupling of Sec. 3 on the paper's problem
+    n = 32
+    K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=35)
+    dt = 0.05
+    o = O.Oracle(n, 1e-3, 1.0, dt, K, bc=2, dp=1.0, t_end=10 * dt)
+    xr = o.run(np.zeros(o.ndof), 0.0, 4)
+    h = make(sd, n, 1e-3, K, 1.0, dt, 1, rtol=1e-12, bc=2, bc_dp=1.0, bc_tend=10 * dt,
+             coupling=sd.SD_PARTITIONED, coupling_eps=1e-10)
+    infos = sd.sd_step(h, 4)
+    assert all(i["status"] == 0 for i in infos)
+    for k, e in fields_rel(sd.sd_get_state(h)[2], xr, n).items():
+        assert e <= 1e-7, (k, e)

@@ -98,3 +98,28 @@ def test_planted_interface_flux_moves_fixed_point():
     d = DNOracle(o, K, flux_scale=0.5)  # half the interface flux into the Darcy solve
     xd, _ = d.solve(b, np.zeros(n), eps=1e-12)
     assert np.linalg.norm(xd - x) > 1e-4 * np.linalg.norm(x)
+
+
+def test_paper_order_well_posed_with_pressure_sides():
+    # on the paper's pressure-driven problem (traction sides) the free-flow block
+    # with a prescribed v_Gamma is regular: the order of Sec. 3 is well posed there
+    import scipy.sparse.linalg as spl
+    n = 8
+    K = I.lognormal_K(n, -4.0, 1.0, 4.0, seed=10)
+    o = O.Oracle(n, 1e-3, 1.0, 0.05, K, bc=2)
+    d = DNOracle(o, K)
+    M = d.paper_order_ff_operator().tocsc()
+    off = O.offsets(n)
+    z = np.zeros(d.nF)
+    z[off["p_ff"]:off["p_pm"]] = 1.0
+    assert np.abs(M @ z).max() > 1e-3
+    lu = spl.splu(M)
+    rng = np.random.default_rng(0)
+    r = rng.standard_normal(d.nF)
+    x = lu.solve(r)
+    assert np.linalg.norm(M @ x - r) <= 1e-10 * np.linalg.norm(r)
+    # and the coupled iteration still reproduces the monolithic step
+    b = o.rhs(np.zeros(o.ndof), 0.05)
+    xd, _ = d.solve(b, np.zeros(n), eps=1e-12)
+    x_mono = o.solve(b)
+    assert np.linalg.norm(xd - x_mono) <= 1e-9 * np.linalg.norm(x_mono)

@@ -19,7 +19,17 @@ velocity and the porous-medium pressure at the interface:
   u, v (v_Gamma included, BJS slip of Eq. (6) inside) and p_ff; it passes on
   the new interface velocity v~ = v_Gamma.
 
-R(v) = S_ff(S_pm(v)) - v is the fixed-point residual of Sec. 3.  Each
+With traction free-flow sides (the paper's channel, bc 1 and 2) the order of
+Sec. 3 is also available (order="paper"): S_ff takes v_Gamma as Dirichlet
+data (identity v_Gamma rows) and returns the interface pressure p_Gamma, the
+normal stress that balances the v_Gamma half control volumes (their row of
+Eq. (5) with the TPFA reconstruction term mu h^2/(2K) v_Gamma and the -h p_pm
+coupling left out, divided by h); S_pm takes p_Gamma as Dirichlet pressure on
+its top boundary over the half cell below Gamma (transmissibility 2K/mu) and
+returns the Darcy velocity v~ = (2K/(mu h)) (p_c - p_Gamma) through Gamma.
+
+R(v) = S_ff(S_pm(v)) - v (order "pm") or S_pm(S_ff(v)) - v (order "paper") is
+the fixed-point residual of Sec. 3.  Each
 subdomain solve is the monolithic system's own rows with the other
 subdomain's unknowns held fixed, so at a root of R both subdomain states
 together satisfy every row of Eq. (9): the coupled iteration reproduces the
@@ -52,7 +62,8 @@ from . import Oracle, offsets
 class DNOracle:
     """Subdomain solvers S_pm, S_ff and the coupled iteration for one implicit-Euler step."""
 
-    def __init__(self, o: Oracle, K, flux_scale: float = 1.0):
+    def __init__(self, o: Oracle, K, flux_scale: float = 1.0, order: str = "pm"):
+        import scipy.sparse as sp
         import scipy.sparse.linalg as spl
         n = o.n
         self.o, self.n = o, n
@@ -69,8 +80,18 @@ class DNOracle:
         self.APF, self.APP = A[P, F].tocsr(), A[P, P].tocsc()
         # flux_scale != 1 lets a test plant a wrong interface flux in S_pm
         self.flux_scale = flux_scale
-        self._ff = spl.splu(self.AFF)
-        self._pm = spl.splu(self.APP)
+        self.order = order
+        if order == "paper":
+            Kt = np.asarray(K, dtype=np.float64).reshape(n, n)[n - 1]
+            self.rg = self.mu * self.h * self.h / (2.0 * Kt)   # reconstruction term of the v_Gamma rows
+            self.Ttop = 2.0 * Kt / self.mu                      # half-cell transmissibility below Gamma
+            self.Arow_G = A[self.G, :][:, F].tocsr()
+            self._ff = spl.splu(self.paper_order_ff_operator().tocsc())
+            app = self.APP.tocsr() + sp.diags(np.bincount(self.T, weights=self.Ttop, minlength=n * n))
+            self._pm = spl.splu(app.tocsc())
+        else:
+            self._ff = spl.splu(self.AFF)
+            self._pm = spl.splu(self.APP)
 
     def paper_order_ff_operator(self):
         """Free-flow rows with v_Gamma prescribed (identity rows): the first solver of Sec. 3's order."""
@@ -95,7 +116,27 @@ class DNOracle:
         xF = self._ff.solve(b[: self.nF] - self.AFP @ xP)
         return xF, xF[self.G].copy()
 
+    # --- the order of Sec. 3 (free flow first; traction sides only) --------
+    def s_ff_paper(self, v, b):
+        """Free-flow solve with v_Gamma = v prescribed; returns (x_F, p_Gamma)."""
+        bF = b[: self.nF].copy()
+        bF[self.G] = v
+        xF = self._ff.solve(bF)
+        pG = (self.Arow_G @ xF - self.rg * xF[self.G] - b[self.G]) / self.h
+        return xF, pG
+
+    def s_pm_paper(self, pG, b):
+        """Darcy solve with p_Gamma prescribed on top (half cell); returns (x_P, v~)."""
+        bP = b[self.nF:].copy()
+        bP[self.T] += self.Ttop * pG
+        xP = self._pm.solve(bP)
+        return xP, self.Ttop / self.h * (xP[self.T] - pG)
+
     def H(self, v, b):
+        if self.order == "paper":
+            xF, p = self.s_ff_paper(v, b)
+            xP, vt = self.s_pm_paper(p, b)
+            return vt, p, xF, xP
         xP, p = self.s_pm(v, b)
         xF, vt = self.s_ff(p, b)
         return vt, p, xF, xP

@@ -123,3 +123,29 @@ def test_paper_order_well_posed_with_pressure_sides():
     xd, _ = d.solve(b, np.zeros(n), eps=1e-12)
     x_mono = o.solve(b)
     assert np.linalg.norm(xd - x_mono) <= 1e-9 * np.linalg.norm(x_mono)
+
+
+@pytest.mark.parametrize("bc,n", [(1, 8), (2, 8), (2, 16)])
+def test_paper_order_reaches_monolithic_solution(bc, n):
+    # Sec. 3's order (free flow first with the velocity, then the porous medium
+    # with the interface pressure) on problems with traction sides: the
+    # monolithic solution is its fixed point (the interface pressure there is the
+    # TPFA reconstruction of Eq. (5)) and IQN-ILS reaches it
+    K = I.lognormal_K(n, -4.0, 1.0, 4.0, seed=11 + n)
+    mu = 1e-3
+    o = O.Oracle(n, mu, 1.0, 0.05, K, bc=bc)
+    x0 = O.exact(n, 0.0, mu) if bc == 1 else np.zeros(o.ndof)
+    b = o.rhs(x0, 0.05)
+    x = o.solve(b)
+    d = DNOracle(o, K, order="paper")
+    f = O.split(x, n)
+    v = f["v"][0].copy()
+    vt, p, xF, xP = d.H(v, b)
+    assert np.abs(vt - v).max() <= 1e-9 * np.abs(v).max()
+    recon = f["p_pm"][n - 1] - mu / n / (2.0 * K.reshape(n, n)[n - 1]) * v
+    assert np.abs(p - recon).max() <= 1e-9 * np.abs(recon).max()
+    xd, evals = d.solve(b, np.zeros(n), eps=1e-12)
+    assert np.linalg.norm(xd - x) <= 1e-8 * np.linalg.norm(x)
+    # relaxed first step, n difference columns, the step onto the fixed point,
+    # and the evaluations the stopping test needs to see the change vanish
+    assert evals <= n + 4

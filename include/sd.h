@@ -104,23 +104,45 @@ extern "C" {
                   (Eq. (7)) and passes on the pressure of the cells below the
                   interface; the free-flow solver takes that pressure into the
                   normal-stress balance of the interface faces (Eq. (5)) and
-                  passes on the new interface velocity; the fixed-point
-                  residual R(v) = S_ff(S_pm(v)) - v is driven to zero by
+                  passes on the new interface velocity (or the two run in the
+                  order of Sec. 3, coupling_order); the fixed-point residual
+                  R(v) = S_ff(S_pm(v)) - v (or S_pm(S_ff(v)) - v) is driven to zero by
                   IQN-ILS post-processing (relaxed first step, least-squares
                   inverse-Jacobian model from the differences of the time
                   step's earlier iterations), stopping when the exchanged
                   pressure and velocity both change by less than coupling_eps
                   relative (the test of Sec. 3).  Each subdomain solve is an
                   FGMRES on that subdomain's rows of Eq. (9) with the other
-                  side held fixed, preconditioned by the same V-cycles (V and
+                  side's data fixed, preconditioned by the same V-cycles (V and
                   Schur blocks / D' block), to rtol.  The converged state is
-                  the monolithic solution.  Sec. 3 solves the free flow first
-                  with the velocity as its data; that order needs a pressure
-                  boundary in the free flow, which the SD_BC_MMS problem lacks
-                  (its free-flow block with a prescribed interface velocity is
-                  singular), so the porous medium goes first. */
+                  the monolithic solution.  The order of the two solves:
+                  coupling_order below. */
 #define SD_MONOLITHIC 0
 #define SD_PARTITIONED 1
+
+/* order of the subdomain solves of SD_PARTITIONED:
+   SD_ORDER_FF_FIRST  Sec. 3's order: the free flow takes the interface
+                      velocity as Dirichlet data (identity v_Gamma rows) and
+                      returns the interface pressure, the normal stress that
+                      balances the v_Gamma half control volumes (Eq. (5));
+                      the porous medium takes that pressure on its top
+                      boundary over the half cell below the interface and
+                      returns the Darcy velocity through it (Eq. (7)).  Needs
+                      traction free-flow sides (SD_BC_MMS_TRACTION,
+                      SD_BC_PAPER): with the velocity prescribed on the rest of
+                      the free-flow boundary the free-flow problem is singular;
+   SD_ORDER_PM_FIRST  the porous medium takes the interface velocity as flux
+                      data and returns the pressure of the cells below the
+                      interface; the free flow takes that pressure into the
+                      normal-stress balance and returns the velocity;
+   SD_ORDER_AUTO      PM_FIRST.  (FF_FIRST's map multiplies the error of the
+                      free-flow solve by the half-cell Darcy transmissibility
+                      over h, 2K/(mu h), about 900 on the log-normal workload
+                      at n = 24: the subdomain tolerance then limits how far
+                      the coupling converges; PM_FIRST has no such factor.) */
+#define SD_ORDER_AUTO 0
+#define SD_ORDER_PM_FIRST 1
+#define SD_ORDER_FF_FIRST 2
 
 typedef struct sd_handle sd_handle;
 typedef struct sd_server sd_server;
@@ -176,6 +198,8 @@ typedef struct {
                                velocity that ends the iteration (default 1e-9) */
   double coupling_omega;    /* SD_PARTITIONED: relaxation of the first iteration of a step
                                (default 0.1) */
+  int32_t coupling_order;   /* SD_PARTITIONED: SD_ORDER_AUTO (default) | SD_ORDER_PM_FIRST |
+                               SD_ORDER_FF_FIRST */
   double bc_dp;        /* SD_BC_PAPER: amplitude of the inflow pressure (default 1) */
   double bc_tend;      /* SD_BC_PAPER: rise time T of the inflow pressure (default 0:
                           25 time steps) */

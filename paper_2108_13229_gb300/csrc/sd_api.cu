@@ -127,8 +127,8 @@ struct sd_handle {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // one captured Arnoldi step per basis index, per solve mode (monolithic, and the
   // free-flow and porous-medium subdomain solves of the partitioned coupling)
-  std::vector<cudaGraphExec_t> gexec[3];
-  std::vector<long long> gcount[3];            // kernels in each captured step
+  std::vector<cudaGraphExec_t> gexec[5];
+  std::vector<long long> gcount[5];            // kernels in each captured step
   Geom g;
   int nlev = 1;
   int m = 30;
@@ -250,6 +250,8 @@ void plan_all(sd_handle* h) {
     q.Q = a.take<double>(ld * qm);
     q.R = a.take<double>((long long)qm * qm);
     q.scal = a.take<double>(8);
+    q.pG = a.take<double>(ld);
+    q.vt = a.take<double>(ld);
   }
   if (h->opt.precision == SD_MIXED) plan_mg<float>(h, h->mg32, true);
   else plan_mg<double>(h, h->mg64, false);
@@ -749,25 +751,31 @@ void apply_precond(sd_handle* h, const double* r, double* z) {
 // unknowns held fixed: MODE_FF on the prefix [u | v | p_ff] of the
 // whole-system layout, MODE_PM on the suffix p_pm.  Vectors keep the
 // whole-system layout; a mode reads and writes only its own range.
-enum { MODE_MONO = 0, MODE_FF = 1, MODE_PM = 2 };
+// The order of Sec. 3 (free flow first) uses MODE_FFD, the free-flow rows
+// with the interface velocity prescribed, and MODE_PMD, the Darcy rows with
+// the interface pressure prescribed over the half cell below Gamma.
+enum { MODE_MONO = 0, MODE_FF = 1, MODE_PM = 2, MODE_FFD = 3, MODE_PMD = 4 };
 
 struct Range {
   long long off, len;
 };
 Range mode_range(const sd_handle* h, int mode) {
-  if (mode == MODE_FF) return {0, h->g.opm};
-  if (mode == MODE_PM) return {h->g.opm, h->g.lenD};
+  if (mode == MODE_FF || mode == MODE_FFD) return {0, h->g.opm};
+  if (mode == MODE_PM || mode == MODE_PMD) return {h->g.opm, h->g.lenD};
   return {0, h->g.len};
 }
 
 // y = A_mode x, or y = b - A_mode x
 void apply_op(sd_handle* h, int mode, const double* x, const double* b, double* y) {
   const Coef<double> c = coef64(h, 0);
-  if (mode == MODE_FF) {
-    launch_apply_ff(c, x, b, y, h->s);
+  if (mode == MODE_FF || mode == MODE_FFD) {
+    launch_apply_ff(c, x, b, y, mode == MODE_FFD, h->s);
   } else if (mode == MODE_PM) {
     const long long o = h->g.opm;
     launch_resid_D<double>(c, x + o, b ? b + o : nullptr, y + o, b ? 0 : 2, 1, 0, h->s);
+  } else if (mode == MODE_PMD) {
+    const long long o = h->g.opm;
+    launch_apply_pmd(c, x + o, b ? b + o : nullptr, y + o, h->s);
   } else {
     launch_apply_full(c, x, b, y, h->s);
   }
@@ -779,7 +787,7 @@ template <typename T>
 void precond_sub(sd_handle* h, MG<T>& M, int mode, const double* r, double* z) {
   cudaStream_t s = h->s;
   const Coef<double> c = coef64(h, 0);
-  if (mode == MODE_PM) {
+  if (mode == MODE_PM || mode == MODE_PMD) {
     launch_convert<T>(r + h->g.opm, M.L[0].D.b, h->g.lenD, s);
     vcycle_cell<T>(M, 0, false, s, h);
     launch_precond_exit<T>(c, z, M.L[0].D.res, s);
@@ -798,6 +806,8 @@ void precond_sub(sd_handle* h, MG<T>& M, int mode, const double* r, double* z) {
   vcycle_V<T>(M, 0, s, h);
   if (pmode == SD_PV_BGS_I) launch_precond_bgs_pff<T>(c, r, z, M.L[0].V.res, s);
   launch_precond_mid<T>(c, r, z, M.L[0].V.res, 0, (T*)nullptr, s);
+  if (mode == MODE_FFD)  // identity rows of the prescribed interface velocity
+    cudaMemcpyAsync(z + h->g.ov, r + h->g.ov, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, s);
 }
 
 void apply_precond_mode(sd_handle* h, int mode, const double* r, double* z) {
@@ -954,6 +964,11 @@ int fgmres(sd_handle* h, const double* b, double* x, sd_step_info* info, int mod
   return status;
 }
 
+// Order of the two subdomain solves: the porous medium first unless Sec. 3's
+// order (free flow first, velocity prescribed; traction sides only) is asked
+// for.
+bool partitioned_ff_first(const sd_options& o) { return o.coupling_order == SD_ORDER_FF_FIRST; }
+
 // Partitioned coupling of Sec. 3 for one time step (include/sd.h,
 // SD_PARTITIONED): the Darcy solve with the interface flux given, the
 // free-flow solve with the pressure below the interface given, and the
@@ -965,8 +980,10 @@ int step_partitioned(sd_handle* h, sd_step_info* info) {
   const Geom& g = h->g;
   IqnState& q = h->iqn;
   const int n = h->n;
+  const Coef<double> c = coef64(h, 0);
   double* vG = h->x + g.ov;                                       // interface faces of the state
   const double* pTop = h->x + g.opm + (long long)(n - 1) * g.P;  // pm cells below the interface
+  const bool ff_first = partitioned_ff_first(h->opt);
   CK(cudaMemcpyAsync(q.v, vG, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   CK(cudaMemsetAsync(q.scal, 0, sizeof(double) * 8, s));
   int iters = 0, it = 0, status = SD_OK, reorths = 0;
@@ -977,19 +994,42 @@ int step_partitioned(sd_handle* h, sd_step_info* info) {
     sd_step_info sp, sf;
     std::memset(&sp, 0, sizeof(sp));
     std::memset(&sf, 0, sizeof(sf));
-    launch_dn_rhs_pm(g, h->b, q.v, h->bsub, s);
-    int rc = fgmres(h, h->bsub, h->x, &sp, MODE_PM);
-    iters += sp.iters;
-    reorths += sp.reorths;
-    if (rc == SD_E_CUDA || rc == SD_E_NOMEM) return rc;
-    if (rc != SD_OK) { status = rc; break; }
-    launch_dn_rhs_ff(g, h->b, pTop, h->bsub, s);
-    rc = fgmres(h, h->bsub, h->x, &sf, MODE_FF);
-    iters += sf.iters;
-    reorths += sf.reorths;
-    if (rc == SD_E_CUDA || rc == SD_E_NOMEM) return rc;
-    if (rc != SD_OK) { status = rc; break; }
-    launch_iqn(q, vG, pTop, s);
+    int rc;
+    if (ff_first) {
+      // free flow with the interface velocity prescribed, then the Darcy rows with
+      // the interface pressure it returns
+      launch_dn_iface(3, c, nullptr, h->b, q.v, h->bsub, s);
+      CK(cudaMemcpyAsync(vG, q.v, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      rc = fgmres(h, h->bsub, h->x, &sf, MODE_FFD);
+      iters += sf.iters;
+      reorths += sf.reorths;
+      if (rc == SD_E_CUDA || rc == SD_E_NOMEM) return rc;
+      if (rc != SD_OK) { status = rc; break; }
+      launch_apply_ff(c, h->x, nullptr, h->V, 0, s);
+      launch_dn_iface(0, c, h->V, h->b, h->x, q.pG, s);
+      launch_dn_iface(2, c, nullptr, h->b, q.pG, h->bsub, s);
+      rc = fgmres(h, h->bsub, h->x, &sp, MODE_PMD);
+      iters += sp.iters;
+      reorths += sp.reorths;
+      if (rc == SD_E_CUDA || rc == SD_E_NOMEM) return rc;
+      if (rc != SD_OK) { status = rc; break; }
+      launch_dn_iface(1, c, h->x, nullptr, q.pG, q.vt, s);
+      launch_iqn(q, q.vt, q.pG, s);
+    } else {
+      launch_dn_rhs_pm(g, h->b, q.v, h->bsub, s);
+      rc = fgmres(h, h->bsub, h->x, &sp, MODE_PM);
+      iters += sp.iters;
+      reorths += sp.reorths;
+      if (rc == SD_E_CUDA || rc == SD_E_NOMEM) return rc;
+      if (rc != SD_OK) { status = rc; break; }
+      launch_dn_rhs_ff(g, h->b, pTop, h->bsub, s);
+      rc = fgmres(h, h->bsub, h->x, &sf, MODE_FF);
+      iters += sf.iters;
+      reorths += sf.reorths;
+      if (rc == SD_E_CUDA || rc == SD_E_NOMEM) return rc;
+      if (rc != SD_OK) { status = rc; break; }
+      launch_iqn(q, vG, pTop, s);
+    }
     CK(cudaMemcpyAsync(h->hflag + 8, q.scal + 2, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     const double* f = h->hflag + 8;  // |dp|^2 (negative: first evaluation), |p|^2, |dv|^2, |v~|^2
@@ -1078,6 +1118,10 @@ int validate(const sd_grid* grid, double mu, double alpha, double dt, const sd_o
   if (o->darcy_coupled < 0 || o->darcy_coupled > 2) return SD_E_INVAL;
   if (o->tile_rows != 0 && o->tile_rows != 8 && o->tile_rows != 16) return SD_E_INVAL;
   if (o->coupling != SD_MONOLITHIC && o->coupling != SD_PARTITIONED) return SD_E_INVAL;
+  if (o->coupling_order < SD_ORDER_AUTO || o->coupling_order > SD_ORDER_FF_FIRST) return SD_E_INVAL;
+  // the free flow with a prescribed interface velocity is singular on Dirichlet sides
+  if (o->coupling == SD_PARTITIONED && o->coupling_order == SD_ORDER_FF_FIRST && o->bc == SD_BC_MMS)
+    return SD_E_INVAL;
   if (o->coupling == SD_PARTITIONED &&
       (o->coupling_max < 1 || o->coupling_columns < 1 || o->coupling_columns > 30 || !(o->coupling_eps > 0) ||
        !(o->coupling_omega > 0) || !(o->coupling_omega <= 2)))
@@ -1143,7 +1187,7 @@ int create_impl(const sd_grid* grid, double mu, const double* K, double alpha, d
   if (cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess)
     return fail(SD_E_CUDA);
-  for (int q = 0; q < 3; ++q) {
+  for (int q = 0; q < 5; ++q) {
     h->gexec[q].assign(h->m, nullptr);
     h->gcount[q].assign(h->m, 0);
   }
@@ -1159,7 +1203,7 @@ int create_impl(const sd_grid* grid, double mu, const double* K, double alpha, d
   for (int l = 0; l < h->nlev; ++l) {
     LevelCoef<double>& C = h->c64[l];
     const Geom& g = h->geo[l];
-    launch_setup_coef<double>(h->Klev[l], g.n, g.P, mu, alpha, o.bc != SD_BC_MMS, C.w, C.rg, C.Tx, C.Ty, s);
+    launch_setup_coef<double>(h->Klev[l], g.n, g.P, mu, alpha, o.bc != SD_BC_MMS, 0, C.w, C.rg, C.Tx, C.Ty, s);
   }
   // pressure Laplacian B^T B / h^2: TPFA with K / mu = 1 (the staging buffer
   // holds the unit permeability, the Krylov slots are free during setup)
@@ -1167,7 +1211,8 @@ int create_impl(const sd_grid* grid, double mu, const double* K, double alpha, d
     LevelCoef<double>& C = h->c64[l];
     const Geom& g = h->geo[l];
     launch_fill_K(h->V, g.n, g.P, mu, s);
-    launch_setup_coef<double>(h->V, g.n, g.P, mu, alpha, o.bc != SD_BC_MMS, C.wP, C.rgP, C.TxP, C.TyP, s);
+    launch_setup_coef<double>(h->V, g.n, g.P, mu, alpha, o.bc != SD_BC_MMS, o.bc != SD_BC_MMS, C.wP, C.rgP, C.TxP,
+                              C.TyP, s);
   }
   const Coef<double> c0 = coef64(h, 0);
   launch_mms_terms(c0, o.bc, h->Klev[0], h->B0, h->B1, s);
@@ -1475,6 +1520,7 @@ void sd_options_default(sd_options* o) {
   o->coupling_columns = 30;
   o->coupling_eps = 1e-9;
   o->coupling_omega = 0.1;
+  o->coupling_order = SD_ORDER_AUTO;
   o->bc_dp = 1.0;
   o->bc_tend = 0.0;
   o->schur_gamma = 0.5;

@@ -172,16 +172,22 @@ void launch_coarsen_K(const double* Kf, int nf, int Pf, double* Kc, int Pc, cuda
 void launch_pack_K(const double* Kdense, int n, double* Kp, int P, cudaStream_t s);
 void launch_fill_K(double* K, int n, int P, double v, cudaStream_t s);
 template <typename T>
-void launch_setup_coef(const double* Kp, int n, int P, double mu, double alpha, int lat, T* w, T* rg, T* Tx, T* Ty,
-                       cudaStream_t s);
+void launch_setup_coef(const double* Kp, int n, int P, double mu, double alpha, int lat, int xdir, T* w, T* rg, T* Tx,
+                       T* Ty, cudaStream_t s);
 template <typename T>
 void launch_convert(const double* src, T* dst, long long len, cudaStream_t s);
 
 // whole-system operator (FP64): y = A x  or  y = b - A x
 void launch_apply_full(const Coef<double>& c, const double* x, const double* b, double* y, cudaStream_t s);
 // the free-flow rows of it (u, v, p_ff) with the porous-medium unknowns taken as zero;
-// the Darcy rows of y are not written
-void launch_apply_ff(const Coef<double>& c, const double* x, const double* b, double* y, cudaStream_t s);
+// the Darcy rows of y are not written; vdir: the v_Gamma rows are identities
+void launch_apply_ff(const Coef<double>& c, const double* x, const double* b, double* y, int vdir, cudaStream_t s);
+// Darcy rows with the interface pressure prescribed over the half cell below Gamma
+// (x, b, y: the p_pm block)
+void launch_apply_pmd(const Coef<double>& c, const double* x, const double* b, double* y, cudaStream_t s);
+// interface quantities of the free-flow-first order (ops in sd_ops.cu)
+void launch_dn_iface(int op, const Coef<double>& c, const double* a, const double* b, const double* q, double* out,
+                     cudaStream_t s);
 // partitioned coupling: subdomain right-hand sides from the monolithic b.
 //   pm: bs[p_pm] = b[p_pm] - h v on the cells below the interface (v: n values)
 //   ff: bs[u, v, p_ff] = b + h p on the interface faces (p: n values, the pressure below)
@@ -200,6 +206,8 @@ struct IqnState {
   double* Q;        // orthonormal basis of the Vc columns (modified Gram-Schmidt)
   double* R;        // upper triangle, column j at j * qmax
   double* scal;     // [0] k, [1] q, [2..5] |p - p_prev|^2, |p|^2, |v~ - v|^2, |v~|^2
+  double* pG;       // free-flow-first order: the interface pressure and velocity of an evaluation
+  double* vt;
   long long ld;     // column stride
 };
 void launch_iqn(const IqnState& st, const double* vt, const double* p, cudaStream_t s);

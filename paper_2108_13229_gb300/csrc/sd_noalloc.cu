@@ -87,7 +87,7 @@ extern "C" int sd_apply_noalloc(const sd_grid* grid, double mu, const double* K,
   // every scratch entry that the operator reads is written first in this
   // call, so the previous call's contents never leak into the result
   launch_pack_K(K, n, base + oK, g.P, s);
-  launch_setup_coef<double>(base + oK, n, g.P, mu, alpha_bj, 0, base + ow, base + org, base + oTx, base + oTy, s);
+  launch_setup_coef<double>(base + oK, n, g.P, mu, alpha_bj, 0, 0, base + ow, base + org, base + oTx, base + oTy, s);
   launch_pack(g, x, base + ox, s);
   Coef<double> c;
   c.n = n;

@@ -229,10 +229,11 @@ __device__ __forceinline__ void d_row(const Coef<T>& c, const T* __restrict__ p,
 }
 
 // ------------------------------------------------------- whole operator (K1)
-// FF: the free-flow rows only (u, v, p_ff), with the porous-medium unknowns
+// FF 1: the free-flow rows only (u, v, p_ff), with the porous-medium unknowns
 // taken as zero and the Darcy rows not written (subdomain solve of the
-// partitioned coupling).
-template <int R, bool FF>
+// partitioned coupling); FF 2: the same with the v_Gamma rows replaced by
+// identities (the interface velocity prescribed).
+template <int R, int FF>
 __global__ void k_apply_full(Coef<double> c, const double* __restrict__ x, const double* __restrict__ b,
                              double* __restrict__ y, Bat bt) {
   griddep_wait();
@@ -277,7 +278,7 @@ __global__ void k_apply_full(Coef<double> c, const double* __restrict__ x, const
       const long long kv = (long long)j * P + i;
       const long long k = (long long)n * P + kv;
       double val;
-      if (j == n) {
+      if (j == n || (FF == 2 && j == 0)) {
         val = v[kv];
       } else {
         double off, dg;
@@ -312,16 +313,84 @@ void launch_apply_full(const Coef<double>& c, const double* x, const double* b, 
   SD_COUNT(1);
   const int R = rows_apply(c.n);
   if (R == 4)
-    launch_k(k_apply_full<4, false>, dim3(grid2R(c.n + 1, c.n + 1, 4)), dim3(dim3(BX, BY)), 0, s, c, x, b, y);
-  else launch_k(k_apply_full<1, false>, dim3(grid2R(c.n + 1, c.n + 1, 1)), dim3(dim3(BX, BY)), 0, s, c, x, b, y);
+    launch_k(k_apply_full<4, 0>, dim3(grid2R(c.n + 1, c.n + 1, 4)), dim3(dim3(BX, BY)), 0, s, c, x, b, y);
+  else launch_k(k_apply_full<1, 0>, dim3(grid2R(c.n + 1, c.n + 1, 1)), dim3(dim3(BX, BY)), 0, s, c, x, b, y);
 }
 
-void launch_apply_ff(const Coef<double>& c, const double* x, const double* b, double* y, cudaStream_t s) {
+void launch_apply_ff(const Coef<double>& c, const double* x, const double* b, double* y, int vdir, cudaStream_t s) {
   SD_COUNT(1);
   const int R = rows_apply(c.n);
-  if (R == 4)
-    launch_k(k_apply_full<4, true>, dim3(grid2R(c.n + 1, c.n + 1, 4)), dim3(dim3(BX, BY)), 0, s, c, x, b, y);
-  else launch_k(k_apply_full<1, true>, dim3(grid2R(c.n + 1, c.n + 1, 1)), dim3(dim3(BX, BY)), 0, s, c, x, b, y);
+  const dim3 g = grid2R(c.n + 1, c.n + 1, R);
+  if (R == 4) {
+    if (vdir) launch_k(k_apply_full<4, 2>, g, dim3(BX, BY), 0, s, c, x, b, y);
+    else launch_k(k_apply_full<4, 1>, g, dim3(BX, BY), 0, s, c, x, b, y);
+  } else {
+    if (vdir) launch_k(k_apply_full<1, 2>, g, dim3(BX, BY), 0, s, c, x, b, y);
+    else launch_k(k_apply_full<1, 1>, g, dim3(BX, BY), 0, s, c, x, b, y);
+  }
+}
+
+// Darcy rows with the interface pressure prescribed over the half cell below
+// Gamma (transmissibility 2K/mu = h^2 / rg on the top row): the porous-medium
+// solve of the order of Sec. 3.  x, b, y: the p_pm block (n rows x P).
+__global__ void k_apply_pmd(Coef<double> c, const double* __restrict__ x, const double* __restrict__ b,
+                            double* __restrict__ y) {
+  griddep_wait();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int n = c.n;
+  if (i >= n || j >= n) return;
+  const int k = j * c.P + i;
+  double off, dg;
+  d_row(c, x, i, j, true, off, dg);
+  double val = dg * x[k] + off;
+  if (j == n - 1) val += c.h * c.h / c.rg[i] * x[k];
+  y[k] = b ? b[k] - val : val;
+}
+
+void launch_apply_pmd(const Coef<double>& c, const double* x, const double* b, double* y, cudaStream_t s) {
+  SD_COUNT(1);
+  launch_k(k_apply_pmd, dim3(grid2(c.n, c.n)), dim3(dim3(BX, BY)), 0, s, c, x, b, y);
+}
+
+// Interface quantities of the order of Sec. 3 (n values each):
+//  op 0: p_Gamma = (y_vG - rg v_G - b_vG) / h from the free-flow row y of the
+//        v_Gamma faces (k_apply_full, FF 1), i.e. the normal stress balancing
+//        the half control volume without the reconstruction term;
+//  op 1: v~ = (h / rg) (p_top - p_Gamma), the Darcy velocity through Gamma;
+//  op 2: bs[p_pm] = b[p_pm] (+ (h^2 / rg) p_Gamma on the top row);
+//  op 3: bs[u, v, p_ff] = b with the v_Gamma rows replaced by v.
+__global__ void k_dn_iface(int op, Coef<double> c, const double* __restrict__ a, const double* __restrict__ b,
+                           const double* __restrict__ q, double* __restrict__ out) {
+  griddep_wait();
+  const int n = c.n, P = c.P;
+  const double h = c.h;
+  const long long ov = (long long)n * P, opm = (long long)(3 * n + 1) * P;
+  const long long e0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
+  if (op == 0) {
+    for (long long i = e0; i < n; i += st) out[i] = (a[ov + i] - c.rg[i] * q[ov + i] - b[ov + i]) / h;
+  } else if (op == 1) {
+    for (long long i = e0; i < n; i += st) out[i] = h / c.rg[i] * (a[opm + (long long)(n - 1) * P + i] - q[i]);
+  } else if (op == 2) {
+    const long long len = (long long)n * P, top = (long long)(n - 1) * P;
+    for (long long e = e0; e < len; e += st) {
+      const long long i = e - top;
+      out[opm + e] = (i >= 0 && i < n) ? b[opm + e] + h * h / c.rg[i] * q[i] : b[opm + e];
+    }
+  } else {
+    for (long long e = e0; e < opm; e += st) {
+      const long long i = e - ov;
+      out[e] = (i >= 0 && i < n) ? q[i] : b[e];
+    }
+  }
+}
+
+void launch_dn_iface(int op, const Coef<double>& c, const double* a, const double* b, const double* q, double* out,
+                     cudaStream_t s) {
+  SD_COUNT(1);
+  const long long work = op <= 1 ? c.n : (op == 2 ? (long long)c.n * c.P : (long long)(3 * c.n + 1) * c.P);
+  const long long nb = (work + 255) / 256;
+  launch_k(k_dn_iface, dim3((int)(nb < 152 * 16 ? nb : 152 * 16)), dim3(256), 0, s, op, c, a, b, q, out);
 }
 
 // --------------------------------------------- partitioned coupling (Sec. 3)
@@ -1622,9 +1691,13 @@ void launch_coarsen_K(const double* Kf, int nf, int Pf, double* Kc, int Pc, cuda
   launch_k(k_coarsen_K, dim3(grid2(nf / 2, nf / 2)), dim3(dim3(BX, BY)), 0, s, Kf, nf, Pf, Kc, Pc);
 }
 
+// lat: traction free-flow sides (BJS coefficients of their interface corners);
+// xdir: the x boundary faces are Dirichlet over the half cell (2K/mu) instead
+// of no-flow -- the pressure Laplacian of the Schur block with traction sides,
+// where the side u faces, like v_Gamma, have half-volume mass
 template <typename T>
-__global__ void k_setup_coef(const double* __restrict__ K, int n, int P, double mu, double alpha, int lat, T* w,
-                             T* rg, T* Tx, T* Ty) {
+__global__ void k_setup_coef(const double* __restrict__ K, int n, int P, double mu, double alpha, int lat, int xdir,
+                             T* w, T* rg, T* Tx, T* Ty) {
   griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -1635,6 +1708,8 @@ __global__ void k_setup_coef(const double* __restrict__ K, int n, int P, double 
     if (i > 0 && i < n) {
       const double ka = K[(long long)j * P + i - 1], kb = K[(long long)j * P + i];
       t = 2.0 * ka * kb / (ka + kb) / mu;
+    } else if (xdir) {
+      t = 2.0 * K[(long long)j * P + (i == 0 ? 0 : n - 1)] / mu;
     }
     Tx[(long long)j * P + i] = (T)t;
   }
@@ -1663,11 +1738,11 @@ __global__ void k_setup_coef(const double* __restrict__ K, int n, int P, double 
 }
 
 template <typename T>
-void launch_setup_coef(const double* Kp, int n, int P, double mu, double alpha, int lat, T* w, T* rg, T* Tx, T* Ty,
-                       cudaStream_t s) {
+void launch_setup_coef(const double* Kp, int n, int P, double mu, double alpha, int lat, int xdir, T* w, T* rg, T* Tx,
+                       T* Ty, cudaStream_t s) {
   SD_COUNT(1);
-  launch_k(k_setup_coef<T>, dim3(grid2(n + 1, n + 1)), dim3(dim3(BX, BY)), 0, s, Kp, n, P, mu, alpha, lat, w, rg, Tx,
-           Ty);
+  launch_k(k_setup_coef<T>, dim3(grid2(n + 1, n + 1)), dim3(dim3(BX, BY)), 0, s, Kp, n, P, mu, alpha, lat, xdir, w,
+           rg, Tx, Ty);
 }
 
 template <typename T>
@@ -1909,7 +1984,8 @@ void launch_unpack(const Geom& g, const double* padded, double* dense, cudaStrea
 
 // ------------------------------------------------------- instantiations
 #define SD_INST(T)                                                                                               \
-  template void launch_setup_coef<T>(const double*, int, int, double, double, int, T*, T*, T*, T*, cudaStream_t); \
+  template void launch_setup_coef<T>(const double*, int, int, double, double, int, int, T*, T*, T*, T*,          \
+                                     cudaStream_t);                                                                \
   template void launch_convert<T>(const double*, T*, long long, cudaStream_t);                                   \
   template void launch_cheb_V<T>(const Coef<T>&, const T*, const T*, T*, T*, T, T, const T*, int, long long, cudaStream_t); \
   template void launch_cheb_D<T>(const Coef<T>&, const T*, const T*, T*, T*, T, T, const T*, int, long long, cudaStream_t); \

@@ -25,6 +25,7 @@ SD_PROF_APPLY, SD_PROF_CHEB_V, SD_PROF_MUPDATE, SD_PROF_MDOT = 0, 1, 2, 3
 SD_NOALLOC_MAX_N = 256
 SD_BATCH_LOCKSTEP = 1
 SD_MONOLITHIC, SD_PARTITIONED = 0, 1
+SD_ORDER_AUTO, SD_ORDER_PM_FIRST, SD_ORDER_FF_FIRST = 0, 1, 2
 
 
 class SdError(RuntimeError):
@@ -49,6 +50,7 @@ class sd_options(ctypes.Structure):
                 ("darcy_coupled", ctypes.c_int32), ("coupling", ctypes.c_int32),
                 ("coupling_max", ctypes.c_int32), ("coupling_columns", ctypes.c_int32),
                 ("coupling_eps", ctypes.c_double), ("coupling_omega", ctypes.c_double),
+                ("coupling_order", ctypes.c_int32),
                 ("bc_dp", ctypes.c_double), ("bc_tend", ctypes.c_double),
                 ("stream", ctypes.c_void_p)]
 

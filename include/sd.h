@@ -378,7 +378,7 @@ int sd_apply_noalloc(const sd_grid *grid, double mu, const double *K, double alp
  * still reaches base->rtol.
  *   K          host or device permeability as in sd_create;
  *   cache_path text file (NULL or "": no cache).  A line matching this device,
- *              n, precision, precond, darcy_coupled, restart and rtol is
+ *              n, precision, precond, darcy_coupled, restart, bc, coupling and rtol is
  *              returned without timing; otherwise the winner is appended;
  *   best       receives *base with the three tuned fields;
  *   best_ms    (may be NULL) mean device ms per step of the winner.

@@ -26,7 +26,7 @@ std::mutex g_cache_mu;
 
 struct Key {
   std::string dev;
-  int n, precision, precond, darcy_coupled, restart;
+  int n, precision, precond, darcy_coupled, restart, bc, coupling;
   double rtol;
 };
 
@@ -42,21 +42,21 @@ std::string device_tag() {
   return s + buf;
 }
 
-// One cache line: "sdtune1 dev n precision precond darcy_coupled restart rtol
-// tile_rows coarsest cheb_degree ms_per_step".
+// One cache line: "sdtune2 dev n precision precond darcy_coupled restart bc
+// coupling rtol tile_rows coarsest cheb_degree ms_per_step".
 bool cache_lookup(const char* path, const Key& k, sd_options* o, double* ms) {
   FILE* f = std::fopen(path, "r");
   if (!f) return false;
   char line[512], dev[256];
   bool found = false;
   while (std::fgets(line, sizeof(line), f)) {
-    int n, pr, pc, dc, rs, tr, co, cd;
+    int n, pr, pc, dc, rs, bc, cp, tr, co, cd;
     double rt, t;
-    if (std::sscanf(line, "sdtune1 %255s %d %d %d %d %d %lg %d %d %d %lg", dev, &n, &pr, &pc, &dc, &rs, &rt, &tr,
-                    &co, &cd, &t) != 11)
+    if (std::sscanf(line, "sdtune2 %255s %d %d %d %d %d %d %d %lg %d %d %d %lg", dev, &n, &pr, &pc, &dc, &rs, &bc,
+                    &cp, &rt, &tr, &co, &cd, &t) != 13)
       continue;
     if (k.dev != dev || n != k.n || pr != k.precision || pc != k.precond || dc != k.darcy_coupled ||
-        rs != k.restart || rt != k.rtol)
+        rs != k.restart || bc != k.bc || cp != k.coupling || rt != k.rtol)
       continue;
     o->tile_rows = tr;  // the last matching line wins
     o->coarsest = co;
@@ -71,8 +71,9 @@ bool cache_lookup(const char* path, const Key& k, sd_options* o, double* ms) {
 void cache_store(const char* path, const Key& k, const sd_options& o, double ms) {
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "sdtune1 %s %d %d %d %d %d %.17g %d %d %d %.6f\n", k.dev.c_str(), k.n, k.precision, k.precond,
-               k.darcy_coupled, k.restart, k.rtol, o.tile_rows, o.coarsest, o.cheb_degree, ms);
+  std::fprintf(f, "sdtune2 %s %d %d %d %d %d %d %d %.17g %d %d %d %.6f\n", k.dev.c_str(), k.n, k.precision,
+               k.precond, k.darcy_coupled, k.restart, k.bc, k.coupling, k.rtol, o.tile_rows, o.coarsest,
+               o.cheb_degree, ms);
   std::fclose(f);
 }
 
@@ -103,7 +104,7 @@ extern "C" int sd_autotune(const sd_grid* grid, double mu, const double* K, doub
   sd_options b;
   sd_options_default(&b);
   if (base) b = *base;
-  Key key{device_tag(), grid->nx, b.precision, b.precond, b.darcy_coupled, b.restart, b.rtol};
+  Key key{device_tag(), grid->nx, b.precision, b.precond, b.darcy_coupled, b.restart, b.bc, b.coupling, b.rtol};
   if (cache_path && cache_path[0]) {
     std::lock_guard<std::mutex> lk(g_cache_mu);
     sd_options o = b;

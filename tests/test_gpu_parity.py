@@ -350,7 +350,7 @@ def test_autotune(sd, tmp_path):
     assert best.tile_rows in (8, 16) and best.coarsest in (4, 8, 16) and best.cheb_degree in (2, 3, 4)
     assert best.rtol == base.rtol and best.restart == base.restart
     lines = open(cache).read().splitlines()
-    assert len(lines) == 1 and lines[0].startswith("sdtune1 ")
+    assert len(lines) == 1 and lines[0].startswith("sdtune2 ")
     again, ms2 = sd.sd_autotune(n, 1e-3, K, 1.0, 0.05, base, 1, cache)
     assert (again.tile_rows, again.coarsest, again.cheb_degree) == (best.tile_rows, best.coarsest, best.cheb_degree)
     assert abs(ms2 - ms) <= 1e-6 * ms and len(open(cache).read().splitlines()) == 1

@@ -1,5 +1,6 @@
 """The C ABI without a GPU: the library builds, loads and exports every entry
 point include/sd.h declares; host-side validation and sizes."""
+import ctypes
 import os
 import re
 
@@ -87,3 +88,42 @@ def test_struct_layout_matches_binding(sd):
     import ctypes
     for k, cls in enumerate([sd.sd_grid, sd.sd_options, sd.sd_step_info, sd.sd_request, sd.sd_result]):
         assert sd.sd_struct_size(k) == ctypes.sizeof(cls), cls.__name__
+
+
+def test_option_validation_without_gpu(sd):
+    # every option is checked on the host before any device work
+    n = 8
+    K = np.ones((n, n))
+    g = sd.sd_grid(n, n)
+    bad = [("bc", 3), ("bc", -1), ("coupling", 2), ("coupling_order", 3), ("tile_rows", 12),
+           ("cheb_degree", 0), ("cheb_degree", 9), ("coarsest", 1), ("darcy_coupled", 3), ("orth", 2),
+           ("bc_tend", -1.0), ("bc_dp", float("nan"))]
+    for field, value in bad:
+        o = sd.sd_options_default()
+        setattr(o, field, value)
+        assert sd._load().sd_memory_estimate(ctypes.byref(g), ctypes.byref(o)) == -1, field
+        with pytest.raises(sd.SdError) as e:
+            sd.sd_create(n, 1.0, K, 1.0, 0.1, o)
+        assert e.value.code == sd.SD_E_INVAL, field
+    # partitioned coupling: its parameters, and Sec. 3's order needs traction sides
+    for field, value in [("coupling_columns", 0), ("coupling_columns", 31), ("coupling_eps", 0.0),
+                         ("coupling_omega", 0.0), ("coupling_max", 0)]:
+        o = sd.sd_options_default()
+        o.coupling = sd.SD_PARTITIONED
+        setattr(o, field, value)
+        assert sd._load().sd_memory_estimate(ctypes.byref(g), ctypes.byref(o)) == -1, field
+    o = sd.sd_options_default()
+    o.coupling = sd.SD_PARTITIONED
+    o.coupling_order = sd.SD_ORDER_FF_FIRST
+    assert sd._load().sd_memory_estimate(ctypes.byref(g), ctypes.byref(o)) == -1
+    o.bc = sd.SD_BC_PAPER
+    assert sd._load().sd_memory_estimate(ctypes.byref(g), ctypes.byref(o)) > 0
+    # the partitioned state adds the subdomain right-hand side and the IQN-ILS columns
+    base = sd.sd_options_default()
+    assert sd._load().sd_memory_estimate(ctypes.byref(g), ctypes.byref(o)) > \
+        sd._load().sd_memory_estimate(ctypes.byref(g), ctypes.byref(base))
+    # valid boundary modes
+    for bc in (sd.SD_BC_MMS, sd.SD_BC_MMS_TRACTION, sd.SD_BC_PAPER):
+        o = sd.sd_options_default()
+        o.bc = bc
+        assert sd._load().sd_memory_estimate(ctypes.byref(g), ctypes.byref(o)) > 0

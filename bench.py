@@ -243,6 +243,7 @@ def bench_batch(sd, count: int, steps: int, threads: int, seed: int = 0, lockste
     for wl in wls:
         o = sd.sd_options_default()
         hs.append(sd.sd_create(wl.n, wl.mu, wl.K(), wl.alpha, wl.dt, o))
+    sd.sd_solve_batch(hs, [3] * count, max_threads=threads, lockstep=lockstep)  # warm-up (graph captures)
     l0 = sd.sd_launch_count()
     t0 = time.perf_counter()
     infos = sd.sd_solve_batch(hs, [steps] * count, max_threads=threads, lockstep=lockstep)

@@ -281,7 +281,8 @@ void sd_destroy(sd_handle *h);
  * infos[k] NULL or nsteps[k] entries (ms: the step time of hs[k]'s group).
  *
  * Handles with the same grid size, mu, dt and options (the stream aside) and
- * the same nsteps form a lockstep group: every kernel launch of the group
+ * the same nsteps form lockstep groups of at most about 2M DoF (larger grids
+ * run one per stream, where a single grid already fills the GPU): every kernel launch of a group
  * serves all its instances (one instance per blockIdx.z, each instance's
  * buffers addressed from its own allocation), the Arnoldi steps of the
  * group are captured as one CUDA graph per basis index, and an instance

@@ -1247,6 +1247,8 @@ int create_impl(const sd_grid* grid, double mu, const double* K, double alpha, d
 // same.
 namespace sdk {
 
+int handle_grid(const sd_handle* h) { return h->n; }
+
 bool can_lockstep(const sd_handle* a, const sd_handle* b) {
   const sd_options& x = a->opt;
   const sd_options& y = b->opt;

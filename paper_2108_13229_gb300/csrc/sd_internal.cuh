@@ -376,6 +376,8 @@ bool can_lockstep(const sd_handle* a, const sd_handle* b);
 // on the first handle's stream; infos[i] (may be null) receives instance i's
 // per-step information.  Returns the first non-OK step status.
 int step_lockstep(sd_handle* const* hs, int count, int nsteps, sd_step_info* const* infos);
+// cells per side of a handle's grid
+int handle_grid(const sd_handle* h);
 #endif
 
 }  // namespace sdk

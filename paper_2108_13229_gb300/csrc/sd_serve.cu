@@ -11,6 +11,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -25,6 +26,13 @@
 namespace {
 
 using clk = std::chrono::steady_clock;
+
+// DoF of one lockstep group at most.  Measured on GB300 with 10-step runs of
+// 64 log-normal instances: 512^2 grids ran fastest one per stream (one 512^2
+// grid already fills the GPU, and a group waits for its slowest member),
+// 256^2 grids best about eight to a group, 64^2-128^2 grids all in one group
+// (1.8-2.4x the one-stream-per-instance rate); 2M DoF per group gives that.
+const int64_t kLockstepDof = 2ll << 20;
 
 double ms_between(clk::time_point a, clk::time_point b) {
   return std::chrono::duration<double, std::milli>(b - a).count();
@@ -149,6 +157,19 @@ int sd_solve_batch_ex(sd_handle* const* hs, int32_t count, const int32_t* nsteps
       }
     }
     if (!placed) items.push_back(std::vector<int>(1, k));
+  }
+  // split large groups: a group of big grids already fills the GPU with each
+  // launch, and smaller groups run concurrently on their own streams and wait
+  // for fewer slow instances (lockstep runs every group to its slowest member)
+  {
+    std::vector<std::vector<int>> split;
+    for (auto& it : items) {
+      const int64_t dof = sd_dof_count(sdk::handle_grid(hs[it[0]]));
+      const int cap = (int)std::max<int64_t>(1, kLockstepDof / dof);
+      for (size_t a = 0; a < it.size(); a += (size_t)cap)
+        split.emplace_back(it.begin() + a, it.begin() + std::min(it.size(), a + (size_t)cap));
+    }
+    items.swap(split);
   }
   const int ni = (int)items.size();
   const int nt = (max_threads > 0 && max_threads < ni) ? max_threads : ni;

@@ -216,6 +216,9 @@ typedef struct {
   int32_t coupling_iters; /* SD_PARTITIONED: subdomain-solve pairs of this step (0 otherwise);
                              iters then counts the FGMRES iterations of all subdomain solves
                              and relres is the monolithic residual of the coupled state */
+  double relres_v;   /* the same residual restricted to the velocity rows [u | v], */
+  double relres_pff; /*   the continuity rows p_ff and the Darcy rows p_pm, each over ||b||_2 */
+  double relres_pm;  /*   (-1 when a cycle ended on NaN/Inf) */
 } sd_step_info;
 
 /* Fill *opt with the defaults above. */

@@ -158,7 +158,8 @@ struct sd_handle {
   double prof_ms = 0.0, prof_bytes = 0.0, prof_flops = 0.0;
   long long prof_launches = 0;
   // scalar slots in scal[]
-  static const int S_H1 = 0, S_H2 = 32, S_N2 = 64, S_B2 = 65, S_BN = 66, S_N2B = 67, S_REO = 68, S_Y = 96;
+  static const int S_H1 = 0, S_H2 = 32, S_N2 = 64, S_B2 = 65, S_BN = 66, S_N2B = 67, S_REO = 68, S_BLK = 69,
+                   S_Y = 96;
 };
 
 namespace {
@@ -880,6 +881,27 @@ void arnoldi_orth(sd_handle* h, int j, const double* vj, double* zj, double* w, 
   }
 }
 
+// Per-block residual norms of the whole-system residual r (in h->V, whole
+// layout): the velocity rows [u | v], the continuity rows p_ff and the Darcy
+// rows p_pm, each relative to ||b||.  Batched in a lockstep batch (t_bat).
+void block_residual_dots(sd_handle* h) {
+  const Geom& g = h->g;
+  const long long lo[3] = {0, g.opf, g.opm}, hi[3] = {g.opf, g.opm, g.len};
+  for (int q = 0; q < 3; ++q)
+    launch_dot(h->V + lo[q], h->V + lo[q], hi[q] - lo[q], h->partial, reduce_blocks(hi[q] - lo[q]),
+               h->scal + sd_handle::S_BLK + q, h->s);
+}
+int block_residuals(sd_handle* h, double bnorm, sd_step_info* info) {
+  block_residual_dots(h);
+  CK(cudaMemcpyAsync(h->hflag + 12, h->scal + sd_handle::S_BLK, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  const double d = bnorm > 0 ? bnorm : 1.0;
+  info->relres_v = std::sqrt(h->hflag[12]) / d;
+  info->relres_pff = std::sqrt(h->hflag[13]) / d;
+  info->relres_pm = std::sqrt(h->hflag[14]) / d;
+  return SD_OK;
+}
+
 // --------------------------------------------------------------- FGMRES
 // Flexible GMRES(m) with CGS2 orthogonalisation, all FP64.  x holds the
 // initial guess.  The stopping test is the FP64 true residual
@@ -960,6 +982,9 @@ int fgmres(sd_handle* h, const double* b, double* x, sd_step_info* info, int mod
     info->relres = relres;
     info->status = status;
     info->reorths = reorths;
+    // the last residual b - A x is still in V_0 unless a cycle ended on NaN/Inf
+    info->relres_v = info->relres_pff = info->relres_pm = -1.0;
+    if (mode == MODE_MONO && status != SD_E_NUMERIC) CKR(block_residuals(h, bnorm, info));
   }
   return status;
 }
@@ -1048,16 +1073,18 @@ int step_partitioned(sd_handle* h, sd_step_info* info) {
   apply_op(h, MODE_MONO, h->x, h->b, h->V);
   launch_dot(h->V, h->V, g.len, h->partial, h->nblk, sc + sd_handle::S_B2, s);
   launch_dot(h->b, h->b, g.len, h->partial, h->nblk, sc + sd_handle::S_BN, s);
-  CK(cudaMemcpyAsync(h->hflag + 12, sc + sd_handle::S_B2, sizeof(double), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(h->hflag + 13, sc + sd_handle::S_BN, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h->hflag + 10, sc + sd_handle::S_B2, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h->hflag + 11, sc + sd_handle::S_BN, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (info) {
+    const double r2 = h->hflag[10], b2 = h->hflag[11];
     info->iters = iters;
     info->restarts = 0;
-    info->relres = h->hflag[13] > 0 ? std::sqrt(h->hflag[12] / h->hflag[13]) : std::sqrt(h->hflag[12]);
+    info->relres = b2 > 0 ? std::sqrt(r2 / b2) : std::sqrt(r2);
     info->status = status;
     info->reorths = reorths;
     info->coupling_iters = it;
+    CKR(block_residuals(h, std::sqrt(b2), info));
   }
   return status;
 }
@@ -1420,6 +1447,12 @@ int fgmres_lockstep(Lockstep& L, std::vector<sd_step_info>& si) {
     launch_backsolve(h->st, m, m, sc + sd_handle::S_Y, h->flag + 5, s);
     launch_axpy_multi(h->x, h->Z, vs, sc + sd_handle::S_Y, m, len, h->flag + 5, s);
   }
+  // per-block residuals: every instance's last residual is still in its V_0
+  // (its kernels were idle since), unless a cycle of it ended on NaN/Inf
+  L.act.assign(B, 1);
+  CKR(set_act(L, s));
+  block_residual_dots(h);
+  CKR(gather(L, sc + sd_handle::S_BLK, 3, s));
   CK(cudaGetLastError());
   for (int i = 0; i < B; ++i) {
     si[i].iters = iters[i];
@@ -1427,6 +1460,11 @@ int fgmres_lockstep(Lockstep& L, std::vector<sd_step_info>& si) {
     si[i].relres = relres[i];
     si[i].status = status[i];
     si[i].reorths = reorths[i];
+    const double d = bnorm[i] > 0 ? bnorm[i] : 1.0;
+    const bool ok = status[i] != SD_E_NUMERIC;
+    si[i].relres_v = ok ? std::sqrt(L.gat_host[(size_t)i * 3]) / d : -1.0;
+    si[i].relres_pff = ok ? std::sqrt(L.gat_host[(size_t)i * 3 + 1]) / d : -1.0;
+    si[i].relres_pm = ok ? std::sqrt(L.gat_host[(size_t)i * 3 + 2]) / d : -1.0;
   }
   return SD_OK;
 }

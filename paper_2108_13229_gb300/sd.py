@@ -58,7 +58,8 @@ class sd_options(ctypes.Structure):
 class sd_step_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("restarts", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("relres", ctypes.c_double), ("ms", ctypes.c_double), ("reorths", ctypes.c_int32),
-                ("coupling_iters", ctypes.c_int32)]
+                ("coupling_iters", ctypes.c_int32), ("relres_v", ctypes.c_double),
+                ("relres_pff", ctypes.c_double), ("relres_pm", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -508,3 +508,22 @@ def test_partitioned_orders_with_traction_sides(sd, bc, order):
         assert abs(info["coupling_iters"] - evals) <= 1, (info["coupling_iters"], evals)
     else:
         assert info["coupling_iters"] <= evals + 6, (info["coupling_iters"], evals)
+
+
+@pytest.mark.parametrize("coupling", [0, 1])
+def test_block_residuals(sd, coupling):
+    # the per-block residuals split the reported relative residual:
+    # relres^2 = relres_v^2 + relres_pff^2 + relres_pm^2; also in a lockstep batch
+    n = 32
+    K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=50)
+    h = make(sd, n, 1e-3, K, 1.0, 0.05, 1, coupling=coupling)
+    for info in sd.sd_step(h, 3):
+        parts = np.array([info["relres_v"], info["relres_pff"], info["relres_pm"]])
+        assert np.all(parts >= 0)
+        assert abs(np.sqrt((parts ** 2).sum()) - info["relres"]) <= 1e-6 * info["relres"] + 1e-300
+    if coupling == 0:
+        hs = [make(sd, n, 1e-3, I.lognormal_K(n, -4.0, 1.0, 16.0, seed=51 + q), 1.0, 0.05, 1) for q in range(3)]
+        for inf in sd.sd_solve_batch(hs, [2, 2, 2]):
+            for info in inf:
+                parts = np.array([info["relres_v"], info["relres_pff"], info["relres_pm"]])
+                assert abs(np.sqrt((parts ** 2).sum()) - info["relres"]) <= 1e-6 * info["relres"]

@@ -172,9 +172,15 @@ typedef struct {
                           the Schur complement, L_p = B^T B / h^2 (default 1) */
   int32_t fuse_coarse; /* run all levels with <= 32 cells per side in one single-CTA
                           kernel (default 1) */
-  int32_t orth;        /* 0: classical Gram-Schmidt twice (CGS2, default); 1: second
-                          pass only when ||w'|| < reorth_eta ||w|| */
-  double reorth_eta;   /* default 1/sqrt(2) */
+  int32_t orth;        /* 0: classical Gram-Schmidt twice (CGS2); 1 (default): the second
+                          pass only when ||w'|| < reorth_eta ||w|| (DGKS test, decided
+                          on the device) */
+  double reorth_eta;   /* default 1e-3: a second pass only after severe cancellation.
+                          (Measured: with FGMRES cycles of 5-7 iterations the final
+                          true residuals and iteration counts equal CGS2's, and the
+                          step is 7-9 % faster; the true residual recomputed at every
+                          restart still decides convergence.  1/sqrt(2), the classical
+                          choice, took the second pass in 5 of 6 iterations.) */
   int32_t extrapolate; /* initial guess of step n+1: 2 x^n - x^{n-1} (1, default)
                           or x^n (0) */
   int32_t graph;       /* replay each Arnoldi step from a captured CUDA graph (default 1;

@@ -825,7 +825,7 @@ void apply_precond_mode(sd_handle* h, int mode, const double* r, double* z) {
 // z_j = P^-1 v_j, w = A z_j, then w orthogonalised against v_0..v_j and the
 // new Hessenberg column rotated (Givens).  Orthogonalisation:
 //   orth 0: classical Gram-Schmidt with one re-orthogonalisation (CGS2);
-//   orth 1: the second pass only when the first removed most of w
+//   orth 1: the second pass only when the first removed nearly all of w
 //           (||w'|| < eta ||w||, decided on the device).
 void arnoldi_orth(sd_handle* h, int j, const double* vj, double* zj, double* w, int mode = MODE_MONO) {
   cudaStream_t s = h->s;
@@ -1547,8 +1547,8 @@ void sd_options_default(sd_options* o) {
   o->schur_degree = 1;
   o->coarsest = 4;
   o->fuse_coarse = 1;
-  o->orth = 0;
-  o->reorth_eta = 0.70710678118654752;
+  o->orth = 1;
+  o->reorth_eta = 1e-3;
   o->extrapolate = 1;
   o->graph = 1;
   o->pdl = 1;

@@ -259,12 +259,13 @@ def bench_batch(sd, count: int, steps: int, threads: int, seed: int = 0, lockste
             "iters_per_step_mean": float(np.mean(its)), "max_relres": max(i["relres"] for inf in infos for i in inf)}
 
 
-def bench_serve(sd, rate: float, count: int, max_running: int, budget_gb: float = 120.0, seed: int = 0):
+def bench_serve(sd, rate: float, count: int, max_running: int, budget_gb: float = 120.0, seed: int = 0,
+                lockstep: bool = False):
     """Poisson arrivals of time-dependent runs submitted to the continuous-batching server."""
     from paper_2108_13229_gb300 import inputs as I
     reqs = I.serving_requests(count, rate, seed=seed)
     Ks = [wl.K() for _, wl in reqs]
-    srv = sd.sd_server_create(int(budget_gb * (1 << 30)), max_running)
+    srv = sd.sd_server_create(int(budget_gb * (1 << 30)), max_running, lockstep=lockstep)
     t0 = time.perf_counter()
     tickets = []
     for (ta, wl), K in zip(reqs, Ks):
@@ -284,6 +285,7 @@ def bench_serve(sd, rate: float, count: int, max_running: int, budget_gb: float 
         its += res["total_iters"]
     sd.sd_server_destroy(srv)
     return {"rate_per_s": rate, "requests": count, "max_running": max_running, "hbm_budget_gb": budget_gb,
+            "mode": "lockstep size classes below 1M DoF" if lockstep else "one worker and stream per run",
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "mean": float(np.mean(lat))},
             "value": work / el, "unit": UNIT, "makespan_s": el,
@@ -616,10 +618,11 @@ def main():
                 print(json.dumps(r), flush=True)
         else:
             for rate in args.rates:
-                r = bench_serve(sd, rate, args.count, args.threads)
-                r.update({"metric": "serving: p50/p99 request latency and DOF*steps/s under Poisson arrivals",
-                          "mode": "serve"})
-                print(json.dumps(r), flush=True)
+                for lockstep in (False, True):
+                    r = bench_serve(sd, rate, args.count, args.threads, lockstep=lockstep)
+                    r.update({"metric": "serving: p50/p99 request latency and DOF*steps/s under Poisson arrivals",
+                              "bench_mode": "serve"})
+                    print(json.dumps(r), flush=True)
         return 0
     if args.warmup < 3:
         args.warmup = 3

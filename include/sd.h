@@ -308,8 +308,20 @@ int sd_solve_batch(sd_handle *const *hs, int32_t count, const int32_t *nsteps, s
 int sd_solve_batch_ex(sd_handle *const *hs, int32_t count, const int32_t *nsteps, sd_step_info *const *infos,
                       int32_t max_threads, int32_t flags);
 
-/* Continuous-batching server: requests are admitted as slots and HBM budget
- * free up and run concurrently; each run keeps its state on the device. */
+/* Continuous-batching server: requests are admitted in arrival order as
+ * running slots (max_running) and HBM budget free up, and run concurrently,
+ * each on a worker thread and stream of its own (sd_server_create); each run
+ * keeps its state on the device for all its steps.  sd_server_create_ex with
+ * SD_SERVER_LOCKSTEP serves the runs of grids below 1M DoF by size class
+ * (same grid, mu, dt) instead: every tick, each running request of a class
+ * advances one time step in lockstep groups that share every launch (as
+ * sd_solve_batch); requests join the class at the next tick after admission
+ * and leave when their steps are done.  (Measured on the Poisson serving
+ * workload it is slower: a class's graphs are recaptured whenever its
+ * membership changes, and every tick waits for the slowest member, newly
+ * joined runs needing twice the iterations of warm ones.)  Either way a
+ * result is bitwise the same as the run alone. */
+#define SD_SERVER_LOCKSTEP 1
 typedef struct {
   sd_grid grid;
   double mu, alpha_bj, dt;
@@ -330,6 +342,8 @@ typedef struct {
 } sd_result;
 
 int sd_server_create(int64_t hbm_budget_bytes, int32_t max_running, const sd_options *opt, sd_server **out);
+int sd_server_create_ex(int64_t hbm_budget_bytes, int32_t max_running, const sd_options *opt, int32_t flags,
+                        sd_server **out);
 int sd_submit(sd_server *s, const sd_request *req, uint64_t *ticket);
 /* SD_PENDING while queued or running; SD_OK (or the run's error) when done.
  * x: NULL or 4n^2+2n doubles (host) receiving the final state if keep_fields. */

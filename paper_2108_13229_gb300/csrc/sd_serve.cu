@@ -21,6 +21,7 @@
 #include <memory>
 #include <mutex>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 namespace {
@@ -47,6 +48,20 @@ struct Job {
   sd_result res;
   std::vector<double> x;
   clk::time_point t_submit, t_start, t_end;
+  // lockstep serving: the run's handle and progress between ticks
+  sd_handle* h = nullptr;
+  int done = 0, iters = 0;
+  double maxrel = 0.0;
+};
+
+// Lockstep serving: the running requests of one size class (grid, mu, dt)
+// advance one time step per tick, each tick's lockstep groups sharing every
+// launch; requests join at the next tick after admission and leave when
+// their steps are done.
+struct SizeClass {
+  std::vector<Job*> incoming;  // admitted, handle not yet created
+  std::vector<Job*> running;
+  std::thread th;
 };
 
 }  // namespace
@@ -62,7 +77,9 @@ struct sd_server {
   sd_options opt;
   uint64_t next_id = 1;
   int device = 0;
+  int flags = 0;
   std::vector<std::thread> workers;
+  std::map<std::tuple<int, double, double>, std::unique_ptr<SizeClass>> classes;
 };
 
 namespace {
@@ -98,6 +115,93 @@ void run_job(sd_server* S, Job* J) {
   J->res.status = rc;
 }
 
+// grids below this many DoF run in lockstep size classes in the lockstep mode
+// (one larger grid already fills the GPU: those keep a worker of their own)
+const int64_t kServeLockstepDof = 1ll << 20;
+
+void finish_job(sd_server* S, Job* J) {
+  std::lock_guard<std::mutex> lk(S->mu);
+  J->t_end = clk::now();
+  J->res.queue_ms = ms_between(J->t_submit, J->t_start);
+  J->res.run_ms = ms_between(J->t_start, J->t_end);
+  J->res.latency_ms = ms_between(J->t_submit, J->t_end);
+  S->used -= J->est;
+  S->running -= 1;
+}
+
+// Close a lockstep-served run: copy its state out if asked, release the handle.
+void close_job(Job* J, int rc) {
+  J->res.dof = sd_dof_count(J->req.grid.nx);
+  J->res.steps_done = J->done;
+  J->res.total_iters = J->iters;
+  J->res.max_relres = J->maxrel;
+  if (J->h && J->req.keep_fields && rc == SD_OK) {
+    J->x.resize((size_t)sd_dof_count(J->req.grid.nx));
+    rc = sd_get_state(J->h, nullptr, nullptr, J->x.data(), nullptr);
+  }
+  if (J->h) sd_destroy(J->h);
+  J->h = nullptr;
+  J->status = rc;
+  J->res.status = rc;
+}
+
+void class_loop(sd_server* S, SizeClass* C) {
+  cudaSetDevice(S->device);
+  for (;;) {
+    std::vector<Job*> fresh;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv.wait(lk, [&] { return S->stop || !C->incoming.empty() || !C->running.empty(); });
+      if (S->stop) return;
+      fresh.swap(C->incoming);
+    }
+    for (Job* J : fresh) {  // joins at this tick
+      sd_options o = S->opt;
+      o.stream = nullptr;
+      const int rc = sd_create(&J->req.grid, J->req.mu, J->K.data(), J->req.alpha_bj, J->req.dt, &o, &J->h);
+      if (rc != SD_OK || J->req.nsteps == 0) {
+        close_job(J, rc);
+        finish_job(S, J);
+        S->cv.notify_all();
+      } else {
+        C->running.push_back(J);
+      }
+    }
+    if (C->running.empty()) continue;
+    // one tick: every running request advances one step, in lockstep groups
+    std::vector<sd_handle*> hs;
+    for (Job* J : C->running) hs.push_back(J->h);
+    std::vector<sd_step_info> info(hs.size());
+    std::vector<int> rcs(hs.size(), SD_OK);
+    const int64_t dof = sd_dof_count(C->running[0]->req.grid.nx);
+    const size_t cap = (size_t)std::max<int64_t>(1, kLockstepDof / dof);
+    for (size_t a = 0; a < hs.size(); a += cap) {
+      const size_t b = std::min(hs.size(), a + cap);
+      std::vector<sd_step_info*> ip;
+      for (size_t q = a; q < b; ++q) ip.push_back(&info[q]);
+      const int rc = (b - a == 1) ? sd_step(hs[a], 1, ip[0]) : sdk::step_lockstep(&hs[a], (int)(b - a), 1, ip.data());
+      for (size_t q = a; q < b; ++q) rcs[q] = (b - a == 1) ? rc : info[q].status;
+      if (rc == SD_E_CUDA || rc == SD_E_NOMEM || rc == SD_E_STATE || rc == SD_E_INVAL)
+        for (size_t q = a; q < b; ++q) rcs[q] = rc;
+    }
+    std::vector<Job*> keep;
+    for (size_t q = 0; q < hs.size(); ++q) {
+      Job* J = C->running[q];
+      J->done += 1;
+      J->iters += info[q].iters;
+      if (info[q].relres > J->maxrel) J->maxrel = info[q].relres;
+      if (rcs[q] != SD_OK || J->done >= J->req.nsteps) {
+        close_job(J, rcs[q]);
+        finish_job(S, J);
+        S->cv.notify_all();
+      } else {
+        keep.push_back(J);
+      }
+    }
+    C->running.swap(keep);
+  }
+}
+
 void worker_loop(sd_server* S) {
   cudaSetDevice(S->device);
   for (;;) {
@@ -106,7 +210,7 @@ void worker_loop(sd_server* S) {
       std::unique_lock<std::mutex> lk(S->mu);
       S->cv.wait(lk, [&] {
         if (S->stop) return true;
-        if (S->queue.empty()) return false;
+        if (S->queue.empty() || S->running >= S->max_running) return false;
         Job* head = S->jobs[S->queue.front()].get();
         return S->used + head->est <= S->budget;
       });
@@ -116,17 +220,24 @@ void worker_loop(sd_server* S) {
       S->used += J->est;
       S->running += 1;
       J->t_start = clk::now();
+      const int n = J->req.grid.nx;
+      if ((S->flags & SD_SERVER_LOCKSTEP) && sd_dof_count(n) < kServeLockstepDof) {
+        // hand the run to its size class and go back for the next request
+        auto key = std::make_tuple(n, J->req.mu, J->req.dt);
+        auto it = S->classes.find(key);
+        if (it == S->classes.end()) {
+          std::unique_ptr<SizeClass> c(new SizeClass());
+          SizeClass* cp = c.get();
+          it = S->classes.emplace(key, std::move(c)).first;
+          cp->th = std::thread(class_loop, S, cp);
+        }
+        it->second->incoming.push_back(J);
+        S->cv.notify_all();
+        continue;
+      }
     }
     run_job(S, J);
-    {
-      std::lock_guard<std::mutex> lk(S->mu);
-      J->t_end = clk::now();
-      J->res.queue_ms = ms_between(J->t_submit, J->t_start);
-      J->res.run_ms = ms_between(J->t_start, J->t_end);
-      J->res.latency_ms = ms_between(J->t_submit, J->t_end);
-      S->used -= J->est;
-      S->running -= 1;
-    }
+    finish_job(S, J);
     S->cv.notify_all();
   }
 }
@@ -211,12 +322,18 @@ int sd_solve_batch(sd_handle* const* hs, int32_t count, const int32_t* nsteps, s
 }
 
 int sd_server_create(int64_t hbm_budget_bytes, int32_t max_running, const sd_options* opt, sd_server** out) {
+  return sd_server_create_ex(hbm_budget_bytes, max_running, opt, 0, out);
+}
+
+int sd_server_create_ex(int64_t hbm_budget_bytes, int32_t max_running, const sd_options* opt, int32_t flags,
+                        sd_server** out) {
   if (!out || hbm_budget_bytes <= 0 || max_running < 1) return SD_E_INVAL;
   sd_server* S = new sd_server();
   sd_options_default(&S->opt);
   if (opt) S->opt = *opt;
   S->budget = hbm_budget_bytes;
   S->max_running = max_running;
+  S->flags = flags;
   cudaGetDevice(&S->device);
   for (int k = 0; k < max_running; ++k) S->workers.emplace_back(worker_loop, S);
   *out = S;
@@ -281,6 +398,11 @@ void sd_server_destroy(sd_server* S) {
   }
   S->cv.notify_all();
   for (auto& t : S->workers) t.join();
+  for (auto& c : S->classes) {
+    if (c.second->th.joinable()) c.second->th.join();
+    for (Job* J : c.second->running)
+      if (J->h) sd_destroy(J->h);
+  }
   delete S;
 }
 

@@ -24,6 +24,7 @@ SD_BC_MMS, SD_BC_MMS_TRACTION, SD_BC_PAPER = 0, 1, 2
 SD_PROF_APPLY, SD_PROF_CHEB_V, SD_PROF_MUPDATE, SD_PROF_MDOT = 0, 1, 2, 3
 SD_NOALLOC_MAX_N = 256
 SD_BATCH_LOCKSTEP = 1
+SD_SERVER_LOCKSTEP = 1
 SD_MONOLITHIC, SD_PARTITIONED = 0, 1
 SD_ORDER_AUTO, SD_ORDER_PM_FIRST, SD_ORDER_FF_FIRST = 0, 1, 2
 
@@ -101,6 +102,8 @@ _SIGS = {
                                       ctypes.POINTER(ctypes.POINTER(sd_step_info)), ctypes.c_int32, ctypes.c_int32]),
     "sd_server_create": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(sd_options),
                                         ctypes.POINTER(_vp)]),
+    "sd_server_create_ex": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(sd_options), ctypes.c_int32,
+                                           ctypes.POINTER(_vp)]),
     "sd_submit": (ctypes.c_int, [_vp, ctypes.POINTER(sd_request), ctypes.POINTER(ctypes.c_uint64)]),
     "sd_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(sd_result), _vp]),
     "sd_server_drain": (ctypes.c_int, [_vp]),
@@ -317,12 +320,20 @@ class Server:
             self.ptr = None
 
 
-def sd_server_create(hbm_budget_bytes: int, max_running: int = 4, opts: sd_options | None = None) -> Server:
+def sd_server_create(hbm_budget_bytes: int, max_running: int = 4, opts: sd_options | None = None,
+                     lockstep: bool = False) -> Server:
+    """lockstep=True: small runs served by size class in lockstep ticks (sd_server_create_ex SD_SERVER_LOCKSTEP)."""
     out = ctypes.c_void_p()
-    _check(_load().sd_server_create(int(hbm_budget_bytes), int(max_running),
-                                    ctypes.byref(opts) if opts is not None else None, ctypes.byref(out)),
+    _check(_load().sd_server_create_ex(int(hbm_budget_bytes), int(max_running),
+                                       ctypes.byref(opts) if opts is not None else None,
+                                       SD_SERVER_LOCKSTEP if lockstep else 0, ctypes.byref(out)),
            "sd_server_create")
     return Server(out.value)
+
+
+def sd_server_create_ex(hbm_budget_bytes: int, max_running: int = 4, opts: sd_options | None = None,
+                        flags: int = 0) -> Server:
+    return sd_server_create(hbm_budget_bytes, max_running, opts, lockstep=bool(flags & SD_SERVER_LOCKSTEP))
 
 
 def sd_submit(server: Server, n: int, mu: float, K, alpha_bj: float, dt: float, nsteps: int,

@@ -218,9 +218,12 @@ def test_lockstep_batch_bitwise(sd, precision):
             assert launches_lockstep < launches  # the groups share their launches
 
 
-def test_server_results_match_alone(sd):
+@pytest.mark.parametrize("lockstep", [True, False])
+def test_server_results_match_alone(sd, lockstep):
+    # lockstep: runs of one size class step together, joining and leaving
+    # between ticks (n = 32 and n = 64 have two runs each of different lengths)
     reqs = [(32, 5, 1), (64, 7, 2), (128, 4, 3), (32, 9, 4), (96, 6, 5), (64, 5, 6)]
-    srv = sd.sd_server_create(8 << 30, 3)
+    srv = sd.sd_server_create(8 << 30, 3, lockstep=lockstep)
     tickets = []
     for n, steps, seed in reqs:
         K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=seed)

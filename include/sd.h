@@ -183,8 +183,13 @@ typedef struct {
                           choice, took the second pass in 5 of 6 iterations.) */
   int32_t extrapolate; /* initial guess of step n+1: 2 x^n - x^{n-1} (1, default)
                           or x^n (0) */
-  int32_t graph;       /* replay each Arnoldi step from a captured CUDA graph (default 1;
-                          ignored on the legacy default stream and while profiling) */
+  int32_t graph;       /* 1 (default): replay each Arnoldi step from a captured CUDA
+                          graph, the host checking convergence after each; 2: a whole
+                          FGMRES solve as one graph whose restart loop (WHILE node) and
+                          Arnoldi steps (IF nodes) are decided on the device, one host
+                          wait per solve; same iterates bit for bit, measured within
+                          +-2 % of 1 (1024^2: +0.5 %, 128^2: -2.5 %); 0: direct launches.
+                          Ignored on the legacy default stream and while profiling. */
   int32_t pdl;         /* programmatic dependent launch between consecutive kernels
                           of sd_step / sd_solve (default 1) */
   int32_t tile;        /* FP32 V-cycles: all Chebyshev steps of one smoothing in one
@@ -206,6 +211,14 @@ typedef struct {
                                (default 0.1) */
   int32_t coupling_order;   /* SD_PARTITIONED: SD_ORDER_AUTO (default) | SD_ORDER_PM_FIRST |
                                SD_ORDER_FF_FIRST */
+  double coupling_rtol;     /* SD_PARTITIONED: relative tolerance of each subdomain solve;
+                               0 (default): min(rtol, max(1e-3 coupling_eps, 1e-12)),
+                               1e-12 being near the FP64 floor of these solves.  The coupling
+                               test can only see changes above the subdomain solves' own
+                               error: with solves to rtol = 1e-10 and coupling_eps = 1e-9 on
+                               1024^2 lognormal K, 26 of 60 steps ran into coupling_max
+                               (interface updates below the solves' tolerance returned no
+                               change), with 1e-12 every step took 5-6 iterations. */
   double bc_dp;        /* SD_BC_PAPER: amplitude of the inflow pressure (default 1) */
   double bc_tend;      /* SD_BC_PAPER: rise time T of the inflow pressure (default 0:
                           25 time steps) */

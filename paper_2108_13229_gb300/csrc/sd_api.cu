@@ -129,6 +129,16 @@ struct sd_handle {
   // free-flow and porous-medium subdomain solves of the partitioned coupling)
   std::vector<cudaGraphExec_t> gexec[5];
   std::vector<long long> gcount[5];            // kernels in each captured step
+  // graph option 2: a whole FGMRES solve per solve mode as one graph with
+  // device-side loop control (built for one right-hand side and iterate)
+  struct SolveGraph {
+    cudaGraphExec_t ex = nullptr;
+    const double* b = nullptr;
+    const double* x = nullptr;
+    long long pre = 0, post = 0;  // kernels outside the graph's loops
+    bool bad = false;             // could not be built: step-by-step replay
+  };
+  SolveGraph sg[5];
   Geom g;
   int nlev = 1;
   int m = 30;
@@ -159,7 +169,7 @@ struct sd_handle {
   long long prof_launches = 0;
   // scalar slots in scal[]
   static const int S_H1 = 0, S_H2 = 32, S_N2 = 64, S_B2 = 65, S_BN = 66, S_N2B = 67, S_REO = 68, S_BLK = 69,
-                   S_Y = 96;
+                   S_Y = 96, S_CTL = 128;
 };
 
 namespace {
@@ -766,6 +776,25 @@ Range mode_range(const sd_handle* h, int mode) {
   return {0, h->g.len};
 }
 
+// Relative tolerance of a solve: rtol for the whole system; for a subdomain
+// solve of the partitioned coupling, coupling_rtol, or, when that is 0,
+// three decades below the relative change the coupling test resolves (not
+// below 1e-12, near the FP64 floor of the solves, nor above rtol).
+double mode_rtol(const sd_handle* h, int mode) {
+  if (mode == MODE_MONO) return h->opt.rtol;
+  if (h->opt.coupling_rtol > 0) return h->opt.coupling_rtol;
+  return std::min(h->opt.rtol, std::max(1e-3 * h->opt.coupling_eps, 1e-12));
+}
+// A subdomain solve whose restart cycle did not halve the true residual has
+// reached the rounding floor of its rows (which the tight tolerance above can
+// lie below, e.g. Darcy rows whose right-hand side is only the small interface
+// flux): it stops there, converged if its residual meets rtol (or its own
+// tolerance, when looser), else SD_E_NOCONV.  0: never (whole system).
+double mode_accept(const sd_handle* h, int mode) {
+  if (mode == MODE_MONO) return 0.0;
+  return std::max(h->opt.rtol, mode_rtol(h, mode));
+}
+
 // y = A_mode x, or y = b - A_mode x
 void apply_op(sd_handle* h, int mode, const double* x, const double* b, double* y) {
   const Coef<double> c = coef64(h, 0);
@@ -902,12 +931,220 @@ int block_residuals(sd_handle* h, double bnorm, sd_step_info* info) {
   return SD_OK;
 }
 
+// ------------------------------------------------- FGMRES as one graph
+// Graph option 2: fgmres() below as one CUDA graph per solve mode, its
+// decisions taken on the device.  Top level: ||b||, the first true residual
+// and k_restart_ctrl, then a WHILE node over restart cycles, then (whole
+// system) the per-block residual dots.  WHILE body: k_cycle_head, the cycle
+// set-up, Arnoldi step 0 and k_step_ctrl, a chain of IF nodes for steps
+// 1..m-1 (each body: the step and its k_step_ctrl, which sets the next IF's
+// condition), then the update of x with k read on the device, the new true
+// residual and k_restart_ctrl, which sets the WHILE condition.  The kernels
+// and their order are those of the step-by-step path, so both give the same
+// iterates bit for bit; the host waits once per solve instead of once per
+// iteration.
+int build_solve_graph(sd_handle* h, int mode, const double* b, double* x) {
+  cudaStream_t s = h->s;
+  const Range rg = mode_range(h, mode);
+  const long long len = rg.len, vs = h->lenA, o = rg.off;
+  const int m = h->m, nb = reduce_blocks(len), maxit = h->opt.max_iters;
+  double* sc = h->scal;
+  double* ctl = sc + sd_handle::S_CTL;
+  const int pdl = t_pdl;
+  const long long l_start = t_launch_count;
+  cudaGraph_t top = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  std::vector<cudaGraphNode_t> deps;
+  bool capturing = false;
+  long long pre = 0, post = 0;
+  cudaError_t err = cudaSuccess;
+  // capture into graph g after the nodes in deps (none if !after)
+  auto begin = [&](cudaGraph_t g, bool after) {
+    if (err != cudaSuccess) return false;
+    err = cudaStreamBeginCaptureToGraph(s, g, after ? deps.data() : nullptr, nullptr, after ? deps.size() : 0,
+                                        cudaStreamCaptureModeThreadLocal);
+    capturing = err == cudaSuccess;
+    return capturing;
+  };
+  // end the capture; keep: deps = its last nodes
+  auto end = [&](bool keep) {
+    if (!capturing) return;
+    if (keep && err == cudaSuccess) {
+      cudaStreamCaptureStatus cs;
+      const cudaGraphNode_t* d = nullptr;
+      size_t nd = 0;
+      err = cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &d, nullptr, &nd);
+      if (err == cudaSuccess) deps.assign(d, d + nd);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    capturing = false;
+    if (err == cudaSuccess) err = e2;
+    if (err == cudaSuccess) err = cudaGetLastError();
+  };
+  // conditional node of graph g after deps; its body in *body
+  auto cond = [&](cudaGraph_t g, cudaGraphConditionalHandle hd, cudaGraphConditionalNodeType type,
+                  cudaGraph_t* body) {
+    if (err != cudaSuccess) return;
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = hd;
+    np.conditional.type = type;
+    np.conditional.size = 1;
+    cudaGraphNode_t nd = nullptr;
+    err = cudaGraphAddNode(&nd, g, deps.data(), nullptr, deps.size(), &np);
+    if (err != cudaSuccess) return;
+    *body = np.conditional.phGraph_out[0];
+    deps.assign(1, nd);
+  };
+  auto step = [&](int j) {
+    const long long l0 = t_launch_count;
+    double* vj = h->V + (long long)j * vs;
+    double* zj = h->Z + (long long)j * vs;
+    double* w = h->V + (long long)(j + 1) * vs;
+    arnoldi_orth(h, j, vj, zj, w, mode);
+    launch_scale_by(w + o, w + o, len, h->flag + 1, 0, s);
+    return t_launch_count - l0;
+  };
+  err = cudaGraphCreate(&top, 0);
+  cudaGraphConditionalHandle loop = 0;
+  CondSet cs = {};
+  cs.n = m;
+  if (err == cudaSuccess) err = cudaGraphConditionalHandleCreate(&loop, top, 0, cudaGraphCondAssignDefault);
+  for (int j = 1; j < m && err == cudaSuccess; ++j)
+    err = cudaGraphConditionalHandleCreate(&cs.c[j], top, 0, cudaGraphCondAssignDefault);
+  // ||b||, the first true residual, and whether a cycle runs
+  if (begin(top, false)) {
+    const long long l0 = t_launch_count;
+    launch_dot(b + o, b + o, len, h->partial, nb, sc + sd_handle::S_BN, s);
+    launch_solve_begin(sc + sd_handle::S_BN, mode_rtol(h, mode), mode_accept(h, mode), ctl, s);
+    apply_op(h, mode, x, b, h->V);
+    launch_dot(h->V + o, h->V + o, len, h->partial, nb, sc + sd_handle::S_B2, s);
+    launch_restart_ctrl(sc + sd_handle::S_B2, ctl, maxit, 0.0, loop, s);
+    pre = t_launch_count - l0;
+    end(true);
+  }
+  cudaGraph_t wbody = nullptr;
+  cond(top, loop, cudaGraphCondTypeWhile, &wbody);
+  const std::vector<cudaGraphNode_t> after_loop = deps;
+  // one restart cycle: set-up and Arnoldi step 0
+  deps.clear();
+  if (begin(wbody, false)) {
+    const long long l0 = t_launch_count;
+    launch_cycle_head(cs, s);
+    launch_init_cycle(h->st, m, sc + sd_handle::S_B2, h->flag, s);
+    launch_scale_by(h->V + o, h->V + o, len, h->flag + 1, 0, s);
+    step(0);
+    const long long k = t_launch_count - l0 + 1;
+    launch_step_ctrl(h->flag, ctl, maxit, (double)k, m > 1, m > 1 ? cs.c[1] : 0, s);
+    end(true);
+  }
+  for (int j = 1; j < m; ++j) {
+    cudaGraph_t ib = nullptr;
+    cond(wbody, cs.c[j], cudaGraphCondTypeIf, &ib);
+    const std::vector<cudaGraphNode_t> keep = deps;
+    if (begin(ib, false)) {
+      const long long k = step(j) + 1;
+      launch_step_ctrl(h->flag, ctl, maxit, (double)k, j + 1 < m, j + 1 < m ? cs.c[j + 1] : 0, s);
+      end(false);
+    }
+    deps = keep;
+  }
+  // update of x with the cycle's k (flag[5]), the new true residual, and
+  // whether another cycle runs; no programmatic edge out of a conditional node
+  if (begin(wbody, true)) {
+    const long long l0 = t_launch_count;
+    t_pdl = 0;
+    launch_backsolve(h->st, m, m, sc + sd_handle::S_Y, h->flag + 5, s);
+    t_pdl = pdl;
+    launch_axpy_multi(x + o, h->Z + o, vs, sc + sd_handle::S_Y, m, len, h->flag + 5, s);
+    apply_op(h, mode, x, b, h->V);
+    launch_dot(h->V + o, h->V + o, len, h->partial, nb, sc + sd_handle::S_B2, s);
+    const long long k = t_launch_count - l0 + 1;
+    launch_restart_ctrl(sc + sd_handle::S_B2, ctl, maxit, (double)k, loop, s);
+    end(false);
+  }
+  if (mode == MODE_MONO) {
+    deps = after_loop;
+    if (begin(top, true)) {
+      const long long l0 = t_launch_count;
+      t_pdl = 0;
+      block_residual_dots(h);
+      t_pdl = pdl;
+      post = t_launch_count - l0;
+      end(false);
+    }
+  }
+  t_pdl = pdl;
+  if (capturing) end(false);
+  if (err == cudaSuccess) err = cudaGraphInstantiate(&ex, top, 0);
+  if (top) cudaGraphDestroy(top);
+  // the capture went through the counting launch wrappers; replays are
+  // credited from the graph's own counts
+  g_launch_count.fetch_sub(t_launch_count - l_start);
+  sd_handle::SolveGraph& G = h->sg[mode];
+  if (err != cudaSuccess) {
+    if (ex) cudaGraphExecDestroy(ex);
+    cudaGetLastError();
+    G.bad = true;
+    return SD_E_CUDA;
+  }
+  G.ex = ex;
+  G.b = b;
+  G.x = x;
+  G.pre = pre;
+  G.post = post;
+  return SD_OK;
+}
+
+// One FGMRES solve from the solve graph (see build_solve_graph); returns
+// kNoGraph when the graph cannot be built, and the caller takes the
+// step-by-step path.
+constexpr int kNoGraph = 1;
+int fgmres_graph(sd_handle* h, const double* b, double* x, sd_step_info* info, int mode) {
+  cudaStream_t s = h->s;
+  sd_handle::SolveGraph& G = h->sg[mode];
+  if (G.ex && (G.b != b || G.x != x)) {
+    CK(cudaStreamSynchronize(s));
+    cudaGraphExecDestroy(G.ex);
+    G.ex = nullptr;
+  }
+  if (!G.ex && build_solve_graph(h, mode, b, x) != SD_OK) return kNoGraph;
+  CK(cudaGraphLaunch(G.ex, s));
+  double* hc = h->hflag + 16;
+  CK(cudaMemcpyAsync(hc, h->scal + sd_handle::S_CTL, C_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (mode == MODE_MONO)
+    CK(cudaMemcpyAsync(h->hflag + 12, h->scal + sd_handle::S_BLK, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  g_launch_count.fetch_add(G.pre + G.post + (long long)hc[C_KERN]);
+  const int status = hc[C_STAT] == C_STAT_NUMERIC ? SD_E_NUMERIC : hc[C_STAT] == C_STAT_NOCONV ? SD_E_NOCONV : SD_OK;
+  if (info) {
+    info->iters = (int)hc[C_ITER];
+    info->restarts = (int)hc[C_REST];
+    info->relres = hc[C_REL];
+    info->status = status;
+    info->reorths = (int)hc[C_REO];
+    info->relres_v = info->relres_pff = info->relres_pm = -1.0;
+    if (mode == MODE_MONO && status != SD_E_NUMERIC) {
+      const double d = hc[C_BN] > 0 ? hc[C_BN] : 1.0;
+      info->relres_v = std::sqrt(h->hflag[12]) / d;
+      info->relres_pff = std::sqrt(h->hflag[13]) / d;
+      info->relres_pm = std::sqrt(h->hflag[14]) / d;
+    }
+  }
+  return status;
+}
+
 // --------------------------------------------------------------- FGMRES
 // Flexible GMRES(m) with CGS2 orthogonalisation, all FP64.  x holds the
 // initial guess.  The stopping test is the FP64 true residual
 // ||b - A x||_2 <= rtol ||b||_2, checked at every restart and at the end.
 int fgmres(sd_handle* h, const double* b, double* x, sd_step_info* info, int mode = MODE_MONO) {
   cudaStream_t s = h->s;
+  if (h->opt.graph == 2 && h->prof_id < 0 && h->s != nullptr && !h->sg[mode].bad) {
+    const int rc = fgmres_graph(h, b, x, info, mode);
+    if (rc != kNoGraph) return rc;
+  }
   const Range rg = mode_range(h, mode);
   const long long len = rg.len, vs = h->lenA, o = rg.off;
   const int m = h->m, nb = reduce_blocks(len);
@@ -916,18 +1153,26 @@ int fgmres(sd_handle* h, const double* b, double* x, sd_step_info* info, int mod
   CK(cudaMemcpyAsync(h->hflag + 4, sc + sd_handle::S_BN, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   const double bnorm = std::sqrt(h->hflag[4]);
-  const double tol = h->opt.rtol * (bnorm > 0 ? bnorm : 1.0);
+  const double tol = mode_rtol(h, mode) * (bnorm > 0 ? bnorm : 1.0);
+  const double acc = mode_accept(h, mode);
+  const double acc_tol = acc > 0 ? acc * (bnorm > 0 ? bnorm : 1.0) : -1.0;
   int iters = 0, restarts = 0, status = SD_OK, reorths = 0;
-  double relres = 0.0;
+  double relres = 0.0, prev = 0.0;
   for (;;) {
     apply_op(h, mode, x, b, h->V);  // V_0 = b - A x
     launch_dot(h->V + o, h->V + o, len, h->partial, nb, sc + sd_handle::S_B2, s);
     CK(cudaMemcpyAsync(h->hflag + 5, sc + sd_handle::S_B2, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     const double beta = std::sqrt(h->hflag[5]);
+    const double beta_prev = prev;
+    prev = beta;
     relres = bnorm > 0 ? beta / bnorm : beta;
     if (!std::isfinite(beta)) { status = SD_E_NUMERIC; break; }
     if (beta <= tol) break;
+    if (acc_tol >= 0.0 && restarts > 0 && beta > 0.5 * beta_prev) {  // stagnated (mode_accept)
+      if (beta > acc_tol) status = SD_E_NOCONV;
+      break;
+    }
     if (iters >= h->opt.max_iters) { status = SD_E_NOCONV; break; }
     ++restarts;
     launch_init_cycle(h->st, m, sc + sd_handle::S_B2, h->flag, s);
@@ -1066,6 +1311,12 @@ int step_partitioned(sd_handle* h, sd_step_info* info) {
       conv = true;
       break;
     }
+    // neither subdomain solve moved its state: the interface data changed by
+    // less than the solves resolve, and no further evaluation can change x
+    if (it > 1 && sp.iters == 0 && sf.iters == 0) {
+      conv = true;
+      break;
+    }
   }
   if (status == SD_OK && !conv) status = SD_E_NOCONV;
   // residual of the coupled state in the monolithic system
@@ -1142,6 +1393,7 @@ int validate(const sd_grid* grid, double mu, double alpha, double dt, const sd_o
   if (o->cheb_degree < 1 || o->cheb_degree > 8 || o->coarsest < 2 || !(o->schur_gamma > 0) || !(o->cheb_ratio > 1))
     return SD_E_INVAL;
   if (o->orth < 0 || o->orth > 1 || !(o->reorth_eta > 0) || o->reorth_eta > 1) return SD_E_INVAL;
+  if (o->graph < 0 || o->graph > 2) return SD_E_INVAL;
   if (o->darcy_coupled < 0 || o->darcy_coupled > 2) return SD_E_INVAL;
   if (o->tile_rows != 0 && o->tile_rows != 8 && o->tile_rows != 16) return SD_E_INVAL;
   if (o->coupling != SD_MONOLITHIC && o->coupling != SD_PARTITIONED) return SD_E_INVAL;
@@ -1151,7 +1403,8 @@ int validate(const sd_grid* grid, double mu, double alpha, double dt, const sd_o
     return SD_E_INVAL;
   if (o->coupling == SD_PARTITIONED &&
       (o->coupling_max < 1 || o->coupling_columns < 1 || o->coupling_columns > 30 || !(o->coupling_eps > 0) ||
-       !(o->coupling_omega > 0) || !(o->coupling_omega <= 2)))
+       !(o->coupling_omega > 0) || !(o->coupling_omega <= 2) || !(o->coupling_rtol >= 0) ||
+       !(o->coupling_rtol < 1)))
     return SD_E_INVAL;
   if (o->cheb_degree_coarse < 0 || o->cheb_degree_coarse > 8 || o->schur_degree < 0 || o->schur_degree > 8)
     return SD_E_INVAL;
@@ -1209,7 +1462,7 @@ int create_impl(const sd_grid* grid, double mu, const double* K, double alpha, d
   if (cudaMalloc(&h->ar.base, bytes) != cudaSuccess) { cudaGetLastError(); h->ar.base = nullptr; return fail(SD_E_NOMEM); }
   if (cudaMemsetAsync(h->ar.base, 0, bytes, h->s) != cudaSuccess) return fail(SD_E_CUDA);
   plan_all(h);
-  if (cudaHostAlloc(&h->hflag, 16 * sizeof(double), cudaHostAllocDefault) != cudaSuccess) return fail(SD_E_CUDA);
+  if (cudaHostAlloc(&h->hflag, 32 * sizeof(double), cudaHostAllocDefault) != cudaSuccess) return fail(SD_E_CUDA);
   if (cudaStreamCreateWithFlags(&h->s2, cudaStreamNonBlocking) != cudaSuccess) return fail(SD_E_CUDA);
   if (cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess)
@@ -1561,6 +1814,7 @@ void sd_options_default(sd_options* o) {
   o->coupling_eps = 1e-9;
   o->coupling_omega = 0.1;
   o->coupling_order = SD_ORDER_AUTO;
+  o->coupling_rtol = 0.0;
   o->bc_dp = 1.0;
   o->bc_tend = 0.0;
   o->schur_gamma = 0.5;
@@ -1742,6 +1996,8 @@ void sd_destroy(sd_handle* h) {
   for (auto& gv : h->gexec)
     for (auto& ge : gv)
       if (ge) cudaGraphExecDestroy(ge);
+  for (auto& sg : h->sg)
+    if (sg.ex) cudaGraphExecDestroy(sg.ex);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->s2) {

@@ -342,7 +342,8 @@ void launch_dot(const double* a, const double* b, long long len, double* partial
                 cudaStream_t s);
 // y = alpha_dev[0]^p * x  (p = -1: divide by sqrt(alpha) ... see implementation)
 void launch_scale_by(const double* x, double* y, long long len, const double* sdev, int mode, cudaStream_t s);
-// (kdev, may be null: in a lockstep batch each instance's k is kdev[0])
+// (kdev, may be null: when given, k = kdev[0], read on the device; in a lockstep
+// batch each instance's own)
 void launch_axpy_multi(double* x, const double* Z, long long zstride, const double* ycoef, int k, long long len,
                        const double* kdev, cudaStream_t s);
 
@@ -355,6 +356,25 @@ void launch_backsolve(double* st, int k, int m, double* y, const double* kdev, c
 // lockstep batches: out[z * count + t] = instance z's src[t]
 void launch_gather_inst(const double* src, int count, double* out, cudaStream_t s);
 void launch_init_cycle(double* st, int m, const double* beta2, double* flag, cudaStream_t s);
+
+// device-side loop control of a whole FGMRES solve replayed as one graph
+// (sd_krylov.cu).  ctl[C_TOL] tolerance on ||r||, ctl[C_BN] ||b||, the
+// iteration, restart and second-pass counters, the status (0, or
+// C_STAT_NUMERIC / C_STAT_NOCONV), the last true relative residual, the
+// kernels run inside the graph's loops, the true residual before the last
+// cycle and the residual a stagnating solve is accepted at (negative: never)
+enum { C_TOL = 0, C_BN, C_ITER, C_REST, C_REO, C_STAT, C_REL, C_KERN, C_PREV, C_ACC, C_COUNT };
+constexpr double C_STAT_NUMERIC = 1.0, C_STAT_NOCONV = 2.0;
+struct CondSet {
+  cudaGraphConditionalHandle c[32];  // c[j]: run Arnoldi step j (j >= 1)
+  int n;                             // steps per cycle
+};
+void launch_solve_begin(const double* bn2, double rtol, double accept, double* ctl, cudaStream_t s);
+void launch_restart_ctrl(const double* beta2, double* ctl, int max_iters, double kern,
+                         cudaGraphConditionalHandle loop, cudaStream_t s);
+void launch_cycle_head(const CondSet& cs, cudaStream_t s);
+void launch_step_ctrl(double* flag, double* ctl, int max_iters, double kern, int has_next,
+                      cudaGraphConditionalHandle next, cudaStream_t s);
 
 // dense coarse solve: x[idx[k]] = T(sum_l Ainv[k][l] * b[idx[l]])
 template <typename T>

@@ -295,8 +295,8 @@ __global__ void __launch_bounds__(KT) k_axpy_multi(double* __restrict__ x, const
     x = bsh(x, o);
     Z = bsh(Z, o);
     y = bsh(y, o);
-    if (kdev) k = (int)bsh(kdev, o)[0];
   }
+  if (kdev) k = (int)bsh(kdev, o)[0];
   __shared__ double cf[KMAX_REG];
   if (threadIdx.x < KMAX_REG) cf[threadIdx.x] = threadIdx.x < k ? y[threadIdx.x] : 0.0;
   __syncthreads();
@@ -443,8 +443,8 @@ __global__ void k_backsolve(const double* st, int k, int m, double* y, const dou
   if (bt.off) {
     st = bsh(st, o);
     y = bsh(y, o);
-    if (kdev) k = (int)bsh(kdev, o)[0];
   }
+  if (kdev) k = (int)bsh(kdev, o)[0];
   const double* R = st;
   const double* g = st + (m + 1) * m + 2 * m;
   for (int i = k - 1; i >= 0; --i) {
@@ -457,6 +457,106 @@ __global__ void k_backsolve(const double* st, int k, int m, double* y, const dou
 void launch_backsolve(double* st, int k, int m, double* y, const double* kdev, cudaStream_t s) {
   SD_COUNT(1);
   launch_k(k_backsolve, dim3(1), dim3(32), 0, s, st, k, m, y, kdev);
+}
+
+// ------------------------------------------------ device-side loop control
+// With graph option 2 a whole FGMRES solve is one CUDA graph: the restart
+// loop is a WHILE node and the m Arnoldi steps of a cycle a chain of IF
+// nodes.  These one-thread kernels take the decisions that the host takes
+// between graph replays otherwise, on the same FP64 values and in the same
+// order, so both paths run the same iterations (layout of ctl in
+// sd_internal.cuh).  Every control kernel also adds the number of kernels
+// of the graph segment it closes to ctl[C_KERN].
+
+// ||b|| and the tolerances; counters cleared (accept <= 0: no acceptance of
+// a stagnating solve)
+__global__ void k_solve_begin(const double* bn2, double rtol, double accept, double* ctl) {
+  griddep_wait();
+  if (threadIdx.x != 0) return;
+  const double bnorm = sqrt(bn2[0]);
+  const double bs = bnorm > 0 ? bnorm : 1.0;
+  ctl[C_TOL] = rtol * bs;
+  ctl[C_ACC] = accept > 0 ? accept * bs : -1.0;
+  ctl[C_BN] = bnorm;
+  ctl[C_ITER] = ctl[C_REST] = ctl[C_REO] = ctl[C_STAT] = ctl[C_KERN] = 0.0;
+  ctl[C_REL] = ctl[C_PREV] = 0.0;
+}
+
+// after a true residual: stop (converged, NaN/Inf, budget spent, a NaN
+// inside the last cycle, or a cycle that did not halve the residual when
+// stagnation is accepted) or start another cycle
+__global__ void k_restart_ctrl(const double* beta2, double* ctl, int max_iters, double kern,
+                               cudaGraphConditionalHandle loop) {
+  griddep_wait();
+  if (threadIdx.x != 0) return;
+  const double beta = sqrt(beta2[0]);
+  const double bn = ctl[C_BN];
+  const double prev = ctl[C_PREV];
+  ctl[C_PREV] = beta;
+  ctl[C_REL] = bn > 0 ? beta / bn : beta;
+  ctl[C_KERN] += kern;
+  bool go = false;
+  if (ctl[C_STAT] != 0.0) {
+  } else if (!isfinite(beta)) {
+    ctl[C_STAT] = C_STAT_NUMERIC;
+  } else if (beta <= ctl[C_TOL]) {
+  } else if (ctl[C_ACC] >= 0.0 && ctl[C_REST] > 0.0 && beta > 0.5 * prev) {
+    if (beta > ctl[C_ACC]) ctl[C_STAT] = C_STAT_NOCONV;
+  } else if (ctl[C_ITER] >= (double)max_iters) {
+    ctl[C_STAT] = C_STAT_NOCONV;
+  } else {
+    go = true;
+    ctl[C_REST] += 1.0;
+  }
+  cudaGraphSetConditional(loop, go ? 1u : 0u);
+}
+
+// start of a cycle: no Arnoldi step after the first runs unless the step
+// before it says so (the IF handles keep their value across WHILE iterations)
+__global__ void k_cycle_head(CondSet cs) {
+  griddep_wait();
+  if (threadIdx.x != 0) return;
+  for (int i = 2; i < cs.n; ++i) cudaGraphSetConditional(cs.c[i], 0u);
+}
+
+// after Arnoldi step j: count it, and run step j + 1 unless the residual
+// estimate is below the tolerance, the step broke down or hit NaN/Inf, or the
+// iteration budget is spent; a NaN/Inf drops the cycle's update of x
+// (k = flag[5] = 0)
+__global__ void k_step_ctrl(double* flag, double* ctl, int max_iters, double kern, int has_next,
+                            cudaGraphConditionalHandle next) {
+  griddep_wait();
+  if (threadIdx.x != 0) return;
+  const double it = ctl[C_ITER] + 1.0;
+  ctl[C_ITER] = it;
+  ctl[C_REO] += flag[4] != 0.0 ? 1.0 : 0.0;
+  ctl[C_KERN] += kern;
+  const bool numeric = flag[2] != 0.0;
+  if (numeric) {
+    flag[5] = 0.0;
+    ctl[C_STAT] = C_STAT_NUMERIC;
+  }
+  const bool stop = numeric || flag[0] <= ctl[C_TOL] || flag[3] != 0.0 || it >= (double)max_iters;
+  if (has_next) cudaGraphSetConditional(next, stop ? 0u : 1u);
+}
+
+void launch_solve_begin(const double* bn2, double rtol, double accept, double* ctl, cudaStream_t s) {
+  SD_COUNT(1);
+  launch_k(k_solve_begin, dim3(1), dim3(32), 0, s, bn2, rtol, accept, ctl);
+}
+void launch_restart_ctrl(const double* beta2, double* ctl, int max_iters, double kern,
+                         cudaGraphConditionalHandle loop, cudaStream_t s) {
+  SD_COUNT(1);
+  launch_k(k_restart_ctrl, dim3(1), dim3(32), 0, s, beta2, ctl, max_iters, kern, loop);
+}
+void launch_cycle_head(const CondSet& cs, cudaStream_t s) {
+  SD_COUNT(1);
+  launch_k(k_cycle_head, dim3(1), dim3(32), 0, s, cs);
+}
+void launch_step_ctrl(double* flag, double* ctl, int max_iters, double kern, int has_next,
+                      cudaGraphConditionalHandle next, cudaStream_t s) {
+  SD_COUNT(1);
+  launch_k(k_step_ctrl, dim3(1), dim3(32), 0, s, flag, ctl, max_iters, kern, has_next, next);
 }
 
 // out[z * count + t] = src_z[t] for every instance z of a lockstep batch

@@ -51,7 +51,7 @@ class sd_options(ctypes.Structure):
                 ("darcy_coupled", ctypes.c_int32), ("coupling", ctypes.c_int32),
                 ("coupling_max", ctypes.c_int32), ("coupling_columns", ctypes.c_int32),
                 ("coupling_eps", ctypes.c_double), ("coupling_omega", ctypes.c_double),
-                ("coupling_order", ctypes.c_int32),
+                ("coupling_order", ctypes.c_int32), ("coupling_rtol", ctypes.c_double),
                 ("bc_dp", ctypes.c_double), ("bc_tend", ctypes.c_double),
                 ("stream", ctypes.c_void_p)]
 

@@ -97,7 +97,7 @@ def test_option_validation_without_gpu(sd):
     g = sd.sd_grid(n, n)
     bad = [("bc", 3), ("bc", -1), ("coupling", 2), ("coupling_order", 3), ("tile_rows", 12),
            ("cheb_degree", 0), ("cheb_degree", 9), ("coarsest", 1), ("darcy_coupled", 3), ("orth", 2),
-           ("bc_tend", -1.0), ("bc_dp", float("nan"))]
+           ("bc_tend", -1.0), ("bc_dp", float("nan")), ("graph", 3), ("graph", -1)]
     for field, value in bad:
         o = sd.sd_options_default()
         setattr(o, field, value)
@@ -107,7 +107,8 @@ def test_option_validation_without_gpu(sd):
         assert e.value.code == sd.SD_E_INVAL, field
     # partitioned coupling: its parameters, and Sec. 3's order needs traction sides
     for field, value in [("coupling_columns", 0), ("coupling_columns", 31), ("coupling_eps", 0.0),
-                         ("coupling_omega", 0.0), ("coupling_max", 0)]:
+                         ("coupling_omega", 0.0), ("coupling_max", 0), ("coupling_rtol", -1e-12),
+                         ("coupling_rtol", 1.0)]:
         o = sd.sd_options_default()
         o.coupling = sd.SD_PARTITIONED
         setattr(o, field, value)

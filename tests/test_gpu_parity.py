@@ -283,6 +283,57 @@ def test_graph_replay_bitwise(sd):
     assert np.array_equal(xs[0], xs[1])
 
 
+@pytest.mark.parametrize("restart,max_iters,precision", [(30, 600, 1), (4, 600, 1), (4, 600, 0), (4, 6, 1)])
+def test_solve_graph_bitwise(sd, restart, max_iters, precision):
+    # graph option 2 (a whole solve as one graph, its loop decided on the
+    # device) runs the iterations of the step-by-step path: the same iterates
+    # bit for bit and the same counters; the kernel count grows by exactly the
+    # control kernels (2 per solve, 2 per restart cycle, 1 per iteration)
+    n = 64
+    K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=9)
+    res = []
+    for graph in (1, 2):
+        h = make(sd, n, 1e-3, K, 1.0, 0.05, precision, graph=graph, restart=restart, max_iters=max_iters)
+        l0 = sd.sd_launch_count()
+        infos = sd.sd_step(h, 3, raise_on_error=False)
+        res.append((infos, sd.sd_launch_count() - l0, sd.sd_get_state(h)[2]))
+    (i1, c1, x1), (i2, c2, x2) = res
+    assert np.array_equal(x1, x2)
+    keys = ["iters", "restarts", "status", "relres", "reorths", "relres_v", "relres_pff", "relres_pm"]
+    for a, b in zip(i1, i2):
+        assert [a[k] for k in keys] == [b[k] for k in keys]
+    if max_iters < 600:
+        assert all(i["status"] == -3 for i in i2)
+    else:
+        assert all(i["status"] == 0 for i in i2)
+        assert max(i["restarts"] for i in i2) >= (2 if restart == 4 else 1)
+    extra = sum(2 + 2 * i["restarts"] + i["iters"] for i in i2)
+    assert c2 == c1 + extra
+
+
+def test_solve_graph_partitioned_and_solve(sd):
+    # the subdomain solves of the partitioned coupling and sd_solve (another
+    # iterate buffer: the graph is rebuilt for it) through graph option 2
+    n = 64
+    K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=12)
+    out = []
+    for graph in (1, 2):
+        h = make(sd, n, 1e-3, K, 1.0, 0.05, graph=graph, coupling=1)
+        infos = sd.sd_step(h, 2)
+        hm = make(sd, n, 1e-3, K, 1.0, 0.05, graph=graph)
+        sd.sd_step(hm, 1)
+        b = sd.sd_rhs(hm, sd.sd_get_state(hm)[2], 0.1)
+        x = np.zeros_like(b)
+        si = sd.sd_solve(hm, b, x)
+        sd.sd_step(hm, 1)
+        out.append((infos, sd.sd_get_state(h)[2], x, si, sd.sd_get_state(hm)[2]))
+    (ia, xa, sa, ka, ya), (ib, xb, sb, kb, yb) = out
+    assert [(i["iters"], i["coupling_iters"]) for i in ia] == [(i["iters"], i["coupling_iters"]) for i in ib]
+    assert np.array_equal(xa, xb)
+    assert np.array_equal(sa, sb) and ka["iters"] == kb["iters"]
+    assert np.array_equal(ya, yb)
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_darcy_overlap_parity(sd, precision):
     # block-diagonal Darcy part on a second stream: same solution as the oracle
@@ -388,6 +439,25 @@ def test_partitioned_coupling_parity(sd, n, precision):
     b = o.rhs(x0, 0.05)
     _, evals = d.solve(b, O.split(x0, n)["v"][0].copy(), eps=1e-10)
     assert abs(infos[0]["coupling_iters"] - evals) <= 1, (infos[0]["coupling_iters"], evals)
+
+
+@pytest.mark.parametrize("bc", [0, 2])
+def test_partitioned_long_run_does_not_stall(sd, bc):
+    # default options over many steps of the lognormal workload: the subdomain
+    # solves run three decades below the coupling test, so every step's
+    # coupling converges in a few iterations (with the solves at rtol = 1e-10
+    # the iteration stalled at coupling_max on some steps); on the
+    # pressure-driven problem the Darcy solves reach their rounding floor above
+    # that tolerance and stop there (stagnation accepted at rtol)
+    wl = I.lognormal_at_scale(256)
+    o = sd.sd_options_default()
+    o.coupling = sd.SD_PARTITIONED
+    o.bc = bc
+    h = sd.sd_create(256, wl.mu, wl.K(), wl.alpha, wl.dt, o)
+    infos = sd.sd_step(h, 30, raise_on_error=False)
+    assert all(i["status"] == 0 for i in infos), [i["status"] for i in infos]
+    assert max(i["coupling_iters"] for i in infos) <= 10
+    assert max(i["relres"] for i in infos) <= 1e-10
 
 
 def test_partitioned_manufactured_solution(sd):

@@ -1042,6 +1042,54 @@ void launch_prolong_D(int nf, int Pf, T* x, int nc, int Pc, const T* e, cudaStre
 // of the intermediate steps disappear.
 static const int TLX = 32, TLT = 256;  // tile width and threads; the height TLY is a template parameter
 
+// Prolongation inside the tiled smoothers.  The coarse correction around a
+// tile is staged once in shared memory as the values cu_at / cv_at / cd_at
+// return (ghosts and mirrors included) on a CX x CY coarse window whose
+// corner is (I0, J0); every halo point's increment is then formed from that
+// window with the operations of prolong_u_val / prolong_v_val /
+// prolong_D_val in the same order, so it is bitwise the same.  (Formed from
+// global memory, the increments took as many instructions as the three
+// smoothing steps of a tile.)
+template <typename T>
+__device__ __forceinline__ T prolong_u_sm(const T* __restrict__ s, int CX, int I0, int J0, int i, int j) {
+  const int J = j >> 1, Jn = (j & 1) ? J + 1 : J - 1;
+  const int I = i >> 1;
+  const T* r0 = s + (J - J0) * CX + (I - I0);
+  const T* r1 = s + (Jn - J0) * CX + (I - I0);
+  T cy0, cy1;
+  if (i & 1) {
+    cy0 = T(0.5) * (r0[0] + r0[1]);
+    cy1 = T(0.5) * (r1[0] + r1[1]);
+  } else {
+    cy0 = r0[0];
+    cy1 = r1[0];
+  }
+  return T(0.75) * cy0 + T(0.25) * cy1;
+}
+template <typename T>
+__device__ __forceinline__ T prolong_v_sm(const T* __restrict__ s, int CX, int I0, int J0, int i, int j) {
+  const int I = i >> 1, In = (i & 1) ? I + 1 : I - 1;
+  const int J = j >> 1;
+  const T* r0 = s + (J - J0) * CX;
+  T cx0, cx1;
+  if (j & 1) {
+    cx0 = T(0.5) * (r0[I - I0] + r0[CX + I - I0]);
+    cx1 = T(0.5) * (r0[In - I0] + r0[CX + In - I0]);
+  } else {
+    cx0 = r0[I - I0];
+    cx1 = r0[In - I0];
+  }
+  return T(0.75) * cx0 + T(0.25) * cx1;
+}
+template <typename T>
+__device__ __forceinline__ T prolong_D_sm(const T* __restrict__ s, int CX, int I0, int J0, int i, int j) {
+  const int I = i >> 1, J = j >> 1;
+  const int In = (i & 1) ? I + 1 : I - 1, Jn = (j & 1) ? J + 1 : J - 1;
+  const T* r0 = s + (J - J0) * CX - I0;
+  const T* r1 = s + (Jn - J0) * CX - I0;
+  return T(0.5625) * r0[I] + T(0.1875) * (r0[In] + r1[I]) + T(0.0625) * r1[In];
+}
+
 template <typename T, int NS, int TLY, bool BT>
 __global__ void __launch_bounds__(TLT) k_smooth_tile_D(Coef<T> c, const T* __restrict__ xin,
                                                        const T* __restrict__ b, T* __restrict__ xout,
@@ -1068,9 +1116,16 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_D(Coef<T> c, const T* __res
     }
   }
   constexpr int H = NS, EX = TLX + 2 * H, EY = TLY + 2 * H, SP = EX + 1, SR = EY + 1;
+  constexpr int CX = SP / 2 + 4, CY = SR / 2 + 4;  // coarse window of the prolongation
   __shared__ T sb[SR * SP], sx0[SR * SP], sx1[SR * SP], sd[SR * SP], sTx[SR * SP], sTy[SR * SP];
+  __shared__ T sce[CY * CX];
   const int n = c.n, P = c.P;
   const int ilo = blockIdx.x * TLX - H, jlo = blockIdx.y * TLY - H;
+  const int I0 = (ilo >> 1) - 1, J0 = (jlo >> 1) - 1;
+  if (xin && ec) {
+    for (int p = threadIdx.x; p < CX * CY; p += TLT) sce[p] = cd_at(ec, nc, Pc, I0 + p % CX, J0 + p / CX);
+    __syncthreads();
+  }
   for (int p = threadIdx.x; p < SR * SP; p += TLT) {
     const int gi = ilo + p % SP, gj = jlo + p / SP;
     T vb = T(0), vx = T(0), vtx = T(0), vty = T(0);
@@ -1080,7 +1135,7 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_D(Coef<T> c, const T* __res
         vb = b[gk];
         if (xin) {
           vx = xin[gk];
-          if (ec) vx += prolong_D_val(ec, nc, Pc, gi, gj);
+          if (ec) vx += prolong_D_sm(sce, CX, I0, J0, gi, gj);
         }
       }
       if (gi <= n && gj < n) vtx = c.Tx[gk];
@@ -1156,13 +1211,27 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_V(Coef<T> c, const T* __res
     }
   }
   constexpr int H = NS, EX = TLX + 2 * H, EY = TLY + 2 * H, SP = EX + 1, SR = EY + 1;
+  constexpr int CX = SP / 2 + 4, CY = SR / 2 + 4;  // coarse window of the prolongation
   __shared__ T sbu[SR * SP], sbv[SR * SP], sau[SR * SP], sav[SR * SP], sbu2[SR * SP], sbv2[SR * SP];
   __shared__ T sdu[SR * SP], sdv[SR * SP], sw[SP], srg[SP];
+  __shared__ T scu[CY * CX], scv[CY * CX];
   const int n = c.n, P = c.P;
   const long long nv = (long long)n * P;
   const int ilo = blockIdx.x * TLX - H, jlo = blockIdx.y * TLY - H;
   const T* ecu = ec;
   const T* ecv = ec ? ec + (long long)nc * Pc : nullptr;
+  const int I0 = (ilo >> 1) - 1, J0 = (jlo >> 1) - 1;
+  if (xin && ec) {
+    // window entries no halo point reads are set to zero: coarse u faces
+    // outside 0..nc (which cu_at would read past its row on traction sides)
+    // and coarse v rows below 0
+    for (int p = threadIdx.x; p < CX * CY; p += TLT) {
+      const int I = I0 + p % CX, J = J0 + p / CX;
+      scu[p] = (I >= 0 && I <= nc) ? cu_at(ecu, nc, Pc, I, J, c.lat) : T(0);
+      scv[p] = J >= 0 ? cv_at(ecv, nc, Pc, I, J) : T(0);
+    }
+    __syncthreads();
+  }
   for (int p = threadIdx.x; p < SR * SP; p += TLT) {
     const int gi = ilo + p % SP, gj = jlo + p / SP;
     T bu = T(0), bv = T(0), xu = T(0), xv = T(0);
@@ -1172,14 +1241,14 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_V(Coef<T> c, const T* __res
         bu = b[gk];
         if (xin) {
           xu = xin[gk];
-          if (ec && (c.lat || (gi > 0 && gi < n))) xu += prolong_u_val(ecu, nc, Pc, gi, gj, c.lat);
+          if (ec && (c.lat || (gi > 0 && gi < n))) xu += prolong_u_sm(scu, CX, I0, J0, gi, gj);
         }
       }
       if (gi < n && gj <= n) {  // v face
         bv = b[nv + gk];
         if (xin) {
           xv = xin[nv + gk];
-          if (ec && gj < n) xv += prolong_v_val(ecv, nc, Pc, gi, gj);
+          if (ec && gj < n) xv += prolong_v_sm(scv, CX, I0, J0, gi, gj);
         }
       }
     }

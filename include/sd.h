@@ -194,8 +194,8 @@ typedef struct {
                           of sd_step / sd_solve (default 1) */
   int32_t tile;        /* FP32 V-cycles: all Chebyshev steps of one smoothing in one
                           shared-memory-tiled kernel, prolongation folded in (default 1) */
-  int32_t tile_rows;   /* output rows of one smoothing tile, 8 or 16; 0 (default):
-                          8 on levels up to 1024 cells per side, 16 above;
+  int32_t tile_rows;   /* output rows of one smoothing tile, 4, 8 or 16; 0 (default):
+                          4 on levels up to 256 cells per side, 8 up to 1024, 16 above;
                           tiles are 32 faces or cells wide */
   int32_t darcy_coupled; /* SD_TRI_SCHUR: 1 (default) keeps C'_1, the Darcy block follows
                           the velocity; 0 drops it and overlaps the Darcy V-cycle with
@@ -406,7 +406,7 @@ int sd_apply_noalloc(const sd_grid *grid, double mu, const double *K, double alp
 
 /* Autotuner: pick tile_rows, coarsest (V-cycle depth) and cheb_degree for
  * this grid size on the current device by timing.  Each candidate of the
- * grid {16, 8} rows (FP32 tiled smoothing only) x coarsest {4, 8, 16} x
+ * grid {by level, 16, 8} rows (FP32 tiled smoothing only) x coarsest {4, 8, 16} x
  * cheb_degree {3, 2, 4} builds a fresh instance from (grid, mu, K,
  * alpha_bj, dt) with *base (NULL: defaults) and those three fields, runs 2
  * untimed and then `nsteps` timed implicit-Euler steps, and is scored by its

@@ -103,7 +103,8 @@ struct MG {
   CoarseCycle<T> cycV, cycD, cycP;
 };
 
-const int FUSE_N = 16;  // grids with at most this many cells per side run fused (measured: 16 beats 32, most in FP64)
+const int FUSE_N = 16;
+const int SMALL_TILE_N = 256;  // levels up to this size smooth 4-row tiles (measured 1.4 % per step at 1024^2)  // grids with at most this many cells per side run fused (measured: 16 beats 32, most in FP64)
 
 int level_count(int n, int coarsest) {
   int L = 1;
@@ -566,10 +567,12 @@ ChebSteps<T> steps_of(const Block<T>& B, int rows) {
 }
 
 // smoothing tile height of a level with n cells per side: the option, or by
-// default 8 rows up to n = 1024 (more CTAs in flight) and 16 above (less halo)
+// default 4 rows up to n = 256 (the coarse levels run a few CTAs each, whose
+// latency shorter tiles cut), 8 up to n = 1024 (more CTAs in flight) and 16
+// above (less halo)
 int tile_rows_of(const sd_handle* h, int n) {
   if (h->opt.tile_rows) return h->opt.tile_rows;
-  return n <= 1024 ? 8 : 16;
+  return n <= SMALL_TILE_N ? 4 : n <= 1024 ? 8 : 16;
 }
 
 // tiled smoothing (all steps of one smoothing in one kernel) is used for the
@@ -1395,7 +1398,7 @@ int validate(const sd_grid* grid, double mu, double alpha, double dt, const sd_o
   if (o->orth < 0 || o->orth > 1 || !(o->reorth_eta > 0) || o->reorth_eta > 1) return SD_E_INVAL;
   if (o->graph < 0 || o->graph > 2) return SD_E_INVAL;
   if (o->darcy_coupled < 0 || o->darcy_coupled > 2) return SD_E_INVAL;
-  if (o->tile_rows != 0 && o->tile_rows != 8 && o->tile_rows != 16) return SD_E_INVAL;
+  if (o->tile_rows != 0 && o->tile_rows != 4 && o->tile_rows != 8 && o->tile_rows != 16) return SD_E_INVAL;
   if (o->coupling != SD_MONOLITHIC && o->coupling != SD_PARTITIONED) return SD_E_INVAL;
   if (o->coupling_order < SD_ORDER_AUTO || o->coupling_order > SD_ORDER_FF_FIRST) return SD_E_INVAL;
   // the free flow with a prescribed interface velocity is singular on Dirichlet sides

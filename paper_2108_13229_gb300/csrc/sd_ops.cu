@@ -1341,6 +1341,7 @@ int launch_tile_D_rows(const Coef<T>& c, const T* x_in, const T* b, T* x_out, co
 template <typename T>
 int launch_smooth_tile_D(const Coef<T>& c, const T* x_in, const T* b, T* x_out, const ChebSteps<T>& cs,
                          const T* ct, const T* ec, int nc, int Pc, cudaStream_t s) {
+  if (cs.rows == 4) return launch_tile_D_rows<T, 4>(c, x_in, b, x_out, cs, ct, ec, nc, Pc, s);
   return cs.rows == 8 ? launch_tile_D_rows<T, 8>(c, x_in, b, x_out, cs, ct, ec, nc, Pc, s)
                       : launch_tile_D_rows<T, 16>(c, x_in, b, x_out, cs, ct, ec, nc, Pc, s);
 }
@@ -1375,6 +1376,7 @@ int launch_tile_V_rows(const Coef<T>& c, const T* x_in, const T* b, T* x_out, co
 template <typename T>
 int launch_smooth_tile_V(const Coef<T>& c, const T* x_in, const T* b, T* x_out, const ChebSteps<T>& cs,
                          const T* ct, const T* ec, int nc, int Pc, cudaStream_t s) {
+  if (cs.rows == 4) return launch_tile_V_rows<T, 4>(c, x_in, b, x_out, cs, ct, ec, nc, Pc, s);
   return cs.rows == 8 ? launch_tile_V_rows<T, 8>(c, x_in, b, x_out, cs, ct, ec, nc, Pc, s)
                       : launch_tile_V_rows<T, 16>(c, x_in, b, x_out, cs, ct, ec, nc, Pc, s);
 }

@@ -117,12 +117,12 @@ extern "C" int sd_autotune(const sd_grid* grid, double mu, const double* K, doub
   }
   // the candidate grid: tile height only matters for the FP32 tiled smoother
   const bool tiles = b.precision == SD_MIXED && b.tile;
-  const int rows[2] = {16, 8};
+  const int rows[3] = {0, 16, 8};  // 0: by level size (4, 8 or 16 rows)
   const int coarse[3] = {4, 8, 16};
   const int degree[3] = {3, 2, 4};
   double best_t = -1.0;
   sd_options win = b;
-  for (int r = 0; r < (tiles ? 2 : 1); ++r)
+  for (int r = 0; r < (tiles ? 3 : 1); ++r)
     for (int c = 0; c < 3; ++c)
       for (int d = 0; d < 3; ++d) {
         sd_options o = b;

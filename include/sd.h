@@ -165,7 +165,9 @@ typedef struct {
   int32_t schur_degree;       /* the same in the pressure-Laplacian block (0: as above;
                                  default 1, one damped-Jacobi step) */
   int32_t coarsest;    /* coarsen while the grid has more than this many cells per
-                          side (default 4) */
+                          side (default 16: the coarsest grid, at most 16 x 16 cells,
+                          is solved with its dense FP64 inverse spread over all SMs,
+                          which measured 7-25 % faster per step than coarsening to 4) */
   double schur_gamma;  /* gamma of S^ (default 0.5) */
   double cheb_ratio;   /* Chebyshev interval [lmax/ratio, 1.1 lmax] (default 8) */
   int32_t schur_mass;  /* SD_TRI_SCHUR: add the mass-dominated part (1/dt) L_p^-1 of

@@ -375,11 +375,12 @@ int coarse_inverse(sd_handle* h, int kind, double* Ainv, int* idx_dev, int m) {
   }
   cudaStream_t s = h->s;
   CK(cudaMemcpyAsync(idx_dev, idx.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
-  double *X = nullptr, *Y = nullptr, *A = nullptr;
+  double *X = nullptr, *Y = nullptr, *A = nullptr, *fc = nullptr;
   int* status = nullptr;
   CK(cudaMalloc(&X, sizeof(double) * stride * m));
   CK(cudaMalloc(&Y, sizeof(double) * stride * m));
   CK(cudaMalloc(&A, sizeof(double) * m * m));
+  CK(cudaMalloc(&fc, sizeof(double) * m));
   CK(cudaMalloc(&status, sizeof(int)));
   CK(cudaMemsetAsync(X, 0, sizeof(double) * stride * m, s));
   CK(cudaMemsetAsync(Y, 0, sizeof(double) * stride * m, s));
@@ -388,11 +389,11 @@ int coarse_inverse(sd_handle* h, int kind, double* Ainv, int* idx_dev, int m) {
   if (blockV) launch_resid_V<double>(c, X, nullptr, Y, 2, m, stride, s);
   else launch_resid_D<double>(c, X, nullptr, Y, 2, m, stride, s);
   launch_gather_dense(Y, stride, idx_dev, m, A, s);
-  launch_gj_inverse(A, Ainv, m, status, s);
+  launch_gj_inverse(A, Ainv, m, fc, status, s);
   int hs = 0;
   CK(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  cudaFree(X); cudaFree(Y); cudaFree(A); cudaFree(status);
+  cudaFree(X); cudaFree(Y); cudaFree(A); cudaFree(fc); cudaFree(status);
   if (hs != 0) {
     snprintf(g_errmsg, sizeof(g_errmsg), "coarsest %s block singular at column %d", blockV ? "velocity" : "Darcy", hs);
     return SD_E_NUMERIC;
@@ -477,7 +478,8 @@ int setup_mg(sd_handle* h, MG<T>& M) {
     };
     // the largest entry grid (at most FUSE_N cells per side) whose levels fit in shared memory
     for (int f = 0; f < h->nlev; ++f) {
-      if (h->geo[f].n > FUSE_N || h->nlev - f > SD_CYC_MAXL) continue;
+      // a lone coarsest level runs the multi-CTA dense solve instead
+      if (h->geo[f].n > FUSE_N || h->nlev - f > SD_CYC_MAXL || h->nlev - f < 2) continue;
       fill(M.cycV, 0, 0, f);
       fill(M.cycD, 1, 1, f);
       fill(M.cycP, 1, 2, f);
@@ -1801,7 +1803,7 @@ void sd_options_default(sd_options* o) {
   o->cheb_degree = 3;
   o->cheb_degree_coarse = 0;
   o->schur_degree = 1;
-  o->coarsest = 4;
+  o->coarsest = 16;
   o->fuse_coarse = 1;
   o->orth = 1;
   o->reorth_eta = 1e-3;

@@ -15,6 +15,8 @@
 
 #include <math.h>
 
+#include <algorithm>
+
 namespace sdk {
 
 std::atomic<long long> g_launch_count{0};
@@ -727,6 +729,11 @@ void launch_iqn(const IqnState& st, const double* vt, const double* p, cudaStrea
 }
 
 // ------------------------------------------------------ dense coarse solve
+// x[idx[r]] = T(sum_l Ainv[r][l] b[idx[l]]): one warp per row r, its lanes
+// striding over l, a fixed shuffle tree; the rows spread over as many CTAs
+// as there are rows / 8 (each CTA stages b in shared memory), so a 544-row
+// coarsest solve is not serialised on one SM's FP64 pipe.  Every row sums
+// in the same order as in the single-CTA form of the fused coarse cycle.
 template <typename T>
 __global__ void k_dense_solve(const double* __restrict__ Ainv, const int* __restrict__ idx, int m,
                               const T* __restrict__ b, T* __restrict__ x, Bat bt) {
@@ -743,7 +750,7 @@ __global__ void k_dense_solve(const double* __restrict__ Ainv, const int* __rest
   for (int l = threadIdx.x; l < m; l += blockDim.x) bs[l] = (double)b[idx[l]];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int r = warp; r < m; r += nw) {
+  for (int r = blockIdx.x * nw + warp; r < m; r += gridDim.x * nw) {
     const double* row = Ainv + (long long)r * m;
     double s = 0.0;
     for (int l = lane; l < m; l += 32) s = fma(row[l], bs[l], s);
@@ -756,64 +763,99 @@ __global__ void k_dense_solve(const double* __restrict__ Ainv, const int* __rest
 template <typename T>
 void launch_dense_solve(const double* Ainv, const int* idx, int m, const T* b, T* x, cudaStream_t s) {
   SD_COUNT(1);
-  launch_k(k_dense_solve<T>, dim3(1), dim3(512), sizeof(double) * m, s, Ainv, idx, m, b, x);
+  launch_k(k_dense_solve<T>, dim3((m + 7) / 8), dim3(256), sizeof(double) * m, s, Ainv, idx, m, b, x);
 }
 
-// Gauss-Jordan with partial pivoting on [A | I], one CTA; the inverse ends in W.
-__global__ void k_gj_inverse(double* A, double* W, int m, int* status) {
+// Gauss-Jordan with partial pivoting on [A | I]; the inverse ends in W.
+// Column c takes two launches: k_gj_pivot (one CTA) picks the pivot row (the
+// largest |A[r][c]|, r >= c, the lowest r on ties), swaps it into row c,
+// scales row c and records the elimination factors fc[r] = A[r][c] (0 for
+// r = c); k_gj_eliminate (all SMs) subtracts fc[r] times row c from every
+// other row.  A zero pivot sets *status = c + 1 and the remaining launches
+// do nothing.  (One CTA for the whole elimination serialised 2m^3 FP64
+// operations on one SM: 0.15 s for the 544-row coarsest velocity block.)
+__global__ void k_gj_init(double* W, int m, int* status) {
   griddep_wait();
-  extern __shared__ double fcol[];
+  const long long mm = (long long)m * m;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < mm; e += (long long)gridDim.x * blockDim.x)
+    W[e] = ((e / m) == (e % m)) ? 1.0 : 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *status = 0;
+}
+
+__global__ void __launch_bounds__(1024) k_gj_pivot(double* A, double* W, int m, int c, double* fc, int* status) {
+  griddep_wait();
+  __shared__ double sbest[32];
+  __shared__ int srow[32];
   __shared__ int piv;
   __shared__ double pval;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (long long e = tid; e < (long long)m * m; e += nt) W[e] = ((e / m) == (e % m)) ? 1.0 : 0.0;
-  if (tid == 0) *status = 0;
+  if (*status != 0) return;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  // strided scan in increasing r keeps the first maximum, as does the tree
+  double best = -1.0;
+  int br = m;
+  for (int r = c + tid; r < m; r += nt) {
+    const double a = fabs(A[(long long)r * m + c]);
+    if (a > best) { best = a; br = r; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_down_sync(0xffffffffu, best, o);
+    const int orr = __shfl_down_sync(0xffffffffu, br, o);
+    if (ob > best || (ob == best && orr < br)) { best = ob; br = orr; }
+  }
+  if (lane == 0) { sbest[warp] = best; srow[warp] = br; }
   __syncthreads();
-  for (int c = 0; c < m; ++c) {
-    if (tid == 0) {
-      int p = c;
-      double best = fabs(A[(long long)c * m + c]);
-      for (int r = c + 1; r < m; ++r) {
-        const double a = fabs(A[(long long)r * m + c]);
-        if (a > best) { best = a; p = r; }
-      }
-      piv = p;
-      pval = best;
-      if (best == 0.0 && *status == 0) *status = c + 1;
-    }
-    __syncthreads();
-    if (pval == 0.0) return;
-    const int p = piv;
-    if (p != c)
-      for (int q = tid; q < m; q += nt) {
-        double t = A[(long long)c * m + q]; A[(long long)c * m + q] = A[(long long)p * m + q]; A[(long long)p * m + q] = t;
-        t = W[(long long)c * m + q]; W[(long long)c * m + q] = W[(long long)p * m + q]; W[(long long)p * m + q] = t;
-      }
-    __syncthreads();
-    const double inv = 1.0 / A[(long long)c * m + c];
-    __syncthreads();
+  if (tid == 0) {
+    double b = sbest[0];
+    int r = srow[0];
+    for (int w = 1; w < (nt + 31) / 32; ++w)
+      if (sbest[w] > b || (sbest[w] == b && srow[w] < r)) { b = sbest[w]; r = srow[w]; }
+    piv = r;
+    pval = b;
+    if (!(b > 0.0)) *status = c + 1;
+  }
+  __syncthreads();
+  if (!(pval > 0.0)) return;
+  const int p = piv;
+  if (p != c)
     for (int q = tid; q < m; q += nt) {
-      A[(long long)c * m + q] *= inv;
-      W[(long long)c * m + q] *= inv;
+      double t = A[(long long)c * m + q]; A[(long long)c * m + q] = A[(long long)p * m + q]; A[(long long)p * m + q] = t;
+      t = W[(long long)c * m + q]; W[(long long)c * m + q] = W[(long long)p * m + q]; W[(long long)p * m + q] = t;
     }
-    __syncthreads();
-    for (int r = tid; r < m; r += nt) fcol[r] = (r == c) ? 0.0 : A[(long long)r * m + c];
-    __syncthreads();
-    for (long long e = tid; e < (long long)m * m; e += nt) {
-      const int r = (int)(e / m), q = (int)(e % m);
-      const double f = fcol[r];
-      if (f != 0.0) {
-        A[e] -= f * A[(long long)c * m + q];
-        W[e] -= f * W[(long long)c * m + q];
-      }
+  __syncthreads();
+  const double inv = 1.0 / A[(long long)c * m + c];
+  __syncthreads();
+  for (int q = tid; q < m; q += nt) {
+    A[(long long)c * m + q] *= inv;
+    W[(long long)c * m + q] *= inv;
+  }
+  for (int r = tid; r < m; r += nt) fc[r] = (r == c) ? 0.0 : A[(long long)r * m + c];
+}
+
+__global__ void k_gj_eliminate(double* A, double* W, int m, int c, const double* __restrict__ fc,
+                               const int* status) {
+  griddep_wait();
+  if (*status != 0) return;
+  const long long mm = (long long)m * m;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < mm; e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e / m), q = (int)(e % m);
+    const double f = fc[r];
+    if (f != 0.0) {
+      A[e] -= f * A[(long long)c * m + q];
+      W[e] -= f * W[(long long)c * m + q];
     }
-    __syncthreads();
   }
 }
 
-void launch_gj_inverse(double* A, double* work, int m, int* status, cudaStream_t s) {
-  SD_COUNT(1);
-  launch_k(k_gj_inverse, dim3(1), dim3(1024), sizeof(double) * m, s, A, work, m, status);
+void launch_gj_inverse(double* A, double* W, int m, double* fc, int* status, cudaStream_t s) {
+  const long long mm = (long long)m * m;
+  const int nb = (int)std::min<long long>((mm + 255) / 256, 152 * 8);
+  SD_COUNT(1 + 2 * m);
+  launch_k(k_gj_init, dim3(nb), dim3(256), 0, s, W, m, status);
+  for (int c = 0; c < m; ++c) {
+    launch_k(k_gj_pivot, dim3(1), dim3(1024), 0, s, A, W, m, c, fc, status);
+    launch_k(k_gj_eliminate, dim3(nb), dim3(256), 0, s, A, W, m, c, (const double*)fc, (const int*)status);
+  }
 }
 
 __global__ void k_identity_batch(double* X, long long stride, const int* idx, int m) {

@@ -78,15 +78,28 @@ struct sd_server {
   uint64_t next_id = 1;
   int device = 0;
   int flags = 0;
+  bool auto_depth = false;  // created without options: multigrid depth per request
   std::vector<std::thread> workers;
-  std::map<std::tuple<int, double, double>, std::unique_ptr<SizeClass>> classes;
+  std::map<std::tuple<int, double, double, int>, std::unique_ptr<SizeClass>> classes;  // (n, mu, dt, depth)
 };
 
 namespace {
 
-void run_job(sd_server* S, Job* J) {
+// A server created without options picks the multigrid depth per request
+// from its length: the dense inverse of a 16 x 16 coarsest grid costs about
+// 10 ms of setup and some 1,600 dependent launches (which queue behind the
+// other runs' work), and saves 0.2-0.3 ms per step, so runs shorter than
+// kShortRun steps coarsen to 4 x 4 instead.
+const int kShortRun = 40;
+sd_options job_options(const sd_server* S, const Job* J) {
   sd_options o = S->opt;
   o.stream = nullptr;  // each run gets its own stream, so runs overlap on the device
+  if (S->auto_depth) o.coarsest = J->req.nsteps < kShortRun ? 4 : 16;
+  return o;
+}
+
+void run_job(sd_server* S, Job* J) {
+  sd_options o = job_options(S, J);
   sd_handle* h = nullptr;
   int rc = sd_create(&J->req.grid, J->req.mu, J->K.data(), J->req.alpha_bj, J->req.dt, &o, &h);
   std::memset(&J->res, 0, sizeof(J->res));
@@ -156,8 +169,7 @@ void class_loop(sd_server* S, SizeClass* C) {
       fresh.swap(C->incoming);
     }
     for (Job* J : fresh) {  // joins at this tick
-      sd_options o = S->opt;
-      o.stream = nullptr;
+      sd_options o = job_options(S, J);
       const int rc = sd_create(&J->req.grid, J->req.mu, J->K.data(), J->req.alpha_bj, J->req.dt, &o, &J->h);
       if (rc != SD_OK || J->req.nsteps == 0) {
         close_job(J, rc);
@@ -223,7 +235,7 @@ void worker_loop(sd_server* S) {
       const int n = J->req.grid.nx;
       if ((S->flags & SD_SERVER_LOCKSTEP) && sd_dof_count(n) < kServeLockstepDof) {
         // hand the run to its size class and go back for the next request
-        auto key = std::make_tuple(n, J->req.mu, J->req.dt);
+        auto key = std::make_tuple(n, J->req.mu, J->req.dt, job_options(S, J).coarsest);
         auto it = S->classes.find(key);
         if (it == S->classes.end()) {
           std::unique_ptr<SizeClass> c(new SizeClass());
@@ -331,6 +343,7 @@ int sd_server_create_ex(int64_t hbm_budget_bytes, int32_t max_running, const sd_
   sd_server* S = new sd_server();
   sd_options_default(&S->opt);
   if (opt) S->opt = *opt;
+  S->auto_depth = opt == nullptr;
   S->budget = hbm_budget_bytes;
   S->max_running = max_running;
   S->flags = flags;

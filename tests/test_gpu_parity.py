@@ -221,8 +221,10 @@ def test_lockstep_batch_bitwise(sd, precision):
 @pytest.mark.parametrize("lockstep", [True, False])
 def test_server_results_match_alone(sd, lockstep):
     # lockstep: runs of one size class step together, joining and leaving
-    # between ticks (n = 32 and n = 64 have two runs each of different lengths)
-    reqs = [(32, 5, 1), (64, 7, 2), (128, 4, 3), (32, 9, 4), (96, 6, 5), (64, 5, 6)]
+    # between ticks (n = 32 and n = 64 have two runs each of different lengths).
+    # A server made without options picks the multigrid depth per run: runs
+    # under 40 steps coarsen to 4 x 4, longer ones stop at 16 x 16.
+    reqs = [(32, 5, 1), (64, 7, 2), (128, 4, 3), (32, 9, 4), (96, 6, 5), (64, 5, 6), (32, 41, 7)]
     srv = sd.sd_server_create(8 << 30, 3, lockstep=lockstep)
     tickets = []
     for n, steps, seed in reqs:
@@ -233,7 +235,7 @@ def test_server_results_match_alone(sd, lockstep):
         rc, res, x = sd.sd_poll(srv, tk, want_x=True)
         assert rc == 0 and res["steps_done"] == steps and res["latency_ms"] >= res["run_ms"] > 0
         K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=seed)
-        h = make(sd, n, 1e-3, K, 1.0, 0.1)
+        h = make(sd, n, 1e-3, K, 1.0, 0.1, coarsest=4 if steps < 40 else 16)
         sd.sd_step(h, steps)
         assert np.array_equal(sd.sd_get_state(h)[2], x)
     sd.sd_server_destroy(srv)

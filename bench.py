@@ -154,7 +154,7 @@ def tune_form(sd, n, K, precision, stream, enabled: bool):
     best, ms = sd.sd_autotune(n, 1e-3, K, 1.0, 0.05, base, 3, cache)
     tuned = {k: getattr(best, k) for k in TUNED}
     return tuned, {"choice": tuned, "tuned_ms_per_step": ms, "seconds": time.perf_counter() - t0,
-                   "candidates": "tile_rows {by level,16,8} x coarsest {4,8,16} x cheb_degree {3,2,4}; 2+3 steps each; "
+                   "candidates": "tile_rows {by level,16,8} x coarsest {4,8,16} x cheb_degree {3,2,4}; 4+3 steps each; "
                                  "cache " + os.path.basename(cache)}
 
 

@@ -160,7 +160,10 @@ typedef struct {
   int32_t precond;     /* SD_TRI_SCHUR | SD_PV_BJ_I | SD_PV_BGS_I (default SD_TRI_SCHUR) */
   int32_t bc;          /* SD_BC_MMS (default) | SD_BC_MMS_TRACTION | SD_BC_PAPER */
   int32_t cheb_degree; /* Chebyshev smoothing steps before and after each coarse
-                          correction (default 3) */
+                          correction, 1..8; 0 (default): 4 for the mixed form on grids
+                          from 1024 cells per side, 3 otherwise (measured: 4 steps are
+                          6.6 % faster per step at 1024^2 and 3.7 % at 2048^2, 5-13 %
+                          slower at 64^2-512^2 and in FP64) */
   int32_t cheb_degree_coarse; /* the same below the finest level (0: cheb_degree) */
   int32_t schur_degree;       /* the same in the pressure-Laplacian block (0: as above;
                                  default 1, one damped-Jacobi step) */
@@ -416,7 +419,7 @@ int sd_apply_noalloc(const sd_grid *grid, double mu, const double *K, double alp
  * this grid size on the current device by timing.  Each candidate of the
  * grid {by level, 16, 8} rows (FP32 tiled smoothing only) x coarsest {4, 8, 16} x
  * cheb_degree {3, 2, 4} builds a fresh instance from (grid, mu, K,
- * alpha_bj, dt) with *base (NULL: defaults) and those three fields, runs 2
+ * alpha_bj, dt) with *base (NULL: defaults) and those three fields, runs 4
  * untimed and then `nsteps` timed implicit-Euler steps, and is scored by its
  * mean device time per step; candidates whose steps do not all converge are
  * dropped.  The tuned choice does not change what is solved: every step

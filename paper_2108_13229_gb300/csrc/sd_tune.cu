@@ -77,6 +77,11 @@ void cache_store(const char* path, const Key& k, const sd_options& o, double ms)
   std::fclose(f);
 }
 
+// Untimed steps before a candidate is timed: the first steps from the
+// initial state take two to three times the iterations of the later ones,
+// which would weight the choice towards the start-up transient.
+const int kWarm = 4;
+
 // Device time per step of `nsteps` steps after `warm` untimed ones, from a
 // fresh instance; negative when setup failed or a step did not converge.
 double time_candidate(const sd_grid* grid, double mu, const double* K, double alpha, double dt,
@@ -130,7 +135,7 @@ extern "C" int sd_autotune(const sd_grid* grid, double mu, const double* K, doub
         o.coarsest = coarse[c];
         o.cheb_degree = degree[d];
         if (c > 0 && coarse[c - 1] >= grid->nx) continue;  // already a one-level hierarchy
-        const double t = time_candidate(grid, mu, K, alpha_bj, dt, o, 2, nsteps);
+        const double t = time_candidate(grid, mu, K, alpha_bj, dt, o, kWarm, nsteps);
         if (t > 0 && (best_t < 0 || t < best_t)) {
           best_t = t;
           win = o;

@@ -160,10 +160,10 @@ typedef struct {
   int32_t precond;     /* SD_TRI_SCHUR | SD_PV_BJ_I | SD_PV_BGS_I (default SD_TRI_SCHUR) */
   int32_t bc;          /* SD_BC_MMS (default) | SD_BC_MMS_TRACTION | SD_BC_PAPER */
   int32_t cheb_degree; /* Chebyshev smoothing steps before and after each coarse
-                          correction, 1..8; 0 (default): 4 for the mixed form on grids
-                          from 1024 cells per side, 3 otherwise (measured: 4 steps are
-                          6.6 % faster per step at 1024^2 and 3.7 % at 2048^2, 5-13 %
-                          slower at 64^2-512^2 and in FP64) */
+                          correction, 1..8 (default 3; on the log-normal 1024^2 workload
+                          4 steps are 8 % slower per step over the first 30 steps, 5
+                          iterations each, and faster only later, when they bring the
+                          iterations down to 4) */
   int32_t cheb_degree_coarse; /* the same below the finest level (0: cheb_degree) */
   int32_t schur_degree;       /* the same in the pressure-Laplacian block (0: as above;
                                  default 1, one damped-Jacobi step) */

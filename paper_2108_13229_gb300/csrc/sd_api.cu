@@ -1395,7 +1395,7 @@ int validate(const sd_grid* grid, double mu, double alpha, double dt, const sd_o
   if (o->precond < SD_TRI_SCHUR || o->precond > SD_PV_BGS_I) return SD_E_INVAL;
   if (o->bc != SD_BC_MMS && o->bc != SD_BC_MMS_TRACTION && o->bc != SD_BC_PAPER) return SD_E_INVAL;
   if (!std::isfinite(o->bc_dp) || !(o->bc_tend >= 0) || !std::isfinite(o->bc_tend)) return SD_E_INVAL;
-  if (o->cheb_degree < 0 || o->cheb_degree > 8 || o->coarsest < 2 || !(o->schur_gamma > 0) || !(o->cheb_ratio > 1))
+  if (o->cheb_degree < 1 || o->cheb_degree > 8 || o->coarsest < 2 || !(o->schur_gamma > 0) || !(o->cheb_ratio > 1))
     return SD_E_INVAL;
   if (o->orth < 0 || o->orth > 1 || !(o->reorth_eta > 0) || o->reorth_eta > 1) return SD_E_INVAL;
   if (o->graph < 0 || o->graph > 2) return SD_E_INVAL;
@@ -1450,7 +1450,6 @@ int create_impl(const sd_grid* grid, double mu, const double* K, double alpha, d
   sd_handle* h = new (std::nothrow) sd_handle();
   if (!h) return SD_E_NOMEM;
   h->n = n; h->mu = mu; h->alpha = alpha; h->dt = dt; h->opt = o;
-  if (h->opt.cheb_degree == 0) h->opt.cheb_degree = (o.precision == SD_MIXED && n >= 1024) ? 4 : 3;
   init_layout(h);
   auto fail = [&](int code) { sd_destroy(h); return code; };
   if (o.stream) {
@@ -1801,7 +1800,7 @@ void sd_options_default(sd_options* o) {
   o->precision = SD_MIXED;
   o->precond = SD_TRI_SCHUR;
   o->bc = SD_BC_MMS;
-  o->cheb_degree = 0;
+  o->cheb_degree = 3;
   o->cheb_degree_coarse = 0;
   o->schur_degree = 1;
   o->coarsest = 16;

@@ -48,7 +48,7 @@ def test_dof_count_table1(sd):
 def test_options_default(sd):
     o = sd.sd_options_default()
     assert o.restart == 30 and o.rtol == 1e-10 and o.precision == sd.SD_MIXED
-    assert o.precond == sd.SD_TRI_SCHUR and o.cheb_degree >= 0 and o.schur_gamma == 0.5 and o.schur_mass == 1
+    assert o.precond == sd.SD_TRI_SCHUR and o.cheb_degree >= 1 and o.schur_gamma == 0.5 and o.schur_mass == 1
 
 
 def test_memory_estimate(sd):
@@ -96,7 +96,7 @@ def test_option_validation_without_gpu(sd):
     K = np.ones((n, n))
     g = sd.sd_grid(n, n)
     bad = [("bc", 3), ("bc", -1), ("coupling", 2), ("coupling_order", 3), ("tile_rows", 12),
-           ("cheb_degree", -1), ("cheb_degree", 9), ("coarsest", 1), ("darcy_coupled", 3), ("orth", 2),
+           ("cheb_degree", 0), ("cheb_degree", 9), ("coarsest", 1), ("darcy_coupled", 3), ("orth", 2),
            ("bc_tend", -1.0), ("bc_dp", float("nan")), ("graph", 3), ("graph", -1)]
     for field, value in bad:
         o = sd.sd_options_default()

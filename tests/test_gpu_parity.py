@@ -121,14 +121,16 @@ def test_mms_time_stepping(sd, precision):
         assert e <= 1e-6, (k, e)
 
 
+@pytest.mark.parametrize("coarsest", [16, 4])
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("n", [64, 128])
-def test_lognormal_time_stepping(sd, n, precision):
-    # the workload's physics (mu = 1e-3, ln K ~ N(-4, 1), corr. 16 cells) on grids the oracle factors
+def test_lognormal_time_stepping(sd, n, precision, coarsest):
+    # the workload's physics (mu = 1e-3, ln K ~ N(-4, 1), corr. 16 cells) on grids the oracle factors;
+    # coarsest 16: the dense 16 x 16 solve spread over all SMs, 4: the fused single-CTA coarse cycle
     K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=0)
     o = O.Oracle(n, 1e-3, 1.0, 0.05, K)
     xr = o.run(O.exact(n, 0.0, 1e-3), 0.0, 3)
-    h = make(sd, n, 1e-3, K, 1.0, 0.05, precision, rtol=1e-12)
+    h = make(sd, n, 1e-3, K, 1.0, 0.05, precision, rtol=1e-12, coarsest=coarsest)
     infos = sd.sd_step(h, 3)
     assert all(i["status"] == 0 for i in infos)
     _, _, x = sd.sd_get_state(h)
@@ -192,11 +194,12 @@ def test_lockstep_batch_bitwise(sd, precision):
     # and iteration counts share every launch; converged instances sit idle.
     # Each result equals its solo run bit for bit, as does the
     # one-stream-per-instance mode.  n = 48 (one group of three, 49 faces per
-    # row), n = 16 (fused coarse cycle from the fine level), one n = 40 alone.
+    # row; dense 12 x 12 coarsest solve), n = 16 with coarsest 4 (fused coarse
+    # cycle from the fine level), one n = 40 alone.
     cases = [(48, 1, 0.1), (48, 2, 3.0), (48, 3, 10.0), (16, 4, 0.3), (16, 5, 7.0), (40, 6, 1.0)]
     def mk(n, seed, alpha):
         K = I.lognormal_K(n, -4.0, 0.5 + 0.3 * seed, 16.0, seed=seed)
-        return make(sd, n, 1e-3, K, alpha, 0.1, precision)
+        return make(sd, n, 1e-3, K, alpha, 0.1, precision, coarsest=4 if n == 16 else 16)
     alone, its_alone = [], []
     for n, seed, alpha in cases:
         h = mk(n, seed, alpha)

@@ -186,8 +186,13 @@ typedef struct {
                           step is 7-9 % faster; the true residual recomputed at every
                           restart still decides convergence.  1/sqrt(2), the classical
                           choice, took the second pass in 5 of 6 iterations.) */
-  int32_t extrapolate; /* initial guess of step n+1: 2 x^n - x^{n-1} (1, default)
-                          or x^n (0) */
+  int32_t extrapolate; /* initial guess of step n+1: 3 x^n - 3 x^{n-1} + x^{n-2} (2,
+                          default; quadratic in time, linear while only two levels are
+                          known), 2 x^n - x^{n-1} (1) or x^n (0).  The stopping test is
+                          unchanged.  Measured on the log-normal workload: steps 20-40
+                          take 2-3 FGMRES iterations instead of 5 at 1024^2 (1.45 against
+                          3.35 ms/step), 2-3 instead of 5 at 2048^2 and 3 instead of 6
+                          at 256^2; the pressure-driven problem 14-17 instead of 16-19. */
   int32_t graph;       /* 1 (default): replay each Arnoldi step from a captured CUDA
                           graph, the host checking convergence after each; 2: a whole
                           FGMRES solve as one graph whose restart loop (WHILE node) and
@@ -280,10 +285,20 @@ int sd_get_fields(sd_handle *h, double *u, double *v, double *p_ff, double *p_pm
  * whole-system vector x^n and the previous time level x^{n-1} used by the
  * extrapolated initial guess (any output may be NULL; a NULL xprev in
  * sd_set_state clears the history, so the next step starts from x^n).
- * Resuming from a saved (t, step, x, xprev) reproduces the uninterrupted run
- * bit for bit. */
+ * With extrapolate 1 (or 0), resuming from a saved (t, step, x, xprev)
+ * reproduces the uninterrupted run bit for bit; with extrapolate 2 the level
+ * before, x^{n-2}, is also needed (sd_get_history / sd_set_history), else the
+ * first resumed step extrapolates linearly (same tolerance, other bits). */
 int sd_get_state(sd_handle *h, double *t, int64_t *step, double *x, double *xprev);
 int sd_set_state(sd_handle *h, double t, int64_t step, const double *x, const double *xprev);
+
+/* x^{n-2} of the quadratic extrapolation (extrapolate 2), dense layout as x.
+ * sd_get_history returns SD_E_STATE when the handle does not hold it (fewer
+ * than three time levels, extrapolate < 2, or after sd_set_state without
+ * sd_set_history); sd_set_history, called after sd_set_state with an xprev,
+ * installs it (SD_E_STATE without that xprev or with extrapolate < 2). */
+int sd_get_history(sd_handle *h, double *xprev2);
+int sd_set_history(sd_handle *h, const double *xprev2);
 
 /* y = A x with A the matrix of Eq. (9) (whole-system layout). */
 int sd_apply(sd_handle *h, const double *x, double *y);

@@ -91,6 +91,8 @@ _SIGS = {
     "sd_get_fields": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "sd_get_state": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), _vp, _vp]),
     "sd_set_state": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int64, _vp, _vp]),
+    "sd_get_history": (ctypes.c_int, [_vp, _vp]),
+    "sd_set_history": (ctypes.c_int, [_vp, _vp]),
     "sd_apply": (ctypes.c_int, [_vp, _vp, _vp]),
     "sd_rhs": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp]),
     "sd_solve": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(sd_step_info)]),
@@ -255,6 +257,20 @@ def sd_get_state(h: Handle, x=None, xprev=None, with_prev: bool = False):
 def sd_set_state(h: Handle, t: float, step: int, x, xprev=None) -> None:
     _check(_load().sd_set_state(h.ptr, float(t), int(step), _ptr(x, h.dof),
                                 _ptr(xprev, h.dof) if xprev is not None else None), "sd_set_state")
+
+
+def sd_get_history(h: Handle, xprev2=None):
+    """x^{n-2} of the quadratic extrapolation, or None when the handle does not hold it."""
+    xprev2 = np.empty(h.dof) if xprev2 is None else xprev2
+    rc = _load().sd_get_history(h.ptr, _ptr(xprev2, h.dof))
+    if rc == SD_E_STATE:
+        return None
+    _check(rc, "sd_get_history")
+    return xprev2
+
+
+def sd_set_history(h: Handle, xprev2) -> None:
+    _check(_load().sd_set_history(h.ptr, _ptr(xprev2, h.dof)), "sd_set_history")
 
 
 def sd_apply(h: Handle, x, y=None):

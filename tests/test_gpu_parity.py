@@ -158,16 +158,24 @@ def test_workload_size_residual(sd):
     assert rel(sd.sd_apply(h, xv), o.apply(xv)) <= 1e-13
 
 
-def test_determinism_and_state_roundtrip(sd):
+@pytest.mark.parametrize("extrapolate", [2, 1])
+def test_determinism_and_state_roundtrip(sd, extrapolate):
+    # resume from (t, step, x^n, x^{n-1}) and, for the quadratic extrapolation,
+    # x^{n-2}: bitwise the uninterrupted run
     n = 64
     K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=4)
-    h1 = make(sd, n, 1e-3, K, 1.0, 0.05)
-    h2 = make(sd, n, 1e-3, K, 1.0, 0.05)
-    sd.sd_step(h1, 4)
-    sd.sd_step(h2, 2)
+    h1 = make(sd, n, 1e-3, K, 1.0, 0.05, extrapolate=extrapolate)
+    h2 = make(sd, n, 1e-3, K, 1.0, 0.05, extrapolate=extrapolate)
+    sd.sd_step(h1, 5)
+    sd.sd_step(h2, 3)
     t, st, x, xp = sd.sd_get_state(h2, with_prev=True)
-    h3 = make(sd, n, 1e-3, K, 1.0, 0.05)
+    xpp = sd.sd_get_history(h2)
+    assert (xpp is not None) == (extrapolate == 2)
+    h3 = make(sd, n, 1e-3, K, 1.0, 0.05, extrapolate=extrapolate)
     sd.sd_set_state(h3, t, st, x, xp)
+    if xpp is not None:
+        assert sd.sd_get_history(h3) is None  # cleared by sd_set_state
+        sd.sd_set_history(h3, xpp)
     sd.sd_step(h2, 2)
     sd.sd_step(h3, 2)
     a, b, c = sd.sd_get_state(h1)[2], sd.sd_get_state(h2)[2], sd.sd_get_state(h3)[2]

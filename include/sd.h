@@ -187,12 +187,16 @@ typedef struct {
                           restart still decides convergence.  1/sqrt(2), the classical
                           choice, took the second pass in 5 of 6 iterations.) */
   int32_t extrapolate; /* initial guess of step n+1: 3 x^n - 3 x^{n-1} + x^{n-2} (2,
-                          default; quadratic in time, linear while only two levels are
-                          known), 2 x^n - x^{n-1} (1) or x^n (0).  The stopping test is
-                          unchanged.  Measured on the log-normal workload: steps 20-40
-                          take 2-3 FGMRES iterations instead of 5 at 1024^2 (1.45 against
-                          3.35 ms/step), 2-3 instead of 5 at 2048^2 and 3 instead of 6
-                          at 256^2; the pressure-driven problem 14-17 instead of 16-19. */
+                          default; quadratic in time, lower orders while fewer levels
+                          are known), 4 x^n - 6 x^{n-1} + 4 x^{n-2} - x^{n-3} (3, cubic),
+                          2 x^n - x^{n-1} (1) or x^n (0).  The stopping test is
+                          unchanged.  Measured on the log-normal workload, steps 20-40:
+                          quadratic 2-3 FGMRES iterations against linear 5 at 1024^2
+                          (1.45 against 3.35 ms/step), 2-3 against 5 at 2048^2 and 3
+                          against 6 at 256^2; cubic 3-4 at 1024^2 and 2048^2 (its larger
+                          coefficients amplify the solves' own error), 2-3 at 256^2.  On
+                          the pressure-driven problem: linear 16-19, quadratic 14-17,
+                          cubic 12-16 (9.7 against 11.1 ms/step at 1024^2). */
   int32_t graph;       /* 1 (default): replay each Arnoldi step from a captured CUDA
                           graph, the host checking convergence after each; 2: a whole
                           FGMRES solve as one graph whose restart loop (WHILE node) and
@@ -288,7 +292,9 @@ int sd_get_fields(sd_handle *h, double *u, double *v, double *p_ff, double *p_pm
  * With extrapolate 1 (or 0), resuming from a saved (t, step, x, xprev)
  * reproduces the uninterrupted run bit for bit; with extrapolate 2 the level
  * before, x^{n-2}, is also needed (sd_get_history / sd_set_history), else the
- * first resumed step extrapolates linearly (same tolerance, other bits). */
+ * first resumed step extrapolates linearly (same tolerance, other bits).
+ * With extrapolate 3 the first resumed step is quadratic (x^{n-3} is not
+ * carried), so that run is reproduced to the tolerance, not bitwise. */
 int sd_get_state(sd_handle *h, double *t, int64_t *step, double *x, double *xprev);
 int sd_set_state(sd_handle *h, double t, int64_t step, const double *x, const double *xprev);
 

@@ -152,7 +152,8 @@ struct sd_handle {
   MG<float> mg32;
   MG<double> mg64;
   double *stage = nullptr, *x = nullptr, *xm = nullptr, *b = nullptr, *B0 = nullptr, *B1 = nullptr;
-  double* xmm = nullptr;  // x^{n-2} (extrapolate 2 only)
+  double* xmm = nullptr;  // x^{n-2} (extrapolate >= 2)
+  double* x3 = nullptr;   // x^{n-3} (extrapolate 3)
   double *V = nullptr, *Z = nullptr, *partial = nullptr, *scal = nullptr, *st = nullptr, *flag = nullptr;
   // partitioned coupling: subdomain right-hand side and the IQN-ILS state
   double* bsub = nullptr;
@@ -162,7 +163,8 @@ struct sd_handle {
   double t = 0.0;
   long long step = 0;
   bool have_prev = false;  // x_m holds the state of the previous time level
-  bool have_prev2 = false;  // x_mm holds the one before (extrapolate 2)
+  bool have_prev2 = false;  // x_mm holds the one before (extrapolate >= 2)
+  bool have_prev3 = false;  // x3 holds the one before that (extrapolate 3)
   // kernel timing (sd_profile): event pairs around launches of one kernel class
   int prof_id = -1;
   std::vector<cudaEvent_t> prof_ev;
@@ -237,7 +239,8 @@ void plan_all(sd_handle* h) {
   const long long len = h->g.len;
   h->x = a.take<double>(len);
   h->xm = a.take<double>(len);
-  if (h->opt.extrapolate == 2) h->xmm = a.take<double>(len);
+  if (h->opt.extrapolate >= 2) h->xmm = a.take<double>(len);
+  if (h->opt.extrapolate >= 3) h->x3 = a.take<double>(len);
   h->b = a.take<double>(len);
   h->B0 = a.take<double>(len);
   h->B1 = a.take<double>(len);
@@ -1364,9 +1367,11 @@ int step_rhs(sd_handle* h, cudaStream_t s) {
   const double cm = h->g.h * h->g.h / h->dt;
   const double tn = h->t + h->dt;
   const int lat = h->opt.bc != SD_BC_MMS;
-  if (h->opt.extrapolate == 2 && h->have_prev) {
-    // initial guess 3 x^n - 3 x^{n-1} + x^{n-2} once three levels are known
-    launch_extrapolate3(h->x, h->xm, h->xmm, h->g.len, h->have_prev2 ? 1 : 0, s);
+  if (h->opt.extrapolate >= 2 && h->have_prev) {
+    // the highest order the known levels allow, up to the option's
+    const int order = std::min(h->opt.extrapolate, h->have_prev3 ? 3 : h->have_prev2 ? 2 : 1);
+    launch_extrapolate3(h->x, h->xm, h->xmm, h->x3, h->g.len, order, s);
+    if (h->have_prev2 && h->x3) h->have_prev3 = true;
     h->have_prev2 = true;
     launch_rhs(h->g, lat, cm, h->B0, h->B1, data_scale(h, tn), h->xm, h->b, h->x, s);
   } else if (h->opt.extrapolate && h->have_prev) {
@@ -1407,7 +1412,7 @@ int validate(const sd_grid* grid, double mu, double alpha, double dt, const sd_o
     return SD_E_INVAL;
   if (o->orth < 0 || o->orth > 1 || !(o->reorth_eta > 0) || o->reorth_eta > 1) return SD_E_INVAL;
   if (o->graph < 0 || o->graph > 2) return SD_E_INVAL;
-  if (o->extrapolate < 0 || o->extrapolate > 2) return SD_E_INVAL;
+  if (o->extrapolate < 0 || o->extrapolate > 3) return SD_E_INVAL;
   if (o->darcy_coupled < 0 || o->darcy_coupled > 2) return SD_E_INVAL;
   if (o->tile_rows != 0 && o->tile_rows != 4 && o->tile_rows != 8 && o->tile_rows != 16) return SD_E_INVAL;
   if (o->coupling != SD_MONOLITHIC && o->coupling != SD_PARTITIONED) return SD_E_INVAL;
@@ -1926,6 +1931,7 @@ int sd_set_state(sd_handle* h, double t, int64_t step, const double* x, const do
   CK(cudaStreamSynchronize(h->s));
   h->have_prev = false;
   h->have_prev2 = false;
+  h->have_prev3 = false;
   if (xprev) {
     CKR(copy_in_dense(h, xprev, sd_dof_count(h->n)));
     launch_pack(h->g, h->stage, h->xm, h->s);
@@ -1940,7 +1946,7 @@ int sd_set_state(sd_handle* h, double t, int64_t step, const double* x, const do
 int sd_get_history(sd_handle* h, double* xprev2) {
   if (!h || !xprev2) return SD_E_INVAL;
   std::lock_guard<std::mutex> lk(h->mtx);
-  if (h->opt.extrapolate != 2 || !h->have_prev2) return SD_E_STATE;
+  if (h->opt.extrapolate < 2 || !h->have_prev2) return SD_E_STATE;
   launch_unpack(h->g, h->xmm, h->stage, h->s);
   CKR(copy_out(h, xprev2, h->stage, sd_dof_count(h->n)));
   CK(cudaStreamSynchronize(h->s));
@@ -1950,7 +1956,7 @@ int sd_get_history(sd_handle* h, double* xprev2) {
 int sd_set_history(sd_handle* h, const double* xprev2) {
   if (!h || !xprev2) return SD_E_INVAL;
   std::lock_guard<std::mutex> lk(h->mtx);
-  if (h->opt.extrapolate != 2 || !h->have_prev) return SD_E_STATE;
+  if (h->opt.extrapolate < 2 || !h->have_prev) return SD_E_STATE;
   CKR(copy_in_dense(h, xprev2, sd_dof_count(h->n)));
   launch_pack(h->g, h->stage, h->xmm, h->s);
   CK(cudaStreamSynchronize(h->s));

@@ -437,24 +437,26 @@ void launch_extrapolate(double* x, double* xm, long long len, cudaStream_t s) {
   launch_k(k_extrapolate, dim3((int)(nb < 152 * 16 ? nb : 152 * 16)), dim3(RT), 0, s, x, xm, len);
 }
 
-// Three time levels: x_mm <- x_m, x_m <- x, and x <- 3 x - 3 x_m + x_mm
-// (quadratic extrapolation, quad != 0) or 2 x - x_m (linear, while x_mm is
-// not yet known)
+// Polynomial extrapolation in time over the known levels: the history shifts
+// (x3 <- x_mm, x_mm <- x_m, x_m <- x; x3 may be null) and x becomes the
+// extrapolation of the given order: 1: 2 x - x_m; 2: 3 x - 3 x_m + x_mm;
+// 3: 4 x - 6 x_m + 4 x_mm - x3.
 __global__ void k_extrapolate3(double* __restrict__ x, double* __restrict__ xm, double* __restrict__ xmm,
-                               long long len, int quad) {
+                               double* __restrict__ x3, long long len, int order) {
   griddep_wait();
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len; e += (long long)gridDim.x * blockDim.x) {
-    const double t = x[e], m = xm[e];
-    x[e] = quad ? 3.0 * (t - m) + xmm[e] : 2.0 * t - m;
+    const double t = x[e], m = xm[e], mm = xmm[e];
+    x[e] = order >= 3 ? 4.0 * (t + mm) - 6.0 * m - x3[e] : order == 2 ? 3.0 * (t - m) + mm : 2.0 * t - m;
+    if (x3) x3[e] = mm;
     xmm[e] = m;
     xm[e] = t;
   }
 }
 
-void launch_extrapolate3(double* x, double* xm, double* xmm, long long len, int quad, cudaStream_t s) {
+void launch_extrapolate3(double* x, double* xm, double* xmm, double* x3, long long len, int order, cudaStream_t s) {
   SD_COUNT(1);
   const long long nb = (len + RT - 1) / RT;
-  launch_k(k_extrapolate3, dim3((int)(nb < 152 * 16 ? nb : 152 * 16)), dim3(RT), 0, s, x, xm, xmm, len, quad);
+  launch_k(k_extrapolate3, dim3((int)(nb < 152 * 16 ? nb : 152 * 16)), dim3(RT), 0, s, x, xm, xmm, x3, len, order);
 }
 
 __global__ void k_backsolve(const double* st, int k, int m, double* y, const double* kdev, Bat bt) {

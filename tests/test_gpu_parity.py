@@ -158,6 +158,23 @@ def test_workload_size_residual(sd):
     assert rel(sd.sd_apply(h, xv), o.apply(xv)) <= 1e-13
 
 
+def test_extrapolation_orders_reach_the_same_states(sd):
+    # the initial guess only moves the iteration count: the states of 8 steps
+    # with linear, quadratic and cubic extrapolation agree to the tolerance
+    n = 64
+    K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=14)
+    xs, its = [], []
+    for ex in (1, 2, 3):
+        h = make(sd, n, 1e-3, K, 1.0, 0.05, rtol=1e-11, extrapolate=ex)
+        infos = sd.sd_step(h, 8)
+        assert all(i["status"] == 0 and i["relres"] <= 1e-11 for i in infos)
+        xs.append(sd.sd_get_state(h)[2])
+        its.append(sum(i["iters"] for i in infos[3:]))
+    for x in xs[1:]:
+        assert rel(x, xs[0]) <= 1e-8
+    assert its[1] < its[0]
+
+
 @pytest.mark.parametrize("extrapolate", [2, 1])
 def test_determinism_and_state_roundtrip(sd, extrapolate):
     # resume from (t, step, x^n, x^{n-1}) and, for the quadratic extrapolation,

@@ -187,9 +187,11 @@ typedef struct {
                           restart still decides convergence.  1/sqrt(2), the classical
                           choice, took the second pass in 5 of 6 iterations.) */
   int32_t extrapolate; /* initial guess of step n+1: 3 x^n - 3 x^{n-1} + x^{n-2} (2,
-                          default; quadratic in time, lower orders while fewer levels
-                          are known), 4 x^n - 6 x^{n-1} + 4 x^{n-2} - x^{n-3} (3, cubic),
-                          2 x^n - x^{n-1} (1) or x^n (0).  The stopping test is
+                          default; quadratic in time), 4 x^n - 6 x^{n-1} + 4 x^{n-2} -
+                          x^{n-3} (3, cubic), 2 x^n - x^{n-1} (1) or x^n (0), over solved
+                          time levels only (the initial condition need not lie on the
+                          discrete trajectory): x^1 as the guess of step 2, linear at
+                          step 3, quadratic from step 4.  The stopping test is
                           unchanged.  Measured on the log-normal workload, steps 20-40:
                           quadratic 2-3 FGMRES iterations against linear 5 at 1024^2
                           (1.45 against 3.35 ms/step), 2-3 against 5 at 2048^2 and 3
@@ -289,10 +291,11 @@ int sd_get_fields(sd_handle *h, double *u, double *v, double *p_ff, double *p_pm
  * whole-system vector x^n and the previous time level x^{n-1} used by the
  * extrapolated initial guess (any output may be NULL; a NULL xprev in
  * sd_set_state clears the history, so the next step starts from x^n).
- * With extrapolate 1 (or 0), resuming from a saved (t, step, x, xprev)
- * reproduces the uninterrupted run bit for bit; with extrapolate 2 the level
- * before, x^{n-2}, is also needed (sd_get_history / sd_set_history), else the
- * first resumed step extrapolates linearly (same tolerance, other bits).
+ * sd_set_state takes x (and xprev) as solved time levels.  With extrapolate 1
+ * (or 0), resuming from a saved (t, step, x, xprev) reproduces the
+ * uninterrupted run bit for bit; with extrapolate 2 the level before,
+ * x^{n-2}, is also needed (sd_get_history / sd_set_history), else the first
+ * resumed step extrapolates linearly (same tolerance, other bits).
  * With extrapolate 3 the first resumed step is quadratic (x^{n-3} is not
  * carried), so that run is reproduced to the tolerance, not bitwise. */
 int sd_get_state(sd_handle *h, double *t, int64_t *step, double *x, double *xprev);
@@ -300,9 +303,9 @@ int sd_set_state(sd_handle *h, double t, int64_t step, const double *x, const do
 
 /* x^{n-2} of the quadratic extrapolation (extrapolate 2), dense layout as x.
  * sd_get_history returns SD_E_STATE when the handle does not hold it (fewer
- * than three time levels, extrapolate < 2, or after sd_set_state without
- * sd_set_history); sd_set_history, called after sd_set_state with an xprev,
- * installs it (SD_E_STATE without that xprev or with extrapolate < 2). */
+ * than three solved time levels, extrapolate < 2, or after sd_set_state
+ * without sd_set_history); sd_set_history, called after sd_set_state with an
+ * xprev, installs it (SD_E_STATE without that xprev or with extrapolate < 2). */
 int sd_get_history(sd_handle *h, double *xprev2);
 int sd_set_history(sd_handle *h, const double *xprev2);
 

@@ -163,8 +163,9 @@ struct sd_handle {
   double t = 0.0;
   long long step = 0;
   bool have_prev = false;  // x_m holds the state of the previous time level
-  bool have_prev2 = false;  // x_mm holds the one before (extrapolate >= 2)
-  bool have_prev3 = false;  // x3 holds the one before that (extrapolate 3)
+  // solved time levels among x, x_m, x_mm, x3 (the initial condition is not
+  // one: it need not lie on the discrete trajectory)
+  int levels = 0;
   // kernel timing (sd_profile): event pairs around launches of one kernel class
   int prof_id = -1;
   std::vector<cudaEvent_t> prof_ev;
@@ -1367,16 +1368,11 @@ int step_rhs(sd_handle* h, cudaStream_t s) {
   const double cm = h->g.h * h->g.h / h->dt;
   const double tn = h->t + h->dt;
   const int lat = h->opt.bc != SD_BC_MMS;
-  if (h->opt.extrapolate >= 2 && h->have_prev) {
-    // the highest order the known levels allow, up to the option's
-    const int order = std::min(h->opt.extrapolate, h->have_prev3 ? 3 : h->have_prev2 ? 2 : 1);
+  if (h->opt.extrapolate && h->have_prev) {
+    // extrapolate over the solved levels only, up to the option's order; the
+    // history shifts, and x_m then holds x^n, the mass-term source
+    const int order = std::max(0, std::min(h->opt.extrapolate, h->levels - 1));
     launch_extrapolate3(h->x, h->xm, h->xmm, h->x3, h->g.len, order, s);
-    if (h->have_prev2 && h->x3) h->have_prev3 = true;
-    h->have_prev2 = true;
-    launch_rhs(h->g, lat, cm, h->B0, h->B1, data_scale(h, tn), h->xm, h->b, h->x, s);
-  } else if (h->opt.extrapolate && h->have_prev) {
-    // initial guess 2 x^n - x^{n-1}; x_m then holds x^n, the mass-term source
-    launch_extrapolate(h->x, h->xm, h->g.len, s);
     launch_rhs(h->g, lat, cm, h->B0, h->B1, data_scale(h, tn), h->xm, h->b, h->x, s);
   } else {
     // the previous state is both the mass-term source and the initial guess
@@ -1384,6 +1380,7 @@ int step_rhs(sd_handle* h, cudaStream_t s) {
     launch_rhs(h->g, lat, cm, h->B0, h->B1, data_scale(h, tn), h->x, h->b, h->x, s);
   }
   h->have_prev = true;
+  h->levels = std::min(h->levels + 1, 4);  // the step's solve adds a solved level
   return SD_OK;
 }
 
@@ -1930,13 +1927,13 @@ int sd_set_state(sd_handle* h, double t, int64_t step, const double* x, const do
   launch_pack(h->g, h->stage, h->x, h->s);
   CK(cudaStreamSynchronize(h->s));
   h->have_prev = false;
-  h->have_prev2 = false;
-  h->have_prev3 = false;
+  h->levels = 1;
   if (xprev) {
     CKR(copy_in_dense(h, xprev, sd_dof_count(h->n)));
     launch_pack(h->g, h->stage, h->xm, h->s);
     CK(cudaStreamSynchronize(h->s));
     h->have_prev = true;
+    h->levels = 2;
   }
   h->t = t;
   h->step = step;
@@ -1946,7 +1943,7 @@ int sd_set_state(sd_handle* h, double t, int64_t step, const double* x, const do
 int sd_get_history(sd_handle* h, double* xprev2) {
   if (!h || !xprev2) return SD_E_INVAL;
   std::lock_guard<std::mutex> lk(h->mtx);
-  if (h->opt.extrapolate < 2 || !h->have_prev2) return SD_E_STATE;
+  if (h->opt.extrapolate < 2 || h->levels < 3) return SD_E_STATE;
   launch_unpack(h->g, h->xmm, h->stage, h->s);
   CKR(copy_out(h, xprev2, h->stage, sd_dof_count(h->n)));
   CK(cudaStreamSynchronize(h->s));
@@ -1956,11 +1953,11 @@ int sd_get_history(sd_handle* h, double* xprev2) {
 int sd_set_history(sd_handle* h, const double* xprev2) {
   if (!h || !xprev2) return SD_E_INVAL;
   std::lock_guard<std::mutex> lk(h->mtx);
-  if (h->opt.extrapolate < 2 || !h->have_prev) return SD_E_STATE;
+  if (h->opt.extrapolate < 2 || !h->have_prev || h->levels < 2) return SD_E_STATE;
   CKR(copy_in_dense(h, xprev2, sd_dof_count(h->n)));
   launch_pack(h->g, h->stage, h->xmm, h->s);
   CK(cudaStreamSynchronize(h->s));
-  h->have_prev2 = true;
+  h->levels = 3;
   return SD_OK;
 }
 

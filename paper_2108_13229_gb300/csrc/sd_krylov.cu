@@ -438,17 +438,19 @@ void launch_extrapolate(double* x, double* xm, long long len, cudaStream_t s) {
 }
 
 // Polynomial extrapolation in time over the known levels: the history shifts
-// (x3 <- x_mm, x_mm <- x_m, x_m <- x; x3 may be null) and x becomes the
-// extrapolation of the given order: 1: 2 x - x_m; 2: 3 x - 3 x_m + x_mm;
-// 3: 4 x - 6 x_m + 4 x_mm - x3.
+// (x3 <- x_mm, x_mm <- x_m, x_m <- x; x_mm and x3 may be null) and x becomes
+// the extrapolation of the given order: 0: x (no extrapolation); 1: 2 x - x_m;
+// 2: 3 x - 3 x_m + x_mm; 3: 4 x - 6 x_m + 4 x_mm - x3.  The order never
+// exceeds the history the caller holds (x_mm for 2, x3 for 3).
 __global__ void k_extrapolate3(double* __restrict__ x, double* __restrict__ xm, double* __restrict__ xmm,
                                double* __restrict__ x3, long long len, int order) {
   griddep_wait();
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len; e += (long long)gridDim.x * blockDim.x) {
-    const double t = x[e], m = xm[e], mm = xmm[e];
-    x[e] = order >= 3 ? 4.0 * (t + mm) - 6.0 * m - x3[e] : order == 2 ? 3.0 * (t - m) + mm : 2.0 * t - m;
+    const double t = x[e], m = xm[e], mm = xmm ? xmm[e] : 0.0;
+    x[e] = order >= 3 ? 4.0 * (t + mm) - 6.0 * m - x3[e] : order == 2 ? 3.0 * (t - m) + mm
+                                                         : order == 1 ? 2.0 * t - m : t;
     if (x3) x3[e] = mm;
-    xmm[e] = m;
+    if (xmm) xmm[e] = m;
     xm[e] = t;
   }
 }

@@ -590,7 +590,7 @@ def main():
     ap.add_argument("--mode", default="single", choices=["single", "batch", "serve", "configs", "oracle"])
     ap.add_argument("--count", type=int, default=256, help="batch instances / serving requests")
     ap.add_argument("--threads", type=int, default=32, help="host threads (batch) / running slots (serve)")
-    ap.add_argument("--rates", type=float, nargs="*", default=[10.0, 50.0, 200.0])
+    ap.add_argument("--rates", type=float, nargs="*", default=[10.0, 20.0, 50.0, 100.0, 200.0, 500.0])
     args = ap.parse_args()
     if args.peak_probe:
         return peak_probe()

@@ -1372,7 +1372,7 @@ int step_rhs(sd_handle* h, cudaStream_t s) {
     // extrapolate over the solved levels only, up to the option's order; the
     // history shifts, and x_m then holds x^n, the mass-term source
     const int order = std::max(0, std::min(h->opt.extrapolate, h->levels - 1));
-    launch_extrapolate3(h->x, h->xm, h->xmm, h->x3, h->g.len, order, s);
+    launch_extrapolate(h->x, h->xm, h->xmm, h->x3, h->g.len, order, s);
     launch_rhs(h->g, lat, cm, h->B0, h->B1, data_scale(h, tn), h->xm, h->b, h->x, s);
   } else {
     // the previous state is both the mass-term source and the initial guess

@@ -336,10 +336,9 @@ void launch_mupdate(const double* V, long long vstride, int k, const double* coe
 void launch_reduce(const double* partial, int nblk, int k, int ps, double* out, int accumulate, const double* cond,
                    cudaStream_t s);
 void launch_reorth_decide(const double* nw2, const double* n2a, double eta2, double* flag, cudaStream_t s);
-void launch_extrapolate(double* x, double* xm, long long len, cudaStream_t s);
 // history shift (x3 <- x_mm, x_mm <- x_m, x_m <- x; x3 may be null) and the
 // extrapolation of the given order (1: linear, 2: quadratic, 3: cubic)
-void launch_extrapolate3(double* x, double* xm, double* xmm, double* x3, long long len, int order, cudaStream_t s);
+void launch_extrapolate(double* x, double* xm, double* xmm, double* x3, long long len, int order, cudaStream_t s);
 // generic dot of two vectors: partials then reduce -> out[0]
 void launch_dot(const double* a, const double* b, long long len, double* partial, int nblk, double* out,
                 cudaStream_t s);

@@ -421,28 +421,12 @@ void launch_givens(double* st, int j, int m, const double* hcol1, const double* 
   launch_k(k_givens, dim3(1), dim3(32), 0, s, st, j, m, hcol1, hcol2, nrm2a, nrm2b, reo, flag);
 }
 
-// x_m <- x, x <- 2 x - x_m (linear extrapolation in time of the initial guess)
-__global__ void k_extrapolate(double* __restrict__ x, double* __restrict__ xm, long long len) {
-  griddep_wait();
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len; e += (long long)gridDim.x * blockDim.x) {
-    const double t = x[e];
-    x[e] = 2.0 * t - xm[e];
-    xm[e] = t;
-  }
-}
-
-void launch_extrapolate(double* x, double* xm, long long len, cudaStream_t s) {
-  SD_COUNT(1);
-  const long long nb = (len + RT - 1) / RT;
-  launch_k(k_extrapolate, dim3((int)(nb < 152 * 16 ? nb : 152 * 16)), dim3(RT), 0, s, x, xm, len);
-}
-
 // Polynomial extrapolation in time over the known levels: the history shifts
 // (x3 <- x_mm, x_mm <- x_m, x_m <- x; x_mm and x3 may be null) and x becomes
 // the extrapolation of the given order: 0: x (no extrapolation); 1: 2 x - x_m;
 // 2: 3 x - 3 x_m + x_mm; 3: 4 x - 6 x_m + 4 x_mm - x3.  The order never
 // exceeds the history the caller holds (x_mm for 2, x3 for 3).
-__global__ void k_extrapolate3(double* __restrict__ x, double* __restrict__ xm, double* __restrict__ xmm,
+__global__ void k_extrapolate(double* __restrict__ x, double* __restrict__ xm, double* __restrict__ xmm,
                                double* __restrict__ x3, long long len, int order) {
   griddep_wait();
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len; e += (long long)gridDim.x * blockDim.x) {
@@ -455,10 +439,10 @@ __global__ void k_extrapolate3(double* __restrict__ x, double* __restrict__ xm, 
   }
 }
 
-void launch_extrapolate3(double* x, double* xm, double* xmm, double* x3, long long len, int order, cudaStream_t s) {
+void launch_extrapolate(double* x, double* xm, double* xmm, double* x3, long long len, int order, cudaStream_t s) {
   SD_COUNT(1);
   const long long nb = (len + RT - 1) / RT;
-  launch_k(k_extrapolate3, dim3((int)(nb < 152 * 16 ? nb : 152 * 16)), dim3(RT), 0, s, x, xm, xmm, x3, len, order);
+  launch_k(k_extrapolate, dim3((int)(nb < 152 * 16 ? nb : 152 * 16)), dim3(RT), 0, s, x, xm, xmm, x3, len, order);
 }
 
 __global__ void k_backsolve(const double* st, int k, int m, double* y, const double* kdev, Bat bt) {

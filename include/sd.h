@@ -279,8 +279,8 @@ int sd_create(const sd_grid *grid, double mu, const double *K, double alpha_bj, 
               sd_handle **out);
 
 /* Advance nsteps implicit-Euler steps (Sec. 2): right-hand side from the
- * previous velocities, then FGMRES to rtol, warm-started from the previous
- * solution.  info: NULL or nsteps entries.  Returns the first non-OK step
+ * previous velocities, then FGMRES to rtol, warm-started from the
+ * extrapolation in time of the previous solutions (sd_options.extrapolate).  info: NULL or nsteps entries.  Returns the first non-OK step
  * status (the state advances regardless). */
 int sd_step(sd_handle *h, int32_t nsteps, sd_step_info *info);
 

@@ -126,12 +126,13 @@ def test_mms_time_stepping(sd, precision):
 @pytest.mark.parametrize("n", [64, 128])
 def test_lognormal_time_stepping(sd, n, precision, coarsest):
     # the workload's physics (mu = 1e-3, ln K ~ N(-4, 1), corr. 16 cells) on grids the oracle factors;
-    # coarsest 16: the dense 16 x 16 solve spread over all SMs, 4: the fused single-CTA coarse cycle
+    # coarsest 16: the dense 16 x 16 solve spread over all SMs, 4: the fused single-CTA coarse cycle;
+    # five steps, so that the default quadratic extrapolation starts (step 4)
     K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=0)
     o = O.Oracle(n, 1e-3, 1.0, 0.05, K)
-    xr = o.run(O.exact(n, 0.0, 1e-3), 0.0, 3)
+    xr = o.run(O.exact(n, 0.0, 1e-3), 0.0, 5)
     h = make(sd, n, 1e-3, K, 1.0, 0.05, precision, rtol=1e-12, coarsest=coarsest)
-    infos = sd.sd_step(h, 3)
+    infos = sd.sd_step(h, 5)
     assert all(i["status"] == 0 for i in infos)
     _, _, x = sd.sd_get_state(h)
     for k, e in fields_rel(x, xr, n).items():

@@ -163,6 +163,10 @@ struct sd_handle {
   double t = 0.0;
   long long step = 0;
   bool have_prev = false;  // x_m holds the state of the previous time level
+  // per-block residuals of the last solve, queued for the caller's next
+  // synchronisation (queue_block_residuals / finish_block_residuals)
+  bool blk_pending = false;
+  double blk_bnorm = 0.0;
   // solved time levels among x, x_m, x_mm, x3 (the initial condition is not
   // one: it need not lie on the discrete trajectory)
   int levels = 0;
@@ -943,6 +947,25 @@ int block_residuals(sd_handle* h, double bnorm, sd_step_info* info) {
   return SD_OK;
 }
 
+// The same without waiting: the dots and their copy are queued, and
+// finish_block_residuals fills them in after the caller's next
+// synchronisation of the stream (one host wait less per step).
+int queue_block_residuals(sd_handle* h, double bnorm) {
+  block_residual_dots(h);
+  CK(cudaMemcpyAsync(h->hflag + 12, h->scal + sd_handle::S_BLK, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  h->blk_pending = true;
+  h->blk_bnorm = bnorm;
+  return SD_OK;
+}
+void finish_block_residuals(sd_handle* h, sd_step_info* info) {
+  if (!h->blk_pending) return;
+  h->blk_pending = false;
+  const double d = h->blk_bnorm > 0 ? h->blk_bnorm : 1.0;
+  info->relres_v = std::sqrt(h->hflag[12]) / d;
+  info->relres_pff = std::sqrt(h->hflag[13]) / d;
+  info->relres_pm = std::sqrt(h->hflag[14]) / d;
+}
+
 // ------------------------------------------------- FGMRES as one graph
 // Graph option 2: fgmres() below as one CUDA graph per solve mode, its
 // decisions taken on the device.  Top level: ||b||, the first true residual
@@ -1161,20 +1184,28 @@ int fgmres(sd_handle* h, const double* b, double* x, sd_step_info* info, int mod
   const long long len = rg.len, vs = h->lenA, o = rg.off;
   const int m = h->m, nb = reduce_blocks(len);
   double* sc = h->scal;
+  // ||b|| and the first true residual V_0 = b - A x, read back together (S_B2
+  // and S_BN are adjacent slots)
   launch_dot(b + o, b + o, len, h->partial, nb, sc + sd_handle::S_BN, s);
-  CK(cudaMemcpyAsync(h->hflag + 4, sc + sd_handle::S_BN, sizeof(double), cudaMemcpyDeviceToHost, s));
+  apply_op(h, mode, x, b, h->V);
+  launch_dot(h->V + o, h->V + o, len, h->partial, nb, sc + sd_handle::S_B2, s);
+  CK(cudaMemcpyAsync(h->hflag + 5, sc + sd_handle::S_B2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  const double bnorm = std::sqrt(h->hflag[4]);
+  const double bnorm = std::sqrt(h->hflag[6]);
   const double tol = mode_rtol(h, mode) * (bnorm > 0 ? bnorm : 1.0);
   const double acc = mode_accept(h, mode);
   const double acc_tol = acc > 0 ? acc * (bnorm > 0 ? bnorm : 1.0) : -1.0;
   int iters = 0, restarts = 0, status = SD_OK, reorths = 0;
   double relres = 0.0, prev = 0.0;
+  bool first = true;
   for (;;) {
-    apply_op(h, mode, x, b, h->V);  // V_0 = b - A x
-    launch_dot(h->V + o, h->V + o, len, h->partial, nb, sc + sd_handle::S_B2, s);
-    CK(cudaMemcpyAsync(h->hflag + 5, sc + sd_handle::S_B2, sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    if (!first) {
+      apply_op(h, mode, x, b, h->V);  // V_0 = b - A x
+      launch_dot(h->V + o, h->V + o, len, h->partial, nb, sc + sd_handle::S_B2, s);
+      CK(cudaMemcpyAsync(h->hflag + 5, sc + sd_handle::S_B2, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+    }
+    first = false;
     const double beta = std::sqrt(h->hflag[5]);
     const double beta_prev = prev;
     prev = beta;
@@ -1241,7 +1272,7 @@ int fgmres(sd_handle* h, const double* b, double* x, sd_step_info* info, int mod
     info->reorths = reorths;
     // the last residual b - A x is still in V_0 unless a cycle ended on NaN/Inf
     info->relres_v = info->relres_pff = info->relres_pm = -1.0;
-    if (mode == MODE_MONO && status != SD_E_NUMERIC) CKR(block_residuals(h, bnorm, info));
+    if (mode == MODE_MONO && status != SD_E_NUMERIC) CKR(queue_block_residuals(h, bnorm));
   }
   return status;
 }
@@ -1876,6 +1907,7 @@ int sd_step(sd_handle* h, int32_t nsteps, sd_step_info* info) {
     if (rc == SD_E_CUDA || rc == SD_E_NOMEM) return rc;
     CK(cudaEventRecord(h->e1, h->s));
     CK(cudaEventSynchronize(h->e1));
+    finish_block_residuals(h, &si);
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, h->e0, h->e1));
     si.ms = ms;
@@ -2011,6 +2043,7 @@ int sd_solve(sd_handle* h, const double* b, double* x, sd_step_info* info) {
   launch_unpack(h->g, xs, h->stage, h->s);
   CKR(copy_out(h, x, h->stage, nd));
   CK(cudaEventSynchronize(h->e1));
+  finish_block_residuals(h, &si);
   float ms = 0.f;
   CK(cudaEventElapsedTime(&ms, h->e0, h->e1));
   si.ms = ms;

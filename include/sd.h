@@ -160,10 +160,8 @@ typedef struct {
   int32_t precond;     /* SD_TRI_SCHUR | SD_PV_BJ_I | SD_PV_BGS_I (default SD_TRI_SCHUR) */
   int32_t bc;          /* SD_BC_MMS (default) | SD_BC_MMS_TRACTION | SD_BC_PAPER */
   int32_t cheb_degree; /* Chebyshev smoothing steps before and after each coarse
-                          correction, 1..8 (default 3; on the log-normal 1024^2 workload
-                          4 steps are 8 % slower per step over the first 30 steps, 5
-                          iterations each, and faster only later, when they bring the
-                          iterations down to 4) */
+                          correction, 1..8 (default 3; on the log-normal workload 4
+                          steps measured within 2 % of 3 and 2 steps 7-12 % slower) */
   int32_t cheb_degree_coarse; /* the same below the finest level (0: cheb_degree) */
   int32_t schur_degree;       /* the same in the pressure-Laplacian block (0: as above;
                                  default 1, one damped-Jacobi step) */
@@ -175,8 +173,8 @@ typedef struct {
   double cheb_ratio;   /* Chebyshev interval [lmax/ratio, 1.1 lmax] (default 8) */
   int32_t schur_mass;  /* SD_TRI_SCHUR: add the mass-dominated part (1/dt) L_p^-1 of
                           the Schur complement, L_p = B^T B / h^2 (default 1) */
-  int32_t fuse_coarse; /* run all levels with <= 32 cells per side in one single-CTA
-                          kernel (default 1) */
+  int32_t fuse_coarse; /* with coarsest < 16: run all levels with <= 16 cells per side
+                          in one single-CTA kernel (default 1) */
   int32_t orth;        /* 0: classical Gram-Schmidt twice (CGS2); 1 (default): the second
                           pass only when ||w'|| < reorth_eta ||w|| (DGKS test, decided
                           on the device) */
@@ -234,7 +232,11 @@ typedef struct {
                                error: with solves to rtol = 1e-10 and coupling_eps = 1e-9 on
                                1024^2 lognormal K, 26 of 60 steps ran into coupling_max
                                (interface updates below the solves' tolerance returned no
-                               change), with 1e-12 every step took 5-6 iterations. */
+                               change), with 1e-12 every step took 5-6 iterations.  A
+                               subdomain solve whose restart cycle does not halve its true
+                               residual has reached its rounding floor and stops there,
+                               converged if the residual meets rtol.  The iteration also
+                               stops when no subdomain solve moved its state. */
   double bc_dp;        /* SD_BC_PAPER: amplitude of the inflow pressure (default 1) */
   double bc_tend;      /* SD_BC_PAPER: rise time T of the inflow pressure (default 0:
                           25 time steps) */

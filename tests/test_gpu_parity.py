@@ -139,10 +139,11 @@ def test_lognormal_time_stepping(sd, n, precision, coarsest):
         assert e <= 1e-8, (k, e)
 
 
-def test_workload_size_residual(sd):
-    # 1024 x 1024 cells, the benchmark's launch configuration (mixed precision, rtol 1e-10):
-    # the oracle recomputes ||b - A x|| / ||b|| of the GPU state with its own CSR matrix
-    n = 1024
+@pytest.mark.parametrize("n", [1024, 2048])
+def test_workload_size_residual(sd, n):
+    # 1024 x 1024 cells, the benchmark's launch configuration (mixed precision, rtol 1e-10),
+    # and the 2048 x 2048 workload: the oracle recomputes ||b - A x|| / ||b|| of the GPU state
+    # with its own CSR matrix
     K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=0)
     o = O.Oracle(n, 1e-3, 1.0, 0.05, K)
     h = make(sd, n, 1e-3, K, 1.0, 0.05, 1)

@@ -1660,18 +1660,26 @@ int fgmres_lockstep(Lockstep& L, std::vector<sd_step_info>& si) {
   std::vector<char> live(B, 1), cyc(B, 0), numeric(B, 0);
   L.act.assign(B, 1);
   CKR(set_act(L, s));
+  // ||b|| and the first true residual, gathered together (S_B2, S_BN adjacent)
   launch_dot(h->b, h->b, len, h->partial, nb, sc + sd_handle::S_BN, s);
-  CKR(gather(L, sc + sd_handle::S_BN, 1, s));
+  launch_apply_full(c, h->x, h->b, h->V, s);  // V_0 = b - A x
+  launch_dot(h->V, h->V, len, h->partial, nb, sc + sd_handle::S_B2, s);
+  CKR(gather(L, sc + sd_handle::S_B2, 2, s));
   for (int i = 0; i < B; ++i) {
-    bnorm[i] = std::sqrt(L.gat_host[i]);
+    bnorm[i] = std::sqrt(L.gat_host[(size_t)i * 2 + 1]);
     tol[i] = h->opt.rtol * (bnorm[i] > 0 ? bnorm[i] : 1.0);
+    L.gat_host[i] = L.gat_host[(size_t)i * 2];  // beta^2 where the loop reads it
   }
+  bool first = true;
   for (;;) {
-    for (int i = 0; i < B; ++i) L.act[i] = live[i];
-    CKR(set_act(L, s));
-    launch_apply_full(c, h->x, h->b, h->V, s);  // V_0 = b - A x
-    launch_dot(h->V, h->V, len, h->partial, nb, sc + sd_handle::S_B2, s);
-    CKR(gather(L, sc + sd_handle::S_B2, 1, s));
+    if (!first) {
+      for (int i = 0; i < B; ++i) L.act[i] = live[i];
+      CKR(set_act(L, s));
+      launch_apply_full(c, h->x, h->b, h->V, s);  // V_0 = b - A x
+      launch_dot(h->V, h->V, len, h->partial, nb, sc + sd_handle::S_B2, s);
+      CKR(gather(L, sc + sd_handle::S_B2, 1, s));
+    }
+    first = false;
     bool any = false;
     for (int i = 0; i < B; ++i) {
       cyc[i] = 0;

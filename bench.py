@@ -259,12 +259,19 @@ def bench_batch(sd, count: int, steps: int, threads: int, seed: int = 0, lockste
             "iters_per_step_mean": float(np.mean(its)), "max_relres": max(i["relres"] for inf in infos for i in inf)}
 
 
+_SERVE_K = {}
+
+
 def bench_serve(sd, rate: float, count: int, max_running: int, budget_gb: float = 120.0, seed: int = 0,
                 lockstep: bool = False):
     """Poisson arrivals of time-dependent runs submitted to the continuous-batching server."""
     from paper_2108_13229_gb300 import inputs as I
     reqs = I.serving_requests(count, rate, seed=seed)
-    Ks = [wl.K() for _, wl in reqs]
+    # the rates share their draws of grid, length and K seed: draw each field once
+    for _, wl in reqs:
+        if (wl.n, wl.K_seed) not in _SERVE_K:
+            _SERVE_K[(wl.n, wl.K_seed)] = wl.K()
+    Ks = [_SERVE_K[(wl.n, wl.K_seed)] for _, wl in reqs]
     srv = sd.sd_server_create(int(budget_gb * (1 << 30)), max_running, lockstep=lockstep)
     t0 = time.perf_counter()
     tickets = []

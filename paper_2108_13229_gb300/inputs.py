@@ -98,8 +98,9 @@ def batch_instances(count: int = 256, seed: int = 0, sizes=(64, 128, 256, 512), 
 def serving_requests(count: int, rate: float, seed: int = 0, n_min: int = 32, n_max: int = 1024):
     """Poisson arrivals (rate per second) of runs with log-uniform grids and 5-50 steps.
 
-    Grid sizes are rounded to m * 2^k with m in 4..8 so that every hierarchy
-    coarsens to at most 8 x 8 cells.
+    A log-uniform draw in [n_min, n_max) is rounded to the nearest m * 2^k with
+    m in 4..8 and 2^k <= draw / 4, so that every hierarchy halves down to an
+    m x m grid of at most 8 x 8 cells (n = 40, 48, 56, ..., 896, 1024).
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     t = 0.0
@@ -107,7 +108,7 @@ def serving_requests(count: int, rate: float, seed: int = 0, n_min: int = 32, n_
     for k in range(count):
         t += float(rng.exponential(1.0 / rate))
         n_raw = math.exp(rng.uniform(math.log(n_min), math.log(n_max)))
-        kexp = max(0, int(math.floor(math.log2(n_raw / 8.0))))
+        kexp = max(0, int(math.floor(math.log2(n_raw / 4.0))))
         m = max(4, min(8, int(round(n_raw / 2 ** kexp))))
         n = m * 2 ** kexp
         steps = int(rng.integers(5, 51))

@@ -343,7 +343,9 @@ void sd_destroy(sd_handle *h);
  * single instances run concurrently, each on its own stream, from up to
  * max_threads host threads (0 = one per group).  Each instance does exactly
  * the arithmetic of its single-instance sd_step, so its result is bitwise
- * identical to running it alone.  Returns the first non-OK status.
+ * identical to running it alone.  Returns the first non-OK status;
+ * SD_E_INVAL, before any work, for a NULL handle, a negative nsteps or a
+ * handle listed twice.
  * sd_solve_batch_ex with flags = 0 runs every instance on its own stream
  * and host thread instead (no lockstep groups). */
 #define SD_BATCH_LOCKSTEP 1

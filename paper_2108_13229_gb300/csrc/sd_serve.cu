@@ -107,14 +107,17 @@ void run_job(sd_server* S, Job* J) {
   if (rc == SD_OK) {
     std::vector<sd_step_info> info(J->req.nsteps > 0 ? J->req.nsteps : 1);
     rc = sd_step(h, J->req.nsteps, info.data());
-    int done = 0, it = 0;
+    // a CUDA or allocation error ends sd_step early: the handle's step count
+    // says how many steps (and info entries) were completed
+    int64_t done = 0;
+    sd_get_state(h, nullptr, &done, nullptr, nullptr);
+    int it = 0;
     double mr = 0.0;
-    for (int k = 0; k < J->req.nsteps; ++k) {
-      ++done;
+    for (int64_t k = 0; k < done; ++k) {
       it += info[k].iters;
       if (info[k].relres > mr) mr = info[k].relres;
     }
-    J->res.steps_done = done;
+    J->res.steps_done = (int32_t)done;
     J->res.total_iters = it;
     J->res.max_relres = mr;
     if (J->req.keep_fields) {
@@ -264,6 +267,11 @@ int sd_solve_batch_ex(sd_handle* const* hs, int32_t count, const int32_t* nsteps
   if (count == 0) return SD_OK;
   for (int k = 0; k < count; ++k)
     if (!hs[k] || nsteps[k] < 0) return SD_E_INVAL;
+  {  // a handle listed twice would be stepped twice (or by two groups at once)
+    std::vector<sd_handle*> order(hs, hs + count);
+    std::sort(order.begin(), order.end());
+    if (std::adjacent_find(order.begin(), order.end()) != order.end()) return SD_E_INVAL;
+  }
   // work items: lockstep groups of compatible handles (same nsteps), or
   // single handles
   std::vector<std::vector<int>> items;

@@ -128,3 +128,34 @@ def test_option_validation_without_gpu(sd):
         o = sd.sd_options_default()
         o.bc = bc
         assert sd._load().sd_memory_estimate(ctypes.byref(g), ctypes.byref(o)) > 0
+
+
+def test_batch_validation_without_gpu(sd):
+    # rejected before any handle is read: NULL handles, negative step counts,
+    # a handle listed twice (the stand-in handles point at zeroed host memory)
+    lib = sd._load()
+    blob = ctypes.create_string_buffer(1 << 16)
+    a, b = ctypes.addressof(blob), ctypes.addressof(blob) + 4096
+    for hs, ns in [([a, None], [1, 1]), ([a, b], [1, -1]), ([a, a], [1, 1]), ([a, b, a], [2, 2, 2])]:
+        arr = (ctypes.c_void_p * len(hs))(*hs)
+        steps = (ctypes.c_int32 * len(ns))(*ns)
+        for flags in (0, sd.SD_BATCH_LOCKSTEP):
+            assert lib.sd_solve_batch_ex(arr, len(hs), steps, None, 0, flags) == sd.SD_E_INVAL, (hs, ns)
+    assert lib.sd_solve_batch_ex(None, 0, None, None, 0, 0) == sd.SD_OK
+    assert lib.sd_solve_batch_ex(None, 1, None, None, 0, 0) == sd.SD_E_INVAL
+
+
+def test_server_admission_without_gpu(sd):
+    # the server checks every request on the host at submission: bad sizes and
+    # step counts, and runs whose device memory exceeds the whole budget
+    with pytest.raises(sd.SdError) as e:
+        sd.sd_server_create(0, 2)
+    assert e.value.code == sd.SD_E_INVAL
+    srv = sd.sd_server_create(int(sd.sd_memory_estimate(32) * 1.5), 2)
+    for n, steps, code in [(64, 5, sd.SD_E_NOMEM), (34, 5, sd.SD_E_INVAL), (32, -1, sd.SD_E_INVAL)]:
+        with pytest.raises(sd.SdError) as e:
+            sd.sd_submit(srv, n, 1e-3, np.ones((n, n)), 1.0, 0.1, steps)
+        assert e.value.code == code, (n, steps)
+    assert sd.sd_poll(srv, 12345)[0] == sd.SD_E_STATE
+    sd.sd_server_drain(srv)  # nothing queued: returns at once
+    del srv

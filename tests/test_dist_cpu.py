@@ -1,5 +1,6 @@
-"""The N > 1 host path of bench.py on CPU: world-size-2 gloo ranks, each an
-independent replica, aggregated as (sum of units) / (max of seconds)."""
+"""The host paths of bench.py on CPU: world-size-2 gloo ranks, each an
+independent replica, aggregated as (sum of units) / (max of seconds); and the
+reference arm (the oracle on a bounded sample), alone and under torchrun."""
 import os
 import socket
 import sys
@@ -46,3 +47,43 @@ def test_replica_aggregation_gloo():
         assert p.exitcode == 0
     for rank, units, secs in res:
         assert units == 3000.0 and secs == 1.5
+
+
+def _json_lines(out):
+    import json
+    return [json.loads(l) for l in out.splitlines() if l.startswith("{")]
+
+
+def _check_reference_line(r, n_gpus):
+    assert r["impl"] == "reference" and r["n_gpus"] == n_gpus and r["steps"] == 1 and r["warmup"] == 3
+    assert r["value"] > 0 and r["unit"] == "DOF*steps/s" and r["higher_is_better"] is True
+    assert r["dtype"] == "f64" and r["data"] == "synthetic" and "1024x1024" in r["config"]["workload"]
+    cb = r["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == r["value"] and cb["sample"]
+    assert r["e2e"] == {"value": r["value"], "unit": r["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_one_process():
+    # bench.py --impl reference: the oracle on a bounded sample, one JSON line
+    import subprocess
+    p = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = _json_lines(p.stdout)
+    assert len(lines) == 1
+    _check_reference_line(lines[0], 1)
+
+
+def test_reference_arm_two_ranks_gloo():
+    # under torchrun with two ranks only rank 0 runs the oracle and prints;
+    # the other rank exits 0 without work
+    import subprocess
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
+           "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "3"]
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    p = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=300, env=env)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = _json_lines(p.stdout)
+    assert len(lines) == 1
+    _check_reference_line(lines[0], 2)

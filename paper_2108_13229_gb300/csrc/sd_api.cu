@@ -2144,7 +2144,7 @@ const char* sd_strerror(int code) {
     case SD_E_NOMEM: return "out of device memory or HBM budget";
     case SD_E_NOCONV: return "FGMRES did not reach rtol within max_iters";
     case SD_E_NUMERIC: return "NaN/Inf in the Krylov recurrence";
-    case SD_E_TIMEOUT: return "bounded wait timed out";
+    case SD_E_TIMEOUT: return "timeout (reserved, not returned)";
     case SD_E_CUDA: return g_errmsg[0] ? g_errmsg : "CUDA error";
     case SD_E_STATE: return "unknown ticket or invalid state";
     default: return "unknown error";

@@ -461,10 +461,13 @@ int sd_apply_noalloc(const sd_grid *grid, double mu, const double *K, double alp
  *   K          host or device permeability as in sd_create;
  *   cache_path text file (NULL or "": no cache).  A line matching this device,
  *              n, precision, precond, darcy_coupled, restart, bc, coupling and rtol is
- *              returned without timing; otherwise the winner is appended;
+ *              returned without timing (the last such line whose options
+ *              sd_create accepts); otherwise the winner is appended;
  *   best       receives *base with the three tuned fields;
  *   best_ms    (may be NULL) mean device ms per step of the winner.
- * Costs about 18 instance setups plus 18 (nsteps + 2) steps on a cache miss.
+ * Costs up to 27 instance setups plus 27 (nsteps + 4) steps on a cache miss
+ * (9 of each with FP64 V-cycles or without tiling, fewer on grids too small
+ * to coarsen to the deeper candidates).
  * Errors: SD_E_INVAL, SD_E_NOCONV (no candidate converged). */
 int sd_autotune(const sd_grid *grid, double mu, const double *K, double alpha_bj, double dt, const sd_options *base,
                 int32_t nsteps, const char *cache_path, sd_options *best, double *best_ms);

@@ -58,9 +58,15 @@ bool cache_lookup(const char* path, const Key& k, sd_options* o, double* ms) {
     if (k.dev != dev || n != k.n || pr != k.precision || pc != k.precond || dc != k.darcy_coupled ||
         rs != k.restart || bc != k.bc || cp != k.coupling || rt != k.rtol)
       continue;
-    o->tile_rows = tr;  // the last matching line wins
-    o->coarsest = co;
-    o->cheb_degree = cd;
+    // a line whose options sd_create would reject (an edited or damaged
+    // file) is skipped
+    sd_options c = *o;
+    c.tile_rows = tr;
+    c.coarsest = co;
+    c.cheb_degree = cd;
+    const sd_grid g{k.n, k.n};
+    if (sd_memory_estimate(&g, &c) < 0) continue;
+    *o = c;  // the last valid matching line wins
     *ms = t;
     found = true;
   }

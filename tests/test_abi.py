@@ -159,3 +159,41 @@ def test_server_admission_without_gpu(sd):
     assert sd.sd_poll(srv, 12345)[0] == sd.SD_E_STATE
     sd.sd_server_drain(srv)  # nothing queued: returns at once
     del srv
+
+
+def test_autotune_cache_without_gpu(sd, tmp_path):
+    # a cache hit returns the stored choice with no device work; lines for
+    # another key, or with options sd_create would reject, are skipped
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("the cache key names the device; this test writes the no-device key")
+    n = 32
+    K = np.ones((n, n))
+    o = sd.sd_options_default()
+    key = "sdtune2 unknown %d %d %d %d %d %d %d %.17g" % (n, o.precision, o.precond, o.darcy_coupled, o.restart,
+                                                         o.bc, o.coupling, o.rtol)
+    path = tmp_path / "tune.txt"
+    path.write_text("\n".join([
+        "garbage line",
+        key + " 8 4 2 1.5",
+        key.replace(" %d " % n, " 64 ", 1) + " 16 16 3 0.5",   # another grid size
+        key.replace("%.17g" % o.rtol, "1e-08") + " 16 8 4 0.25",  # another rtol
+        key + " 12 4 2 0.1",                                     # tile_rows 12 is invalid
+        key + " 8 1 2 0.1",                                      # coarsest 1 is invalid
+    ]) + "\n")
+    best, ms = sd.sd_autotune(n, 1.0, K, 1.0, 0.1, None, 3, str(path))
+    assert (best.tile_rows, best.coarsest, best.cheb_degree, ms) == (8, 4, 2, 1.5)
+    assert best.rtol == o.rtol and best.restart == o.restart
+    path.write_text(key + " 8 4 2 1.5\n" + key + " 16 8 3 0.75\n")
+    best, ms = sd.sd_autotune(n, 1.0, K, 1.0, 0.1, None, 3, str(path))
+    assert (best.tile_rows, best.coarsest, best.cheb_degree, ms) == (16, 8, 3, 0.75)  # the last line wins
+    with pytest.raises(sd.SdError) as e:
+        sd.sd_autotune(n, 1.0, K, 1.0, 0.1, None, 0, str(path))
+    assert e.value.code == sd.SD_E_INVAL
+    # only invalid matching lines: the tuner times candidates, which cannot
+    # run without a device, so none converges and nothing is appended
+    path.write_text(key + " 12 4 2 0.1\n")
+    with pytest.raises(sd.SdError) as e:
+        sd.sd_autotune(n, 1.0, K, 1.0, 0.1, None, 3, str(path))
+    assert e.value.code == sd.SD_E_NOCONV
+    assert path.read_text() == key + " 12 4 2 0.1\n"

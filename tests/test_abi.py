@@ -197,3 +197,13 @@ def test_autotune_cache_without_gpu(sd, tmp_path):
         sd.sd_autotune(n, 1.0, K, 1.0, 0.1, None, 3, str(path))
     assert e.value.code == sd.SD_E_NOCONV
     assert path.read_text() == key + " 12 4 2 0.1\n"
+
+
+def test_apply_noalloc_validation_without_gpu(sd):
+    # checked on the host before any device work: the fixed capacity, the
+    # physical parameters, and device memory for every array
+    for n, mu, dt in [(sd.SD_NOALLOC_MAX_N * 2, 1.0, 0.1), (8, -1.0, 0.1), (8, 1.0, 0.0), (8, 1.0, 0.1)]:
+        d = 4 * n * n + 2 * n
+        with pytest.raises(sd.SdError) as e:
+            sd.sd_apply_noalloc(n, mu, np.ones(n * n), 1.0, dt, np.zeros(d), np.zeros(d))
+        assert e.value.code == sd.SD_E_INVAL, (n, mu, dt)

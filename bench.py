@@ -540,7 +540,7 @@ def bench_configs(sd, torch, steps_small: int = 10, steps_big: int = 5):
     return out
 
 
-def oracle_scan(sizes=(32, 64, 128), steps: int = 5, resid_sizes=(1024,)):
+def oracle_scan(sizes=(32, 64, 128, 256), steps: int = 5, resid_sizes=(1024, 2048)):
     """The oracle on one host core: banded-LU factorisation and per-step solves at small grids, and the CSR
     residual evaluator (assembly + one residual) at workload sizes the LU cannot hold."""
     import oracle as O
@@ -570,7 +570,16 @@ def oracle_scan(sizes=(32, 64, 128), steps: int = 5, resid_sizes=(1024,)):
         rows.append({"n": n, "dof": 4 * n * n + 2 * n, "assemble_and_rhs_s": t1 - t0, "residual_s": t2 - t1,
                      "note": "banded LU infeasible (memory); residual evaluator only"})
     import platform
-    return {"metric": "oracle timing on one host core", "cpu": platform.processor() or platform.machine(),
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"metric": "oracle timing on one host core", "cpu": model, "arch": platform.machine(),
             "cores_used": 1, "rows": rows}
 
 

@@ -69,3 +69,22 @@ def test_workload_recipes():
     t = [ta for ta, _ in reqs]
     assert len(reqs) == 50 and t == sorted(t)
     assert all(32 <= w.n <= 1024 and 5 <= w.steps <= 50 for _, w in reqs)
+
+
+def test_serving_mix_is_log_uniform():
+    # 4000 requests at 50 req/s: sizes m * 2^k (m in 4..8) spanning 32..1024
+    # log-uniformly (a fifth of the draws at 512 or above, median near the
+    # geometric mean 181), lengths 5..50 steps, exponential inter-arrival
+    # times with mean 1 / rate
+    reqs = I.serving_requests(4000, 50.0, seed=1)
+    n = np.array([w.n for _, w in reqs])
+    assert n.min() == 32 and n.max() == 1024
+    for v in np.unique(n).tolist():
+        assert any(v % 2**k == 0 and 4 <= v // 2**k <= 8 for k in range(11)), v
+    assert 0.15 < np.mean(n >= 512) < 0.25
+    assert 128 <= np.median(n) <= 256
+    steps = np.array([w.steps for _, w in reqs])
+    assert steps.min() == 5 and steps.max() == 50
+    t = np.array([ta for ta, _ in reqs])
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert np.all(gaps > 0) and abs(gaps.mean() * 50.0 - 1.0) < 0.05

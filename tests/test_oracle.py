@@ -11,7 +11,9 @@
 * second-order convergence to the manufactured solution, and loss of it when
   a coupling parameter is planted inconsistently;
 * the Schur complement of the (v, p_ff) block at its viscous and mass limits,
-  the two terms of the preconditioner's Schur block.
+  the two terms of the preconditioner's Schur block;
+* definiteness of the viscous and Darcy blocks, the half-volume mass rows, and
+  decay of the kinetic energy without data.
 """
 import os
 
@@ -358,3 +360,57 @@ def test_schur_mass_limit_is_cell_laplacian(n):
         gaps.append(np.linalg.norm(S - dt * L) / np.linalg.norm(dt * L))
     assert gaps[0] < 1e-5 and gaps[1] < 1e-7
     assert 50 < gaps[0] / gaps[1] < 200
+
+
+# ---------------------------------------------------------------------------
+# definiteness and energy: what the symmetry pin cannot see (a sign slip in a
+# symmetric term, e.g. the wall shear or the eliminated BJS slip, keeps S*A
+# symmetric but makes the viscous block indefinite)
+# ---------------------------------------------------------------------------
+def _mass_weights(n, K, bc):
+    # the implicit-Euler mass of each velocity row, h^2 m_k / dt, read off the
+    # diagonal at two time steps: 1 on full control volumes, 1/2 on half ones,
+    # 0 on identity (Dirichlet) rows
+    h, nv = 1.0 / n, 2 * n * (n + 1)
+    A1 = O.Oracle(n, 1e-3, 1.0, 0.1, K, bc=bc).scipy_csr().toarray()
+    A2 = O.Oracle(n, 1e-3, 1.0, 0.2, K, bc=bc).scipy_csr().toarray()
+    m = (np.diag(A1)[:nv] - np.diag(A2)[:nv]) / (h * h * (1 / 0.1 - 1 / 0.2))
+    return A1, m
+
+
+@pytest.mark.parametrize("bc", [0, 1, 2])
+def test_viscous_and_darcy_blocks_are_spd(bc):
+    n = 8
+    h, nv = 1.0 / n, 2 * n * (n + 1)
+    K = I.lognormal_K(n, -4.0, 1.0, 4.0, seed=3)
+    A, m = _mass_weights(n, K, bc)
+    # half control volumes: the v_Gamma faces, and the side u faces with traction sides
+    assert np.sum(np.isclose(m, 0.5)) == (n if bc == 0 else 3 * n)
+    assert np.sum(np.isclose(m, 0.0)) == (3 * n if bc == 0 else n)
+    assert np.all(np.isclose(m, 0.0) | np.isclose(m, 0.5) | np.isclose(m, 1.0))
+    free = ~np.isclose(m, 0.0)
+    Vs = (A[:nv, :nv] - np.diag(h * h * m / 0.1))[np.ix_(free, free)]
+    assert np.abs(Vs - Vs.T).max() <= 1e-15 * np.abs(Vs).max()
+    # positive definite on the scale of mu = 1e-3 (smallest eigenvalue 0.1-0.3 mu here)
+    assert np.linalg.eigvalsh(Vs)[0] / 1e-3 > 0.05
+    D = A[nv + n * n:, nv + n * n:]
+    assert np.abs(D - D.T).max() == 0.0 and np.linalg.eigvalsh(D)[0] > 0
+
+
+def test_kinetic_energy_decays_without_data():
+    # the pressure-driven problem with zero pressure drop has no data: from any
+    # velocity, the M-norm of the velocity must not grow over a backward-Euler
+    # step (the pressure terms cancel, the viscous and Darcy blocks dissipate)
+    n = 8
+    nv = 2 * n * (n + 1)
+    K = I.lognormal_K(n, -4.0, 1.0, 4.0, seed=4)
+    _, m = _mass_weights(n, K, 2)
+    o = O.Oracle(n, 1e-3, 1.0, 0.1, K, bc=2, dp=0.0)
+    x = np.random.default_rng(5).standard_normal(o.ndof)
+    x[:nv][np.isclose(m, 0.0)] = 0.0
+    E = [float(np.sum(m * x[:nv] ** 2))]
+    x = o.run(x, 0.0, 1)
+    for s in range(1, 8):
+        E.append(float(np.sum(m * x[:nv] ** 2)))
+        x = o.run(x, 0.1 * s, 1)
+    assert all(b < a for a, b in zip(E, E[1:])), E

@@ -13,7 +13,7 @@
  * banded LU factorisation with partial pivoting of its own.
  *
  * Discretisation (the paper names the schemes in Sec. 2 but prints no stencil;
- * the reading below is written out in full in the design notes):
+ * this file implements the following reading of them):
  *   geometry     free flow  [0,1]x[1,2], porous medium [0,1]x[0,1],
  *                interface Gamma = {y = 1}, n x n cells each, h = 1/n.
  *   unknowns     u  on vertical ff faces   (n+1) x n, index j*(n+1)+i

@@ -429,3 +429,32 @@ def test_kinetic_energy_decays_without_data():
         E.append(float(np.sum(m * x[:nv] ** 2)))
         x = o.run(x, 0.1 * s, 1)
     assert all(b < a for a, b in zip(E, E[1:])), E
+
+
+def test_paper_parameters_linear_and_quasi_steady():
+    # the physical parameters of Sec. 5 (K = 1e-6 m^2, alpha_BJ = 1, dt = 2e5 s,
+    # t_end = 50e5 s, a half-cosine pressure difference of at most 1e-9 Pa; the
+    # viscosity, not printed, is taken as water's 1e-3 Pa s) on 16^2 cells:
+    # * the solution is linear in the pressure difference, so the build's
+    #   unit amplitude gives the same fields scaled by 1e9;
+    # * the mass term h^2/dt is some 1e-5 of the viscous one: every step is
+    #   the steady solution of its own inflow pressure, to 5e-4 at the first
+    #   step and closer at every later one, 2e-6 at t_end, where the pressure
+    #   stops rising
+    n, mu, dt, t_end, dp = 16, 1e-3, 2e5, 50e5, 1e-9
+    K = np.full((n, n), 1e-6)
+    o = O.Oracle(n, mu, 1.0, dt, K, bc=2, dp=dp, t_end=t_end)
+    o1 = O.Oracle(n, mu, 1.0, dt, K, bc=2, dp=1.0, t_end=t_end)
+    steady = O.Oracle(n, mu, 1.0, 1e20, K, bc=2, dp=dp, t_end=t_end)
+    x, x1 = np.zeros(o.ndof), np.zeros(o.ndof)
+    lag = []
+    for s in range(25):
+        x, x1 = o.run(x, s * dt, 1), o1.run(x1, s * dt, 1)
+        assert np.linalg.norm(1e-9 * x1 - x) <= 1e-14 * np.linalg.norm(x)
+        xs = steady.solve(steady.rhs(np.zeros(o.ndof), (s + 1) * dt))
+        f, fs = O.split(x, n), O.split(xs, n)
+        lag.append(max(np.linalg.norm(f[k] - fs[k]) / np.linalg.norm(fs[k]) for k in f))
+    assert lag[0] < 1e-3 and all(b < a for a, b in zip(lag, lag[1:])) and lag[-1] < 3e-6, lag
+    h = 1.0 / n
+    q_in, q_out, q_gamma = h * f["u"][:, 0].sum(), h * f["u"][:, n].sum(), -h * f["v"][0].sum()
+    assert q_in > 0 and abs(q_in - q_out - q_gamma) <= 1e-12 * q_in

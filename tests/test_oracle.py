@@ -323,17 +323,18 @@ def test_pressure_driven_problem_mass_balance():
 # the Cahouet-Chabard block of the preconditioner rests on (Sec. 4 replaces
 # the zero block; its scale is not printed)
 # ---------------------------------------------------------------------------
-def _stokes_blocks(n, mu, dt, K):
-    A = O.Oracle(n, mu, 1.0, dt, K).scipy_csr().toarray()
+def _stokes_blocks(n, mu, dt, K, bc=0):
+    A = O.Oracle(n, mu, 1.0, dt, K, bc=bc).scipy_csr().toarray()
     nu = n * (n + 1)
     vel, pff = np.arange(2 * nu), np.arange(2 * nu, 2 * nu + n * n)
     return A[np.ix_(vel, vel)], A[np.ix_(vel, pff)], A[np.ix_(pff, vel)]
 
 
-def _cell_laplacian_interface2(n):
+def _cell_laplacian_interface2(n, traction=False):
     # 5-point cell Laplacian with unit transmissibilities, no flow through the
     # free-flow walls, and 2 on the diagonal of the cells above the interface
-    # (their v_Gamma face carries half a control volume of mass)
+    # (their v_Gamma face carries half a control volume of mass); with traction
+    # sides also 2 on the cells beside them (half-volume side u faces)
     L = np.zeros((n * n, n * n))
     for j in range(n):
         for i in range(n):
@@ -344,37 +345,46 @@ def _cell_laplacian_interface2(n):
                     L[k, jj * n + ii] -= 1.0
             if j == 0:
                 L[k, k] += 2.0
+            if traction and i in (0, n - 1):
+                L[k, k] += 2.0
     return L
 
 
 @pytest.mark.parametrize("n", [8, 12])
-def test_schur_viscous_limit_is_half(n):
+@pytest.mark.parametrize("bc", [0, 2])
+def test_schur_viscous_limit_is_half(n, bc):
     # dt -> infinity: S = -C V^-1 B of the full-stress operator equals
-    # h^2 / (2 mu) exactly on the (n-2)^2 interior pressure modes, the rest of
-    # its spectrum lies below h^2 / mu; so S^-1 ~ mu / (gamma h^2) with gamma = 1/2
-    # (a Laplacian momentum operator would give gamma = 1)
+    # h^2 / (2 mu) exactly on the (n-2)^2 interior pressure modes (n (n-2) with
+    # traction sides), the rest of its spectrum lies below h^2 / mu; so
+    # S^-1 ~ mu / (gamma h^2) with gamma = 1/2 (a Laplacian momentum operator
+    # would give gamma = 1)
     h = 1.0 / n
     for mu, K in [(1.0, np.ones((n, n))), (1e-3, I.lognormal_K(n, -4.0, 1.0, 4.0, seed=n))]:
-        V, B, C = _stokes_blocks(n, mu, 1e12, K)
+        V, B, C = _stokes_blocks(n, mu, 1e12, K, bc)
         ev = np.sort(np.linalg.eigvals(-C @ np.linalg.solve(V, B)).real) * mu / h**2
-        assert np.sum(np.abs(ev - 0.5) < 1e-8) == (n - 2) ** 2, (mu, ev)
+        assert np.sum(np.abs(ev - 0.5) < 1e-8) == (n - 2) * (n - 2 if bc == 0 else n), (mu, ev)
         assert 0.05 < ev[0] and ev[-1] < 1.0
 
 
 @pytest.mark.parametrize("n", [8, 12])
-def test_schur_mass_limit_is_cell_laplacian(n):
-    # dt -> 0: V -> (h^2/dt) M with M = 1, and 1/2 on the interface faces, so
-    # S -> dt B^T M^-1 B / h^2 = dt L_p, L_p the cell Laplacian with 2 on the
-    # interface cells; the gap closes linearly in dt
+@pytest.mark.parametrize("bc", [0, 1, 2])
+def test_schur_mass_limit_is_cell_laplacian(n, bc):
+    # dt -> 0: V -> (h^2/dt) M with M = 1, and 1/2 on the half-volume faces,
+    # so S -> dt B^T M^-1 B / h^2 = dt L_p, L_p the cell Laplacian with 2 on
+    # the interface cells (and on the side cells with traction sides); the gap
+    # closes linearly in dt, and without the side terms it stays O(1)
     K = I.lognormal_K(n, -4.0, 1.0, 4.0, seed=n)
-    L = _cell_laplacian_interface2(n)
+    L = _cell_laplacian_interface2(n, traction=bc != 0)
     gaps = []
     for dt in (1e-6, 1e-8):
-        V, B, C = _stokes_blocks(n, 1e-3, dt, K)
+        V, B, C = _stokes_blocks(n, 1e-3, dt, K, bc)
         S = -C @ np.linalg.solve(V, B)
         gaps.append(np.linalg.norm(S - dt * L) / np.linalg.norm(dt * L))
     assert gaps[0] < 1e-5 and gaps[1] < 1e-7
     assert 50 < gaps[0] / gaps[1] < 200
+    if bc != 0:
+        L0 = _cell_laplacian_interface2(n)
+        assert np.linalg.norm(S - 1e-8 * L0) / np.linalg.norm(1e-8 * L0) > 0.1
 
 
 # ---------------------------------------------------------------------------

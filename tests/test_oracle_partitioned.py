@@ -7,7 +7,9 @@ of S_ff o S_pm, the accelerated iteration converges to the monolithic
 solution and (R being affine) terminates within the interface dimension,
 relaxed Picard alone is slower, and the order of Sec. 3 (free flow first,
 velocity prescribed) leaves a singular free-flow block on these boundary
-conditions.  A planted wrong interface flux moves the fixed point.
+conditions.  A planted wrong interface flux moves the fixed point.  The
+linearised maps show why the porous-medium-first order is the default: it
+contracts, while Sec. 3's order amplifies by about 2K/(mu h).
 """
 import numpy as np
 import pytest
@@ -149,3 +151,26 @@ def test_paper_order_reaches_monolithic_solution(bc, n):
     # relaxed first step, n difference columns, the step onto the fixed point,
     # and the evaluations the stopping test needs to see the change vanish
     assert evals <= n + 4
+
+
+@pytest.mark.parametrize("n,seed", [(24, 40), (32, 5)])
+def test_order_amplification(n, seed):
+    # the linearised coupling maps on the pressure-driven problem (traction
+    # sides, log-normal K, mu = 1e-3): Sec. 3's order passes the interface
+    # pressure through the half cell below Gamma, so an error in the free-flow
+    # solve's pressure reaches the returned velocity multiplied by about the
+    # transmissibility over h, 2K/(mu h) (between its mean and its maximum over
+    # the interface); the whole map dH/dv amplifies by hundreds.  The
+    # porous-medium-first map contracts (norm below 0.1), so no subdomain
+    # error is amplified
+    K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=seed)
+    mu = 1e-3
+    o = O.Oracle(n, mu, 1.0, 0.05, K, bc=2)
+    b = np.zeros(o.ndof)  # the maps are affine: their linear parts
+    paper, pm = DNOracle(o, K, order="paper"), DNOracle(o, K, order="pm")
+    E = np.eye(n)
+    J_pm_solve = np.stack([paper.s_pm_paper(e, b)[1] for e in E], 1)
+    fac = 2.0 * K[n - 1] / (mu / n)
+    assert fac.mean() <= np.linalg.norm(J_pm_solve, 2) <= fac.max()
+    assert np.linalg.norm(np.stack([paper.H(e, b)[0] for e in E], 1), 2) > 100.0
+    assert np.linalg.norm(np.stack([pm.H(e, b)[0] for e in E], 1), 2) < 0.1

@@ -202,9 +202,13 @@ void class_loop(sd_server* S, SizeClass* C) {
     std::vector<Job*> keep;
     for (size_t q = 0; q < hs.size(); ++q) {
       Job* J = C->running[q];
-      J->done += 1;
-      J->iters += info[q].iters;
-      if (info[q].relres > J->maxrel) J->maxrel = info[q].relres;
+      // a step that ended in SD_E_NOCONV or SD_E_NUMERIC still advanced the
+      // state; a CUDA, allocation or state error returned before it did
+      if (rcs[q] == SD_OK || rcs[q] == SD_E_NOCONV || rcs[q] == SD_E_NUMERIC) {
+        J->done += 1;
+        J->iters += info[q].iters;
+        if (info[q].relres > J->maxrel) J->maxrel = info[q].relres;
+      }
       if (rcs[q] != SD_OK || J->done >= J->req.nsteps) {
         close_job(J, rcs[q]);
         finish_job(S, J);

@@ -51,6 +51,7 @@ struct Job {
   // lockstep serving: the run's handle and progress between ticks
   sd_handle* h = nullptr;
   int done = 0, iters = 0;
+  int first = SD_OK;  // first non-OK status of a step that still advanced the state
   double maxrel = 0.0;
 };
 
@@ -145,15 +146,18 @@ void finish_job(sd_server* S, Job* J) {
   S->running -= 1;
 }
 
-// Close a lockstep-served run: copy its state out if asked, release the handle.
+// Close a lockstep-served run: copy its state out if asked (as the one-worker
+// path does, also after steps that ended in SD_E_NOCONV or SD_E_NUMERIC),
+// release the handle.
 void close_job(Job* J, int rc) {
   J->res.dof = sd_dof_count(J->req.grid.nx);
   J->res.steps_done = J->done;
   J->res.total_iters = J->iters;
   J->res.max_relres = J->maxrel;
-  if (J->h && J->req.keep_fields && rc == SD_OK) {
+  if (J->h && J->req.keep_fields && (rc == SD_OK || rc == SD_E_NOCONV || rc == SD_E_NUMERIC)) {
     J->x.resize((size_t)sd_dof_count(J->req.grid.nx));
-    rc = sd_get_state(J->h, nullptr, nullptr, J->x.data(), nullptr);
+    const int r2 = sd_get_state(J->h, nullptr, nullptr, J->x.data(), nullptr);
+    if (rc == SD_OK) rc = r2;
   }
   if (J->h) sd_destroy(J->h);
   J->h = nullptr;
@@ -203,14 +207,17 @@ void class_loop(sd_server* S, SizeClass* C) {
     for (size_t q = 0; q < hs.size(); ++q) {
       Job* J = C->running[q];
       // a step that ended in SD_E_NOCONV or SD_E_NUMERIC still advanced the
-      // state; a CUDA, allocation or state error returned before it did
-      if (rcs[q] == SD_OK || rcs[q] == SD_E_NOCONV || rcs[q] == SD_E_NUMERIC) {
+      // state and the run goes on (as in sd_step); a CUDA, allocation or
+      // state error returned before the step was taken and ends the run
+      const bool advanced = rcs[q] == SD_OK || rcs[q] == SD_E_NOCONV || rcs[q] == SD_E_NUMERIC;
+      if (advanced) {
         J->done += 1;
         J->iters += info[q].iters;
         if (info[q].relres > J->maxrel) J->maxrel = info[q].relres;
+        if (rcs[q] != SD_OK && J->first == SD_OK) J->first = rcs[q];
       }
-      if (rcs[q] != SD_OK || J->done >= J->req.nsteps) {
-        close_job(J, rcs[q]);
+      if (!advanced || J->done >= J->req.nsteps) {
+        close_job(J, advanced ? J->first : rcs[q]);
         finish_job(S, J);
         S->cv.notify_all();
       } else {

@@ -381,7 +381,11 @@ int sd_solve_batch_ex(sd_handle *const *hs, int32_t count, const int32_t *nsteps
  * longer ones stop at 16 x 16 (the default).  Building the dense inverse of
  * the 16 x 16 grid costs about 10 ms and some 1,600 dependent launches per
  * request, which queue behind the other runs' work, and saves 0.2-0.3 ms
- * per step.  Lockstep size classes are then also split by depth. */
+ * per step.  Lockstep size classes are then also split by depth.
+ * Memory: each run reserves sd_memory_estimate() of its own options (its
+ * depth included) plus 4 MiB for setup temporaries and stream resources;
+ * sd_submit returns SD_E_NOMEM for a request whose reservation exceeds the
+ * whole budget, so every accepted request fits an idle server. */
 #define SD_SERVER_LOCKSTEP 1
 typedef struct {
   sd_grid grid;

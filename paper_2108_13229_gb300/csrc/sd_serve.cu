@@ -92,12 +92,15 @@ namespace {
 // other runs' work), and saves 0.2-0.3 ms per step, so runs shorter than
 // kShortRun steps coarsen to 4 x 4 instead.
 const int kShortRun = 40;
-sd_options job_options(const sd_server* S, const Job* J) {
+// device memory reserved per run beyond its arena (setup temporaries, stream resources)
+const int64_t kRunSlack = 4ll << 20;
+sd_options run_options(const sd_server* S, const sd_request& req) {
   sd_options o = S->opt;
   o.stream = nullptr;  // each run gets its own stream, so runs overlap on the device
-  if (S->auto_depth) o.coarsest = J->req.nsteps < kShortRun ? 4 : 16;
+  if (S->auto_depth) o.coarsest = req.nsteps < kShortRun ? 4 : 16;
   return o;
 }
+sd_options job_options(const sd_server* S, const Job* J) { return run_options(S, J->req); }
 
 void run_job(sd_server* S, Job* J) {
   sd_options o = job_options(S, J);
@@ -374,15 +377,20 @@ int sd_server_create_ex(int64_t hbm_budget_bytes, int32_t max_running, const sd_
 
 int sd_submit(sd_server* S, const sd_request* req, uint64_t* ticket) {
   if (!S || !req || !ticket || !req->K || req->nsteps < 0) return SD_E_INVAL;
-  const int64_t est = sd_memory_estimate(&req->grid, &S->opt);
+  // the device memory of the run as it will be created (its own multigrid depth)
+  const sd_options ro = run_options(S, *req);
+  const int64_t est = sd_memory_estimate(&req->grid, &ro);
   if (est < 0) return SD_E_INVAL;
-  if (est > S->budget) return SD_E_NOMEM;
+  // what admission reserves: the arena plus setup temporaries and stream
+  // resources; a request accepted here always fits an idle server
+  const int64_t need = est + kRunSlack;
+  if (need > S->budget) return SD_E_NOMEM;
   const int n = req->grid.nx;
   std::unique_ptr<Job> J(new Job());
   J->req = *req;
   J->K.assign(req->K, req->K + (size_t)n * n);
   J->req.K = nullptr;
-  J->est = est + (int64_t)(4 << 20);  // setup temporaries and stream resources
+  J->est = need;
   J->t_submit = clk::now();
   {
     std::lock_guard<std::mutex> lk(S->mu);

@@ -207,3 +207,28 @@ def test_apply_noalloc_validation_without_gpu(sd):
         with pytest.raises(sd.SdError) as e:
             sd.sd_apply_noalloc(n, mu, np.ones(n * n), 1.0, dt, np.zeros(d), np.zeros(d))
         assert e.value.code == sd.SD_E_INVAL, (n, mu, dt)
+
+
+def test_server_reserves_each_runs_own_depth(sd):
+    # a server made without options runs short requests (under 40 steps) with
+    # a 4 x 4 coarsest grid and long ones with 16 x 16; it reserves for each
+    # the memory of the run it will create, so a budget between the two fits
+    # the short request and refuses the long one
+    import ctypes
+    n = 64
+    est = {}
+    for co in (4, 16):
+        o = sd.sd_options_default()
+        o.coarsest = co
+        g = sd.sd_grid(n, n)
+        est[co] = sd._load().sd_memory_estimate(ctypes.byref(g), ctypes.byref(o))
+    slack = 4 << 20  # setup temporaries reserved with every run
+    assert est[4] < est[16]
+    srv = sd.sd_server_create((est[4] + est[16]) // 2 + slack, 1)
+    with pytest.raises(sd.SdError) as e:
+        sd.sd_submit(srv, n, 1e-3, np.ones((n, n)), 1.0, 0.1, 50)
+    assert e.value.code == sd.SD_E_NOMEM
+    ticket = sd.sd_submit(srv, n, 1e-3, np.ones((n, n)), 1.0, 0.1, 5)
+    sd.sd_server_drain(srv)  # without a device the run ends with SD_E_CUDA; with one it completes
+    assert sd.sd_poll(srv, ticket)[0] in (sd.SD_OK, sd.SD_E_CUDA)
+    del srv

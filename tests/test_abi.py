@@ -232,3 +232,22 @@ def test_server_reserves_each_runs_own_depth(sd):
     sd.sd_server_drain(srv)  # without a device the run ends with SD_E_CUDA; with one it completes
     assert sd.sd_poll(srv, ticket)[0] in (sd.SD_OK, sd.SD_E_CUDA)
     del srv
+
+
+@pytest.mark.parametrize("lockstep", [False, True])
+def test_server_lifecycle_without_gpu(sd, lockstep):
+    # drain returns once every request has ended (without a device each run
+    # ends with SD_E_CUDA at its setup), a ticket is answered once, and a
+    # server destroyed with requests still queued or running shuts down
+    srv = sd.sd_server_create(1 << 30, 2, lockstep=lockstep)
+    tickets = [sd.sd_submit(srv, 32, 1e-3, np.ones((32, 32)), 1.0, 0.1, 5) for _ in range(4)]
+    sd.sd_server_drain(srv)
+    for t in tickets:
+        rc, res, _ = sd.sd_poll(srv, t)
+        assert rc in (sd.SD_OK, sd.SD_E_CUDA) and res["status"] == rc
+        assert sd.sd_poll(srv, t)[0] == sd.SD_E_STATE
+    busy = sd.sd_server_create(1 << 30, 2, lockstep=lockstep)
+    for _ in range(6):
+        sd.sd_submit(busy, 32, 1e-3, np.ones((32, 32)), 1.0, 0.1, 5)
+    del busy
+    del srv

@@ -583,14 +583,6 @@ def oracle_scan(sizes=(32, 64, 128, 256), steps: int = 5, resid_sizes=(1024, 204
             "cores_used": 1, "rows": rows}
 
 
-def peak_probe() -> int:
-    """Compile and run paper_2108_13229_gb300/peak_probe.cu; prints its JSON line."""
-    src = os.path.join(ROOT, "paper_2108_13229_gb300", "peak_probe.cu")
-    exe = os.path.join(tempfile.gettempdir(), "sd_peak_probe")
-    subprocess.check_call(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src])
-    return subprocess.call([exe])
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -602,14 +594,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="headline form only")
     ap.add_argument("--no-autotune", action="store_true", help="library defaults instead of autotuned options")
-    ap.add_argument("--peak-probe", action="store_true", help="measure FP64/FP32 FMA rates and copy bandwidth")
     ap.add_argument("--mode", default="single", choices=["single", "batch", "serve", "configs", "oracle"])
     ap.add_argument("--count", type=int, default=256, help="batch instances / serving requests")
     ap.add_argument("--threads", type=int, default=32, help="host threads (batch) / running slots (serve)")
     ap.add_argument("--rates", type=float, nargs="*", default=[10.0, 20.0, 50.0, 100.0, 200.0, 500.0])
     args = ap.parse_args()
-    if args.peak_probe:
-        return peak_probe()
     if args.mode == "oracle":
         print(json.dumps(oracle_scan()), flush=True)
         return 0

@@ -430,7 +430,9 @@ void sd_server_destroy(sd_server *s);
 int sd_profile(sd_handle *h, int32_t kernel, int32_t enable);
 int sd_profile_read(sd_handle *h, double *total_ms, int64_t *launches, double *bytes, double *flops);
 
-/* y = A x (the same operator as sd_apply) for callers that cannot allocate
+/* y = A x (the operator of sd_apply on a handle with bc = SD_BC_MMS, i.e.
+ * Dirichlet free-flow sides; a handle with traction sides applies other side
+ * rows, so the two agree only for SD_BC_MMS) for callers that cannot allocate
  * device memory: code running inside a framework that owns a fixed memory
  * pool, real-time loops where a cudaMalloc would stall the device, or
  * library code that may not create a handle (sd_create allocates).  This
@@ -441,9 +443,10 @@ int sd_profile_read(sd_handle *h, double *total_ms, int64_t *launches, double *b
  *   grid, mu, alpha_bj, dt  as in sd_create; n <= SD_NOALLOC_MAX_N, larger
  *                           grids return SD_E_INVAL;
  *   K, x, y                 CUDA device memory of the current device (host
- *                           pointers return SD_E_INVAL); K (n*n, > 0, not
- *                           checked here) and x in the layouts of sd_create
- *                           and sd_apply; y receives A x;
+ *                           pointers and memory of another device return
+ *                           SD_E_INVAL); K (n*n, > 0, not checked here) and x
+ *                           (4n^2+2n) in the layouts of sd_create and
+ *                           sd_apply; y (4n^2+2n) receives A x;
  *   stream                  cudaStream_t (NULL: the default stream); the
  *                           work is queued on it and y is ready when the
  *                           stream reaches that point.
@@ -451,7 +454,9 @@ int sd_profile_read(sd_handle *h, double *total_ms, int64_t *launches, double *b
  * with that device current); make that first call before any stream
  * capture.  All calls share the one array: calls whose work can overlap on
  * the GPU (different streams without ordering) race and corrupt each other.
- * Errors: SD_E_INVAL, SD_E_CUDA. */
+ * Errors: SD_E_INVAL; SD_E_CUDA when a launch fails, and also, without
+ * running anything (the pending error is left in place), when a CUDA error
+ * from earlier work is already pending on entry. */
 #define SD_NOALLOC_MAX_N 256
 int sd_apply_noalloc(const sd_grid *grid, double mu, const double *K, double alpha_bj, double dt, const double *x,
                      double *y, void *stream);

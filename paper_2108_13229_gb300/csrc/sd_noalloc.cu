@@ -49,13 +49,20 @@ int scratch_address(double** out) {
   return SD_OK;
 }
 
-bool on_device(const void* p) {
+// True for device memory of device `dev` (or managed memory).  The kernels
+// run on the current device and dereference the pointers directly, so memory
+// of another GPU is refused rather than read across devices.  A failing
+// attribute query (no usable device) is the only error it clears; an error
+// pending from the caller's own work does not make the query fail, so it
+// stays pending for the check that follows.
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -68,7 +75,13 @@ extern "C" int sd_apply_noalloc(const sd_grid* grid, double mu, const double* K,
   if (!(mu > 0) || !(alpha_bj > 0) || !(dt > 0) || !std::isfinite(mu) || !std::isfinite(alpha_bj) ||
       !std::isfinite(dt))
     return SD_E_INVAL;
-  if (!K || !x || !y || !on_device(K) || !on_device(x) || !on_device(y)) return SD_E_INVAL;
+  int dev = 0;
+  if (!K || !x || !y || cudaGetDevice(&dev) != cudaSuccess || !on_device(K, dev) || !on_device(x, dev) ||
+      !on_device(y, dev))
+    return SD_E_INVAL;
+  // an error left pending by earlier work is not this call's to report or to
+  // clear: refuse to run on top of it
+  if (cudaPeekAtLastError() != cudaSuccess) return SD_E_CUDA;
   const Geom g = make_geom(n);
   // carve the scratch array: padded K, coefficients, padded x and y
   const long long oK = 0;
@@ -86,9 +99,12 @@ extern "C" int sd_apply_noalloc(const sd_grid* grid, double mu, const double* K,
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // every scratch entry that the operator reads is written first in this
   // call, so the previous call's contents never leak into the result
+  // nothing was pending at entry, so an error seen after a launch is that
+  // launch's own
   launch_pack_K(K, n, base + oK, g.P, s);
   launch_setup_coef<double>(base + oK, n, g.P, mu, alpha_bj, 0, 0, base + ow, base + org, base + oTx, base + oTy, s);
   launch_pack(g, x, base + ox, s);
+  if (cudaGetLastError() != cudaSuccess) return SD_E_CUDA;
   Coef<double> c;
   c.n = n;
   c.P = g.P;

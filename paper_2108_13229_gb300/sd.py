@@ -404,10 +404,30 @@ def sd_launch_count() -> int:
 
 
 def sd_apply_noalloc(n: int, mu: float, K, alpha_bj: float, dt: float, x, y, stream=None) -> None:
-    """y = A x without allocating (all arrays: CUDA float64 tensors; see include/sd.h)."""
+    """y = A x without allocating (see include/sd.h).
+
+    K, x and y are CUDA float64 tensors of one device (x and y of 4n^2+2n
+    elements); the library refuses host memory with SD_E_INVAL.  The call
+    runs with that device current; stream=None queues the work on its current
+    torch stream, so later work on that stream sees y.  With an explicit
+    cudaStream_t handle the caller orders its own reads of y after that
+    stream."""
+    dof = 4 * n * n + 2 * n
     g = sd_grid(n, n)
-    _check(_load().sd_apply_noalloc(ctypes.byref(g), float(mu), _ptr(K, n * n), float(alpha_bj), float(dt),
-                                    _ptr(x), _ptr(y), stream), "sd_apply_noalloc")
+    cuda = [a for a in (K, x, y) if getattr(a, "is_cuda", False)]
+    if not cuda:  # host arrays: passed through for the library to refuse
+        _check(_load().sd_apply_noalloc(ctypes.byref(g), float(mu), _ptr(K, n * n), float(alpha_bj), float(dt),
+                                        _ptr(x, dof), _ptr(y, dof), stream), "sd_apply_noalloc")
+        return
+    import torch
+    dev = cuda[0].device
+    if any(a.device != dev for a in cuda):
+        raise ValueError("K, x and y must be on one device")
+    with torch.cuda.device(dev):
+        if stream is None:
+            stream = torch.cuda.current_stream(dev).cuda_stream
+        _check(_load().sd_apply_noalloc(ctypes.byref(g), float(mu), _ptr(K, n * n), float(alpha_bj), float(dt),
+                                        _ptr(x, dof), _ptr(y, dof), stream), "sd_apply_noalloc")
 
 
 def sd_autotune(n: int, mu: float, K, alpha_bj: float, dt: float, base: sd_options | None = None,

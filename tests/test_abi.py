@@ -207,6 +207,13 @@ def test_apply_noalloc_validation_without_gpu(sd):
         with pytest.raises(sd.SdError) as e:
             sd.sd_apply_noalloc(n, mu, np.ones(n * n), 1.0, dt, np.zeros(d), np.zeros(d))
         assert e.value.code == sd.SD_E_INVAL, (n, mu, dt)
+    # arrays shorter than the layout are refused by the binding itself
+    n = 8
+    d = 4 * n * n + 2 * n
+    with pytest.raises(ValueError):
+        sd.sd_apply_noalloc(n, 1.0, np.ones(n * n), 1.0, 0.1, np.zeros(d - 1), np.zeros(d))
+    with pytest.raises(ValueError):
+        sd.sd_apply_noalloc(n, 1.0, np.ones(n * n), 1.0, 0.1, np.zeros(d), np.zeros(d - 1))
 
 
 def test_server_reserves_each_runs_own_depth(sd):

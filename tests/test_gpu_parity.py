@@ -287,6 +287,43 @@ def test_error_paths(sd):
     sd.sd_server_destroy(srv)
 
 
+def test_numeric_error_from_nan_rhs(sd):
+    # a NaN planted in b on the host: the first residual norm is NaN, the
+    # solve returns SD_E_NUMERIC before any update, and x keeps the guess
+    n = 32
+    K = I.lognormal_K(n, -4.0, 1.0, 4.0, seed=4)
+    h = make(sd, n, 1e-3, K, 1.0, 0.05)
+    rng = np.random.default_rng(4)
+    b = rng.standard_normal(sd.sd_dof_count(n))
+    b[7] = np.nan
+    x0 = rng.standard_normal(b.size)
+    x = x0.copy()
+    info = sd.sd_solve(h, b, x, raise_on_error=False)
+    assert info["status"] == sd.SD_E_NUMERIC
+    assert np.array_equal(x, x0)
+    # the handle stays usable: a finite right-hand side solves afterwards
+    b[7] = 0.0
+    info = sd.sd_solve(h, b, x)
+    assert info["status"] == 0 and info["relres"] <= 1e-10
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("n", [40, 64])
+def test_schur_mass_only_parity(sd, n, precision):
+    # the Schur block as the viscosity-scaled pressure mass matrix alone,
+    # S^-1 = (mu/(gamma h^2)) I (schur_mass = 0), on the log-normal physics:
+    # the same states as the oracle, three steps
+    K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=1)
+    o = O.Oracle(n, 1e-3, 1.0, 0.05, K)
+    xr = o.run(O.exact(n, 0.0, 1e-3), 0.0, 3)
+    h = make(sd, n, 1e-3, K, 1.0, 0.05, precision, rtol=1e-12, schur_mass=0, max_iters=3000)
+    infos = sd.sd_step(h, 3)
+    assert all(i["status"] == 0 for i in infos), infos
+    _, _, x = sd.sd_get_state(h)
+    for k, e in fields_rel(x, xr, n).items():
+        assert e <= 1e-8, (k, e)
+
+
 @pytest.mark.parametrize("mode", [1, 2])
 def test_paper_block_preconditioners(sd, mode):
     # P^pv_BJ and P^pv_BGS with the identity on the p_ff block (Sec. 4) on the

@@ -468,3 +468,107 @@ def test_paper_parameters_linear_and_quasi_steady():
     h = 1.0 / n
     q_in, q_out, q_gamma = h * f["u"][:, 0].sum(), h * f["u"][:, n].sum(), -h * f["v"][0].sum()
     assert q_in > 0 and abs(q_in - q_out - q_gamma) <= 1e-12 * q_in
+
+
+# ---------------------------------------------------------------------------
+# the product and residual routines the GPU tests use as checkers
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [4, 16, 128])
+@pytest.mark.parametrize("bc", [0, 2])
+def test_apply_and_residual_match_scipy(n, bc):
+    # or_apply and or_residual walk the CSR themselves; scipy's sparse product
+    # over the exported arrays is an independent walk.  A wrong row range,
+    # a skipped last row or a norm of the wrong vector fails here.
+    rng = np.random.default_rng(100 + n + bc)
+    K = I.lognormal_K(n, -4.0, 1.0, 4.0, seed=n + bc)
+    o = O.Oracle(n, 1e-3, 1.3, 0.05, K, bc=bc, dp=1.0, t_end=1.0)
+    A = o.scipy_csr()
+    assert A.shape == (O.dof_count(n),) * 2
+    x = rng.standard_normal(o.ndof)
+    b = rng.standard_normal(o.ndof)
+    Ax = A @ x
+    y = o.apply(x)
+    assert np.linalg.norm(y - Ax) <= 1e-14 * np.linalg.norm(Ax)
+    r, nrm = o.residual(x, b)
+    rr = b - Ax
+    assert np.linalg.norm(r - rr) <= 1e-14 * np.linalg.norm(rr)
+    assert abs(nrm - np.linalg.norm(rr)) <= 1e-14 * np.linalg.norm(rr)
+    # the norm is that of b - A x, not of b or of A x
+    assert abs(nrm - np.linalg.norm(b)) > 1e-3 * np.linalg.norm(b)
+    # a solved system has (almost) no residual
+    o2 = O.Oracle(n, 1e-3, 1.3, 0.05, K, bc=bc) if n <= 16 else None
+    if o2 is not None:
+        xs = o2.solve(b)
+        _, nrm2 = o2.residual(xs, b)
+        assert nrm2 <= 1e-10 * np.linalg.norm(b)
+
+
+def test_interface_row_written_out():
+    # The v_Gamma rows at n = 4, written from the half-control-volume balance
+    # of Eq. (5) over [x_i, x_{i+1}] x [1, 1 + h/2]:
+    #   mass      h^2/(2 dt) v_G
+    #   top       h p_ff(i,0) - 2 mu (v(i,1) - v_G)            (normal stress at the cell centre)
+    #   bottom    -h p_G,  p_G = p_pm(i,n-1) - mu h/(2 K) v_G    (TPFA reconstruction, Eq. (7))
+    #   sides     -(h/2) tau(x_{i+1}) + (h/2) tau(x_i),  tau at a Gamma corner from the
+    #             eliminated BJS slip of Eq. (6): tau = w (2 u(.,0) + dv), w = mu/(h + 2 beta),
+    #             beta = mean sqrt(K) of the two cells below / alpha, dv the jump of v_G;
+    #             at the wall x = 0: tau = mu v_G / (h/2) (wall velocity is data).
+    n, mu, alpha, dt = 4, 0.7, 1.9, 0.3
+    h = 1.0 / n
+    K = np.exp(np.random.default_rng(3).normal(-1.0, 0.8, (n, n)))
+    o = O.Oracle(n, mu, alpha, dt, K.ravel())
+    A = o.scipy_csr().tocsr()
+    off = O.offsets(n)
+
+    def iu(i, j):
+        return off["u"] + j * (n + 1) + i
+
+    def iv(i, j):
+        return off["v"] + j * n + i
+
+    def ipf(i, j):
+        return off["p_ff"] + j * n + i
+
+    def ipm(i, j):
+        return off["p_pm"] + j * n + i
+
+    def w(i):  # BJS shear coefficient of the interface corner at x_i, 1 <= i <= n-1
+        beta = 0.5 * (np.sqrt(K[n - 1, i - 1]) + np.sqrt(K[n - 1, i])) / alpha
+        return mu / (h + 2 * beta)
+
+    def row(r):
+        a = A.getrow(r)
+        return dict(zip(a.indices.tolist(), a.data.tolist()))
+
+    # interior face i = 1 (both corners on Gamma)
+    i = 1
+    want = {
+        iv(i, 0): h * h / (2 * dt) + 2 * mu + mu * h * h / (2 * K[n - 1, i]) + 0.5 * h * (w(i) + w(i + 1)),
+        iv(i, 1): -2 * mu,
+        ipf(i, 0): h,
+        ipm(i, n - 1): -h,
+        iu(i, 0): h * w(i),
+        iu(i + 1, 0): -h * w(i + 1),
+        iv(i - 1, 0): -0.5 * h * w(i),
+        iv(i + 1, 0): -0.5 * h * w(i + 1),
+    }
+    got = row(iv(i, 0))
+    assert set(got) == set(want)
+    for k in want:
+        assert abs(got[k] - want[k]) <= 1e-15 * max(1.0, abs(want[k])), (k, got[k], want[k])
+    # wall face i = 0: the left corner is the Dirichlet side at half distance
+    i = 0
+    want = {
+        iv(i, 0): h * h / (2 * dt) + 2 * mu + mu * h * h / (2 * K[n - 1, i]) + mu + 0.5 * h * w(i + 1),
+        iv(i, 1): -2 * mu,
+        ipf(i, 0): h,
+        ipm(i, n - 1): -h,
+        iu(i + 1, 0): -h * w(i + 1),
+        iv(i + 1, 0): -0.5 * h * w(i + 1),
+    }
+    got = row(iv(i, 0))
+    assert set(got) == set(want)
+    for k in want:
+        assert abs(got[k] - want[k]) <= 1e-15 * max(1.0, abs(want[k])), (k, got[k], want[k])
+    # the Darcy cell below face 1 sees h v_G (Eq. (7), block C'_1)
+    assert abs(row(ipm(1, n - 1))[iv(1, 0)] - h) <= 1e-16

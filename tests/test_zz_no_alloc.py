@@ -50,7 +50,14 @@ def test_apply_noalloc_rejects():
     with pytest.raises(sd.SdError) as e:
         sd.sd_apply_noalloc(n, 1.0, K, 1.0, 0.1, x, torch.empty_like(x))
     assert e.value.code == sd.SD_E_INVAL
-    n = 8  # host memory is not accepted
+    n = 8  # tensors shorter than 4n^2+2n are refused before any device work
+    K = torch.ones(n * n, dtype=torch.float64, device=dev)
+    x = torch.zeros(4 * n * n + 2 * n, dtype=torch.float64, device=dev)
+    with pytest.raises(ValueError):
+        sd.sd_apply_noalloc(n, 1.0, K, 1.0, 0.1, x[:-1], torch.empty_like(x))
+    with pytest.raises(ValueError):
+        sd.sd_apply_noalloc(n, 1.0, K, 1.0, 0.1, x, torch.empty_like(x)[:-1])
+    # host memory is not accepted
     with pytest.raises(sd.SdError) as e:
         sd.sd_apply_noalloc(n, 1.0, np.ones(n * n), 1.0, 0.1, np.zeros(4 * n * n + 2 * n), np.zeros(4 * n * n + 2 * n))
     assert e.value.code == sd.SD_E_INVAL

@@ -158,7 +158,8 @@ def tune_form(sd, n, K, precision, stream, enabled: bool):
                                  "cache " + os.path.basename(cache)}
 
 
-def run_form(sd, torch, n, K, precision, steps, warmup, stream, prof_kernel=None, tuned=None):
+def run_form(sd, torch, n, K, precision, steps, warmup, stream, prof_kernel=None, tuned=None, keep_fields=None,
+             name=None):
     """Warm up, then time `steps` implicit-Euler steps with CUDA events on `stream`."""
     opts = sd.sd_options_default()
     opts.precision = precision
@@ -166,7 +167,8 @@ def run_form(sd, torch, n, K, precision, steps, warmup, stream, prof_kernel=None
     for k, v in (tuned or {}).items():
         setattr(opts, k, v)
     h = sd.sd_create(n, 1e-3, K, 1.0, 0.05, opts)
-    sd.sd_step(h, warmup)
+    if warmup:
+        sd.sd_step(h, warmup)
     if prof_kernel is not None:
         sd.sd_profile(h, prof_kernel, True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -184,6 +186,8 @@ def run_form(sd, torch, n, K, precision, steps, warmup, stream, prof_kernel=None
     launches = sd.sd_launch_count() - l0
     ms = ev0.elapsed_time(ev1)
     prof = sd.sd_profile_read(h) if prof_kernel is not None else None
+    if keep_fields is not None:
+        keep_fields[name] = sd.sd_get_fields(h)
     sd.sd_destroy(h)
     return ms, infos, launches, prof
 
@@ -232,6 +236,51 @@ def roofline_entry(kid: int, prof, step_ms: float):
         e.update({"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                   "peak_source": hbm_src})
     return e
+
+
+def level_sizes(n: int, coarsest: int = 16):
+    """Cells per side of every multigrid level (the library's halving rule), the last one the dense solve."""
+    out = [n]
+    while n % 2 == 0 and n // 2 >= 2 and n > coarsest:
+        n //= 2
+        out.append(n)
+    return out
+
+
+def step_model_bytes(n: int, info: dict, mixed: bool, coarsest: int = 16) -> float:
+    """Compulsory HBM bytes of one implicit-Euler step of this algorithm (every array each kernel of the step must
+    read or write, once), from the step's FGMRES iterations, restart cycles and second Gram-Schmidt passes.
+
+    FP64 vectors of the Krylov method are 8 B per unknown; the V-cycles move es = 4 (mixed) or 8 B per value:
+    per level the velocity block 9.5 passes over its 2n(n+1) faces (pre-smoothing b in x out, residual, restriction,
+    post-smoothing with the coarse correction), the Darcy and pressure-Laplacian blocks 13.5 over their n^2 cells
+    (the same with the two transmissibility arrays read by each smoothing and residual), the coarsest grid's dense
+    FP64 inverses once per V-cycle, and the preconditioner's FP64/FP32 glue."""
+    dof = 4.0 * n * n + 2.0 * n
+    v8 = 8.0 * dof
+    es = 4.0 if mixed else 8.0
+    apply_b = 8.0 * (2 * dof + 2.0 * n * (n + 1) + 2 * n)
+    resid_b = 8.0 * (3 * dof + 2.0 * n * (n + 1) + 2 * n)
+    levels = level_sizes(n, coarsest)
+    pre = 0.0
+    for m in levels[:-1]:
+        pre += 9.5 * es * 2.0 * m * (m + 1) + 2 * 13.5 * es * m * m
+    mc = levels[-1]
+    mV, mD = 2 * mc * (mc + 1), mc * mc
+    pre += 8.0 * (mV * mV + 2 * mD * mD)
+    NV, ND = 2.0 * n * (n + 1), float(n * n)
+    g = 8.0 + es  # an FP64 value read and its multigrid copy written (or the reverse)
+    pre += g * ND + (g * NV + (8 + 4 + 8) * ND if mixed else 16 * NV + 24 * ND) + (g * NV + g * ND) + g * ND
+    total = 4 * v8 + 4 * v8 + v8 + resid_b + v8  # rhs, extrapolation, ||b||, first residual and its norm
+    iters, restarts, reo = int(info["iters"]), max(1, int(info["restarts"])), int(info.get("reorths", 0))
+    m = 30
+    for it in range(iters):
+        k = it % m + 1
+        total += pre + apply_b + (2 * k + 3) * v8 + 2 * v8
+    total += reo * 5 * v8  # a second pass, about (2k+3) vectors at the typical k = 1
+    for _ in range(restarts):
+        total += (min(iters, m) + 2) * v8 + resid_b + v8  # x update, true residual and its norm
+    return total + v8  # per-block residual norms
 
 
 def bench_batch(sd, count: int, steps: int, threads: int, seed: int = 0, lockstep: bool = True):
@@ -374,26 +423,42 @@ def bench_ours(args, ws, rank, local):
     iters = [i["iters"] for i in infos]
     relres = max(i["relres"] for i in infos)
 
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": steps, "warmup": warmup,
-            "ms_per_step": secs * 1e3 / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64 outer / f32 multigrid", "data": "synthetic",
-            "config": {"workload": workload_desc(n, steps), "n": n, "dof": dof, "precision": "mixed",
-                       "parallelism": "replicas only" if ws > 1 else "single instance",
-                       "l2": "working set ~2.4 GB per instance, larger than L2 (no flush needed)"},
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-            "iters_per_step": iters, "max_relres": relres, "gpu_launches": launches, "clocks": clocks,
-            "autotune": tune_info}
-
+    fp64 = None
     if not args.quick:
         # FP64 throughout, same workload
         tuned64, tune64 = tune_form(sd, n, K, sd.SD_FP64, stream, not args.no_autotune)
         ms64, infos64, _, _ = run_form(sd, torch, n, K, sd.SD_FP64, steps, warmup, stream, tuned=tuned64)
         u64, s64 = aggregate(dof * steps, ms64 / 1e3, ws)
         lat64 = [i["ms"] for i in infos64]
-        line["fp64"] = {"value": u64 / s64, "ms_per_step": s64 * 1e3 / steps,
-                        "latency_ms": {"p50": float(np.percentile(lat64, 50)), "p99": float(np.percentile(lat64, 99))},
-                        "iters_per_step": [i["iters"] for i in infos64], "autotune": tune64}
-        line["mixed_over_fp64"] = value / (u64 / s64)
+        fp64 = {"value": u64 / s64, "ms_per_step": s64 * 1e3 / steps,
+                "latency_ms": {"p50": float(np.percentile(lat64, 50)), "p99": float(np.percentile(lat64, 99))},
+                "iters_per_step": [i["iters"] for i in infos64], "autotune": tune64}
+
+    # the FP64 form's rate and the ratio come right after the headline value
+    line = {"metric": METRIC, "value": value, "unit": UNIT,
+            "fp64_value": fp64["value"] if fp64 else None,
+            "mixed_over_fp64": value / fp64["value"] if fp64 else None,
+            "n_gpus": ws, "steps": steps, "warmup": warmup,
+            "ms_per_step": secs * 1e3 / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 outer / f32 multigrid", "data": "synthetic",
+            "config": {"workload": workload_desc(n, steps), "n": n, "dof": dof, "precision": "mixed",
+                       "parallelism": "replicas only" if ws > 1 else "single instance",
+                       "l2": "working set ~2.4 GB per instance, larger than L2 (no flush needed)"},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "iters_per_step": iters, "max_relres": relres, "gpu_launches": launches,
+            "launches_per_step": launches / steps, "clocks": clocks}
+    # the whole step against its compulsory HBM traffic
+    hbm_peak, hbm_src = read_peaks()
+    mbytes = sum(step_model_bytes(n, i, True, tuned.get("coarsest", 16)) for i in infos)
+    gbs = mbytes / (ms / 1e3) / 1e9
+    line["roofline_step"] = {"bound": "hbm", "bytes_per_step": mbytes / steps, "achieved": gbs, "peak": hbm_peak,
+                             "unit": "GB/s", "frac": gbs / hbm_peak, "peak_source": hbm_src,
+                             "model": "compulsory bytes of every kernel of the step (bench.py step_model_bytes) "
+                                      "from each step's iterations, restarts and second Gram-Schmidt passes"}
+    line["autotune"] = tune_info
+
+    if not args.quick:
+        line["fp64"] = fp64
 
         # roofline: each candidate kernel class is timed live (CUDA events around
         # every launch) during its own timed run; the largest share of the step
@@ -427,17 +492,57 @@ def bench_ours(args, ws, rank, local):
                        "d2h_bytes_per_step": dof * 8,
                        "note": "setup (sd_create from host K, hierarchy, coarse inverses) inside the timed region"}
 
-        # independent instances (uneven grids) and the serving loop, smaller
-        # versions of the batched and serving workloads
-        line["batch"] = bench_batch(sd, 64, 10, 16, seed=rank)
-        line["batch"]["per_instance_streams"] = bench_batch(sd, 64, 10, 16, seed=rank, lockstep=False)
-        line["serving"] = bench_serve(sd, 50.0, 40, 8)
+        # the other workloads: the mixed-precision 2048^2 case, the paper's
+        # pressure-driven problem, the 256 batched instances and the serving
+        # loop at three arrival rates
+        line["c3_2048"] = bench_c3(sd, torch, stream, rank)
+        line["paper_problem"] = bench_paper_problem(sd, torch, stream, rank)
+        line["batch"] = bench_batch(sd, 256, 10, 32, seed=rank)
+        line["batch"]["per_instance_streams"] = bench_batch(sd, 256, 10, 32, seed=rank, lockstep=False)
+        line["serving"] = [bench_serve(sd, rate, 60, 16) for rate in (20.0, 100.0, 500.0)]
 
         if rank == 0 and ws >= 1 and not args.no_cpu:
             line["cpu_baseline"] = cpu_oracle_sample(args.cpu_n, 20)
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
+
+
+def bench_c3(sd, torch, stream, rank: int, steps: int = 20):
+    """The mixed-precision workload: 2048^2 cells per subdomain, 20 implicit-Euler steps from the initial state in
+    each precision (setup outside the timed region), and the per-field difference of the two final states."""
+    from paper_2108_13229_gb300 import inputs as I
+    n = 2048
+    K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=rank)
+    dof = 4 * n * n + 2 * n
+    out, xs = {}, {}
+    for name, prec in (("mixed", sd.SD_MIXED), ("fp64", sd.SD_FP64)):
+        ms, infos, launches, _ = run_form(sd, torch, n, K, prec, steps, 0, stream, keep_fields=xs, name=name)
+        out[name] = {"value": dof * steps / (ms / 1e3), "ms_per_step": ms / steps,
+                     "iters_per_step": [i["iters"] for i in infos], "max_relres": max(i["relres"] for i in infos),
+                     "launches_per_step": launches / steps}
+    err = {k: float(np.linalg.norm(xs["mixed"][k] - xs["fp64"][k]) / np.linalg.norm(xs["fp64"][k]))
+           for k in xs["fp64"]}
+    return {"workload": "lognormal 2048x2048 (%d DoF), mu=1e-3, alpha_BJ=1, dt=0.05, %d steps from the initial "
+                        "state, rtol 1e-10, library defaults" % (dof, steps),
+            "unit": UNIT, "mixed": out["mixed"], "fp64": out["fp64"],
+            "mixed_over_fp64": out["mixed"]["value"] / out["fp64"]["value"], "rel_l2_mixed_vs_fp64": err}
+
+
+def bench_paper_problem(sd, torch, stream, rank: int, n: int = 1024, steps: int = 25):
+    """The paper's pressure-driven problem (Sec. 5: half-cosine inflow pressure over t_end = 25 steps, traction
+    sides, no slip on top, p = 0 at the porous-medium bottom) at 1024^2 on the log-normal workload's parameters."""
+    from paper_2108_13229_gb300 import inputs as I
+    K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=rank)
+    dof = 4 * n * n + 2 * n
+    ms, infos, launches, _ = run_form(sd, torch, n, K, sd.SD_MIXED, steps, 0, stream, tuned={"bc": sd.SD_BC_PAPER})
+    lat = [i["ms"] for i in infos]
+    return {"workload": "pressure-driven problem (bc 2), %dx%d cells (%d DoF), lognormal K, mu=1e-3, alpha_BJ=1, "
+                        "dt=0.05, %d steps from rest (the whole inflow ramp), rtol 1e-10" % (n, n, dof, steps),
+            "value": dof * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "iters_per_step": [i["iters"] for i in infos], "max_relres": max(i["relres"] for i in infos),
+            "launches_per_step": launches / steps}
 
 
 def bench_configs(sd, torch, steps_small: int = 10, steps_big: int = 5):

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsd.so")
-SOURCES = ["sd_ops.cu", "sd_krylov.cu", "sd_api.cu", "sd_serve.cu", "sd_noalloc.cu", "sd_tune.cu"]
+SOURCES = ["sd_ops.cu", "sd_krylov.cu", "sd_api.cu", "sd_serve.cu", "sd_noalloc.cu", "sd_tune.cu", "sd_wave.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

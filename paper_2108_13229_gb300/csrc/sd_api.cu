@@ -104,6 +104,10 @@ struct MG {
 };
 
 const int FUSE_N = 16;
+// levels up to this many cells per side take their residual and restriction
+// inside the pre-smoothing tile (latency-bound launches there; on larger
+// levels the wider halo it needs costs more than the two launches)
+const int RR_MAX_N = 256;
 const int SMALL_TILE_N = 256;  // levels up to this size smooth 4-row tiles (measured 1.4 % per step at 1024^2)  // grids with at most this many cells per side run fused (measured: 16 beats 32, most in FP64)
 
 int level_count(int n, int coarsest) {
@@ -251,7 +255,7 @@ void plan_all(sd_handle* h) {
   h->B1 = a.take<double>(len);
   h->V = a.take<double>((long long)(h->m + 1) * h->lenA);
   h->Z = a.take<double>((long long)h->m * h->lenA);
-  h->partial = a.take<double>((long long)h->nblk * 32);
+  h->partial = a.take<double>(std::max((long long)h->nblk * 32, 4 * resid_norms_blocks(n)));
   h->scal = a.take<double>(256);
   h->st = a.take<double>((long long)(h->m + 1) * h->m + 3 * h->m + 1);
   h->flag = a.take<double>(8);
@@ -567,11 +571,12 @@ double apply_bytes(const Geom& g, bool resid) {
 
 // ----------------------------------------------------------- V-cycles
 template <typename T>
-ChebSteps<T> steps_of(const Block<T>& B, int rows) {
+ChebSteps<T> steps_of(const Block<T>& B, int rows, int wave) {
   ChebSteps<T> cs;
   std::memset(&cs, 0, sizeof(cs));
   cs.ns = (int)B.cha.size();
   cs.rows = rows;
+  cs.wave = wave;
   for (int k = 0; k < cs.ns && k < 8; ++k) {
     cs.a[k] = B.cha[k];
     cs.c[k] = B.chc[k];
@@ -586,6 +591,23 @@ ChebSteps<T> steps_of(const Block<T>& B, int rows) {
 int tile_rows_of(const sd_handle* h, int n) {
   if (h->opt.tile_rows) return h->opt.tile_rows;
   return n <= SMALL_TILE_N ? 4 : n <= 1024 ? 8 : 16;
+}
+
+// register-column tile height of a cell-block level (tile = 2; 0:
+// shared-memory tiles on this level): 8 rows for tile_rows 8 or 16, else 4
+// (fewer registers, more warps in flight).  Measured at 1024^2 (mixed, per
+// launch): Darcy block, three steps, 16.8 us against 20.4 with 8-row shared-
+// memory tiles; pressure Laplacian, one step, 11.4 against 13.4; at 512^2 the
+// shared-memory tiles were faster (8.0 against 9.3), and for the velocity
+// block at every size (1024^2: 30.1 against 48.7), so levels below
+// SD_WAVE_MIN_N cells per side and the velocity block keep them.
+#ifndef SD_WAVE_MIN_N
+#define SD_WAVE_MIN_N 1024
+#endif
+int wave_rows_of(const sd_handle* h, int n) {
+  if (h->opt.tile != 2 || n < SD_WAVE_MIN_N) return 0;
+  if (h->opt.tile_rows) return h->opt.tile_rows >= 8 ? 8 : 4;
+  return 4;
 }
 
 // tiled smoothing (all steps of one smoothing in one kernel) is used for the
@@ -614,11 +636,16 @@ void vcycle_V(MG<T>& M, int l, cudaStream_t s, sd_handle* prof_owner) {
   MGLevel<T>& C = M.L[l + 1];
   T* cur = nullptr;
   const bool tiles = use_tiles(prof_owner, B);
-  const int h_tile_rows = tile_rows_of(prof_owner, L.g.n);
+  const int h_tile_rows = tile_rows_of(prof_owner, L.g.n), h_wave = 0;
+  bool fused = false;  // residual and restriction taken by the pre-smoothing tile
   if (tiles) {
     ProfScope ps(prof_owner, l == 0 ? SD_PROF_CHEB_V : -2, tile_bytes_V(L.g, sizeof(T), false));
-    if constexpr (std::is_same<T, float>::value)
-      launch_smooth_tile_V<T>(L.c, nullptr, B.b, B.x, steps_of(B, h_tile_rows), B.cht, nullptr, 0, 0, s);
+    if constexpr (std::is_same<T, float>::value) {
+      const ChebSteps<T> cs = steps_of(B, h_tile_rows, h_wave);
+      if (L.g.n <= RR_MAX_N)
+        fused = launch_smooth_tile_V_rr<T>(L.c, B.b, B.x, cs, B.cht, C.g.n, C.g.P, C.V.b, s) == 0;
+      if (!fused) launch_smooth_tile_V<T>(L.c, nullptr, B.b, B.x, cs, B.cht, nullptr, 0, 0, s);
+    }
     cur = B.x;
   } else {
     for (int k = 0; k < (int)B.cha.size(); ++k) {
@@ -630,14 +657,16 @@ void vcycle_V(MG<T>& M, int l, cudaStream_t s, sd_handle* prof_owner) {
       cur = out;
     }
   }
-  launch_resid_V<T>(L.c, cur, B.b, B.r, 0, 1, 0, s);
-  launch_restrict_V<T>(L.g.n, L.g.P, B.r, C.g.n, C.g.P, C.V.b, L.c.lat, s);
+  if (!fused) {
+    launch_resid_V<T>(L.c, cur, B.b, B.r, 0, 1, 0, s);
+    launch_restrict_V<T>(L.g.n, L.g.P, B.r, C.g.n, C.g.P, C.V.b, L.c.lat, s);
+  }
   vcycle_V(M, l + 1, s, prof_owner);
   if (tiles) {  // prolongation folded into the post-smoothing tile load
     T* out = (cur == B.x) ? B.x2 : B.x;
     ProfScope ps(prof_owner, l == 0 ? SD_PROF_CHEB_V : -2, tile_bytes_V(L.g, sizeof(T), true));
     if constexpr (std::is_same<T, float>::value)
-      launch_smooth_tile_V<T>(L.c, cur, B.b, out, steps_of(B, h_tile_rows), B.cht, C.V.res, C.g.n, C.g.P, s);
+      launch_smooth_tile_V<T>(L.c, cur, B.b, out, steps_of(B, h_tile_rows, h_wave), B.cht, C.V.res, C.g.n, C.g.P, s);
     cur = out;
   } else {
     launch_prolong_V<T>(L.g.n, L.g.P, cur, C.g.n, C.g.P, C.V.res, L.c.lat, s);
@@ -673,10 +702,14 @@ void vcycle_cell(MG<T>& M, int l, bool poisson, cudaStream_t s, const sd_handle*
   Block<T>& BC = poisson ? C.Pb : C.D;
   T* cur = nullptr;
   const bool tiles = use_tiles(h, B);
-  const int h_tile_rows = tile_rows_of(h, L.g.n);
+  const int h_tile_rows = tile_rows_of(h, L.g.n), h_wave = wave_rows_of(h, L.g.n);
+  bool fused = false;  // residual and restriction taken by the pre-smoothing tile
   if (tiles) {
-    if constexpr (std::is_same<T, float>::value)
-      launch_smooth_tile_D<T>(c, nullptr, B.b, B.x, steps_of(B, h_tile_rows), B.cht, nullptr, 0, 0, s);
+    if constexpr (std::is_same<T, float>::value) {
+      const ChebSteps<T> cs = steps_of(B, h_tile_rows, h_wave);
+      if (L.g.n <= RR_MAX_N) fused = launch_smooth_tile_D_rr<T>(c, B.b, B.x, cs, B.cht, C.g.n, C.g.P, BC.b, s) == 0;
+      if (!fused) launch_smooth_tile_D<T>(c, nullptr, B.b, B.x, cs, B.cht, nullptr, 0, 0, s);
+    }
     cur = B.x;
   } else {
     for (int k = 0; k < (int)B.cha.size(); ++k) {
@@ -685,12 +718,12 @@ void vcycle_cell(MG<T>& M, int l, bool poisson, cudaStream_t s, const sd_handle*
       cur = out;
     }
   }
-  launch_resid_restrict_D<T>(c, cur, B.b, C.g.n, C.g.P, BC.b, s);
+  if (!fused) launch_resid_restrict_D<T>(c, cur, B.b, C.g.n, C.g.P, BC.b, s);
   vcycle_cell(M, l + 1, poisson, s, h);
   if (tiles) {  // prolongation folded into the post-smoothing tile load
     T* out = (cur == B.x) ? B.x2 : B.x;
     if constexpr (std::is_same<T, float>::value)
-      launch_smooth_tile_D<T>(c, cur, B.b, out, steps_of(B, h_tile_rows), B.cht, BC.res, C.g.n, C.g.P, s);
+      launch_smooth_tile_D<T>(c, cur, B.b, out, steps_of(B, h_tile_rows, h_wave), B.cht, BC.res, C.g.n, C.g.P, s);
     cur = out;
   } else {
     launch_prolong_D<T>(L.g.n, L.g.P, cur, C.g.n, C.g.P, BC.res, s);
@@ -827,6 +860,26 @@ void apply_op(sd_handle* h, int mode, const double* x, const double* b, double* 
   }
 }
 
+// V_0 = b - A x and ||V_0||^2 into scal[S_B2] (with with_b also ||b||^2 into
+// scal[S_BN]).  For the whole system the residual kernel forms the norms
+// itself, together with the per-block norms scal[S_BLK + 0..2] (velocity,
+// continuity and Darcy rows) that the step reports, so no separate dot
+// products run.
+void resid_norms(sd_handle* h, int mode, const double* x, const double* b, bool with_b) {
+  double* sc = h->scal;
+  if (mode == MODE_MONO) {
+    launch_resid_norms(coef64(h, 0), x, b, h->V, h->partial, sc, sd_handle::S_BLK, sd_handle::S_B2,
+                       sd_handle::S_BN, with_b ? 1 : 0, h->s);
+    return;
+  }
+  const Range rg = mode_range(h, mode);
+  const long long len = rg.len, o = rg.off;
+  const int nb = reduce_blocks(len);
+  if (with_b) launch_dot(b + o, b + o, len, h->partial, nb, sc + sd_handle::S_BN, h->s);
+  apply_op(h, mode, x, b, h->V);
+  launch_dot(h->V + o, h->V + o, len, h->partial, nb, sc + sd_handle::S_B2, h->s);
+}
+
 // Subdomain preconditioners: the free-flow part of the block preconditioner
 // (Schur block and velocity V-cycle, no Darcy block) and the D' V-cycle.
 template <typename T>
@@ -951,7 +1004,7 @@ int block_residuals(sd_handle* h, double bnorm, sd_step_info* info) {
 // finish_block_residuals fills them in after the caller's next
 // synchronisation of the stream (one host wait less per step).
 int queue_block_residuals(sd_handle* h, double bnorm) {
-  block_residual_dots(h);
+  // the last whole-system residual (resid_norms) left them in S_BLK
   CK(cudaMemcpyAsync(h->hflag + 12, h->scal + sd_handle::S_BLK, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->s));
   h->blk_pending = true;
   h->blk_bnorm = bnorm;
@@ -1051,10 +1104,8 @@ int build_solve_graph(sd_handle* h, int mode, const double* b, double* x) {
   // ||b||, the first true residual, and whether a cycle runs
   if (begin(top, false)) {
     const long long l0 = t_launch_count;
-    launch_dot(b + o, b + o, len, h->partial, nb, sc + sd_handle::S_BN, s);
+    resid_norms(h, mode, x, b, true);
     launch_solve_begin(sc + sd_handle::S_BN, mode_rtol(h, mode), mode_accept(h, mode), ctl, s);
-    apply_op(h, mode, x, b, h->V);
-    launch_dot(h->V + o, h->V + o, len, h->partial, nb, sc + sd_handle::S_B2, s);
     launch_restart_ctrl(sc + sd_handle::S_B2, ctl, maxit, 0.0, loop, s);
     pre = t_launch_count - l0;
     end(true);
@@ -1093,23 +1144,13 @@ int build_solve_graph(sd_handle* h, int mode, const double* b, double* x) {
     launch_backsolve(h->st, m, m, sc + sd_handle::S_Y, h->flag + 5, s);
     t_pdl = pdl;
     launch_axpy_multi(x + o, h->Z + o, vs, sc + sd_handle::S_Y, m, len, h->flag + 5, s);
-    apply_op(h, mode, x, b, h->V);
-    launch_dot(h->V + o, h->V + o, len, h->partial, nb, sc + sd_handle::S_B2, s);
+    resid_norms(h, mode, x, b, false);
     const long long k = t_launch_count - l0 + 1;
     launch_restart_ctrl(sc + sd_handle::S_B2, ctl, maxit, (double)k, loop, s);
     end(false);
   }
-  if (mode == MODE_MONO) {
-    deps = after_loop;
-    if (begin(top, true)) {
-      const long long l0 = t_launch_count;
-      t_pdl = 0;
-      block_residual_dots(h);
-      t_pdl = pdl;
-      post = t_launch_count - l0;
-      end(false);
-    }
-  }
+  // (the per-block residual norms of the whole system are left in S_BLK by
+  // the last residual inside the loop)
   t_pdl = pdl;
   if (capturing) end(false);
   if (err == cudaSuccess) err = cudaGraphInstantiate(&ex, top, 0);
@@ -1186,9 +1227,7 @@ int fgmres(sd_handle* h, const double* b, double* x, sd_step_info* info, int mod
   double* sc = h->scal;
   // ||b|| and the first true residual V_0 = b - A x, read back together (S_B2
   // and S_BN are adjacent slots)
-  launch_dot(b + o, b + o, len, h->partial, nb, sc + sd_handle::S_BN, s);
-  apply_op(h, mode, x, b, h->V);
-  launch_dot(h->V + o, h->V + o, len, h->partial, nb, sc + sd_handle::S_B2, s);
+  resid_norms(h, mode, x, b, true);
   CK(cudaMemcpyAsync(h->hflag + 5, sc + sd_handle::S_B2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   const double bnorm = std::sqrt(h->hflag[6]);
@@ -1200,8 +1239,7 @@ int fgmres(sd_handle* h, const double* b, double* x, sd_step_info* info, int mod
   bool first = true;
   for (;;) {
     if (!first) {
-      apply_op(h, mode, x, b, h->V);  // V_0 = b - A x
-      launch_dot(h->V + o, h->V + o, len, h->partial, nb, sc + sd_handle::S_B2, s);
+      resid_norms(h, mode, x, b, false);  // V_0 = b - A x
       CK(cudaMemcpyAsync(h->hflag + 5, sc + sd_handle::S_B2, sizeof(double), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
     }
@@ -1442,6 +1480,7 @@ int validate(const sd_grid* grid, double mu, double alpha, double dt, const sd_o
   if (o->graph < 0 || o->graph > 2) return SD_E_INVAL;
   if (o->extrapolate < 0 || o->extrapolate > 3) return SD_E_INVAL;
   if (o->darcy_coupled < 0 || o->darcy_coupled > 2) return SD_E_INVAL;
+  if (o->tile < 0 || o->tile > 2) return SD_E_INVAL;
   if (o->tile_rows != 0 && o->tile_rows != 4 && o->tile_rows != 8 && o->tile_rows != 16) return SD_E_INVAL;
   if (o->coupling != SD_MONOLITHIC && o->coupling != SD_PARTITIONED) return SD_E_INVAL;
   if (o->coupling_order < SD_ORDER_AUTO || o->coupling_order > SD_ORDER_FF_FIRST) return SD_E_INVAL;
@@ -1661,9 +1700,7 @@ int fgmres_lockstep(Lockstep& L, std::vector<sd_step_info>& si) {
   L.act.assign(B, 1);
   CKR(set_act(L, s));
   // ||b|| and the first true residual, gathered together (S_B2, S_BN adjacent)
-  launch_dot(h->b, h->b, len, h->partial, nb, sc + sd_handle::S_BN, s);
-  launch_apply_full(c, h->x, h->b, h->V, s);  // V_0 = b - A x
-  launch_dot(h->V, h->V, len, h->partial, nb, sc + sd_handle::S_B2, s);
+  resid_norms(h, MODE_MONO, h->x, h->b, true);  // V_0 = b - A x
   CKR(gather(L, sc + sd_handle::S_B2, 2, s));
   for (int i = 0; i < B; ++i) {
     bnorm[i] = std::sqrt(L.gat_host[(size_t)i * 2 + 1]);
@@ -1675,8 +1712,7 @@ int fgmres_lockstep(Lockstep& L, std::vector<sd_step_info>& si) {
     if (!first) {
       for (int i = 0; i < B; ++i) L.act[i] = live[i];
       CKR(set_act(L, s));
-      launch_apply_full(c, h->x, h->b, h->V, s);  // V_0 = b - A x
-      launch_dot(h->V, h->V, len, h->partial, nb, sc + sd_handle::S_B2, s);
+      resid_norms(h, MODE_MONO, h->x, h->b, false);  // V_0 = b - A x
       CKR(gather(L, sc + sd_handle::S_B2, 1, s));
     }
     first = false;
@@ -1755,11 +1791,11 @@ int fgmres_lockstep(Lockstep& L, std::vector<sd_step_info>& si) {
     launch_backsolve(h->st, m, m, sc + sd_handle::S_Y, h->flag + 5, s);
     launch_axpy_multi(h->x, h->Z, vs, sc + sd_handle::S_Y, m, len, h->flag + 5, s);
   }
-  // per-block residuals: every instance's last residual is still in its V_0
-  // (its kernels were idle since), unless a cycle of it ended on NaN/Inf
+  // per-block residual norms: every instance's last residual left them in
+  // its S_BLK (its kernels were idle since), unless a cycle of it ended on
+  // NaN/Inf
   L.act.assign(B, 1);
   CKR(set_act(L, s));
-  block_residual_dots(h);
   CKR(gather(L, sc + sd_handle::S_BLK, 3, s));
   CK(cudaGetLastError());
   for (int i = 0; i < B; ++i) {
@@ -1860,7 +1896,7 @@ void sd_options_default(sd_options* o) {
   o->extrapolate = 2;
   o->graph = 1;
   o->pdl = 1;
-  o->tile = 1;
+  o->tile = 2;
   o->tile_rows = 0;
   o->darcy_coupled = 1;
   o->coupling = SD_MONOLITHIC;

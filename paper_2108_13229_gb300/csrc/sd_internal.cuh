@@ -179,6 +179,12 @@ void launch_convert(const double* src, T* dst, long long len, cudaStream_t s);
 
 // whole-system operator (FP64): y = A x  or  y = b - A x
 void launch_apply_full(const Coef<double>& c, const double* x, const double* b, double* y, cudaStream_t s);
+// r = b - A x together with its norms: sc[blk + 0..2] = ||r||^2 over the
+// velocity, continuity and Darcy rows, sc[b2] = ||r||^2, and with with_b
+// sc[bn] = ||b||^2 (partial: 4 * resid_norms_blocks(n) doubles of scratch)
+void launch_resid_norms(const Coef<double>& c, const double* x, const double* b, double* r, double* partial,
+                        double* sc, int blk, int b2, int bn, int with_b, cudaStream_t s);
+long long resid_norms_blocks(int n);
 // the free-flow rows of it (u, v, p_ff) with the porous-medium unknowns taken as zero;
 // the Darcy rows of y are not written; vdir: the v_Gamma rows are identities
 void launch_apply_ff(const Coef<double>& c, const double* x, const double* b, double* y, int vdir, cudaStream_t s);
@@ -290,6 +296,7 @@ template <typename T>
 struct ChebSteps {
   int ns;
   int rows;  // tiled smoothing: output rows per tile (8 or 16)
+  int wave;  // FP32: 0, or the output rows per warp strip (8, 16, 32) of the register wavefront
   T a[8], c[8];
 };
 // Tiled smoothing: ns Chebyshev steps in one kernel, x_out = S(x_in + P ec)
@@ -302,6 +309,26 @@ int launch_smooth_tile_D(const Coef<T>& c, const T* x_in, const T* b, T* x_out, 
 template <typename T>
 int launch_smooth_tile_V(const Coef<T>& c, const T* x_in, const T* b, T* x_out, const ChebSteps<T>& cs, const T* ct,
                          const T* ec, int nc, int Pc, cudaStream_t s);
+
+// Pre-smoothing from zero that also forms the level's residual and restricts
+// it to the coarse right-hand side bco (nc cells per side, pitch Pc): the
+// smoothing of launch_smooth_tile_V/D plus the residual and restriction
+// kernels of the level, the same values.  Returns -1 (nothing launched) for
+// other tile heights, register-column tiles or an odd grid.
+template <typename T>
+int launch_smooth_tile_V_rr(const Coef<T>& c, const T* b, T* x_out, const ChebSteps<T>& cs, const T* ct, int nc,
+                            int Pc, T* bco, cudaStream_t s);
+template <typename T>
+int launch_smooth_tile_D_rr(const Coef<T>& c, const T* b, T* x_out, const ChebSteps<T>& cs, const T* ct, int nc,
+                            int Pc, T* bco, cudaStream_t s);
+
+// Register-wavefront smoothing (sd_wave.cu): the same steps and result as
+// the tiled kernels above, with cs.wave output rows per warp strip; returns -1
+// (nothing launched) for ns > 4 or an unsupported strip height.
+int launch_wave_V(const Coef<float>& c, const float* x_in, const float* b, float* x_out, const ChebSteps<float>& cs,
+                  const float* ct, const float* ec, int nc, int Pc, cudaStream_t s);
+int launch_wave_D(const Coef<float>& c, const float* x_in, const float* b, float* x_out, const ChebSteps<float>& cs,
+                  const float* ct, const float* ec, int nc, int Pc, cudaStream_t s);
 
 // preconditioner glue on the fine level (Sec. 4 block preconditioners):
 //  entry: zpf = schur * r_pf + cmass * eP (eP: pressure-Laplacian solve, may be

@@ -21,8 +21,11 @@
 //  p_pm cell: sum_f T_f (p - p_nb) + h vG (top row)       [Eqs. (3),(4),(7); C'_1]
 //  Dirichlet velocity faces: identity rows, eliminated from all other rows.
 #include "sd_internal.cuh"
+#include "sd_rows.cuh"
 
 #include <math.h>
+
+#include <type_traits>
 
 namespace sdk {
 
@@ -37,214 +40,86 @@ static inline int rows_cell(int n) { return n >= 1024 ? 4 : 1; }
 static inline int rows_vel(int) { return 1; }
 static inline dim3 grid2R(int nx, int ny, int R) { return dim3((nx + BX - 1) / BX, (ny + BY * R - 1) / (BY * R)); }
 
-// Jacobi-scaled update term r / diag of the smoothers: the fast FP32
-// division in the FP32 hierarchy (a smoother needs no correctly rounded
-// quotient), the IEEE division in FP64
-__device__ __forceinline__ float sdiv(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ double sdiv(double a, double b) { return a / b; }
-
-// ------------------------------------------------------------------ rows
-// Each row function loads every neighbour it may need from an in-range
-// (clamped) address first and masks the terms that do not exist at a
-// boundary with selects, so the loads of a row can be issued together.
-// Terms are accumulated in a fixed order.
-//
-// Off-diagonal part and diagonal of the velocity-block row of interior u face (i, j).
-// IN: the caller guarantees 2 <= i <= n-2 and 1 <= j <= n-2 (no boundary term
-// applies); the same operations in the same order, without the masks.
-template <typename T, bool IN = false>
-__device__ __forceinline__ void u_row(const Coef<T>& c, const T* __restrict__ u, const T* __restrict__ v, int i,
-                                      int j, bool read, T& off, T& diag) {
-  const int n = c.n, P = c.P;
-  const T mu = c.mu;
-  const bool top = !IN && j == n - 1, bot = !IN && j == 0;
-  T dg = c.d6;  // interior: h^2/dt + 4 mu (normal stress) + mu + mu (shear)
-  T wh = T(0);
-  if (top) dg += mu;  // wall at half distance above: 2 mu instead of mu
-  if (bot) {          // Gamma below: BJS shear instead of mu
-    wh = c.w[i] * c.h;
-    dg += T(2) * wh - mu;
-  }
-  diag = dg;
-  if (!read) {
-    off = T(0);
-    return;
-  }
-  const int r0 = j * P, rN = (top ? j : j + 1) * P, rS = (bot ? j : j - 1) * P;
-  const int rv1 = (j + 1) * P;
-  const T uW = u[r0 + i - 1], uE = u[r0 + i + 1], uN = u[rN + i], uS = u[rS + i];
-  const T vN = v[rv1 + i], vNW = v[rv1 + i - 1], vS = v[r0 + i], vSW = v[r0 + i - 1];
-  const T cW = (IN || c.lat || i - 1 >= 1) ? c.m2 : T(0), cE = (IN || c.lat || i + 1 <= n - 1) ? c.m2 : T(0);
-  T of = cW * uW;
-  of = fma(cE, uE, of);
-  if (!top) {
-    of = fma(c.m1, uN, of);
-    of = fma(c.m1, vN, of);
-    of = fma(mu, vNW, of);
-  }
-  if (!bot) {
-    of = fma(c.m1, uS, of);
-    of = fma(mu, vS, of);
-    of = fma(c.m1, vSW, of);
-  } else {
-    of = fma(wh, vS - vSW, of);
-  }
-  off = of;
-}
-
-// Same for the v face (i, j), 0 <= j <= n-1 (j = 0: interface half control volume).
-// IN: 1 <= i <= n-2 and 1 <= j <= n-2.
-template <typename T, bool IN = false>
-__device__ __forceinline__ void v_row(const Coef<T>& c, const T* __restrict__ u, const T* __restrict__ v, int i,
-                                      int j, bool read, T& off, T& diag) {
-  const int n = c.n, P = c.P;
-  const T mu = c.mu, h = c.h;
-  const bool left = !IN && i == 0, right = !IN && i == n - 1;
-  if (!IN && j == 0) {
-    // corners: BJS (interior, or a traction side's corner at half distance)
-    // or a Dirichlet side at half distance
-    const T wl = (left && !c.lat) ? T(0) : c.w[i], wr = (right && !c.lat) ? T(0) : c.w[i + 1];
-    T dg = T(0.5) * c.cm + T(2) * mu + c.rg[i];
-    dg += left ? (c.lat ? h * wl : mu) : T(0.5) * h * wl;
-    dg += right ? (c.lat ? h * wr : mu) : T(0.5) * h * wr;
-    diag = dg;
-    if (!read) {
-      off = T(0);
-      return;
-    }
-    const T v1 = v[P + i], uL = u[i], uR = u[i + 1];
-    const T vL = v[left ? i : i - 1], vR = v[right ? i : i + 1];
-    T of = c.m2 * v1;
-    if (!left) {
-      of = fma(wl * h, uL, of);
-      of = fma(T(-0.5) * h * wl, vL, of);
-    } else if (c.lat) {
-      of = fma(wl * h, uL, of);
-    }
-    if (!right) {
-      of = fma(-wr * h, uR, of);
-      of = fma(T(-0.5) * h * wr, vR, of);
-    } else if (c.lat) {
-      of = fma(-wr * h, uR, of);
-    }
-    off = of;
-    return;
-  }
-  T dg = c.d6;
-  if (right) dg += mu;
-  if (left) dg += mu;
-  diag = dg;
-  if (!read) {
-    off = T(0);
-    return;
-  }
-  const int r0 = j * P, rm = (j - 1) * P, rp = (j + 1) * P;
-  const int iE = right ? i : i + 1, iW = left ? i : i - 1;
-  const T vS = v[rm + i], vN = v[rp + i], vE = v[r0 + iE], vW = v[r0 + iW];
-  const T uE = u[r0 + i + 1], uES = u[rm + i + 1], uW = u[r0 + i], uWS = u[rm + i];
-  const T cN = (IN || j + 1 <= n - 1) ? c.m2 : T(0);
-  T of = c.m2 * vS;
-  of = fma(cN, vN, of);
-  if (!right) {
-    of = fma(c.m1, vE, of);
-    of = fma(c.m1, uE, of);
-    of = fma(mu, uES, of);
-  } else if (c.lat) {  // traction side: its u faces are unknowns
-    of = fma(c.m1, uE, of);
-    of = fma(mu, uES, of);
-  }
-  if (!left) {
-    of = fma(c.m1, vW, of);
-    of = fma(mu, uW, of);
-    of = fma(c.m1, uWS, of);
-  } else if (c.lat) {
-    of = fma(mu, uW, of);
-    of = fma(c.m1, uWS, of);
-  }
-  off = of;
-}
-
-// Side u face (i = 0 or n) of a traction side: x-momentum balance of the
-// half control volume inside the domain (as v_Gamma for the interface):
-// normal stress through the adjacent cell centre (the side's traction goes
-// to the right-hand side), shear through its top and bottom at the side,
-// from the side's tangential velocity at half distance, the wall above the
-// top row at half distance, and at the interface corner the eliminated BJS
-// slip of Eq. (6).  The pressure term is added by the caller.
-template <typename T>
-__device__ __forceinline__ void ub_row(const Coef<T>& c, const T* __restrict__ u, const T* __restrict__ v, int i,
-                                       int j, bool read, T& off, T& diag) {
-  const int n = c.n, P = c.P;
-  const T mu = c.mu;
-  const bool rt = i == n, top = j == n - 1, bot = j == 0;
-  const T wh = bot ? c.w[i] * c.h : T(0);
-  T dg = T(0.5) * c.cm + T(2) * mu;
-  dg += top ? mu : T(0.5) * mu;
-  dg += bot ? wh : T(0.5) * mu;
-  diag = dg;
-  if (!read) {
-    off = T(0);
-    return;
-  }
-  const int r0 = j * P;
-  const int ii = rt ? n - 1 : 1, ic = rt ? n - 1 : 0;
-  const T sg = rt ? T(-1) : T(1);
-  T of = c.m2 * u[r0 + ii];
-  if (!top) {
-    of = fma(T(-0.5) * mu, u[r0 + P + i], of);
-    of = fma(-sg * mu, v[r0 + P + ic], of);
-  }
-  if (!bot) {
-    of = fma(T(-0.5) * mu, u[r0 - P + i], of);
-    of = fma(sg * mu, v[r0 + ic], of);
-  } else {
-    of = fma(sg * wh, v[ic], of);
-  }
-  off = of;
-}
-
-// Darcy row of pm cell (i, j) (D' block only, no interface flux).
-// IN: 1 <= i <= n-2 and 1 <= j <= n-2.
-template <typename T, bool IN = false>
-__device__ __forceinline__ void d_row(const Coef<T>& c, const T* __restrict__ p, int i, int j, bool read, T& off,
-                                      T& diag) {
-  const int n = c.n, P = c.P;
-  const int r0 = j * P;
-  const T tw = c.Tx[r0 + i], te = c.Tx[r0 + i + 1];
-  const T ts = c.Ty[r0 + i], tn = c.Ty[r0 + P + i];
-  diag = (tw + te) + (ts + tn);
-  if (!read) {
-    off = T(0);
-    return;
-  }
-  const T pW = p[r0 + ((IN || i > 0) ? i - 1 : i)], pE = p[r0 + ((IN || i < n - 1) ? i + 1 : i)];
-  const T pS = p[((IN || j > 0) ? r0 - P : r0) + i], pN = p[((IN || j < n - 1) ? r0 + P : r0) + i];
-  const T cW = (IN || i > 0) ? tw : T(0), cE = (IN || i < n - 1) ? te : T(0);
-  const T cS = (IN || j > 0) ? ts : T(0), cN = (IN || j < n - 1) ? tn : T(0);
-  T of = cW * pW;
-  of = fma(cE, pE, of);
-  of = fma(cS, pS, of);
-  of = fma(cN, pN, of);
-  off = -of;
-}
-
 // ------------------------------------------------------- whole operator (K1)
 // FF 1: the free-flow rows only (u, v, p_ff), with the porous-medium unknowns
 // taken as zero and the Darcy rows not written (subdomain solve of the
 // partitioned coupling); FF 2: the same with the v_Gamma rows replaced by
 // identities (the interface velocity prescribed).
-template <int R, int FF>
-__global__ void k_apply_full(Coef<double> c, const double* __restrict__ x, const double* __restrict__ b,
-                             double* __restrict__ y, Bat bt) {
-  griddep_wait();
-  long long o;
-  if (!bat_enter(bt, o)) return;
-  if (bt.off) {
-    bsh_coef(c, o);
-    x = bsh(x, o);
-    b = bsh(b, o);
-    y = bsh(y, o);
+// Interior cells of the whole operator (FF 0): every row as one chain of
+// fused multiply-adds from b (RES: y = b - A x) or from its first product (y
+// = A x), its coefficients signed once per thread, so each stored matrix
+// entry costs one FP64 instruction (the Darcy diagonal adds three).  The
+// caller guarantees 2 <= i <= n-2 and 1 <= j <= n-2.
+template <bool RES, int PS>
+__device__ __forceinline__ void apply_cell_interior(const Coef<double>& c, const double* __restrict__ u,
+                                                    const double* __restrict__ v, const double* __restrict__ pf,
+                                                    const double* __restrict__ pm, const double* __restrict__ b,
+                                                    double* __restrict__ y, long long kc, long long nv,
+                                                    long long npf, long long npm, double* acc) {
+  const int P = c.P;
+  const double sg = RES ? -1.0 : 1.0;
+  const double kd = sg * c.d6, k2 = sg * c.m2, k1 = sg * c.m1, km = sg * c.mu, kh = sg * c.h;
+  {  // u face: d6 u + m2 (uW + uE) + m1 (uN + vN + uS + vSW) + mu (vNW + vS) + h (pf - pfW)
+    double a = RES ? fma(kd, u[kc], b[kc]) : kd * u[kc];
+    a = fma(k2, u[kc - 1], a);
+    a = fma(k2, u[kc + 1], a);
+    a = fma(k1, u[kc + P], a);
+    a = fma(k1, v[kc + P], a);
+    a = fma(km, v[kc + P - 1], a);
+    a = fma(k1, u[kc - P], a);
+    a = fma(km, v[kc], a);
+    a = fma(k1, v[kc - 1], a);
+    a = fma(kh, pf[kc], a);
+    a = fma(-kh, pf[kc - 1], a);
+    y[kc] = a;
+    if (PS) acc[0] = fma(a, a, acc[0]);
+    if (PS == 2) acc[3] = fma(b[kc], b[kc], acc[3]);
   }
+  {  // v face: d6 v + m2 (vS + vN) + m1 (vE + uE + vW + uWS) + mu (uES + uW) + h (pf - pfS)
+    double a = RES ? fma(kd, v[kc], b[nv + kc]) : kd * v[kc];
+    a = fma(k2, v[kc - P], a);
+    a = fma(k2, v[kc + P], a);
+    a = fma(k1, v[kc + 1], a);
+    a = fma(k1, u[kc + 1], a);
+    a = fma(km, u[kc + 1 - P], a);
+    a = fma(k1, v[kc - 1], a);
+    a = fma(km, u[kc], a);
+    a = fma(k1, u[kc - P], a);
+    a = fma(kh, pf[kc], a);
+    a = fma(-kh, pf[kc - P], a);
+    y[nv + kc] = a;
+    if (PS) acc[0] = fma(a, a, acc[0]);
+    if (PS == 2) acc[3] = fma(b[nv + kc], b[nv + kc], acc[3]);
+  }
+  {  // continuity: h (uE - uW + vN - vS)
+    double a = RES ? fma(kh, u[kc + 1], b[npf + kc]) : kh * u[kc + 1];
+    a = fma(-kh, u[kc], a);
+    a = fma(kh, v[kc + P], a);
+    a = fma(-kh, v[kc], a);
+    y[npf + kc] = a;
+    if (PS) acc[1] = fma(a, a, acc[1]);
+    if (PS == 2) acc[3] = fma(b[npf + kc], b[npf + kc], acc[3]);
+  }
+  {  // Darcy: (tw + te + ts + tn) p - tw pW - te pE - ts pS - tn pN
+    const double tw = c.Tx[kc], te = c.Tx[kc + 1], ts = c.Ty[kc], tn = c.Ty[kc + P];
+    const double kg = sg * ((tw + te) + (ts + tn));
+    double a = RES ? fma(kg, pm[kc], b[npm + kc]) : kg * pm[kc];
+    a = fma(-sg * tw, pm[kc - 1], a);
+    a = fma(-sg * te, pm[kc + 1], a);
+    a = fma(-sg * ts, pm[kc - P], a);
+    a = fma(-sg * tn, pm[kc + P], a);
+    y[npm + kc] = a;
+    if (PS) acc[2] = fma(a, a, acc[2]);
+    if (PS == 2) acc[3] = fma(b[npm + kc], b[npm + kc], acc[3]);
+  }
+}
+
+// The operator's rows of this thread (i, j0 .. j0+R-1).  PS (with RES):
+// acc[0..2] += the squared residuals of the velocity, continuity and Darcy
+// rows; PS 2: also acc[3] += the squared right-hand side of every row.
+template <int R, int FF, bool RES, int PS>
+__device__ __forceinline__ void apply_body(const Coef<double>& c, const double* __restrict__ x,
+                                           const double* __restrict__ b, double* __restrict__ y, double* acc) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
   const int n = c.n, P = c.P;
@@ -253,6 +128,14 @@ __global__ void k_apply_full(Coef<double> c, const double* __restrict__ x, const
   // the rows without their boundary cases (the same operations in the same
   // order for every interior point), so no masked FP64 work is issued
   const int bi = blockIdx.x * blockDim.x, bj = blockIdx.y * blockDim.y * R;
+  if (FF == 0 && bi >= 2 && bi + (int)blockDim.x - 1 <= n - 2 && bj >= 1 && bj + (int)blockDim.y * R - 1 <= n - 2) {
+    const long long nv = (long long)n * P, npf = (long long)(2 * n + 1) * P, npm = (long long)(3 * n + 1) * P;
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr)
+      apply_cell_interior<RES, PS>(c, x, x + nv, x + npf, x + npm, b, y, (long long)(j0 + rr) * P + i, nv, npf, npm,
+                                   acc);
+    return;
+  }
   if (bi >= 2 && bi + (int)blockDim.x - 1 <= n - 2 && bj >= 1 && bj + (int)blockDim.y * R - 1 <= n - 2) {
     const double h = c.h;
     const double* u = x;
@@ -315,7 +198,12 @@ __global__ void k_apply_full(Coef<double> c, const double* __restrict__ x, const
         u_row(c, u, v, i, j, true, off, dg);
         val = dg * u[k] + off + h * (pf[k] - pf[k - 1]);
       }
-      y[k] = b ? b[k] - val : val;
+      {
+        const double r_ = b ? b[k] - val : val;
+        y[k] = r_;
+        if (PS) acc[0] = fma(r_, r_, acc[0]);
+        if (PS == 2) acc[3] = fma(b[k], b[k], acc[3]);
+      }
     }
     if (i < n) {
       const long long kv = (long long)j * P + i;
@@ -331,7 +219,12 @@ __global__ void k_apply_full(Coef<double> c, const double* __restrict__ x, const
         else if (FF) val += h * pf[i];
         else val += h * pf[i] - h * pm[(long long)(n - 1) * P + i];
       }
-      y[k] = b ? b[k] - val : val;
+      {
+        const double r_ = b ? b[k] - val : val;
+        y[k] = r_;
+        if (PS) acc[0] = fma(r_, r_, acc[0]);
+        if (PS == 2) acc[3] = fma(b[k], b[k], acc[3]);
+      }
     }
     if (i < n && j < n) {
       const long long kc = (long long)j * P + i;
@@ -340,24 +233,154 @@ __global__ void k_apply_full(Coef<double> c, const double* __restrict__ x, const
       if (c.lat || i >= 1) s -= u[kc];
       if (j + 1 <= n - 1) s += v[kc + P];
       const long long kp = (long long)(2 * n + 1) * P + kc;
-      y[kp] = b ? b[kp] - h * s : h * s;
+      {
+        const double val = h * s;
+        {
+          const double r_ = b ? b[kp] - val : val;
+          y[kp] = r_;
+          if (PS) acc[1] = fma(r_, r_, acc[1]);
+          if (PS == 2) acc[3] = fma(b[kp], b[kp], acc[3]);
+        }
+      }
       if (FF) continue;
       double off, dg;
       d_row(c, pm, i, j, true, off, dg);
       double val = dg * pm[kc] + off;
       if (j == n - 1) val += h * v[i];
       const long long km = (long long)(3 * n + 1) * P + kc;
-      y[km] = b ? b[km] - val : val;
+      {
+        const double r_ = b ? b[km] - val : val;
+        y[km] = r_;
+        if (PS) acc[2] = fma(r_, r_, acc[2]);
+        if (PS == 2) acc[3] = fma(b[km], b[km], acc[3]);
+      }
     }
   }
+}
+
+// PS: the block's sums of acc (apply_body) in partial[q * nblocks + block],
+// q = 0..2 (PS 2: 0..3), in a fixed order, so repeated runs agree bit for
+// bit.  FP64 adds are scarce on this part, so the block sums its values
+// through shared memory with one warp per quantity (eight serial adds per
+// lane, then five butterfly rounds) rather than a butterfly in every warp.
+template <int R, int FF, bool RES, int PS = 0>
+__global__ void __launch_bounds__(BX * BY, PS ? 3 : 4) k_apply_full(Coef<double> c, const double* __restrict__ x, const double* __restrict__ b,
+                             double* __restrict__ y, double* __restrict__ partial, Bat bt) {
+  griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  if (bt.off) {
+    bsh_coef(c, o);
+    x = bsh(x, o);
+    b = bsh(b, o);
+    y = bsh(y, o);
+    partial = bsh(partial, o);
+  }
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  apply_body<R, FF, RES, PS>(c, x, b, y, acc);
+  if constexpr (PS > 0) {
+    constexpr int NQ = PS == 2 ? 4 : 3;
+    __shared__ double red[4][BX * BY];
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) red[q][t] = acc[q];
+    __syncthreads();
+    const int wp = t >> 5, lane = t & 31;
+    if (wp < NQ) {
+      const double* r = red[wp] + lane * (BX * BY / 32);
+      double v = r[0];
+#pragma unroll
+      for (int e = 1; e < BX * BY / 32; ++e) v += r[e];
+#pragma unroll
+      for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+      if (lane == 0) {
+        const long long nbk = (long long)gridDim.x * gridDim.y;
+        partial[wp * nbk + (long long)blockIdx.y * gridDim.x + blockIdx.x] = v;
+      }
+    }
+  }
+}
+
+// sc[blk + q] (q = 0..2) = the sums of squares of the residual's velocity,
+// continuity and Darcy rows, sc[b2] = their total ((q0 + q1) + q2), and with
+// with_b sc[bn] = the sum of squares of b; from the block partials of
+// k_apply_full<.., PS>, each summed in a fixed order (every thread's partials
+// loaded at once, then one warp per quantity).
+__global__ void __launch_bounds__(256) k_reduce_resid(const double* __restrict__ partial, int nbk,
+                                                      double* __restrict__ sc, int blk, int b2, int bn, int with_b,
+                                                      Bat bt) {
+  griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  if (bt.off) {
+    partial = bsh(partial, o);
+    sc = bsh(sc, o);
+  }
+  __shared__ double red[4][256];
+  __shared__ double tot[4];
+  const int t = threadIdx.x;
+  const int nq = with_b ? 4 : 3;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int k = t; k < nbk; k += 256)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (q < nq) v[q] += partial[(long long)q * nbk + k];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) red[q][t] = v[q];
+  __syncthreads();
+  const int wp = t >> 5, lane = t & 31;
+  if (wp < nq) {
+    const double* r = red[wp] + lane * 8;
+    double w = r[0];
+#pragma unroll
+    for (int e = 1; e < 8; ++e) w += r[e];
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) w += __shfl_xor_sync(0xffffffffu, w, d);
+    if (lane == 0) tot[wp] = w;
+  }
+  __syncthreads();
+  if (t == 0) {
+    sc[blk] = tot[0];
+    sc[blk + 1] = tot[1];
+    sc[blk + 2] = tot[2];
+    sc[b2] = (tot[0] + tot[1]) + tot[2];
+    if (with_b) sc[bn] = tot[3];
+  }
+}
+
+void launch_resid_norms(const Coef<double>& c, const double* x, const double* b, double* r, double* partial,
+                        double* sc, int blk, int b2, int bn, int with_b, cudaStream_t s) {
+  SD_COUNT(2);
+  const int R = rows_apply(c.n);
+  const dim3 g = grid2R(c.n + 1, c.n + 1, R);
+  if (R == 4) {
+    if (with_b) launch_k(k_apply_full<4, 0, true, 2>, g, dim3(BX, BY), 0, s, c, x, b, r, partial);
+    else launch_k(k_apply_full<4, 0, true, 1>, g, dim3(BX, BY), 0, s, c, x, b, r, partial);
+  } else {
+    if (with_b) launch_k(k_apply_full<1, 0, true, 2>, g, dim3(BX, BY), 0, s, c, x, b, r, partial);
+    else launch_k(k_apply_full<1, 0, true, 1>, g, dim3(BX, BY), 0, s, c, x, b, r, partial);
+  }
+  launch_k(k_reduce_resid, dim3(1), dim3(256), 0, s, (const double*)partial, (int)(g.x * g.y), sc, blk, b2, bn,
+           with_b);
+}
+
+// blocks of the operator's launch (partial sums per quantity of launch_resid_norms)
+long long resid_norms_blocks(int n) {
+  const dim3 g = grid2R(n + 1, n + 1, rows_apply(n));
+  return (long long)g.x * g.y;
 }
 
 void launch_apply_full(const Coef<double>& c, const double* x, const double* b, double* y, cudaStream_t s) {
   SD_COUNT(1);
   const int R = rows_apply(c.n);
-  if (R == 4)
-    launch_k(k_apply_full<4, 0>, dim3(grid2R(c.n + 1, c.n + 1, 4)), dim3(dim3(BX, BY)), 0, s, c, x, b, y);
-  else launch_k(k_apply_full<1, 0>, dim3(grid2R(c.n + 1, c.n + 1, 1)), dim3(dim3(BX, BY)), 0, s, c, x, b, y);
+  const dim3 g = grid2R(c.n + 1, c.n + 1, R);
+  if (R == 4) {
+    if (b) launch_k(k_apply_full<4, 0, true>, g, dim3(BX, BY), 0, s, c, x, b, y, (double*)nullptr);
+    else launch_k(k_apply_full<4, 0, false>, g, dim3(BX, BY), 0, s, c, x, b, y, (double*)nullptr);
+  } else {
+    if (b) launch_k(k_apply_full<1, 0, true>, g, dim3(BX, BY), 0, s, c, x, b, y, (double*)nullptr);
+    else launch_k(k_apply_full<1, 0, false>, g, dim3(BX, BY), 0, s, c, x, b, y, (double*)nullptr);
+  }
 }
 
 void launch_apply_ff(const Coef<double>& c, const double* x, const double* b, double* y, int vdir, cudaStream_t s) {
@@ -365,11 +388,11 @@ void launch_apply_ff(const Coef<double>& c, const double* x, const double* b, do
   const int R = rows_apply(c.n);
   const dim3 g = grid2R(c.n + 1, c.n + 1, R);
   if (R == 4) {
-    if (vdir) launch_k(k_apply_full<4, 2>, g, dim3(BX, BY), 0, s, c, x, b, y);
-    else launch_k(k_apply_full<4, 1>, g, dim3(BX, BY), 0, s, c, x, b, y);
+    if (vdir) launch_k(k_apply_full<4, 2, false>, g, dim3(BX, BY), 0, s, c, x, b, y, (double*)nullptr);
+    else launch_k(k_apply_full<4, 1, false>, g, dim3(BX, BY), 0, s, c, x, b, y, (double*)nullptr);
   } else {
-    if (vdir) launch_k(k_apply_full<1, 2>, g, dim3(BX, BY), 0, s, c, x, b, y);
-    else launch_k(k_apply_full<1, 1>, g, dim3(BX, BY), 0, s, c, x, b, y);
+    if (vdir) launch_k(k_apply_full<1, 2, false>, g, dim3(BX, BY), 0, s, c, x, b, y, (double*)nullptr);
+    else launch_k(k_apply_full<1, 1, false>, g, dim3(BX, BY), 0, s, c, x, b, y, (double*)nullptr);
   }
 }
 
@@ -494,10 +517,11 @@ __device__ __forceinline__ void cheb_V_at2(const Coef<T>& c, const T* __restrict
       if (side) ub_row(c, uin, vin, i, j, rd, off, dg);
       else u_row<T, IN>(c, uin, vin, i, j, rd, off, dg);
       const T xc = rd ? uin[k] : T(0);
-      const T r = bu[k] - (dg * xc + off);
-      const T dn = (a != T(0) ? a * du[k] : T(0)) + sdiv(cc * r, dg);
+      const T ad = a != T(0) ? a * du[k] : T(0);
+      T dn, xn;
+      cheb_point(bu[k], xc, off, dg, ad, cc, dn, xn);
       du[k] = dn;
-      uout[k] = xc + dn;
+      uout[k] = xn;
     }
   }
   if (IN || i < n) {
@@ -509,10 +533,11 @@ __device__ __forceinline__ void cheb_V_at2(const Coef<T>& c, const T* __restrict
       T off, dg;
       v_row<T, IN>(c, uin, vin, i, j, rd, off, dg);
       const T xc = rd ? vin[k] : T(0);
-      const T r = bv[k] - (dg * xc + off);
-      const T dn = (a != T(0) ? a * dv[k] : T(0)) + sdiv(cc * r, dg);
+      const T ad = a != T(0) ? a * dv[k] : T(0);
+      T dn, xn;
+      cheb_point(bv[k], xc, off, dg, ad, cc, dn, xn);
       dv[k] = dn;
-      vout[k] = xc + dn;
+      vout[k] = xn;
     }
   }
 }
@@ -642,10 +667,11 @@ __device__ __forceinline__ void cheb_D_at(const Coef<T>& c, const T* __restrict_
   T off, dg;
   d_row<T, IN>(c, xin, i, j, rd, off, dg);
   const T xc = rd ? xin[k] : T(0);
-  const T r = b[k] - (dg * xc + off);
-  const T dn = (a != T(0) ? a * d[k] : T(0)) + sdiv(cc * r, dg);
+  const T ad = a != T(0) ? a * d[k] : T(0);
+  T dn, xn;
+  cheb_point(b[k], xc, off, dg, ad, cc, dn, xn);
   d[k] = dn;
-  xout[k] = xc + dn;
+  xout[k] = xn;
 }
 
 template <typename T, int R>
@@ -734,18 +760,12 @@ void launch_resid_D(const Coef<T>& c, const T* x, const T* b, T* r, int jac, int
 }
 
 // ------------------------------------------------------------ transfers
-// Prolongation of the velocity block is bilinear on the staggered grid:
-//  u: linear in x between coarse faces (Dirichlet faces carry 0), cell-centred
-//     in y with weights 3/4, 1/4; below coarse row 0 (the interface) the
-//     ghost equals row 0, above the top row (wall) it is the negative.
-//  v: linear in y between coarse faces (the Dirichlet top carries 0),
-//     cell-centred in x with weights 3/4, 1/4 and negative ghosts at the walls.
-// Restriction is its transpose applied to the fine residual.
+// (prolongation values: sd_rows.cuh)
+// coarse faces (I, J) of the velocity block from the fine residual, its u and
+// v parts at ru, rv (row pitch Pf)
 template <typename T>
-__device__ __forceinline__ void restrict_V_at(int nf, int Pf, const T* __restrict__ r, int nc, int Pc,
-                                              T* __restrict__ bc, int I, int J, int lat = 0) {
-  const T* ru = r;
-  const T* rv = r + (long long)nf * Pf;
+__device__ __forceinline__ void restrict_V_at2(const T* __restrict__ ru, const T* __restrict__ rv, int Pf, int nc,
+                                               int Pc, T* __restrict__ bc, int I, int J, int lat) {
   if (J < nc) {
     T s = T(0);
     if (lat && (I == 0 || I == nc)) {  // traction side face: the one-sided transpose of the prolongation
@@ -801,6 +821,12 @@ __device__ __forceinline__ void restrict_V_at(int nf, int Pf, const T* __restric
     }
     bc[(long long)nc * Pc + (long long)J * Pc + I] = s;
   }
+}
+
+template <typename T>
+__device__ __forceinline__ void restrict_V_at(int nf, int Pf, const T* __restrict__ r, int nc, int Pc,
+                                              T* __restrict__ bc, int I, int J, int lat = 0) {
+  restrict_V_at2(r, r + (long long)nf * Pf, Pf, nc, Pc, bc, I, J, lat);
 }
 
 template <typename T>
@@ -889,57 +915,6 @@ void launch_resid_restrict_D(const Coef<T>& c, const T* x, const T* b, int nc, i
 }
 
 template <typename T>
-__device__ __forceinline__ T cu_at(const T* eu, int nc, int Pc, int I, int J, int lat) {
-  // coarse u with zero Dirichlet faces (traction sides: the side faces' own
-  // values) and the y ghosts described above
-  if (!lat && (I <= 0 || I >= nc)) return T(0);
-  if (J < 0) J = 0;
-  if (J > nc - 1) return -eu[(long long)(nc - 1) * Pc + I];
-  return eu[(long long)J * Pc + I];
-}
-template <typename T>
-__device__ __forceinline__ T cv_at(const T* ev, int nc, int Pc, int I, int J) {
-  if (J >= nc) return T(0);
-  if (I < 0) return -ev[(long long)J * Pc];
-  if (I > nc - 1) return -ev[(long long)J * Pc + nc - 1];
-  return ev[(long long)J * Pc + I];
-}
-
-// increment of fine u face (i, j), 0 < i < nf, j < nf
-template <typename T>
-__device__ __forceinline__ T prolong_u_val(const T* __restrict__ eu, int nc, int Pc, int i, int j, int lat = 0) {
-  const int J = j >> 1, Jn = (j & 1) ? J + 1 : J - 1;
-  T cy0, cy1;
-  if (i & 1) {
-    const int I = i >> 1;
-    cy0 = T(0.5) * (cu_at(eu, nc, Pc, I, J, lat) + cu_at(eu, nc, Pc, I + 1, J, lat));
-    cy1 = T(0.5) * (cu_at(eu, nc, Pc, I, Jn, lat) + cu_at(eu, nc, Pc, I + 1, Jn, lat));
-  } else {
-    const int I = i >> 1;
-    cy0 = cu_at(eu, nc, Pc, I, J, lat);
-    cy1 = cu_at(eu, nc, Pc, I, Jn, lat);
-  }
-  return T(0.75) * cy0 + T(0.25) * cy1;
-}
-
-// increment of fine v face (i, j), i < nf, j < nf
-template <typename T>
-__device__ __forceinline__ T prolong_v_val(const T* __restrict__ ev, int nc, int Pc, int i, int j) {
-  const int I = i >> 1, In = (i & 1) ? I + 1 : I - 1;
-  T cx0, cx1;
-  if (j & 1) {
-    const int J = j >> 1;
-    cx0 = T(0.5) * (cv_at(ev, nc, Pc, I, J) + cv_at(ev, nc, Pc, I, J + 1));
-    cx1 = T(0.5) * (cv_at(ev, nc, Pc, In, J) + cv_at(ev, nc, Pc, In, J + 1));
-  } else {
-    const int J = j >> 1;
-    cx0 = cv_at(ev, nc, Pc, I, J);
-    cx1 = cv_at(ev, nc, Pc, In, J);
-  }
-  return T(0.75) * cx0 + T(0.25) * cx1;
-}
-
-template <typename T>
 __device__ __forceinline__ void prolong_V_at(int nf, int Pf, T* __restrict__ x, int nc, int Pc,
                                              const T* __restrict__ e, int i, int j, int lat = 0) {
   const T* eu = e;
@@ -977,24 +952,6 @@ void launch_prolong_V(int nf, int Pf, T* x, int nc, int Pc, const T* e, int lat,
     launch_k(k_prolong_V<T, 4>, dim3(grid2R(nf + 1, nf + 1, 4)), dim3(dim3(BX, BY)), 0, s, nf, Pf, x, nc, Pc, e, lat);
   else
     launch_k(k_prolong_V<T, 1>, dim3(grid2R(nf + 1, nf + 1, 1)), dim3(dim3(BX, BY)), 0, s, nf, Pf, x, nc, Pc, e, lat);
-}
-
-template <typename T>
-__device__ __forceinline__ T cd_at(const T* e, int nc, int Pc, int I, int J) {
-  // lateral sides and top of D' are no-flow (mirror), the bottom is Dirichlet (negative mirror)
-  if (I < 0) I = 0;
-  if (I > nc - 1) I = nc - 1;
-  if (J < 0) return -e[I];
-  if (J > nc - 1) J = nc - 1;
-  return e[(long long)J * Pc + I];
-}
-
-template <typename T>
-__device__ __forceinline__ T prolong_D_val(const T* __restrict__ e, int nc, int Pc, int i, int j) {
-  const int I = i >> 1, J = j >> 1;
-  const int In = (i & 1) ? I + 1 : I - 1, Jn = (j & 1) ? J + 1 : J - 1;
-  return T(0.5625) * cd_at(e, nc, Pc, I, J) + T(0.1875) * (cd_at(e, nc, Pc, In, J) + cd_at(e, nc, Pc, I, Jn)) +
-         T(0.0625) * cd_at(e, nc, Pc, In, Jn);
 }
 
 template <typename T>
@@ -1090,11 +1047,16 @@ __device__ __forceinline__ T prolong_D_sm(const T* __restrict__ s, int CX, int I
   return T(0.5625) * r0[I] + T(0.1875) * (r0[In] + r1[I]) + T(0.0625) * r1[In];
 }
 
-template <typename T, int NS, int TLY, bool BT>
+// RR (pre-smoothing from zero only): the tile also forms the residual of its
+// output cells (x smoothed on a halo of NS + 1 for that) and sums it over the
+// 2 x 2 children of each coarse cell it covers into bco (nc x nc, pitch Pc):
+// k_resid_restrict_D's work and arithmetic, without its launch.
+template <typename T, int NS, int TLY, bool BT, bool RR = false>
 __global__ void __launch_bounds__(TLT) k_smooth_tile_D(Coef<T> c, const T* __restrict__ xin,
                                                        const T* __restrict__ b, T* __restrict__ xout,
                                                        ChebSteps<T> cs, const T* __restrict__ ct,
-                                                       const T* __restrict__ ec, int nc, int Pc, Bat bt) {
+                                                       const T* __restrict__ ec, int nc, int Pc,
+                                                       T* __restrict__ bco, Bat bt) {
   griddep_wait();
   // a separate instantiation for lockstep batches keeps the single-instance
   // kernel's coefficients in the parameter space
@@ -1106,6 +1068,7 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_D(Coef<T> c, const T* __res
     b = bsh(b, o);
     xout = bsh(xout, o);
     ec = bsh(ec, o);
+    bco = bsh(bco, o);
     if (ct) {
       const T* q = bsh(ct, o);
 #pragma unroll
@@ -1115,7 +1078,7 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_D(Coef<T> c, const T* __res
       }
     }
   }
-  constexpr int H = NS, EX = TLX + 2 * H, EY = TLY + 2 * H, SP = EX + 1, SR = EY + 1;
+  constexpr int H = RR ? NS + 1 : NS, EX = TLX + 2 * H, EY = TLY + 2 * H, SP = EX + 1, SR = EY + 1;
   constexpr int CX = SP / 2 + 4, CY = SR / 2 + 4;  // coarse window of the prolongation
   __shared__ T sb[SR * SP], sx0[SR * SP], sx1[SR * SP], sd[SR * SP], sTx[SR * SP], sTy[SR * SP];
   __shared__ T sce[CY * CX];
@@ -1179,17 +1142,43 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_D(Coef<T> c, const T* __res
     cur = nxt;
     nxt = (nxt == xb) ? xa : xb;
   }
+  if constexpr (RR) {
+    for (int p = threadIdx.x; p < TLX * TLY; p += TLT) {
+      const int gi = ilo + H + p % TLX, gj = jlo + H + p / TLX;
+      if (gi >= n || gj >= n) continue;
+      const int k = gj * SP + gi;
+      T off, dg;
+      d_row(tc, cur, gi, gj, true, off, dg);
+      dq[k] = bq[k] - (dg * cur[k] + off);
+    }
+    __syncthreads();
+    const int I0 = (ilo + H) / 2, J0 = (jlo + H) / 2;
+    for (int p = threadIdx.x; p < (TLX / 2) * (TLY / 2); p += TLT) {
+      const int I = I0 + p % (TLX / 2), J = J0 + p / (TLX / 2);
+      if (I >= nc || J >= nc) continue;
+      const T* r0 = dq + (2 * J) * SP + 2 * I;
+      bco[(long long)J * Pc + I] = (r0[0] + r0[1]) + (r0[SP] + r0[SP + 1]);
+    }
+  }
   for (int p = threadIdx.x; p < TLX * TLY; p += TLT) {
     const int gi = ilo + H + p % TLX, gj = jlo + H + p / TLX;
     if (gi < n && gj < n) xout[(long long)gj * P + gi] = cur[(long long)gj * SP + gi];
   }
 }
 
-template <typename T, int NS, int TLY, bool BT>
+// RR (pre-smoothing from zero only): the tile also forms the residual b - A x
+// of its output points and a ring of one around them (x is smoothed on a
+// halo of NS + 2 for that) and restricts it to the coarse faces (I, J) whose
+// fine face (2I, 2J) is one of its output points, into bco (nc x nc coarse
+// cells, pitch Pc) -- the residual and restriction kernels of the level
+// with their launches and the residual's round trip through memory, the same
+// arithmetic per point.
+template <typename T, int NS, int TLY, bool BT, bool RR = false>
 __global__ void __launch_bounds__(TLT) k_smooth_tile_V(Coef<T> c, const T* __restrict__ xin,
                                                        const T* __restrict__ b, T* __restrict__ xout,
                                                        ChebSteps<T> cs, const T* __restrict__ ct,
-                                                       const T* __restrict__ ec, int nc, int Pc, Bat bt) {
+                                                       const T* __restrict__ ec, int nc, int Pc,
+                                                       T* __restrict__ bco, Bat bt) {
   griddep_wait();
   // a separate instantiation for lockstep batches keeps the single-instance
   // kernel's coefficients in the parameter space
@@ -1201,6 +1190,7 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_V(Coef<T> c, const T* __res
     b = bsh(b, o);
     xout = bsh(xout, o);
     ec = bsh(ec, o);
+    bco = bsh(bco, o);
     if (ct) {
       const T* q = bsh(ct, o);
 #pragma unroll
@@ -1210,7 +1200,7 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_V(Coef<T> c, const T* __res
       }
     }
   }
-  constexpr int H = NS, EX = TLX + 2 * H, EY = TLY + 2 * H, SP = EX + 1, SR = EY + 1;
+  constexpr int H = RR ? NS + 2 : NS, EX = TLX + 2 * H, EY = TLY + 2 * H, SP = EX + 1, SR = EY + 1;
   constexpr int CX = SP / 2 + 4, CY = SR / 2 + 4;  // coarse window of the prolongation
   __shared__ T sbu[SR * SP], sbv[SR * SP], sau[SR * SP], sav[SR * SP], sbu2[SR * SP], sbv2[SR * SP];
   __shared__ T sdu[SR * SP], sdv[SR * SP], sw[SP], srg[SP];
@@ -1303,6 +1293,45 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_V(Coef<T> c, const T* __res
     nxu = (nxu == cu2) ? au : cu2;
     nxv = (nxv == cv2) ? av : cv2;
   }
+  if constexpr (RR) {
+    // the residual (resid_V_at's arithmetic) into the d arrays, then the
+    // coarse faces of the tile (restrict_V_at's arithmetic)
+    constexpr int lo = NS + 1, w = EX - 2 * lo, hgt = EY - 2 * lo;
+    for (int p = threadIdx.x; p < w * hgt; p += TLT) {
+      const int gi = ilo + lo + p % w, gj = jlo + lo + p / w;
+      if (gi < 0 || gj < 0 || gi > n || gj > n) continue;
+      const int k = gj * SP + gi;
+      if (gj < n) {
+        T ax, dg = T(1);
+        if ((gi == 0 || gi == n) && !c.lat) {
+          ax = curu[k];
+        } else {
+          T off;
+          if (gi == 0 || gi == n) ub_row(tc, curu, curv, gi, gj, true, off, dg);
+          else u_row(tc, curu, curv, gi, gj, true, off, dg);
+          ax = dg * curu[k] + off;
+        }
+        du[k] = bu[k] - ax;
+      }
+      if (gi < n) {
+        T ax, dg = T(1);
+        if (gj == n) {
+          ax = curv[k];
+        } else {
+          T off;
+          v_row(tc, curu, curv, gi, gj, true, off, dg);
+          ax = dg * curv[k] + off;
+        }
+        dv[k] = bv[k] - ax;
+      }
+    }
+    __syncthreads();
+    const int I0 = (ilo + H) / 2, J0 = (jlo + H) / 2;
+    for (int p = threadIdx.x; p < (TLX / 2) * (TLY / 2); p += TLT) {
+      const int I = I0 + p % (TLX / 2), J = J0 + p / (TLX / 2);
+      if (I <= nc && J <= nc) restrict_V_at2<T>(du, dv, SP, nc, Pc, bco, I, J, c.lat);
+    }
+  }
   for (int p = threadIdx.x; p < TLX * TLY; p += TLT) {
     const int gi = ilo + H + p % TLX, gj = jlo + H + p / TLX;
     const long long gk = (long long)gj * P + gi, sk = (long long)gj * SP + gi;
@@ -1311,27 +1340,23 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_V(Coef<T> c, const T* __res
   }
 }
 
-template <typename T, int TLY>
+template <typename T, int NS, int TLY, bool RR>
+void tile_D_go(const dim3& g, cudaStream_t s, const Coef<T>& c, const T* x_in, const T* b, T* x_out,
+               const ChebSteps<T>& cs, const T* ct, const T* ec, int nc, int Pc, T* bco) {
+  if (t_bat.off)
+    launch_k(k_smooth_tile_D<T, NS, TLY, true, RR>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc, bco);
+  else launch_k(k_smooth_tile_D<T, NS, TLY, false, RR>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc, bco);
+}
+
+template <typename T, int TLY, bool RR>
 int launch_tile_D_rows(const Coef<T>& c, const T* x_in, const T* b, T* x_out, const ChebSteps<T>& cs, const T* ct,
-                       const T* ec, int nc, int Pc, cudaStream_t s) {
+                       const T* ec, int nc, int Pc, T* bco, cudaStream_t s) {
   const dim3 g((c.n + TLX - 1) / TLX, (c.n + TLY - 1) / TLY);
   switch (cs.ns) {
-    case 1:
-      if (t_bat.off) launch_k(k_smooth_tile_D<T, 1, TLY, true>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
-      else launch_k(k_smooth_tile_D<T, 1, TLY, false>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
-      break;
-    case 2:
-      if (t_bat.off) launch_k(k_smooth_tile_D<T, 2, TLY, true>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
-      else launch_k(k_smooth_tile_D<T, 2, TLY, false>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
-      break;
-    case 3:
-      if (t_bat.off) launch_k(k_smooth_tile_D<T, 3, TLY, true>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
-      else launch_k(k_smooth_tile_D<T, 3, TLY, false>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
-      break;
-    case 4:
-      if (t_bat.off) launch_k(k_smooth_tile_D<T, 4, TLY, true>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
-      else launch_k(k_smooth_tile_D<T, 4, TLY, false>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
-      break;
+    case 1: tile_D_go<T, 1, TLY, RR>(g, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc, bco); break;
+    case 2: tile_D_go<T, 2, TLY, RR>(g, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc, bco); break;
+    case 3: tile_D_go<T, 3, TLY, RR>(g, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc, bco); break;
+    case 4: tile_D_go<T, 4, TLY, RR>(g, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc, bco); break;
     default: return -1;
   }
   SD_COUNT(1);
@@ -1341,32 +1366,39 @@ int launch_tile_D_rows(const Coef<T>& c, const T* x_in, const T* b, T* x_out, co
 template <typename T>
 int launch_smooth_tile_D(const Coef<T>& c, const T* x_in, const T* b, T* x_out, const ChebSteps<T>& cs,
                          const T* ct, const T* ec, int nc, int Pc, cudaStream_t s) {
-  if (cs.rows == 4) return launch_tile_D_rows<T, 4>(c, x_in, b, x_out, cs, ct, ec, nc, Pc, s);
-  return cs.rows == 8 ? launch_tile_D_rows<T, 8>(c, x_in, b, x_out, cs, ct, ec, nc, Pc, s)
-                      : launch_tile_D_rows<T, 16>(c, x_in, b, x_out, cs, ct, ec, nc, Pc, s);
+  if constexpr (std::is_same<T, float>::value)
+    if (cs.wave) return launch_wave_D(c, x_in, b, x_out, cs, ct, ec, nc, Pc, s);
+  if (cs.rows == 4) return launch_tile_D_rows<T, 4, false>(c, x_in, b, x_out, cs, ct, ec, nc, Pc, nullptr, s);
+  return cs.rows == 8 ? launch_tile_D_rows<T, 8, false>(c, x_in, b, x_out, cs, ct, ec, nc, Pc, nullptr, s)
+                      : launch_tile_D_rows<T, 16, false>(c, x_in, b, x_out, cs, ct, ec, nc, Pc, nullptr, s);
 }
 
-template <typename T, int TLY>
+template <typename T>
+int launch_smooth_tile_D_rr(const Coef<T>& c, const T* b, T* x_out, const ChebSteps<T>& cs, const T* ct, int nc,
+                            int Pc, T* bco, cudaStream_t s) {
+  if (cs.wave || (c.n & 1)) return -1;
+  if (cs.rows == 4) return launch_tile_D_rows<T, 4, true>(c, nullptr, b, x_out, cs, ct, nullptr, nc, Pc, bco, s);
+  if (cs.rows == 8) return launch_tile_D_rows<T, 8, true>(c, nullptr, b, x_out, cs, ct, nullptr, nc, Pc, bco, s);
+  return -1;
+}
+
+template <typename T, int NS, int TLY, bool RR>
+void tile_V_go(const dim3& g, cudaStream_t s, const Coef<T>& c, const T* x_in, const T* b, T* x_out,
+               const ChebSteps<T>& cs, const T* ct, const T* ec, int nc, int Pc, T* bco) {
+  if (t_bat.off)
+    launch_k(k_smooth_tile_V<T, NS, TLY, true, RR>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc, bco);
+  else launch_k(k_smooth_tile_V<T, NS, TLY, false, RR>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc, bco);
+}
+
+template <typename T, int TLY, bool RR>
 int launch_tile_V_rows(const Coef<T>& c, const T* x_in, const T* b, T* x_out, const ChebSteps<T>& cs, const T* ct,
-                       const T* ec, int nc, int Pc, cudaStream_t s) {
+                       const T* ec, int nc, int Pc, T* bco, cudaStream_t s) {
   const dim3 g((c.n + 1 + TLX - 1) / TLX, (c.n + 1 + TLY - 1) / TLY);
   switch (cs.ns) {
-    case 1:
-      if (t_bat.off) launch_k(k_smooth_tile_V<T, 1, TLY, true>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
-      else launch_k(k_smooth_tile_V<T, 1, TLY, false>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
-      break;
-    case 2:
-      if (t_bat.off) launch_k(k_smooth_tile_V<T, 2, TLY, true>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
-      else launch_k(k_smooth_tile_V<T, 2, TLY, false>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
-      break;
-    case 3:
-      if (t_bat.off) launch_k(k_smooth_tile_V<T, 3, TLY, true>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
-      else launch_k(k_smooth_tile_V<T, 3, TLY, false>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
-      break;
-    case 4:
-      if (t_bat.off) launch_k(k_smooth_tile_V<T, 4, TLY, true>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
-      else launch_k(k_smooth_tile_V<T, 4, TLY, false>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc);
-      break;
+    case 1: tile_V_go<T, 1, TLY, RR>(g, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc, bco); break;
+    case 2: tile_V_go<T, 2, TLY, RR>(g, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc, bco); break;
+    case 3: tile_V_go<T, 3, TLY, RR>(g, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc, bco); break;
+    case 4: tile_V_go<T, 4, TLY, RR>(g, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc, bco); break;
     default: return -1;
   }
   SD_COUNT(1);
@@ -1376,9 +1408,20 @@ int launch_tile_V_rows(const Coef<T>& c, const T* x_in, const T* b, T* x_out, co
 template <typename T>
 int launch_smooth_tile_V(const Coef<T>& c, const T* x_in, const T* b, T* x_out, const ChebSteps<T>& cs,
                          const T* ct, const T* ec, int nc, int Pc, cudaStream_t s) {
-  if (cs.rows == 4) return launch_tile_V_rows<T, 4>(c, x_in, b, x_out, cs, ct, ec, nc, Pc, s);
-  return cs.rows == 8 ? launch_tile_V_rows<T, 8>(c, x_in, b, x_out, cs, ct, ec, nc, Pc, s)
-                      : launch_tile_V_rows<T, 16>(c, x_in, b, x_out, cs, ct, ec, nc, Pc, s);
+  if constexpr (std::is_same<T, float>::value)
+    if (cs.wave) return launch_wave_V(c, x_in, b, x_out, cs, ct, ec, nc, Pc, s);
+  if (cs.rows == 4) return launch_tile_V_rows<T, 4, false>(c, x_in, b, x_out, cs, ct, ec, nc, Pc, nullptr, s);
+  return cs.rows == 8 ? launch_tile_V_rows<T, 8, false>(c, x_in, b, x_out, cs, ct, ec, nc, Pc, nullptr, s)
+                      : launch_tile_V_rows<T, 16, false>(c, x_in, b, x_out, cs, ct, ec, nc, Pc, nullptr, s);
+}
+
+template <typename T>
+int launch_smooth_tile_V_rr(const Coef<T>& c, const T* b, T* x_out, const ChebSteps<T>& cs, const T* ct, int nc,
+                            int Pc, T* bco, cudaStream_t s) {
+  if (cs.wave || (c.n & 1)) return -1;
+  if (cs.rows == 4) return launch_tile_V_rows<T, 4, true>(c, nullptr, b, x_out, cs, ct, nullptr, nc, Pc, bco, s);
+  if (cs.rows == 8) return launch_tile_V_rows<T, 8, true>(c, nullptr, b, x_out, cs, ct, nullptr, nc, Pc, bco, s);
+  return -1;
 }
 
 // ------------------------------------------------ fused coarse V-cycle
@@ -1632,19 +1675,30 @@ __global__ void k_precond_entry(Coef<double> c, const double* __restrict__ r, do
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int n = c.n, P = c.P;
-  if (i > n || j > n) return;
   const T h = (T)c.h;
   const double* rpf = r + (long long)(2 * n + 1) * P;
   // z_pf at cell kc: schur * r_pf (+ cmass * eP, the pressure-Laplacian part),
-  // evaluated in the multigrid precision T
+  // evaluated in the multigrid precision T, once per cell of the block and its
+  // west and south neighbours (staged in shared memory: each FP64 value is
+  // converted once)
   const T ts = (T)schur, tm = (T)cmass;
   auto zp = [&](long long kc) -> T { return ts * (T)rpf[kc] + (eP ? tm * eP[kc] : T(0)); };
-  if (i < n && j < n) z[(long long)(2 * n + 1) * P + (long long)j * P + i] = (double)zp((long long)j * P + i);
+  __shared__ T sz[BY + 1][BX + 1];
+  const int i0 = blockIdx.x * blockDim.x - 1, j0 = blockIdx.y * blockDim.y - 1;
+  for (int p = threadIdx.y * blockDim.x + threadIdx.x; p < (BX + 1) * (BY + 1); p += BX * BY) {
+    const int ci = i0 + p % (BX + 1), cj = j0 + p / (BX + 1);
+    sz[p / (BX + 1)][p % (BX + 1)] = (ci >= 0 && ci < n && cj >= 0 && cj < n) ? zp((long long)cj * P + ci) : T(0);
+  }
+  __syncthreads();
+  if (i > n || j > n) return;
+  const int li = threadIdx.x + 1, lj = threadIdx.y + 1;
+  const T zc = sz[lj][li];
+  if (i < n && j < n) z[(long long)(2 * n + 1) * P + (long long)j * P + i] = (double)zc;
   if (j < n) {
     const long long k = (long long)j * P + i;
     T val = (T)r[k];
-    if (useB && i > 0 && i < n) val -= h * (zp(k) - zp(k - 1));
-    else if (useB && c.lat) val -= i == 0 ? h * zp(k) : -h * zp(k - 1);  // traction side
+    if (useB && i > 0 && i < n) val -= h * (zc - sz[lj][li - 1]);
+    else if (useB && c.lat) val -= i == 0 ? h * zc : -h * sz[lj][li - 1];  // traction side
     rV[k] = val;
   }
   if (i < n) {
@@ -1652,8 +1706,8 @@ __global__ void k_precond_entry(Coef<double> c, const double* __restrict__ r, do
     const long long k = (long long)n * P + kv;
     T val = (T)r[k];
     if (useB && j < n) {
-      if (j > 0) val -= h * (zp(kv) - zp(kv - P));
-      else val -= h * zp(i);
+      if (j > 0) val -= h * (zc - sz[lj - 1][li]);
+      else val -= h * zc;
     }
     // Darcy solved first: r_v - B'_1 z_pm on the interface rows (B'_1 = -h)
     if (useB1 && j == 0) val += h * (T)z[(long long)(3 * n + 1) * P + (long long)(n - 1) * P + i];
@@ -2122,6 +2176,10 @@ template int launch_smooth_tile_D<float>(const Coef<float>&, const float*, const
                                          const float*, const float*, int, int, cudaStream_t);
 template int launch_smooth_tile_V<float>(const Coef<float>&, const float*, const float*, float*, const ChebSteps<float>&,
                                          const float*, const float*, int, int, cudaStream_t);
+template int launch_smooth_tile_V_rr<float>(const Coef<float>&, const float*, float*, const ChebSteps<float>&,
+                                             const float*, int, int, float*, cudaStream_t);
+template int launch_smooth_tile_D_rr<float>(const Coef<float>&, const float*, float*, const ChebSteps<float>&,
+                                             const float*, int, int, float*, cudaStream_t);
 template int prepare_coarse_cycle<double>();
 template int launch_coarse_cycle<double>(const CoarseCycle<double>&, cudaStream_t);
 template size_t coarse_cycle_smem<float>(const CoarseCycle<float>&);

@@ -312,13 +312,17 @@ def test_numeric_error_from_nan_rhs(sd):
 def test_schur_mass_only_parity(sd, n, precision):
     # the Schur block as the viscosity-scaled pressure mass matrix alone,
     # S^-1 = (mu/(gamma h^2)) I (schur_mass = 0), on the log-normal physics:
-    # the same states as the oracle, three steps
+    # the same states as the oracle, three steps.  The residual test bounds
+    # the error only through the condition number, and this weaker Schur block
+    # leaves iterates whose p_ff error (1.7e-8 at rtol 1e-12, n = 40) sits
+    # above the per-field bound, so the solve runs to rtol 1e-13.
     K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=1)
     o = O.Oracle(n, 1e-3, 1.0, 0.05, K)
     xr = o.run(O.exact(n, 0.0, 1e-3), 0.0, 3)
-    h = make(sd, n, 1e-3, K, 1.0, 0.05, precision, rtol=1e-12, schur_mass=0, max_iters=3000)
+    h = make(sd, n, 1e-3, K, 1.0, 0.05, precision, rtol=1e-13, schur_mass=0, max_iters=3000)
     infos = sd.sd_step(h, 3)
     assert all(i["status"] == 0 for i in infos), infos
+    print("schur_mass=0 n=%d precision=%d iterations per step:" % (n, precision), [i["iters"] for i in infos])
     _, _, x = sd.sd_get_state(h)
     for k, e in fields_rel(x, xr, n).items():
         assert e <= 1e-8, (k, e)
@@ -445,14 +449,17 @@ def test_pdl_bitwise(sd):
     assert np.array_equal(xs[0], xs[1])
 
 
-@pytest.mark.parametrize("n", [64, 96, 256])
+@pytest.mark.parametrize("n", [64, 96, 256, 1024])
 def test_tiled_smoothing_bitwise(sd, n):
     # all Chebyshev steps of a smoothing in one tiled kernel, prolongation folded
-    # in, with 16-, 8- or 4-row tiles (0: by level size): the same arithmetic per point as the per-step
-    # kernels (n = 96: 97 faces per row, a one-face ragged tile column)
+    # in, with 16-, 8- or 4-row tiles (0: by level size), and in register-column
+    # tiles (tile 2) of the same heights: the same arithmetic per point as the
+    # per-step kernels (n = 96: 97 faces per row, a one-face ragged tile column;
+    # 97 = 3 * 26 + 19, a ragged register strip).  Register tiles are used on
+    # levels of at least 512 cells per side, so n = 1024 is in the list.
     K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=11)
     xs = []
-    for tile, rows in ((0, 16), (1, 16), (1, 8), (1, 4), (1, 0)):
+    for tile, rows in ((0, 16), (1, 16), (1, 8), (1, 4), (1, 0), (2, 16), (2, 8), (2, 4), (2, 0)):
         h = make(sd, n, 1e-3, K, 1.0, 0.05, 1, tile=tile, tile_rows=rows)
         sd.sd_step(h, 3)
         xs.append(sd.sd_get_state(h)[2])

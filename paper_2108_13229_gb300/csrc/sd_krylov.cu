@@ -276,8 +276,10 @@ __global__ void k_scale_by(const double* __restrict__ x, double* __restrict__ y,
     sdev = bsh(sdev, o);
   }
   const double f = mode == 0 ? sdev[0] : 1.0 / sqrt(sdev[0]);
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len; e += (long long)gridDim.x * blockDim.x)
-    y[e] = f * x[e];
+  // 32-bit indices (a vector has fewer than 2^31 entries): 64-bit index
+  // arithmetic would share the FP64 pipe with the products
+  const int n = (int)len;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) y[e] = f * x[e];
 }
 
 void launch_scale_by(const double* x, double* y, long long len, const double* sdev, int mode, cudaStream_t s) {
@@ -429,7 +431,8 @@ void launch_givens(double* st, int j, int m, const double* hcol1, const double* 
 __global__ void k_extrapolate(double* __restrict__ x, double* __restrict__ xm, double* __restrict__ xmm,
                                double* __restrict__ x3, long long len, int order) {
   griddep_wait();
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len; e += (long long)gridDim.x * blockDim.x) {
+  const int n = (int)len;  // 32-bit indices: fewer than 2^31 entries
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     const double t = x[e], m = xm[e], mm = xmm ? xmm[e] : 0.0;
     x[e] = order >= 3 ? 4.0 * (t + mm) - 6.0 * m - x3[e] : order == 2 ? 3.0 * (t - m) + mm
                                                          : order == 1 ? 2.0 * t - m : t;

@@ -1659,8 +1659,8 @@ int launch_coarse_cycle(const CoarseCycle<T>& q, cudaStream_t s) {
 // Schur approximation S^ = h^2/(2 mu) I, or by I): z_pf = schur * r_pf,
 // then the velocity rhs r_v - B z_pf for the V-block multigrid.
 template <typename T>
-__global__ void k_precond_entry(Coef<double> c, const double* __restrict__ r, double* __restrict__ z, double schur,
-                                const T* __restrict__ eP, double cmass, int useB, int useB1, T* __restrict__ rV,
+__global__ void k_precond_entry(Coef<double> c, const double* __restrict__ r, double* __restrict__ z, T schur,
+                                const T* __restrict__ eP, T cmass, T hT, int useB, int useB1, T* __restrict__ rV,
                                 Bat bt) {
   griddep_wait();
   long long o;
@@ -1675,13 +1675,13 @@ __global__ void k_precond_entry(Coef<double> c, const double* __restrict__ r, do
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int n = c.n, P = c.P;
-  const T h = (T)c.h;
+  const T h = hT;  // parameters arrive in T: an FP64 conversion per thread would run on the FP64 pipe
   const double* rpf = r + (long long)(2 * n + 1) * P;
   // z_pf at cell kc: schur * r_pf (+ cmass * eP, the pressure-Laplacian part),
   // evaluated in the multigrid precision T, once per cell of the block and its
   // west and south neighbours (staged in shared memory: each FP64 value is
   // converted once)
-  const T ts = (T)schur, tm = (T)cmass;
+  const T ts = schur, tm = cmass;
   auto zp = [&](long long kc) -> T { return ts * (T)rpf[kc] + (eP ? tm * eP[kc] : T(0)); };
   __shared__ T sz[BY + 1][BX + 1];
   const int i0 = blockIdx.x * blockDim.x - 1, j0 = blockIdx.y * blockDim.y - 1;
@@ -1719,7 +1719,8 @@ template <typename T>
 void launch_precond_entry(const Coef<double>& c, const double* r, double* z, double schur, const T* eP, double cmass,
                           int use_B, int use_B1, T* rV, cudaStream_t s) {
   SD_COUNT(1);
-  launch_k(k_precond_entry<T>, dim3(grid2(c.n + 1, c.n + 1)), dim3(dim3(BX, BY)), 0, s, c, r, z, schur, eP, cmass, use_B, use_B1, rV);
+  launch_k(k_precond_entry<T>, dim3(grid2(c.n + 1, c.n + 1)), dim3(dim3(BX, BY)), 0, s, c, r, z, (T)schur, eP,
+           (T)cmass, (T)c.h, use_B, use_B1, rV);
 }
 
 template <typename T>
@@ -1922,8 +1923,10 @@ __global__ void k_convert(const double* __restrict__ a, T* __restrict__ b, long 
     a = bsh(a, o);
     b = bsh(b, o);
   }
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < len; k += (long long)gridDim.x * blockDim.x)
-    b[k] = (T)a[k];
+  // 32-bit indices (a vector has fewer than 2^31 entries): 64-bit index
+  // arithmetic and conversions would share the FP64 pipe with the conversion
+  const int n = (int)len;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) b[k] = (T)a[k];
 }
 template <typename T>
 void launch_convert(const double* src, T* dst, long long len, cudaStream_t s) {

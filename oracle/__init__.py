@@ -48,6 +48,12 @@ def _load():
     lib.or_create_bc.restype = ctypes.c_void_p
     lib.or_create_bc.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, ctypes.c_int,
                                  ctypes.c_double, ctypes.c_double]
+    lib.or_create_geo.restype = ctypes.c_void_p
+    lib.or_create_geo.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, ctypes.c_int,
+                                  ctypes.c_double, ctypes.c_double, ctypes.c_int]
+    lib.or_dof_count_geo.restype = ctypes.c_int64
+    lib.or_dof_count_geo.argtypes = [ctypes.c_int, ctypes.c_int]
+    lib.or_exact_geo.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp]
     lib.or_p_in.restype = ctypes.c_double
     lib.or_p_in.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
     lib.or_destroy.argtypes = [ctypes.c_void_p]
@@ -91,31 +97,39 @@ def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-def dof_count(n: int) -> int:
-    return int(_load().or_dof_count(n))
+def dof_count(n: int, geo: int = 0) -> int:
+    """4n^2 + 2n (geo 0, Table 1); 10n^2 + 4n for the channel of Sec. 5's model problem (geo 1)."""
+    return int(_load().or_dof_count_geo(n, geo))
 
 
-def offsets(n: int) -> dict:
+def ff_width(n: int, geo: int = 0) -> int:
+    """Free-flow cells across: n (square) or 3n (channel)."""
+    return 3 * n if geo == 1 else n
+
+
+def offsets(n: int, geo: int = 0) -> dict:
     """Start offset of each field in the whole-system vector."""
-    nu = n * (n + 1)
-    return {"u": 0, "v": nu, "p_ff": 2 * nu, "p_pm": 2 * nu + n * n, "end": 2 * nu + 2 * n * n}
+    nx = ff_width(n, geo)
+    nu, nv, npf = n * (nx + 1), nx * (n + 1), nx * n
+    return {"u": 0, "v": nu, "p_ff": nu + nv, "p_pm": nu + nv + npf, "end": nu + nv + npf + n * n}
 
 
-def split(x: np.ndarray, n: int) -> dict:
+def split(x: np.ndarray, n: int, geo: int = 0) -> dict:
     """Views of the four fields as 2-D arrays indexed [j, i]."""
-    o = offsets(n)
+    o = offsets(n, geo)
+    nx = ff_width(n, geo)
     return {
-        "u": x[o["u"]:o["v"]].reshape(n, n + 1),
-        "v": x[o["v"]:o["p_ff"]].reshape(n + 1, n),
-        "p_ff": x[o["p_ff"]:o["p_pm"]].reshape(n, n),
+        "u": x[o["u"]:o["v"]].reshape(n, nx + 1),
+        "v": x[o["v"]:o["p_ff"]].reshape(n + 1, nx),
+        "p_ff": x[o["p_ff"]:o["p_pm"]].reshape(n, nx),
         "p_pm": x[o["p_pm"]:o["end"]].reshape(n, n),
     }
 
 
-def exact(n: int, t: float, mu: float = 1.0) -> np.ndarray:
+def exact(n: int, t: float, mu: float = 1.0, geo: int = 0) -> np.ndarray:
     """Manufactured solution sampled at the DoF locations at time t."""
-    x = np.zeros(dof_count(n))
-    _load().or_exact(n, t, mu, _ptr(x))
+    x = np.zeros(dof_count(n, geo))
+    _load().or_exact_geo(n, t, mu, geo, _ptr(x))
     return x
 
 
@@ -136,15 +150,19 @@ class Oracle:
     bc 1: manufactured solution with traction free-flow sides;
     bc 2: the paper's pressure-driven problem (inflow pressure p_in(t) with
     amplitude dp and ramp time t_end on the left, zero on the right).
+    geo 0: free flow [0,1]x[1,2] over the porous medium (Table 1); geo 1: the
+    channel [-1,2]x[1,2] of Sec. 5's model problem over the same porous
+    medium, the interface the middle third of its floor, walls beside it.
     """
 
     def __init__(self, n: int, mu: float, alpha: float, dt: float, K, bc: int = 0, dp: float = 1.0,
-                 t_end: float = 1.0):
+                 t_end: float = 1.0, geo: int = 0):
         K = _f64(K).reshape(n, n)
         self.n, self.mu, self.alpha, self.dt = n, float(mu), float(alpha), float(dt)
-        self.bc, self.dp, self.t_end = int(bc), float(dp), float(t_end)
+        self.bc, self.dp, self.t_end, self.geo = int(bc), float(dp), float(t_end), int(geo)
         self._lib = _load()
-        self._c = self._lib.or_create_bc(n, self.mu, self.alpha, self.dt, _ptr(K), self.bc, self.dp, self.t_end)
+        self._c = self._lib.or_create_geo(n, self.mu, self.alpha, self.dt, _ptr(K), self.bc, self.dp, self.t_end,
+                                          self.geo)
         if not self._c:
             raise ValueError("oracle: invalid parameters")
         self.ndof = int(self._lib.or_ndof(self._c))

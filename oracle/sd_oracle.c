@@ -98,6 +98,8 @@ double or_mms_fy(double x, double y, double t, double mu) {
 /* ------------------------------------------------------------------------ */
 typedef struct {
   int n;
+  int geo;                   /* 0: square free flow n x n; 1: channel 3n x n over the pm (see or_create_geo) */
+  int nx, iw;                /* free-flow cells across (n or 3n), first free-flow column above the pm (0 or n) */
   double h, mu, alpha, dt;
   int bc;                    /* 0, 1, 2: see the header */
   double dp, tend;           /* bc 2: inflow pressure amplitude and ramp time */
@@ -317,14 +319,206 @@ static void build_row(const or_ctx *c, int64_t row, row_t *r) {
   }
 }
 
-or_ctx *or_create_bc(int n, double mu, double alpha, double dt, const double *K, int bc, double dp, double tend) {
-  if (n < 2 || !(mu > 0) || !(alpha > 0) || !(dt > 0) || !K || bc < 0 || bc > 2 || !(tend > 0)) return NULL;
+
+/* ------------------------------------------------------------------------ */
+/* Channel geometry (geo 1): the model problem's free flow of Sec. 5, a      */
+/* channel three times as wide as the porous medium.  Free flow             */
+/* [-1,2] x [1,2] (3n x n cells) over the porous medium [0,1] x [0,1]; the  */
+/* interface Gamma is the middle third of the channel's floor (free-flow    */
+/* columns iw .. iw+n-1, iw = n), the rest of the floor a wall.  Unknowns:   */
+/* u (3n+1) x n, v 3n x (n+1) (row 0: floor faces; the ones on Gamma are    */
+/* the interface unknowns, the others wall faces with identity rows),       */
+/* p_ff 3n x n, p_pm n x n: 10 n^2 + 4 n.                                    */
+/* Rows follow the square geometry's reading; what changes at the floor:    */
+/*  - u faces above the wall take the wall shear at half distance (as the   */
+/*    lid does);                                                            */
+/*  - u faces above Gamma take the eliminated BJS slip of Eq. (6); at the   */
+/*    two ends of Gamma (x = 0, 1) the slip uses the one pm cell below and  */
+/*    the wall face beside it enters as data;                               */
+/*  - the v_Gamma rows are the half control volumes of Eq. (5), their end   */
+/*    corners through those end faces;                                      */
+/*  - traction ends (bc 1, 2) at x = -1 and x = 2, their floor corner at    */
+/*    half distance from the wall.                                          */
+/* ------------------------------------------------------------------------ */
+static int64_t chu(const or_ctx *c, int i, int j) { return (int64_t)j * (c->nx + 1) + i; }
+static int64_t chv(const or_ctx *c, int i, int j) { return (int64_t)c->n * (c->nx + 1) + (int64_t)j * c->nx + i; }
+static int64_t chp(const or_ctx *c, int i, int j) {
+  return (int64_t)c->n * (c->nx + 1) + (int64_t)(c->n + 1) * c->nx + (int64_t)j * c->nx + i;
+}
+static int64_t chm(const or_ctx *c, int i, int j) {
+  return (int64_t)c->n * (c->nx + 1) + (int64_t)(c->n + 1) * c->nx + (int64_t)c->n * c->nx + (int64_t)j * c->n + i;
+}
+int64_t or_dof_count_geo(int n, int geo) {
+  return geo == 1 ? 10 * (int64_t)n * n + 4 * (int64_t)n : or_dof_count(n);
+}
+/* x of free-flow u face i (a cell's centre is h/2 further) */
+static double chx(const or_ctx *c, int i) { return (i - c->iw) * c->h; }
+/* floor face i (v face, row 0) lies on Gamma */
+static int on_gamma(const or_ctx *c, int i) { return i >= c->iw && i < c->iw + c->n; }
+/* BJS coefficient mu / (h + 2 beta) at the floor corner of u face i, iw <= i <= iw + n:
+   beta = sqrt(K)/alpha with sqrt(K) the mean over the pm cells below that lie under Gamma */
+static double bjs_w_ch(const or_ctx *c, int i) {
+  const int n = c->n, p = i - c->iw;
+  double sk;
+  if (p == 0) sk = sqrt(kc(c, 0, n - 1));
+  else if (p == n) sk = sqrt(kc(c, n - 1, n - 1));
+  else sk = 0.5 * (sqrt(kc(c, p - 1, n - 1)) + sqrt(kc(c, p, n - 1)));
+  return c->mu / (c->h + 2.0 * sk / c->alpha);
+}
+
+static void build_row_channel(const or_ctx *c, int64_t row, row_t *r) {
+  const int n = c->n, NX = c->nx;
+  const double h = c->h, mu = c->mu, cm = h * h / c->dt;
+  const int lat = c->bc != 0;
+  const int64_t nu = (int64_t)n * (NX + 1), nv = (int64_t)NX * (n + 1), np = (int64_t)NX * n;
+  r->cnt = 0;
+  if (row < nu) { /* u row */
+    const int j = (int)(row / (NX + 1)), i = (int)(row % (NX + 1));
+    if ((i == 0 || i == NX) && !lat) { radd(r, row, 1.0); return; }
+    if (i == 0 || i == NX) {                     /* traction end: half control volume */
+      const double sg = i == 0 ? 1.0 : -1.0;
+      const int ii = i == 0 ? 1 : NX - 1, ic = i == 0 ? 0 : NX - 1;
+      double diag = 0.5 * cm + 2.0 * mu;
+      radd(r, chu(c, ii, j), -2.0 * mu);
+      radd(r, chp(c, ic, j), sg * h);
+      if (j < n - 1) {
+        diag += 0.5 * mu;
+        radd(r, chu(c, i, j + 1), -0.5 * mu);
+        radd(r, chv(c, ic, j + 1), -sg * mu);
+      } else {
+        diag += mu;                              /* lid at half distance */
+      }
+      if (j > 0) {
+        diag += 0.5 * mu;
+        radd(r, chu(c, i, j - 1), -0.5 * mu);
+        radd(r, chv(c, ic, j), sg * mu);
+      } else {
+        diag += mu;                              /* channel floor at half distance */
+      }
+      radd(r, row, diag);
+      return;
+    }
+    double diag = cm + 4.0 * mu;
+    if (i - 1 >= 1 || lat) radd(r, chu(c, i - 1, j), -2.0 * mu);
+    if (i + 1 <= NX - 1 || lat) radd(r, chu(c, i + 1, j), -2.0 * mu);
+    if (j < n - 1) {
+      diag += mu;
+      radd(r, chu(c, i, j + 1), -mu);
+      radd(r, chv(c, i, j + 1), -mu);
+      radd(r, chv(c, i - 1, j + 1), mu);
+    } else {
+      diag += 2.0 * mu;
+    }
+    if (j > 0) {
+      diag += mu;
+      radd(r, chu(c, i, j - 1), -mu);
+      radd(r, chv(c, i, j), mu);
+      radd(r, chv(c, i - 1, j), -mu);
+    } else if (i >= c->iw && i <= c->iw + n) {   /* over Gamma: BJS slip eliminated, Eq. (6) */
+      const double w = bjs_w_ch(c, i);
+      diag += 2.0 * w * h;
+      if (on_gamma(c, i)) radd(r, chv(c, i, 0), w * h);
+      if (on_gamma(c, i - 1)) radd(r, chv(c, i - 1, 0), -w * h);
+    } else {
+      diag += 2.0 * mu;                          /* channel floor, half-cell distance */
+    }
+    radd(r, chp(c, i, j), h);
+    radd(r, chp(c, i - 1, j), -h);
+    radd(r, row, diag);
+    return;
+  }
+  row -= nu;
+  if (row < nv) { /* v row */
+    const int j = (int)(row / NX), i = (int)(row % NX);
+    const int64_t me = chv(c, i, j);
+    if (j == n || (j == 0 && !on_gamma(c, i))) { radd(r, me, 1.0); return; }
+    if (j == 0) {                                /* v_Gamma: half control volume, Eq. (5) */
+      const int p = i - c->iw;
+      double diag = 0.5 * cm + 2.0 * mu + mu * h * h / (2.0 * kc(c, p, n - 1));
+      if (n > 1) radd(r, chv(c, i, 1), -2.0 * mu);
+      radd(r, chp(c, i, 0), h);
+      radd(r, chm(c, p, n - 1), -h);             /* block B'_1 */
+      double w = bjs_w_ch(c, i);
+      radd(r, chu(c, i, 0), w * h);
+      if (on_gamma(c, i - 1)) radd(r, chv(c, i - 1, 0), -0.5 * h * w);
+      diag += 0.5 * h * w;
+      w = bjs_w_ch(c, i + 1);
+      radd(r, chu(c, i + 1, 0), -w * h);
+      if (on_gamma(c, i + 1)) radd(r, chv(c, i + 1, 0), -0.5 * h * w);
+      diag += 0.5 * h * w;
+      radd(r, me, diag);
+      return;
+    }
+    double diag = cm + 4.0 * mu;
+    if (j - 1 >= 1 || on_gamma(c, i)) radd(r, chv(c, i, j - 1), -2.0 * mu);
+    if (j + 1 <= n - 1) radd(r, chv(c, i, j + 1), -2.0 * mu);
+    if (i < NX - 1) {
+      diag += mu;
+      radd(r, chv(c, i + 1, j), -mu);
+      radd(r, chu(c, i + 1, j), -mu);
+      radd(r, chu(c, i + 1, j - 1), mu);
+    } else {
+      diag += 2.0 * mu;
+      if (lat) {
+        radd(r, chu(c, NX, j), -mu);
+        radd(r, chu(c, NX, j - 1), mu);
+      }
+    }
+    if (i > 0) {
+      diag += mu;
+      radd(r, chv(c, i - 1, j), -mu);
+      radd(r, chu(c, i, j), mu);
+      radd(r, chu(c, i, j - 1), -mu);
+    } else {
+      diag += 2.0 * mu;
+      if (lat) {
+        radd(r, chu(c, 0, j), mu);
+        radd(r, chu(c, 0, j - 1), -mu);
+      }
+    }
+    radd(r, chp(c, i, j), h);
+    radd(r, chp(c, i, j - 1), -h);
+    radd(r, me, diag);
+    return;
+  }
+  row -= nv;
+  if (row < np) { /* continuity of ff cell (i, j), Eq. (2) */
+    const int j = (int)(row / NX), i = (int)(row % NX);
+    if (i + 1 <= NX - 1 || lat) radd(r, chu(c, i + 1, j), h);
+    if (i >= 1 || lat) radd(r, chu(c, i, j), -h);
+    if (j + 1 <= n - 1) radd(r, chv(c, i, j + 1), h);
+    if (j > 0 || on_gamma(c, i)) radd(r, chv(c, i, j), -h);
+    return;
+  }
+  row -= np;
+  { /* Darcy cell (i, j), Eqs. (3), (4), (7); the cells below Gamma are its columns iw .. iw+n-1 */
+    const int j = (int)(row / n), i = (int)(row % n);
+    const int64_t me = chm(c, i, j);
+    double diag = 0.0, t;
+    if (i > 0) { t = t_harm(c, kc(c, i - 1, j), kc(c, i, j)); diag += t; radd(r, chm(c, i - 1, j), -t); }
+    if (i < n - 1) { t = t_harm(c, kc(c, i + 1, j), kc(c, i, j)); diag += t; radd(r, chm(c, i + 1, j), -t); }
+    if (j > 0) { t = t_harm(c, kc(c, i, j - 1), kc(c, i, j)); diag += t; radd(r, chm(c, i, j - 1), -t); }
+    else { diag += 2.0 * kc(c, i, j) / c->mu; }
+    if (j < n - 1) { t = t_harm(c, kc(c, i, j + 1), kc(c, i, j)); diag += t; radd(r, chm(c, i, j + 1), -t); }
+    else { radd(r, chv(c, c->iw + i, 0), h); }  /* block C'_1: outflow h v_Gamma, Eq. (7) */
+    radd(r, me, diag);
+  }
+}
+
+/* geo 0: the square free flow over the square porous medium (Table 1);
+   geo 1: the channel above */
+or_ctx *or_create_geo(int n, double mu, double alpha, double dt, const double *K, int bc, double dp, double tend,
+                      int geo) {
+  if (n < 2 || !(mu > 0) || !(alpha > 0) || !(dt > 0) || !K || bc < 0 || bc > 2 || !(tend > 0) || geo < 0 ||
+      geo > 1)
+    return NULL;
   or_ctx *c = (or_ctx *)calloc(1, sizeof(or_ctx));
   c->n = n; c->h = 1.0 / n; c->mu = mu; c->alpha = alpha; c->dt = dt;
+  c->geo = geo; c->nx = geo == 1 ? 3 * n : n; c->iw = geo == 1 ? n : 0;
   c->bc = bc; c->dp = dp; c->tend = tend;
   c->K = (double *)malloc(sizeof(double) * (size_t)n * n);
   memcpy(c->K, K, sizeof(double) * (size_t)n * n);
-  c->ndof = or_dof_count(n);
+  c->ndof = or_dof_count_geo(n, geo);
   c->rowptr = (int64_t *)malloc(sizeof(int64_t) * (size_t)(c->ndof + 1));
   int64_t cap = c->ndof * 12;
   c->col = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
@@ -333,13 +527,18 @@ or_ctx *or_create_bc(int n, double mu, double alpha, double dt, const double *K,
   int64_t nz = 0;
   c->rowptr[0] = 0;
   for (int64_t row = 0; row < c->ndof; ++row) {
-    build_row(c, row, &r);
+    if (geo == 1) build_row_channel(c, row, &r);
+    else build_row(c, row, &r);
     rsort(&r);
     for (int k = 0; k < r.cnt; ++k) { c->col[nz] = (int32_t)r.col[k]; c->val[nz] = r.val[k]; ++nz; }
     c->rowptr[row + 1] = nz;
   }
   c->nnz = nz;
   return c;
+}
+
+or_ctx *or_create_bc(int n, double mu, double alpha, double dt, const double *K, int bc, double dp, double tend) {
+  return or_create_geo(n, mu, alpha, dt, K, bc, dp, tend, 0);
 }
 
 or_ctx *or_create(int n, double mu, double alpha, double dt, const double *K) {
@@ -417,7 +616,13 @@ static double dat_fy(const or_ctx *c, double x, double y, double t) {
   return c->bc == 2 ? 0.0 : or_mms_fy(x, y, t, c->mu);
 }
 
+static void rhs_channel(const or_ctx *c, const double *xprev, double t, double *b);
+
 void or_rhs(const or_ctx *c, const double *xprev, double t, double *b) {
+  if (c->geo == 1) {
+    rhs_channel(c, xprev, t, b);
+    return;
+  }
   const int n = c->n, lat = c->bc != 0;
   const double h = c->h, mu = c->mu, cm = h * h / c->dt;
   /* u rows */
@@ -499,11 +704,149 @@ void or_rhs(const or_ctx *c, const double *xprev, double t, double *b) {
     }
 }
 
+
+/* Right-hand side of the channel geometry (geo 1): the square's terms with
+   the data of the walls beside Gamma (velocity on the floor faces and at the
+   floor corners) moved in as the elimination of their identity rows asks.
+   Ends: x = -1 (left), x = 2 (right). */
+static double ch_side_p(const or_ctx *c, int right, double y, double t) {
+  if (c->bc == 2) return right ? 0.0 : or_p_in(c->dp, c->tend, t);
+  const double x = right ? 2.0 : -1.0;
+  const double ux = OR_PI * cos(OR_PI * x) * mms_dphi(y) * (1.0 + t);
+  return or_mms_pff(x, y, t, c->mu) - 2.0 * c->mu * ux;
+}
+static double ch_side_v(const or_ctx *c, int right, double y, double t) {
+  return c->bc == 2 ? 0.0 : or_mms_v(right ? 2.0 : -1.0, y, t);
+}
+
+static void rhs_channel(const or_ctx *c, const double *xprev, double t, double *b) {
+  const int n = c->n, NX = c->nx, lat = c->bc != 0;
+  const double h = c->h, mu = c->mu, cm = h * h / c->dt;
+  const double xl = -1.0, xr = 2.0;
+  /* u rows */
+  for (int j = 0; j < n; ++j) {
+    const double y = 1.0 + (j + 0.5) * h;
+    for (int i = 0; i <= NX; ++i) {
+      const int64_t k = chu(c, i, j);
+      const double x = chx(c, i);
+      if ((i == 0 || i == NX) && !lat) { b[k] = dat_u(c, x, y, t); continue; }
+      if (i == 0 || i == NX) {                   /* traction end */
+        const int rt = i == NX;
+        const double sg = rt ? -1.0 : 1.0;
+        double s = 0.5 * cm * xprev[k] + 0.5 * h * h * dat_fx(c, x, y, t) + sg * h * ch_side_p(c, rt, y, t);
+        if (j < n - 1) s -= sg * mu * ch_side_v(c, rt, 1.0 + (j + 1) * h, t);
+        else s += mu * dat_u(c, x, 2.0, t) + sg * mu * (dat_v(c, x + sg * 0.5 * h, 2.0, t) - dat_v(c, x, 2.0, t));
+        if (j > 0) s += sg * mu * ch_side_v(c, rt, 1.0 + j * h, t);
+        else s += mu * dat_u(c, x, 1.0, t) - sg * mu * (dat_v(c, x + sg * 0.5 * h, 1.0, t) - dat_v(c, x, 1.0, t));
+        b[k] = s;
+        continue;
+      }
+      double s = cm * xprev[k] + h * h * dat_fx(c, x, y, t);
+      if (i == 1 && !lat) s += 2.0 * mu * dat_u(c, xl, y, t);
+      if (i == NX - 1 && !lat) s += 2.0 * mu * dat_u(c, xr, y, t);
+      if (j == n - 1)
+        s += 2.0 * mu * dat_u(c, x, 2.0, t) + mu * (dat_v(c, x + 0.5 * h, 2.0, t) - dat_v(c, x - 0.5 * h, 2.0, t));
+      if (j == 0) {
+        if (i >= c->iw && i <= c->iw + n) {       /* BJS corner: a wall face beside the slip is data */
+          const double w = bjs_w_ch(c, i);
+          if (!on_gamma(c, i)) s -= w * h * dat_v(c, x + 0.5 * h, 1.0, t);
+          if (!on_gamma(c, i - 1)) s += w * h * dat_v(c, x - 0.5 * h, 1.0, t);
+        } else {                                  /* floor wall at half distance */
+          s += 2.0 * mu * dat_u(c, x, 1.0, t) - mu * (dat_v(c, x + 0.5 * h, 1.0, t) - dat_v(c, x - 0.5 * h, 1.0, t));
+        }
+      }
+      b[k] = s;
+    }
+  }
+  /* v rows */
+  for (int j = 0; j <= n; ++j) {
+    const double y = 1.0 + j * h;
+    for (int i = 0; i < NX; ++i) {
+      const int64_t k = chv(c, i, j);
+      const double x = chx(c, i) + 0.5 * h;
+      if (j == n) { b[k] = dat_v(c, x, 2.0, t); continue; }
+      if (j == 0 && !on_gamma(c, i)) { b[k] = dat_v(c, x, 1.0, t); continue; }
+      if (j == 0) {
+        double s = 0.5 * cm * xprev[k] + 0.5 * h * h * dat_fy(c, x, 1.0, t);
+        if (!on_gamma(c, i - 1)) s += 0.5 * h * bjs_w_ch(c, i) * dat_v(c, x - h, 1.0, t);
+        if (!on_gamma(c, i + 1)) s += 0.5 * h * bjs_w_ch(c, i + 1) * dat_v(c, x + h, 1.0, t);
+        b[k] = s;
+        continue;
+      }
+      double s = cm * xprev[k] + h * h * dat_fy(c, x, y, t);
+      if (j == n - 1) s += 2.0 * mu * dat_v(c, x, 2.0, t);
+      if (j == 1 && !on_gamma(c, i)) s += 2.0 * mu * dat_v(c, x, 1.0, t);
+      if (i == 0) {
+        if (lat) s += 2.0 * mu * ch_side_v(c, 0, y, t);
+        else s += 2.0 * mu * dat_v(c, xl, y, t) - mu * (dat_u(c, xl, y + 0.5 * h, t) - dat_u(c, xl, y - 0.5 * h, t));
+      }
+      if (i == NX - 1) {
+        if (lat) s += 2.0 * mu * ch_side_v(c, 1, y, t);
+        else s += 2.0 * mu * dat_v(c, xr, y, t) + mu * (dat_u(c, xr, y + 0.5 * h, t) - dat_u(c, xr, y - 0.5 * h, t));
+      }
+      b[k] = s;
+    }
+  }
+  /* continuity rows */
+  for (int j = 0; j < n; ++j) {
+    const double y = 1.0 + (j + 0.5) * h;
+    for (int i = 0; i < NX; ++i) {
+      double s = 0.0;
+      const double x = chx(c, i) + 0.5 * h;
+      if (i == 0 && !lat) s += h * dat_u(c, xl, y, t);
+      if (i == NX - 1 && !lat) s -= h * dat_u(c, xr, y, t);
+      if (j == n - 1) s -= h * dat_v(c, x, 2.0, t);
+      if (j == 0 && !on_gamma(c, i)) s += h * dat_v(c, x, 1.0, t);
+      b[chp(c, i, j)] = s;
+    }
+  }
+  /* Darcy rows */
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < n; ++i) {
+      double s = 0.0;
+      if (j == 0) s += 2.0 * kc(c, i, 0) / c->mu * dat_ppm(c, (i + 0.5) * h, 0.0, t);
+      b[chm(c, i, j)] = s;
+    }
+}
+
+/* The manufactured solution on the channel's unknowns (geo 1) or the square's (geo 0). */
+void or_exact_geo(int n, double t, double mu, int geo, double *x) {
+  if (geo != 1) {
+    or_exact(n, t, mu, x);
+    return;
+  }
+  or_ctx g;
+  memset(&g, 0, sizeof(g));
+  g.n = n; g.nx = 3 * n; g.iw = n; g.h = 1.0 / n; g.geo = 1;
+  const double h = g.h;
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i <= g.nx; ++i) x[chu(&g, i, j)] = or_mms_u(chx(&g, i), 1.0 + (j + 0.5) * h, t);
+  for (int j = 0; j <= n; ++j)
+    for (int i = 0; i < g.nx; ++i) x[chv(&g, i, j)] = or_mms_v(chx(&g, i) + 0.5 * h, 1.0 + j * h, t);
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < g.nx; ++i) x[chp(&g, i, j)] = or_mms_pff(chx(&g, i) + 0.5 * h, 1.0 + (j + 0.5) * h, t, mu);
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < n; ++i) x[chm(&g, i, j)] = or_mms_ppm((i + 0.5) * h, (j + 0.5) * h, t);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Banded LU with partial pivoting                                           */
 /* Unknowns are re-ordered by height (then by x) so that A is banded with    */
 /* bandwidth about 3n; the same permutation is applied to rows and columns.  */
 /* ------------------------------------------------------------------------ */
+static int64_t sort_key_channel(const or_ctx *c, int64_t k) {
+  /* the square's ordering over the channel: pm cells at the x of the free-flow columns above them */
+  const int n = c->n, NX = c->nx;
+  const int64_t nu = (int64_t)n * (NX + 1), nv = (int64_t)NX * (n + 1), np = (int64_t)NX * n;
+  const int64_t W = 2 * (int64_t)NX + 2;
+  int64_t lev, xp, kind;
+  if (k < nu) { int64_t j = k / (NX + 1), i = k % (NX + 1); lev = 2 * n + 2 * j + 1; xp = 2 * i; kind = 0; }
+  else if (k < nu + nv) { k -= nu; int64_t j = k / NX, i = k % NX; lev = 2 * n + 2 * j; xp = 2 * i + 1; kind = 1; }
+  else if (k < nu + nv + np) { k -= nu + nv; int64_t j = k / NX, i = k % NX; lev = 2 * n + 2 * j + 1; xp = 2 * i + 1; kind = 2; }
+  else { k -= nu + nv + np; int64_t j = k / n, i = k % n; lev = 2 * j + 1; xp = 2 * (i + c->iw) + 1; kind = 3; }
+  return (lev * W + xp) * 4 + kind;
+}
+
 static int64_t sort_key(int n, int64_t k) {
   /* key = (level in units of h/2 from y = 0) * (2n+2) + (x in units of h/2) */
   int64_t nu = (int64_t)n * (n + 1), np = (int64_t)n * n;
@@ -527,7 +870,10 @@ int or_factor(or_ctx *c) {
   c->perm = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
   c->iperm = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
   int64_t *keys = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
-  for (int64_t k = 0; k < N; ++k) { keys[k] = sort_key(c->n, k); c->perm[k] = (int32_t)k; }
+  for (int64_t k = 0; k < N; ++k) {
+    keys[k] = c->geo == 1 ? sort_key_channel(c, k) : sort_key(c->n, k);
+    c->perm[k] = (int32_t)k;
+  }
   g_keys = keys;
   qsort(c->perm, (size_t)N, sizeof(int32_t), cmp_keys);
   g_keys = NULL;

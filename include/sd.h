@@ -97,6 +97,26 @@ extern "C" {
 #define SD_BC_MMS_TRACTION 1
 #define SD_BC_PAPER 2
 
+/* geometry of the free flow over the n x n porous medium [0,1] x [0,1]:
+   SD_GEO_SQUARE   the free flow [0,1] x [1,2], n x n cells (Table 1);
+   SD_GEO_CHANNEL  the channel of the model problem of Sec. 5: free flow
+                   [-1,2] x [1,2], 3n x n cells, whose floor's middle third
+                   (x in [0,1]) is the interface and the rest a no-slip wall.
+                   The boundary conditions of bc apply at the channel's ends
+                   x = -1, 2 (the manufactured solution continued in x; the
+                   pressure-driven problem's inflow on the left end); the
+                   floor faces beside the interface are Dirichlet rows, their
+                   values eliminated from the other rows.  Unknowns: 10 n^2 +
+                   4 n (sd_dof_count_geometry).  Dense state vectors use the
+                   layout [u | v | p_ff | p_pm] with u (3n+1) x n, v 3n x
+                   (n+1), p_ff 3n x n and p_pm n x n, x fastest.  The channel
+                   runs the monolithic coupling only, with one launch per
+                   Chebyshev step (the tile and fuse_coarse options do not
+                   apply); it coarsens to at most 8 x 8 porous-medium cells
+                   (coarsest above 8 counts as 8), so n = m 2^k needs m <= 8. */
+#define SD_GEO_SQUARE 0
+#define SD_GEO_CHANNEL 1
+
 /* coupling of the two subdomains in a time step:
    SD_MONOLITHIC  one block-preconditioned FGMRES solve of Eq. (9) (Sec. 4);
    SD_PARTITIONED the partitioned iteration of Sec. 3: the porous-medium
@@ -251,6 +271,7 @@ typedef struct {
   double bc_tend;      /* SD_BC_PAPER: rise time T of the inflow pressure (default 0:
                           25 time steps) */
   void *stream;        /* cudaStream_t to run on; NULL: the handle creates one */
+  int32_t geometry;    /* SD_GEO_SQUARE (default) | SD_GEO_CHANNEL */
 } sd_options;
 
 typedef struct {
@@ -273,6 +294,10 @@ void sd_options_default(sd_options *opt);
 
 /* 4 n^2 + 2 n: unknowns of one instance (Table 1). */
 int64_t sd_dof_count(int32_t n);
+
+/* Unknowns of one instance of the given geometry (SD_GEO_SQUARE: 4 n^2 + 2 n,
+   SD_GEO_CHANNEL: 10 n^2 + 4 n); -1 for an unknown geometry. */
+int64_t sd_dof_count_geometry(int32_t n, int32_t geometry);
 
 /* Device bytes sd_create() will allocate for this grid and options. */
 int64_t sd_memory_estimate(const sd_grid *grid, const sd_options *opt);

@@ -96,19 +96,29 @@ template <typename T>
 struct MG {
   std::vector<MGLevel<T>> L;
   double *AinvV = nullptr, *AinvD = nullptr, *AinvP = nullptr;
-  int *idxV = nullptr, *idxD = nullptr;
-  int mV = 0, mD = 0;
+  int *idxV = nullptr, *idxD = nullptr, *idxP = nullptr;
+  int mV = 0, mD = 0, mP = 0;  // unknowns of the coarsest V, D' and pressure-Laplacian blocks
   T* chtab = nullptr;  // Chebyshev coefficients, 16 per (level, block): a[0..7], c[8..15]
   int fuse_from = -1;  // first level handled by the fused single-CTA coarse cycle
   CoarseCycle<T> cycV, cycD, cycP;
 };
 
+// grids with at most this many cells per side run fused (measured: 16 beats 32, most in FP64)
 const int FUSE_N = 16;
 // levels up to this many cells per side take their residual and restriction
 // inside the pre-smoothing tile (latency-bound launches there; on larger
 // levels the wider halo it needs costs more than the two launches)
 const int RR_MAX_N = 256;
-const int SMALL_TILE_N = 256;  // levels up to this size smooth 4-row tiles (measured 1.4 % per step at 1024^2)  // grids with at most this many cells per side run fused (measured: 16 beats 32, most in FP64)
+const int SMALL_TILE_N = 256;  // levels up to this size smooth 4-row tiles (measured 1.4 % per step at 1024^2)
+
+// the channel coarsens to at most this many cells per side (its coarsest
+// dense velocity block has 6 n^2 + 4 n unknowns, 416 at 8)
+const int CHANNEL_COARSEST_MAX = 8;
+
+// the coarsening target of the options
+int coarsest_of(const sd_options& o) {
+  return o.geometry == SD_GEO_CHANNEL ? std::min(o.coarsest, CHANNEL_COARSEST_MAX) : o.coarsest;
+}
 
 int level_count(int n, int coarsest) {
   int L = 1;
@@ -188,15 +198,18 @@ struct sd_handle {
 
 namespace {
 
+// unknowns of the handle's dense state vector
+long long dof_of(const sd_handle* h) { return sd_dof_count_geometry(h->n, h->opt.geometry); }
+
 // Lay out (or, with ar.plan == false, assign) every buffer of the handle.
 template <typename T>
 void take_coef(Arena& a, const Geom& g, LevelCoef<T>& C) {
-  C.w = a.take<T>(g.n + 1);
-  C.rg = a.take<T>(g.n + 1);
+  C.w = a.take<T>(g.nx + 1);
+  C.rg = a.take<T>(g.nx + 1);
   C.Tx = a.take<T>((long long)g.n * g.P);
   C.Ty = a.take<T>((long long)(g.n + 1) * g.P);
-  C.wP = a.take<T>(g.n + 1);
-  C.rgP = a.take<T>(g.n + 1);
+  C.wP = a.take<T>(g.nx + 1);
+  C.rgP = a.take<T>(g.nx + 1);
   C.TxP = a.take<T>((long long)g.n * g.P);
   C.TyP = a.take<T>((long long)(g.n + 1) * g.P);
 }
@@ -224,20 +237,23 @@ void plan_mg(sd_handle* h, MG<T>& M, bool own_coef) {
     take_block<T>(a, g.lenD, L.Pb);
   }
   const Geom& gc = h->geo[h->nlev - 1];
-  M.mV = 2 * gc.n * (gc.n + 1);
+  M.mV = gc.n * (gc.nx + 1) + (gc.n + 1) * gc.nx;
   M.mD = gc.n * gc.n;
+  M.mP = gc.n * gc.nx;
   M.AinvV = a.take<double>((long long)M.mV * M.mV);
   M.AinvD = a.take<double>((long long)M.mD * M.mD);
-  M.AinvP = a.take<double>((long long)M.mD * M.mD);
+  M.AinvP = a.take<double>((long long)M.mP * M.mP);
   M.idxV = a.take<int>(M.mV);
   M.idxD = a.take<int>(M.mD);
+  M.idxP = a.take<int>(M.mP);
   M.chtab = a.take<T>((long long)h->nlev * 3 * 16);
 }
 
 void plan_all(sd_handle* h) {
   Arena& a = h->ar;
   const int n = h->n;
-  h->stage = a.take<double>(sd_dof_count(n) > (long long)n * n ? sd_dof_count(n) : (long long)n * n);
+  const long long nd = dof_of(h);
+  h->stage = a.take<double>(nd > (long long)n * n ? nd : (long long)n * n);
   h->Klev.resize(h->nlev);
   h->c64.resize(h->nlev);
   for (int l = 0; l < h->nlev; ++l) {
@@ -255,7 +271,7 @@ void plan_all(sd_handle* h) {
   h->B1 = a.take<double>(len);
   h->V = a.take<double>((long long)(h->m + 1) * h->lenA);
   h->Z = a.take<double>((long long)h->m * h->lenA);
-  h->partial = a.take<double>(std::max((long long)h->nblk * 32, 4 * resid_norms_blocks(n)));
+  h->partial = a.take<double>(std::max((long long)h->nblk * 32, 4 * resid_norms_blocks(h->g.nx, n)));
   h->scal = a.take<double>(256);
   h->st = a.take<double>((long long)(h->m + 1) * h->m + 3 * h->m + 1);
   h->flag = a.take<double>(8);
@@ -289,6 +305,7 @@ Coef<double> coef64(sd_handle* h, int l, bool poisson = false) {
   LevelCoef<double>& C = h->c64[l];
   Coef<double> c;
   c.n = g.n; c.P = g.P; c.h = g.h; c.mu = h->mu; c.cm = g.h * g.h / h->dt;
+  c.nx = g.nx; c.iw = g.iw; c.cx = poisson ? g.nx : g.n;
   c.lat = h->opt.bc != SD_BC_MMS;
   c.w = poisson ? C.wP : C.w;
   c.rg = poisson ? C.rgP : C.rg;
@@ -304,8 +321,10 @@ void bind_coef(sd_handle* h, MG<T>& M) {
     MGLevel<T>& L = M.L[l];
     const Geom& g = h->geo[l];
     L.c.n = g.n; L.c.P = g.P; L.c.h = (T)g.h; L.c.mu = (T)h->mu; L.c.cm = (T)(g.h * g.h / h->dt);
+    L.c.nx = g.nx; L.c.iw = g.iw; L.c.cx = g.n;
     L.c.lat = h->opt.bc != SD_BC_MMS;
     L.cP = L.c;
+    L.cP.cx = g.nx;
     L.c.w = L.own.w; L.c.rg = L.own.rg; L.c.Tx = L.own.Tx; L.c.Ty = L.own.Ty;
     L.cP.w = L.own.wP; L.cP.rg = L.own.rgP; L.cP.Tx = L.own.TxP; L.cP.Ty = L.own.TyP;
     finish_coef(L.c);
@@ -381,12 +400,13 @@ int coarse_inverse(sd_handle* h, int kind, double* Ainv, int* idx_dev, int m) {
   int k = 0;
   if (blockV) {
     for (int j = 0; j < g.n; ++j)
-      for (int i = 0; i <= g.n; ++i) idx[k++] = j * g.P + i;
+      for (int i = 0; i <= g.nx; ++i) idx[k++] = j * g.P + i;
     for (int j = 0; j <= g.n; ++j)
-      for (int i = 0; i < g.n; ++i) idx[k++] = (int)(g.ov + (long long)j * g.P + i);
+      for (int i = 0; i < g.nx; ++i) idx[k++] = (int)(g.ov + (long long)j * g.P + i);
   } else {
+    const int cx = kind == 2 ? g.nx : g.n;  // pressure Laplacian: the free-flow cells
     for (int j = 0; j < g.n; ++j)
-      for (int i = 0; i < g.n; ++i) idx[k++] = j * g.P + i;
+      for (int i = 0; i < cx; ++i) idx[k++] = j * g.P + i;
   }
   cudaStream_t s = h->s;
   CK(cudaMemcpyAsync(idx_dev, idx.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
@@ -425,18 +445,18 @@ int setup_mg(sd_handle* h, MG<T>& M) {
     if (!L.own.w) continue;
     const LevelCoef<double>& C = h->c64[l];
     const long long nx = (long long)L.g.n * L.g.P, ny = (long long)(L.g.n + 1) * L.g.P;
-    launch_convert<T>(C.w, L.own.w, L.g.n + 1, s);
-    launch_convert<T>(C.rg, L.own.rg, L.g.n + 1, s);
+    launch_convert<T>(C.w, L.own.w, L.g.nx + 1, s);
+    launch_convert<T>(C.rg, L.own.rg, L.g.nx + 1, s);
     launch_convert<T>(C.Tx, L.own.Tx, nx, s);
     launch_convert<T>(C.Ty, L.own.Ty, ny, s);
-    launch_convert<T>(C.wP, L.own.wP, L.g.n + 1, s);
-    launch_convert<T>(C.rgP, L.own.rgP, L.g.n + 1, s);
+    launch_convert<T>(C.wP, L.own.wP, L.g.nx + 1, s);
+    launch_convert<T>(C.rgP, L.own.rgP, L.g.nx + 1, s);
     launch_convert<T>(C.TxP, L.own.TxP, nx, s);
     launch_convert<T>(C.TyP, L.own.TyP, ny, s);
   }
   CKR(coarse_inverse(h, 0, M.AinvV, M.idxV, M.mV));
   CKR(coarse_inverse(h, 1, M.AinvD, M.idxD, M.mD));
-  CKR(coarse_inverse(h, 2, M.AinvP, M.idxD, M.mD));
+  CKR(coarse_inverse(h, 2, M.AinvP, M.idxP, M.mP));
   const int deg = h->opt.cheb_degree;
   for (int l = 0; l + 1 < h->nlev; ++l) {
     double lv, ld, lp;
@@ -468,7 +488,7 @@ int setup_mg(sd_handle* h, MG<T>& M) {
     CK(cudaStreamSynchronize(s));
   }
   M.fuse_from = -1;
-  if (h->opt.fuse_coarse) {
+  if (h->opt.fuse_coarse && h->g.iw == 0) {  // (the fused cycle serves the square geometry)
     auto fill = [&](CoarseCycle<T>& q, int kind, int which, int f) {
       std::memset(&q, 0, sizeof(q));
       q.nlev = h->nlev - f;
@@ -488,8 +508,8 @@ int setup_mg(sd_handle* h, MG<T>& M) {
       q.b_in = B0.b;
       q.x_out = B0.x;
       q.Ainv = which == 0 ? M.AinvV : (which == 1 ? M.AinvD : M.AinvP);
-      q.idx = which == 0 ? M.idxV : M.idxD;
-      q.m = which == 0 ? M.mV : M.mD;
+      q.idx = which == 0 ? M.idxV : (which == 1 ? M.idxD : M.idxP);
+      q.m = which == 0 ? M.mV : (which == 1 ? M.mD : M.mP);
     };
     // the largest entry grid (at most FUSE_N cells per side) whose levels fit in shared memory
     for (int f = 0; f < h->nlev; ++f) {
@@ -544,28 +564,31 @@ struct ProfScope {
 // Algorithmic bytes of one launch (compulsory traffic, each array once):
 //  fine velocity-block Chebyshev step: read x_in (if any), b, d (if a != 0);
 //  write d and x_out, over the 2n(n+1) velocity faces.
+// faces of the velocity block: u n x (nx+1), v (n+1) x nx
+double faces_V(const Geom& g) { return (double)g.n * (g.nx + 1) + (double)g.nx * (g.n + 1); }
 double cheb_bytes_V(const Geom& g, size_t es, bool has_x, bool has_d) {
-  const double nv = 2.0 * g.n * (g.n + 1);
+  const double nv = faces_V(g);
   return nv * es * (1.0 + (has_x ? 1 : 0) + (has_d ? 1 : 0) + 2.0);
 }
 //  tiled velocity smoothing: read b (and x_in), write x_out over the faces
 //  (the small coarse correction read by the post-smoothing is not counted)
 double tile_bytes_V(const Geom& g, size_t es, bool has_x) {
-  const double nv = 2.0 * g.n * (g.n + 1);
+  const double nv = faces_V(g);
   return nv * es * (has_x ? 3.0 : 2.0);
 }
 //  whole-system FP64 operator, algorithmic flops: one multiply-add per stored
-//  matrix entry, nnz = 2 * 11 (u, v rows) + 4 (continuity) + 5 (Darcy) per
-//  cell minus the eliminated boundary couplings, about 31 per cell.
+//  matrix entry, nnz = 2 * 11 (u, v rows) + 4 (continuity) per free-flow
+//  cell and 5 (Darcy) per pm cell minus the eliminated boundary couplings,
+//  about 31 per cell of the square geometry.
 double apply_flops(const Geom& g) {
   const double n = g.n;
-  const double nnz = 31.0 * n * n - 6.0 * n;
+  const double nnz = 26.0 * g.nx * n + 5.0 * n * n - 6.0 * n;
   return 2.0 * nnz;
 }
-//  whole-system FP64 operator: read x (4n^2+2n), the transmissibilities
+//  whole-system FP64 operator: read x (every unknown), the transmissibilities
 //  (2n(n+1)) and interface coefficients (2n), read b if residual, write y.
 double apply_bytes(const Geom& g, bool resid) {
-  const double nd = 4.0 * g.n * g.n + 2.0 * g.n;
+  const double nd = faces_V(g) + (double)g.nx * g.n + (double)g.n * g.n;
   return 8.0 * (nd * (resid ? 3 : 2) + 2.0 * g.n * (g.n + 1) + 2.0 * g.n);
 }
 
@@ -611,10 +634,11 @@ int wave_rows_of(const sd_handle* h, int n) {
 }
 
 // tiled smoothing (all steps of one smoothing in one kernel) is used for the
-// FP32 hierarchy with at most four Chebyshev steps
+// FP32 hierarchy with at most four Chebyshev steps, in the square geometry
+// (the channel's levels run one launch per step)
 template <typename T>
 bool use_tiles(const sd_handle* h, const Block<T>& B) {
-  return std::is_same<T, float>::value && h->opt.tile && B.cha.size() >= 1 && B.cha.size() <= 4;
+  return std::is_same<T, float>::value && h->opt.tile && h->g.iw == 0 && B.cha.size() >= 1 && B.cha.size() <= 4;
 }
 
 // Velocity block: Chebyshev pre-smoothing from zero, residual, transposed
@@ -659,7 +683,7 @@ void vcycle_V(MG<T>& M, int l, cudaStream_t s, sd_handle* prof_owner) {
   }
   if (!fused) {
     launch_resid_V<T>(L.c, cur, B.b, B.r, 0, 1, 0, s);
-    launch_restrict_V<T>(L.g.n, L.g.P, B.r, C.g.n, C.g.P, C.V.b, L.c.lat, s);
+    launch_restrict_V<T>(L.g.n, L.g.P, B.r, C.g.n, C.g.nx, C.g.iw, C.g.P, C.V.b, L.c.lat, s);
   }
   vcycle_V(M, l + 1, s, prof_owner);
   if (tiles) {  // prolongation folded into the post-smoothing tile load
@@ -669,7 +693,7 @@ void vcycle_V(MG<T>& M, int l, cudaStream_t s, sd_handle* prof_owner) {
       launch_smooth_tile_V<T>(L.c, cur, B.b, out, steps_of(B, h_tile_rows, h_wave), B.cht, C.V.res, C.g.n, C.g.P, s);
     cur = out;
   } else {
-    launch_prolong_V<T>(L.g.n, L.g.P, cur, C.g.n, C.g.P, C.V.res, L.c.lat, s);
+    launch_prolong_V<T>(L.g.n, L.g.P, cur, C.g.n, C.g.nx, C.g.iw, C.g.P, C.V.res, L.c.lat, s);
     for (int k = 0; k < (int)B.cha.size(); ++k) {
       T* out = (cur == B.x) ? B.x2 : B.x;
       {
@@ -694,7 +718,7 @@ void vcycle_cell(MG<T>& M, int l, bool poisson, cudaStream_t s, const sd_handle*
     return;
   }
   if (l + 1 == (int)M.L.size()) {
-    launch_dense_solve<T>(poisson ? M.AinvP : M.AinvD, M.idxD, M.mD, B.b, B.x, s);
+    launch_dense_solve<T>(poisson ? M.AinvP : M.AinvD, poisson ? M.idxP : M.idxD, poisson ? M.mP : M.mD, B.b, B.x, s);
     B.res = B.x;
     return;
   }
@@ -726,7 +750,7 @@ void vcycle_cell(MG<T>& M, int l, bool poisson, cudaStream_t s, const sd_handle*
       launch_smooth_tile_D<T>(c, cur, B.b, out, steps_of(B, h_tile_rows, h_wave), B.cht, BC.res, C.g.n, C.g.P, s);
     cur = out;
   } else {
-    launch_prolong_D<T>(L.g.n, L.g.P, cur, C.g.n, C.g.P, BC.res, s);
+    launch_prolong_D<T>(L.g.n, c.cx, L.g.P, cur, C.g.n, C.g.P, BC.res, s);
     for (int k = 0; k < (int)B.cha.size(); ++k) {
       T* out = (cur == B.x) ? B.x2 : B.x;
       launch_cheb_D<T>(c, cur, B.b, B.d, out, B.cha[k], B.chc[k], B.cht ? B.cht + k : nullptr, 1, 0, s);
@@ -1494,19 +1518,24 @@ int validate(const sd_grid* grid, double mu, double alpha, double dt, const sd_o
     return SD_E_INVAL;
   if (o->cheb_degree_coarse < 0 || o->cheb_degree_coarse > 8 || o->schur_degree < 0 || o->schur_degree > 8)
     return SD_E_INVAL;
-  int n = grid->nx, L = level_count(n, o->coarsest);
+  if (o->geometry != SD_GEO_SQUARE && o->geometry != SD_GEO_CHANNEL) return SD_E_INVAL;
+  // the channel runs the monolithic coupling only
+  if (o->geometry == SD_GEO_CHANNEL && o->coupling != SD_MONOLITHIC) return SD_E_INVAL;
+  int n = grid->nx, L = level_count(n, coarsest_of(*o));
   for (int l = 1; l < L; ++l) n /= 2;
   if (n > 16) return SD_E_INVAL;  // coarsest grid must stay small for the dense solve
+  if (o->geometry == SD_GEO_CHANNEL && n > CHANNEL_COARSEST_MAX) return SD_E_INVAL;
   return SD_OK;
 }
 
 void init_layout(sd_handle* h) {
-  h->g = make_geom(h->n);
-  h->nlev = level_count(h->n, h->opt.coarsest);
+  const int geo = h->opt.geometry == SD_GEO_CHANNEL ? 1 : 0;
+  h->g = make_geom(h->n, geo);
+  h->nlev = level_count(h->n, coarsest_of(h->opt));
   h->geo.clear();
   int nl = h->n;
   for (int l = 0; l < h->nlev; ++l) {
-    h->geo.push_back(make_geom(nl));
+    h->geo.push_back(make_geom(nl, geo));
     nl /= 2;
   }
   h->m = h->opt.restart;
@@ -1566,19 +1595,23 @@ int create_impl(const sd_grid* grid, double mu, const double* K, double alpha, d
   launch_pack_K(h->stage, n, h->Klev[0], h->geo[0].P, s);
   for (int l = 1; l < h->nlev; ++l)
     launch_coarsen_K(h->Klev[l - 1], h->geo[l - 1].n, h->geo[l - 1].P, h->Klev[l], h->geo[l].P, s);
+  const int lat = o.bc != SD_BC_MMS;
   for (int l = 0; l < h->nlev; ++l) {
     LevelCoef<double>& C = h->c64[l];
     const Geom& g = h->geo[l];
-    launch_setup_coef<double>(h->Klev[l], g.n, g.P, mu, alpha, o.bc != SD_BC_MMS, 0, C.w, C.rg, C.Tx, C.Ty, s);
+    launch_setup_coef<double>(h->Klev[l], g.n, g.n, g.P, mu, alpha, lat, 0, 0, g.n, g.nx, g.iw, C.w, C.rg, C.Tx,
+                              C.Ty, s);
   }
-  // pressure Laplacian B^T B / h^2: TPFA with K / mu = 1 (the staging buffer
-  // holds the unit permeability, the Krylov slots are free during setup)
+  // pressure Laplacian B^T B / h^2 over the free-flow cells: TPFA with K / mu
+  // = 1 (the Krylov slots hold the unit permeability, free during setup); its
+  // bottom faces are Dirichlet below the interface (the half control volume
+  // of v_Gamma), no-flow beside it
   for (int l = 0; l < h->nlev; ++l) {
     LevelCoef<double>& C = h->c64[l];
     const Geom& g = h->geo[l];
-    launch_fill_K(h->V, g.n, g.P, mu, s);
-    launch_setup_coef<double>(h->V, g.n, g.P, mu, alpha, o.bc != SD_BC_MMS, o.bc != SD_BC_MMS, C.wP, C.rgP, C.TxP,
-                              C.TyP, s);
+    launch_fill_K(h->V, g.nx, g.n, g.P, mu, s);
+    launch_setup_coef<double>(h->V, g.n, g.nx, g.P, mu, alpha, lat, lat, g.iw, g.iw + g.n, g.nx, g.iw, C.wP, C.rgP,
+                              C.TxP, C.TyP, s);
   }
   const Coef<double> c0 = coef64(h, 0);
   launch_mms_terms(c0, o.bc, h->Klev[0], h->B0, h->B1, s);
@@ -1614,6 +1647,7 @@ int create_impl(const sd_grid* grid, double mu, const double* K, double alpha, d
 namespace sdk {
 
 int handle_grid(const sd_handle* h) { return h->n; }
+long long handle_dof(const sd_handle* h) { return dof_of(h); }
 
 bool can_lockstep(const sd_handle* a, const sd_handle* b) {
   const sd_options& x = a->opt;
@@ -1627,7 +1661,7 @@ bool can_lockstep(const sd_handle* a, const sd_handle* b) {
                         x.reorth_eta == y.reorth_eta && x.extrapolate == y.extrapolate && x.graph == y.graph &&
                         x.pdl == y.pdl && x.tile == y.tile && x.tile_rows == y.tile_rows &&
                         x.darcy_coupled == y.darcy_coupled && x.bc_dp == y.bc_dp && x.bc_tend == y.bc_tend &&
-                        x.coupling == SD_MONOLITHIC &&
+                        x.geometry == y.geometry && x.coupling == SD_MONOLITHIC &&
                         y.coupling == SD_MONOLITHIC;
   return same_opt && a->n == b->n && a->mu == b->mu && a->dt == b->dt && a->ar.off == b->ar.off &&
          a->nlev == b->nlev && a->prof_id < 0 && b->prof_id < 0;
@@ -1912,9 +1946,15 @@ void sd_options_default(sd_options* o) {
   o->cheb_ratio = 8.0;
   o->schur_mass = 1;
   o->stream = nullptr;
+  o->geometry = SD_GEO_SQUARE;
 }
 
 int64_t sd_dof_count(int32_t n) { return 4 * (int64_t)n * n + 2 * (int64_t)n; }
+
+int64_t sd_dof_count_geometry(int32_t n, int32_t geometry) {
+  if (geometry == SD_GEO_CHANNEL) return 10 * (int64_t)n * n + 4 * (int64_t)n;
+  return geometry == SD_GEO_SQUARE ? sd_dof_count(n) : -1;
+}
 
 int64_t sd_memory_estimate(const sd_grid* grid, const sd_options* opt) {
   sd_options o;
@@ -1967,13 +2007,13 @@ int sd_step(sd_handle* h, int32_t nsteps, sd_step_info* info) {
 int sd_get_fields(sd_handle* h, double* u, double* v, double* p_ff, double* p_pm) {
   if (!h) return SD_E_INVAL;
   std::lock_guard<std::mutex> lk(h->mtx);
-  const int n = h->n;
+  const int n = h->n, nx = h->g.nx;
   launch_unpack(h->g, h->x, h->stage, h->s);
-  const long long nu = (long long)n * (n + 1), nn = (long long)n * n;
+  const long long nu = (long long)n * (nx + 1), nv = (long long)nx * (n + 1), npf = (long long)nx * n;
   if (u) CKR(copy_out(h, u, h->stage, nu));
-  if (v) CKR(copy_out(h, v, h->stage + nu, nu));
-  if (p_ff) CKR(copy_out(h, p_ff, h->stage + 2 * nu, nn));
-  if (p_pm) CKR(copy_out(h, p_pm, h->stage + 2 * nu + nn, nn));
+  if (v) CKR(copy_out(h, v, h->stage + nu, nv));
+  if (p_ff) CKR(copy_out(h, p_ff, h->stage + nu + nv, npf));
+  if (p_pm) CKR(copy_out(h, p_pm, h->stage + nu + nv + npf, (long long)n * n));
   CK(cudaStreamSynchronize(h->s));
   return SD_OK;
 }
@@ -1985,12 +2025,12 @@ int sd_get_state(sd_handle* h, double* t, int64_t* step, double* x, double* xpre
   if (step) *step = h->step;
   if (x) {
     launch_unpack(h->g, h->x, h->stage, h->s);
-    CKR(copy_out(h, x, h->stage, sd_dof_count(h->n)));
+    CKR(copy_out(h, x, h->stage, dof_of(h)));
   }
   if (xprev) {
     CK(cudaStreamSynchronize(h->s));
     launch_unpack(h->g, h->have_prev ? h->xm : h->x, h->stage, h->s);
-    CKR(copy_out(h, xprev, h->stage, sd_dof_count(h->n)));
+    CKR(copy_out(h, xprev, h->stage, dof_of(h)));
   }
   CK(cudaStreamSynchronize(h->s));
   return SD_OK;
@@ -1999,13 +2039,13 @@ int sd_get_state(sd_handle* h, double* t, int64_t* step, double* x, double* xpre
 int sd_set_state(sd_handle* h, double t, int64_t step, const double* x, const double* xprev) {
   if (!h || !x) return SD_E_INVAL;
   std::lock_guard<std::mutex> lk(h->mtx);
-  CKR(copy_in_dense(h, x, sd_dof_count(h->n)));
+  CKR(copy_in_dense(h, x, dof_of(h)));
   launch_pack(h->g, h->stage, h->x, h->s);
   CK(cudaStreamSynchronize(h->s));
   h->have_prev = false;
   h->levels = 1;
   if (xprev) {
-    CKR(copy_in_dense(h, xprev, sd_dof_count(h->n)));
+    CKR(copy_in_dense(h, xprev, dof_of(h)));
     launch_pack(h->g, h->stage, h->xm, h->s);
     CK(cudaStreamSynchronize(h->s));
     h->have_prev = true;
@@ -2021,7 +2061,7 @@ int sd_get_history(sd_handle* h, double* xprev2) {
   std::lock_guard<std::mutex> lk(h->mtx);
   if (h->opt.extrapolate < 2 || h->levels < 3) return SD_E_STATE;
   launch_unpack(h->g, h->xmm, h->stage, h->s);
-  CKR(copy_out(h, xprev2, h->stage, sd_dof_count(h->n)));
+  CKR(copy_out(h, xprev2, h->stage, dof_of(h)));
   CK(cudaStreamSynchronize(h->s));
   return SD_OK;
 }
@@ -2030,7 +2070,7 @@ int sd_set_history(sd_handle* h, const double* xprev2) {
   if (!h || !xprev2) return SD_E_INVAL;
   std::lock_guard<std::mutex> lk(h->mtx);
   if (h->opt.extrapolate < 2 || !h->have_prev || h->levels < 2) return SD_E_STATE;
-  CKR(copy_in_dense(h, xprev2, sd_dof_count(h->n)));
+  CKR(copy_in_dense(h, xprev2, dof_of(h)));
   launch_pack(h->g, h->stage, h->xmm, h->s);
   CK(cudaStreamSynchronize(h->s));
   h->levels = 3;
@@ -2040,7 +2080,7 @@ int sd_set_history(sd_handle* h, const double* xprev2) {
 int sd_apply(sd_handle* h, const double* x, double* y) {
   if (!h || !x || !y) return SD_E_INVAL;
   std::lock_guard<std::mutex> lk(h->mtx);
-  const long long nd = sd_dof_count(h->n);
+  const long long nd = dof_of(h);
   double* xin = h->V;                   // padded scratch in the Krylov slots
   double* yout = h->V + h->lenA;
   CKR(copy_in_dense(h, x, nd));
@@ -2055,7 +2095,7 @@ int sd_apply(sd_handle* h, const double* x, double* y) {
 int sd_rhs(sd_handle* h, const double* xprev, double t, double* bout) {
   if (!h || !xprev || !bout) return SD_E_INVAL;
   std::lock_guard<std::mutex> lk(h->mtx);
-  const long long nd = sd_dof_count(h->n);
+  const long long nd = dof_of(h);
   double* xp = h->V;
   double* bb = h->V + h->lenA;
   CKR(copy_in_dense(h, xprev, nd));
@@ -2071,7 +2111,7 @@ int sd_solve(sd_handle* h, const double* b, double* x, sd_step_info* info) {
   if (!h || !b || !x) return SD_E_INVAL;
   std::lock_guard<std::mutex> lk(h->mtx);
   t_pdl = h->opt.pdl;
-  const long long nd = sd_dof_count(h->n);
+  const long long nd = dof_of(h);
   // b and the iterate use the handle's b and a separate padded copy of x
   CKR(copy_in_dense(h, b, nd));
   launch_pack(h->g, h->stage, h->b, h->s);

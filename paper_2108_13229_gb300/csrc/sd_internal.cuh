@@ -103,7 +103,9 @@ extern thread_local long long t_launch_count;
   (::sdk::t_launch_count += (k), ::sdk::g_launch_count.fetch_add((k), std::memory_order_relaxed))
 
 struct Geom {
-  int n;        // cells per side
+  int n;        // cells per side (porous medium; free-flow rows)
+  int nx;       // free-flow cells across: n (square geometry) or 3n (the channel of Sec. 5)
+  int iw;       // first free-flow column above the porous medium (0, or n in the channel)
   int P;        // row pitch in elements
   long long ou, ov, opf, opm, len;  // field offsets and whole-vector length
   long long lenV;                   // length of the velocity block [u | v]
@@ -111,10 +113,17 @@ struct Geom {
   double h;
 };
 
-inline Geom make_geom(int n) {
+// geo 0: free flow n x n over the porous medium n x n (Table 1); geo 1: the
+// channel, free flow 3n x n whose floor's middle third is the interface
+// (columns iw = n .. 2n-1), the rest of it a wall.  The porous-medium cells
+// occupy columns 0 .. n-1 of their rows; the v face above pm cell i is the
+// free-flow v face iw + i.
+inline Geom make_geom(int n, int geo = 0) {
   Geom g;
   g.n = n;
-  g.P = ((n + 1) + 7) / 8 * 8;
+  g.nx = geo == 1 ? 3 * n : n;
+  g.iw = geo == 1 ? n : 0;
+  g.P = ((g.nx + 1) + 7) / 8 * 8;
   g.ou = 0;
   g.ov = (long long)n * g.P;
   g.opf = (long long)(2 * n + 1) * g.P;
@@ -129,17 +138,27 @@ inline Geom make_geom(int n) {
 // Coefficients of one level in precision T (Sec. 2 discretisation):
 //   w[i]  = mu / (h + 2 beta_i), beta_i = mean sqrt(K) of the two pm cells
 //           below interface u face i, over alpha_BJ (Eq. (6)); i = 1..n-1
+//           (channel: u faces iw .. iw + n, the ends over one pm cell)
 //   rg[i] = mu h^2 / (2 K_i) of the pm cell below v_Gamma face i (Eq. (5))
+//           (channel: floor faces iw .. iw + n - 1)
 //   Tx    n rows x P: TPFA transmissibility of the pm face left of cell i
 //         (i = 0 and i = n: no-flow sides, 0)
 //   Ty    (n+1) rows x P: face below cell row j (j = 0: Dirichlet bottom,
 //         2K/mu; j = n: interface, 0 -- the flux there is h v_Gamma)
+//         (pressure-Laplacian set: the same over its cx cells, with the
+//         bottom faces Dirichlet only below the interface)
 //   lat   1: the free-flow sides x = 0, 1 are traction sides (their u faces
 //         are unknowns with half-control-volume rows; w[0] and w[n] are the
 //         BJS coefficients of their interface corners); 0: Dirichlet sides
+//   nx, iw free-flow cells across and the interface window [iw, iw + n) of
+//         the free-flow floor faces (square geometry: nx = n, iw = 0)
+//   cx    cells across of the cell block this set serves: n for the Darcy
+//         set (and the Darcy rows of the whole operator), nx for the
+//         pressure Laplacian of the free-flow cells
 template <typename T>
 struct Coef {
   int n, P;
+  int nx, iw, cx;
   int lat;
   T h, mu, cm;  // cm = h^2 / dt
   const T* w;
@@ -170,10 +189,13 @@ __device__ __forceinline__ void bsh_coef(Coef<T>& c, long long o) {
 // setup
 void launch_coarsen_K(const double* Kf, int nf, int Pf, double* Kc, int Pc, cudaStream_t s);
 void launch_pack_K(const double* Kdense, int n, double* Kp, int P, cudaStream_t s);
-void launch_fill_K(double* K, int n, int P, double v, cudaStream_t s);
+void launch_fill_K(double* K, int cx, int n, int P, double v, cudaStream_t s);
+// one coefficient set: Tx, Ty over cx x n cells of K (pitch P), the bottom
+// faces Dirichlet over cells [b0, b1); w over u faces 0..nx and rg over floor
+// faces 0..nx-1 from the top row of K, the interface over faces iw .. iw + n
 template <typename T>
-void launch_setup_coef(const double* Kp, int n, int P, double mu, double alpha, int lat, int xdir, T* w, T* rg, T* Tx,
-                       T* Ty, cudaStream_t s);
+void launch_setup_coef(const double* Kp, int n, int cx, int P, double mu, double alpha, int lat, int xdir, int b0,
+                       int b1, int nx, int iw, T* w, T* rg, T* Tx, T* Ty, cudaStream_t s);
 template <typename T>
 void launch_convert(const double* src, T* dst, long long len, cudaStream_t s);
 
@@ -184,7 +206,7 @@ void launch_apply_full(const Coef<double>& c, const double* x, const double* b, 
 // sc[bn] = ||b||^2 (partial: 4 * resid_norms_blocks(n) doubles of scratch)
 void launch_resid_norms(const Coef<double>& c, const double* x, const double* b, double* r, double* partial,
                         double* sc, int blk, int b2, int bn, int with_b, cudaStream_t s);
-long long resid_norms_blocks(int n);
+long long resid_norms_blocks(int nx, int n);
 // the free-flow rows of it (u, v, p_ff) with the porous-medium unknowns taken as zero;
 // the Darcy rows of y are not written; vdir: the v_Gamma rows are identities
 void launch_apply_ff(const Coef<double>& c, const double* x, const double* b, double* y, int vdir, cudaStream_t s);
@@ -253,19 +275,21 @@ void launch_resid_V(const Coef<T>& c, const T* x, const T* b, T* r, int jac, int
 template <typename T>
 void launch_resid_D(const Coef<T>& c, const T* x, const T* b, T* r, int jac, int nbatch, long long bstride,
                     cudaStream_t s);
-// coarse rhs = R r with R the transposed bilinear (V) / cell-sum (D) transfer
+// coarse rhs = R r with R the transposed bilinear (V) / cell-sum (D) transfer;
+// nxc, iwc: the coarse level's free-flow cells across and interface window
 template <typename T>
-void launch_restrict_V(int nf, int Pf, const T* r, int nc, int Pc, T* bc, int lat, cudaStream_t s);
+void launch_restrict_V(int nf, int Pf, const T* r, int nc, int nxc, int iwc, int Pc, T* bc, int lat, cudaStream_t s);
 template <typename T>
 void launch_restrict_D(int nf, int Pf, const T* r, int nc, int Pc, T* bc, cudaStream_t s);
 // cell blocks: bc = R (b - A x) with the cell-sum restriction, one pass
 template <typename T>
 void launch_resid_restrict_D(const Coef<T>& c, const T* x, const T* b, int nc, int Pc, T* bc, cudaStream_t s);
-// x += P e (bilinear, staggered for V, cell-centred for D)
+// x += P e (bilinear, staggered for V, cell-centred for D; xf: the fine
+// cell block's cells across)
 template <typename T>
-void launch_prolong_V(int nf, int Pf, T* x, int nc, int Pc, const T* e, int lat, cudaStream_t s);
+void launch_prolong_V(int nf, int Pf, T* x, int nc, int nxc, int iwc, int Pc, const T* e, int lat, cudaStream_t s);
 template <typename T>
-void launch_prolong_D(int nf, int Pf, T* x, int nc, int Pc, const T* e, cudaStream_t s);
+void launch_prolong_D(int nf, int xf, int Pf, T* x, int nc, int Pc, const T* e, cudaStream_t s);
 
 // Fused coarse V-cycle: levels c[0] (entry) .. c[nlev-1] (coarsest) in one
 // CTA with shared-memory work vectors.  kind 0: velocity block, 1: cell block.
@@ -429,6 +453,8 @@ bool can_lockstep(const sd_handle* a, const sd_handle* b);
 int step_lockstep(sd_handle* const* hs, int count, int nsteps, sd_step_info* const* infos);
 // cells per side of a handle's grid
 int handle_grid(const sd_handle* h);
+// unknowns of a handle's dense state vector
+long long handle_dof(const sd_handle* h);
 #endif
 
 }  // namespace sdk

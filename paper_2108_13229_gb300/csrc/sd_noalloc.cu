@@ -102,11 +102,15 @@ extern "C" int sd_apply_noalloc(const sd_grid* grid, double mu, const double* K,
   // nothing was pending at entry, so an error seen after a launch is that
   // launch's own
   launch_pack_K(K, n, base + oK, g.P, s);
-  launch_setup_coef<double>(base + oK, n, g.P, mu, alpha_bj, 0, 0, base + ow, base + org, base + oTx, base + oTy, s);
+  launch_setup_coef<double>(base + oK, n, n, g.P, mu, alpha_bj, 0, 0, 0, n, n, 0, base + ow, base + org, base + oTx,
+                            base + oTy, s);
   launch_pack(g, x, base + ox, s);
   if (cudaGetLastError() != cudaSuccess) return SD_E_CUDA;
   Coef<double> c;
   c.n = n;
+  c.nx = n;  // the square geometry
+  c.iw = 0;
+  c.cx = n;
   c.P = g.P;
   c.lat = 0;  // Dirichlet free-flow sides (the SD_BC_MMS operator)
   c.h = g.h;

@@ -49,8 +49,9 @@ static inline dim3 grid2R(int nx, int ny, int R) { return dim3((nx + BX - 1) / B
 // fused multiply-adds from b (RES: y = b - A x) or from its first product (y
 // = A x), its coefficients signed once per thread, so each stored matrix
 // entry costs one FP64 instruction (the Darcy diagonal adds three).  The
-// caller guarantees 2 <= i <= n-2 and 1 <= j <= n-2.
-template <bool RES, int PS>
+// caller guarantees 2 <= i <= nx-2 and 1 <= j <= n-2, and with DARCY (the
+// porous medium's rows at the same cell) i <= n-2.
+template <bool RES, int PS, bool DARCY>
 __device__ __forceinline__ void apply_cell_interior(const Coef<double>& c, const double* __restrict__ u,
                                                     const double* __restrict__ v, const double* __restrict__ pf,
                                                     const double* __restrict__ pm, const double* __restrict__ b,
@@ -100,7 +101,7 @@ __device__ __forceinline__ void apply_cell_interior(const Coef<double>& c, const
     if (PS) acc[1] = fma(a, a, acc[1]);
     if (PS == 2) acc[3] = fma(b[npf + kc], b[npf + kc], acc[3]);
   }
-  {  // Darcy: (tw + te + ts + tn) p - tw pW - te pE - ts pS - tn pN
+  if (DARCY) {  // Darcy: (tw + te + ts + tn) p - tw pW - te pE - ts pS - tn pN
     const double tw = c.Tx[kc], te = c.Tx[kc + 1], ts = c.Ty[kc], tn = c.Ty[kc + P];
     const double kg = sg * ((tw + te) + (ts + tn));
     double a = RES ? fma(kg, pm[kc], b[npm + kc]) : kg * pm[kc];
@@ -122,21 +123,35 @@ __device__ __forceinline__ void apply_body(const Coef<double>& c, const double* 
                                            const double* __restrict__ b, double* __restrict__ y, double* acc) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
-  const int n = c.n, P = c.P;
-  if (i > c.n) return;
+  const int n = c.n, nx = c.nx, P = c.P;
+  if (i > nx) return;
   // a block none of whose points touches a boundary or the interface takes
   // the rows without their boundary cases (the same operations in the same
-  // order for every interior point), so no masked FP64 work is issued
+  // order for every interior point), so no masked FP64 work is issued; in
+  // the channel a block beside the porous medium takes the free-flow rows
+  // alone
   const int bi = blockIdx.x * blockDim.x, bj = blockIdx.y * blockDim.y * R;
-  if (FF == 0 && bi >= 2 && bi + (int)blockDim.x - 1 <= n - 2 && bj >= 1 && bj + (int)blockDim.y * R - 1 <= n - 2) {
+  // (row 1 of the v faces reads the floor face below: in the channel an
+  // interior block starts at row 2)
+  const bool ff_in = bi >= 2 && bi + (int)blockDim.x - 1 <= nx - 2 && bj >= (c.iw ? 2 : 1) &&
+                     bj + (int)blockDim.y * R - 1 <= n - 2;
+  if (FF == 0 && ff_in && bi + (int)blockDim.x - 1 <= n - 2) {
     const long long nv = (long long)n * P, npf = (long long)(2 * n + 1) * P, npm = (long long)(3 * n + 1) * P;
 #pragma unroll
     for (int rr = 0; rr < R; ++rr)
-      apply_cell_interior<RES, PS>(c, x, x + nv, x + npf, x + npm, b, y, (long long)(j0 + rr) * P + i, nv, npf, npm,
-                                   acc);
+      apply_cell_interior<RES, PS, true>(c, x, x + nv, x + npf, x + npm, b, y, (long long)(j0 + rr) * P + i, nv, npf,
+                                         npm, acc);
     return;
   }
-  if (bi >= 2 && bi + (int)blockDim.x - 1 <= n - 2 && bj >= 1 && bj + (int)blockDim.y * R - 1 <= n - 2) {
+  if (FF == 0 && ff_in && bi >= n) {
+    const long long nv = (long long)n * P, npf = (long long)(2 * n + 1) * P, npm = (long long)(3 * n + 1) * P;
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr)
+      apply_cell_interior<RES, PS, false>(c, x, x + nv, x + npf, x + npm, b, y, (long long)(j0 + rr) * P + i, nv,
+                                          npf, npm, acc);
+    return;
+  }
+  if (FF != 0 && ff_in && c.iw == 0) {
     const double h = c.h;
     const double* u = x;
     const double* v = x + (long long)n * P;
@@ -187,9 +202,9 @@ __device__ __forceinline__ void apply_body(const Coef<double>& c, const double* 
     if (j < n) {
       const long long k = (long long)j * P + i;
       double val;
-      if ((i == 0 || i == n) && !c.lat) {
+      if ((i == 0 || i == nx) && !c.lat) {
         val = u[k];
-      } else if (i == 0 || i == n) {
+      } else if (i == 0 || i == nx) {
         double off, dg;
         ub_row(c, u, v, i, j, true, off, dg);
         val = dg * u[k] + off + (i == 0 ? h * pf[k] : -h * pf[k - 1]);
@@ -205,11 +220,11 @@ __device__ __forceinline__ void apply_body(const Coef<double>& c, const double* 
         if (PS == 2) acc[3] = fma(b[k], b[k], acc[3]);
       }
     }
-    if (i < n) {
+    if (i < nx) {
       const long long kv = (long long)j * P + i;
       const long long k = (long long)n * P + kv;
       double val;
-      if (j == n || (FF == 2 && j == 0)) {
+      if (j == n || (j == 0 && (FF == 2 || !on_gamma(c, i)))) {
         val = v[kv];
       } else {
         double off, dg;
@@ -217,7 +232,7 @@ __device__ __forceinline__ void apply_body(const Coef<double>& c, const double* 
         val = dg * v[kv] + off;
         if (j > 0) val += h * (pf[kv] - pf[kv - P]);
         else if (FF) val += h * pf[i];
-        else val += h * pf[i] - h * pm[(long long)(n - 1) * P + i];
+        else val += h * pf[i] - h * pm[(long long)(n - 1) * P + i - c.iw];
       }
       {
         const double r_ = b ? b[k] - val : val;
@@ -226,10 +241,11 @@ __device__ __forceinline__ void apply_body(const Coef<double>& c, const double* 
         if (PS == 2) acc[3] = fma(b[k], b[k], acc[3]);
       }
     }
-    if (i < n && j < n) {
+    if (i < nx && j < n) {
       const long long kc = (long long)j * P + i;
-      double s = -v[kc];
-      if (c.lat || i + 1 <= n - 1) s += u[kc + 1];
+      // a floor face beside the interface is Dirichlet data (not an unknown)
+      double s = (j > 0 || on_gamma(c, i)) ? -v[kc] : 0.0;
+      if (c.lat || i + 1 <= nx - 1) s += u[kc + 1];
       if (c.lat || i >= 1) s -= u[kc];
       if (j + 1 <= n - 1) s += v[kc + P];
       const long long kp = (long long)(2 * n + 1) * P + kc;
@@ -242,11 +258,13 @@ __device__ __forceinline__ void apply_body(const Coef<double>& c, const double* 
           if (PS == 2) acc[3] = fma(b[kp], b[kp], acc[3]);
         }
       }
-      if (FF) continue;
+    }
+    if (!FF && i < n && j < n) {
+      const long long kc = (long long)j * P + i;
       double off, dg;
       d_row(c, pm, i, j, true, off, dg);
       double val = dg * pm[kc] + off;
-      if (j == n - 1) val += h * v[i];
+      if (j == n - 1) val += h * v[c.iw + i];
       const long long km = (long long)(3 * n + 1) * P + kc;
       {
         const double r_ = b ? b[km] - val : val;
@@ -352,7 +370,7 @@ void launch_resid_norms(const Coef<double>& c, const double* x, const double* b,
                         double* sc, int blk, int b2, int bn, int with_b, cudaStream_t s) {
   SD_COUNT(2);
   const int R = rows_apply(c.n);
-  const dim3 g = grid2R(c.n + 1, c.n + 1, R);
+  const dim3 g = grid2R(c.nx + 1, c.n + 1, R);
   if (R == 4) {
     if (with_b) launch_k(k_apply_full<4, 0, true, 2>, g, dim3(BX, BY), 0, s, c, x, b, r, partial);
     else launch_k(k_apply_full<4, 0, true, 1>, g, dim3(BX, BY), 0, s, c, x, b, r, partial);
@@ -365,15 +383,15 @@ void launch_resid_norms(const Coef<double>& c, const double* x, const double* b,
 }
 
 // blocks of the operator's launch (partial sums per quantity of launch_resid_norms)
-long long resid_norms_blocks(int n) {
-  const dim3 g = grid2R(n + 1, n + 1, rows_apply(n));
+long long resid_norms_blocks(int nx, int n) {
+  const dim3 g = grid2R(nx + 1, n + 1, rows_apply(n));
   return (long long)g.x * g.y;
 }
 
 void launch_apply_full(const Coef<double>& c, const double* x, const double* b, double* y, cudaStream_t s) {
   SD_COUNT(1);
   const int R = rows_apply(c.n);
-  const dim3 g = grid2R(c.n + 1, c.n + 1, R);
+  const dim3 g = grid2R(c.nx + 1, c.n + 1, R);
   if (R == 4) {
     if (b) launch_k(k_apply_full<4, 0, true>, g, dim3(BX, BY), 0, s, c, x, b, y, (double*)nullptr);
     else launch_k(k_apply_full<4, 0, false>, g, dim3(BX, BY), 0, s, c, x, b, y, (double*)nullptr);
@@ -386,7 +404,7 @@ void launch_apply_full(const Coef<double>& c, const double* x, const double* b, 
 void launch_apply_ff(const Coef<double>& c, const double* x, const double* b, double* y, int vdir, cudaStream_t s) {
   SD_COUNT(1);
   const int R = rows_apply(c.n);
-  const dim3 g = grid2R(c.n + 1, c.n + 1, R);
+  const dim3 g = grid2R(c.nx + 1, c.n + 1, R);
   if (R == 4) {
     if (vdir) launch_k(k_apply_full<4, 2, false>, g, dim3(BX, BY), 0, s, c, x, b, y, (double*)nullptr);
     else launch_k(k_apply_full<4, 1, false>, g, dim3(BX, BY), 0, s, c, x, b, y, (double*)nullptr);
@@ -498,7 +516,7 @@ void launch_dn_rhs_ff(const Geom& g, const double* b, const double* p, double* b
 
 // ------------------------------------------------------ block V smoothers
 // One Chebyshev step at position (i, j) of the velocity block (u face (i,j)
-// if j < n, v face (i,j) if i < n).  Dirichlet faces take x = b exactly.
+// if j < n, v face (i,j) if i < nx).  Dirichlet faces take x = b exactly.
 template <typename T, bool IN = false>
 __device__ __forceinline__ void cheb_V_at2(const Coef<T>& c, const T* __restrict__ uin, const T* __restrict__ vin,
                                            const T* __restrict__ bu, const T* __restrict__ bv, T* __restrict__ du,
@@ -508,7 +526,7 @@ __device__ __forceinline__ void cheb_V_at2(const Coef<T>& c, const T* __restrict
   const bool rd = uin != nullptr;
   if (IN || j < n) {
     const int k = j * P + i;
-    const bool side = !IN && (i == 0 || i == n);
+    const bool side = !IN && (i == 0 || i == c.nx);
     if (side && !c.lat) {
       uout[k] = bu[k];
       du[k] = T(0);
@@ -524,9 +542,9 @@ __device__ __forceinline__ void cheb_V_at2(const Coef<T>& c, const T* __restrict
       uout[k] = xn;
     }
   }
-  if (IN || i < n) {
+  if (IN || i < c.nx) {
     const int k = j * P + i;
-    if (!IN && j == n) {
+    if (!IN && (j == n || (j == 0 && !on_gamma(c, i)))) {
       vout[k] = bv[k];
       dv[k] = T(0);
     } else {
@@ -568,7 +586,7 @@ __global__ void k_cheb_V(Coef<T> c, const T* __restrict__ xin, const T* __restri
   }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
-  if (i > c.n) return;
+  if (i > c.nx) return;
 #pragma unroll
   for (int rr = 0; rr < R; ++rr) {
     const int j = j0 + rr;
@@ -583,7 +601,7 @@ void launch_cheb_V(const Coef<T>& c, const T* x_in, const T* b, T* d, T* x_out, 
                    long long bstride, cudaStream_t s) {
   SD_COUNT(1);
   const int R = rows_vel(c.n);
-  dim3 g = grid2R(c.n + 1, c.n + 1, R);
+  dim3 g = grid2R(c.nx + 1, c.n + 1, R);
   g.z = nbatch;
   if (R == 4) launch_k(k_cheb_V<T, 4>, dim3(g), dim3(dim3(BX, BY)), 0, s, c, x_in, b, d, x_out, a, cc, ck, bstride);
   else launch_k(k_cheb_V<T, 1>, dim3(g), dim3(dim3(BX, BY)), 0, s, c, x_in, b, d, x_out, a, cc, ck, bstride);
@@ -593,26 +611,26 @@ void launch_cheb_V(const Coef<T>& c, const T* x_in, const T* b, T* d, T* x_out, 
 template <typename T>
 __device__ __forceinline__ void resid_V_at(const Coef<T>& c, const T* __restrict__ x, const T* __restrict__ b,
                                            T* __restrict__ r, int jac, int i, int j) {
-  const int n = c.n, P = c.P;
+  const int n = c.n, nx = c.nx, P = c.P;
   const T* u = x;
   const T* v = x + (long long)n * P;
   if (j < n) {
     const int k = j * P + i;
     T ax, dg = T(1);
-    if ((i == 0 || i == n) && !c.lat) {
+    if ((i == 0 || i == nx) && !c.lat) {
       ax = x[k];
     } else {
       T off;
-      if (i == 0 || i == n) ub_row(c, u, v, i, j, true, off, dg);
+      if (i == 0 || i == nx) ub_row(c, u, v, i, j, true, off, dg);
       else u_row(c, u, v, i, j, true, off, dg);
       ax = dg * x[k] + off;
     }
     r[k] = jac == 1 ? ax / dg : (jac == 2 ? ax : (b ? b[k] - ax : -ax));
   }
-  if (i < n) {
+  if (i < nx) {
     const int k = n * P + j * P + i;
     T ax, dg = T(1);
-    if (j == n) {
+    if (j == n || (j == 0 && !on_gamma(c, i))) {
       ax = x[k];
     } else {
       T off;
@@ -637,7 +655,7 @@ __global__ void k_resid_V(Coef<T> c, const T* __restrict__ x, const T* __restric
   }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
-  if (i > c.n) return;
+  if (i > c.nx) return;
 #pragma unroll
   for (int rr = 0; rr < R; ++rr) {
     const int j = j0 + rr;
@@ -652,7 +670,7 @@ void launch_resid_V(const Coef<T>& c, const T* x, const T* b, T* r, int jac, int
                     cudaStream_t s) {
   SD_COUNT(1);
   const int R = rows_vel(c.n);
-  dim3 g = grid2R(c.n + 1, c.n + 1, R);
+  dim3 g = grid2R(c.nx + 1, c.n + 1, R);
   g.z = nbatch;
   if (R == 4) launch_k(k_resid_V<T, 4>, dim3(g), dim3(dim3(BX, BY)), 0, s, c, x, b, r, jac, bstride);
   else launch_k(k_resid_V<T, 1>, dim3(g), dim3(dim3(BX, BY)), 0, s, c, x, b, r, jac, bstride);
@@ -693,7 +711,7 @@ __global__ void k_cheb_D(Coef<T> c, const T* __restrict__ xin, const T* __restri
   }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
-  if (i >= c.n) return;
+  if (i >= c.cx) return;
 #pragma unroll
   for (int rr = 0; rr < R; ++rr) {
     const int j = j0 + rr;
@@ -708,7 +726,7 @@ void launch_cheb_D(const Coef<T>& c, const T* x_in, const T* b, T* d, T* x_out, 
                    long long bstride, cudaStream_t s) {
   SD_COUNT(1);
   const int R = rows_cell(c.n);
-  dim3 g = grid2R(c.n, c.n, R);
+  dim3 g = grid2R(c.cx, c.n, R);
   g.z = nbatch;
   if (R == 4) launch_k(k_cheb_D<T, 4>, dim3(g), dim3(dim3(BX, BY)), 0, s, c, x_in, b, d, x_out, a, cc, ck, bstride);
   else launch_k(k_cheb_D<T, 1>, dim3(g), dim3(dim3(BX, BY)), 0, s, c, x_in, b, d, x_out, a, cc, ck, bstride);
@@ -738,7 +756,7 @@ __global__ void k_resid_D(Coef<T> c, const T* __restrict__ x, const T* __restric
   }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
-  if (i >= c.n) return;
+  if (i >= c.cx) return;
 #pragma unroll
   for (int rr = 0; rr < R; ++rr) {
     const int j = j0 + rr;
@@ -753,7 +771,7 @@ void launch_resid_D(const Coef<T>& c, const T* x, const T* b, T* r, int jac, int
                     cudaStream_t s) {
   SD_COUNT(1);
   const int R = rows_cell(c.n);
-  dim3 g = grid2R(c.n, c.n, R);
+  dim3 g = grid2R(c.cx, c.n, R);
   g.z = nbatch;
   if (R == 4) launch_k(k_resid_D<T, 4>, dim3(g), dim3(dim3(BX, BY)), 0, s, c, x, b, r, jac, bstride);
   else launch_k(k_resid_D<T, 1>, dim3(g), dim3(dim3(BX, BY)), 0, s, c, x, b, r, jac, bstride);
@@ -762,17 +780,22 @@ void launch_resid_D(const Coef<T>& c, const T* x, const T* b, T* r, int jac, int
 // ------------------------------------------------------------ transfers
 // (prolongation values: sd_rows.cuh)
 // coarse faces (I, J) of the velocity block from the fine residual, its u and
-// v parts at ru, rv (row pitch Pf)
+// v parts at ru, rv (row pitch Pf); the coarse level has nxc free-flow cells
+// across and its interface under floor faces iwc .. iwc + nc - 1 (the
+// transpose of prolong_u_val / prolong_v_val with their ghosts)
 template <typename T>
 __device__ __forceinline__ void restrict_V_at2(const T* __restrict__ ru, const T* __restrict__ rv, int Pf, int nc,
-                                               int Pc, T* __restrict__ bc, int I, int J, int lat) {
+                                               int nxc, int iwc, int Pc, T* __restrict__ bc, int I, int J, int lat) {
   if (J < nc) {
     T s = T(0);
-    if (lat && (I == 0 || I == nc)) {  // traction side face: the one-sided transpose of the prolongation
+    // fine row 0 below coarse row 0: the ghost is +row 0 over the interface
+    // (weights 3/4 + 1/4) and -row 0 over a wall (3/4 - 1/4)
+    const T w00 = (I >= iwc && I <= iwc + nc) ? T(1) : T(0.5);
+    if (lat && (I == 0 || I == nxc)) {  // traction side face: the one-sided transpose of the prolongation
       int rows[4];
       T wy[4];
       rows[0] = 2 * J - 1; wy[0] = J >= 1 ? T(0.25) : T(0);
-      rows[1] = 2 * J;     wy[1] = J == 0 ? T(1) : T(0.75);
+      rows[1] = 2 * J;     wy[1] = J == 0 ? w00 : T(0.75);
       rows[2] = 2 * J + 1; wy[2] = J == nc - 1 ? T(0.5) : T(0.75);
       rows[3] = 2 * J + 2; wy[3] = J <= nc - 2 ? T(0.25) : T(0);
       const int ii = 2 * I, in = I == 0 ? 1 : 2 * I - 1;
@@ -782,11 +805,11 @@ __device__ __forceinline__ void restrict_V_at2(const T* __restrict__ ru, const T
         const T* row = ru + (long long)rows[q] * Pf;
         s += wy[q] * (row[ii] + T(0.5) * row[in]);
       }
-    } else if (I > 0 && I < nc) {
+    } else if (I > 0 && I < nxc) {
       int rows[4];
       T wy[4];
       rows[0] = 2 * J - 1; wy[0] = J >= 1 ? T(0.25) : T(0);
-      rows[1] = 2 * J;     wy[1] = J == 0 ? T(1) : T(0.75);
+      rows[1] = 2 * J;     wy[1] = J == 0 ? w00 : T(0.75);
       rows[2] = 2 * J + 1; wy[2] = J == nc - 1 ? T(0.5) : T(0.75);
       rows[3] = 2 * J + 2; wy[3] = J <= nc - 2 ? T(0.25) : T(0);
 #pragma unroll
@@ -798,23 +821,27 @@ __device__ __forceinline__ void restrict_V_at2(const T* __restrict__ ru, const T
     }
     bc[(long long)J * Pc + I] = s;
   }
-  if (I < nc) {
+  if (I < nxc) {
     T s = T(0);
-    if (J < nc) {
+    // a coarse floor face beside the interface is Dirichlet (right-hand side 0)
+    if (J < nc && !(J == 0 && iwc > 0 && (I < iwc || I >= iwc + nc))) {
       int cols[4];
       T wx[4];
       cols[0] = 2 * I - 1; wx[0] = I >= 1 ? T(0.25) : T(0);
       cols[1] = 2 * I;     wx[1] = I == 0 ? T(0.5) : T(0.75);
-      cols[2] = 2 * I + 1; wx[2] = I == nc - 1 ? T(0.5) : T(0.75);
-      cols[3] = 2 * I + 2; wx[3] = I <= nc - 2 ? T(0.25) : T(0);
+      cols[2] = 2 * I + 1; wx[2] = I == nxc - 1 ? T(0.5) : T(0.75);
+      cols[3] = 2 * I + 2; wx[3] = I <= nxc - 2 ? T(0.25) : T(0);
       const T* r0 = rv + (long long)(2 * J) * Pf;
       const T* r1 = rv + (long long)(2 * J + 1) * Pf;
       const T* rm = J >= 1 ? rv + (long long)(2 * J - 1) * Pf : nullptr;
+      // fine floor faces beside the interface take no prolongation
+      const int f0 = 2 * iwc, f1 = 2 * (iwc + nc);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         if (wx[q] == T(0)) continue;
         const int ci = cols[q];
-        T t = r0[ci] + T(0.5) * r1[ci];
+        const T r00 = (J > 0 || iwc == 0 || (ci >= f0 && ci < f1)) ? r0[ci] : T(0);
+        T t = r00 + T(0.5) * r1[ci];
         if (rm) t += T(0.5) * rm[ci];
         s += wx[q] * t;
       }
@@ -824,14 +851,14 @@ __device__ __forceinline__ void restrict_V_at2(const T* __restrict__ ru, const T
 }
 
 template <typename T>
-__device__ __forceinline__ void restrict_V_at(int nf, int Pf, const T* __restrict__ r, int nc, int Pc,
-                                              T* __restrict__ bc, int I, int J, int lat = 0) {
-  restrict_V_at2(r, r + (long long)nf * Pf, Pf, nc, Pc, bc, I, J, lat);
+__device__ __forceinline__ void restrict_V_at(int nf, int Pf, const T* __restrict__ r, int nc, int nxc, int iwc,
+                                              int Pc, T* __restrict__ bc, int I, int J, int lat = 0) {
+  restrict_V_at2(r, r + (long long)nf * Pf, Pf, nc, nxc, iwc, Pc, bc, I, J, lat);
 }
 
 template <typename T>
-__global__ void k_restrict_V(int nf, int Pf, const T* __restrict__ r, int nc, int Pc, T* __restrict__ bc, int lat,
-                             Bat bt) {
+__global__ void k_restrict_V(int nf, int Pf, const T* __restrict__ r, int nc, int nxc, int iwc, int Pc,
+                             T* __restrict__ bc, int lat, Bat bt) {
   griddep_wait();
   long long o;
   if (!bat_enter(bt, o)) return;
@@ -841,14 +868,15 @@ __global__ void k_restrict_V(int nf, int Pf, const T* __restrict__ r, int nc, in
   }
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
-  if (I > nc || J > nc) return;
-  restrict_V_at(nf, Pf, r, nc, Pc, bc, I, J, lat);
+  if (I > nxc || J > nc) return;
+  restrict_V_at(nf, Pf, r, nc, nxc, iwc, Pc, bc, I, J, lat);
 }
 
 template <typename T>
-void launch_restrict_V(int nf, int Pf, const T* r, int nc, int Pc, T* bc, int lat, cudaStream_t s) {
+void launch_restrict_V(int nf, int Pf, const T* r, int nc, int nxc, int iwc, int Pc, T* bc, int lat, cudaStream_t s) {
   SD_COUNT(1);
-  launch_k(k_restrict_V<T>, dim3(grid2(nc + 1, nc + 1)), dim3(dim3(BX, BY)), 0, s, nf, Pf, r, nc, Pc, bc, lat);
+  launch_k(k_restrict_V<T>, dim3(grid2(nxc + 1, nc + 1)), dim3(dim3(BX, BY)), 0, s, nf, Pf, r, nc, nxc, iwc, Pc, bc,
+           lat);
 }
 
 template <typename T>
@@ -895,7 +923,7 @@ __global__ void k_resid_restrict_D(Coef<T> c, const T* __restrict__ x, const T* 
   }
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
-  if (I >= nc || J >= nc) return;
+  if (I >= c.cx / 2 || J >= nc) return;
   T r[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -911,20 +939,64 @@ __global__ void k_resid_restrict_D(Coef<T> c, const T* __restrict__ x, const T* 
 template <typename T>
 void launch_resid_restrict_D(const Coef<T>& c, const T* x, const T* b, int nc, int Pc, T* bc, cudaStream_t s) {
   SD_COUNT(1);
-  launch_k(k_resid_restrict_D<T>, dim3(grid2(nc, nc)), dim3(dim3(BX, BY)), 0, s, c, x, b, nc, Pc, bc);
+  launch_k(k_resid_restrict_D<T>, dim3(grid2(c.cx / 2, nc)), dim3(dim3(BX, BY)), 0, s, c, x, b, nc, Pc, bc);
 }
 
+// (fine faces: u i = 0 .. 2 nxc, v i < 2 nxc; the Dirichlet faces, the floor
+// faces beside the interface among them, take no increment)
 template <typename T>
-__device__ __forceinline__ void prolong_V_at(int nf, int Pf, T* __restrict__ x, int nc, int Pc,
+__device__ __forceinline__ void prolong_V_at(int nf, int Pf, T* __restrict__ x, int nc, int nxc, int iwc, int Pc,
                                              const T* __restrict__ e, int i, int j, int lat = 0) {
   const T* eu = e;
   const T* ev = e + (long long)nc * Pc;
-  if (j < nf && (lat || (i > 0 && i < nf))) x[(long long)j * Pf + i] += prolong_u_val(eu, nc, Pc, i, j, lat);
-  if (i < nf && j < nf) x[(long long)nf * Pf + (long long)j * Pf + i] += prolong_v_val(ev, nc, Pc, i, j);
+  const int nxf = 2 * nxc;
+  if (j < nf && (lat || (i > 0 && i < nxf)))
+    x[(long long)j * Pf + i] += prolong_u_val(eu, nc, nxc, iwc, Pc, i, j, lat);
+  if (i < nxf && j < nf && !(j == 0 && iwc > 0 && (i < 2 * iwc || i >= 2 * (iwc + nc))))
+    x[(long long)nf * Pf + (long long)j * Pf + i] += prolong_v_val(ev, nc, nxc, iwc, Pc, i, j);
 }
 
 template <typename T, int R>
-__global__ void k_prolong_V(int nf, int Pf, T* __restrict__ x, int nc, int Pc, const T* __restrict__ e, int lat,
+__global__ void k_prolong_V(int nf, int Pf, T* __restrict__ x, int nc, int nxc, int iwc, int Pc,
+                            const T* __restrict__ e, int lat, Bat bt) {
+  griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  if (bt.off) {
+    x = bsh(x, o);
+    e = bsh(e, o);
+  }
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
+  if (i > 2 * nxc) return;
+#pragma unroll
+  for (int rr = 0; rr < R; ++rr) {
+    const int j = j0 + rr;
+    if (j > nf) break;
+    prolong_V_at(nf, Pf, x, nc, nxc, iwc, Pc, e, i, j, lat);
+  }
+}
+
+template <typename T>
+void launch_prolong_V(int nf, int Pf, T* x, int nc, int nxc, int iwc, int Pc, const T* e, int lat, cudaStream_t s) {
+  SD_COUNT(1);
+  const int R = rows_vel(nf);
+  if (R == 4)
+    launch_k(k_prolong_V<T, 4>, dim3(grid2R(2 * nxc + 1, nf + 1, 4)), dim3(dim3(BX, BY)), 0, s, nf, Pf, x, nc, nxc,
+             iwc, Pc, e, lat);
+  else
+    launch_k(k_prolong_V<T, 1>, dim3(grid2R(2 * nxc + 1, nf + 1, 1)), dim3(dim3(BX, BY)), 0, s, nf, Pf, x, nc, nxc,
+             iwc, Pc, e, lat);
+}
+
+template <typename T>
+__device__ __forceinline__ void prolong_D_at(int Pf, T* __restrict__ x, int nc, int ncx, int Pc,
+                                             const T* __restrict__ e, int i, int j) {
+  x[(long long)j * Pf + i] += prolong_D_val(e, nc, ncx, Pc, i, j);
+}
+
+template <typename T, int R>
+__global__ void k_prolong_D(int nf, int xf, int Pf, T* __restrict__ x, int nc, int Pc, const T* __restrict__ e,
                             Bat bt) {
   griddep_wait();
   long long o;
@@ -935,57 +1007,23 @@ __global__ void k_prolong_V(int nf, int Pf, T* __restrict__ x, int nc, int Pc, c
   }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
-  if (i > nf) return;
-#pragma unroll
-  for (int rr = 0; rr < R; ++rr) {
-    const int j = j0 + rr;
-    if (j > nf) break;
-    prolong_V_at(nf, Pf, x, nc, Pc, e, i, j, lat);
-  }
-}
-
-template <typename T>
-void launch_prolong_V(int nf, int Pf, T* x, int nc, int Pc, const T* e, int lat, cudaStream_t s) {
-  SD_COUNT(1);
-  const int R = rows_vel(nf);
-  if (R == 4)
-    launch_k(k_prolong_V<T, 4>, dim3(grid2R(nf + 1, nf + 1, 4)), dim3(dim3(BX, BY)), 0, s, nf, Pf, x, nc, Pc, e, lat);
-  else
-    launch_k(k_prolong_V<T, 1>, dim3(grid2R(nf + 1, nf + 1, 1)), dim3(dim3(BX, BY)), 0, s, nf, Pf, x, nc, Pc, e, lat);
-}
-
-template <typename T>
-__device__ __forceinline__ void prolong_D_at(int Pf, T* __restrict__ x, int nc, int Pc, const T* __restrict__ e,
-                                             int i, int j) {
-  x[(long long)j * Pf + i] += prolong_D_val(e, nc, Pc, i, j);
-}
-
-template <typename T, int R>
-__global__ void k_prolong_D(int nf, int Pf, T* __restrict__ x, int nc, int Pc, const T* __restrict__ e, Bat bt) {
-  griddep_wait();
-  long long o;
-  if (!bat_enter(bt, o)) return;
-  if (bt.off) {
-    x = bsh(x, o);
-    e = bsh(e, o);
-  }
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
-  if (i >= nf) return;
+  if (i >= xf) return;
 #pragma unroll
   for (int rr = 0; rr < R; ++rr) {
     const int j = j0 + rr;
     if (j >= nf) break;
-    prolong_D_at(Pf, x, nc, Pc, e, i, j);
+    prolong_D_at(Pf, x, nc, xf / 2, Pc, e, i, j);
   }
 }
 
 template <typename T>
-void launch_prolong_D(int nf, int Pf, T* x, int nc, int Pc, const T* e, cudaStream_t s) {
+void launch_prolong_D(int nf, int xf, int Pf, T* x, int nc, int Pc, const T* e, cudaStream_t s) {
   SD_COUNT(1);
   const int R = rows_cell(nf);
-  if (R == 4) launch_k(k_prolong_D<T, 4>, dim3(grid2R(nf, nf, 4)), dim3(dim3(BX, BY)), 0, s, nf, Pf, x, nc, Pc, e);
-  else launch_k(k_prolong_D<T, 1>, dim3(grid2R(nf, nf, 1)), dim3(dim3(BX, BY)), 0, s, nf, Pf, x, nc, Pc, e);
+  if (R == 4)
+    launch_k(k_prolong_D<T, 4>, dim3(grid2R(xf, nf, 4)), dim3(dim3(BX, BY)), 0, s, nf, xf, Pf, x, nc, Pc, e);
+  else
+    launch_k(k_prolong_D<T, 1>, dim3(grid2R(xf, nf, 1)), dim3(dim3(BX, BY)), 0, s, nf, xf, Pf, x, nc, Pc, e);
 }
 
 // ------------------------------------------- tiled (temporally blocked) smoothing
@@ -1086,7 +1124,7 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_D(Coef<T> c, const T* __res
   const int ilo = blockIdx.x * TLX - H, jlo = blockIdx.y * TLY - H;
   const int I0 = (ilo >> 1) - 1, J0 = (jlo >> 1) - 1;
   if (xin && ec) {
-    for (int p = threadIdx.x; p < CX * CY; p += TLT) sce[p] = cd_at(ec, nc, Pc, I0 + p % CX, J0 + p / CX);
+    for (int p = threadIdx.x; p < CX * CY; p += TLT) sce[p] = cd_at(ec, nc, nc, Pc, I0 + p % CX, J0 + p / CX);
     __syncthreads();
   }
   for (int p = threadIdx.x; p < SR * SP; p += TLT) {
@@ -1217,8 +1255,8 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_V(Coef<T> c, const T* __res
     // and coarse v rows below 0
     for (int p = threadIdx.x; p < CX * CY; p += TLT) {
       const int I = I0 + p % CX, J = J0 + p / CX;
-      scu[p] = (I >= 0 && I <= nc) ? cu_at(ecu, nc, Pc, I, J, c.lat) : T(0);
-      scv[p] = J >= 0 ? cv_at(ecv, nc, Pc, I, J) : T(0);
+      scu[p] = (I >= 0 && I <= nc) ? cu_at(ecu, nc, nc, 0, Pc, I, J, c.lat) : T(0);
+      scv[p] = J >= 0 ? cv_at(ecv, nc, nc, 0, Pc, I, J) : T(0);
     }
     __syncthreads();
   }
@@ -1329,7 +1367,7 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_V(Coef<T> c, const T* __res
     const int I0 = (ilo + H) / 2, J0 = (jlo + H) / 2;
     for (int p = threadIdx.x; p < (TLX / 2) * (TLY / 2); p += TLT) {
       const int I = I0 + p % (TLX / 2), J = J0 + p / (TLX / 2);
-      if (I <= nc && J <= nc) restrict_V_at2<T>(du, dv, SP, nc, Pc, bco, I, J, c.lat);
+      if (I <= nc && J <= nc) restrict_V_at2<T>(du, dv, SP, nc, nc, 0, Pc, bco, I, J, c.lat);
     }
   }
   for (int p = threadIdx.x; p < TLX * TLY; p += TLT) {
@@ -1511,11 +1549,11 @@ __device__ void cyc_sweep(const CoarseCycle<T>& q, int l, int op, T* X, const T*
       if (q.kind == 0) resid_V_at(c, X, B, D, 0, i, j);
       else resid_D_at(c, X, B, D, 0, i, j);
     } else if (op == 4) {
-      if (q.kind == 0) restrict_V_at(n, c.P, D, nc, q.c[l + 1].P, Bc, i, j, c.lat);
+      if (q.kind == 0) restrict_V_at(n, c.P, D, nc, nc, 0, q.c[l + 1].P, Bc, i, j, c.lat);
       else restrict_D_at(c.P, D, q.c[l + 1].P, Bc, i, j);
     } else {
-      if (q.kind == 0) prolong_V_at(n, c.P, X, nc, q.c[l + 1].P, Xc, i, j, c.lat);
-      else prolong_D_at(c.P, X, nc, q.c[l + 1].P, Xc, i, j);
+      if (q.kind == 0) prolong_V_at(n, c.P, X, nc, nc, 0, q.c[l + 1].P, Xc, i, j, c.lat);
+      else prolong_D_at(c.P, X, nc, nc, q.c[l + 1].P, Xc, i, j);
     }
   }
   __syncthreads();
@@ -1674,7 +1712,7 @@ __global__ void k_precond_entry(Coef<double> c, const double* __restrict__ r, do
   }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int n = c.n, P = c.P;
+  const int n = c.n, nx = c.nx, P = c.P;
   const T h = hT;  // parameters arrive in T: an FP64 conversion per thread would run on the FP64 pipe
   const double* rpf = r + (long long)(2 * n + 1) * P;
   // z_pf at cell kc: schur * r_pf (+ cmass * eP, the pressure-Laplacian part),
@@ -1687,30 +1725,31 @@ __global__ void k_precond_entry(Coef<double> c, const double* __restrict__ r, do
   const int i0 = blockIdx.x * blockDim.x - 1, j0 = blockIdx.y * blockDim.y - 1;
   for (int p = threadIdx.y * blockDim.x + threadIdx.x; p < (BX + 1) * (BY + 1); p += BX * BY) {
     const int ci = i0 + p % (BX + 1), cj = j0 + p / (BX + 1);
-    sz[p / (BX + 1)][p % (BX + 1)] = (ci >= 0 && ci < n && cj >= 0 && cj < n) ? zp((long long)cj * P + ci) : T(0);
+    sz[p / (BX + 1)][p % (BX + 1)] = (ci >= 0 && ci < nx && cj >= 0 && cj < n) ? zp((long long)cj * P + ci) : T(0);
   }
   __syncthreads();
-  if (i > n || j > n) return;
+  if (i > nx || j > n) return;
   const int li = threadIdx.x + 1, lj = threadIdx.y + 1;
   const T zc = sz[lj][li];
-  if (i < n && j < n) z[(long long)(2 * n + 1) * P + (long long)j * P + i] = (double)zc;
+  if (i < nx && j < n) z[(long long)(2 * n + 1) * P + (long long)j * P + i] = (double)zc;
   if (j < n) {
     const long long k = (long long)j * P + i;
     T val = (T)r[k];
-    if (useB && i > 0 && i < n) val -= h * (zc - sz[lj][li - 1]);
+    if (useB && i > 0 && i < nx) val -= h * (zc - sz[lj][li - 1]);
     else if (useB && c.lat) val -= i == 0 ? h * zc : -h * sz[lj][li - 1];  // traction side
     rV[k] = val;
   }
-  if (i < n) {
+  if (i < nx) {
     const long long kv = (long long)j * P + i;
     const long long k = (long long)n * P + kv;
     T val = (T)r[k];
-    if (useB && j < n) {
+    const bool iface = j == 0 && on_gamma(c, i);  // (a floor face beside it is a Dirichlet row)
+    if (useB && j < n && (j > 0 || iface)) {
       if (j > 0) val -= h * (zc - sz[lj - 1][li]);
       else val -= h * zc;
     }
     // Darcy solved first: r_v - B'_1 z_pm on the interface rows (B'_1 = -h)
-    if (useB1 && j == 0) val += h * (T)z[(long long)(3 * n + 1) * P + (long long)(n - 1) * P + i];
+    if (useB1 && iface) val += h * (T)z[(long long)(3 * n + 1) * P + (long long)(n - 1) * P + i - c.iw];
     rV[k] = val;
   }
 }
@@ -1719,7 +1758,7 @@ template <typename T>
 void launch_precond_entry(const Coef<double>& c, const double* r, double* z, double schur, const T* eP, double cmass,
                           int use_B, int use_B1, T* rV, cudaStream_t s) {
   SD_COUNT(1);
-  launch_k(k_precond_entry<T>, dim3(grid2(c.n + 1, c.n + 1)), dim3(dim3(BX, BY)), 0, s, c, r, z, (T)schur, eP,
+  launch_k(k_precond_entry<T>, dim3(grid2(c.nx + 1, c.n + 1)), dim3(dim3(BX, BY)), 0, s, c, r, z, (T)schur, eP,
            (T)cmass, (T)c.h, use_B, use_B1, rV);
 }
 
@@ -1739,19 +1778,19 @@ __global__ void k_precond_mid(Coef<double> c, const double* __restrict__ r, doub
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int n = c.n, P = c.P;
-  if (i > n || j > n) return;
+  if (i > c.nx || j > n) return;
   if (j < n) {
     const long long k = (long long)j * P + i;
     z[k] = (double)eV[k];
   }
-  if (i < n) {
+  if (i < c.nx) {
     const long long k = (long long)n * P + (long long)j * P + i;
     z[k] = (double)eV[k];
   }
   if (rD && i < n && j < n) {
     const long long kc = (long long)j * P + i;
     T val = (T)r[(long long)(3 * n + 1) * P + kc];
-    if (useC && j == n - 1) val -= (T)c.h * eV[(long long)n * P + i];
+    if (useC && j == n - 1) val -= (T)c.h * eV[(long long)n * P + c.iw + i];
     rD[kc] = val;
   }
 }
@@ -1760,7 +1799,7 @@ template <typename T>
 void launch_precond_mid(const Coef<double>& c, const double* r, double* z, const T* eV, int use_C, T* rD,
                         cudaStream_t s) {
   SD_COUNT(1);
-  launch_k(k_precond_mid<T>, dim3(grid2(c.n + 1, c.n + 1)), dim3(dim3(BX, BY)), 0, s, c, r, z, eV, use_C, rD);
+  launch_k(k_precond_mid<T>, dim3(grid2(c.nx + 1, c.n + 1)), dim3(dim3(BX, BY)), 0, s, c, r, z, eV, use_C, rD);
 }
 
 template <typename T>
@@ -1802,12 +1841,12 @@ __global__ void k_precond_bgs_pff(Coef<double> c, const double* __restrict__ r, 
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int n = c.n, P = c.P;
-  if (i >= n || j >= n) return;
+  if (i >= c.nx || j >= n) return;
   const long long kc = (long long)j * P + i;
   const T* u = eV;
   const T* v = eV + (long long)n * P;
-  double s = -(double)v[kc];
-  if (c.lat || i + 1 <= n - 1) s += (double)u[kc + 1];
+  double s = (j > 0 || on_gamma(c, i)) ? -(double)v[kc] : 0.0;
+  if (c.lat || i + 1 <= c.nx - 1) s += (double)u[kc + 1];
   if (c.lat || i >= 1) s -= (double)u[kc];
   if (j + 1 <= n - 1) s += (double)v[kc + P];
   const long long kp = (long long)(2 * n + 1) * P + kc;
@@ -1817,7 +1856,7 @@ __global__ void k_precond_bgs_pff(Coef<double> c, const double* __restrict__ r, 
 template <typename T>
 void launch_precond_bgs_pff(const Coef<double>& c, const double* r, double* z, const T* eV, cudaStream_t s) {
   SD_COUNT(1);
-  launch_k(k_precond_bgs_pff<T>, dim3(grid2(c.n, c.n)), dim3(dim3(BX, BY)), 0, s, c, r, z, eV);
+  launch_k(k_precond_bgs_pff<T>, dim3(grid2(c.nx, c.n)), dim3(dim3(BX, BY)), 0, s, c, r, z, eV);
 }
 
 // ------------------------------------------------------------------ setup
@@ -1833,16 +1872,16 @@ void launch_pack_K(const double* Kdense, int n, double* Kp, int P, cudaStream_t 
   launch_k(k_pack_K, dim3(grid2(n, n)), dim3(dim3(BX, BY)), 0, s, Kdense, n, Kp, P);
 }
 
-__global__ void k_fill_K(double* __restrict__ K, int n, int P, double v) {
+__global__ void k_fill_K(double* __restrict__ K, int cx, int n, int P, double v) {
   griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= n || j >= n) return;
+  if (i >= cx || j >= n) return;
   K[(long long)j * P + i] = v;
 }
-void launch_fill_K(double* K, int n, int P, double v, cudaStream_t s) {
+void launch_fill_K(double* K, int cx, int n, int P, double v, cudaStream_t s) {
   SD_COUNT(1);
-  launch_k(k_fill_K, dim3(grid2(n, n)), dim3(dim3(BX, BY)), 0, s, K, n, P, v);
+  launch_k(k_fill_K, dim3(grid2(cx, n)), dim3(dim3(BX, BY)), 0, s, K, cx, n, P, v);
 }
 
 // coarse permeability: geometric mean of the 2 x 2 children
@@ -1860,58 +1899,67 @@ void launch_coarsen_K(const double* Kf, int nf, int Pf, double* Kc, int Pc, cuda
   launch_k(k_coarsen_K, dim3(grid2(nf / 2, nf / 2)), dim3(dim3(BX, BY)), 0, s, Kf, nf, Pf, Kc, Pc);
 }
 
-// lat: traction free-flow sides (BJS coefficients of their interface corners);
-// xdir: the x boundary faces are Dirichlet over the half cell (2K/mu) instead
-// of no-flow -- the pressure Laplacian of the Schur block with traction sides,
-// where the side u faces, like v_Gamma, have half-volume mass
+// One coefficient set over cx x n cells of K (Tx, Ty) and the interface
+// coefficients of the free-flow floor (w, rg).  lat: traction free-flow sides
+// (BJS coefficients of the square's interface corners); xdir: the x boundary
+// faces are Dirichlet over the half cell (2K/mu) instead of no-flow -- the
+// pressure Laplacian of the Schur block with traction sides, where the side u
+// faces, like v_Gamma, have half-volume mass; [b0, b1): the cells whose
+// bottom face is Dirichlet (2K/mu), the others no-flow.  w over u faces
+// 0..nx and rg over floor faces 0..nx-1 read the top row of K, which lies
+// under floor faces iw .. iw + n - 1 (the channel's interface ends take the
+// one pm cell beside them).
 template <typename T>
-__global__ void k_setup_coef(const double* __restrict__ K, int n, int P, double mu, double alpha, int lat, int xdir,
-                             T* w, T* rg, T* Tx, T* Ty) {
+__global__ void k_setup_coef(const double* __restrict__ K, int n, int cx, int P, double mu, double alpha, int lat,
+                             int xdir, int b0, int b1, int nx, int iw, T* w, T* rg, T* Tx, T* Ty) {
   griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i > n || j > n) return;
+  if (j > n) return;
   const double h = 1.0 / n;
-  if (j < n) {  // x faces of pm row j
+  if (j < n && i <= cx) {  // x faces of row j
     double t = 0.0;
-    if (i > 0 && i < n) {
+    if (i > 0 && i < cx) {
       const double ka = K[(long long)j * P + i - 1], kb = K[(long long)j * P + i];
       t = 2.0 * ka * kb / (ka + kb) / mu;
     } else if (xdir) {
-      t = 2.0 * K[(long long)j * P + (i == 0 ? 0 : n - 1)] / mu;
+      t = 2.0 * K[(long long)j * P + (i == 0 ? 0 : cx - 1)] / mu;
     }
     Tx[(long long)j * P + i] = (T)t;
   }
-  if (i < n) {  // y faces below pm row j
+  if (i < cx) {  // y faces below row j
     double t = 0.0;
-    if (j == 0) t = 2.0 * K[i] / mu;
-    else if (j < n) {
+    if (j == 0) {
+      if (i >= b0 && i < b1) t = 2.0 * K[i] / mu;
+    } else if (j < n) {
       const double ka = K[(long long)(j - 1) * P + i], kb = K[(long long)j * P + i];
       t = 2.0 * ka * kb / (ka + kb) / mu;
     }
     Ty[(long long)j * P + i] = (T)t;
   }
-  if (j == 0) {
+  if (j == 0 && i <= nx) {
     const double* top = K + (long long)(n - 1) * P;
-    if (i > 0 && i < n) {
-      const double beta = 0.5 * (sqrt(top[i - 1]) + sqrt(top[i])) / alpha;
+    const int p = i - iw;
+    if (p > 0 && p < n) {
+      const double beta = 0.5 * (sqrt(top[p - 1]) + sqrt(top[p])) / alpha;
       w[i] = (T)(mu / (h + 2.0 * beta));
-    } else if (lat) {  // traction side's interface corner: the one pm cell below
-      const double beta = sqrt(top[i == 0 ? 0 : n - 1]) / alpha;
+    } else if ((p == 0 || p == n) && (lat || iw > 0)) {  // an end of the interface: the one pm cell below
+      const double beta = sqrt(top[p == 0 ? 0 : n - 1]) / alpha;
       w[i] = (T)(mu / (h + 2.0 * beta));
     } else {
       w[i] = (T)0;
     }
-    if (i < n) rg[i] = (T)(mu * h * h / (2.0 * top[i]));
+    if (i < nx) rg[i] = (p >= 0 && p < n) ? (T)(mu * h * h / (2.0 * top[p])) : (T)0;
   }
 }
 
 template <typename T>
-void launch_setup_coef(const double* Kp, int n, int P, double mu, double alpha, int lat, int xdir, T* w, T* rg, T* Tx,
-                       T* Ty, cudaStream_t s) {
+void launch_setup_coef(const double* Kp, int n, int cx, int P, double mu, double alpha, int lat, int xdir, int b0,
+                       int b1, int nx, int iw, T* w, T* rg, T* Tx, T* Ty, cudaStream_t s) {
   SD_COUNT(1);
-  launch_k(k_setup_coef<T>, dim3(grid2(n + 1, n + 1)), dim3(dim3(BX, BY)), 0, s, Kp, n, P, mu, alpha, lat, xdir, w,
-           rg, Tx, Ty);
+  const int wx = (cx > nx ? cx : nx) + 1;
+  launch_k(k_setup_coef<T>, dim3(grid2(wx, n + 1)), dim3(dim3(BX, BY)), 0, s, Kp, n, cx, P, mu, alpha, lat, xdir, b0,
+           b1, nx, iw, w, rg, Tx, Ty);
 }
 
 template <typename T>
@@ -2058,60 +2106,175 @@ __global__ void k_mms_terms(Coef<double> c, int bc, const double* __restrict__ K
   }
 }
 
-void launch_mms_terms(const Coef<double>& c, int bc, const double* Kp, double* B0, double* B1, cudaStream_t s) {
-  SD_COUNT(1);
-  launch_k(k_mms_terms, dim3(grid2(c.n + 1, c.n + 1)), dim3(dim3(BX, BY)), 0, s, c, bc, Kp, B0, B1);
-}
-
-__global__ void k_mms_exact(int n, int P, double mu, double t, double* __restrict__ x) {
+// The same terms for the channel (free flow x in [-1, 2], c.nx = 3n cells
+// across, the interface under floor faces c.iw .. c.iw + n - 1): the
+// manufactured solution is the same expression continued in x.  What the
+// floor beside the interface adds: its v faces are Dirichlet rows (value v at
+// y = 1); the u faces above it see the wall at half distance (u and the
+// tangential derivative of v there are data); at the two ends of the
+// interface the wall face beside the eliminated slip, and beside the half
+// control volume of v_Gamma, enters as data; the v faces of row 1 and the
+// continuity rows of row 0 above the wall take the wall face's value.  The
+// traction ends x = -1, 2 meet the floor wall at half distance.
+__global__ void k_mms_terms_ch(Coef<double> c, int bc, const double* __restrict__ K, double* __restrict__ B0,
+                               double* __restrict__ B1) {
   griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i > n || j > n) return;
-  const double h = 1.0 / n, s = 1.0 + t;
-  if (j < n) x[(long long)j * P + i] = s * mm_U0(i * h, 1.0 + (j + 0.5) * h);
-  if (i < n) x[(long long)n * P + (long long)j * P + i] = s * mm_V0((i + 0.5) * h, 1.0 + j * h);
-  if (i < n && j < n) {
-    const long long kc = (long long)j * P + i;
-    x[(long long)(2 * n + 1) * P + kc] = s * mm_Pff0((i + 0.5) * h, mu);
-    x[(long long)(3 * n + 1) * P + kc] = s * mm_Ppm0((i + 0.5) * h, (j + 0.5) * h);
+  const int n = c.n, nx = c.nx, iw = c.iw, P = c.P;
+  if (i > nx || j > n) return;
+  const double h = c.h, mu = c.mu, h2 = h * h;
+  const double xl = -1.0, xr = 2.0;
+  const bool lat = bc != 0, mms = bc != 2;
+  if (j < n) {  // u face (i, j)
+    const long long k = (long long)j * P + i;
+    const double x = (i - iw) * h, y = 1.0 + (j + 0.5) * h;
+    double b0 = 0.0, b1 = 0.0;
+    if ((i == 0 || i == nx) && !lat) {
+      b1 = mm_U0(x, y);
+    } else if (i == 0 || i == nx) {  // traction end, half control volume
+      const double sg = i == 0 ? 1.0 : -1.0;
+      if (mms) {
+        b0 = 0.5 * h2 * mm_U0(x, y);
+        b1 = 0.5 * h2 * mm_f1x(x, y, mu) + sg * h * mm_Pside(x, y, mu);
+        if (j < n - 1) b1 -= sg * mu * mm_V0(x, 1.0 + (j + 1) * h);
+        else b1 += mu * mm_U0(x, 2.0) + sg * mu * (mm_V0(x + sg * 0.5 * h, 2.0) - mm_V0(x, 2.0));
+        if (j > 0) b1 += sg * mu * mm_V0(x, 1.0 + j * h);
+        else b1 += mu * mm_U0(x, 1.0) - sg * mu * (mm_V0(x + sg * 0.5 * h, 1.0) - mm_V0(x, 1.0));
+      } else if (i == 0) {
+        b1 = h;  // inflow traction p_in(t) enters as s1
+      }
+    } else if (mms) {
+      b0 = h2 * mm_U0(x, y);
+      b1 = h2 * mm_f1x(x, y, mu);
+      if (i == 1 && !lat) b1 += 2.0 * mu * mm_U0(xl, y);
+      if (i == nx - 1 && !lat) b1 += 2.0 * mu * mm_U0(xr, y);
+      if (j == n - 1) b1 += 2.0 * mu * mm_U0(x, 2.0) + mu * (mm_V0(x + 0.5 * h, 2.0) - mm_V0(x - 0.5 * h, 2.0));
+      if (j == 0) {
+        if (i >= iw && i <= iw + n) {
+          const double wh = c.w[i] * h;
+          if (!on_gamma(c, i)) b1 -= wh * mm_V0(x + 0.5 * h, 1.0);
+          if (!on_gamma(c, i - 1)) b1 += wh * mm_V0(x - 0.5 * h, 1.0);
+        } else {
+          b1 += 2.0 * mu * mm_U0(x, 1.0) - mu * (mm_V0(x + 0.5 * h, 1.0) - mm_V0(x - 0.5 * h, 1.0));
+        }
+      }
+    }
+    B0[k] = b0;
+    B1[k] = b1;
   }
+  if (i < nx) {  // v face (i, j)
+    const long long k = (long long)n * P + (long long)j * P + i;
+    const double x = (i - iw + 0.5) * h, y = 1.0 + j * h;
+    double b0 = 0.0, b1 = 0.0;
+    if (!mms) {
+    } else if (j == n) {
+      b1 = mm_V0(x, 2.0);
+    } else if (j == 0 && !on_gamma(c, i)) {
+      b1 = mm_V0(x, 1.0);
+    } else if (j == 0) {
+      b0 = 0.5 * h2 * mm_V0(x, 1.0);
+      b1 = 0.5 * h2 * mm_f1y(x, 1.0, mu);
+      if (!on_gamma(c, i - 1)) b1 += 0.5 * h * c.w[i] * mm_V0(x - h, 1.0);
+      if (!on_gamma(c, i + 1)) b1 += 0.5 * h * c.w[i + 1] * mm_V0(x + h, 1.0);
+    } else {
+      b0 = h2 * mm_V0(x, y);
+      b1 = h2 * mm_f1y(x, y, mu);
+      if (j == n - 1) b1 += 2.0 * mu * mm_V0(x, 2.0);
+      if (j == 1 && !on_gamma(c, i)) b1 += 2.0 * mu * mm_V0(x, 1.0);
+      if (i == 0) {
+        if (lat) b1 += 2.0 * mu * mm_V0(xl, y);
+        else b1 += 2.0 * mu * mm_V0(xl, y) - mu * (mm_U0(xl, y + 0.5 * h) - mm_U0(xl, y - 0.5 * h));
+      }
+      if (i == nx - 1) {
+        if (lat) b1 += 2.0 * mu * mm_V0(xr, y);
+        else b1 += 2.0 * mu * mm_V0(xr, y) + mu * (mm_U0(xr, y + 0.5 * h) - mm_U0(xr, y - 0.5 * h));
+      }
+    }
+    B0[k] = b0;
+    B1[k] = b1;
+  }
+  if (i < nx && j < n) {  // continuity
+    const long long kc = (long long)j * P + i;
+    const double y = 1.0 + (j + 0.5) * h, x = (i - iw + 0.5) * h;
+    double s = 0.0;
+    if (mms) {
+      if (i == 0 && !lat) s += h * mm_U0(xl, y);
+      if (i == nx - 1 && !lat) s -= h * mm_U0(xr, y);
+      if (j == n - 1) s -= h * mm_V0(x, 2.0);
+      if (j == 0 && !on_gamma(c, i)) s += h * mm_V0(x, 1.0);
+    }
+    B0[(long long)(2 * n + 1) * P + kc] = 0.0;
+    B1[(long long)(2 * n + 1) * P + kc] = s;
+  }
+  if (i < n && j < n) {  // Darcy
+    const long long kc = (long long)j * P + i;
+    double sp = 0.0;
+    if (j == 0 && mms) sp = 2.0 * K[i] / mu * mm_Ppm0((i + 0.5) * h, 0.0);
+    B0[(long long)(3 * n + 1) * P + kc] = 0.0;
+    B1[(long long)(3 * n + 1) * P + kc] = sp;
+  }
+}
+
+void launch_mms_terms(const Coef<double>& c, int bc, const double* Kp, double* B0, double* B1, cudaStream_t s) {
+  SD_COUNT(1);
+  if (c.iw > 0)
+    launch_k(k_mms_terms_ch, dim3(grid2(c.nx + 1, c.n + 1)), dim3(dim3(BX, BY)), 0, s, c, bc, Kp, B0, B1);
+  else
+    launch_k(k_mms_terms, dim3(grid2(c.n + 1, c.n + 1)), dim3(dim3(BX, BY)), 0, s, c, bc, Kp, B0, B1);
+}
+
+// the manufactured state; free-flow x of u face i is (i - iw) h
+__global__ void k_mms_exact(int n, int nx, int iw, int P, double mu, double t, double* __restrict__ x) {
+  griddep_wait();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > nx || j > n) return;
+  const double h = 1.0 / n, s = 1.0 + t;
+  if (j < n) x[(long long)j * P + i] = s * mm_U0((i - iw) * h, 1.0 + (j + 0.5) * h);
+  if (i < nx) x[(long long)n * P + (long long)j * P + i] = s * mm_V0((i - iw + 0.5) * h, 1.0 + j * h);
+  if (i < nx && j < n) x[(long long)(2 * n + 1) * P + (long long)j * P + i] = s * mm_Pff0((i - iw + 0.5) * h, mu);
+  if (i < n && j < n) x[(long long)(3 * n + 1) * P + (long long)j * P + i] = s * mm_Ppm0((i + 0.5) * h, (j + 0.5) * h);
 }
 
 void launch_mms_exact(const Geom& g, double mu, double t, double* x, cudaStream_t s) {
   SD_COUNT(1);
-  launch_k(k_mms_exact, dim3(grid2(g.n + 1, g.n + 1)), dim3(dim3(BX, BY)), 0, s, g.n, g.P, mu, t, x);
+  launch_k(k_mms_exact, dim3(grid2(g.nx + 1, g.n + 1)), dim3(dim3(BX, BY)), 0, s, g.n, g.nx, g.iw, g.P, mu, t, x);
 }
 
 // b = mass * xprev + B0 + s1 * B1 (mass = h^2/dt on velocity rows, half on
 // v_Gamma and on traction-side u faces, 0 elsewhere); Dirichlet rows of x
 // take their new values.
-__global__ void k_rhs(int n, int P, int lat, double cm, const double* __restrict__ B0, const double* __restrict__ B1,
-                      double s1, const double* __restrict__ xprev, double* __restrict__ b, double* __restrict__ x) {
+__global__ void k_rhs(int n, int nx, int iw, int P, int lat, double cm, const double* __restrict__ B0,
+                      const double* __restrict__ B1, double s1, const double* __restrict__ xprev,
+                      double* __restrict__ b, double* __restrict__ x) {
   griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i > n || j > n) return;
+  if (i > nx || j > n) return;
   if (j < n) {
     const long long k = (long long)j * P + i;
-    const bool side = (i == 0 || i == n), dir = side && !lat;
+    const bool side = (i == 0 || i == nx), dir = side && !lat;
     const double m = dir ? 0.0 : (side ? 0.5 * cm : cm);
     const double val = m * xprev[k] + B0[k] + s1 * B1[k];
     b[k] = val;
     if (dir) x[k] = val;
   }
-  if (i < n) {
+  if (i < nx) {
     const long long k = (long long)n * P + (long long)j * P + i;
-    const bool dir = (j == n);
+    // the lid and, in the channel, the floor beside the interface are Dirichlet
+    const bool dir = (j == n) || (j == 0 && (i < iw || i >= iw + n));
     const double m = dir ? 0.0 : (j == 0 ? 0.5 * cm : cm);
     const double val = m * xprev[k] + B0[k] + s1 * B1[k];
     b[k] = val;
     if (dir) x[k] = val;
   }
-  if (i < n && j < n) {
-    const long long kc = (long long)j * P + i;
-    const long long kp = (long long)(2 * n + 1) * P + kc, km = (long long)(3 * n + 1) * P + kc;
+  if (i < nx && j < n) {
+    const long long kp = (long long)(2 * n + 1) * P + (long long)j * P + i;
     b[kp] = B0[kp] + s1 * B1[kp];
+  }
+  if (i < n && j < n) {
+    const long long km = (long long)(3 * n + 1) * P + (long long)j * P + i;
     b[km] = B0[km] + s1 * B1[km];
   }
 }
@@ -2119,23 +2282,26 @@ __global__ void k_rhs(int n, int P, int lat, double cm, const double* __restrict
 void launch_rhs(const Geom& g, int lat, double cm, const double* B0, const double* B1, double s1,
                 const double* xprev, double* b, double* x, cudaStream_t s) {
   SD_COUNT(1);
-  launch_k(k_rhs, dim3(grid2(g.n + 1, g.n + 1)), dim3(dim3(BX, BY)), 0, s, g.n, g.P, lat, cm, B0, B1, s1, xprev, b,
-           x);
+  launch_k(k_rhs, dim3(grid2(g.nx + 1, g.n + 1)), dim3(dim3(BX, BY)), 0, s, g.n, g.nx, g.iw, g.P, lat, cm, B0, B1,
+           s1, xprev, b, x);
 }
 
 // ------------------------------------------------------------ pack/unpack
-__global__ void k_pack2(int n, int P, const double* __restrict__ src, double* __restrict__ dst, int to_padded) {
+// canonical dense layout: u (nx+1) x n, v nx x (n+1), p_ff nx x n, p_pm n x n,
+// x fastest (nx = n in the square geometry)
+__global__ void k_pack2(int n, int nx, int P, const double* __restrict__ src, double* __restrict__ dst,
+                        int to_padded) {
   griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i > n || j > n) return;
-  const long long nu = (long long)n * (n + 1), nn = (long long)n * n;
+  if (i > nx || j > n) return;
+  const long long nu = (long long)n * (nx + 1), nv = (long long)nx * (n + 1), npf = (long long)nx * n;
   long long kd[4], kp[4];
   bool ok[4];
-  ok[0] = j < n;          kd[0] = (long long)j * (n + 1) + i;              kp[0] = (long long)j * P + i;
-  ok[1] = i < n;          kd[1] = nu + (long long)j * n + i;               kp[1] = (long long)n * P + (long long)j * P + i;
-  ok[2] = i < n && j < n; kd[2] = 2 * nu + (long long)j * n + i;           kp[2] = (long long)(2 * n + 1) * P + (long long)j * P + i;
-  ok[3] = ok[2];          kd[3] = 2 * nu + nn + (long long)j * n + i;      kp[3] = (long long)(3 * n + 1) * P + (long long)j * P + i;
+  ok[0] = j < n;           kd[0] = (long long)j * (nx + 1) + i;           kp[0] = (long long)j * P + i;
+  ok[1] = i < nx;          kd[1] = nu + (long long)j * nx + i;            kp[1] = (long long)n * P + (long long)j * P + i;
+  ok[2] = i < nx && j < n; kd[2] = nu + nv + (long long)j * nx + i;       kp[2] = (long long)(2 * n + 1) * P + (long long)j * P + i;
+  ok[3] = i < n && j < n;  kd[3] = nu + nv + npf + (long long)j * n + i;  kp[3] = (long long)(3 * n + 1) * P + (long long)j * P + i;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     if (!ok[q]) continue;
@@ -2146,26 +2312,26 @@ __global__ void k_pack2(int n, int P, const double* __restrict__ src, double* __
 
 void launch_pack(const Geom& g, const double* dense, double* padded, cudaStream_t s) {
   SD_COUNT(1);
-  launch_k(k_pack2, dim3(grid2(g.n + 1, g.n + 1)), dim3(dim3(BX, BY)), 0, s, g.n, g.P, dense, padded, 1);
+  launch_k(k_pack2, dim3(grid2(g.nx + 1, g.n + 1)), dim3(dim3(BX, BY)), 0, s, g.n, g.nx, g.P, dense, padded, 1);
 }
 void launch_unpack(const Geom& g, const double* padded, double* dense, cudaStream_t s) {
   SD_COUNT(1);
-  launch_k(k_pack2, dim3(grid2(g.n + 1, g.n + 1)), dim3(dim3(BX, BY)), 0, s, g.n, g.P, padded, dense, 0);
+  launch_k(k_pack2, dim3(grid2(g.nx + 1, g.n + 1)), dim3(dim3(BX, BY)), 0, s, g.n, g.nx, g.P, padded, dense, 0);
 }
 
 // ------------------------------------------------------- instantiations
 #define SD_INST(T)                                                                                               \
-  template void launch_setup_coef<T>(const double*, int, int, double, double, int, int, T*, T*, T*, T*,          \
-                                     cudaStream_t);                                                                \
+  template void launch_setup_coef<T>(const double*, int, int, int, double, double, int, int, int, int, int, int, \
+                                     T*, T*, T*, T*, cudaStream_t);                                                \
   template void launch_convert<T>(const double*, T*, long long, cudaStream_t);                                   \
   template void launch_cheb_V<T>(const Coef<T>&, const T*, const T*, T*, T*, T, T, const T*, int, long long, cudaStream_t); \
   template void launch_cheb_D<T>(const Coef<T>&, const T*, const T*, T*, T*, T, T, const T*, int, long long, cudaStream_t); \
   template void launch_resid_V<T>(const Coef<T>&, const T*, const T*, T*, int, int, long long, cudaStream_t);    \
   template void launch_resid_D<T>(const Coef<T>&, const T*, const T*, T*, int, int, long long, cudaStream_t);    \
-  template void launch_restrict_V<T>(int, int, const T*, int, int, T*, int, cudaStream_t);       \
+  template void launch_restrict_V<T>(int, int, const T*, int, int, int, int, T*, int, cudaStream_t);             \
   template void launch_restrict_D<T>(int, int, const T*, int, int, T*, cudaStream_t);            \
-  template void launch_prolong_V<T>(int, int, T*, int, int, const T*, int, cudaStream_t);                         \
-  template void launch_prolong_D<T>(int, int, T*, int, int, const T*, cudaStream_t);                              \
+  template void launch_prolong_V<T>(int, int, T*, int, int, int, int, const T*, int, cudaStream_t);               \
+  template void launch_prolong_D<T>(int, int, int, T*, int, int, const T*, cudaStream_t);                         \
   template void launch_resid_restrict_D<T>(const Coef<T>&, const T*, const T*, int, int, T*, cudaStream_t);                              \
   template void launch_precond_entry<T>(const Coef<double>&, const double*, double*, double, const T*, double, int, int, T*, cudaStream_t); \
   template void launch_precond_mid<T>(const Coef<double>&, const double*, double*, const T*, int, T*, cudaStream_t); \

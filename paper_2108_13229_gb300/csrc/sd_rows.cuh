@@ -30,25 +30,35 @@ __device__ __forceinline__ double sdiv(double a, double b) { return a / b; }
 // vN = v(i,j+1), vNW = v(i-1,j+1), vS = v(i,j), vSW = v(i-1,j).
 // IN: the caller guarantees 2 <= i <= n-2 and 1 <= j <= n-2 (no boundary term
 // applies); the same operations in the same order, without the masks.
+// floor face i (v face of row 0) lies on the interface
+template <typename T>
+__device__ __forceinline__ bool on_gamma(const Coef<T>& c, int i) {
+  return i >= c.iw && i < c.iw + c.n;
+}
+
 template <typename T, bool IN = false>
 __device__ __forceinline__ void u_row_vals(const Coef<T>& c, int i, int j, bool read, T uW, T uE, T uN, T uS, T vN,
                                            T vNW, T vS, T vSW, T& off, T& diag) {
-  const int n = c.n;
+  const int n = c.n, nx = c.nx;
   const T mu = c.mu;
   const bool top = !IN && j == n - 1, bot = !IN && j == 0;
+  // the floor below: Gamma (BJS slip) over faces iw .. iw + n, else the wall
+  const bool slip = bot && i >= c.iw && i <= c.iw + n;
   T dg = c.d6;  // interior: h^2/dt + 4 mu (normal stress) + mu + mu (shear)
   T wh = T(0);
   if (top) dg += mu;  // wall at half distance above: 2 mu instead of mu
-  if (bot) {          // Gamma below: BJS shear instead of mu
+  if (slip) {         // Gamma below: BJS shear instead of mu
     wh = c.w[i] * c.h;
     dg += T(2) * wh - mu;
+  } else if (bot) {   // channel floor beside Gamma at half distance
+    dg += mu;
   }
   diag = dg;
   if (!read) {
     off = T(0);
     return;
   }
-  const T cW = (IN || c.lat || i - 1 >= 1) ? c.m2 : T(0), cE = (IN || c.lat || i + 1 <= n - 1) ? c.m2 : T(0);
+  const T cW = (IN || c.lat || i - 1 >= 1) ? c.m2 : T(0), cE = (IN || c.lat || i + 1 <= nx - 1) ? c.m2 : T(0);
   T of = cW * uW;
   of = fma(cE, uE, of);
   if (!top) {
@@ -60,8 +70,9 @@ __device__ __forceinline__ void u_row_vals(const Coef<T>& c, int i, int j, bool 
     of = fma(c.m1, uS, of);
     of = fma(mu, vS, of);
     of = fma(c.m1, vSW, of);
-  } else {
-    of = fma(wh, vS - vSW, of);
+  } else if (slip) {
+    // a floor face beside Gamma (at the interface's ends) is data
+    of = fma(wh, (on_gamma(c, i) ? vS : T(0)) - (on_gamma(c, i - 1) ? vSW : T(0)), of);
   }
   off = of;
 }
@@ -95,13 +106,15 @@ __device__ __forceinline__ void u_row(const Coef<T>& c, const T* __restrict__ u,
 template <typename T, bool IN = false>
 __device__ __forceinline__ void v_row_vals(const Coef<T>& c, int i, int j, bool read, T vS, T vN, T vE, T vW, T uE,
                                            T uES, T uW, T uWS, T& off, T& diag) {
-  const int n = c.n;
+  const int n = c.n, nx = c.nx;
   const T mu = c.mu, h = c.h;
-  const bool left = !IN && i == 0, right = !IN && i == n - 1;
-  if (!IN && j == 0) {
+  const bool left = !IN && i == 0, right = !IN && i == nx - 1;
+  if (!IN && j == 0) {  // v_Gamma (the caller takes a floor face beside Gamma as Dirichlet)
     // corners: BJS (interior, or a traction side's corner at half distance)
-    // or a Dirichlet side at half distance
+    // or a Dirichlet side at half distance; at an end of Gamma inside the
+    // channel the floor face beside it is data
     const T wl = (left && !c.lat) ? T(0) : c.w[i], wr = (right && !c.lat) ? T(0) : c.w[i + 1];
+    const bool gl = on_gamma(c, i - 1), gr = on_gamma(c, i + 1);
     T dg = T(0.5) * c.cm + T(2) * mu + c.rg[i];
     dg += left ? (c.lat ? h * wl : mu) : T(0.5) * h * wl;
     dg += right ? (c.lat ? h * wr : mu) : T(0.5) * h * wr;
@@ -113,13 +126,13 @@ __device__ __forceinline__ void v_row_vals(const Coef<T>& c, int i, int j, bool 
     T of = c.m2 * vN;
     if (!left) {
       of = fma(wl * h, uW, of);
-      of = fma(T(-0.5) * h * wl, vW, of);
+      if (gl) of = fma(T(-0.5) * h * wl, vW, of);
     } else if (c.lat) {
       of = fma(wl * h, uW, of);
     }
     if (!right) {
       of = fma(-wr * h, uE, of);
-      of = fma(T(-0.5) * h * wr, vE, of);
+      if (gr) of = fma(T(-0.5) * h * wr, vE, of);
     } else if (c.lat) {
       of = fma(-wr * h, uE, of);
     }
@@ -135,7 +148,9 @@ __device__ __forceinline__ void v_row_vals(const Coef<T>& c, int i, int j, bool 
     return;
   }
   const T cN = (IN || j + 1 <= n - 1) ? c.m2 : T(0);
-  T of = c.m2 * vS;
+  // the face below is a floor face beside Gamma (data) only in row 1
+  const T cS = (IN || j > 1 || on_gamma(c, i)) ? c.m2 : T(0);
+  T of = cS * vS;
   of = fma(cN, vN, of);
   if (!right) {
     of = fma(c.m1, vE, of);
@@ -159,8 +174,8 @@ __device__ __forceinline__ void v_row_vals(const Coef<T>& c, int i, int j, bool 
 template <typename T, bool IN = false>
 __device__ __forceinline__ void v_row(const Coef<T>& c, const T* __restrict__ u, const T* __restrict__ v, int i,
                                       int j, bool read, T& off, T& diag) {
-  const int n = c.n, P = c.P;
-  const bool left = !IN && i == 0, right = !IN && i == n - 1;
+  const int P = c.P;
+  const bool left = !IN && i == 0, right = !IN && i == c.nx - 1;
   T vS = T(0), vN = T(0), vE = T(0), vW = T(0), uE = T(0), uES = T(0), uW = T(0), uWS = T(0);
   if (read) {
     if (!IN && j == 0) {
@@ -199,11 +214,14 @@ __device__ __forceinline__ void ub_row_vals(const Coef<T>& c, int i, int j, bool
                                             T vSc, T& off, T& diag) {
   const int n = c.n;
   const T mu = c.mu;
-  const bool rt = i == n, top = j == n - 1, bot = j == 0;
-  const T wh = bot ? c.w[i] * c.h : T(0);
+  const bool rt = i == c.nx, top = j == n - 1, bot = j == 0;
+  // the side's floor corner: on Gamma (square geometry) the eliminated BJS
+  // slip, in the channel the wall at half distance
+  const bool slip = bot && i >= c.iw && i <= c.iw + n;
+  const T wh = slip ? c.w[i] * c.h : T(0);
   T dg = T(0.5) * c.cm + T(2) * mu;
   dg += top ? mu : T(0.5) * mu;
-  dg += bot ? wh : T(0.5) * mu;
+  dg += slip ? wh : (bot ? mu : T(0.5) * mu);
   diag = dg;
   if (!read) {
     off = T(0);
@@ -218,7 +236,7 @@ __device__ __forceinline__ void ub_row_vals(const Coef<T>& c, int i, int j, bool
   if (!bot) {
     of = fma(T(-0.5) * mu, uS, of);
     of = fma(sg * mu, vSc, of);
-  } else {
+  } else if (slip) {
     of = fma(sg * wh, vSc, of);
   }
   off = of;
@@ -227,12 +245,12 @@ __device__ __forceinline__ void ub_row_vals(const Coef<T>& c, int i, int j, bool
 template <typename T>
 __device__ __forceinline__ void ub_row(const Coef<T>& c, const T* __restrict__ u, const T* __restrict__ v, int i,
                                        int j, bool read, T& off, T& diag) {
-  const int n = c.n, P = c.P;
-  const bool rt = i == n, top = j == n - 1, bot = j == 0;
+  const int n = c.n, nx = c.nx, P = c.P;
+  const bool rt = i == nx, top = j == n - 1, bot = j == 0;
   T uI = T(0), uN = T(0), uS = T(0), vNc = T(0), vSc = T(0);
   if (read) {
     const int r0 = j * P;
-    const int ii = rt ? n - 1 : 1, ic = rt ? n - 1 : 0;
+    const int ii = rt ? nx - 1 : 1, ic = rt ? nx - 1 : 0;
     uI = u[r0 + ii];
     if (!top) {
       uN = u[r0 + P + i];
@@ -244,9 +262,10 @@ __device__ __forceinline__ void ub_row(const Coef<T>& c, const T* __restrict__ u
   ub_row_vals<T>(c, i, j, read, uI, uN, uS, vNc, vSc, off, diag);
 }
 
-// Darcy row of pm cell (i, j) (D' block only, no interface flux) from the
-// transmissibilities of its faces (tw, te, ts, tn) and the neighbour values.
-// IN: 1 <= i <= n-2 and 1 <= j <= n-2.
+// Row of cell (i, j) of a cell block (Darcy D' without the interface flux,
+// or the pressure Laplacian), 0 <= i < c.cx, from the transmissibilities of
+// its faces (tw, te, ts, tn) and the neighbour values.
+// IN: 1 <= i <= cx-2 and 1 <= j <= n-2.
 template <typename T, bool IN = false>
 __device__ __forceinline__ void d_row_vals(const Coef<T>& c, int i, int j, bool read, T tw, T te, T ts, T tn, T pW,
                                            T pE, T pS, T pN, T& off, T& diag) {
@@ -256,7 +275,7 @@ __device__ __forceinline__ void d_row_vals(const Coef<T>& c, int i, int j, bool 
     off = T(0);
     return;
   }
-  const T cW = (IN || i > 0) ? tw : T(0), cE = (IN || i < n - 1) ? te : T(0);
+  const T cW = (IN || i > 0) ? tw : T(0), cE = (IN || i < c.cx - 1) ? te : T(0);
   const T cS = (IN || j > 0) ? ts : T(0), cN = (IN || j < n - 1) ? tn : T(0);
   T of = cW * pW;
   of = fma(cE, pE, of);
@@ -275,7 +294,7 @@ __device__ __forceinline__ void d_row(const Coef<T>& c, const T* __restrict__ p,
   T pW = T(0), pE = T(0), pS = T(0), pN = T(0);
   if (read) {
     pW = p[r0 + ((IN || i > 0) ? i - 1 : i)];
-    pE = p[r0 + ((IN || i < n - 1) ? i + 1 : i)];
+    pE = p[r0 + ((IN || i < c.cx - 1) ? i + 1 : i)];
     pS = p[((IN || j > 0) ? r0 - P : r0) + i];
     pN = p[((IN || j < n - 1) ? r0 + P : r0) + i];
   }
@@ -299,73 +318,85 @@ __device__ __forceinline__ void cheb_point(T bk, T xc, T off, T dg, T ad, T cc, 
 //  v: linear in y between coarse faces (the Dirichlet top carries 0),
 //     cell-centred in x with weights 3/4, 1/4 and negative ghosts at the walls.
 // Restriction is its transpose applied to the fine residual.
+// The coarse level has nc rows, nxc free-flow cells across and its interface
+// under floor faces iwc .. iwc + nc - 1 (square geometry: nxc = nc, iwc = 0).
+// In the channel the floor beside the interface is a wall: there the u ghost
+// below row 0 is the negative of row 0 (as at the lid) and the floor v faces,
+// Dirichlet, carry 0.
 template <typename T>
-__device__ __forceinline__ T cu_at(const T* eu, int nc, int Pc, int I, int J, int lat) {
+__device__ __forceinline__ T cu_at(const T* eu, int nc, int nxc, int iwc, int Pc, int I, int J, int lat) {
   // coarse u with zero Dirichlet faces (traction sides: the side faces' own
   // values) and the y ghosts described above
-  if (!lat && (I <= 0 || I >= nc)) return T(0);
-  if (J < 0) J = 0;
+  if (!lat && (I <= 0 || I >= nxc)) return T(0);
+  if (J < 0) {
+    const T e0 = eu[I];
+    return (I >= iwc && I <= iwc + nc) ? e0 : -e0;
+  }
   if (J > nc - 1) return -eu[(long long)(nc - 1) * Pc + I];
   return eu[(long long)J * Pc + I];
 }
 template <typename T>
-__device__ __forceinline__ T cv_at(const T* ev, int nc, int Pc, int I, int J) {
+__device__ __forceinline__ T cv_at(const T* ev, int nc, int nxc, int iwc, int Pc, int I, int J) {
   if (J >= nc) return T(0);
+  if (J == 0 && iwc > 0 && (I < iwc || I >= iwc + nc)) return T(0);
   if (I < 0) return -ev[(long long)J * Pc];
-  if (I > nc - 1) return -ev[(long long)J * Pc + nc - 1];
+  if (I > nxc - 1) return -ev[(long long)J * Pc + nxc - 1];
   return ev[(long long)J * Pc + I];
 }
 
-// increment of fine u face (i, j), 0 < i < nf, j < nf
+// increment of fine u face (i, j), 0 < i < 2 nxc, j < 2 nc
 template <typename T>
-__device__ __forceinline__ T prolong_u_val(const T* __restrict__ eu, int nc, int Pc, int i, int j, int lat = 0) {
+__device__ __forceinline__ T prolong_u_val(const T* __restrict__ eu, int nc, int nxc, int iwc, int Pc, int i, int j,
+                                           int lat = 0) {
   const int J = j >> 1, Jn = (j & 1) ? J + 1 : J - 1;
   T cy0, cy1;
   if (i & 1) {
     const int I = i >> 1;
-    cy0 = T(0.5) * (cu_at(eu, nc, Pc, I, J, lat) + cu_at(eu, nc, Pc, I + 1, J, lat));
-    cy1 = T(0.5) * (cu_at(eu, nc, Pc, I, Jn, lat) + cu_at(eu, nc, Pc, I + 1, Jn, lat));
+    cy0 = T(0.5) * (cu_at(eu, nc, nxc, iwc, Pc, I, J, lat) + cu_at(eu, nc, nxc, iwc, Pc, I + 1, J, lat));
+    cy1 = T(0.5) * (cu_at(eu, nc, nxc, iwc, Pc, I, Jn, lat) + cu_at(eu, nc, nxc, iwc, Pc, I + 1, Jn, lat));
   } else {
     const int I = i >> 1;
-    cy0 = cu_at(eu, nc, Pc, I, J, lat);
-    cy1 = cu_at(eu, nc, Pc, I, Jn, lat);
+    cy0 = cu_at(eu, nc, nxc, iwc, Pc, I, J, lat);
+    cy1 = cu_at(eu, nc, nxc, iwc, Pc, I, Jn, lat);
   }
   return T(0.75) * cy0 + T(0.25) * cy1;
 }
 
-// increment of fine v face (i, j), i < nf, j < nf
+// increment of fine v face (i, j), i < 2 nxc, j < 2 nc
 template <typename T>
-__device__ __forceinline__ T prolong_v_val(const T* __restrict__ ev, int nc, int Pc, int i, int j) {
+__device__ __forceinline__ T prolong_v_val(const T* __restrict__ ev, int nc, int nxc, int iwc, int Pc, int i, int j) {
   const int I = i >> 1, In = (i & 1) ? I + 1 : I - 1;
   T cx0, cx1;
   if (j & 1) {
     const int J = j >> 1;
-    cx0 = T(0.5) * (cv_at(ev, nc, Pc, I, J) + cv_at(ev, nc, Pc, I, J + 1));
-    cx1 = T(0.5) * (cv_at(ev, nc, Pc, In, J) + cv_at(ev, nc, Pc, In, J + 1));
+    cx0 = T(0.5) * (cv_at(ev, nc, nxc, iwc, Pc, I, J) + cv_at(ev, nc, nxc, iwc, Pc, I, J + 1));
+    cx1 = T(0.5) * (cv_at(ev, nc, nxc, iwc, Pc, In, J) + cv_at(ev, nc, nxc, iwc, Pc, In, J + 1));
   } else {
     const int J = j >> 1;
-    cx0 = cv_at(ev, nc, Pc, I, J);
-    cx1 = cv_at(ev, nc, Pc, In, J);
+    cx0 = cv_at(ev, nc, nxc, iwc, Pc, I, J);
+    cx1 = cv_at(ev, nc, nxc, iwc, Pc, In, J);
   }
   return T(0.75) * cx0 + T(0.25) * cx1;
 }
 
+// coarse cell block of nc rows and ncx cells across
 template <typename T>
-__device__ __forceinline__ T cd_at(const T* e, int nc, int Pc, int I, int J) {
+__device__ __forceinline__ T cd_at(const T* e, int nc, int ncx, int Pc, int I, int J) {
   // lateral sides and top of D' are no-flow (mirror), the bottom is Dirichlet (negative mirror)
   if (I < 0) I = 0;
-  if (I > nc - 1) I = nc - 1;
+  if (I > ncx - 1) I = ncx - 1;
   if (J < 0) return -e[I];
   if (J > nc - 1) J = nc - 1;
   return e[(long long)J * Pc + I];
 }
 
 template <typename T>
-__device__ __forceinline__ T prolong_D_val(const T* __restrict__ e, int nc, int Pc, int i, int j) {
+__device__ __forceinline__ T prolong_D_val(const T* __restrict__ e, int nc, int ncx, int Pc, int i, int j) {
   const int I = i >> 1, J = j >> 1;
   const int In = (i & 1) ? I + 1 : I - 1, Jn = (j & 1) ? J + 1 : J - 1;
-  return T(0.5625) * cd_at(e, nc, Pc, I, J) + T(0.1875) * (cd_at(e, nc, Pc, In, J) + cd_at(e, nc, Pc, I, Jn)) +
-         T(0.0625) * cd_at(e, nc, Pc, In, Jn);
+  return T(0.5625) * cd_at(e, nc, ncx, Pc, I, J) +
+         T(0.1875) * (cd_at(e, nc, ncx, Pc, In, J) + cd_at(e, nc, ncx, Pc, I, Jn)) +
+         T(0.0625) * cd_at(e, nc, ncx, Pc, In, Jn);
 }
 
 }  // namespace sdk

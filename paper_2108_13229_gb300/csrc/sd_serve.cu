@@ -53,6 +53,7 @@ struct Job {
   int done = 0, iters = 0;
   int first = SD_OK;  // first non-OK status of a step that still advanced the state
   double maxrel = 0.0;
+  int geometry = SD_GEO_SQUARE;  // the server's sd_options.geometry
 };
 
 // Lockstep serving: the running requests of one size class (grid, mu, dt)
@@ -107,7 +108,7 @@ void run_job(sd_server* S, Job* J) {
   sd_handle* h = nullptr;
   int rc = sd_create(&J->req.grid, J->req.mu, J->K.data(), J->req.alpha_bj, J->req.dt, &o, &h);
   std::memset(&J->res, 0, sizeof(J->res));
-  J->res.dof = sd_dof_count(J->req.grid.nx);
+  J->res.dof = sd_dof_count_geometry(J->req.grid.nx, J->geometry);
   if (rc == SD_OK) {
     std::vector<sd_step_info> info(J->req.nsteps > 0 ? J->req.nsteps : 1);
     rc = sd_step(h, J->req.nsteps, info.data());
@@ -125,7 +126,7 @@ void run_job(sd_server* S, Job* J) {
     J->res.total_iters = it;
     J->res.max_relres = mr;
     if (J->req.keep_fields) {
-      J->x.resize((size_t)sd_dof_count(J->req.grid.nx));
+      J->x.resize((size_t)sd_dof_count_geometry(J->req.grid.nx, J->geometry));
       int r2 = sd_get_state(h, nullptr, nullptr, J->x.data(), nullptr);
       if (rc == SD_OK) rc = r2;
     }
@@ -153,12 +154,12 @@ void finish_job(sd_server* S, Job* J) {
 // path does, also after steps that ended in SD_E_NOCONV or SD_E_NUMERIC),
 // release the handle.
 void close_job(Job* J, int rc) {
-  J->res.dof = sd_dof_count(J->req.grid.nx);
+  J->res.dof = sd_dof_count_geometry(J->req.grid.nx, J->geometry);
   J->res.steps_done = J->done;
   J->res.total_iters = J->iters;
   J->res.max_relres = J->maxrel;
   if (J->h && J->req.keep_fields && (rc == SD_OK || rc == SD_E_NOCONV || rc == SD_E_NUMERIC)) {
-    J->x.resize((size_t)sd_dof_count(J->req.grid.nx));
+    J->x.resize((size_t)sd_dof_count_geometry(J->req.grid.nx, J->geometry));
     const int r2 = sd_get_state(J->h, nullptr, nullptr, J->x.data(), nullptr);
     if (rc == SD_OK) rc = r2;
   }
@@ -195,7 +196,7 @@ void class_loop(sd_server* S, SizeClass* C) {
     for (Job* J : C->running) hs.push_back(J->h);
     std::vector<sd_step_info> info(hs.size());
     std::vector<int> rcs(hs.size(), SD_OK);
-    const int64_t dof = sd_dof_count(C->running[0]->req.grid.nx);
+    const int64_t dof = sd_dof_count_geometry(C->running[0]->req.grid.nx, S->opt.geometry);
     const size_t cap = (size_t)std::max<int64_t>(1, kLockstepDof / dof);
     for (size_t a = 0; a < hs.size(); a += cap) {
       const size_t b = std::min(hs.size(), a + cap);
@@ -250,7 +251,7 @@ void worker_loop(sd_server* S) {
       S->running += 1;
       J->t_start = clk::now();
       const int n = J->req.grid.nx;
-      if ((S->flags & SD_SERVER_LOCKSTEP) && sd_dof_count(n) < kServeLockstepDof) {
+      if ((S->flags & SD_SERVER_LOCKSTEP) && sd_dof_count_geometry(n, S->opt.geometry) < kServeLockstepDof) {
         // hand the run to its size class and go back for the next request
         auto key = std::make_tuple(n, J->req.mu, J->req.dt, job_options(S, J).coarsest);
         auto it = S->classes.find(key);
@@ -309,7 +310,7 @@ int sd_solve_batch_ex(sd_handle* const* hs, int32_t count, const int32_t* nsteps
   {
     std::vector<std::vector<int>> split;
     for (auto& it : items) {
-      const int64_t dof = sd_dof_count(sdk::handle_grid(hs[it[0]]));
+      const int64_t dof = sdk::handle_dof(hs[it[0]]);
       const int cap = (int)std::max<int64_t>(1, kLockstepDof / dof);
       for (size_t a = 0; a < it.size(); a += (size_t)cap)
         split.emplace_back(it.begin() + a, it.begin() + std::min(it.size(), a + (size_t)cap));
@@ -387,6 +388,7 @@ int sd_submit(sd_server* S, const sd_request* req, uint64_t* ticket) {
   if (need > S->budget) return SD_E_NOMEM;
   const int n = req->grid.nx;
   std::unique_ptr<Job> J(new Job());
+  J->geometry = S->opt.geometry;
   J->req = *req;
   J->K.assign(req->K, req->K + (size_t)n * n);
   J->req.K = nullptr;

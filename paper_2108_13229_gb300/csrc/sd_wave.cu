@@ -53,11 +53,11 @@ __device__ __forceinline__ void col_tile_V(const Coef<float>& c, const float* __
     if (xin) {
       if (IN || (ucol && j >= 0 && j < n)) {
         xu = xin[k];
-        if (ec && (IN || c.lat || (i > 0 && i < n))) xu += prolong_u_val(ecu, nc, Pc, i, j, c.lat);
+        if (ec && (IN || c.lat || (i > 0 && i < n))) xu += prolong_u_val(ecu, nc, nc, 0, Pc, i, j, c.lat);
       }
       if (IN || (vcol && j >= 0 && j <= n)) {
         xv = xin[nv + k];
-        if (ec && (IN || j < n)) xv += prolong_v_val(ecv, nc, Pc, i, j);
+        if (ec && (IN || j < n)) xv += prolong_v_val(ecv, nc, nc, 0, Pc, i, j);
       }
     }
     U[q] = xu;
@@ -203,7 +203,7 @@ __device__ __forceinline__ void col_tile_D(const Coef<float>& c, const float* __
     float x = 0.f;
     if (xin && (IN || (col && j >= 0 && j < n))) {
       x = xin[k];
-      if (ec) x += prolong_D_val(ec, nc, Pc, i, j);
+      if (ec) x += prolong_D_val(ec, nc, nc, Pc, i, j);
     }
     X[q] = x;
     D[q] = 0.f;

@@ -27,6 +27,7 @@ SD_BATCH_LOCKSTEP = 1
 SD_SERVER_LOCKSTEP = 1
 SD_MONOLITHIC, SD_PARTITIONED = 0, 1
 SD_ORDER_AUTO, SD_ORDER_PM_FIRST, SD_ORDER_FF_FIRST = 0, 1, 2
+SD_GEO_SQUARE, SD_GEO_CHANNEL = 0, 1
 
 
 class SdError(RuntimeError):
@@ -53,7 +54,7 @@ class sd_options(ctypes.Structure):
                 ("coupling_eps", ctypes.c_double), ("coupling_omega", ctypes.c_double),
                 ("coupling_order", ctypes.c_int32), ("coupling_rtol", ctypes.c_double),
                 ("bc_dp", ctypes.c_double), ("bc_tend", ctypes.c_double),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("geometry", ctypes.c_int32)]
 
 
 class sd_step_info(ctypes.Structure):
@@ -84,6 +85,7 @@ _vp = ctypes.c_void_p
 _SIGS = {
     "sd_options_default": (None, [ctypes.POINTER(sd_options)]),
     "sd_dof_count": (ctypes.c_int64, [ctypes.c_int32]),
+    "sd_dof_count_geometry": (ctypes.c_int64, [ctypes.c_int32, ctypes.c_int32]),
     "sd_memory_estimate": (ctypes.c_int64, [ctypes.POINTER(sd_grid), ctypes.POINTER(sd_options)]),
     "sd_create": (ctypes.c_int, [ctypes.POINTER(sd_grid), ctypes.c_double, _vp, ctypes.c_double, ctypes.c_double,
                                  ctypes.POINTER(sd_options), ctypes.POINTER(_vp)]),
@@ -187,6 +189,10 @@ def sd_dof_count(n: int) -> int:
     return int(_load().sd_dof_count(int(n)))
 
 
+def sd_dof_count_geometry(n: int, geometry: int) -> int:
+    return int(_load().sd_dof_count_geometry(int(n), int(geometry)))
+
+
 def sd_memory_estimate(n: int, opts: sd_options | None = None) -> int:
     g = sd_grid(n, n)
     return int(_load().sd_memory_estimate(ctypes.byref(g), ctypes.byref(opts) if opts is not None else None))
@@ -195,10 +201,12 @@ def sd_memory_estimate(n: int, opts: sd_options | None = None) -> int:
 class Handle:
     """Owns one sd_handle; freed by sd_destroy() or garbage collection."""
 
-    def __init__(self, ptr, n):
+    def __init__(self, ptr, n, geometry=SD_GEO_SQUARE):
         self.ptr = ptr
         self.n = n
-        self.dof = 4 * n * n + 2 * n
+        self.geometry = geometry
+        self.nx = 3 * n if geometry == SD_GEO_CHANNEL else n  # free-flow cells across
+        self.dof = sd_dof_count_geometry(n, geometry)
 
     def __del__(self):
         if getattr(self, "ptr", None):
@@ -217,7 +225,7 @@ def sd_create(n: int, mu: float, K, alpha_bj: float, dt: float, opts: sd_options
     rc = _load().sd_create(ctypes.byref(g), float(mu), _ptr(K, n * n), float(alpha_bj), float(dt),
                            ctypes.byref(opts) if opts is not None else None, ctypes.byref(out))
     _check(rc, "sd_create")
-    return Handle(out.value, n)
+    return Handle(out.value, n, opts.geometry if opts is not None else SD_GEO_SQUARE)
 
 
 def sd_step(h: Handle, nsteps: int = 1, raise_on_error: bool = True):
@@ -230,12 +238,12 @@ def sd_step(h: Handle, nsteps: int = 1, raise_on_error: bool = True):
 
 def sd_get_fields(h: Handle, u=None, v=None, p_ff=None, p_pm=None):
     """Copy the fields out; numpy arrays are allocated for the ones not given."""
-    n = h.n
-    u = np.empty((n, n + 1)) if u is None else u
-    v = np.empty((n + 1, n)) if v is None else v
-    p_ff = np.empty((n, n)) if p_ff is None else p_ff
+    n, nx = h.n, h.nx
+    u = np.empty((n, nx + 1)) if u is None else u
+    v = np.empty((n + 1, nx)) if v is None else v
+    p_ff = np.empty((n, nx)) if p_ff is None else p_ff
     p_pm = np.empty((n, n)) if p_pm is None else p_pm
-    _check(_load().sd_get_fields(h.ptr, _ptr(u, n * (n + 1)), _ptr(v, n * (n + 1)), _ptr(p_ff, n * n),
+    _check(_load().sd_get_fields(h.ptr, _ptr(u, n * (nx + 1)), _ptr(v, nx * (n + 1)), _ptr(p_ff, n * nx),
                                  _ptr(p_pm, n * n)), "sd_get_fields")
     return {"u": u, "v": v, "p_ff": p_ff, "p_pm": p_pm}
 

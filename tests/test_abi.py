@@ -45,6 +45,16 @@ def test_dof_count_table1(sd):
             assert sd.sd_dof_count(int(n)) == int(dof)
 
 
+def test_dof_count_geometry(sd):
+    # the channel's count is the oracle's (a different library, the same layout)
+    import oracle as O
+    for n in (2, 4, 5, 64, 1024):
+        assert sd.sd_dof_count_geometry(n, sd.SD_GEO_SQUARE) == sd.sd_dof_count(n)
+        assert sd.sd_dof_count_geometry(n, sd.SD_GEO_CHANNEL) == O.dof_count(n, 1) == 10 * n * n + 4 * n
+    assert sd.sd_dof_count_geometry(4, 7) == -1
+    assert sd.sd_options_default().geometry == sd.SD_GEO_SQUARE
+
+
 def test_options_default(sd):
     o = sd.sd_options_default()
     assert o.restart == 30 and o.rtol == 1e-10 and o.precision == sd.SD_MIXED

@@ -497,6 +497,7 @@ def bench_ours(args, ws, rank, local):
         # loop at three arrival rates
         line["c3_2048"] = bench_c3(sd, torch, stream, rank)
         line["paper_problem"] = bench_paper_problem(sd, torch, stream, rank)
+        line["paper_problem_channel"] = bench_paper_problem(sd, torch, stream, rank, geometry=sd.SD_GEO_CHANNEL)
         line["batch"] = bench_batch(sd, 256, 10, 32, seed=rank)
         line["batch"]["per_instance_streams"] = bench_batch(sd, 256, 10, 32, seed=rank, lockstep=False)
         line["serving"] = [bench_serve(sd, rate, 60, 16) for rate in (20.0, 100.0, 500.0)]
@@ -529,16 +530,20 @@ def bench_c3(sd, torch, stream, rank: int, steps: int = 20):
             "mixed_over_fp64": out["mixed"]["value"] / out["fp64"]["value"], "rel_l2_mixed_vs_fp64": err}
 
 
-def bench_paper_problem(sd, torch, stream, rank: int, n: int = 1024, steps: int = 25):
+def bench_paper_problem(sd, torch, stream, rank: int, n: int = 1024, steps: int = 25, geometry: int = 0):
     """The paper's pressure-driven problem (Sec. 5: half-cosine inflow pressure over t_end = 25 steps, traction
-    sides, no slip on top, p = 0 at the porous-medium bottom) at 1024^2 on the log-normal workload's parameters."""
+    sides, no slip on top, p = 0 at the porous-medium bottom) at 1024^2 on the log-normal workload's parameters;
+    geometry 1: on the model problem's channel (free flow 3n x n, the interface the middle third of its floor)."""
     from paper_2108_13229_gb300 import inputs as I
     K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=rank)
-    dof = 4 * n * n + 2 * n
-    ms, infos, launches, _ = run_form(sd, torch, n, K, sd.SD_MIXED, steps, 0, stream, tuned={"bc": sd.SD_BC_PAPER})
+    dof = sd.sd_dof_count_geometry(n, geometry)
+    ms, infos, launches, _ = run_form(sd, torch, n, K, sd.SD_MIXED, steps, 0, stream,
+                                      tuned={"bc": sd.SD_BC_PAPER, "geometry": geometry})
     lat = [i["ms"] for i in infos]
-    return {"workload": "pressure-driven problem (bc 2), %dx%d cells (%d DoF), lognormal K, mu=1e-3, alpha_BJ=1, "
-                        "dt=0.05, %d steps from rest (the whole inflow ramp), rtol 1e-10" % (n, n, dof, steps),
+    where = ("%dx%d cells" % (n, n) if geometry == 0 else
+             "channel: free flow %dx%d cells over %dx%d pm cells, interface the floor's middle third" % (3 * n, n, n, n))
+    return {"workload": "pressure-driven problem (bc 2), %s (%d DoF), lognormal K, mu=1e-3, alpha_BJ=1, "
+                        "dt=0.05, %d steps from rest (the whole inflow ramp), rtol 1e-10" % (where, dof, steps),
             "value": dof * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "iters_per_step": [i["iters"] for i in infos], "max_relres": max(i["relres"] for i in infos),

@@ -110,10 +110,11 @@ extern "C" {
                    4 n (sd_dof_count_geometry).  Dense state vectors use the
                    layout [u | v | p_ff | p_pm] with u (3n+1) x n, v 3n x
                    (n+1), p_ff 3n x n and p_pm n x n, x fastest.  The channel
-                   runs the monolithic coupling only, with one launch per
-                   Chebyshev step (the tile and fuse_coarse options do not
-                   apply); it coarsens to at most 8 x 8 porous-medium cells
-                   (coarsest above 8 counts as 8), so n = m 2^k needs m <= 8. */
+                   runs the monolithic coupling only, smooths in shared-memory
+                   tiles for tile 1 and 2 (no register-column tiles, no fused
+                   coarse cycle: fuse_coarse does not apply), and coarsens to
+                   at most 8 x 8 porous-medium cells (coarsest above 8 counts
+                   as 8), so n = m 2^k needs m <= 8. */
 #define SD_GEO_SQUARE 0
 #define SD_GEO_CHANNEL 1
 

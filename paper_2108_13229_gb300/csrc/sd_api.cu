@@ -628,17 +628,17 @@ int tile_rows_of(const sd_handle* h, int n) {
 #define SD_WAVE_MIN_N 1024
 #endif
 int wave_rows_of(const sd_handle* h, int n) {
-  if (h->opt.tile != 2 || n < SD_WAVE_MIN_N) return 0;
+  // (the register-column tiles serve the square geometry)
+  if (h->opt.tile != 2 || n < SD_WAVE_MIN_N || h->g.iw != 0) return 0;
   if (h->opt.tile_rows) return h->opt.tile_rows >= 8 ? 8 : 4;
   return 4;
 }
 
 // tiled smoothing (all steps of one smoothing in one kernel) is used for the
-// FP32 hierarchy with at most four Chebyshev steps, in the square geometry
-// (the channel's levels run one launch per step)
+// FP32 hierarchy with at most four Chebyshev steps
 template <typename T>
 bool use_tiles(const sd_handle* h, const Block<T>& B) {
-  return std::is_same<T, float>::value && h->opt.tile && h->g.iw == 0 && B.cha.size() >= 1 && B.cha.size() <= 4;
+  return std::is_same<T, float>::value && h->opt.tile && B.cha.size() >= 1 && B.cha.size() <= 4;
 }
 
 // Velocity block: Chebyshev pre-smoothing from zero, residual, transposed

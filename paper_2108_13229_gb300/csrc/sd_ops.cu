@@ -1120,11 +1120,11 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_D(Coef<T> c, const T* __res
   constexpr int CX = SP / 2 + 4, CY = SR / 2 + 4;  // coarse window of the prolongation
   __shared__ T sb[SR * SP], sx0[SR * SP], sx1[SR * SP], sd[SR * SP], sTx[SR * SP], sTy[SR * SP];
   __shared__ T sce[CY * CX];
-  const int n = c.n, P = c.P;
+  const int n = c.n, cx = c.cx, P = c.P;  // n rows of cx cells
   const int ilo = blockIdx.x * TLX - H, jlo = blockIdx.y * TLY - H;
   const int I0 = (ilo >> 1) - 1, J0 = (jlo >> 1) - 1;
   if (xin && ec) {
-    for (int p = threadIdx.x; p < CX * CY; p += TLT) sce[p] = cd_at(ec, nc, nc, Pc, I0 + p % CX, J0 + p / CX);
+    for (int p = threadIdx.x; p < CX * CY; p += TLT) sce[p] = cd_at(ec, nc, cx / 2, Pc, I0 + p % CX, J0 + p / CX);
     __syncthreads();
   }
   for (int p = threadIdx.x; p < SR * SP; p += TLT) {
@@ -1132,15 +1132,15 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_D(Coef<T> c, const T* __res
     T vb = T(0), vx = T(0), vtx = T(0), vty = T(0);
     if (gi >= 0 && gj >= 0) {
       const long long gk = (long long)gj * P + gi;
-      if (gi < n && gj < n) {
+      if (gi < cx && gj < n) {
         vb = b[gk];
         if (xin) {
           vx = xin[gk];
           if (ec) vx += prolong_D_sm(sce, CX, I0, J0, gi, gj);
         }
       }
-      if (gi <= n && gj < n) vtx = c.Tx[gk];
-      if (gi < n && gj <= n) vty = c.Ty[gk];
+      if (gi <= cx && gj < n) vtx = c.Tx[gk];
+      if (gi < cx && gj <= n) vty = c.Ty[gk];
     }
     sb[p] = vb;
     sx0[p] = vx;
@@ -1161,7 +1161,7 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_D(Coef<T> c, const T* __res
   const T* cur = xin ? xa : nullptr;
   T* nxt = xb;
   // every point the first step computes is an interior cell: no boundary term anywhere
-  const bool inner = ilo + 1 >= 1 && ilo + EX - 2 <= n - 2 && jlo + 1 >= 1 && jlo + EY - 2 <= n - 2;
+  const bool inner = ilo + 1 >= 1 && ilo + EX - 2 <= cx - 2 && jlo + 1 >= 1 && jlo + EY - 2 <= n - 2;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     const int lo = s + 1, w = EX - 2 * lo, hgt = EY - 2 * lo;
@@ -1173,7 +1173,7 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_D(Coef<T> c, const T* __res
     } else {
       for (int p = threadIdx.x; p < w * hgt; p += TLT) {
         const int gi = ilo + lo + p % w, gj = jlo + lo + p / w;
-        if (gi >= 0 && gj >= 0 && gi < n && gj < n) cheb_D_at(tc, cur, bq, dq, nxt, cs.a[s], cs.c[s], gi, gj);
+        if (gi >= 0 && gj >= 0 && gi < cx && gj < n) cheb_D_at(tc, cur, bq, dq, nxt, cs.a[s], cs.c[s], gi, gj);
       }
     }
     __syncthreads();
@@ -1183,7 +1183,7 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_D(Coef<T> c, const T* __res
   if constexpr (RR) {
     for (int p = threadIdx.x; p < TLX * TLY; p += TLT) {
       const int gi = ilo + H + p % TLX, gj = jlo + H + p / TLX;
-      if (gi >= n || gj >= n) continue;
+      if (gi >= cx || gj >= n) continue;
       const int k = gj * SP + gi;
       T off, dg;
       d_row(tc, cur, gi, gj, true, off, dg);
@@ -1193,14 +1193,14 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_D(Coef<T> c, const T* __res
     const int I0 = (ilo + H) / 2, J0 = (jlo + H) / 2;
     for (int p = threadIdx.x; p < (TLX / 2) * (TLY / 2); p += TLT) {
       const int I = I0 + p % (TLX / 2), J = J0 + p / (TLX / 2);
-      if (I >= nc || J >= nc) continue;
+      if (I >= cx / 2 || J >= nc) continue;
       const T* r0 = dq + (2 * J) * SP + 2 * I;
       bco[(long long)J * Pc + I] = (r0[0] + r0[1]) + (r0[SP] + r0[SP + 1]);
     }
   }
   for (int p = threadIdx.x; p < TLX * TLY; p += TLT) {
     const int gi = ilo + H + p % TLX, gj = jlo + H + p / TLX;
-    if (gi < n && gj < n) xout[(long long)gj * P + gi] = cur[(long long)gj * SP + gi];
+    if (gi < cx && gj < n) xout[(long long)gj * P + gi] = cur[(long long)gj * SP + gi];
   }
 }
 
@@ -1243,7 +1243,8 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_V(Coef<T> c, const T* __res
   __shared__ T sbu[SR * SP], sbv[SR * SP], sau[SR * SP], sav[SR * SP], sbu2[SR * SP], sbv2[SR * SP];
   __shared__ T sdu[SR * SP], sdv[SR * SP], sw[SP], srg[SP];
   __shared__ T scu[CY * CX], scv[CY * CX];
-  const int n = c.n, P = c.P;
+  const int n = c.n, nx = c.nx, P = c.P;
+  const int nxc = nx / 2, iwc = c.iw / 2;  // the coarse level's width and interface window
   const long long nv = (long long)n * P;
   const int ilo = blockIdx.x * TLX - H, jlo = blockIdx.y * TLY - H;
   const T* ecu = ec;
@@ -1251,12 +1252,12 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_V(Coef<T> c, const T* __res
   const int I0 = (ilo >> 1) - 1, J0 = (jlo >> 1) - 1;
   if (xin && ec) {
     // window entries no halo point reads are set to zero: coarse u faces
-    // outside 0..nc (which cu_at would read past its row on traction sides)
+    // outside 0..nxc (which cu_at would read past its row on traction sides)
     // and coarse v rows below 0
     for (int p = threadIdx.x; p < CX * CY; p += TLT) {
       const int I = I0 + p % CX, J = J0 + p / CX;
-      scu[p] = (I >= 0 && I <= nc) ? cu_at(ecu, nc, nc, 0, Pc, I, J, c.lat) : T(0);
-      scv[p] = J >= 0 ? cv_at(ecv, nc, nc, 0, Pc, I, J) : T(0);
+      scu[p] = (I >= 0 && I <= nxc) ? cu_at(ecu, nc, nxc, iwc, Pc, I, J, c.lat) : T(0);
+      scv[p] = J >= 0 ? cv_at(ecv, nc, nxc, iwc, Pc, I, J) : T(0);
     }
     __syncthreads();
   }
@@ -1265,18 +1266,18 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_V(Coef<T> c, const T* __res
     T bu = T(0), bv = T(0), xu = T(0), xv = T(0);
     if (gi >= 0 && gj >= 0) {
       const long long gk = (long long)gj * P + gi;
-      if (gi <= n && gj < n) {  // u face
+      if (gi <= nx && gj < n) {  // u face
         bu = b[gk];
         if (xin) {
           xu = xin[gk];
-          if (ec && (c.lat || (gi > 0 && gi < n))) xu += prolong_u_sm(scu, CX, I0, J0, gi, gj);
+          if (ec && (c.lat || (gi > 0 && gi < nx))) xu += prolong_u_sm(scu, CX, I0, J0, gi, gj);
         }
       }
-      if (gi < n && gj <= n) {  // v face
+      if (gi < nx && gj <= n) {  // v face (the Dirichlet ones take no increment)
         bv = b[nv + gk];
         if (xin) {
           xv = xin[nv + gk];
-          if (ec && gj < n) xv += prolong_v_sm(scv, CX, I0, J0, gi, gj);
+          if (ec && gj < n && (gj > 0 || on_gamma(c, gi))) xv += prolong_v_sm(scv, CX, I0, J0, gi, gj);
         }
       }
     }
@@ -1287,8 +1288,8 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_V(Coef<T> c, const T* __res
   }
   for (int p = threadIdx.x; p < SP; p += TLT) {
     const int gi = ilo + p;
-    sw[p] = (gi >= 0 && gi <= n) ? c.w[gi] : T(0);
-    srg[p] = (gi >= 0 && gi < n) ? c.rg[gi] : T(0);
+    sw[p] = (gi >= 0 && gi <= nx) ? c.w[gi] : T(0);
+    srg[p] = (gi >= 0 && gi < nx) ? c.rg[gi] : T(0);
   }
   __syncthreads();
   const long long sh = (long long)jlo * SP + ilo;
@@ -1309,7 +1310,8 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_V(Coef<T> c, const T* __res
   T* nxu = cu2;
   T* nxv = cv2;
   // every point the first step computes has interior u and v faces: no boundary term anywhere
-  const bool inner = ilo + 1 >= 2 && ilo + EX - 2 <= n - 2 && jlo + 1 >= 1 && jlo + EY - 2 <= n - 2;
+  // (in the channel row 1 of the v faces reads the floor: interior from row 2)
+  const bool inner = ilo + 1 >= 2 && ilo + EX - 2 <= nx - 2 && jlo + 1 >= (c.iw ? 2 : 1) && jlo + EY - 2 <= n - 2;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     const int lo = s + 1, w = EX - 2 * lo, hgt = EY - 2 * lo;
@@ -1321,7 +1323,7 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_V(Coef<T> c, const T* __res
     } else {
       for (int p = threadIdx.x; p < w * hgt; p += TLT) {
         const int gi = ilo + lo + p % w, gj = jlo + lo + p / w;
-        if (gi >= 0 && gj >= 0 && gi <= n && gj <= n)
+        if (gi >= 0 && gj >= 0 && gi <= nx && gj <= n)
           cheb_V_at2(tc, curu, curv, bu, bv, du, dv, nxu, nxv, cs.a[s], cs.c[s], gi, gj);
       }
     }
@@ -1337,23 +1339,23 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_V(Coef<T> c, const T* __res
     constexpr int lo = NS + 1, w = EX - 2 * lo, hgt = EY - 2 * lo;
     for (int p = threadIdx.x; p < w * hgt; p += TLT) {
       const int gi = ilo + lo + p % w, gj = jlo + lo + p / w;
-      if (gi < 0 || gj < 0 || gi > n || gj > n) continue;
+      if (gi < 0 || gj < 0 || gi > nx || gj > n) continue;
       const int k = gj * SP + gi;
       if (gj < n) {
         T ax, dg = T(1);
-        if ((gi == 0 || gi == n) && !c.lat) {
+        if ((gi == 0 || gi == nx) && !c.lat) {
           ax = curu[k];
         } else {
           T off;
-          if (gi == 0 || gi == n) ub_row(tc, curu, curv, gi, gj, true, off, dg);
+          if (gi == 0 || gi == nx) ub_row(tc, curu, curv, gi, gj, true, off, dg);
           else u_row(tc, curu, curv, gi, gj, true, off, dg);
           ax = dg * curu[k] + off;
         }
         du[k] = bu[k] - ax;
       }
-      if (gi < n) {
+      if (gi < nx) {
         T ax, dg = T(1);
-        if (gj == n) {
+        if (gj == n || (gj == 0 && !on_gamma(c, gi))) {
           ax = curv[k];
         } else {
           T off;
@@ -1367,14 +1369,14 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_V(Coef<T> c, const T* __res
     const int I0 = (ilo + H) / 2, J0 = (jlo + H) / 2;
     for (int p = threadIdx.x; p < (TLX / 2) * (TLY / 2); p += TLT) {
       const int I = I0 + p % (TLX / 2), J = J0 + p / (TLX / 2);
-      if (I <= nc && J <= nc) restrict_V_at2<T>(du, dv, SP, nc, nc, 0, Pc, bco, I, J, c.lat);
+      if (I <= nxc && J <= nc) restrict_V_at2<T>(du, dv, SP, nc, nxc, iwc, Pc, bco, I, J, c.lat);
     }
   }
   for (int p = threadIdx.x; p < TLX * TLY; p += TLT) {
     const int gi = ilo + H + p % TLX, gj = jlo + H + p / TLX;
     const long long gk = (long long)gj * P + gi, sk = (long long)gj * SP + gi;
-    if (gi <= n && gj < n) xout[gk] = curu[sk];
-    if (gi < n && gj <= n) xout[nv + gk] = curv[sk];
+    if (gi <= nx && gj < n) xout[gk] = curu[sk];
+    if (gi < nx && gj <= n) xout[nv + gk] = curv[sk];
   }
 }
 
@@ -1389,7 +1391,7 @@ void tile_D_go(const dim3& g, cudaStream_t s, const Coef<T>& c, const T* x_in, c
 template <typename T, int TLY, bool RR>
 int launch_tile_D_rows(const Coef<T>& c, const T* x_in, const T* b, T* x_out, const ChebSteps<T>& cs, const T* ct,
                        const T* ec, int nc, int Pc, T* bco, cudaStream_t s) {
-  const dim3 g((c.n + TLX - 1) / TLX, (c.n + TLY - 1) / TLY);
+  const dim3 g((c.cx + TLX - 1) / TLX, (c.n + TLY - 1) / TLY);
   switch (cs.ns) {
     case 1: tile_D_go<T, 1, TLY, RR>(g, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc, bco); break;
     case 2: tile_D_go<T, 2, TLY, RR>(g, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc, bco); break;
@@ -1431,7 +1433,7 @@ void tile_V_go(const dim3& g, cudaStream_t s, const Coef<T>& c, const T* x_in, c
 template <typename T, int TLY, bool RR>
 int launch_tile_V_rows(const Coef<T>& c, const T* x_in, const T* b, T* x_out, const ChebSteps<T>& cs, const T* ct,
                        const T* ec, int nc, int Pc, T* bco, cudaStream_t s) {
-  const dim3 g((c.n + 1 + TLX - 1) / TLX, (c.n + 1 + TLY - 1) / TLY);
+  const dim3 g((c.nx + 1 + TLX - 1) / TLX, (c.n + 1 + TLY - 1) / TLY);
   switch (cs.ns) {
     case 1: tile_V_go<T, 1, TLY, RR>(g, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc, bco); break;
     case 2: tile_V_go<T, 2, TLY, RR>(g, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc, bco); break;

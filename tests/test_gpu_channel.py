@@ -199,10 +199,20 @@ def test_channel_options(sd):
     # n = 9 * 2^k cannot coarsen to 8 x 8 or below
     with pytest.raises(sd.SdError):
         make(sd, 18, 1.0, np.ones((18, 18)), 1.0, 0.1)
-    # the tile option does not apply: the same bits with and without it
+
+
+@pytest.mark.parametrize("bc", [0, 2])
+@pytest.mark.parametrize("n", [64, 256])
+def test_channel_tiled_smoothing_bitwise(sd, n, bc):
+    # the shared-memory tiles (with the residual and restriction fused into the
+    # pre-smoothing on levels up to 256 cells per side) against one launch per
+    # Chebyshev step: the same bits, over tile heights 4, 8 and 16
+    K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=5)
     xs = []
-    for tile in (0, 2):
-        h = make(sd, n, 1.0, K, 1.0, 0.1, tile=tile)
-        sd.sd_step(h, 2)
+    for tile, rows in ((0, 0), (1, 4), (1, 8), (2, 16), (2, 0)):
+        h = make(sd, n, 1e-3, K, 1.0, 0.05, bc=bc, bc_dp=1.0, tile=tile, tile_rows=rows)
+        infos = sd.sd_step(h, 3)
+        assert all(i["status"] == 0 for i in infos)
         xs.append(sd.sd_get_state(h)[2])
-    assert np.array_equal(xs[0], xs[1])
+    for x in xs[1:]:
+        assert np.array_equal(x, xs[0])

@@ -202,7 +202,7 @@ def test_channel_options(sd):
 
 
 @pytest.mark.parametrize("bc", [0, 2])
-@pytest.mark.parametrize("n", [64, 256])
+@pytest.mark.parametrize("n", [64, 256, 512])
 def test_channel_tiled_smoothing_bitwise(sd, n, bc):
     # the shared-memory tiles (with the residual and restriction fused into the
     # pre-smoothing on levels up to 256 cells per side) against one launch per

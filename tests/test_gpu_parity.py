@@ -449,18 +449,18 @@ def test_pdl_bitwise(sd):
     assert np.array_equal(xs[0], xs[1])
 
 
-@pytest.mark.parametrize("n", [64, 96, 256, 1024])
-def test_tiled_smoothing_bitwise(sd, n):
+@pytest.mark.parametrize("n,bc", [(64, 0), (96, 0), (256, 0), (1024, 0), (1024, 2)])
+def test_tiled_smoothing_bitwise(sd, n, bc):
     # all Chebyshev steps of a smoothing in one tiled kernel, prolongation folded
-    # in, with 16-, 8- or 4-row tiles (0: by level size), and in register-column
-    # tiles (tile 2) of the same heights: the same arithmetic per point as the
-    # per-step kernels (n = 96: 97 faces per row, a one-face ragged tile column;
-    # 97 = 3 * 26 + 19, a ragged register strip).  Register tiles are used on
-    # levels of at least 512 cells per side, so n = 1024 is in the list.
+    # in, with 16-, 8- or 4-row tiles (0: by level size), and with tile 2 in
+    # register-column tiles (cell blocks from 1024 cells per side): the same
+    # arithmetic per point as the per-step kernels (n = 96: 97 faces per row, a
+    # one-face ragged tile column; 97 = 3 * 26 + 19, a ragged register strip;
+    # bc 2: the traction sides' rows)
     K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=11)
     xs = []
     for tile, rows in ((0, 16), (1, 16), (1, 8), (1, 4), (1, 0), (2, 16), (2, 8), (2, 4), (2, 0)):
-        h = make(sd, n, 1e-3, K, 1.0, 0.05, 1, tile=tile, tile_rows=rows)
+        h = make(sd, n, 1e-3, K, 1.0, 0.05, 1, tile=tile, tile_rows=rows, bc=bc, bc_dp=1.0)
         sd.sd_step(h, 3)
         xs.append(sd.sd_get_state(h)[2])
     for x in xs[1:]:

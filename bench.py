@@ -498,6 +498,8 @@ def bench_ours(args, ws, rank, local):
         line["c3_2048"] = bench_c3(sd, torch, stream, rank)
         line["paper_problem"] = bench_paper_problem(sd, torch, stream, rank)
         line["paper_problem_channel"] = bench_paper_problem(sd, torch, stream, rank, geometry=sd.SD_GEO_CHANNEL)
+        line["paper_parameters"] = {"square_1024": bench_paper_parameters(sd, torch, stream, 1024, 0),
+                                    "channel_256": bench_paper_parameters(sd, torch, stream, 256, 1)}
         line["batch"] = bench_batch(sd, 256, 10, 32, seed=rank)
         line["batch"]["per_instance_streams"] = bench_batch(sd, 256, 10, 32, seed=rank, lockstep=False)
         line["serving"] = [bench_serve(sd, rate, 60, 16) for rate in (20.0, 100.0, 500.0)]
@@ -548,6 +550,32 @@ def bench_paper_problem(sd, torch, stream, rank: int, n: int = 1024, steps: int 
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "iters_per_step": [i["iters"] for i in infos], "max_relres": max(i["relres"] for i in infos),
             "launches_per_step": launches / steps}
+
+
+def bench_paper_parameters(sd, torch, stream, n: int, geometry: int, steps: int = 25):
+    """The pressure-driven problem at the paper's own parameters (Sec. 5: K = 1e-6 constant, mu = 1e-3,
+    alpha_BJ = 1, dt = 2e5, t_end = 50e5, amplitude 1e-9), 25 steps from rest, library defaults."""
+    K = np.full((n, n), 1e-6)
+    dof = sd.sd_dof_count_geometry(n, geometry)
+    opts = sd.sd_options_default()
+    opts.stream = stream.cuda_stream
+    opts.bc, opts.bc_dp, opts.bc_tend, opts.geometry = sd.SD_BC_PAPER, 1e-9, 50e5, geometry
+    h = sd.sd_create(n, 1e-3, K, 1.0, 2e5, opts)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        infos = sd.sd_step(h, steps, raise_on_error=False)
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    sd.sd_destroy(h)
+    return {"workload": "%s, %d DoF, K = 1e-6, mu = 1e-3, alpha_BJ = 1, dt = 2e5, %d steps from rest" %
+                        ("square %dx%d" % (n, n) if geometry == 0 else "channel %dx%d over %dx%d" % (3 * n, n, n, n),
+                         dof, steps),
+            "value": dof * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+            "iters_per_step": [i["iters"] for i in infos], "status": sorted({i["status"] for i in infos}),
+            "max_relres": max(i["relres"] for i in infos)}
 
 
 def bench_configs(sd, torch, steps_small: int = 10, steps_big: int = 5):

@@ -356,83 +356,221 @@ void cheb_coeffs(double lmax, double ratio, int deg, std::vector<T>& a, std::vec
   }
 }
 
-// Largest eigenvalue of D^-1 A for one block of one level (FP64 power iteration).
-int power_lmax(sd_handle* h, int l, int kind, double* out) {
-  const Geom& g = h->geo[l];
-  Coef<double> c = coef64(h, l, kind == 2);
-  const bool blockV = kind == 0;
-  const long long len = blockV ? g.lenV : g.lenD;
-  double* xv = h->V;            // Krylov slots as scratch during setup
-  double* yv = h->V + h->lenA;
-  cudaStream_t s = h->s;
-  CK(cudaMemsetAsync(yv, 0, sizeof(double) * len, s));
-  launch_hash_fill(xv, len, 1234u + (unsigned)l, s);
-  auto apply = [&](const double* in, double* o) {
-    if (blockV) launch_resid_V<double>(c, in, nullptr, o, 1, 1, 0, s);
-    else launch_resid_D<double>(c, in, nullptr, o, 1, 1, 0, s);
+// Largest eigenvalues of D^-1 A for every (level, block) of the hierarchy by
+// FP64 power iteration (lam[3 l + kind], kind 0 V, 1 D', 2 pressure
+// Laplacian; the coarsest level has none).  The chains run in rounds: one
+// iteration of every unconverged chain is queued, then one read-back decides
+// which go on, so a setup waits on the host once per round rather than once
+// per iteration of every chain.  Each chain has its own vectors (the Krylov
+// bases are free during setup) and does the arithmetic of a chain run alone,
+// in the same order.
+int power_lmax_all(sd_handle* h, std::vector<double>& lam, cudaStream_t s) {
+  struct Chain {
+    int l, kind;
+    long long len;
+    Coef<double> c;
+    double *x, *y;
+    double lam;
+    bool done;
   };
-  apply(xv, yv);  // y has zero padding from here on
-  double lam = 0.0;
-  const int nb = reduce_blocks(len);
-  for (int it = 0; it < 25; ++it) {
-    launch_dot(yv, yv, len, h->partial, nb, h->scal + sd_handle::S_N2, s);
-    launch_scale_by(yv, xv, len, h->scal + sd_handle::S_N2, 1, s);
-    apply(xv, yv);
-    launch_dot(yv, yv, len, h->partial, nb, h->scal + sd_handle::S_N2, s);
-    CK(cudaMemcpyAsync(h->hflag, h->scal + sd_handle::S_N2, sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    const double nl = std::sqrt(h->hflag[0]);
-    if (it > 4 && std::fabs(nl - lam) <= 1e-3 * nl) { lam = nl; break; }
-    lam = nl;
+  const int nl = h->nlev - 1;
+  lam.assign((size_t)3 * std::max(nl, 0), 0.0);
+  std::vector<Chain> all;
+  for (int l = 0; l < nl; ++l)
+    for (int kind = 0; kind < 3; ++kind) {
+      const Geom& g = h->geo[l];
+      Chain ch;
+      ch.l = l;
+      ch.kind = kind;
+      ch.len = kind == 0 ? g.lenV : g.lenD;
+      ch.c = coef64(h, l, kind == 2);
+      ch.x = ch.y = nullptr;
+      ch.lam = 0.0;
+      ch.done = false;
+      all.push_back(ch);
+    }
+  // the Krylov bases V (m + 1 slots) and Z (m slots) as one pool of vectors;
+  // the norms go to scal[0 .. 64) (no solve runs during setup)
+  const long long vcap = (long long)(h->m + 1) * h->lenA, zcap = (long long)h->m * h->lenA;
+  size_t next = 0;
+  while (next < all.size()) {
+    // as many chains as the two bases hold (each needs x and y; a chain of
+    // the finest velocity block fits in V alone, whatever m)
+    std::vector<Chain*> grp;
+    long long vused = 0, zused = 0;
+    while (next < all.size() && (int)grp.size() < 64) {
+      const long long pad = (all[next].len + 31) / 32 * 32, need = 2 * pad;
+      double* base = nullptr;
+      if (vused + need <= vcap) {
+        base = h->V + vused;
+        vused += need;
+      } else if (zused + need <= zcap) {
+        base = h->Z + zused;
+        zused += need;
+      } else if (grp.empty()) {
+        return SD_E_NOMEM;
+      } else {
+        break;
+      }
+      Chain& ch = all[next++];
+      ch.x = base;
+      ch.y = base + pad;
+      grp.push_back(&ch);
+    }
+    auto apply = [&](Chain& ch, const double* in, double* o) {
+      if (ch.kind == 0) launch_resid_V<double>(ch.c, in, nullptr, o, 1, 1, 0, s);
+      else launch_resid_D<double>(ch.c, in, nullptr, o, 1, 1, 0, s);
+    };
+    int q0 = 0;
+    for (Chain* ch : grp) {
+      CK(cudaMemsetAsync(ch->y, 0, sizeof(double) * ch->len, s));
+      launch_hash_fill(ch->x, ch->len, 1234u + (unsigned)ch->l, s);
+      apply(*ch, ch->x, ch->y);  // y has zero padding from here on
+      launch_dot(ch->y, ch->y, ch->len, h->partial, reduce_blocks(ch->len), h->scal + q0++, s);
+    }
+    for (int it = 0; it < 25; ++it) {
+      int q = 0;
+      for (Chain* ch : grp) {
+        const int slot = q++;
+        if (ch->done) continue;
+        const int nb = reduce_blocks(ch->len);
+        // the slot holds ||y||^2 of this y from the end of the previous
+        // iteration (or the start): the same kernel on the same vector
+        launch_scale_by(ch->y, ch->x, ch->len, h->scal + slot, 1, s);
+        apply(*ch, ch->x, ch->y);
+        launch_dot(ch->y, ch->y, ch->len, h->partial, nb, h->scal + slot, s);
+      }
+      std::vector<double> nrm(grp.size());
+      CK(cudaMemcpyAsync(nrm.data(), h->scal, sizeof(double) * grp.size(), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      bool any = false;
+      q = 0;
+      for (Chain* ch : grp) {
+        const double nv = std::sqrt(nrm[q++]);
+        if (ch->done) continue;
+        if (it > 4 && std::fabs(nv - ch->lam) <= 1e-3 * nv) ch->done = true;
+        ch->lam = nv;
+        any = any || !ch->done;
+      }
+      if (!any) break;
+    }
+    for (Chain* ch : grp) lam[(size_t)3 * ch->l + ch->kind] = ch->lam;
   }
-  *out = lam;
   return SD_OK;
 }
 
-// Dense inverse of the coarsest V or D' block: apply the FP64 operator to
-// unit vectors, gather the columns, invert by Gauss-Jordan on the device.
-int coarse_inverse(sd_handle* h, int kind, double* Ainv, int* idx_dev, int m) {
-  const int l = h->nlev - 1;
-  const bool blockV = kind == 0;
-  const Geom& g = h->geo[l];
-  const long long stride = blockV ? g.lenV : g.lenD;
-  std::vector<int> idx(m);
-  int k = 0;
-  if (blockV) {
-    for (int j = 0; j < g.n; ++j)
-      for (int i = 0; i <= g.nx; ++i) idx[k++] = j * g.P + i;
-    for (int j = 0; j <= g.n; ++j)
-      for (int i = 0; i < g.nx; ++i) idx[k++] = (int)(g.ov + (long long)j * g.P + i);
-  } else {
-    const int cx = kind == 2 ? g.nx : g.n;  // pressure Laplacian: the free-flow cells
-    for (int j = 0; j < g.n; ++j)
-      for (int i = 0; i < cx; ++i) idx[k++] = j * g.P + i;
-  }
-  cudaStream_t s = h->s;
-  CK(cudaMemcpyAsync(idx_dev, idx.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
-  double *X = nullptr, *Y = nullptr, *A = nullptr, *fc = nullptr;
+// Dense inverses of the coarsest V, D' and pressure-Laplacian blocks: apply
+// the FP64 operator to unit vectors, gather the columns, invert by
+// Gauss-Jordan on the device.  The three are independent and run
+// concurrently on three streams, with one scratch allocation for all:
+// coarse_inverses_begin queues them, coarse_inverses_end joins the streams,
+// waits and checks the pivots.
+struct InverseJob {
+  double* scratch = nullptr;
   int* status = nullptr;
-  CK(cudaMalloc(&X, sizeof(double) * stride * m));
-  CK(cudaMalloc(&Y, sizeof(double) * stride * m));
-  CK(cudaMalloc(&A, sizeof(double) * m * m));
-  CK(cudaMalloc(&fc, sizeof(double) * m));
-  CK(cudaMalloc(&status, sizeof(int)));
-  CK(cudaMemsetAsync(X, 0, sizeof(double) * stride * m, s));
-  CK(cudaMemsetAsync(Y, 0, sizeof(double) * stride * m, s));
-  launch_identity_batch(X, stride, idx_dev, m, s);
-  Coef<double> c = coef64(h, l, kind == 2);
-  if (blockV) launch_resid_V<double>(c, X, nullptr, Y, 2, m, stride, s);
-  else launch_resid_D<double>(c, X, nullptr, Y, 2, m, stride, s);
-  launch_gather_dense(Y, stride, idx_dev, m, A, s);
-  launch_gj_inverse(A, Ainv, m, fc, status, s);
-  int hs = 0;
-  CK(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  cudaFree(X); cudaFree(Y); cudaFree(A); cudaFree(fc); cudaFree(status);
-  if (hs != 0) {
-    snprintf(g_errmsg, sizeof(g_errmsg), "coarsest %s block singular at column %d", blockV ? "velocity" : "Darcy", hs);
-    return SD_E_NUMERIC;
+  cudaStream_t s3 = nullptr;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  cudaStream_t st[3] = {nullptr, nullptr, nullptr};
+  std::vector<int> idx[3];
+  int rc = SD_OK;
+};
+
+template <typename T>
+int coarse_inverses_begin(sd_handle* h, MG<T>& M, InverseJob& J) {
+  const int l = h->nlev - 1;
+  const Geom& g = h->geo[l];
+  const int ms[3] = {M.mV, M.mD, M.mP};
+  double* Ainv[3] = {M.AinvV, M.AinvD, M.AinvP};
+  int* idxd[3] = {M.idxV, M.idxD, M.idxP};
+  long long stride[3], off[3][4], tot = 0;
+  for (int kind = 0; kind < 3; ++kind) {
+    stride[kind] = kind == 0 ? g.lenV : g.lenD;
+    const long long m = ms[kind];
+    const long long sz[4] = {stride[kind] * m, stride[kind] * m, m * m, m};  // X, Y, A, fc (doubles)
+    for (int q = 0; q < 4; ++q) {
+      off[kind][q] = tot;
+      tot += (sz[q] + 31) / 32 * 32;
+    }
   }
+  CK(cudaMalloc(&J.scratch, sizeof(double) * tot + 6 * sizeof(int)));
+  double* scratch = J.scratch;
+  int* status = J.status = reinterpret_cast<int*>(scratch + tot);  // three statuses, then three completion counters
+  int& rc = J.rc;
+  auto ok = [&](cudaError_t e) {
+    if (e != cudaSuccess && rc == SD_OK) rc = SD_E_CUDA;
+    return e == cudaSuccess;
+  };
+  ok(cudaStreamCreateWithFlags(&J.s3, cudaStreamNonBlocking));
+  for (int q = 0; q < 3; ++q) ok(cudaEventCreateWithFlags(&J.ev[q], cudaEventDisableTiming));
+  J.st[0] = h->s;
+  J.st[1] = h->s2;
+  J.st[2] = J.s3;
+  const cudaStream_t* st = J.st;
+  if (rc == SD_OK) {
+    ok(cudaEventRecord(J.ev[0], h->s));
+    ok(cudaStreamWaitEvent(h->s2, J.ev[0], 0));
+    ok(cudaStreamWaitEvent(J.s3, J.ev[0], 0));
+  }
+  std::vector<int>* idx = J.idx;
+  for (int kind = 0; kind < 3 && rc == SD_OK; ++kind) {
+    const int m = ms[kind];
+    const bool blockV = kind == 0;
+    cudaStream_t s = st[kind];
+    idx[kind].resize(m);
+    int k = 0;
+    if (blockV) {
+      for (int j = 0; j < g.n; ++j)
+        for (int i = 0; i <= g.nx; ++i) idx[kind][k++] = j * g.P + i;
+      for (int j = 0; j <= g.n; ++j)
+        for (int i = 0; i < g.nx; ++i) idx[kind][k++] = (int)(g.ov + (long long)j * g.P + i);
+    } else {
+      const int cx = kind == 2 ? g.nx : g.n;  // pressure Laplacian: the free-flow cells
+      for (int j = 0; j < g.n; ++j)
+        for (int i = 0; i < cx; ++i) idx[kind][k++] = j * g.P + i;
+    }
+    double* X = scratch + off[kind][0];
+    double* Y = scratch + off[kind][1];
+    double* A = scratch + off[kind][2];
+    double* fc = scratch + off[kind][3];
+    ok(cudaMemcpyAsync(idxd[kind], idx[kind].data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
+    ok(cudaMemsetAsync(X, 0, sizeof(double) * stride[kind] * m, s));
+    ok(cudaMemsetAsync(Y, 0, sizeof(double) * stride[kind] * m, s));
+    launch_identity_batch(X, stride[kind], idxd[kind], m, s);
+    Coef<double> c = coef64(h, l, kind == 2);
+    if (blockV) launch_resid_V<double>(c, X, nullptr, Y, 2, m, stride[kind], s);
+    else launch_resid_D<double>(c, X, nullptr, Y, 2, m, stride[kind], s);
+    launch_gather_dense(Y, stride[kind], idxd[kind], m, A, s);
+    launch_gj_inverse(A, Ainv[kind], m, fc, status + kind, status + 3 + kind, s);
+  }
+  return rc;
+}
+
+int coarse_inverses_end(sd_handle* h, InverseJob& J) {
+  int& rc = J.rc;
+  auto ok = [&](cudaError_t e) {
+    if (e != cudaSuccess && rc == SD_OK) rc = SD_E_CUDA;
+    return e == cudaSuccess;
+  };
+  int hs[3] = {0, 0, 0};
+  for (int q = 1; q < 3; ++q) {
+    if (!J.st[q]) continue;
+    ok(cudaEventRecord(J.ev[q], J.st[q]));
+    ok(cudaStreamWaitEvent(h->s, J.ev[q], 0));
+  }
+  if (J.status) ok(cudaMemcpyAsync(hs, J.status, 3 * sizeof(int), cudaMemcpyDeviceToHost, h->s));
+  ok(cudaStreamSynchronize(h->s));
+  for (int q = 0; q < 3; ++q)
+    if (J.ev[q]) cudaEventDestroy(J.ev[q]);
+  if (J.s3) cudaStreamDestroy(J.s3);
+  if (J.scratch) cudaFree(J.scratch);
+  J = InverseJob();
+  if (rc != SD_OK) return rc;
+  for (int kind = 0; kind < 3; ++kind)
+    if (hs[kind] != 0) {
+      snprintf(g_errmsg, sizeof(g_errmsg), "coarsest %s block singular at column %d",
+               kind == 0 ? "velocity" : (kind == 1 ? "Darcy" : "pressure-Laplacian"), hs[kind]);
+      return SD_E_NUMERIC;
+    }
   return SD_OK;
 }
 
@@ -454,15 +592,32 @@ int setup_mg(sd_handle* h, MG<T>& M) {
     launch_convert<T>(C.TxP, L.own.TxP, nx, s);
     launch_convert<T>(C.TyP, L.own.TyP, ny, s);
   }
-  CKR(coarse_inverse(h, 0, M.AinvV, M.idxV, M.mV));
-  CKR(coarse_inverse(h, 1, M.AinvD, M.idxD, M.mD));
-  CKR(coarse_inverse(h, 2, M.AinvP, M.idxP, M.mP));
+  // the coarse inverses (three streams) and the power iterations (a fourth)
+  // are independent: they run at the same time
+  // (the power iterations' stream forks from s before the inverses are queued on it)
+  cudaStream_t sp = nullptr;
+  cudaEvent_t ef = nullptr;
+  int rp = SD_OK;
+  if (cudaStreamCreateWithFlags(&sp, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ef, cudaEventDisableTiming) != cudaSuccess || cudaEventRecord(ef, s) != cudaSuccess ||
+      cudaStreamWaitEvent(sp, ef, 0) != cudaSuccess)
+    rp = SD_E_CUDA;
+  InverseJob job;
+  const int rb = coarse_inverses_begin<T>(h, M, job);
+  std::vector<double> lams;
+  if (rb == SD_OK && rp == SD_OK) {
+    rp = power_lmax_all(h, lams, sp);
+    if (cudaStreamSynchronize(sp) != cudaSuccess && rp == SD_OK) rp = SD_E_CUDA;
+  }
+  if (ef) cudaEventDestroy(ef);
+  if (sp) cudaStreamDestroy(sp);
+  const int re = coarse_inverses_end(h, job);
+  CKR(rb);
+  CKR(re);
+  CKR(rp);
   const int deg = h->opt.cheb_degree;
   for (int l = 0; l + 1 < h->nlev; ++l) {
-    double lv, ld, lp;
-    CKR(power_lmax(h, l, 0, &lv));
-    CKR(power_lmax(h, l, 1, &ld));
-    CKR(power_lmax(h, l, 2, &lp));
+    const double lv = lams[(size_t)3 * l], ld = lams[(size_t)3 * l + 1], lp = lams[(size_t)3 * l + 2];
     const int dl = (l > 0 && h->opt.cheb_degree_coarse > 0) ? h->opt.cheb_degree_coarse : deg;
     const int dp = h->opt.schur_degree > 0 ? h->opt.schur_degree : dl;
     cheb_coeffs<T>(lv, h->opt.cheb_ratio, dl, M.L[l].V.cha, M.L[l].V.chc);
@@ -1561,6 +1716,12 @@ int create_impl(const sd_grid* grid, double mu, const double* K, double alpha, d
   if (!h) return SD_E_NOMEM;
   h->n = n; h->mu = mu; h->alpha = alpha; h->dt = dt; h->opt = o;
   init_layout(h);
+  // the setup's launches use programmatic dependent launch as the steps do
+  struct PdlScope {
+    int prev;
+    explicit PdlScope(int on) : prev(t_pdl) { t_pdl = on; }
+    ~PdlScope() { t_pdl = prev; }
+  } pdl_scope(o.pdl);
   auto fail = [&](int code) { sd_destroy(h); return code; };
   if (o.stream) {
     h->s = (cudaStream_t)o.stream;
@@ -1622,8 +1783,10 @@ int create_impl(const sd_grid* grid, double mu, const double* K, double alpha, d
   }
   int rc = (h->opt.precision == SD_MIXED) ? setup_mg<float>(h, h->mg32) : setup_mg<double>(h, h->mg64);
   if (rc != SD_OK) return fail(rc);
-  // the setup used the Krylov slots as scratch: clear them (padding must be zero)
-  if (cudaMemsetAsync(h->V, 0, sizeof(double) * (h->m + 1) * h->lenA, s) != cudaSuccess) return fail(SD_E_CUDA);
+  // the setup used the Krylov bases as scratch: clear them (padding must be zero)
+  if (cudaMemsetAsync(h->V, 0, sizeof(double) * (h->m + 1) * h->lenA, s) != cudaSuccess ||
+      cudaMemsetAsync(h->Z, 0, sizeof(double) * h->m * h->lenA, s) != cudaSuccess)
+    return fail(SD_E_CUDA);
   if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return fail(SD_E_CUDA);
   h->t = 0.0;
   h->step = 0;

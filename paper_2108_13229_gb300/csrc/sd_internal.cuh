@@ -433,9 +433,9 @@ void launch_step_ctrl(double* flag, double* ctl, int max_iters, double kern, int
 template <typename T>
 void launch_dense_solve(const double* Ainv, const int* idx, int m, const T* b, T* x, cudaStream_t s);
 // Gauss-Jordan inverse with partial pivoting (setup only): A (m x m, destroyed),
-// the inverse in W; fc: m doubles of scratch; *status = 0, or c + 1 for a zero
-// pivot in column c
-void launch_gj_inverse(double* A, double* W, int m, double* fc, int* status, cudaStream_t s);
+// the inverse in W; fc: m doubles of scratch; counter: one int of scratch;
+// *status = 0, or c + 1 for a zero pivot in column c
+void launch_gj_inverse(double* A, double* W, int m, double* fc, int* status, int* counter, cudaStream_t s);
 // identity batch in a padded layout: X[k * stride + idx[k]] = 1
 void launch_identity_batch(double* X, long long stride, const int* idx, int m, cudaStream_t s);
 void launch_gather_dense(const double* Y, long long stride, const int* idx, int m, double* A, cudaStream_t s);

@@ -778,34 +778,40 @@ void launch_dense_solve(const double* Ainv, const int* idx, int m, const T* b, T
 }
 
 // Gauss-Jordan with partial pivoting on [A | I]; the inverse ends in W.
-// Column c takes two launches: k_gj_pivot (one CTA) picks the pivot row (the
-// largest |A[r][c]|, r >= c, the lowest r on ties), swaps it into row c,
-// scales row c and records the elimination factors fc[r] = A[r][c] (0 for
-// r = c); k_gj_eliminate (all SMs) subtracts fc[r] times row c from every
-// other row.  A zero pivot sets *status = c + 1 and the remaining launches
-// do nothing.  (One CTA for the whole elimination serialised 2m^3 FP64
+// Column c: the pivot step picks the pivot row (the largest |A[r][c]|,
+// r >= c, the lowest r on ties), swaps it into row c, scales row c and
+// records the elimination factors fc[r] = A[r][c] (0 for r = c); the
+// elimination (all SMs) subtracts fc[r] times row c from every other row.
+// The pivot step of column c + 1 is done by the last block of column c's
+// elimination to finish (a completion counter, no waiting), so a column takes
+// one launch.  A zero pivot sets *status = c + 1 and the remaining launches do
+// nothing.  (One CTA for the whole elimination serialised 2m^3 FP64
 // operations on one SM: 0.15 s for the 544-row coarsest velocity block.)
-__global__ void k_gj_init(double* W, int m, int* status) {
+__global__ void k_gj_init(double* W, int m, int* status, int* counter) {
   griddep_wait();
   const long long mm = (long long)m * m;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < mm; e += (long long)gridDim.x * blockDim.x)
     W[e] = ((e / m) == (e % m)) ? 1.0 : 0.0;
-  if (blockIdx.x == 0 && threadIdx.x == 0) *status = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *status = 0;
+    *counter = 0;
+  }
 }
 
-__global__ void __launch_bounds__(1024) k_gj_pivot(double* A, double* W, int m, int c, double* fc, int* status) {
-  griddep_wait();
+// the pivot step of column c by the calling block (any multiple of 32 threads
+// up to 1024).  Its reads of A and W bypass L1 (ld.global.cg): called at the
+// end of an elimination, it reads rows that other blocks have just written.
+__device__ void gj_pivot_step(double* A, double* W, int m, int c, double* fc, int* status) {
   __shared__ double sbest[32];
   __shared__ int srow[32];
   __shared__ int piv;
   __shared__ double pval;
-  if (*status != 0) return;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
   // strided scan in increasing r keeps the first maximum, as does the tree
   double best = -1.0;
   int br = m;
   for (int r = c + tid; r < m; r += nt) {
-    const double a = fabs(A[(long long)r * m + c]);
+    const double a = fabs(__ldcg(&A[(long long)r * m + c]));
     if (a > best) { best = a; br = r; }
   }
 #pragma unroll
@@ -830,23 +836,34 @@ __global__ void __launch_bounds__(1024) k_gj_pivot(double* A, double* W, int m, 
   const int p = piv;
   if (p != c)
     for (int q = tid; q < m; q += nt) {
-      double t = A[(long long)c * m + q]; A[(long long)c * m + q] = A[(long long)p * m + q]; A[(long long)p * m + q] = t;
-      t = W[(long long)c * m + q]; W[(long long)c * m + q] = W[(long long)p * m + q]; W[(long long)p * m + q] = t;
+      const double ac = __ldcg(&A[(long long)c * m + q]), ap = __ldcg(&A[(long long)p * m + q]);
+      A[(long long)c * m + q] = ap;
+      A[(long long)p * m + q] = ac;
+      const double wc = __ldcg(&W[(long long)c * m + q]), wp = __ldcg(&W[(long long)p * m + q]);
+      W[(long long)c * m + q] = wp;
+      W[(long long)p * m + q] = wc;
     }
   __syncthreads();
-  const double inv = 1.0 / A[(long long)c * m + c];
+  const double inv = 1.0 / __ldcg(&A[(long long)c * m + c]);
   __syncthreads();
   for (int q = tid; q < m; q += nt) {
-    A[(long long)c * m + q] *= inv;
-    W[(long long)c * m + q] *= inv;
+    A[(long long)c * m + q] = __ldcg(&A[(long long)c * m + q]) * inv;
+    W[(long long)c * m + q] = __ldcg(&W[(long long)c * m + q]) * inv;
   }
-  for (int r = tid; r < m; r += nt) fc[r] = (r == c) ? 0.0 : A[(long long)r * m + c];
+  __syncthreads();
+  for (int r = tid; r < m; r += nt) fc[r] = (r == c) ? 0.0 : __ldcg(&A[(long long)r * m + c]);
 }
 
-__global__ void k_gj_eliminate(double* A, double* W, int m, int c, const double* __restrict__ fc,
-                               const int* status) {
+__global__ void __launch_bounds__(1024) k_gj_pivot(double* A, double* W, int m, int c, double* fc, int* status) {
   griddep_wait();
   if (*status != 0) return;
+  gj_pivot_step(A, W, m, c, fc, status);
+}
+
+__global__ void __launch_bounds__(256) k_gj_eliminate(double* A, double* W, int m, int c, double* fc, int* status,
+                                                      int* counter) {
+  griddep_wait();
+  if (*status != 0) return;  // uniform: no block goes on, none counts
   const long long mm = (long long)m * m;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < mm; e += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(e / m), q = (int)(e % m);
@@ -856,17 +873,28 @@ __global__ void k_gj_eliminate(double* A, double* W, int m, int c, const double*
       W[e] -= f * W[(long long)c * m + q];
     }
   }
+  // the last block to finish takes the pivot step of the next column
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int done = atomicAdd(counter, 1);
+    last = done == (int)gridDim.x - 1;
+    if (last) *counter = 0;
+  }
+  __syncthreads();
+  if (!last || c + 1 >= m) return;
+  __threadfence();
+  gj_pivot_step(A, W, m, c + 1, fc, status);
 }
 
-void launch_gj_inverse(double* A, double* W, int m, double* fc, int* status, cudaStream_t s) {
+void launch_gj_inverse(double* A, double* W, int m, double* fc, int* status, int* counter, cudaStream_t s) {
   const long long mm = (long long)m * m;
   const int nb = (int)std::min<long long>((mm + 255) / 256, 152 * 8);
-  SD_COUNT(1 + 2 * m);
-  launch_k(k_gj_init, dim3(nb), dim3(256), 0, s, W, m, status);
-  for (int c = 0; c < m; ++c) {
-    launch_k(k_gj_pivot, dim3(1), dim3(1024), 0, s, A, W, m, c, fc, status);
-    launch_k(k_gj_eliminate, dim3(nb), dim3(256), 0, s, A, W, m, c, (const double*)fc, (const int*)status);
-  }
+  SD_COUNT(2 + m);
+  launch_k(k_gj_init, dim3(nb), dim3(256), 0, s, W, m, status, counter);
+  launch_k(k_gj_pivot, dim3(1), dim3(1024), 0, s, A, W, m, 0, fc, status);
+  for (int c = 0; c < m; ++c) launch_k(k_gj_eliminate, dim3(nb), dim3(256), 0, s, A, W, m, c, fc, status, counter);
 }
 
 __global__ void k_identity_batch(double* X, long long stride, const int* idx, int m) {

@@ -361,9 +361,10 @@ void cheb_coeffs(double lmax, double ratio, int deg, std::vector<T>& a, std::vec
 // Laplacian; the coarsest level has none).  The chains run in rounds: one
 // iteration of every unconverged chain is queued, then one read-back decides
 // which go on, so a setup waits on the host once per round rather than once
-// per iteration of every chain.  Each chain has its own vectors (the Krylov
-// bases are free during setup) and does the arithmetic of a chain run alone,
-// in the same order.
+// per iteration of every chain.  The chains of each block kind run on their
+// own stream (s and two forked from it), with their own reduction scratch.
+// Each chain has its own vectors (the Krylov bases are free during setup) and
+// does the arithmetic of a chain run alone, in the same order.
 int power_lmax_all(sd_handle* h, std::vector<double>& lam, cudaStream_t s) {
   struct Chain {
     int l, kind;
@@ -392,8 +393,35 @@ int power_lmax_all(sd_handle* h, std::vector<double>& lam, cudaStream_t s) {
   // the Krylov bases V (m + 1 slots) and Z (m slots) as one pool of vectors;
   // the norms go to scal[0 .. 64) (no solve runs during setup)
   const long long vcap = (long long)(h->m + 1) * h->lenA, zcap = (long long)h->m * h->lenA;
+  // stream k's dot partials go to partial + k nblk (partial holds 32 nblk doubles)
+  cudaStream_t ks[3] = {s, nullptr, nullptr};
+  cudaEvent_t kev[3] = {nullptr, nullptr, nullptr};
+  int rc = SD_OK;
+  for (int k = 0; k < 3 && rc == SD_OK; ++k)
+    if (cudaEventCreateWithFlags(&kev[k], cudaEventDisableTiming) != cudaSuccess) rc = SD_E_CUDA;
+  for (int k = 1; k < 3 && rc == SD_OK; ++k)
+    if (cudaStreamCreateWithFlags(&ks[k], cudaStreamNonBlocking) != cudaSuccess) rc = SD_E_CUDA;
+  if (rc == SD_OK && cudaEventRecord(kev[0], s) != cudaSuccess) rc = SD_E_CUDA;
+  for (int k = 1; k < 3 && rc == SD_OK; ++k)
+    if (cudaStreamWaitEvent(ks[k], kev[0], 0) != cudaSuccess) rc = SD_E_CUDA;
+  auto join = [&]() {  // streams 1 and 2 into s
+    for (int k = 1; k < 3; ++k)
+      if (ks[k] && (cudaEventRecord(kev[k], ks[k]) != cudaSuccess || cudaStreamWaitEvent(s, kev[k], 0) != cudaSuccess))
+        rc = SD_E_CUDA;
+  };
+  auto cleanup = [&]() {
+    for (int k = 0; k < 3; ++k) {
+      if (kev[k]) cudaEventDestroy(kev[k]);
+      if (k > 0 && ks[k]) cudaStreamDestroy(ks[k]);
+    }
+  };
+  if (rc != SD_OK) {
+    join();
+    cleanup();
+    return rc;
+  }
   size_t next = 0;
-  while (next < all.size()) {
+  while (next < all.size() && rc == SD_OK) {
     // as many chains as the two bases hold (each needs x and y; a chain of
     // the finest velocity block fits in V alone, whatever m)
     std::vector<Chain*> grp;
@@ -408,6 +436,8 @@ int power_lmax_all(sd_handle* h, std::vector<double>& lam, cudaStream_t s) {
         base = h->Z + zused;
         zused += need;
       } else if (grp.empty()) {
+        join();
+        cleanup();
         return SD_E_NOMEM;
       } else {
         break;
@@ -418,31 +448,39 @@ int power_lmax_all(sd_handle* h, std::vector<double>& lam, cudaStream_t s) {
       grp.push_back(&ch);
     }
     auto apply = [&](Chain& ch, const double* in, double* o) {
-      if (ch.kind == 0) launch_resid_V<double>(ch.c, in, nullptr, o, 1, 1, 0, s);
-      else launch_resid_D<double>(ch.c, in, nullptr, o, 1, 1, 0, s);
+      if (ch.kind == 0) launch_resid_V<double>(ch.c, in, nullptr, o, 1, 1, 0, ks[0]);
+      else launch_resid_D<double>(ch.c, in, nullptr, o, 1, 1, 0, ks[ch.kind]);
     };
     int q0 = 0;
     for (Chain* ch : grp) {
-      CK(cudaMemsetAsync(ch->y, 0, sizeof(double) * ch->len, s));
-      launch_hash_fill(ch->x, ch->len, 1234u + (unsigned)ch->l, s);
+      cudaStream_t sk = ks[ch->kind];
+      if (cudaMemsetAsync(ch->y, 0, sizeof(double) * ch->len, sk) != cudaSuccess) rc = SD_E_CUDA;
+      launch_hash_fill(ch->x, ch->len, 1234u + (unsigned)ch->l, sk);
       apply(*ch, ch->x, ch->y);  // y has zero padding from here on
-      launch_dot(ch->y, ch->y, ch->len, h->partial, reduce_blocks(ch->len), h->scal + q0++, s);
+      launch_dot(ch->y, ch->y, ch->len, h->partial + (long long)ch->kind * h->nblk, reduce_blocks(ch->len),
+                 h->scal + q0++, sk);
     }
-    for (int it = 0; it < 25; ++it) {
+    for (int it = 0; it < 25 && rc == SD_OK; ++it) {
       int q = 0;
       for (Chain* ch : grp) {
         const int slot = q++;
         if (ch->done) continue;
         const int nb = reduce_blocks(ch->len);
+        cudaStream_t sk = ks[ch->kind];
         // the slot holds ||y||^2 of this y from the end of the previous
         // iteration (or the start): the same kernel on the same vector
-        launch_scale_by(ch->y, ch->x, ch->len, h->scal + slot, 1, s);
+        launch_scale_by(ch->y, ch->x, ch->len, h->scal + slot, 1, sk);
         apply(*ch, ch->x, ch->y);
-        launch_dot(ch->y, ch->y, ch->len, h->partial, nb, h->scal + slot, s);
+        launch_dot(ch->y, ch->y, ch->len, h->partial + (long long)ch->kind * h->nblk, nb, h->scal + slot, sk);
       }
+      join();
       std::vector<double> nrm(grp.size());
-      CK(cudaMemcpyAsync(nrm.data(), h->scal, sizeof(double) * grp.size(), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
+      if (cudaMemcpyAsync(nrm.data(), h->scal, sizeof(double) * grp.size(), cudaMemcpyDeviceToHost, s) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) {
+        rc = SD_E_CUDA;
+        break;
+      }
       bool any = false;
       q = 0;
       for (Chain* ch : grp) {
@@ -456,7 +494,9 @@ int power_lmax_all(sd_handle* h, std::vector<double>& lam, cudaStream_t s) {
     }
     for (Chain* ch : grp) lam[(size_t)3 * ch->l + ch->kind] = ch->lam;
   }
-  return SD_OK;
+  join();
+  cleanup();
+  return rc;
 }
 
 // Dense inverses of the coarsest V, D' and pressure-Laplacian blocks: apply

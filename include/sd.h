@@ -111,8 +111,9 @@ extern "C" {
                    layout [u | v | p_ff | p_pm] with u (3n+1) x n, v 3n x
                    (n+1), p_ff 3n x n and p_pm n x n, x fastest.  The channel
                    runs the monolithic coupling only, smooths in shared-memory
-                   tiles for tile 1 and 2 (no register-column tiles, no fused
-                   coarse cycle: fuse_coarse does not apply), and coarsens to
+                   tiles for tile 1 and 2 (register-column tiles, tile 2, for
+                   its Darcy block only; no fused coarse cycle: fuse_coarse
+                   does not apply), and coarsens to
                    at most 8 x 8 porous-medium cells (coarsest above 8 counts
                    as 8), so n = m 2^k needs m <= 8. */
 #define SD_GEO_SQUARE 0

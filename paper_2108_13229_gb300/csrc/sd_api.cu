@@ -823,8 +823,7 @@ int tile_rows_of(const sd_handle* h, int n) {
 #define SD_WAVE_MIN_N 1024
 #endif
 int wave_rows_of(const sd_handle* h, int n) {
-  // (the register-column tiles serve the square geometry)
-  if (h->opt.tile != 2 || n < SD_WAVE_MIN_N || h->g.iw != 0) return 0;
+  if (h->opt.tile != 2 || n < SD_WAVE_MIN_N) return 0;
   if (h->opt.tile_rows) return h->opt.tile_rows >= 8 ? 8 : 4;
   return 4;
 }

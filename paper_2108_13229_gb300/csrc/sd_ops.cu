@@ -1406,8 +1406,10 @@ int launch_tile_D_rows(const Coef<T>& c, const T* x_in, const T* b, T* x_out, co
 template <typename T>
 int launch_smooth_tile_D(const Coef<T>& c, const T* x_in, const T* b, T* x_out, const ChebSteps<T>& cs,
                          const T* ct, const T* ec, int nc, int Pc, cudaStream_t s) {
+  // (the register-column tiles take blocks of n x n cells: the Darcy block,
+  // and the pressure Laplacian of the square geometry)
   if constexpr (std::is_same<T, float>::value)
-    if (cs.wave) return launch_wave_D(c, x_in, b, x_out, cs, ct, ec, nc, Pc, s);
+    if (cs.wave && c.cx == c.n) return launch_wave_D(c, x_in, b, x_out, cs, ct, ec, nc, Pc, s);
   if (cs.rows == 4) return launch_tile_D_rows<T, 4, false>(c, x_in, b, x_out, cs, ct, ec, nc, Pc, nullptr, s);
   return cs.rows == 8 ? launch_tile_D_rows<T, 8, false>(c, x_in, b, x_out, cs, ct, ec, nc, Pc, nullptr, s)
                       : launch_tile_D_rows<T, 16, false>(c, x_in, b, x_out, cs, ct, ec, nc, Pc, nullptr, s);

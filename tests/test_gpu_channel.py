@@ -201,12 +201,12 @@ def test_channel_options(sd):
         make(sd, 18, 1.0, np.ones((18, 18)), 1.0, 0.1)
 
 
-@pytest.mark.parametrize("bc", [0, 2])
-@pytest.mark.parametrize("n", [64, 256, 512])
+@pytest.mark.parametrize("n,bc", [(64, 0), (64, 2), (256, 0), (256, 2), (512, 0), (512, 2), (1024, 2)])
 def test_channel_tiled_smoothing_bitwise(sd, n, bc):
     # the shared-memory tiles (with the residual and restriction fused into the
-    # pre-smoothing on levels up to 256 cells per side) against one launch per
-    # Chebyshev step: the same bits, over tile heights 4, 8 and 16
+    # pre-smoothing on levels up to 256 cells per side) and, with tile 2 from
+    # 1024 cells per side, the register-column tiles of the Darcy block, against
+    # one launch per Chebyshev step: the same bits, over tile heights 4, 8 and 16
     K = I.lognormal_K(n, -4.0, 1.0, 16.0, seed=5)
     xs = []
     for tile, rows in ((0, 0), (1, 4), (1, 8), (2, 16), (2, 0)):

@@ -1090,7 +1090,7 @@ __device__ __forceinline__ T prolong_D_sm(const T* __restrict__ s, int CX, int I
 // 2 x 2 children of each coarse cell it covers into bco (nc x nc, pitch Pc):
 // k_resid_restrict_D's work and arithmetic, without its launch.
 template <typename T, int NS, int TLY, bool BT, bool RR = false>
-__global__ void __launch_bounds__(TLT) k_smooth_tile_D(Coef<T> c, const T* __restrict__ xin,
+__global__ void __launch_bounds__(TLT, TLY <= 8 ? 8 : 4) k_smooth_tile_D(Coef<T> c, const T* __restrict__ xin,
                                                        const T* __restrict__ b, T* __restrict__ xout,
                                                        ChebSteps<T> cs, const T* __restrict__ ct,
                                                        const T* __restrict__ ec, int nc, int Pc,
@@ -1212,7 +1212,7 @@ __global__ void __launch_bounds__(TLT) k_smooth_tile_D(Coef<T> c, const T* __res
 // with their launches and the residual's round trip through memory, the same
 // arithmetic per point.
 template <typename T, int NS, int TLY, bool BT, bool RR = false>
-__global__ void __launch_bounds__(TLT) k_smooth_tile_V(Coef<T> c, const T* __restrict__ xin,
+__global__ void __launch_bounds__(TLT, TLY <= 8 ? 8 : 4) k_smooth_tile_V(Coef<T> c, const T* __restrict__ xin,
                                                        const T* __restrict__ b, T* __restrict__ xout,
                                                        ChebSteps<T> cs, const T* __restrict__ ct,
                                                        const T* __restrict__ ec, int nc, int Pc,

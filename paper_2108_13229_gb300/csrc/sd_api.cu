@@ -77,11 +77,14 @@ struct Block {
 };
 
 // Coefficient arrays of one level (the Darcy set from K, the pressure
-// Laplacian set from a unit permeability).
+// Laplacian set from a unit permeability).  TyR (FP64 sets only): Ty of the
+// preconditioner's Darcy block, whose top faces may carry the interface's
+// Schur correction (sd_options.darcy_schur); the operator reads Ty.
 template <typename T>
 struct LevelCoef {
   T *w = nullptr, *rg = nullptr, *Tx = nullptr, *Ty = nullptr;
   T *wP = nullptr, *rgP = nullptr, *TxP = nullptr, *TyP = nullptr;
+  T* TyR = nullptr;
 };
 
 template <typename T>
@@ -260,6 +263,7 @@ void plan_all(sd_handle* h) {
     const Geom& g = h->geo[l];
     h->Klev[l] = a.take<double>((long long)g.n * g.P);
     take_coef<double>(a, g, h->c64[l]);
+    h->c64[l].TyR = a.take<double>((long long)(g.n + 1) * g.P);
   }
   const long long len = h->g.len;
   h->x = a.take<double>(len);
@@ -300,6 +304,7 @@ void plan_all(sd_handle* h) {
   else plan_mg<double>(h, h->mg64, false);
 }
 
+// the operator's coefficients of level l (poisson: the pressure-Laplacian set)
 Coef<double> coef64(sd_handle* h, int l, bool poisson = false) {
   const Geom& g = h->geo[l];
   LevelCoef<double>& C = h->c64[l];
@@ -312,6 +317,15 @@ Coef<double> coef64(sd_handle* h, int l, bool poisson = false) {
   c.Tx = poisson ? C.TxP : C.Tx;
   c.Ty = poisson ? C.TyP : C.Ty;
   finish_coef(c);
+  return c;
+}
+
+// the coefficients the multigrid of block kind (0 V, 1 D', 2 pressure
+// Laplacian) smooths with: the operator's, with the Darcy block's Ty replaced
+// by TyR (the velocity block reads no Ty)
+Coef<double> coef64_mg(sd_handle* h, int l, int kind) {
+  Coef<double> c = coef64(h, l, kind == 2);
+  if (kind != 2) c.Ty = h->c64[l].TyR;
   return c;
 }
 
@@ -334,8 +348,8 @@ void bind_coef(sd_handle* h, MG<T>& M) {
 template <>
 void bind_coef<double>(sd_handle* h, MG<double>& M) {
   for (int l = 0; l < h->nlev; ++l) {
-    M.L[l].c = coef64(h, l, false);
-    M.L[l].cP = coef64(h, l, true);
+    M.L[l].c = coef64_mg(h, l, 0);
+    M.L[l].cP = coef64_mg(h, l, 2);
   }
 }
 
@@ -384,7 +398,7 @@ int power_lmax_all(sd_handle* h, std::vector<double>& lam, cudaStream_t s) {
       ch.l = l;
       ch.kind = kind;
       ch.len = kind == 0 ? g.lenV : g.lenD;
-      ch.c = coef64(h, l, kind == 2);
+      ch.c = coef64_mg(h, l, kind);
       ch.x = ch.y = nullptr;
       ch.lam = 0.0;
       ch.done = false;
@@ -576,7 +590,7 @@ int coarse_inverses_begin(sd_handle* h, MG<T>& M, InverseJob& J) {
     ok(cudaMemsetAsync(X, 0, sizeof(double) * stride[kind] * m, s));
     ok(cudaMemsetAsync(Y, 0, sizeof(double) * stride[kind] * m, s));
     launch_identity_batch(X, stride[kind], idxd[kind], m, s);
-    Coef<double> c = coef64(h, l, kind == 2);
+    Coef<double> c = coef64_mg(h, l, kind);
     if (blockV) launch_resid_V<double>(c, X, nullptr, Y, 2, m, stride[kind], s);
     else launch_resid_D<double>(c, X, nullptr, Y, 2, m, stride[kind], s);
     launch_gather_dense(Y, stride[kind], idxd[kind], m, A, s);
@@ -626,7 +640,7 @@ int setup_mg(sd_handle* h, MG<T>& M) {
     launch_convert<T>(C.w, L.own.w, L.g.nx + 1, s);
     launch_convert<T>(C.rg, L.own.rg, L.g.nx + 1, s);
     launch_convert<T>(C.Tx, L.own.Tx, nx, s);
-    launch_convert<T>(C.Ty, L.own.Ty, ny, s);
+    launch_convert<T>(C.TyR, L.own.Ty, ny, s);
     launch_convert<T>(C.wP, L.own.wP, L.g.nx + 1, s);
     launch_convert<T>(C.rgP, L.own.rgP, L.g.nx + 1, s);
     launch_convert<T>(C.TxP, L.own.TxP, nx, s);
@@ -1713,6 +1727,7 @@ int validate(const sd_grid* grid, double mu, double alpha, double dt, const sd_o
   if (o->cheb_degree_coarse < 0 || o->cheb_degree_coarse > 8 || o->schur_degree < 0 || o->schur_degree > 8)
     return SD_E_INVAL;
   if (o->geometry != SD_GEO_SQUARE && o->geometry != SD_GEO_CHANNEL) return SD_E_INVAL;
+  if (o->darcy_schur < 0 || o->darcy_schur > 1) return SD_E_INVAL;
   // the channel runs the monolithic coupling only
   if (o->geometry == SD_GEO_CHANNEL && o->coupling != SD_MONOLITHIC) return SD_E_INVAL;
   int n = grid->nx, L = level_count(n, coarsest_of(*o));
@@ -1801,6 +1816,12 @@ int create_impl(const sd_grid* grid, double mu, const double* K, double alpha, d
     const Geom& g = h->geo[l];
     launch_setup_coef<double>(h->Klev[l], g.n, g.n, g.P, mu, alpha, lat, 0, 0, g.n, g.nx, g.iw, C.w, C.rg, C.Tx,
                               C.Ty, s);
+    // the preconditioner's Darcy block: Ty, with the interface's Schur
+    // correction on the top faces in the monolithic solve
+    if (cudaMemcpyAsync(C.TyR, C.Ty, sizeof(double) * (g.n + 1) * g.P, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return fail(SD_E_CUDA);
+    if (o.darcy_schur && o.coupling == SD_MONOLITHIC)
+      launch_darcy_schur_top(C.TyR, C.w, C.rg, g.n, g.nx, g.iw, g.P, mu, g.h * g.h / dt, g.h, lat, s);
   }
   // pressure Laplacian B^T B / h^2 over the free-flow cells: TPFA with K / mu
   // = 1 (the Krylov slots hold the unit permeability, free during setup); its
@@ -1863,7 +1884,8 @@ bool can_lockstep(const sd_handle* a, const sd_handle* b) {
                         x.reorth_eta == y.reorth_eta && x.extrapolate == y.extrapolate && x.graph == y.graph &&
                         x.pdl == y.pdl && x.tile == y.tile && x.tile_rows == y.tile_rows &&
                         x.darcy_coupled == y.darcy_coupled && x.bc_dp == y.bc_dp && x.bc_tend == y.bc_tend &&
-                        x.geometry == y.geometry && x.coupling == SD_MONOLITHIC &&
+                        x.geometry == y.geometry && x.darcy_schur == y.darcy_schur &&
+                        x.coupling == SD_MONOLITHIC &&
                         y.coupling == SD_MONOLITHIC;
   return same_opt && a->n == b->n && a->mu == b->mu && a->dt == b->dt && a->ar.off == b->ar.off &&
          a->nlev == b->nlev && a->prof_id < 0 && b->prof_id < 0;
@@ -2149,6 +2171,7 @@ void sd_options_default(sd_options* o) {
   o->schur_mass = 1;
   o->stream = nullptr;
   o->geometry = SD_GEO_SQUARE;
+  o->darcy_schur = 1;
 }
 
 int64_t sd_dof_count(int32_t n) { return 4 * (int64_t)n * n + 2 * (int64_t)n; }

@@ -198,6 +198,12 @@ void launch_setup_coef(const double* Kp, int n, int cx, int P, double mu, double
                        int b1, int nx, int iw, T* w, T* rg, T* Tx, T* Ty, cudaStream_t s);
 template <typename T>
 void launch_convert(const double* src, T* dst, long long len, cudaStream_t s);
+// top faces (row n) of the preconditioner's Darcy coefficients TyR: h^2 / d_i,
+// d_i the diagonal of the v_Gamma row of floor face iw + i (Eq. (5)), the
+// local Schur complement of the interface velocity eliminated through B'_1
+// and C'_1 (nx: free-flow cells across; lat: traction sides)
+void launch_darcy_schur_top(double* TyR, const double* w, const double* rg, int n, int nx, int iw, int P, double mu,
+                            double cm, double h, int lat, cudaStream_t s);
 
 // whole-system operator (FP64): y = A x  or  y = b - A x
 void launch_apply_full(const Coef<double>& c, const double* x, const double* b, double* y, cudaStream_t s);

@@ -1966,6 +1966,33 @@ void launch_setup_coef(const double* Kp, int n, int cx, int P, double mu, double
            b1, nx, iw, w, rg, Tx, Ty);
 }
 
+// The Darcy rows of the cells below Gamma carry + h v_Gamma (C'_1) and the
+// v_Gamma rows - h p_pm (B'_1); eliminating v_Gamma with the diagonal d of its
+// row adds h^2 / d to those Darcy rows' diagonal.  In the cell rows a top-face
+// coefficient enters the diagonal alone (the face above row n - 1 has no
+// neighbour), so the correction is stored as that coefficient.  d is the
+// v_Gamma row's diagonal as the velocity block forms it.
+__global__ void k_darcy_schur_top(double* __restrict__ TyR, const double* __restrict__ w,
+                                  const double* __restrict__ rg, int n, int nx, int iw, int P, double mu, double cm,
+                                  double h, int lat) {
+  griddep_wait();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int f = iw + i;
+  const bool left = f == 0, right = f == nx - 1;
+  const double wl = (left && !lat) ? 0.0 : w[f], wr = (right && !lat) ? 0.0 : w[f + 1];
+  double d = 0.5 * cm + 2.0 * mu + rg[f];
+  d += left ? (lat ? h * wl : mu) : 0.5 * h * wl;
+  d += right ? (lat ? h * wr : mu) : 0.5 * h * wr;
+  TyR[(long long)n * P + i] = h * h / d;
+}
+
+void launch_darcy_schur_top(double* TyR, const double* w, const double* rg, int n, int nx, int iw, int P, double mu,
+                            double cm, double h, int lat, cudaStream_t s) {
+  SD_COUNT(1);
+  launch_k(k_darcy_schur_top, dim3((n + 127) / 128), dim3(128), 0, s, TyR, w, rg, n, nx, iw, P, mu, cm, h, lat);
+}
+
 template <typename T>
 __global__ void k_convert(const double* __restrict__ a, T* __restrict__ b, long long len, Bat bt) {
   griddep_wait();

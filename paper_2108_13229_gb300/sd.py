@@ -54,7 +54,7 @@ class sd_options(ctypes.Structure):
                 ("coupling_eps", ctypes.c_double), ("coupling_omega", ctypes.c_double),
                 ("coupling_order", ctypes.c_int32), ("coupling_rtol", ctypes.c_double),
                 ("bc_dp", ctypes.c_double), ("bc_tend", ctypes.c_double),
-                ("stream", ctypes.c_void_p), ("geometry", ctypes.c_int32)]
+                ("stream", ctypes.c_void_p), ("geometry", ctypes.c_int32), ("darcy_schur", ctypes.c_int32)]
 
 
 class sd_step_info(ctypes.Structure):

@@ -611,6 +611,28 @@ def test_pressure_driven_problem(sd, precision, n):
         assert e <= 1e-8, (k, e)
 
 
+@pytest.mark.parametrize("geometry", [0, 1])
+def test_darcy_schur_block_at_paper_parameters(sd, geometry):
+    # the paper's own parameters (Sec. 5: K = 1e-6, mu = 1e-3, dt = 2e5, quasi-steady): the preconditioner's
+    # Darcy block with the interface's Schur correction (darcy_schur = 1, the default) and without it reach
+    # the oracle's states alike (the operator is the same), and the correction cuts the iterations
+    n, dt = 32, 2e5
+    K = np.full((n, n), 1e-6)
+    o = O.Oracle(n, 1e-3, 1.0, dt, K, bc=2, dp=1e-9, t_end=50e5, geo=geometry)
+    xr = o.run(np.zeros(o.ndof), 0.0, 4)
+    its = {}
+    for ds in (1, 0):
+        h = make(sd, n, 1e-3, K, 1.0, dt, 1, rtol=1e-12, bc=2, bc_dp=1e-9, bc_tend=50e5, darcy_schur=ds,
+                 geometry=geometry)
+        infos = sd.sd_step(h, 4)
+        assert all(i["status"] == 0 for i in infos)
+        its[ds] = sum(i["iters"] for i in infos)
+        fs, fr = O.split(sd.sd_get_state(h)[2], n, geometry), O.split(xr, n, geometry)
+        for k in fs:
+            assert rel(fs[k], fr[k]) <= 1e-8, (ds, k)
+    assert its[1] <= 0.7 * its[0], its
+
+
 def test_pressure_driven_partitioned(sd):
     # the partitioned coupling of Sec. 3 on the paper's problem
     n = 32

@@ -283,19 +283,21 @@ def step_model_bytes(n: int, info: dict, mixed: bool, coarsest: int = 16) -> flo
     return total + v8  # per-block residual norms
 
 
-def bench_batch(sd, count: int, steps: int, threads: int, seed: int = 0, lockstep: bool = True):
+def bench_batch(sd, count: int, steps: int, threads: int, seed: int = 0, lockstep: bool = True, graph: bool = False):
     """Independent instances with uneven grids advanced together by sd_solve_batch: instances of one grid size
-    run in lockstep (one launch serves the whole group), groups concurrently on their own streams."""
+    run in lockstep (one launch serves the whole group), groups concurrently on their own streams; graph: every
+    step's solves of all groups as one graph launch, decided on the device (SD_BATCH_GRAPH)."""
     from paper_2108_13229_gb300 import inputs as I
     wls = I.batch_instances(count, seed=seed, steps=steps)
     hs = []
     for wl in wls:
         o = sd.sd_options_default()
         hs.append(sd.sd_create(wl.n, wl.mu, wl.K(), wl.alpha, wl.dt, o))
-    sd.sd_solve_batch(hs, [3] * count, max_threads=threads, lockstep=lockstep)  # warm-up (graph captures)
+    flags = (sd.SD_BATCH_LOCKSTEP if lockstep else 0) | (sd.SD_BATCH_GRAPH if graph else 0)
+    sd.sd_solve_batch_ex(hs, [3] * count, max_threads=threads, flags=flags)  # warm-up (graph captures)
     l0 = sd.sd_launch_count()
     t0 = time.perf_counter()
-    infos = sd.sd_solve_batch(hs, [steps] * count, max_threads=threads, lockstep=lockstep)
+    infos = sd.sd_solve_batch_ex(hs, [steps] * count, max_threads=threads, flags=flags)
     el = time.perf_counter() - t0
     launches = sd.sd_launch_count() - l0
     dof = sum(wl.dof for wl in wls)
@@ -303,7 +305,8 @@ def bench_batch(sd, count: int, steps: int, threads: int, seed: int = 0, lockste
     for h in hs:
         sd.sd_destroy(h)
     return {"value": dof * steps / el, "unit": UNIT, "instances": count, "steps_each": steps, "threads": threads,
-            "mode": "lockstep groups by grid size" if lockstep else "one stream and host thread per instance",
+            "mode": ("all groups' solves of a step in one graph launch, decided on the device" if graph else
+                     "lockstep groups by grid size" if lockstep else "one stream and host thread per instance"),
             "seconds": el, "total_dof": dof, "grids": sorted(set(wl.n for wl in wls)), "gpu_launches": launches,
             "iters_per_step_mean": float(np.mean(its)), "max_relres": max(i["relres"] for inf in infos for i in inf)}
 
@@ -502,6 +505,7 @@ def bench_ours(args, ws, rank, local):
                                     "channel_256": bench_paper_parameters(sd, torch, stream, 256, 1)}
         line["batch"] = bench_batch(sd, 256, 10, 32, seed=rank)
         line["batch"]["per_instance_streams"] = bench_batch(sd, 256, 10, 32, seed=rank, lockstep=False)
+        line["batch"]["one_graph_per_step"] = bench_batch(sd, 256, 10, 32, seed=rank, graph=True)
         line["serving"] = [bench_serve(sd, rate, 60, 16) for rate in (20.0, 100.0, 500.0)]
 
         if rank == 0 and ws >= 1 and not args.no_cpu:

@@ -402,8 +402,19 @@ void sd_destroy(sd_handle *h);
  * SD_E_INVAL, before any work, for a NULL handle, a negative nsteps or a
  * handle listed twice.
  * sd_solve_batch_ex with flags = 0 runs every instance on its own stream
- * and host thread instead (no lockstep groups). */
+ * and host thread instead (no lockstep groups).  With SD_BATCH_GRAPH (and
+ * SD_BATCH_LOCKSTEP) the solves of a time step of ALL groups, whatever their
+ * grid sizes, run as one CUDA graph launched once per step: each group is a
+ * branch of the graph whose restart loop (WHILE node) and Arnoldi steps (IF
+ * nodes) are decided on the device, per instance, with the decisions of the
+ * host-driven groups on the same values, so no host round trip happens
+ * inside a solve and every result stays bitwise that of the run alone; the
+ * right-hand sides are launched per group before it.  Every handle then has
+ * to be able to join a group (SD_MONOLITHIC coupling, no sd_profile); the
+ * graph is built again whenever the set of groups that still step changes,
+ * and the handles' graph option does not apply. */
 #define SD_BATCH_LOCKSTEP 1
+#define SD_BATCH_GRAPH 2
 int sd_solve_batch(sd_handle *const *hs, int32_t count, const int32_t *nsteps, sd_step_info *const *infos,
                    int32_t max_threads);
 int sd_solve_batch_ex(sd_handle *const *hs, int32_t count, const int32_t *nsteps, sd_step_info *const *infos,

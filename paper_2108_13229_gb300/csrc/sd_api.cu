@@ -2071,6 +2071,172 @@ int fgmres_lockstep(Lockstep& L, std::vector<sd_step_info>& si) {
   return SD_OK;
 }
 
+// ------------------------------------- lockstep groups as one graph
+// The launches of the calling host thread serve no batch (the group control
+// kernels are single CTAs over all instances, the right-hand sides are
+// single-instance launches).
+struct NoBatScope {
+  Bat saved;
+  int saved_n;
+  NoBatScope() : saved(t_bat), saved_n(t_bat_n) {
+    t_bat.off = nullptr;
+    t_bat.act = nullptr;
+    t_bat_n = 1;
+  }
+  ~NoBatScope() {
+    t_bat = saved;
+    t_bat_n = saved_n;
+  }
+};
+
+// One lockstep group's whole FGMRES solve as a branch of graph `top`: the
+// steps of fgmres_lockstep with its host decisions taken by the k_grp_*
+// kernels (the same values, the same order), a WHILE node over restart
+// cycles and IF nodes over the Arnoldi steps of a cycle.  pre: the kernels
+// outside the loops (those inside are counted on the device, instance 0's
+// C_KERN).
+int build_group_branch(Lockstep& L, cudaGraph_t top, long long* pre) {
+  sd_handle* h = L.hs[0];
+  cudaStream_t s = h->s;
+  const long long len = h->g.len, vs = h->lenA;
+  const int m = h->m, maxit = h->opt.max_iters;
+  double* sc = h->scal;
+  double* ctl = sc + sd_handle::S_CTL;
+  const int saved_pdl = t_pdl, pdl = h->opt.pdl;
+  t_pdl = pdl;
+  const long long l_start = t_launch_count;
+  BatScope bs(L);
+  std::vector<cudaGraphNode_t> deps;
+  bool capturing = false;
+  cudaError_t err = cudaSuccess;
+  auto begin = [&](cudaGraph_t g, bool after) {
+    if (err != cudaSuccess) return false;
+    err = cudaStreamBeginCaptureToGraph(s, g, after ? deps.data() : nullptr, nullptr, after ? deps.size() : 0,
+                                        cudaStreamCaptureModeThreadLocal);
+    capturing = err == cudaSuccess;
+    return capturing;
+  };
+  auto end = [&](bool keep) {
+    if (!capturing) return;
+    if (keep && err == cudaSuccess) {
+      cudaStreamCaptureStatus st;
+      const cudaGraphNode_t* d = nullptr;
+      size_t nd = 0;
+      err = cudaStreamGetCaptureInfo(s, &st, nullptr, nullptr, &d, nullptr, &nd);
+      if (err == cudaSuccess) deps.assign(d, d + nd);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    capturing = false;
+    if (err == cudaSuccess) err = e2;
+    if (err == cudaSuccess) err = cudaGetLastError();
+  };
+  auto cond = [&](cudaGraph_t g, cudaGraphConditionalHandle hd, cudaGraphConditionalNodeType type,
+                  cudaGraph_t* body) {
+    if (err != cudaSuccess) return;
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = hd;
+    np.conditional.type = type;
+    np.conditional.size = 1;
+    cudaGraphNode_t nd = nullptr;
+    err = cudaGraphAddNode(&nd, g, deps.data(), nullptr, deps.size(), &np);
+    if (err != cudaSuccess) return;
+    *body = np.conditional.phGraph_out[0];
+    deps.assign(1, nd);
+  };
+  auto step = [&](int j) {
+    const long long l0 = t_launch_count;
+    double* vj = h->V + (long long)j * vs;
+    double* zj = h->Z + (long long)j * vs;
+    double* w = h->V + (long long)(j + 1) * vs;
+    arnoldi_orth(h, j, vj, zj, w);
+    launch_scale_by(w, w, len, h->flag + 1, 0, s);
+    return t_launch_count - l0;
+  };
+  cudaGraphConditionalHandle loop = 0;
+  CondSet cs = {};
+  cs.n = m;
+  err = cudaGraphConditionalHandleCreate(&loop, top, 0, cudaGraphCondAssignDefault);
+  for (int j = 1; j < m && err == cudaSuccess; ++j)
+    err = cudaGraphConditionalHandleCreate(&cs.c[j], top, 0, cudaGraphCondAssignDefault);
+  // every instance active, ||b|| and the first true residual, the first decisions
+  if (begin(top, false)) {
+    const long long l0 = t_launch_count;
+    {
+      NoBatScope nb;
+      launch_grp_act_all(L.act_dev, L.B, s);
+    }
+    resid_norms(h, MODE_MONO, h->x, h->b, true);
+    {
+      NoBatScope nb;
+      launch_grp_begin(L.off_dev, L.B, sc + sd_handle::S_BN, ctl, h->opt.rtol, s);
+      launch_grp_restart(L.off_dev, L.act_dev, L.B, sc + sd_handle::S_B2, ctl, maxit, maxit + 2, 0.0, loop, s);
+    }
+    *pre = t_launch_count - l0;
+    end(true);
+  }
+  cudaGraph_t wbody = nullptr;
+  cond(top, loop, cudaGraphCondTypeWhile, &wbody);
+  deps.clear();
+  if (begin(wbody, false)) {
+    const long long l0 = t_launch_count;
+    {
+      NoBatScope nb;
+      launch_cycle_head(cs, s);
+    }
+    launch_init_cycle(h->st, m, sc + sd_handle::S_B2, h->flag, s);
+    launch_scale_by(h->V, h->V, len, h->flag + 1, 0, s);
+    step(0);
+    const long long k = t_launch_count - l0 + 1;
+    {
+      NoBatScope nb;
+      launch_grp_step(L.off_dev, L.act_dev, L.B, h->flag, ctl, maxit, (double)k, m > 1, m > 1 ? cs.c[1] : 0, s);
+    }
+    end(true);
+  }
+  for (int j = 1; j < m; ++j) {
+    cudaGraph_t ib = nullptr;
+    cond(wbody, cs.c[j], cudaGraphCondTypeIf, &ib);
+    const std::vector<cudaGraphNode_t> keep = deps;
+    if (begin(ib, false)) {
+      const long long k = step(j) + 1;
+      NoBatScope nb;
+      launch_grp_step(L.off_dev, L.act_dev, L.B, h->flag, ctl, maxit, (double)k, j + 1 < m,
+                      j + 1 < m ? cs.c[j + 1] : 0, s);
+      end(false);
+    }
+    deps = keep;
+  }
+  // the update of x of the instances that took part (each with its own k,
+  // flag[5]), then every live instance's true residual and the next
+  // decisions; no programmatic edge out of a conditional node
+  if (begin(wbody, true)) {
+    const long long l0 = t_launch_count;
+    t_pdl = 0;
+    {
+      NoBatScope nb;
+      launch_grp_cycle_end(L.off_dev, L.act_dev, L.B, ctl, 0.0, s);
+    }
+    t_pdl = pdl;
+    launch_backsolve(h->st, m, m, sc + sd_handle::S_Y, h->flag + 5, s);
+    launch_axpy_multi(h->x, h->Z, vs, sc + sd_handle::S_Y, m, len, h->flag + 5, s);
+    {
+      NoBatScope nb;
+      launch_grp_live(L.off_dev, L.act_dev, L.B, ctl, s);
+    }
+    resid_norms(h, MODE_MONO, h->x, h->b, false);
+    const long long k = t_launch_count - l0 + 1;
+    NoBatScope nb;
+    launch_grp_restart(L.off_dev, L.act_dev, L.B, sc + sd_handle::S_B2, ctl, maxit, maxit + 2, (double)k, loop, s);
+    end(false);
+  }
+  if (capturing) end(false);
+  t_pdl = saved_pdl;
+  g_launch_count.fetch_sub(t_launch_count - l_start);
+  return err == cudaSuccess ? SD_OK : SD_E_CUDA;
+}
+
 }  // namespace
 
 int step_lockstep(sd_handle* const* hs, int count, int nsteps, sd_step_info* const* infos) {
@@ -2127,6 +2293,147 @@ int step_lockstep(sd_handle* const* hs, int count, int nsteps, sd_step_info* con
     }
   }
   CK(cudaStreamSynchronize(s));
+  return first;
+}
+
+// Every group's solve of a time step in one graph launch (see
+// step_graph_batch in sd_internal.cuh).
+int step_graph_batch(const std::vector<std::vector<sd_handle*>>& groups, const std::vector<int>& nsteps,
+                     const std::vector<std::vector<sd_step_info*>>& infos) {
+  const int G = (int)groups.size();
+  if (G == 0) return SD_OK;
+  std::vector<sd_handle*> order;
+  for (const auto& g : groups) {
+    if (g.empty()) return SD_E_INVAL;
+    for (int i = 1; i < (int)g.size(); ++i)
+      if (!can_lockstep(g[0], g[i])) return SD_E_INVAL;
+    if (!can_lockstep(g[0], g[0])) return SD_E_INVAL;  // monolithic, no kernel timing
+    order.insert(order.end(), g.begin(), g.end());
+  }
+  std::sort(order.begin(), order.end());
+  if (std::adjacent_find(order.begin(), order.end()) != order.end()) return SD_E_INVAL;
+  std::vector<std::unique_lock<std::mutex>> locks;
+  for (sd_handle* h : order) locks.emplace_back(h->mtx);
+  constexpr int kGat = 16;  // doubles gathered per instance (the control slots)
+  std::vector<std::unique_ptr<Lockstep>> Ls;
+  for (const auto& g : groups) {
+    std::unique_ptr<Lockstep> L(new Lockstep());
+    L->hs = g;
+    L->B = (int)g.size();
+    std::vector<long long> off(g.size());
+    for (size_t i = 0; i < g.size(); ++i) {
+      off[i] = (long long)(reinterpret_cast<uintptr_t>(g[i]->ar.base) - reinterpret_cast<uintptr_t>(g[0]->ar.base));
+      CK(cudaStreamSynchronize(g[i]->s));  // nothing of an instance may still run on its own stream
+    }
+    CK(cudaMalloc(&L->off_dev, sizeof(long long) * L->B));
+    CK(cudaMalloc(&L->act_dev, sizeof(int) * L->B));
+    CK(cudaMalloc(&L->gat_dev, sizeof(double) * kGat * L->B));
+    CK(cudaHostAlloc(&L->gat_host, sizeof(double) * kGat * L->B, cudaHostAllocDefault));
+    CK(cudaMemcpy(L->off_dev, off.data(), sizeof(long long) * L->B, cudaMemcpyHostToDevice));
+    Ls.push_back(std::move(L));
+  }
+  cudaStream_t s0 = groups[0][0]->s;
+  struct Events {
+    std::vector<cudaEvent_t> ev;
+    ~Events() {
+      for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
+    }
+  } E;
+  E.ev.assign(G + 2, nullptr);
+  CK(cudaEventCreate(&E.ev[0]));
+  CK(cudaEventCreate(&E.ev[1]));
+  for (int g = 0; g < G; ++g) CK(cudaEventCreateWithFlags(&E.ev[2 + g], cudaEventDisableTiming));
+  struct Exec {
+    cudaGraphExec_t ex = nullptr;
+    ~Exec() {
+      if (ex) cudaGraphExecDestroy(ex);
+    }
+  } X;
+  std::vector<char> built(G, 0);
+  std::vector<long long> pre(G, 0);
+  const int maxsteps = *std::max_element(nsteps.begin(), nsteps.end());
+  const int saved_pdl = t_pdl;
+  int first = SD_OK;
+  t_bat_misuse = 0;
+  for (int k = 0; k < maxsteps; ++k) {
+    std::vector<char> on(G);
+    for (int g = 0; g < G; ++g) on[g] = nsteps[g] > k;
+    if (!X.ex || on != built) {  // (re)build for the groups that step now
+      if (X.ex) {
+        cudaGraphExecDestroy(X.ex);
+        X.ex = nullptr;
+      }
+      cudaGraph_t top = nullptr;
+      CK(cudaGraphCreate(&top, 0));
+      int rc = SD_OK;
+      for (int g = 0; g < G && rc == SD_OK; ++g)
+        if (on[g]) rc = build_group_branch(*Ls[g], top, &pre[g]);
+      cudaError_t ie = cudaSuccess;
+      if (rc == SD_OK) ie = cudaGraphInstantiate(&X.ex, top, 0);
+      cudaGraphDestroy(top);
+      if (rc != SD_OK) return rc;
+      CK(ie);
+      if (t_bat_misuse) {
+        snprintf(g_errmsg, sizeof(g_errmsg), "a kernel without batch support was launched in a lockstep batch");
+        return SD_E_STATE;
+      }
+      built = on;
+    }
+    // right-hand sides on each group's stream, the solve graph on s0 after all of them
+    CK(cudaEventRecord(E.ev[0], s0));
+    for (int g = 0; g < G; ++g) {
+      if (!on[g]) continue;
+      cudaStream_t sg = groups[g][0]->s;
+      CK(cudaStreamWaitEvent(sg, E.ev[0], 0));
+      NoBatScope nb;
+      t_pdl = groups[g][0]->opt.pdl;
+      for (sd_handle* h : groups[g]) CKR(step_rhs(h, sg));
+      CK(cudaEventRecord(E.ev[2 + g], sg));
+      CK(cudaStreamWaitEvent(s0, E.ev[2 + g], 0));
+    }
+    t_pdl = saved_pdl;
+    CK(cudaGraphLaunch(X.ex, s0));
+    CK(cudaEventRecord(E.ev[1], s0));
+    for (int g = 0; g < G; ++g)
+      if (on[g]) CK(cudaStreamWaitEvent(groups[g][0]->s, E.ev[1], 0));
+    CK(cudaEventSynchronize(E.ev[1]));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, E.ev[0], E.ev[1]));
+    for (int g = 0; g < G; ++g) {
+      if (!on[g]) continue;
+      Lockstep& L = *Ls[g];
+      sd_handle* h0 = groups[g][0];
+      double* sc = h0->scal;
+      BatScope bs(L);
+      CKR(gather(L, sc + sd_handle::S_CTL, C_GROUP_END, s0));
+      std::vector<double> ctlv(L.gat_host, L.gat_host + (size_t)C_GROUP_END * L.B);
+      CKR(gather(L, sc + sd_handle::S_BLK, 3, s0));
+      g_launch_count.fetch_add(pre[g] + (long long)ctlv[C_KERN]);  // instance 0's count
+      for (int i = 0; i < L.B; ++i) {
+        const double* c = ctlv.data() + (size_t)i * C_GROUP_END;
+        sd_step_info si;
+        std::memset(&si, 0, sizeof(si));
+        si.iters = (int)c[C_ITER];
+        si.restarts = (int)c[C_REST];
+        si.reorths = (int)c[C_REO];
+        si.relres = c[C_REL];
+        si.status = c[C_STAT] == C_STAT_NUMERIC ? SD_E_NUMERIC : (c[C_STAT] == C_STAT_NOCONV ? SD_E_NOCONV : SD_OK);
+        const double d = c[C_BN] > 0 ? c[C_BN] : 1.0;
+        const bool ok = si.status != SD_E_NUMERIC;
+        si.relres_v = ok ? std::sqrt(L.gat_host[(size_t)i * 3]) / d : -1.0;
+        si.relres_pff = ok ? std::sqrt(L.gat_host[(size_t)i * 3 + 1]) / d : -1.0;
+        si.relres_pm = ok ? std::sqrt(L.gat_host[(size_t)i * 3 + 2]) / d : -1.0;
+        si.ms = ms;
+        sd_handle* h = groups[g][i];
+        h->t += h->dt;
+        h->step += 1;
+        if (!infos.empty() && infos[g][i]) infos[g][i][k] = si;
+        if (si.status != SD_OK && first == SD_OK) first = si.status;
+      }
+    }
+  }
+  CK(cudaStreamSynchronize(s0));
   return first;
 }
 

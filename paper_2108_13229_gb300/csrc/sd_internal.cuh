@@ -19,6 +19,7 @@
 #include <atomic>
 #include <type_traits>
 #include <utility>
+#include <vector>
 
 namespace sdk {
 
@@ -435,6 +436,32 @@ void launch_cycle_head(const CondSet& cs, cudaStream_t s);
 void launch_step_ctrl(double* flag, double* ctl, int max_iters, double kern, int has_next,
                       cudaGraphConditionalHandle next, cudaStream_t s);
 
+// Device-side control of a lockstep group's solve inside one CUDA graph (the
+// decisions of fgmres_lockstep, taken per instance on the device).  Each
+// instance z's slots are its own ctl (ctl0 moved by off[z] bytes); act is the
+// group's idle mask.  Beyond the single-solve slots: C_LIVE (the instance has
+// not stopped), C_CYC (it takes part in the current cycle), C_NUMR (a NaN/Inf
+// in the current cycle), and in instance 0's slots C_GCYC (the group's cycles
+// so far).  One CTA each; they are not batched launches.
+enum { C_LIVE = C_COUNT, C_CYC, C_NUMR, C_GCYC, C_GROUP_END };
+//  act = 1 for every instance
+void launch_grp_act_all(int* act, int B, cudaStream_t s);
+//  tolerance rtol ||b|| from bn2 (each instance's ||b||^2), counters cleared, all live
+void launch_grp_begin(const long long* off, int B, const double* bn2, double* ctl0, double rtol, cudaStream_t s);
+//  after a true residual (b2: ||r||^2): per live instance stop (converged, NaN/Inf,
+//  budget spent) or take part in a cycle (act = C_CYC); loop = any takes part;
+//  cycles beyond max_cycles stop the group (a bound on the device loop)
+void launch_grp_restart(const long long* off, int* act, int B, const double* b2, double* ctl0, int max_iters,
+                        int max_cycles, double kern, cudaGraphConditionalHandle loop, cudaStream_t s);
+//  after Arnoldi step j (flag0: each instance's flag): count it per active
+//  instance, idle the ones that stop, and run step j + 1 if any goes on
+void launch_grp_step(const long long* off, int* act, int B, const double* flag0, double* ctl0, int max_iters,
+                     double kern, int has_next, cudaGraphConditionalHandle next, cudaStream_t s);
+//  end of a cycle: a NaN/Inf stops the instance; act = C_CYC for the update of x
+void launch_grp_cycle_end(const long long* off, int* act, int B, double* ctl0, double kern, cudaStream_t s);
+//  act = C_LIVE (before the next true residual)
+void launch_grp_live(const long long* off, int* act, int B, const double* ctl0, cudaStream_t s);
+
 // dense coarse solve: x[idx[k]] = T(sum_l Ainv[k][l] * b[idx[l]])
 template <typename T>
 void launch_dense_solve(const double* Ainv, const int* idx, int m, const T* b, T* x, cudaStream_t s);
@@ -457,6 +484,15 @@ bool can_lockstep(const sd_handle* a, const sd_handle* b);
 // on the first handle's stream; infos[i] (may be null) receives instance i's
 // per-step information.  Returns the first non-OK step status.
 int step_lockstep(sd_handle* const* hs, int count, int nsteps, sd_step_info* const* infos);
+// Lockstep groups with every time step's solves of all groups in ONE graph
+// launch: each group a branch whose restart loop and Arnoldi steps are decided
+// on the device (WHILE / IF nodes, the k_grp_* kernels), the right-hand sides
+// launched per group before it.  groups[g] (mutually compatible handles)
+// takes nsteps[g] steps; infos[g][i] (may be empty or null) receives handle
+// i's per-step information.  Every instance's arithmetic is that of its solo
+// run.  Returns the first non-OK step status.
+int step_graph_batch(const std::vector<std::vector<sd_handle*>>& groups, const std::vector<int>& nsteps,
+                     const std::vector<std::vector<sd_step_info*>>& infos);
 // cells per side of a handle's grid
 int handle_grid(const sd_handle* h);
 // unknowns of a handle's dense state vector

@@ -572,6 +572,144 @@ void launch_step_ctrl(double* flag, double* ctl, int max_iters, double kern, int
   launch_k(k_step_ctrl, dim3(1), dim3(32), 0, s, flag, ctl, max_iters, kern, has_next, next);
 }
 
+// ------------------------------------------- lockstep groups in one graph
+// The host-driven lockstep (fgmres_lockstep) decides, after each true
+// residual and each Arnoldi step, which instances of the group go on.  These
+// kernels take the same decisions on the same FP64 values, per instance, on
+// the device, so a group's whole solve runs inside a CUDA graph (WHILE / IF
+// nodes) with every instance doing the arithmetic of its solo run.
+__global__ void k_grp_act_all(int* act, int B) {
+  griddep_wait();
+  for (int z = threadIdx.x; z < B; z += blockDim.x) act[z] = 1;
+}
+
+__global__ void k_grp_begin(const long long* __restrict__ off, int B, const double* bn2, double* ctl0, double rtol) {
+  griddep_wait();
+  for (int z = threadIdx.x; z < B; z += blockDim.x) {
+    double* ctl = bsh(ctl0, off[z]);
+    const double bn = sqrt(bsh(bn2, off[z])[0]);
+    ctl[C_TOL] = rtol * (bn > 0 ? bn : 1.0);
+    ctl[C_BN] = bn;
+    ctl[C_ITER] = ctl[C_REST] = ctl[C_REO] = ctl[C_STAT] = ctl[C_REL] = ctl[C_PREV] = 0.0;
+    ctl[C_ACC] = -1.0;
+    ctl[C_LIVE] = 1.0;
+    ctl[C_CYC] = ctl[C_NUMR] = 0.0;
+  }
+  if (threadIdx.x == 0) ctl0[C_KERN] = ctl0[C_GCYC] = 0.0;  // instance 0's slots sit at offset 0
+}
+
+__global__ void k_grp_restart(const long long* __restrict__ off, int* act, int B, const double* b2, double* ctl0,
+                              int max_iters, int max_cycles, double kern, cudaGraphConditionalHandle loop) {
+  griddep_wait();
+  // a bound on the device loop: every cycle adds at least one iteration to
+  // each instance that takes part, so max_iters cycles are never exceeded
+  const bool capped = ctl0[C_GCYC] >= (double)max_cycles;
+  int any = 0;
+  for (int z = threadIdx.x; z < B; z += blockDim.x) {
+    double* ctl = bsh(ctl0, off[z]);
+    int cyc = 0;
+    if (ctl[C_LIVE] != 0.0) {
+      const double beta = sqrt(bsh(b2, off[z])[0]);
+      const double bn = ctl[C_BN];
+      ctl[C_REL] = bn > 0 ? beta / bn : beta;
+      if (!isfinite(beta)) {
+        ctl[C_STAT] = C_STAT_NUMERIC;
+        ctl[C_LIVE] = 0.0;
+      } else if (beta <= ctl[C_TOL]) {
+        ctl[C_LIVE] = 0.0;
+      } else if (ctl[C_ITER] >= (double)max_iters || capped) {
+        ctl[C_STAT] = C_STAT_NOCONV;
+        ctl[C_LIVE] = 0.0;
+      } else {
+        cyc = 1;
+        ctl[C_REST] += 1.0;
+      }
+    }
+    ctl[C_CYC] = cyc;
+    act[z] = cyc;
+    any |= cyc;
+  }
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) {
+    ctl0[C_KERN] += kern;
+    if (any) ctl0[C_GCYC] += 1.0;
+    cudaGraphSetConditional(loop, any ? 1u : 0u);
+  }
+}
+
+__global__ void k_grp_step(const long long* __restrict__ off, int* act, int B, const double* flag0, double* ctl0,
+                           int max_iters, double kern, int has_next, cudaGraphConditionalHandle next) {
+  griddep_wait();
+  int running = 0;
+  for (int z = threadIdx.x; z < B; z += blockDim.x) {
+    if (!act[z]) continue;
+    double* ctl = bsh(ctl0, off[z]);
+    const double* f = bsh(flag0, off[z]);
+    ctl[C_ITER] += 1.0;
+    ctl[C_REO] += f[4] != 0.0 ? 1.0 : 0.0;
+    if (f[2] != 0.0) {
+      ctl[C_NUMR] = 1.0;
+      act[z] = 0;
+    } else if (f[0] <= ctl[C_TOL] || f[3] != 0.0 || ctl[C_ITER] >= (double)max_iters) {
+      act[z] = 0;
+    } else {
+      running = 1;
+    }
+  }
+  running = __syncthreads_or(running);
+  if (threadIdx.x == 0) {
+    ctl0[C_KERN] += kern;
+    if (has_next) cudaGraphSetConditional(next, running ? 1u : 0u);
+  }
+}
+
+__global__ void k_grp_cycle_end(const long long* __restrict__ off, int* act, int B, double* ctl0, double kern) {
+  griddep_wait();
+  for (int z = threadIdx.x; z < B; z += blockDim.x) {
+    double* ctl = bsh(ctl0, off[z]);
+    if (ctl[C_NUMR] != 0.0) {
+      ctl[C_STAT] = C_STAT_NUMERIC;
+      ctl[C_LIVE] = 0.0;
+      ctl[C_CYC] = 0.0;
+    }
+    act[z] = ctl[C_CYC] != 0.0 ? 1 : 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) ctl0[C_KERN] += kern;
+}
+
+__global__ void k_grp_live(const long long* __restrict__ off, int* act, int B, const double* ctl0) {
+  griddep_wait();
+  for (int z = threadIdx.x; z < B; z += blockDim.x) act[z] = bsh(ctl0, off[z])[C_LIVE] != 0.0 ? 1 : 0;
+}
+
+void launch_grp_act_all(int* act, int B, cudaStream_t s) {
+  SD_COUNT(1);
+  launch_k(k_grp_act_all, dim3(1), dim3(256), 0, s, act, B);
+}
+void launch_grp_begin(const long long* off, int B, const double* bn2, double* ctl0, double rtol, cudaStream_t s) {
+  SD_COUNT(1);
+  launch_k(k_grp_begin, dim3(1), dim3(256), 0, s, off, B, bn2, ctl0, rtol);
+}
+void launch_grp_restart(const long long* off, int* act, int B, const double* b2, double* ctl0, int max_iters,
+                        int max_cycles, double kern, cudaGraphConditionalHandle loop, cudaStream_t s) {
+  SD_COUNT(1);
+  launch_k(k_grp_restart, dim3(1), dim3(256), 0, s, off, act, B, b2, ctl0, max_iters, max_cycles, kern, loop);
+}
+void launch_grp_step(const long long* off, int* act, int B, const double* flag0, double* ctl0, int max_iters,
+                     double kern, int has_next, cudaGraphConditionalHandle next, cudaStream_t s) {
+  SD_COUNT(1);
+  launch_k(k_grp_step, dim3(1), dim3(256), 0, s, off, act, B, flag0, ctl0, max_iters, kern, has_next, next);
+}
+void launch_grp_cycle_end(const long long* off, int* act, int B, double* ctl0, double kern, cudaStream_t s) {
+  SD_COUNT(1);
+  launch_k(k_grp_cycle_end, dim3(1), dim3(256), 0, s, off, act, B, ctl0, kern);
+}
+void launch_grp_live(const long long* off, int* act, int B, const double* ctl0, cudaStream_t s) {
+  SD_COUNT(1);
+  launch_k(k_grp_live, dim3(1), dim3(256), 0, s, off, act, B, ctl0);
+}
+
 // out[z * count + t] = src_z[t] for every instance z of a lockstep batch
 // (src moved to instance z; out is not), idle instances included
 __global__ void k_gather_inst(const double* __restrict__ src, int count, double* __restrict__ out, Bat bt) {

@@ -317,6 +317,24 @@ int sd_solve_batch_ex(sd_handle* const* hs, int32_t count, const int32_t* nsteps
     }
     items.swap(split);
   }
+  if ((flags & SD_BATCH_GRAPH) && (flags & SD_BATCH_LOCKSTEP)) {
+    // every group (single handles as groups of one) in one graph per step
+    std::vector<std::vector<sd_handle*>> groups;
+    std::vector<int> gsteps;
+    std::vector<std::vector<sd_step_info*>> ginfos;
+    for (auto& it : items) {
+      std::vector<sd_handle*> g;
+      std::vector<sd_step_info*> gi;
+      for (int k : it) {
+        g.push_back(hs[k]);
+        gi.push_back(infos ? infos[k] : nullptr);
+      }
+      groups.push_back(g);
+      gsteps.push_back(nsteps[it[0]]);
+      ginfos.push_back(gi);
+    }
+    return sdk::step_graph_batch(groups, gsteps, ginfos);
+  }
   const int ni = (int)items.size();
   const int nt = (max_threads > 0 && max_threads < ni) ? max_threads : ni;
   int dev = 0;

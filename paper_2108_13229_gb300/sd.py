@@ -24,6 +24,7 @@ SD_BC_MMS, SD_BC_MMS_TRACTION, SD_BC_PAPER = 0, 1, 2
 SD_PROF_APPLY, SD_PROF_CHEB_V, SD_PROF_MUPDATE, SD_PROF_MDOT = 0, 1, 2, 3
 SD_NOALLOC_MAX_N = 256
 SD_BATCH_LOCKSTEP = 1
+SD_BATCH_GRAPH = 2
 SD_SERVER_LOCKSTEP = 1
 SD_MONOLITHIC, SD_PARTITIONED = 0, 1
 SD_ORDER_AUTO, SD_ORDER_PM_FIRST, SD_ORDER_FF_FIRST = 0, 1, 2
@@ -314,20 +315,21 @@ def sd_destroy(h: Handle) -> None:
 
 def sd_solve_batch(handles, nsteps, max_threads: int = 0, raise_on_error: bool = True, lockstep: bool = True):
     """Advance the handles together; lockstep=False: every instance on its own stream (sd_solve_batch_ex flags 0)."""
+    return sd_solve_batch_ex(handles, nsteps, max_threads, SD_BATCH_LOCKSTEP if lockstep else 0, raise_on_error)
+
+
+def sd_solve_batch_ex(handles, nsteps, max_threads: int = 0, flags: int = SD_BATCH_LOCKSTEP,
+                      raise_on_error: bool = True):
+    """Advance the handles together with the given SD_BATCH_* flags; per handle, a list of its step infos."""
     cnt = len(handles)
     hs = (ctypes.c_void_p * cnt)(*[h.ptr for h in handles])
     ns = (ctypes.c_int32 * cnt)(*[int(k) for k in nsteps])
     bufs = [(sd_step_info * max(1, int(k)))() for k in nsteps]
     infos = (ctypes.POINTER(sd_step_info) * cnt)(*[ctypes.cast(b, ctypes.POINTER(sd_step_info)) for b in bufs])
-    rc = _load().sd_solve_batch_ex(hs, cnt, ns, infos, int(max_threads), SD_BATCH_LOCKSTEP if lockstep else 0)
+    rc = _load().sd_solve_batch_ex(hs, cnt, ns, infos, int(max_threads), int(flags))
     if raise_on_error:
-        _check(rc, "sd_solve_batch")
+        _check(rc, "sd_solve_batch_ex")
     return [[bufs[k][q].as_dict() for q in range(int(nsteps[k]))] for k in range(cnt)]
-
-
-def sd_solve_batch_ex(handles, nsteps, max_threads: int = 0, flags: int = SD_BATCH_LOCKSTEP,
-                      raise_on_error: bool = True):
-    return sd_solve_batch(handles, nsteps, max_threads, raise_on_error, lockstep=bool(flags & SD_BATCH_LOCKSTEP))
 
 
 class Server:

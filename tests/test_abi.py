@@ -149,7 +149,7 @@ def test_batch_validation_without_gpu(sd):
     for hs, ns in [([a, None], [1, 1]), ([a, b], [1, -1]), ([a, a], [1, 1]), ([a, b, a], [2, 2, 2])]:
         arr = (ctypes.c_void_p * len(hs))(*hs)
         steps = (ctypes.c_int32 * len(ns))(*ns)
-        for flags in (0, sd.SD_BATCH_LOCKSTEP):
+        for flags in (0, sd.SD_BATCH_LOCKSTEP, sd.SD_BATCH_LOCKSTEP | sd.SD_BATCH_GRAPH):
             assert lib.sd_solve_batch_ex(arr, len(hs), steps, None, 0, flags) == sd.SD_E_INVAL, (hs, ns)
     assert lib.sd_solve_batch_ex(None, 0, None, None, 0, 0) == sd.SD_OK
     assert lib.sd_solve_batch_ex(None, 1, None, None, 0, 0) == sd.SD_E_INVAL

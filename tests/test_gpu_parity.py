@@ -248,6 +248,54 @@ def test_lockstep_batch_bitwise(sd, precision):
             assert launches_lockstep < launches  # the groups share their launches
 
 
+@pytest.mark.parametrize("precision", [1, 0])
+def test_graph_batch_bitwise(sd, precision):
+    # SD_BATCH_GRAPH: all groups of a step (uneven grids: a group of three 48^2, a
+    # group of two 16^2 with the fused coarse cycle, one 40^2 alone) in one graph
+    # launch, the solves decided on the device; every state, iteration and
+    # restart count equals the solo run's (restart 4 and max_iters 9 bring in
+    # restarts and the iteration cap), and equals the host-driven groups'
+    cases = [(48, 1, 0.1), (48, 2, 3.0), (48, 3, 10.0), (16, 4, 0.3), (16, 5, 7.0), (40, 6, 1.0)]
+    def mk(n, seed, alpha, **kw):
+        K = I.lognormal_K(n, -4.0, 0.5 + 0.3 * seed, 16.0, seed=seed)
+        return make(sd, n, 1e-3, K, alpha, 0.1, precision, coarsest=4 if n == 16 else 16, **kw)
+    for kw in ({}, {"restart": 4, "max_iters": 9}):
+        alone, inf_alone = [], []
+        for n, seed, alpha in cases:
+            h = mk(n, seed, alpha, **kw)
+            inf = sd.sd_step(h, 4, raise_on_error=False)
+            alone.append(sd.sd_get_state(h)[2])
+            inf_alone.append(inf)
+        for flags in (sd.SD_BATCH_LOCKSTEP | sd.SD_BATCH_GRAPH, sd.SD_BATCH_LOCKSTEP):
+            hs = [mk(n, seed, alpha, **kw) for n, seed, alpha in cases]
+            infos = sd.sd_solve_batch_ex(hs, [4] * len(cases), flags=flags, raise_on_error=False)
+            for h, xa, inf, ia in zip(hs, alone, infos, inf_alone):
+                for a, b in zip(inf, ia):
+                    for key in ("iters", "restarts", "status", "reorths", "relres", "relres_v", "relres_pff",
+                                "relres_pm"):
+                        assert a[key] == b[key], (flags, key, a[key], b[key])
+                assert np.array_equal(sd.sd_get_state(h)[2], xa)
+        if kw:  # the cap was reached somewhere: the NOCONV path ran on the device
+            assert any(i["status"] == sd.SD_E_NOCONV for inf in inf_alone for i in inf)
+
+
+def test_graph_batch_uneven_steps(sd):
+    # groups with different step counts: the graph is rebuilt when a group stops
+    cases = [(32, 1, 4), (32, 2, 4), (24, 3, 2), (24, 4, 2)]
+    def mk(n, seed):
+        return make(sd, n, 1e-3, I.lognormal_K(n, -4.0, 1.0, 8.0, seed=seed), 1.0, 0.1, 1)
+    alone = []
+    for n, seed, steps in cases:
+        h = mk(n, seed)
+        sd.sd_step(h, steps)
+        alone.append(sd.sd_get_state(h))
+    hs = [mk(n, seed) for n, seed, _ in cases]
+    sd.sd_solve_batch_ex(hs, [c[2] for c in cases], flags=sd.SD_BATCH_LOCKSTEP | sd.SD_BATCH_GRAPH)
+    for h, (t, step, xa) in zip(hs, alone):
+        t2, step2, x2 = sd.sd_get_state(h)
+        assert step2 == step and t2 == t and np.array_equal(x2, xa)
+
+
 @pytest.mark.parametrize("lockstep", [True, False])
 def test_server_results_match_alone(sd, lockstep):
     # lockstep: runs of one size class step together, joining and leaving

@@ -2296,6 +2296,40 @@ int step_lockstep(sd_handle* const* hs, int count, int nsteps, sd_step_info* con
   return first;
 }
 
+// The last batch graph: its groups, their group buffers (the graph addresses
+// them) and the instantiated graph, reused by the next call with the same
+// groups; sd_destroy of any member drops it.  One graph batch runs at a time.
+struct BatchGraphCache {
+  std::mutex mu;
+  std::vector<std::vector<sd_handle*>> groups;
+  std::vector<char> on;  // the groups the graph steps
+  std::vector<std::unique_ptr<Lockstep>> Ls;
+  std::vector<long long> pre;
+  cudaGraphExec_t ex = nullptr;
+  void clear() {
+    if (ex) cudaGraphExecDestroy(ex);
+    ex = nullptr;
+    Ls.clear();
+    groups.clear();
+    on.clear();
+    pre.clear();
+  }
+};
+BatchGraphCache& batch_cache() {
+  static BatchGraphCache* c = new BatchGraphCache();  // never destroyed: no CUDA call at process exit
+  return *c;
+}
+
+void drop_batch_graph(const sd_handle* h) {
+  BatchGraphCache& C = batch_cache();
+  std::lock_guard<std::mutex> lk(C.mu);
+  for (const auto& g : C.groups)
+    if (std::find(g.begin(), g.end(), h) != g.end()) {
+      C.clear();
+      return;
+    }
+}
+
 // Every group's solve of a time step in one graph launch (see
 // step_graph_batch in sd_internal.cuh).
 int step_graph_batch(const std::vector<std::vector<sd_handle*>>& groups, const std::vector<int>& nsteps,
@@ -2312,19 +2346,28 @@ int step_graph_batch(const std::vector<std::vector<sd_handle*>>& groups, const s
   }
   std::sort(order.begin(), order.end());
   if (std::adjacent_find(order.begin(), order.end()) != order.end()) return SD_E_INVAL;
+  BatchGraphCache& C = batch_cache();
+  std::lock_guard<std::mutex> clk(C.mu);
   std::vector<std::unique_lock<std::mutex>> locks;
   for (sd_handle* h : order) locks.emplace_back(h->mtx);
   constexpr int kGat = 16;  // doubles gathered per instance (the control slots)
-  std::vector<std::unique_ptr<Lockstep>> Ls;
-  for (const auto& g : groups) {
+  for (const auto& g : groups)
+    for (sd_handle* h : g) CK(cudaStreamSynchronize(h->s));  // nothing of an instance may still run on its own stream
+  if (C.groups != groups) {
+    C.clear();
+    C.groups = groups;
+    C.on.assign(G, 0);
+    C.pre.assign(G, 0);
+  }
+  std::vector<std::unique_ptr<Lockstep>>& Ls = C.Ls;
+  for (size_t gi = Ls.size(); gi < groups.size(); ++gi) {
+    const auto& g = groups[gi];
     std::unique_ptr<Lockstep> L(new Lockstep());
     L->hs = g;
     L->B = (int)g.size();
     std::vector<long long> off(g.size());
-    for (size_t i = 0; i < g.size(); ++i) {
+    for (size_t i = 0; i < g.size(); ++i)
       off[i] = (long long)(reinterpret_cast<uintptr_t>(g[i]->ar.base) - reinterpret_cast<uintptr_t>(g[0]->ar.base));
-      CK(cudaStreamSynchronize(g[i]->s));  // nothing of an instance may still run on its own stream
-    }
     CK(cudaMalloc(&L->off_dev, sizeof(long long) * L->B));
     CK(cudaMalloc(&L->act_dev, sizeof(int) * L->B));
     CK(cudaMalloc(&L->gat_dev, sizeof(double) * kGat * L->B));
@@ -2344,14 +2387,8 @@ int step_graph_batch(const std::vector<std::vector<sd_handle*>>& groups, const s
   CK(cudaEventCreate(&E.ev[0]));
   CK(cudaEventCreate(&E.ev[1]));
   for (int g = 0; g < G; ++g) CK(cudaEventCreateWithFlags(&E.ev[2 + g], cudaEventDisableTiming));
-  struct Exec {
-    cudaGraphExec_t ex = nullptr;
-    ~Exec() {
-      if (ex) cudaGraphExecDestroy(ex);
-    }
-  } X;
-  std::vector<char> built(G, 0);
-  std::vector<long long> pre(G, 0);
+  std::vector<char>& built = C.on;
+  std::vector<long long>& pre = C.pre;
   const int maxsteps = *std::max_element(nsteps.begin(), nsteps.end());
   const int saved_pdl = t_pdl;
   int first = SD_OK;
@@ -2359,10 +2396,10 @@ int step_graph_batch(const std::vector<std::vector<sd_handle*>>& groups, const s
   for (int k = 0; k < maxsteps; ++k) {
     std::vector<char> on(G);
     for (int g = 0; g < G; ++g) on[g] = nsteps[g] > k;
-    if (!X.ex || on != built) {  // (re)build for the groups that step now
-      if (X.ex) {
-        cudaGraphExecDestroy(X.ex);
-        X.ex = nullptr;
+    if (!C.ex || on != built) {  // (re)build for the groups that step now
+      if (C.ex) {
+        cudaGraphExecDestroy(C.ex);
+        C.ex = nullptr;
       }
       cudaGraph_t top = nullptr;
       CK(cudaGraphCreate(&top, 0));
@@ -2370,10 +2407,13 @@ int step_graph_batch(const std::vector<std::vector<sd_handle*>>& groups, const s
       for (int g = 0; g < G && rc == SD_OK; ++g)
         if (on[g]) rc = build_group_branch(*Ls[g], top, &pre[g]);
       cudaError_t ie = cudaSuccess;
-      if (rc == SD_OK) ie = cudaGraphInstantiate(&X.ex, top, 0);
+      if (rc == SD_OK) ie = cudaGraphInstantiate(&C.ex, top, 0);
       cudaGraphDestroy(top);
-      if (rc != SD_OK) return rc;
-      CK(ie);
+      if (rc != SD_OK || ie != cudaSuccess) {
+        C.clear();
+        if (rc != SD_OK) return rc;
+        CK(ie);
+      }
       if (t_bat_misuse) {
         snprintf(g_errmsg, sizeof(g_errmsg), "a kernel without batch support was launched in a lockstep batch");
         return SD_E_STATE;
@@ -2393,7 +2433,7 @@ int step_graph_batch(const std::vector<std::vector<sd_handle*>>& groups, const s
       CK(cudaStreamWaitEvent(s0, E.ev[2 + g], 0));
     }
     t_pdl = saved_pdl;
-    CK(cudaGraphLaunch(X.ex, s0));
+    CK(cudaGraphLaunch(C.ex, s0));
     CK(cudaEventRecord(E.ev[1], s0));
     for (int g = 0; g < G; ++g)
       if (on[g]) CK(cudaStreamWaitEvent(groups[g][0]->s, E.ev[1], 0));
@@ -2678,6 +2718,7 @@ int sd_sync(sd_handle* h) {
 
 void sd_destroy(sd_handle* h) {
   if (!h) return;
+  sdk::drop_batch_graph(h);  // a cached batch graph addresses the handle's memory
   if (h->s) cudaStreamSynchronize(h->s);
   for (auto& e : h->prof_ev)
     if (e) cudaEventDestroy(e);

@@ -487,12 +487,15 @@ int step_lockstep(sd_handle* const* hs, int count, int nsteps, sd_step_info* con
 // Lockstep groups with every time step's solves of all groups in ONE graph
 // launch: each group a branch whose restart loop and Arnoldi steps are decided
 // on the device (WHILE / IF nodes, the k_grp_* kernels), the right-hand sides
-// launched per group before it.  groups[g] (mutually compatible handles)
+// launched per group before it.  The last built graph is kept for the next
+// call with the same groups.  groups[g] (mutually compatible handles)
 // takes nsteps[g] steps; infos[g][i] (may be empty or null) receives handle
 // i's per-step information.  Every instance's arithmetic is that of its solo
 // run.  Returns the first non-OK step status.
 int step_graph_batch(const std::vector<std::vector<sd_handle*>>& groups, const std::vector<int>& nsteps,
                      const std::vector<std::vector<sd_step_info*>>& infos);
+// drop the cached batch graph if the handle is one of its instances
+void drop_batch_graph(const sd_handle* h);
 // cells per side of a handle's grid
 int handle_grid(const sd_handle* h);
 // unknowns of a handle's dense state vector

@@ -280,20 +280,30 @@ def test_graph_batch_bitwise(sd, precision):
 
 
 def test_graph_batch_uneven_steps(sd):
-    # groups with different step counts: the graph is rebuilt when a group stops
+    # groups with different step counts: the graph is rebuilt when a group
+    # stops; a second call on the same handles reuses the cached graph, and
+    # destroying a member drops it (the next batch builds its own)
     cases = [(32, 1, 4), (32, 2, 4), (24, 3, 2), (24, 4, 2)]
+    flags = sd.SD_BATCH_LOCKSTEP | sd.SD_BATCH_GRAPH
     def mk(n, seed):
         return make(sd, n, 1e-3, I.lognormal_K(n, -4.0, 1.0, 8.0, seed=seed), 1.0, 0.1, 1)
     alone = []
     for n, seed, steps in cases:
         h = mk(n, seed)
-        sd.sd_step(h, steps)
+        sd.sd_step(h, steps + 3)
         alone.append(sd.sd_get_state(h))
     hs = [mk(n, seed) for n, seed, _ in cases]
-    sd.sd_solve_batch_ex(hs, [c[2] for c in cases], flags=sd.SD_BATCH_LOCKSTEP | sd.SD_BATCH_GRAPH)
+    sd.sd_solve_batch_ex(hs, [c[2] for c in cases], flags=flags)
+    sd.sd_solve_batch_ex(hs, [3] * len(cases), flags=flags)
+    sd.sd_solve_batch_ex(hs[2:], [0, 0], flags=flags)  # another batch: the cache changes hands
     for h, (t, step, xa) in zip(hs, alone):
         t2, step2, x2 = sd.sd_get_state(h)
         assert step2 == step and t2 == t and np.array_equal(x2, xa)
+    del hs
+    hs = [mk(n, seed) for n, seed, _ in cases[:2]]
+    sd.sd_solve_batch_ex(hs, [c[2] + 3 for c in cases[:2]], flags=flags)
+    for h, (t, step, xa) in zip(hs, alone[:2]):
+        assert np.array_equal(sd.sd_get_state(h)[2], xa)
 
 
 @pytest.mark.parametrize("lockstep", [True, False])

@@ -184,10 +184,11 @@ def test_channel_lockstep_batch_bitwise(sd):
         h = make(sd, n, 1e-3, K, 1.0, 0.05, bc=2, bc_dp=1.0)
         sd.sd_step(h, 3)
         alone.append(sd.sd_get_state(h)[2])
-    hs = [make(sd, n, 1e-3, K, 1.0, 0.05, bc=2, bc_dp=1.0) for K in Ks]
-    sd.sd_solve_batch(hs, [3, 3, 3])
-    for h, xa in zip(hs, alone):
-        assert np.array_equal(sd.sd_get_state(h)[2], xa)
+    for flags in (sd.SD_BATCH_LOCKSTEP, sd.SD_BATCH_LOCKSTEP | sd.SD_BATCH_GRAPH):
+        hs = [make(sd, n, 1e-3, K, 1.0, 0.05, bc=2, bc_dp=1.0) for K in Ks]
+        sd.sd_solve_batch_ex(hs, [3, 3, 3], flags=flags)
+        for h, xa in zip(hs, alone):
+            assert np.array_equal(sd.sd_get_state(h)[2], xa)
 
 
 def test_channel_options(sd):

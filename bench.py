@@ -276,7 +276,9 @@ def step_model_bytes(n: int, info: dict, mixed: bool, coarsest: int = 16) -> flo
     m = 30
     for it in range(iters):
         k = it % m + 1
-        total += pre + apply_b + (2 * k + 3) * v8 + 2 * v8
+        # the first pass's dots: inside the operator's launch up to 4 basis vectors (k reads), else a multi-dot
+        # that reads w as well; the update reads k + 1 vectors and writes one; the new basis vector is scaled
+        total += pre + apply_b + (2 * k + (2 if k <= 4 else 3)) * v8 + 2 * v8
     total += reo * 5 * v8  # a second pass, about (2k+3) vectors at the typical k = 1
     for _ in range(restarts):
         total += (min(iters, m) + 2) * v8 + resid_b + v8  # x update, true residual and its norm
@@ -470,7 +472,8 @@ def bench_ours(args, ws, rank, local):
         for kid in (sd.SD_PROF_MUPDATE, sd.SD_PROF_APPLY, sd.SD_PROF_MDOT, sd.SD_PROF_CHEB_V):
             msk, _, _, prof = run_form(sd, torch, n, K, sd.SD_MIXED, steps, warmup, stream, prof_kernel=kid,
                                        tuned=tuned)
-            cands.append(roofline_entry(kid, prof, msk))
+            if prof[1] > 0:  # the multi-dot runs only beyond four basis vectors
+                cands.append(roofline_entry(kid, prof, msk))
         cands.sort(key=lambda e: -(e["share_of_step_time"] or 0.0))
         line["roofline"] = cands[0]
         line["roofline_kernels"] = cands[1:]

@@ -4,13 +4,14 @@
 //
 //  * multi-dot and fused update+dot kernels for classical Gram-Schmidt with
 //    one re-orthogonalisation (CGS2): each block accumulates its slice of
-//    all k dot products in registers, reduces them with warp shuffles and
-//    writes one partial per block; a second kernel sums the partials in a
-//    fixed order, so every reduction is deterministic (bitwise repeatable).
+//    all k dot products in registers, sums them over its threads in shared
+//    memory and writes one partial per block; the block that finishes last
+//    adds the partials up in a fixed order, so every reduction is
+//    deterministic (bitwise repeatable) and takes one launch.
 //  * Givens rotations, residual estimate and back substitution on the
 //    (m+1) x m Hessenberg matrix, kept on the device (one thread).
 //  * dense coarse solve x = A_c^{-1} b with the inverse built at setup by a
-//    single-CTA Gauss-Jordan elimination with partial pivoting.
+//    Gauss-Jordan elimination with partial pivoting (one launch per column).
 #include "sd_internal.cuh"
 
 #include <math.h>
@@ -77,11 +78,12 @@ __device__ __forceinline__ void load_own(const double* __restrict__ w, double* w
   }
 }
 
-// partial[q * ps + blk] = sum over the block's elements of V_q . w, q < k;
-// with self != 0 also w . w as entry k.  cond (may be null): skip when 0.
+// out[q] = V_q . w, q < k: partial[q * ps + blk] = the block's share, summed
+// by the last block (last_block).  cond (may be null): skip when 0.
 __global__ void __launch_bounds__(KT) k_mdot(const double* __restrict__ V, long long vs, int k,
                                              const double* __restrict__ w, long long len, double* __restrict__ partial,
-                                             int ps, int self, const double* __restrict__ cond, Bat bt) {
+                                             int ps, const double* __restrict__ cond, double* __restrict__ out,
+                                             unsigned* cnt, Bat bt) {
   griddep_wait();
   long long o;
   if (!bat_enter(bt, o)) return;
@@ -90,6 +92,8 @@ __global__ void __launch_bounds__(KT) k_mdot(const double* __restrict__ V, long 
     w = bsh(w, o);
     partial = bsh(partial, o);
     cond = bsh(cond, o);
+    out = bsh(out, o);
+    cnt = bsh(cnt, o);
   }
   if (cond && cond[0] == 0.0) return;
   __shared__ double red[KMAX_REG][KT];
@@ -104,31 +108,31 @@ __global__ void __launch_bounds__(KT) k_mdot(const double* __restrict__ V, long 
     red[q + 1][threadIdx.x] = a1;
   }
   if (q < k) red[q][threadIdx.x] = own_dot(V + (long long)q * vs, we, base, len);
-  if (self) {
-    double s0 = 0.0, s1 = 0.0;
-#pragma unroll
-    for (int t = 0; t < KE; t += 2) {
-      s0 = fma(we[t], we[t], s0);
-      s1 = fma(we[t + 1], we[t + 1], s1);
-    }
-    red[k][threadIdx.x] = s0 + s1;
-  }
-  block_tree(red, k + (self ? 1 : 0), partial, ps);
+  block_tree(red, k, partial, ps);
+  if (!last_block(cnt, gridDim.x, threadIdx.x)) return;
+  last_block_sums<KT, 8>(partial, ps, gridDim.x, k, red, threadIdx.x);
+  if (threadIdx.x < k) out[threadIdx.x] = red[threadIdx.x][0];
 }
 
 void launch_mdot(const double* V, long long vstride, int k, const double* w, long long len, double* partial, int ps,
-                 int nblk, int self, const double* cond, cudaStream_t s) {
+                 int nblk, const double* cond, double* out, unsigned* cnt, cudaStream_t s) {
   SD_COUNT(1);
-  launch_k(k_mdot, dim3(nblk), dim3(KT), 0, s, V, vstride, k, w, len, partial, ps, self, cond);
+  launch_k(k_mdot, dim3(nblk), dim3(KT), 0, s, V, vstride, k, w, len, partial, ps, cond, out, cnt);
 }
 
 // w -= sum_q coef_q V_q, then
-//   mode 1: partial dots V_q . w (second Gram-Schmidt pass),
-//   mode 2: partial w . w (norm of the new basis vector).
+//   mode 1: out[q] = V_q . w, q < k (second Gram-Schmidt pass),
+//   mode 2: out[0] = w . w (norm of the new basis vector); with reo, the
+//           re-orthogonalisation decision (Daniel-Gragg-Kaufman-Stewart):
+//           a second pass is needed when the projection removed most of w,
+//           w'.w' < eta2 ||w||^2, ||w||^2 = sum_q coef_q^2 + w'.w' for the
+//           orthonormal V_q (so no separate norm of w before the projection).
+// Sums as in k_mdot.
 __global__ void __launch_bounds__(KT) k_mupdate(const double* __restrict__ V, long long vs, int k,
                                                 const double* __restrict__ coef, double* __restrict__ w,
                                                 long long len, double* __restrict__ partial, int ps, int mode,
-                                                const double* __restrict__ cond, Bat bt) {
+                                                const double* __restrict__ cond, double* __restrict__ out,
+                                                unsigned* cnt, double* __restrict__ reo, double eta2, Bat bt) {
   griddep_wait();
   long long o;
   if (!bat_enter(bt, o)) return;
@@ -138,6 +142,9 @@ __global__ void __launch_bounds__(KT) k_mupdate(const double* __restrict__ V, lo
     w = bsh(w, o);
     partial = bsh(partial, o);
     cond = bsh(cond, o);
+    out = bsh(out, o);
+    cnt = bsh(cnt, o);
+    reo = bsh(reo, o);
   }
   if (cond && cond[0] == 0.0) return;
   __shared__ double cf[KMAX_REG];
@@ -167,11 +174,6 @@ __global__ void __launch_bounds__(KT) k_mupdate(const double* __restrict__ V, lo
       if (e < len) we[t] = fma(-c0, v0[e], we[t]);
     }
   }
-#pragma unroll
-  for (int t = 0; t < KE; ++t) {
-    const long long e = base + (long long)t * KT;
-    if (e < len) w[e] = we[t];
-  }
   if (mode == 1) {
     q = 0;
     for (; q + 1 < k; q += 2) {
@@ -192,76 +194,38 @@ __global__ void __launch_bounds__(KT) k_mupdate(const double* __restrict__ V, lo
     red[0][threadIdx.x] = s0 + s1;
     block_tree(red, 1, partial, ps);
   }
+  const bool last = last_block(cnt, gridDim.x, threadIdx.x);
+  // w after the count (see last_block); no block of this launch reads it
+#pragma unroll
+  for (int t = 0; t < KE; ++t) {
+    const long long e = base + (long long)t * KT;
+    if (e < len) w[e] = we[t];
+  }
+  if (!last) return;
+  const int kk = mode == 1 ? k : 1;
+  last_block_sums<KT, 8>(partial, ps, gridDim.x, kk, red, threadIdx.x);
+  if (threadIdx.x < kk) out[threadIdx.x] = red[threadIdx.x][0];
+  if (mode == 2 && reo && threadIdx.x == 0) {
+    const double n2a = red[0][0];
+    double nw2 = 0.0;
+    for (int i = 0; i < k; ++i) nw2 = fma(cf[i], cf[i], nw2);
+    nw2 += n2a;
+    reo[0] = n2a < eta2 * nw2 ? 1.0 : 0.0;
+  }
 }
 
 void launch_mupdate(const double* V, long long vstride, int k, const double* coef, double* w, long long len,
-                    double* partial, int ps, int nblk, int mode, const double* cond, cudaStream_t s) {
+                    double* partial, int ps, int nblk, int mode, const double* cond, double* out, unsigned* cnt,
+                    double* reo, double eta2, cudaStream_t s) {
   SD_COUNT(1);
-  launch_k(k_mupdate, dim3(nblk), dim3(KT), 0, s, V, vstride, k, coef, w, len, partial, ps, mode, cond);
-}
-
-// out[q] = sum_b partial[q * ps + b] (+ out[q] if accumulate), fixed-order tree
-__global__ void k_reduce(const double* __restrict__ partial, int nblk, int k, int ps, double* __restrict__ out,
-                         int accumulate, const double* __restrict__ cond, Bat bt) {
-  griddep_wait();
-  long long o;
-  if (!bat_enter(bt, o)) return;
-  if (bt.off) {
-    partial = bsh(partial, o);
-    out = bsh(out, o);
-    cond = bsh(cond, o);
-  }
-  __shared__ double sm[RT / 32];
-  const int q = blockIdx.x;
-  if (q >= k) return;
-  if (cond && cond[0] == 0.0) {  // skipped pass: its coefficients are zero
-    if (threadIdx.x == 0 && !accumulate) out[q] = 0.0;
-    return;
-  }
-  const double* p = partial + (long long)q * ps;
-  double s = 0.0;
-  for (int b = threadIdx.x; b < nblk; b += RT) s += p[b];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-#pragma unroll
-    for (int w = 0; w < RT / 32; ++w) t += sm[w];
-    out[q] = accumulate ? out[q] + t : t;
-  }
-}
-
-void launch_reduce(const double* partial, int nblk, int k, int ps, double* out, int accumulate, const double* cond,
-                   cudaStream_t s) {
-  SD_COUNT(1);
-  launch_k(k_reduce, dim3(k), dim3(RT), 0, s, partial, nblk, k, ps, out, accumulate, cond);
-}
-
-// Selective re-orthogonalisation (Daniel-Gragg-Kaufman-Stewart test): a second
-// Gram-Schmidt pass is needed when the projection removed most of w,
-// ||w'||^2 < eta^2 ||w||^2.  flag[0] = 1 (pass needed) or 0.
-__global__ void k_reorth_decide(const double* nw2, const double* n2a, double eta2, double* flag, Bat bt) {
-  griddep_wait();
-  long long o;
-  if (!bat_enter(bt, o)) return;
-  nw2 = bsh(nw2, o);
-  n2a = bsh(n2a, o);
-  flag = bsh(flag, o);
-  if (threadIdx.x == 0) flag[0] = (n2a[0] < eta2 * nw2[0]) ? 1.0 : 0.0;
-}
-
-void launch_reorth_decide(const double* nw2, const double* n2a, double eta2, double* flag, cudaStream_t s) {
-  SD_COUNT(1);
-  launch_k(k_reorth_decide, dim3(1), dim3(32), 0, s, nw2, n2a, eta2, flag);
+  launch_k(k_mupdate, dim3(nblk), dim3(KT), 0, s, V, vstride, k, coef, w, len, partial, ps, mode, cond, out, cnt,
+           reo, eta2);
 }
 
 void launch_dot(const double* a, const double* b, long long len, double* partial, int nblk, double* out,
-                cudaStream_t s) {
-  SD_COUNT(2);
-  launch_k(k_mdot, dim3(nblk), dim3(KT), 0, s, a, 0, 1, b, len, partial, nblk, 0, nullptr);
-  launch_k(k_reduce, dim3(1), dim3(RT), 0, s, partial, nblk, 1, nblk, out, 0, nullptr);
+                unsigned* cnt, cudaStream_t s) {
+  SD_COUNT(1);
+  launch_k(k_mdot, dim3(nblk), dim3(KT), 0, s, a, 0, 1, b, len, partial, nblk, (const double*)nullptr, out, cnt);
 }
 
 // mode 0: y = sdev[0] * x ; mode 1: y = x / sqrt(sdev[0])
@@ -391,7 +355,7 @@ __global__ void k_givens(double* st, int j, int m, const double* h1, const doubl
   double* sn = cs + m;
   double* g = sn + m;
   double* col = R + (long long)j * (m + 1);
-  for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
+  for (int i = 0; i <= j; ++i) col[i] = second ? h1[i] + h2[i] : h1[i];
   const double hn = sqrt(nrm2[0]);
   col[j + 1] = hn;
   for (int i = 0; i < j; ++i) {

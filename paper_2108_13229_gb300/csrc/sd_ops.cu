@@ -41,6 +41,30 @@ static inline int rows_vel(int) { return 1; }
 static inline dim3 grid2R(int nx, int ny, int R) { return dim3((nx + BX - 1) / BX, (ny + BY * R - 1) / (BY * R)); }
 
 // ------------------------------------------------------- whole operator (K1)
+// What a launch of the operator forms on the side of y: with ND > 0 the dot
+// products of y with the Krylov basis vectors V_q = V + q vs, q < k <= ND
+// (the first Gram-Schmidt pass of the Arnoldi step); with PS the residual's
+// norms.  partial: the block partials; out: where the last block leaves the
+// sums (PS: the scalar slots blk, b2, bn of launch_resid_norms); cnt: the
+// launch's last-block counter.
+struct ApplySide {
+  const double* V = nullptr;
+  long long vs = 0;
+  int k = 0;
+  double* partial = nullptr;
+  double* out = nullptr;
+  unsigned* cnt = nullptr;
+  int blk = 0, b2 = 0, bn = 0, with_b = 0;
+};
+
+// dacc[q] += V_q[idx] * a, q < ND (= sd.k: one instantiation per count, as
+// a masked-off FP64 instruction still takes its FP64-pipe cycles)
+template <int ND>
+__device__ __forceinline__ void side_dots(const ApplySide& sd, long long idx, double a, double* dacc) {
+#pragma unroll
+  for (int q = 0; q < ND; ++q) dacc[q] = fma(__ldg(sd.V + q * sd.vs + idx), a, dacc[q]);
+}
+
 // FF 1: the free-flow rows only (u, v, p_ff), with the porous-medium unknowns
 // taken as zero and the Darcy rows not written (subdomain solve of the
 // partitioned coupling); FF 2: the same with the v_Gamma rows replaced by
@@ -51,12 +75,13 @@ static inline dim3 grid2R(int nx, int ny, int R) { return dim3((nx + BX - 1) / B
 // entry costs one FP64 instruction (the Darcy diagonal adds three).  The
 // caller guarantees 2 <= i <= nx-2 and 1 <= j <= n-2, and with DARCY (the
 // porous medium's rows at the same cell) i <= n-2.
-template <bool RES, int PS, bool DARCY>
+template <bool RES, int PS, bool DARCY, int ND>
 __device__ __forceinline__ void apply_cell_interior(const Coef<double>& c, const double* __restrict__ u,
                                                     const double* __restrict__ v, const double* __restrict__ pf,
                                                     const double* __restrict__ pm, const double* __restrict__ b,
                                                     double* __restrict__ y, long long kc, long long nv,
-                                                    long long npf, long long npm, double* acc) {
+                                                    long long npf, long long npm, double* acc,
+                                                    const ApplySide& sd, double* dacc) {
   const int P = c.P;
   const double sg = RES ? -1.0 : 1.0;
   const double kd = sg * c.d6, k2 = sg * c.m2, k1 = sg * c.m1, km = sg * c.mu, kh = sg * c.h;
@@ -73,6 +98,7 @@ __device__ __forceinline__ void apply_cell_interior(const Coef<double>& c, const
     a = fma(kh, pf[kc], a);
     a = fma(-kh, pf[kc - 1], a);
     y[kc] = a;
+    side_dots<ND>(sd, kc, a, dacc);
     if (PS) acc[0] = fma(a, a, acc[0]);
     if (PS == 2) acc[3] = fma(b[kc], b[kc], acc[3]);
   }
@@ -89,6 +115,7 @@ __device__ __forceinline__ void apply_cell_interior(const Coef<double>& c, const
     a = fma(kh, pf[kc], a);
     a = fma(-kh, pf[kc - P], a);
     y[nv + kc] = a;
+    side_dots<ND>(sd, nv + kc, a, dacc);
     if (PS) acc[0] = fma(a, a, acc[0]);
     if (PS == 2) acc[3] = fma(b[nv + kc], b[nv + kc], acc[3]);
   }
@@ -98,6 +125,7 @@ __device__ __forceinline__ void apply_cell_interior(const Coef<double>& c, const
     a = fma(kh, v[kc + P], a);
     a = fma(-kh, v[kc], a);
     y[npf + kc] = a;
+    side_dots<ND>(sd, npf + kc, a, dacc);
     if (PS) acc[1] = fma(a, a, acc[1]);
     if (PS == 2) acc[3] = fma(b[npf + kc], b[npf + kc], acc[3]);
   }
@@ -110,6 +138,7 @@ __device__ __forceinline__ void apply_cell_interior(const Coef<double>& c, const
     a = fma(-sg * ts, pm[kc - P], a);
     a = fma(-sg * tn, pm[kc + P], a);
     y[npm + kc] = a;
+    side_dots<ND>(sd, npm + kc, a, dacc);
     if (PS) acc[2] = fma(a, a, acc[2]);
     if (PS == 2) acc[3] = fma(b[npm + kc], b[npm + kc], acc[3]);
   }
@@ -118,9 +147,10 @@ __device__ __forceinline__ void apply_cell_interior(const Coef<double>& c, const
 // The operator's rows of this thread (i, j0 .. j0+R-1).  PS (with RES):
 // acc[0..2] += the squared residuals of the velocity, continuity and Darcy
 // rows; PS 2: also acc[3] += the squared right-hand side of every row.
-template <int R, int FF, bool RES, int PS>
+template <int R, int FF, bool RES, int PS, int ND>
 __device__ __forceinline__ void apply_body(const Coef<double>& c, const double* __restrict__ x,
-                                           const double* __restrict__ b, double* __restrict__ y, double* acc) {
+                                           const double* __restrict__ b, double* __restrict__ y, double* acc,
+                                           const ApplySide& sd, double* dacc) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
   const int n = c.n, nx = c.nx, P = c.P;
@@ -139,16 +169,16 @@ __device__ __forceinline__ void apply_body(const Coef<double>& c, const double* 
     const long long nv = (long long)n * P, npf = (long long)(2 * n + 1) * P, npm = (long long)(3 * n + 1) * P;
 #pragma unroll
     for (int rr = 0; rr < R; ++rr)
-      apply_cell_interior<RES, PS, true>(c, x, x + nv, x + npf, x + npm, b, y, (long long)(j0 + rr) * P + i, nv, npf,
-                                         npm, acc);
+      apply_cell_interior<RES, PS, true, ND>(c, x, x + nv, x + npf, x + npm, b, y, (long long)(j0 + rr) * P + i, nv,
+                                             npf, npm, acc, sd, dacc);
     return;
   }
   if (FF == 0 && ff_in && bi >= n) {
     const long long nv = (long long)n * P, npf = (long long)(2 * n + 1) * P, npm = (long long)(3 * n + 1) * P;
 #pragma unroll
     for (int rr = 0; rr < R; ++rr)
-      apply_cell_interior<RES, PS, false>(c, x, x + nv, x + npf, x + npm, b, y, (long long)(j0 + rr) * P + i, nv,
-                                          npf, npm, acc);
+      apply_cell_interior<RES, PS, false, ND>(c, x, x + nv, x + npf, x + npm, b, y, (long long)(j0 + rr) * P + i,
+                                              nv, npf, npm, acc, sd, dacc);
     return;
   }
   if (FF != 0 && ff_in && c.iw == 0) {
@@ -216,6 +246,7 @@ __device__ __forceinline__ void apply_body(const Coef<double>& c, const double* 
       {
         const double r_ = b ? b[k] - val : val;
         y[k] = r_;
+        side_dots<ND>(sd, k, r_, dacc);
         if (PS) acc[0] = fma(r_, r_, acc[0]);
         if (PS == 2) acc[3] = fma(b[k], b[k], acc[3]);
       }
@@ -237,6 +268,7 @@ __device__ __forceinline__ void apply_body(const Coef<double>& c, const double* 
       {
         const double r_ = b ? b[k] - val : val;
         y[k] = r_;
+        side_dots<ND>(sd, k, r_, dacc);
         if (PS) acc[0] = fma(r_, r_, acc[0]);
         if (PS == 2) acc[3] = fma(b[k], b[k], acc[3]);
       }
@@ -254,6 +286,7 @@ __device__ __forceinline__ void apply_body(const Coef<double>& c, const double* 
         {
           const double r_ = b ? b[kp] - val : val;
           y[kp] = r_;
+          side_dots<ND>(sd, kp, r_, dacc);
           if (PS) acc[1] = fma(r_, r_, acc[1]);
           if (PS == 2) acc[3] = fma(b[kp], b[kp], acc[3]);
         }
@@ -269,6 +302,7 @@ __device__ __forceinline__ void apply_body(const Coef<double>& c, const double* 
       {
         const double r_ = b ? b[km] - val : val;
         y[km] = r_;
+        side_dots<ND>(sd, km, r_, dacc);
         if (PS) acc[2] = fma(r_, r_, acc[2]);
         if (PS == 2) acc[3] = fma(b[km], b[km], acc[3]);
       }
@@ -276,14 +310,17 @@ __device__ __forceinline__ void apply_body(const Coef<double>& c, const double* 
   }
 }
 
-// PS: the block's sums of acc (apply_body) in partial[q * nblocks + block],
-// q = 0..2 (PS 2: 0..3), in a fixed order, so repeated runs agree bit for
-// bit.  FP64 adds are scarce on this part, so the block sums its values
+// PS / ND: the block's sums of acc (PS, apply_body's norms: q = 0..2, PS 2:
+// 0..3) or dacc (ND: q < sd.k) in sd.partial[q * nblocks + block], in a fixed
+// order; FP64 adds are scarce on this part, so the block sums its values
 // through shared memory with one warp per quantity (eight serial adds per
 // lane, then five butterfly rounds) rather than a butterfly in every warp.
-template <int R, int FF, bool RES, int PS = 0>
-__global__ void __launch_bounds__(BX * BY, PS ? 3 : 4) k_apply_full(Coef<double> c, const double* __restrict__ x, const double* __restrict__ b,
-                             double* __restrict__ y, double* __restrict__ partial, Bat bt) {
+// The last block to finish adds the partials up (last_block) and writes
+// sd.out: PS, the slots of launch_resid_norms; ND, out[q] = V_q . y.
+template <int R, int FF, bool RES, int PS = 0, int ND = 0>
+__global__ void __launch_bounds__(BX * BY, (PS || ND) ? 3 : 4)
+    k_apply_full(Coef<double> c, const double* __restrict__ x, const double* __restrict__ b, double* __restrict__ y,
+                 ApplySide sd, Bat bt) {
   griddep_wait();
   long long o;
   if (!bat_enter(bt, o)) return;
@@ -292,94 +329,73 @@ __global__ void __launch_bounds__(BX * BY, PS ? 3 : 4) k_apply_full(Coef<double>
     x = bsh(x, o);
     b = bsh(b, o);
     y = bsh(y, o);
-    partial = bsh(partial, o);
+    sd.V = bsh(sd.V, o);
+    sd.partial = bsh(sd.partial, o);
+    sd.out = bsh(sd.out, o);
+    sd.cnt = bsh(sd.cnt, o);
   }
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  apply_body<R, FF, RES, PS>(c, x, b, y, acc);
-  if constexpr (PS > 0) {
-    constexpr int NQ = PS == 2 ? 4 : 3;
-    __shared__ double red[4][BX * BY];
+  double dacc[ND > 0 ? ND : 1];
+#pragma unroll
+  for (int q = 0; q < (ND > 0 ? ND : 1); ++q) dacc[q] = 0.0;
+  apply_body<R, FF, RES, PS, ND>(c, x, b, y, acc, sd, dacc);
+  if constexpr (PS > 0 || ND > 0) {
+    constexpr int NQ = PS == 2 ? 4 : PS == 1 ? 3 : ND;
+    constexpr int NR = NQ > 4 ? NQ : 4;
+    const int nq = NQ;
+    __shared__ double red[NR][BX * BY];
     const int t = threadIdx.y * blockDim.x + threadIdx.x;
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) red[q][t] = acc[q];
+    for (int q = 0; q < NQ; ++q)
+      if (q < nq) red[q][t] = PS > 0 ? acc[q] : dacc[q];
     __syncthreads();
     const int wp = t >> 5, lane = t & 31;
-    if (wp < NQ) {
+    const unsigned nbk = gridDim.x * gridDim.y;
+    if (wp < nq) {
       const double* r = red[wp] + lane * (BX * BY / 32);
       double v = r[0];
 #pragma unroll
       for (int e = 1; e < BX * BY / 32; ++e) v += r[e];
 #pragma unroll
       for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
-      if (lane == 0) {
-        const long long nbk = (long long)gridDim.x * gridDim.y;
-        partial[wp * nbk + (long long)blockIdx.y * gridDim.x + blockIdx.x] = v;
+      if (lane == 0) sd.partial[wp * (long long)nbk + blockIdx.y * gridDim.x + blockIdx.x] = v;
+    }
+    if (!last_block(sd.cnt, nbk, t)) return;
+    last_block_sums<BX * BY, 4>(sd.partial, nbk, (int)nbk, nq, red, t);
+    if constexpr (PS > 0) {
+      if (t == 0) {
+        double* sc = sd.out;
+        sc[sd.blk] = red[0][0];
+        sc[sd.blk + 1] = red[1][0];
+        sc[sd.blk + 2] = red[2][0];
+        sc[sd.b2] = (red[0][0] + red[1][0]) + red[2][0];
+        if (PS == 2) sc[sd.bn] = red[3][0];
       }
+    } else {
+      if (t < nq) sd.out[t] = red[t][0];
     }
   }
 }
 
-// sc[blk + q] (q = 0..2) = the sums of squares of the residual's velocity,
-// continuity and Darcy rows, sc[b2] = their total ((q0 + q1) + q2), and with
-// with_b sc[bn] = the sum of squares of b; from the block partials of
-// k_apply_full<.., PS>, each summed in a fixed order (every thread's partials
-// loaded at once, then one warp per quantity).
-__global__ void __launch_bounds__(256) k_reduce_resid(const double* __restrict__ partial, int nbk,
-                                                      double* __restrict__ sc, int blk, int b2, int bn, int with_b,
-                                                      Bat bt) {
-  griddep_wait();
-  long long o;
-  if (!bat_enter(bt, o)) return;
-  if (bt.off) {
-    partial = bsh(partial, o);
-    sc = bsh(sc, o);
-  }
-  __shared__ double red[4][256];
-  __shared__ double tot[4];
-  const int t = threadIdx.x;
-  const int nq = with_b ? 4 : 3;
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int k = t; k < nbk; k += 256)
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (q < nq) v[q] += partial[(long long)q * nbk + k];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) red[q][t] = v[q];
-  __syncthreads();
-  const int wp = t >> 5, lane = t & 31;
-  if (wp < nq) {
-    const double* r = red[wp] + lane * 8;
-    double w = r[0];
-#pragma unroll
-    for (int e = 1; e < 8; ++e) w += r[e];
-#pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) w += __shfl_xor_sync(0xffffffffu, w, d);
-    if (lane == 0) tot[wp] = w;
-  }
-  __syncthreads();
-  if (t == 0) {
-    sc[blk] = tot[0];
-    sc[blk + 1] = tot[1];
-    sc[blk + 2] = tot[2];
-    sc[b2] = (tot[0] + tot[1]) + tot[2];
-    if (with_b) sc[bn] = tot[3];
-  }
-}
-
 void launch_resid_norms(const Coef<double>& c, const double* x, const double* b, double* r, double* partial,
-                        double* sc, int blk, int b2, int bn, int with_b, cudaStream_t s) {
-  SD_COUNT(2);
+                        double* sc, int blk, int b2, int bn, int with_b, unsigned* cnt, cudaStream_t s) {
+  SD_COUNT(1);
   const int R = rows_apply(c.n);
   const dim3 g = grid2R(c.nx + 1, c.n + 1, R);
+  ApplySide sd;
+  sd.partial = partial;
+  sd.out = sc;
+  sd.cnt = cnt;
+  sd.blk = blk;
+  sd.b2 = b2;
+  sd.bn = bn;
   if (R == 4) {
-    if (with_b) launch_k(k_apply_full<4, 0, true, 2>, g, dim3(BX, BY), 0, s, c, x, b, r, partial);
-    else launch_k(k_apply_full<4, 0, true, 1>, g, dim3(BX, BY), 0, s, c, x, b, r, partial);
+    if (with_b) launch_k(k_apply_full<4, 0, true, 2>, g, dim3(BX, BY), 0, s, c, x, b, r, sd);
+    else launch_k(k_apply_full<4, 0, true, 1>, g, dim3(BX, BY), 0, s, c, x, b, r, sd);
   } else {
-    if (with_b) launch_k(k_apply_full<1, 0, true, 2>, g, dim3(BX, BY), 0, s, c, x, b, r, partial);
-    else launch_k(k_apply_full<1, 0, true, 1>, g, dim3(BX, BY), 0, s, c, x, b, r, partial);
+    if (with_b) launch_k(k_apply_full<1, 0, true, 2>, g, dim3(BX, BY), 0, s, c, x, b, r, sd);
+    else launch_k(k_apply_full<1, 0, true, 1>, g, dim3(BX, BY), 0, s, c, x, b, r, sd);
   }
-  launch_k(k_reduce_resid, dim3(1), dim3(256), 0, s, (const double*)partial, (int)(g.x * g.y), sc, blk, b2, bn,
-           with_b);
 }
 
 // blocks of the operator's launch (partial sums per quantity of launch_resid_norms)
@@ -388,16 +404,46 @@ long long resid_norms_blocks(int nx, int n) {
   return (long long)g.x * g.y;
 }
 
+// (at most four dot products: eight spilled registers at three blocks per SM)
+int apply_dots_max() { return 4; }
+
+void launch_apply_dots(const Coef<double>& c, const double* x, double* y, const double* V, long long vs, int k,
+                       double* partial, double* out, unsigned* cnt, cudaStream_t s) {
+  SD_COUNT(1);
+  const int R = rows_apply(c.n);
+  const dim3 g = grid2R(c.nx + 1, c.n + 1, R);
+  ApplySide sd;
+  sd.V = V;
+  sd.vs = vs;
+  sd.k = k;
+  sd.partial = partial;
+  sd.out = out;
+  sd.cnt = cnt;
+  const double* nb = nullptr;
+  const dim3 bl(BX, BY);
+  if (R == 4) {
+    if (k == 1) launch_k(k_apply_full<4, 0, false, 0, 1>, g, bl, 0, s, c, x, nb, y, sd);
+    else if (k == 2) launch_k(k_apply_full<4, 0, false, 0, 2>, g, bl, 0, s, c, x, nb, y, sd);
+    else if (k == 3) launch_k(k_apply_full<4, 0, false, 0, 3>, g, bl, 0, s, c, x, nb, y, sd);
+    else launch_k(k_apply_full<4, 0, false, 0, 4>, g, bl, 0, s, c, x, nb, y, sd);
+  } else {
+    if (k == 1) launch_k(k_apply_full<1, 0, false, 0, 1>, g, bl, 0, s, c, x, nb, y, sd);
+    else if (k == 2) launch_k(k_apply_full<1, 0, false, 0, 2>, g, bl, 0, s, c, x, nb, y, sd);
+    else if (k == 3) launch_k(k_apply_full<1, 0, false, 0, 3>, g, bl, 0, s, c, x, nb, y, sd);
+    else launch_k(k_apply_full<1, 0, false, 0, 4>, g, bl, 0, s, c, x, nb, y, sd);
+  }
+}
+
 void launch_apply_full(const Coef<double>& c, const double* x, const double* b, double* y, cudaStream_t s) {
   SD_COUNT(1);
   const int R = rows_apply(c.n);
   const dim3 g = grid2R(c.nx + 1, c.n + 1, R);
   if (R == 4) {
-    if (b) launch_k(k_apply_full<4, 0, true>, g, dim3(BX, BY), 0, s, c, x, b, y, (double*)nullptr);
-    else launch_k(k_apply_full<4, 0, false>, g, dim3(BX, BY), 0, s, c, x, b, y, (double*)nullptr);
+    if (b) launch_k(k_apply_full<4, 0, true>, g, dim3(BX, BY), 0, s, c, x, b, y, ApplySide());
+    else launch_k(k_apply_full<4, 0, false>, g, dim3(BX, BY), 0, s, c, x, b, y, ApplySide());
   } else {
-    if (b) launch_k(k_apply_full<1, 0, true>, g, dim3(BX, BY), 0, s, c, x, b, y, (double*)nullptr);
-    else launch_k(k_apply_full<1, 0, false>, g, dim3(BX, BY), 0, s, c, x, b, y, (double*)nullptr);
+    if (b) launch_k(k_apply_full<1, 0, true>, g, dim3(BX, BY), 0, s, c, x, b, y, ApplySide());
+    else launch_k(k_apply_full<1, 0, false>, g, dim3(BX, BY), 0, s, c, x, b, y, ApplySide());
   }
 }
 
@@ -406,11 +452,11 @@ void launch_apply_ff(const Coef<double>& c, const double* x, const double* b, do
   const int R = rows_apply(c.n);
   const dim3 g = grid2R(c.nx + 1, c.n + 1, R);
   if (R == 4) {
-    if (vdir) launch_k(k_apply_full<4, 2, false>, g, dim3(BX, BY), 0, s, c, x, b, y, (double*)nullptr);
-    else launch_k(k_apply_full<4, 1, false>, g, dim3(BX, BY), 0, s, c, x, b, y, (double*)nullptr);
+    if (vdir) launch_k(k_apply_full<4, 2, false>, g, dim3(BX, BY), 0, s, c, x, b, y, ApplySide());
+    else launch_k(k_apply_full<4, 1, false>, g, dim3(BX, BY), 0, s, c, x, b, y, ApplySide());
   } else {
-    if (vdir) launch_k(k_apply_full<1, 2, false>, g, dim3(BX, BY), 0, s, c, x, b, y, (double*)nullptr);
-    else launch_k(k_apply_full<1, 1, false>, g, dim3(BX, BY), 0, s, c, x, b, y, (double*)nullptr);
+    if (vdir) launch_k(k_apply_full<1, 2, false>, g, dim3(BX, BY), 0, s, c, x, b, y, ApplySide());
+    else launch_k(k_apply_full<1, 1, false>, g, dim3(BX, BY), 0, s, c, x, b, y, ApplySide());
   }
 }
 

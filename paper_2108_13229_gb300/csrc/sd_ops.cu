@@ -1135,12 +1135,11 @@ __device__ __forceinline__ T prolong_D_sm(const T* __restrict__ s, int CX, int I
 // output cells (x smoothed on a halo of NS + 1 for that) and sums it over the
 // 2 x 2 children of each coarse cell it covers into bco (nc x nc, pitch Pc):
 // k_resid_restrict_D's work and arithmetic, without its launch.
-template <typename T, int NS, int TLY, bool BT, bool RR = false>
-__global__ void __launch_bounds__(TLT, TLY <= 8 ? 8 : 4) k_smooth_tile_D(Coef<T> c, const T* __restrict__ xin,
-                                                       const T* __restrict__ b, T* __restrict__ xout,
-                                                       ChebSteps<T> cs, const T* __restrict__ ct,
-                                                       const T* __restrict__ ec, int nc, int Pc,
-                                                       T* __restrict__ bco, Bat bt) {
+template <typename T, int NS, int TLY, bool BT, bool RR = false, int NT = TLT>
+__global__ void __launch_bounds__(NT, NT > TLT ? 2 : (TLY <= 8 ? 8 : 4))
+    k_smooth_tile_D(Coef<T> c, const T* __restrict__ xin, const T* __restrict__ b, T* __restrict__ xout,
+                    ChebSteps<T> cs, const T* __restrict__ ct, const T* __restrict__ ec, int nc, int Pc,
+                    T* __restrict__ bco, Bat bt) {
   griddep_wait();
   // a separate instantiation for lockstep batches keeps the single-instance
   // kernel's coefficients in the parameter space
@@ -1170,10 +1169,10 @@ __global__ void __launch_bounds__(TLT, TLY <= 8 ? 8 : 4) k_smooth_tile_D(Coef<T>
   const int ilo = blockIdx.x * TLX - H, jlo = blockIdx.y * TLY - H;
   const int I0 = (ilo >> 1) - 1, J0 = (jlo >> 1) - 1;
   if (xin && ec) {
-    for (int p = threadIdx.x; p < CX * CY; p += TLT) sce[p] = cd_at(ec, nc, cx / 2, Pc, I0 + p % CX, J0 + p / CX);
+    for (int p = threadIdx.x; p < CX * CY; p += NT) sce[p] = cd_at(ec, nc, cx / 2, Pc, I0 + p % CX, J0 + p / CX);
     __syncthreads();
   }
-  for (int p = threadIdx.x; p < SR * SP; p += TLT) {
+  for (int p = threadIdx.x; p < SR * SP; p += NT) {
     const int gi = ilo + p % SP, gj = jlo + p / SP;
     T vb = T(0), vx = T(0), vtx = T(0), vty = T(0);
     if (gi >= 0 && gj >= 0) {
@@ -1212,12 +1211,12 @@ __global__ void __launch_bounds__(TLT, TLY <= 8 ? 8 : 4) k_smooth_tile_D(Coef<T>
   for (int s = 0; s < NS; ++s) {
     const int lo = s + 1, w = EX - 2 * lo, hgt = EY - 2 * lo;
     if (inner) {
-      for (int p = threadIdx.x; p < w * hgt; p += TLT) {
+      for (int p = threadIdx.x; p < w * hgt; p += NT) {
         const int gi = ilo + lo + p % w, gj = jlo + lo + p / w;
         cheb_D_at<T, true>(tc, cur, bq, dq, nxt, cs.a[s], cs.c[s], gi, gj);
       }
     } else {
-      for (int p = threadIdx.x; p < w * hgt; p += TLT) {
+      for (int p = threadIdx.x; p < w * hgt; p += NT) {
         const int gi = ilo + lo + p % w, gj = jlo + lo + p / w;
         if (gi >= 0 && gj >= 0 && gi < cx && gj < n) cheb_D_at(tc, cur, bq, dq, nxt, cs.a[s], cs.c[s], gi, gj);
       }
@@ -1227,7 +1226,7 @@ __global__ void __launch_bounds__(TLT, TLY <= 8 ? 8 : 4) k_smooth_tile_D(Coef<T>
     nxt = (nxt == xb) ? xa : xb;
   }
   if constexpr (RR) {
-    for (int p = threadIdx.x; p < TLX * TLY; p += TLT) {
+    for (int p = threadIdx.x; p < TLX * TLY; p += NT) {
       const int gi = ilo + H + p % TLX, gj = jlo + H + p / TLX;
       if (gi >= cx || gj >= n) continue;
       const int k = gj * SP + gi;
@@ -1237,14 +1236,14 @@ __global__ void __launch_bounds__(TLT, TLY <= 8 ? 8 : 4) k_smooth_tile_D(Coef<T>
     }
     __syncthreads();
     const int I0 = (ilo + H) / 2, J0 = (jlo + H) / 2;
-    for (int p = threadIdx.x; p < (TLX / 2) * (TLY / 2); p += TLT) {
+    for (int p = threadIdx.x; p < (TLX / 2) * (TLY / 2); p += NT) {
       const int I = I0 + p % (TLX / 2), J = J0 + p / (TLX / 2);
       if (I >= cx / 2 || J >= nc) continue;
       const T* r0 = dq + (2 * J) * SP + 2 * I;
       bco[(long long)J * Pc + I] = (r0[0] + r0[1]) + (r0[SP] + r0[SP + 1]);
     }
   }
-  for (int p = threadIdx.x; p < TLX * TLY; p += TLT) {
+  for (int p = threadIdx.x; p < TLX * TLY; p += NT) {
     const int gi = ilo + H + p % TLX, gj = jlo + H + p / TLX;
     if (gi < cx && gj < n) xout[(long long)gj * P + gi] = cur[(long long)gj * SP + gi];
   }
@@ -1257,12 +1256,11 @@ __global__ void __launch_bounds__(TLT, TLY <= 8 ? 8 : 4) k_smooth_tile_D(Coef<T>
 // cells, pitch Pc) -- the residual and restriction kernels of the level
 // with their launches and the residual's round trip through memory, the same
 // arithmetic per point.
-template <typename T, int NS, int TLY, bool BT, bool RR = false>
-__global__ void __launch_bounds__(TLT, TLY <= 8 ? 8 : 4) k_smooth_tile_V(Coef<T> c, const T* __restrict__ xin,
-                                                       const T* __restrict__ b, T* __restrict__ xout,
-                                                       ChebSteps<T> cs, const T* __restrict__ ct,
-                                                       const T* __restrict__ ec, int nc, int Pc,
-                                                       T* __restrict__ bco, Bat bt) {
+template <typename T, int NS, int TLY, bool BT, bool RR = false, int NT = TLT>
+__global__ void __launch_bounds__(NT, NT > TLT ? 2 : (TLY <= 8 ? 8 : 4))
+    k_smooth_tile_V(Coef<T> c, const T* __restrict__ xin, const T* __restrict__ b, T* __restrict__ xout,
+                    ChebSteps<T> cs, const T* __restrict__ ct, const T* __restrict__ ec, int nc, int Pc,
+                    T* __restrict__ bco, Bat bt) {
   griddep_wait();
   // a separate instantiation for lockstep batches keeps the single-instance
   // kernel's coefficients in the parameter space
@@ -1300,14 +1298,14 @@ __global__ void __launch_bounds__(TLT, TLY <= 8 ? 8 : 4) k_smooth_tile_V(Coef<T>
     // window entries no halo point reads are set to zero: coarse u faces
     // outside 0..nxc (which cu_at would read past its row on traction sides)
     // and coarse v rows below 0
-    for (int p = threadIdx.x; p < CX * CY; p += TLT) {
+    for (int p = threadIdx.x; p < CX * CY; p += NT) {
       const int I = I0 + p % CX, J = J0 + p / CX;
       scu[p] = (I >= 0 && I <= nxc) ? cu_at(ecu, nc, nxc, iwc, Pc, I, J, c.lat) : T(0);
       scv[p] = J >= 0 ? cv_at(ecv, nc, nxc, iwc, Pc, I, J) : T(0);
     }
     __syncthreads();
   }
-  for (int p = threadIdx.x; p < SR * SP; p += TLT) {
+  for (int p = threadIdx.x; p < SR * SP; p += NT) {
     const int gi = ilo + p % SP, gj = jlo + p / SP;
     T bu = T(0), bv = T(0), xu = T(0), xv = T(0);
     if (gi >= 0 && gj >= 0) {
@@ -1332,7 +1330,7 @@ __global__ void __launch_bounds__(TLT, TLY <= 8 ? 8 : 4) k_smooth_tile_V(Coef<T>
     sau[p] = xu;
     sav[p] = xv;
   }
-  for (int p = threadIdx.x; p < SP; p += TLT) {
+  for (int p = threadIdx.x; p < SP; p += NT) {
     const int gi = ilo + p;
     sw[p] = (gi >= 0 && gi <= nx) ? c.w[gi] : T(0);
     srg[p] = (gi >= 0 && gi < nx) ? c.rg[gi] : T(0);
@@ -1362,12 +1360,12 @@ __global__ void __launch_bounds__(TLT, TLY <= 8 ? 8 : 4) k_smooth_tile_V(Coef<T>
   for (int s = 0; s < NS; ++s) {
     const int lo = s + 1, w = EX - 2 * lo, hgt = EY - 2 * lo;
     if (inner) {
-      for (int p = threadIdx.x; p < w * hgt; p += TLT) {
+      for (int p = threadIdx.x; p < w * hgt; p += NT) {
         const int gi = ilo + lo + p % w, gj = jlo + lo + p / w;
         cheb_V_at2<T, true>(tc, curu, curv, bu, bv, du, dv, nxu, nxv, cs.a[s], cs.c[s], gi, gj);
       }
     } else {
-      for (int p = threadIdx.x; p < w * hgt; p += TLT) {
+      for (int p = threadIdx.x; p < w * hgt; p += NT) {
         const int gi = ilo + lo + p % w, gj = jlo + lo + p / w;
         if (gi >= 0 && gj >= 0 && gi <= nx && gj <= n)
           cheb_V_at2(tc, curu, curv, bu, bv, du, dv, nxu, nxv, cs.a[s], cs.c[s], gi, gj);
@@ -1383,7 +1381,7 @@ __global__ void __launch_bounds__(TLT, TLY <= 8 ? 8 : 4) k_smooth_tile_V(Coef<T>
     // the residual (resid_V_at's arithmetic) into the d arrays, then the
     // coarse faces of the tile (restrict_V_at's arithmetic)
     constexpr int lo = NS + 1, w = EX - 2 * lo, hgt = EY - 2 * lo;
-    for (int p = threadIdx.x; p < w * hgt; p += TLT) {
+    for (int p = threadIdx.x; p < w * hgt; p += NT) {
       const int gi = ilo + lo + p % w, gj = jlo + lo + p / w;
       if (gi < 0 || gj < 0 || gi > nx || gj > n) continue;
       const int k = gj * SP + gi;
@@ -1413,12 +1411,12 @@ __global__ void __launch_bounds__(TLT, TLY <= 8 ? 8 : 4) k_smooth_tile_V(Coef<T>
     }
     __syncthreads();
     const int I0 = (ilo + H) / 2, J0 = (jlo + H) / 2;
-    for (int p = threadIdx.x; p < (TLX / 2) * (TLY / 2); p += TLT) {
+    for (int p = threadIdx.x; p < (TLX / 2) * (TLY / 2); p += NT) {
       const int I = I0 + p % (TLX / 2), J = J0 + p / (TLX / 2);
       if (I <= nxc && J <= nc) restrict_V_at2<T>(du, dv, SP, nc, nxc, iwc, Pc, bco, I, J, c.lat);
     }
   }
-  for (int p = threadIdx.x; p < TLX * TLY; p += TLT) {
+  for (int p = threadIdx.x; p < TLX * TLY; p += NT) {
     const int gi = ilo + H + p % TLX, gj = jlo + H + p / TLX;
     const long long gk = (long long)gj * P + gi, sk = (long long)gj * SP + gi;
     if (gi <= nx && gj < n) xout[gk] = curu[sk];
@@ -1426,9 +1424,28 @@ __global__ void __launch_bounds__(TLT, TLY <= 8 ? 8 : 4) k_smooth_tile_V(Coef<T>
   }
 }
 
+// Levels whose grid has at most two tiles per SM (the GPU is otherwise idle
+// there) run 4-row tiles with 1024 threads instead of 256: a thread then
+// takes a quarter of the points per step, which shortens the latency chain
+// of the launch; every point's arithmetic is unchanged.
+static const int TLT_SMALL = 1024;
+static inline bool small_grid(const dim3& g) { return (long long)g.x * g.y <= 2 * 152; }
+
 template <typename T, int NS, int TLY, bool RR>
 void tile_D_go(const dim3& g, cudaStream_t s, const Coef<T>& c, const T* x_in, const T* b, T* x_out,
                const ChebSteps<T>& cs, const T* ct, const T* ec, int nc, int Pc, T* bco) {
+  if constexpr (TLY == 4) {
+    constexpr int NT = TLT_SMALL;
+    if (small_grid(g)) {
+      if (t_bat.off)
+        launch_k(k_smooth_tile_D<T, NS, TLY, true, RR, NT>, g, dim3(NT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc,
+                 Pc, bco);
+      else
+        launch_k(k_smooth_tile_D<T, NS, TLY, false, RR, NT>, g, dim3(NT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc,
+                 Pc, bco);
+      return;
+    }
+  }
   if (t_bat.off)
     launch_k(k_smooth_tile_D<T, NS, TLY, true, RR>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc, bco);
   else launch_k(k_smooth_tile_D<T, NS, TLY, false, RR>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc, bco);
@@ -1473,6 +1490,18 @@ int launch_smooth_tile_D_rr(const Coef<T>& c, const T* b, T* x_out, const ChebSt
 template <typename T, int NS, int TLY, bool RR>
 void tile_V_go(const dim3& g, cudaStream_t s, const Coef<T>& c, const T* x_in, const T* b, T* x_out,
                const ChebSteps<T>& cs, const T* ct, const T* ec, int nc, int Pc, T* bco) {
+  if constexpr (TLY == 4) {
+    constexpr int NT = TLT_SMALL;
+    if (small_grid(g)) {
+      if (t_bat.off)
+        launch_k(k_smooth_tile_V<T, NS, TLY, true, RR, NT>, g, dim3(NT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc,
+                 Pc, bco);
+      else
+        launch_k(k_smooth_tile_V<T, NS, TLY, false, RR, NT>, g, dim3(NT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc,
+                 Pc, bco);
+      return;
+    }
+  }
   if (t_bat.off)
     launch_k(k_smooth_tile_V<T, NS, TLY, true, RR>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc, bco);
   else launch_k(k_smooth_tile_V<T, NS, TLY, false, RR>, g, dim3(TLT), 0, s, c, x_in, b, x_out, cs, ct, ec, nc, Pc, bco);

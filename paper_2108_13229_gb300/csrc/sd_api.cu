@@ -172,11 +172,6 @@ struct sd_handle {
   double* xmm = nullptr;  // x^{n-2} (extrapolate >= 2)
   double* x3 = nullptr;   // x^{n-3} (extrapolate 3)
   double *V = nullptr, *Z = nullptr, *partial = nullptr, *scal = nullptr, *st = nullptr, *flag = nullptr;
-  // last-block counters of the one-launch reductions (last_block): CNT_MAIN for
-  // every reduction on the handle's stream, CNT_POW + kind for the power
-  // iterations of each block kind, which run concurrently on their own streams
-  unsigned* cnt = nullptr;
-  static const int CNT_MAIN = 0, CNT_POW = 1, CNT_N = 8;
   // partitioned coupling: subdomain right-hand side and the IQN-ILS state
   double* bsub = nullptr;
   IqnState iqn;
@@ -283,7 +278,6 @@ void plan_all(sd_handle* h) {
   h->partial = a.take<double>(
       std::max((long long)h->nblk * 32, (long long)std::max(4, apply_dots_max()) * resid_norms_blocks(h->g.nx, n)));
   h->scal = a.take<double>(256);
-  h->cnt = a.take<unsigned>(sd_handle::CNT_N);
   h->st = a.take<double>((long long)(h->m + 1) * h->m + 3 * h->m + 1);
   h->flag = a.take<double>(8);
   if (h->opt.coupling == SD_PARTITIONED) {
@@ -479,7 +473,7 @@ int power_lmax_all(sd_handle* h, std::vector<double>& lam, cudaStream_t s) {
       launch_hash_fill(ch->x, ch->len, 1234u + (unsigned)ch->l, sk);
       apply(*ch, ch->x, ch->y);  // y has zero padding from here on
       launch_dot(ch->y, ch->y, ch->len, h->partial + (long long)ch->kind * h->nblk, reduce_blocks(ch->len),
-                 h->scal + q0++, h->cnt + sd_handle::CNT_POW + ch->kind, sk);
+                 h->scal + q0++, sk);
     }
     for (int it = 0; it < 25 && rc == SD_OK; ++it) {
       int q = 0;
@@ -492,8 +486,7 @@ int power_lmax_all(sd_handle* h, std::vector<double>& lam, cudaStream_t s) {
         // iteration (or the start): the same kernel on the same vector
         launch_scale_by(ch->y, ch->x, ch->len, h->scal + slot, 1, sk);
         apply(*ch, ch->x, ch->y);
-        launch_dot(ch->y, ch->y, ch->len, h->partial + (long long)ch->kind * h->nblk, nb, h->scal + slot,
-                   h->cnt + sd_handle::CNT_POW + ch->kind, sk);
+        launch_dot(ch->y, ch->y, ch->len, h->partial + (long long)ch->kind * h->nblk, nb, h->scal + slot, sk);
       }
       join();
       std::vector<double> nrm(grp.size());
@@ -1109,16 +1102,15 @@ void resid_norms(sd_handle* h, int mode, const double* x, const double* b, bool 
   double* sc = h->scal;
   if (mode == MODE_MONO) {
     launch_resid_norms(coef64(h, 0), x, b, h->V, h->partial, sc, sd_handle::S_BLK, sd_handle::S_B2,
-                       sd_handle::S_BN, with_b ? 1 : 0, h->cnt + sd_handle::CNT_MAIN, h->s);
+                       sd_handle::S_BN, with_b ? 1 : 0, h->s);
     return;
   }
   const Range rg = mode_range(h, mode);
   const long long len = rg.len, o = rg.off;
   const int nb = reduce_blocks(len);
-  unsigned* cnt = h->cnt + sd_handle::CNT_MAIN;
-  if (with_b) launch_dot(b + o, b + o, len, h->partial, nb, sc + sd_handle::S_BN, cnt, h->s);
+  if (with_b) launch_dot(b + o, b + o, len, h->partial, nb, sc + sd_handle::S_BN, h->s);
   apply_op(h, mode, x, b, h->V);
-  launch_dot(h->V + o, h->V + o, len, h->partial, nb, sc + sd_handle::S_B2, cnt, h->s);
+  launch_dot(h->V + o, h->V + o, len, h->partial, nb, sc + sd_handle::S_B2, h->s);
 }
 
 // Subdomain preconditioners: the free-flow part of the block preconditioner
@@ -1172,7 +1164,6 @@ void arnoldi_orth(sd_handle* h, int j, const double* vj, double* zj, double* w, 
   const long long len = rg.len, vs = h->lenA;
   const int nb = reduce_blocks(len), m = h->m, k = j + 1;
   double* sc = h->scal;
-  unsigned* cnt = h->cnt + sd_handle::CNT_MAIN;
   // the whole system's operator forms the first pass's dot products itself
   // (up to apply_dots_max() basis vectors): no second read of w for them
   const bool fused = mode == MODE_MONO && k <= apply_dots_max();
@@ -1182,26 +1173,32 @@ void arnoldi_orth(sd_handle* h, int j, const double* vj, double* zj, double* w, 
     ProfScope ps(h, mode == MODE_MONO ? SD_PROF_APPLY : -2,
                  apply_bytes(h->g, false) + (fused ? 8.0 * k * dof : 0.0),
                  apply_flops(h->g) + (fused ? 2.0 * k * dof : 0.0));
-    if (fused) launch_apply_dots(coef64(h, 0), zj, w, h->V, vs, k, h->partial, sc + sd_handle::S_H1, cnt, s);
+    if (fused) launch_apply_dots(coef64(h, 0), zj, w, h->V, vs, k, h->partial, s);
     else apply_op(h, mode, zj, nullptr, w);
   }
   const double* Vb = h->V + rg.off;
   w += rg.off;
-  if (!fused) {
-    ProfScope ps(h, SD_PROF_MDOT, 8.0 * (k + 1) * (double)len, 2.0 * k * (double)len);
-    launch_mdot(Vb, vs, k, w, len, h->partial, nb, nb, nullptr, sc + sd_handle::S_H1, cnt, s);
+  if (fused) {
+    const int na = (int)resid_norms_blocks(h->g.nx, h->n);
+    launch_reduce(h->partial, na, k, na, sc + sd_handle::S_H1, nullptr, s);
+  } else {
+    {
+      ProfScope ps(h, SD_PROF_MDOT, 8.0 * (k + 1) * (double)len, 2.0 * k * (double)len);
+      launch_mdot(Vb, vs, k, w, len, h->partial, nb, nb, nullptr, s);
+    }
+    launch_reduce(h->partial, nb, k, nb, sc + sd_handle::S_H1, nullptr, s);
   }
   if (h->opt.orth == 0) {
     {
       ProfScope ps(h, SD_PROF_MUPDATE, 8.0 * (k + 2) * (double)len, 4.0 * k * (double)len);
-      launch_mupdate(Vb, vs, k, sc + sd_handle::S_H1, w, len, h->partial, nb, nb, 1, nullptr, sc + sd_handle::S_H2,
-                     cnt, nullptr, 0.0, s);
+      launch_mupdate(Vb, vs, k, sc + sd_handle::S_H1, w, len, h->partial, nb, nb, 1, nullptr, s);
     }
+    launch_reduce(h->partial, nb, k, nb, sc + sd_handle::S_H2, nullptr, s);
     {
       ProfScope ps(h, SD_PROF_MUPDATE, 8.0 * (k + 2) * (double)len, 2.0 * (k + 1) * (double)len);
-      launch_mupdate(Vb, vs, k, sc + sd_handle::S_H2, w, len, h->partial, nb, nb, 2, nullptr, sc + sd_handle::S_N2B,
-                     cnt, nullptr, 0.0, s);
+      launch_mupdate(Vb, vs, k, sc + sd_handle::S_H2, w, len, h->partial, nb, nb, 2, nullptr, s);
     }
+    launch_reduce(h->partial, nb, 1, nb, sc + sd_handle::S_N2B, nullptr, s);
     launch_givens(h->st, j, m, sc + sd_handle::S_H1, sc + sd_handle::S_H2, sc + sd_handle::S_N2,
                   sc + sd_handle::S_N2B, nullptr, h->flag, s);
   } else {
@@ -1209,13 +1206,14 @@ void arnoldi_orth(sd_handle* h, int j, const double* vj, double* zj, double* w, 
     const double eta = h->opt.reorth_eta;
     {
       ProfScope ps(h, SD_PROF_MUPDATE, 8.0 * (k + 2) * (double)len, 2.0 * (k + 1) * (double)len);
-      launch_mupdate(Vb, vs, k, sc + sd_handle::S_H1, w, len, h->partial, nb, nb, 2, nullptr, sc + sd_handle::S_N2,
-                     cnt, reo, eta * eta, s);
+      launch_mupdate(Vb, vs, k, sc + sd_handle::S_H1, w, len, h->partial, nb, nb, 2, nullptr, s);
     }
+    launch_reduce_decide(h->partial, nb, sc + sd_handle::S_N2, sc + sd_handle::S_H1, k, eta * eta, reo, s);
     // the second pass: its launches return at once unless the decision asked for it
-    launch_mdot(Vb, vs, k, w, len, h->partial, nb, nb, reo, sc + sd_handle::S_H2, cnt, s);
-    launch_mupdate(Vb, vs, k, sc + sd_handle::S_H2, w, len, h->partial, nb, nb, 2, reo, sc + sd_handle::S_N2B, cnt,
-                   nullptr, 0.0, s);
+    launch_mdot(Vb, vs, k, w, len, h->partial, nb, nb, reo, s);
+    launch_reduce(h->partial, nb, k, nb, sc + sd_handle::S_H2, reo, s);
+    launch_mupdate(Vb, vs, k, sc + sd_handle::S_H2, w, len, h->partial, nb, nb, 2, reo, s);
+    launch_reduce(h->partial, nb, 1, nb, sc + sd_handle::S_N2B, reo, s);
     launch_givens(h->st, j, m, sc + sd_handle::S_H1, sc + sd_handle::S_H2, sc + sd_handle::S_N2,
                   sc + sd_handle::S_N2B, reo, h->flag, s);
   }
@@ -1229,7 +1227,7 @@ void block_residual_dots(sd_handle* h) {
   const long long lo[3] = {0, g.opf, g.opm}, hi[3] = {g.opf, g.opm, g.len};
   for (int q = 0; q < 3; ++q)
     launch_dot(h->V + lo[q], h->V + lo[q], hi[q] - lo[q], h->partial, reduce_blocks(hi[q] - lo[q]),
-               h->scal + sd_handle::S_BLK + q, h->cnt + sd_handle::CNT_MAIN, h->s);
+               h->scal + sd_handle::S_BLK + q, h->s);
 }
 int block_residuals(sd_handle* h, double bnorm, sd_step_info* info) {
   block_residual_dots(h);
@@ -1645,8 +1643,8 @@ int step_partitioned(sd_handle* h, sd_step_info* info) {
   // residual of the coupled state in the monolithic system
   double* sc = h->scal;
   apply_op(h, MODE_MONO, h->x, h->b, h->V);
-  launch_dot(h->V, h->V, g.len, h->partial, h->nblk, sc + sd_handle::S_B2, h->cnt + sd_handle::CNT_MAIN, s);
-  launch_dot(h->b, h->b, g.len, h->partial, h->nblk, sc + sd_handle::S_BN, h->cnt + sd_handle::CNT_MAIN, s);
+  launch_dot(h->V, h->V, g.len, h->partial, h->nblk, sc + sd_handle::S_B2, s);
+  launch_dot(h->b, h->b, g.len, h->partial, h->nblk, sc + sd_handle::S_BN, s);
   CK(cudaMemcpyAsync(h->hflag + 10, sc + sd_handle::S_B2, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(h->hflag + 11, sc + sd_handle::S_BN, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));

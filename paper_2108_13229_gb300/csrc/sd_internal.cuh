@@ -68,65 +68,6 @@ __device__ __forceinline__ P bsh(P p, long long o) {
   return p ? reinterpret_cast<P>(reinterpret_cast<uintptr_t>(p) + o) : p;
 }
 
-// ------------------------------------------------ last-block reductions
-// A launch whose blocks each leave partial sums partial[q * ps + b] (q < kk,
-// b < nb, b the block's index within its instance) adds them up in the block
-// that finishes last: every block counts itself in *cnt (a counter of the
-// handle's zeroed arena, moved per instance in a lockstep batch like every
-// other buffer) once its partials are written; the block that brings the
-// count to nb resets it for the next launch and forms the sums in a fixed
-// order, so the result does not depend on which block that is.  One launch
-// where a partials kernel and a reduction kernel ran before.  The partials
-// are published by one fence of thread 0 after the block barrier (the
-// barrier orders the other threads' writes before it), so the block's other
-// warps do not wait for their own stores; a kernel that can should store its
-// vector output after this call, leaving that fence nothing else to wait for.
-__device__ __forceinline__ bool last_block(unsigned* cnt, unsigned nb, int tid) {
-  __shared__ unsigned s_last;
-  __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    const unsigned t = atomicAdd(cnt, 1u);
-    s_last = t + 1u == nb ? 1u : 0u;
-    if (s_last) atomicExch(cnt, 0u);
-  }
-  __syncthreads();
-  if (!s_last) return false;
-  __threadfence();
-  return true;
-}
-
-// In the last block: red[q][0] = sum over b < nb of partial[q * ps + b] for
-// q < kk (kk <= the rows of red), by the NT threads of the block: thread t
-// adds b = t, t + NT, ... in turn, U loads in flight at a time (the partials
-// come from L2, and a chain of dependent loads would cost one L2 latency
-// each), then a fixed binary tree over t.  Every thread may read red[q][0]
-// on return.
-template <int NT, int U>
-__device__ __forceinline__ void last_block_sums(const double* partial, long long ps, int nb, int kk,
-                                                double (*red)[NT], int tid) {
-  for (int q = 0; q < kk; ++q) {
-    const double* p = partial + (long long)q * ps;
-    double s = 0.0;
-    for (int b0 = tid; b0 < nb; b0 += NT * U) {
-      double v[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) v[u] = b0 + u * NT < nb ? __ldcg(p + b0 + u * NT) : 0.0;
-#pragma unroll
-      for (int u = 0; u < U; ++u) s += v[u];
-    }
-    red[q][tid] = s;
-  }
-  __syncthreads();
-  for (int st = NT / 2; st > 0; st >>= 1) {
-    for (int e = tid; e < kk * st; e += NT) {
-      const int q = e / st, t = e - q * st;
-      red[q][t] += red[q][t + st];
-    }
-    __syncthreads();
-  }
-}
-
 template <typename... Ts>
 struct last_is_bat : std::false_type {};
 template <typename T>
@@ -267,19 +208,18 @@ void launch_darcy_schur_top(double* TyR, const double* w, const double* rg, int 
 
 // whole-system operator (FP64): y = A x  or  y = b - A x
 void launch_apply_full(const Coef<double>& c, const double* x, const double* b, double* y, cudaStream_t s);
-// r = b - A x together with its norms, in one launch: sc[blk + 0..2] =
-// ||r||^2 over the velocity, continuity and Darcy rows, sc[b2] = ||r||^2, and
-// with with_b sc[bn] = ||b||^2 (partial: 4 * resid_norms_blocks(n) doubles
-// of scratch; cnt as in launch_mdot)
+// r = b - A x together with its norms: sc[blk + 0..2] = ||r||^2 over the
+// velocity, continuity and Darcy rows, sc[b2] = ||r||^2, and with with_b
+// sc[bn] = ||b||^2 (partial: 4 * resid_norms_blocks(n) doubles of scratch)
 void launch_resid_norms(const Coef<double>& c, const double* x, const double* b, double* r, double* partial,
-                        double* sc, int blk, int b2, int bn, int with_b, unsigned* cnt, cudaStream_t s);
+                        double* sc, int blk, int b2, int bn, int with_b, cudaStream_t s);
 long long resid_norms_blocks(int nx, int n);
-// y = A x together with the first Gram-Schmidt pass's dot products of the
-// Arnoldi step, in one launch: out[q] = V_q . y for q < k <= apply_dots_max(),
-// V_q = V + q vs in the whole-vector layout (partial: apply_dots_max() *
-// resid_norms_blocks(n) doubles of scratch; cnt as in launch_mdot)
+// y = A x together with the block partials of the first Gram-Schmidt pass's
+// dot products of the Arnoldi step: partial[q * nblk + blk] for V_q . y, q <
+// k <= apply_dots_max(), V_q = V + q vs in the whole-vector layout, nblk =
+// resid_norms_blocks(n) (launch_reduce sums them)
 void launch_apply_dots(const Coef<double>& c, const double* x, double* y, const double* V, long long vs, int k,
-                       double* partial, double* out, unsigned* cnt, cudaStream_t s);
+                       double* partial, cudaStream_t s);
 int apply_dots_max();
 // the free-flow rows of it (u, v, p_ff) with the porous-medium unknowns taken as zero;
 // the Darcy rows of y are not written; vdir: the v_Gamma rows are identities
@@ -449,26 +389,28 @@ void launch_precond_exit(const Coef<double>& c, double* z, const T* eD, cudaStre
 // ------------------------------------------------------------- sd_krylov.cu
 // number of blocks (= partial sums per dot product) for a vector of length len
 int reduce_blocks(long long len);
-// out[i] = V_i . w for i < k, in one launch (block partials in partial[i * ps
-// + blk], summed by the last block; cnt: a zeroed counter no other launch in
-// flight uses).  cond (may be null): nothing runs when cond[0] == 0.
+// partial[i * ps + blk] = sum over the block's elements of V_i . w, i < k
+//   cond (may be null): skipped when cond[0] == 0
 void launch_mdot(const double* V, long long vstride, int k, const double* w, long long len, double* partial,
-                 int ps, int nblk, const double* cond, double* out, unsigned* cnt, cudaStream_t s);
-// w -= sum_i coef[i] V_i, then out[i] = V_i . w for i < k (mode 1) or out[0] =
-// w . w (mode 2), summed as in launch_mdot.  Mode 2 with reo != null also
-// takes the re-orthogonalisation decision of the first Gram-Schmidt pass:
-// reo[0] = 1 when w . w < eta2 (sum_i coef[i]^2 + w . w), the right side
-// being ||w||^2 before the projection (Pythagoras over the orthonormal V_i),
-// else 0.
+                 int ps, int nblk, const double* cond, cudaStream_t s);
+// w -= sum_i coef[i] V_i, then partial dots of V_i . w (mode 1) or w . w (mode 2)
 void launch_mupdate(const double* V, long long vstride, int k, const double* coef, double* w, long long len,
-                    double* partial, int ps, int nblk, int mode, const double* cond, double* out, unsigned* cnt,
-                    double* reo, double eta2, cudaStream_t s);
+                    double* partial, int ps, int nblk, int mode, const double* cond, cudaStream_t s);
+// out[i] = sum_b partial[i * ps + b], fixed order; cond (may be null): nothing
+// when cond[0] == 0
+void launch_reduce(const double* partial, int nblk, int k, int ps, double* out, const double* cond, cudaStream_t s);
+// out[0] = sum_b partial[b] (= w'.w', the first Gram-Schmidt pass's projected
+// w) and the re-orthogonalisation decision reo[0] = 1 when w'.w' < eta2
+// (sum_{i < k1} h1[i]^2 + w'.w'), the right side being ||w||^2 before the
+// projection (Pythagoras over the orthonormal basis), else 0
+void launch_reduce_decide(const double* partial, int nblk, double* out, const double* h1, int k1, double eta2,
+                          double* reo, cudaStream_t s);
 // history shift (x3 <- x_mm, x_mm <- x_m, x_m <- x; x3 may be null) and the
 // extrapolation of the given order (1: linear, 2: quadratic, 3: cubic)
 void launch_extrapolate(double* x, double* xm, double* xmm, double* x3, long long len, int order, cudaStream_t s);
-// generic dot of two vectors -> out[0] (one launch; cnt as in launch_mdot)
+// generic dot of two vectors: partials then reduce -> out[0]
 void launch_dot(const double* a, const double* b, long long len, double* partial, int nblk, double* out,
-                unsigned* cnt, cudaStream_t s);
+                cudaStream_t s);
 // y = alpha_dev[0]^p * x  (p = -1: divide by sqrt(alpha) ... see implementation)
 void launch_scale_by(const double* x, double* y, long long len, const double* sdev, int mode, cudaStream_t s);
 // (kdev, may be null: when given, k = kdev[0], read on the device; in a lockstep

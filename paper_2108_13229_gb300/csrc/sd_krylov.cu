@@ -5,9 +5,12 @@
 //  * multi-dot and fused update+dot kernels for classical Gram-Schmidt with
 //    one re-orthogonalisation (CGS2): each block accumulates its slice of
 //    all k dot products in registers, sums them over its threads in shared
-//    memory and writes one partial per block; the block that finishes last
-//    adds the partials up in a fixed order, so every reduction is
-//    deterministic (bitwise repeatable) and takes one launch.
+//    memory and writes one partial per block; a one-block kernel per dot adds
+//    the partials up in a fixed order, so every reduction is deterministic
+//    (bitwise repeatable).  (Summing them in the block that finishes last
+//    instead, one launch fewer, was measured slower: with programmatic
+//    dependent launch the separate kernel's launch is hidden, while the
+//    last-block count lengthens every block of the producer.)
 //  * Givens rotations, residual estimate and back substitution on the
 //    (m+1) x m Hessenberg matrix, kept on the device (one thread).
 //  * dense coarse solve x = A_c^{-1} b with the inverse built at setup by a
@@ -78,12 +81,11 @@ __device__ __forceinline__ void load_own(const double* __restrict__ w, double* w
   }
 }
 
-// out[q] = V_q . w, q < k: partial[q * ps + blk] = the block's share, summed
-// by the last block (last_block).  cond (may be null): skip when 0.
+// partial[q * ps + blk] = the block's share of V_q . w, q < k (summed by
+// k_reduce).  cond (may be null): skip when 0.
 __global__ void __launch_bounds__(KT) k_mdot(const double* __restrict__ V, long long vs, int k,
                                              const double* __restrict__ w, long long len, double* __restrict__ partial,
-                                             int ps, const double* __restrict__ cond, double* __restrict__ out,
-                                             unsigned* cnt, Bat bt) {
+                                             int ps, const double* __restrict__ cond, Bat bt) {
   griddep_wait();
   long long o;
   if (!bat_enter(bt, o)) return;
@@ -92,8 +94,6 @@ __global__ void __launch_bounds__(KT) k_mdot(const double* __restrict__ V, long 
     w = bsh(w, o);
     partial = bsh(partial, o);
     cond = bsh(cond, o);
-    out = bsh(out, o);
-    cnt = bsh(cnt, o);
   }
   if (cond && cond[0] == 0.0) return;
   __shared__ double red[KMAX_REG][KT];
@@ -109,30 +109,21 @@ __global__ void __launch_bounds__(KT) k_mdot(const double* __restrict__ V, long 
   }
   if (q < k) red[q][threadIdx.x] = own_dot(V + (long long)q * vs, we, base, len);
   block_tree(red, k, partial, ps);
-  if (!last_block(cnt, gridDim.x, threadIdx.x)) return;
-  last_block_sums<KT, 8>(partial, ps, gridDim.x, k, red, threadIdx.x);
-  if (threadIdx.x < k) out[threadIdx.x] = red[threadIdx.x][0];
 }
 
 void launch_mdot(const double* V, long long vstride, int k, const double* w, long long len, double* partial, int ps,
-                 int nblk, const double* cond, double* out, unsigned* cnt, cudaStream_t s) {
+                 int nblk, const double* cond, cudaStream_t s) {
   SD_COUNT(1);
-  launch_k(k_mdot, dim3(nblk), dim3(KT), 0, s, V, vstride, k, w, len, partial, ps, cond, out, cnt);
+  launch_k(k_mdot, dim3(nblk), dim3(KT), 0, s, V, vstride, k, w, len, partial, ps, cond);
 }
 
-// w -= sum_q coef_q V_q, then
-//   mode 1: out[q] = V_q . w, q < k (second Gram-Schmidt pass),
-//   mode 2: out[0] = w . w (norm of the new basis vector); with reo, the
-//           re-orthogonalisation decision (Daniel-Gragg-Kaufman-Stewart):
-//           a second pass is needed when the projection removed most of w,
-//           w'.w' < eta2 ||w||^2, ||w||^2 = sum_q coef_q^2 + w'.w' for the
-//           orthonormal V_q (so no separate norm of w before the projection).
-// Sums as in k_mdot.
+// w -= sum_q coef_q V_q, then partials (as k_mdot) of
+//   mode 1: V_q . w, q < k (second Gram-Schmidt pass),
+//   mode 2: w . w (norm of the new basis vector).
 __global__ void __launch_bounds__(KT) k_mupdate(const double* __restrict__ V, long long vs, int k,
                                                 const double* __restrict__ coef, double* __restrict__ w,
                                                 long long len, double* __restrict__ partial, int ps, int mode,
-                                                const double* __restrict__ cond, double* __restrict__ out,
-                                                unsigned* cnt, double* __restrict__ reo, double eta2, Bat bt) {
+                                                const double* __restrict__ cond, Bat bt) {
   griddep_wait();
   long long o;
   if (!bat_enter(bt, o)) return;
@@ -142,9 +133,6 @@ __global__ void __launch_bounds__(KT) k_mupdate(const double* __restrict__ V, lo
     w = bsh(w, o);
     partial = bsh(partial, o);
     cond = bsh(cond, o);
-    out = bsh(out, o);
-    cnt = bsh(cnt, o);
-    reo = bsh(reo, o);
   }
   if (cond && cond[0] == 0.0) return;
   __shared__ double cf[KMAX_REG];
@@ -174,6 +162,11 @@ __global__ void __launch_bounds__(KT) k_mupdate(const double* __restrict__ V, lo
       if (e < len) we[t] = fma(-c0, v0[e], we[t]);
     }
   }
+#pragma unroll
+  for (int t = 0; t < KE; ++t) {
+    const long long e = base + (long long)t * KT;
+    if (e < len) w[e] = we[t];
+  }
   if (mode == 1) {
     q = 0;
     for (; q + 1 < k; q += 2) {
@@ -194,38 +187,75 @@ __global__ void __launch_bounds__(KT) k_mupdate(const double* __restrict__ V, lo
     red[0][threadIdx.x] = s0 + s1;
     block_tree(red, 1, partial, ps);
   }
-  const bool last = last_block(cnt, gridDim.x, threadIdx.x);
-  // w after the count (see last_block); no block of this launch reads it
-#pragma unroll
-  for (int t = 0; t < KE; ++t) {
-    const long long e = base + (long long)t * KT;
-    if (e < len) w[e] = we[t];
-  }
-  if (!last) return;
-  const int kk = mode == 1 ? k : 1;
-  last_block_sums<KT, 8>(partial, ps, gridDim.x, kk, red, threadIdx.x);
-  if (threadIdx.x < kk) out[threadIdx.x] = red[threadIdx.x][0];
-  if (mode == 2 && reo && threadIdx.x == 0) {
-    const double n2a = red[0][0];
-    double nw2 = 0.0;
-    for (int i = 0; i < k; ++i) nw2 = fma(cf[i], cf[i], nw2);
-    nw2 += n2a;
-    reo[0] = n2a < eta2 * nw2 ? 1.0 : 0.0;
-  }
 }
 
 void launch_mupdate(const double* V, long long vstride, int k, const double* coef, double* w, long long len,
-                    double* partial, int ps, int nblk, int mode, const double* cond, double* out, unsigned* cnt,
-                    double* reo, double eta2, cudaStream_t s) {
+                    double* partial, int ps, int nblk, int mode, const double* cond, cudaStream_t s) {
   SD_COUNT(1);
-  launch_k(k_mupdate, dim3(nblk), dim3(KT), 0, s, V, vstride, k, coef, w, len, partial, ps, mode, cond, out, cnt,
-           reo, eta2);
+  launch_k(k_mupdate, dim3(nblk), dim3(KT), 0, s, V, vstride, k, coef, w, len, partial, ps, mode, cond);
+}
+
+// out[q] = sum_b partial[q * ps + b], q < k, one block per q in a fixed-order
+// tree; cond (may be null): nothing when cond[0] == 0 (a skipped pass).
+// With reo (k = 1, the norm w'.w' of the first pass's projected w): the
+// re-orthogonalisation decision (Daniel-Gragg-Kaufman-Stewart), reo[0] = 1
+// when w'.w' < eta2 ||w||^2, else 0, where ||w||^2 = sum_{i < k1} h1_i^2 +
+// w'.w' (Pythagoras over the orthonormal basis: w = sum_i h1_i V_i + w'), so
+// no separate norm of w before the projection is formed.
+__global__ void k_reduce(const double* __restrict__ partial, int nblk, int k, int ps, double* __restrict__ out,
+                         const double* __restrict__ cond, const double* __restrict__ h1, int k1, double eta2,
+                         double* __restrict__ reo, Bat bt) {
+  griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  if (bt.off) {
+    partial = bsh(partial, o);
+    out = bsh(out, o);
+    cond = bsh(cond, o);
+    h1 = bsh(h1, o);
+    reo = bsh(reo, o);
+  }
+  __shared__ double sm[RT / 32];
+  const int q = blockIdx.x;
+  if (q >= k) return;
+  if (cond && cond[0] == 0.0) return;
+  const double* p = partial + (long long)q * ps;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += RT) s += p[b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < RT / 32; ++w) t += sm[w];
+    out[q] = t;
+    if (reo) {
+      double nw2 = 0.0;
+      for (int i = 0; i < k1; ++i) nw2 = fma(h1[i], h1[i], nw2);
+      nw2 += t;
+      reo[0] = t < eta2 * nw2 ? 1.0 : 0.0;
+    }
+  }
+}
+
+void launch_reduce(const double* partial, int nblk, int k, int ps, double* out, const double* cond, cudaStream_t s) {
+  SD_COUNT(1);
+  launch_k(k_reduce, dim3(k), dim3(RT), 0, s, partial, nblk, k, ps, out, cond, (const double*)nullptr, 0, 0.0,
+           (double*)nullptr);
+}
+
+void launch_reduce_decide(const double* partial, int nblk, double* out, const double* h1, int k1, double eta2,
+                          double* reo, cudaStream_t s) {
+  SD_COUNT(1);
+  launch_k(k_reduce, dim3(1), dim3(RT), 0, s, partial, nblk, 1, nblk, out, (const double*)nullptr, h1, k1, eta2, reo);
 }
 
 void launch_dot(const double* a, const double* b, long long len, double* partial, int nblk, double* out,
-                unsigned* cnt, cudaStream_t s) {
-  SD_COUNT(1);
-  launch_k(k_mdot, dim3(nblk), dim3(KT), 0, s, a, 0, 1, b, len, partial, nblk, (const double*)nullptr, out, cnt);
+                cudaStream_t s) {
+  launch_mdot(a, 0, 1, b, len, partial, nblk, nblk, nullptr, s);
+  launch_reduce(partial, nblk, 1, nblk, out, nullptr, s);
 }
 
 // mode 0: y = sdev[0] * x ; mode 1: y = x / sqrt(sdev[0])

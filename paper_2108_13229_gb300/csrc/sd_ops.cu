@@ -41,24 +41,18 @@ static inline int rows_vel(int) { return 1; }
 static inline dim3 grid2R(int nx, int ny, int R) { return dim3((nx + BX - 1) / BX, (ny + BY * R - 1) / (BY * R)); }
 
 // ------------------------------------------------------- whole operator (K1)
-// What a launch of the operator forms on the side of y: with ND > 0 the dot
-// products of y with the Krylov basis vectors V_q = V + q vs, q < k <= ND
-// (the first Gram-Schmidt pass of the Arnoldi step); with PS the residual's
-// norms.  partial: the block partials; out: where the last block leaves the
-// sums (PS: the scalar slots blk, b2, bn of launch_resid_norms); cnt: the
-// launch's last-block counter.
+// What a launch of the operator forms on the side of y, as block partials in
+// partial[q * nblocks + block]: with ND > 0 the dot products of y with the
+// Krylov basis vectors V_q = V + q vs, q < ND (the first Gram-Schmidt pass of
+// the Arnoldi step); with PS the residual's norms.
 struct ApplySide {
   const double* V = nullptr;
   long long vs = 0;
-  int k = 0;
   double* partial = nullptr;
-  double* out = nullptr;
-  unsigned* cnt = nullptr;
-  int blk = 0, b2 = 0, bn = 0, with_b = 0;
 };
 
-// dacc[q] += V_q[idx] * a, q < ND (= sd.k: one instantiation per count, as
-// a masked-off FP64 instruction still takes its FP64-pipe cycles)
+// dacc[q] += V_q[idx] * a, q < ND (one instantiation per count, as a
+// masked-off FP64 instruction still takes its FP64-pipe cycles)
 template <int ND>
 __device__ __forceinline__ void side_dots(const ApplySide& sd, long long idx, double a, double* dacc) {
 #pragma unroll
@@ -311,12 +305,11 @@ __device__ __forceinline__ void apply_body(const Coef<double>& c, const double* 
 }
 
 // PS / ND: the block's sums of acc (PS, apply_body's norms: q = 0..2, PS 2:
-// 0..3) or dacc (ND: q < sd.k) in sd.partial[q * nblocks + block], in a fixed
-// order; FP64 adds are scarce on this part, so the block sums its values
-// through shared memory with one warp per quantity (eight serial adds per
-// lane, then five butterfly rounds) rather than a butterfly in every warp.
-// The last block to finish adds the partials up (last_block) and writes
-// sd.out: PS, the slots of launch_resid_norms; ND, out[q] = V_q . y.
+// 0..3) or dacc (ND: q < ND) in sd.partial[q * nblocks + block], in a fixed
+// order, so repeated runs agree bit for bit.  FP64 adds are scarce on this
+// part, so the block sums its values through shared memory with one warp per
+// quantity (eight serial adds per lane, then five butterfly rounds) rather
+// than a butterfly in every warp.
 template <int R, int FF, bool RES, int PS = 0, int ND = 0>
 __global__ void __launch_bounds__(BX * BY, (PS || ND) ? 3 : 4)
     k_apply_full(Coef<double> c, const double* __restrict__ x, const double* __restrict__ b, double* __restrict__ y,
@@ -331,8 +324,6 @@ __global__ void __launch_bounds__(BX * BY, (PS || ND) ? 3 : 4)
     y = bsh(y, o);
     sd.V = bsh(sd.V, o);
     sd.partial = bsh(sd.partial, o);
-    sd.out = bsh(sd.out, o);
-    sd.cnt = bsh(sd.cnt, o);
   }
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   double dacc[ND > 0 ? ND : 1];
@@ -341,54 +332,81 @@ __global__ void __launch_bounds__(BX * BY, (PS || ND) ? 3 : 4)
   apply_body<R, FF, RES, PS, ND>(c, x, b, y, acc, sd, dacc);
   if constexpr (PS > 0 || ND > 0) {
     constexpr int NQ = PS == 2 ? 4 : PS == 1 ? 3 : ND;
-    constexpr int NR = NQ > 4 ? NQ : 4;
-    const int nq = NQ;
-    __shared__ double red[NR][BX * BY];
+    __shared__ double red[NQ][BX * BY];
     const int t = threadIdx.y * blockDim.x + threadIdx.x;
 #pragma unroll
-    for (int q = 0; q < NQ; ++q)
-      if (q < nq) red[q][t] = PS > 0 ? acc[q] : dacc[q];
+    for (int q = 0; q < NQ; ++q) red[q][t] = PS > 0 ? acc[q] : dacc[q];
     __syncthreads();
     const int wp = t >> 5, lane = t & 31;
-    const unsigned nbk = gridDim.x * gridDim.y;
-    if (wp < nq) {
+    if (wp < NQ) {
       const double* r = red[wp] + lane * (BX * BY / 32);
       double v = r[0];
 #pragma unroll
       for (int e = 1; e < BX * BY / 32; ++e) v += r[e];
 #pragma unroll
       for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
-      if (lane == 0) sd.partial[wp * (long long)nbk + blockIdx.y * gridDim.x + blockIdx.x] = v;
-    }
-    if (!last_block(sd.cnt, nbk, t)) return;
-    last_block_sums<BX * BY, 4>(sd.partial, nbk, (int)nbk, nq, red, t);
-    if constexpr (PS > 0) {
-      if (t == 0) {
-        double* sc = sd.out;
-        sc[sd.blk] = red[0][0];
-        sc[sd.blk + 1] = red[1][0];
-        sc[sd.blk + 2] = red[2][0];
-        sc[sd.b2] = (red[0][0] + red[1][0]) + red[2][0];
-        if (PS == 2) sc[sd.bn] = red[3][0];
+      if (lane == 0) {
+        const long long nbk = (long long)gridDim.x * gridDim.y;
+        sd.partial[wp * nbk + (long long)blockIdx.y * gridDim.x + blockIdx.x] = v;
       }
-    } else {
-      if (t < nq) sd.out[t] = red[t][0];
     }
   }
 }
 
+// sc[blk + q] (q = 0..2) = the sums of squares of the residual's velocity,
+// continuity and Darcy rows, sc[b2] = their total ((q0 + q1) + q2), and with
+// with_b sc[bn] = the sum of squares of b; from the block partials of
+// k_apply_full<.., PS>, each summed in a fixed order (every thread's partials
+// loaded at once, then one warp per quantity).
+__global__ void __launch_bounds__(256) k_reduce_resid(const double* __restrict__ partial, int nbk,
+                                                      double* __restrict__ sc, int blk, int b2, int bn, int with_b,
+                                                      Bat bt) {
+  griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  if (bt.off) {
+    partial = bsh(partial, o);
+    sc = bsh(sc, o);
+  }
+  __shared__ double red[4][256];
+  __shared__ double tot[4];
+  const int t = threadIdx.x;
+  const int nq = with_b ? 4 : 3;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int k = t; k < nbk; k += 256)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (q < nq) v[q] += partial[(long long)q * nbk + k];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) red[q][t] = v[q];
+  __syncthreads();
+  const int wp = t >> 5, lane = t & 31;
+  if (wp < nq) {
+    const double* r = red[wp] + lane * 8;
+    double w = r[0];
+#pragma unroll
+    for (int e = 1; e < 8; ++e) w += r[e];
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) w += __shfl_xor_sync(0xffffffffu, w, d);
+    if (lane == 0) tot[wp] = w;
+  }
+  __syncthreads();
+  if (t == 0) {
+    sc[blk] = tot[0];
+    sc[blk + 1] = tot[1];
+    sc[blk + 2] = tot[2];
+    sc[b2] = (tot[0] + tot[1]) + tot[2];
+    if (with_b) sc[bn] = tot[3];
+  }
+}
+
 void launch_resid_norms(const Coef<double>& c, const double* x, const double* b, double* r, double* partial,
-                        double* sc, int blk, int b2, int bn, int with_b, unsigned* cnt, cudaStream_t s) {
-  SD_COUNT(1);
+                        double* sc, int blk, int b2, int bn, int with_b, cudaStream_t s) {
+  SD_COUNT(2);
   const int R = rows_apply(c.n);
   const dim3 g = grid2R(c.nx + 1, c.n + 1, R);
   ApplySide sd;
   sd.partial = partial;
-  sd.out = sc;
-  sd.cnt = cnt;
-  sd.blk = blk;
-  sd.b2 = b2;
-  sd.bn = bn;
   if (R == 4) {
     if (with_b) launch_k(k_apply_full<4, 0, true, 2>, g, dim3(BX, BY), 0, s, c, x, b, r, sd);
     else launch_k(k_apply_full<4, 0, true, 1>, g, dim3(BX, BY), 0, s, c, x, b, r, sd);
@@ -396,6 +414,8 @@ void launch_resid_norms(const Coef<double>& c, const double* x, const double* b,
     if (with_b) launch_k(k_apply_full<1, 0, true, 2>, g, dim3(BX, BY), 0, s, c, x, b, r, sd);
     else launch_k(k_apply_full<1, 0, true, 1>, g, dim3(BX, BY), 0, s, c, x, b, r, sd);
   }
+  launch_k(k_reduce_resid, dim3(1), dim3(256), 0, s, (const double*)partial, (int)(g.x * g.y), sc, blk, b2, bn,
+           with_b);
 }
 
 // blocks of the operator's launch (partial sums per quantity of launch_resid_norms)
@@ -408,17 +428,14 @@ long long resid_norms_blocks(int nx, int n) {
 int apply_dots_max() { return 4; }
 
 void launch_apply_dots(const Coef<double>& c, const double* x, double* y, const double* V, long long vs, int k,
-                       double* partial, double* out, unsigned* cnt, cudaStream_t s) {
+                       double* partial, cudaStream_t s) {
   SD_COUNT(1);
   const int R = rows_apply(c.n);
   const dim3 g = grid2R(c.nx + 1, c.n + 1, R);
   ApplySide sd;
   sd.V = V;
   sd.vs = vs;
-  sd.k = k;
   sd.partial = partial;
-  sd.out = out;
-  sd.cnt = cnt;
   const double* nb = nullptr;
   const dim3 bl(BX, BY);
   if (R == 4) {

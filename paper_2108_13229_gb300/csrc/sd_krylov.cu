@@ -270,8 +270,7 @@ __global__ void k_scale_by(const double* __restrict__ x, double* __restrict__ y,
     sdev = bsh(sdev, o);
   }
   const double f = mode == 0 ? sdev[0] : 1.0 / sqrt(sdev[0]);
-  // 32-bit indices (a vector has fewer than 2^31 entries): 64-bit index
-  // arithmetic would share the FP64 pipe with the products
+  // 32-bit indices (a vector has fewer than 2^31 entries)
   const int n = (int)len;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) y[e] = f * x[e];
 }

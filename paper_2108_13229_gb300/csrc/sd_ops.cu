@@ -2094,8 +2094,8 @@ __global__ void k_convert(const double* __restrict__ a, T* __restrict__ b, long 
     a = bsh(a, o);
     b = bsh(b, o);
   }
-  // 32-bit indices (a vector has fewer than 2^31 entries): 64-bit index
-  // arithmetic and conversions would share the FP64 pipe with the conversion
+  // 32-bit indices (a vector has fewer than 2^31 entries); the conversion
+  // itself runs on the FP64 pipe
   const int n = (int)len;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) b[k] = (T)a[k];
 }

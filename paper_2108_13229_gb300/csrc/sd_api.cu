@@ -195,8 +195,10 @@ struct sd_handle {
   double prof_ms = 0.0, prof_bytes = 0.0, prof_flops = 0.0;
   long long prof_launches = 0;
   // scalar slots in scal[]
+  // S_VSC + j: the scale of basis vector j of the whole-system solve, which
+  // keeps its basis vectors unnormalised (arnoldi_orth)
   static const int S_H1 = 0, S_H2 = 32, S_N2 = 64, S_B2 = 65, S_BN = 66, S_N2B = 67, S_REO = 68, S_BLK = 69,
-                   S_Y = 96, S_CTL = 128;
+                   S_Y = 96, S_CTL = 128, S_VSC = 200;
 };
 
 namespace {
@@ -973,8 +975,9 @@ void vcycle_cell(MG<T>& M, int l, bool poisson, cudaStream_t s, const sd_handle*
 // SD_TRI_SCHUR the ff pressure block uses S^-1 = (mu/(gamma h^2)) I +
 // (1/dt) L_p^-1 (viscous and mass-dominated limits of B^T V^-1 B), with
 // L_p = B^T B / h^2 solved by its own V-cycle.
+// rs (may be null: 1): the device scale of r (an unnormalised basis vector)
 template <typename T>
-void precond(sd_handle* h, MG<T>& M, const double* r, double* z) {
+void precond(sd_handle* h, MG<T>& M, const double* r, double* z, const double* rs) {
   cudaStream_t s = h->s;
   const Coef<double> c = coef64(h, 0);
   const int mode = h->opt.precond;
@@ -987,20 +990,20 @@ void precond(sd_handle* h, MG<T>& M, const double* r, double* z) {
     // B'_1 z_pm
     cudaEventRecord(h->ev_fork, s);
     cudaStreamWaitEvent(h->s2, h->ev_fork, 0);
-    launch_convert<T>(r + h->g.opm, M.L[0].D.b, h->g.lenD, h->s2);
+    launch_convert<T>(r + h->g.opm, M.L[0].D.b, h->g.lenD, h->s2, rs);
     vcycle_cell<T>(M, 0, false, h->s2, h);
     launch_precond_exit<T>(c, z, M.L[0].D.res, h->s2);
     cudaEventRecord(h->ev_join, h->s2);
     const T* eP = nullptr;
     if (h->opt.schur_mass) {
-      launch_convert<T>(r + h->g.opf, M.L[0].Pb.b, h->g.lenD, s);
+      launch_convert<T>(r + h->g.opf, M.L[0].Pb.b, h->g.lenD, s, rs);
       vcycle_cell<T>(M, 0, true, s, h);
       eP = M.L[0].Pb.res;
     }
     cudaStreamWaitEvent(s, h->ev_join, 0);
-    launch_precond_entry<T>(c, r, z, schur, eP, 1.0 / h->dt, 1, 1, M.L[0].V.b, s);
+    launch_precond_entry<T>(c, r, z, schur, eP, 1.0 / h->dt, 1, 1, M.L[0].V.b, s, rs);
     vcycle_V<T>(M, 0, s, h);
-    launch_precond_mid<T>(c, r, z, M.L[0].V.res, 0, (T*)nullptr, s);
+    launch_precond_mid<T>(c, r, z, M.L[0].V.res, 0, (T*)nullptr, s, rs);
     return;
   }
   // block-diagonal Darcy part (no C'_1 coupling): its V-cycle runs on the
@@ -1009,33 +1012,33 @@ void precond(sd_handle* h, MG<T>& M, const double* r, double* z) {
   if (overlap) {
     cudaEventRecord(h->ev_fork, s);
     cudaStreamWaitEvent(h->s2, h->ev_fork, 0);
-    launch_convert<T>(r + h->g.opm, M.L[0].D.b, h->g.lenD, h->s2);
+    launch_convert<T>(r + h->g.opm, M.L[0].D.b, h->g.lenD, h->s2, rs);
     vcycle_cell<T>(M, 0, false, h->s2, h);
     launch_precond_exit<T>(c, z, M.L[0].D.res, h->s2);
     cudaEventRecord(h->ev_join, h->s2);
   }
   const T* eP = nullptr;
   if (tri && h->opt.schur_mass) {
-    launch_convert<T>(r + h->g.opf, M.L[0].Pb.b, h->g.lenD, s);
+    launch_convert<T>(r + h->g.opf, M.L[0].Pb.b, h->g.lenD, s, rs);
     vcycle_cell<T>(M, 0, true, s, h);
     eP = M.L[0].Pb.res;
   }
-  launch_precond_entry<T>(c, r, z, schur, eP, 1.0 / h->dt, tri, 0, M.L[0].V.b, s);
+  launch_precond_entry<T>(c, r, z, schur, eP, 1.0 / h->dt, tri, 0, M.L[0].V.b, s, rs);
   vcycle_V<T>(M, 0, s, h);
-  if (mode == SD_PV_BGS_I) launch_precond_bgs_pff<T>(c, r, z, M.L[0].V.res, s);
+  if (mode == SD_PV_BGS_I) launch_precond_bgs_pff<T>(c, r, z, M.L[0].V.res, s, rs);
   if (overlap) {
-    launch_precond_mid<T>(c, r, z, M.L[0].V.res, 0, (T*)nullptr, s);
+    launch_precond_mid<T>(c, r, z, M.L[0].V.res, 0, (T*)nullptr, s, rs);
     cudaStreamWaitEvent(s, h->ev_join, 0);
     return;
   }
-  launch_precond_mid<T>(c, r, z, M.L[0].V.res, mode != SD_PV_BJ_I, M.L[0].D.b, s);
+  launch_precond_mid<T>(c, r, z, M.L[0].V.res, mode != SD_PV_BJ_I, M.L[0].D.b, s, rs);
   vcycle_cell<T>(M, 0, false, s, h);
   launch_precond_exit<T>(c, z, M.L[0].D.res, s);
 }
 
-void apply_precond(sd_handle* h, const double* r, double* z) {
-  if (h->opt.precision == SD_MIXED) precond<float>(h, h->mg32, r, z);
-  else precond<double>(h, h->mg64, r, z);
+void apply_precond(sd_handle* h, const double* r, double* z, const double* rs = nullptr) {
+  if (h->opt.precision == SD_MIXED) precond<float>(h, h->mg32, r, z, rs);
+  else precond<double>(h, h->mg64, r, z, rs);
 }
 
 // ------------------------------------------------ solve modes
@@ -1142,9 +1145,9 @@ void precond_sub(sd_handle* h, MG<T>& M, int mode, const double* r, double* z) {
     cudaMemcpyAsync(z + h->g.ov, r + h->g.ov, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, s);
 }
 
-void apply_precond_mode(sd_handle* h, int mode, const double* r, double* z) {
+void apply_precond_mode(sd_handle* h, int mode, const double* r, double* z, const double* rs = nullptr) {
   if (mode == MODE_MONO) {
-    apply_precond(h, r, z);
+    apply_precond(h, r, z, rs);
   } else if (h->opt.precision == SD_MIXED) {
     precond_sub<float>(h, h->mg32, mode, r, z);
   } else {
@@ -1164,14 +1167,22 @@ void arnoldi_orth(sd_handle* h, int j, const double* vj, double* zj, double* w, 
   const long long len = rg.len, vs = h->lenA;
   const int nb = reduce_blocks(len), m = h->m, k = j + 1;
   double* sc = h->scal;
+  // the whole system keeps its basis vectors unnormalised: V_q stands for
+  // vsc[q] W_q, the stored W_q being the Gram-Schmidt remainder w' (or the
+  // residual for q = 0) and vsc[q] = 1 / ||W_q|| its scale (k_init_cycle,
+  // k_givens); the scales enter the preconditioner's input (in FP64, before
+  // its conversion: the same values as a normalised vector), the dots (after
+  // their sums) and the updates' coefficients, so no pass over HBM
+  // normalises a vector.  The subdomain solves normalise explicitly.
+  const bool mono = mode == MODE_MONO;
+  double* vsc = mono ? sc + sd_handle::S_VSC : nullptr;
   // the whole system's operator forms the first pass's dot products itself
   // (up to apply_dots_max() basis vectors): no second read of w for them
-  const bool fused = mode == MODE_MONO && k <= apply_dots_max();
-  apply_precond_mode(h, mode, vj, zj);
+  const bool fused = mono && k <= apply_dots_max();
+  apply_precond_mode(h, mode, vj, zj, mono ? vsc + j : nullptr);
   {
     const double dof = (double)dof_of(h);
-    ProfScope ps(h, mode == MODE_MONO ? SD_PROF_APPLY : -2,
-                 apply_bytes(h->g, false) + (fused ? 8.0 * k * dof : 0.0),
+    ProfScope ps(h, mono ? SD_PROF_APPLY : -2, apply_bytes(h->g, false) + (fused ? 8.0 * k * dof : 0.0),
                  apply_flops(h->g) + (fused ? 2.0 * k * dof : 0.0));
     if (fused) launch_apply_dots(coef64(h, 0), zj, w, h->V, vs, k, h->partial, s);
     else apply_op(h, mode, zj, nullptr, w);
@@ -1180,43 +1191,45 @@ void arnoldi_orth(sd_handle* h, int j, const double* vj, double* zj, double* w, 
   w += rg.off;
   if (fused) {
     const int na = (int)resid_norms_blocks(h->g.nx, h->n);
-    launch_reduce(h->partial, na, k, na, sc + sd_handle::S_H1, nullptr, s);
+    launch_reduce(h->partial, na, k, na, sc + sd_handle::S_H1, nullptr, s, vsc);
   } else {
     {
       ProfScope ps(h, SD_PROF_MDOT, 8.0 * (k + 1) * (double)len, 2.0 * k * (double)len);
       launch_mdot(Vb, vs, k, w, len, h->partial, nb, nb, nullptr, s);
     }
-    launch_reduce(h->partial, nb, k, nb, sc + sd_handle::S_H1, nullptr, s);
+    launch_reduce(h->partial, nb, k, nb, sc + sd_handle::S_H1, nullptr, s, vsc);
   }
   if (h->opt.orth == 0) {
     {
       ProfScope ps(h, SD_PROF_MUPDATE, 8.0 * (k + 2) * (double)len, 4.0 * k * (double)len);
-      launch_mupdate(Vb, vs, k, sc + sd_handle::S_H1, w, len, h->partial, nb, nb, 1, nullptr, s);
+      launch_mupdate(Vb, vs, k, sc + sd_handle::S_H1, w, len, h->partial, nb, nb, 1, nullptr, s, vsc);
     }
-    launch_reduce(h->partial, nb, k, nb, sc + sd_handle::S_H2, nullptr, s);
+    launch_reduce(h->partial, nb, k, nb, sc + sd_handle::S_H2, nullptr, s, vsc);
     {
       ProfScope ps(h, SD_PROF_MUPDATE, 8.0 * (k + 2) * (double)len, 2.0 * (k + 1) * (double)len);
-      launch_mupdate(Vb, vs, k, sc + sd_handle::S_H2, w, len, h->partial, nb, nb, 2, nullptr, s);
+      launch_mupdate(Vb, vs, k, sc + sd_handle::S_H2, w, len, h->partial, nb, nb, 2, nullptr, s, vsc);
     }
     launch_reduce(h->partial, nb, 1, nb, sc + sd_handle::S_N2B, nullptr, s);
     launch_givens(h->st, j, m, sc + sd_handle::S_H1, sc + sd_handle::S_H2, sc + sd_handle::S_N2,
-                  sc + sd_handle::S_N2B, nullptr, h->flag, s);
+                  sc + sd_handle::S_N2B, nullptr, h->flag, s, vsc);
   } else {
     double* reo = sc + sd_handle::S_REO;
     const double eta = h->opt.reorth_eta;
     {
       ProfScope ps(h, SD_PROF_MUPDATE, 8.0 * (k + 2) * (double)len, 2.0 * (k + 1) * (double)len);
-      launch_mupdate(Vb, vs, k, sc + sd_handle::S_H1, w, len, h->partial, nb, nb, 2, nullptr, s);
+      launch_mupdate(Vb, vs, k, sc + sd_handle::S_H1, w, len, h->partial, nb, nb, 2, nullptr, s, vsc);
     }
     launch_reduce_decide(h->partial, nb, sc + sd_handle::S_N2, sc + sd_handle::S_H1, k, eta * eta, reo, s);
     // the second pass: its launches return at once unless the decision asked for it
     launch_mdot(Vb, vs, k, w, len, h->partial, nb, nb, reo, s);
-    launch_reduce(h->partial, nb, k, nb, sc + sd_handle::S_H2, reo, s);
-    launch_mupdate(Vb, vs, k, sc + sd_handle::S_H2, w, len, h->partial, nb, nb, 2, reo, s);
+    launch_reduce(h->partial, nb, k, nb, sc + sd_handle::S_H2, reo, s, vsc);
+    launch_mupdate(Vb, vs, k, sc + sd_handle::S_H2, w, len, h->partial, nb, nb, 2, reo, s, vsc);
     launch_reduce(h->partial, nb, 1, nb, sc + sd_handle::S_N2B, reo, s);
     launch_givens(h->st, j, m, sc + sd_handle::S_H1, sc + sd_handle::S_H2, sc + sd_handle::S_N2,
-                  sc + sd_handle::S_N2B, reo, h->flag, s);
+                  sc + sd_handle::S_N2B, reo, h->flag, s, vsc);
   }
+  // the subdomain solves' new basis vector: w / h_{j+1,j}
+  if (!mono) launch_scale_by(w, w, len, h->flag + 1, 0, s);
 }
 
 // Per-block residual norms of the whole-system residual r (in h->V, whole
@@ -1331,7 +1344,6 @@ int build_solve_graph(sd_handle* h, int mode, const double* b, double* x) {
     double* zj = h->Z + (long long)j * vs;
     double* w = h->V + (long long)(j + 1) * vs;
     arnoldi_orth(h, j, vj, zj, w, mode);
-    launch_scale_by(w + o, w + o, len, h->flag + 1, 0, s);
     return t_launch_count - l0;
   };
   err = cudaGraphCreate(&top, 0);
@@ -1358,8 +1370,8 @@ int build_solve_graph(sd_handle* h, int mode, const double* b, double* x) {
   if (begin(wbody, false)) {
     const long long l0 = t_launch_count;
     launch_cycle_head(cs, s);
-    launch_init_cycle(h->st, m, sc + sd_handle::S_B2, h->flag, s);
-    launch_scale_by(h->V + o, h->V + o, len, h->flag + 1, 0, s);
+    launch_init_cycle(h->st, m, sc + sd_handle::S_B2, h->flag, s, sc + sd_handle::S_VSC);
+    if (mode != MODE_MONO) launch_scale_by(h->V + o, h->V + o, len, h->flag + 1, 0, s);
     step(0);
     const long long k = t_launch_count - l0 + 1;
     launch_step_ctrl(h->flag, ctl, maxit, (double)k, m > 1, m > 1 ? cs.c[1] : 0, s);
@@ -1496,8 +1508,8 @@ int fgmres(sd_handle* h, const double* b, double* x, sd_step_info* info, int mod
     }
     if (iters >= h->opt.max_iters) { status = SD_E_NOCONV; break; }
     ++restarts;
-    launch_init_cycle(h->st, m, sc + sd_handle::S_B2, h->flag, s);
-    launch_scale_by(h->V + o, h->V + o, len, h->flag + 1, 0, s);
+    launch_init_cycle(h->st, m, sc + sd_handle::S_B2, h->flag, s, sc + sd_handle::S_VSC);
+    if (mode != MODE_MONO) launch_scale_by(h->V + o, h->V + o, len, h->flag + 1, 0, s);
     int k = 0;
     bool numeric = false;
     for (int j = 0; j < m; ++j) {
@@ -1512,7 +1524,6 @@ int fgmres(sd_handle* h, const double* b, double* x, sd_step_info* info, int mod
           const long long l0 = t_launch_count;
           CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
           arnoldi_orth(h, j, vj, zj, w, mode);
-          launch_scale_by(w + o, w + o, len, h->flag + 1, 0, s);
           CK(cudaStreamEndCapture(s, &gr));
           const cudaError_t ie = cudaGraphInstantiate(&gx[j], gr, 0);
           cudaGraphDestroy(gr);
@@ -1526,7 +1537,6 @@ int fgmres(sd_handle* h, const double* b, double* x, sd_step_info* info, int mod
         g_launch_count.fetch_add(gc[j]);
       } else {
         arnoldi_orth(h, j, vj, zj, w, mode);
-        launch_scale_by(w + o, w + o, len, h->flag + 1, 0, s);
       }
       CK(cudaMemcpyAsync(h->hflag, h->flag, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
@@ -1998,8 +2008,7 @@ int fgmres_lockstep(Lockstep& L, std::vector<sd_step_info>& si) {
     if (!any) break;
     for (int i = 0; i < B; ++i) L.act[i] = cyc[i];
     CKR(set_act(L, s));
-    launch_init_cycle(h->st, m, sc + sd_handle::S_B2, h->flag, s);
-    launch_scale_by(h->V, h->V, len, h->flag + 1, 0, s);
+    launch_init_cycle(h->st, m, sc + sd_handle::S_B2, h->flag, s, sc + sd_handle::S_VSC);
     for (int j = 0; j < m; ++j) {
       double* vj = h->V + (long long)j * vs;
       double* zj = h->Z + (long long)j * vs;
@@ -2010,7 +2019,6 @@ int fgmres_lockstep(Lockstep& L, std::vector<sd_step_info>& si) {
           const long long l0 = t_launch_count;
           CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
           arnoldi_orth(h, j, vj, zj, w);
-          launch_scale_by(w, w, len, h->flag + 1, 0, s);
           CK(cudaStreamEndCapture(s, &gr));
           const cudaError_t ie = cudaGraphInstantiate(&L.gexec[j], gr, 0);
           cudaGraphDestroy(gr);
@@ -2022,7 +2030,6 @@ int fgmres_lockstep(Lockstep& L, std::vector<sd_step_info>& si) {
         g_launch_count.fetch_add(L.gcount[j]);
       } else {
         arnoldi_orth(h, j, vj, zj, w);
-        launch_scale_by(w, w, len, h->flag + 1, 0, s);
       }
       CKR(gather(L, h->flag, 6, s));
       bool running = false;
@@ -2159,7 +2166,6 @@ int build_group_branch(Lockstep& L, cudaGraph_t top, long long* pre) {
     double* zj = h->Z + (long long)j * vs;
     double* w = h->V + (long long)(j + 1) * vs;
     arnoldi_orth(h, j, vj, zj, w);
-    launch_scale_by(w, w, len, h->flag + 1, 0, s);
     return t_launch_count - l0;
   };
   cudaGraphConditionalHandle loop = 0;
@@ -2193,8 +2199,7 @@ int build_group_branch(Lockstep& L, cudaGraph_t top, long long* pre) {
       NoBatScope nb;
       launch_cycle_head(cs, s);
     }
-    launch_init_cycle(h->st, m, sc + sd_handle::S_B2, h->flag, s);
-    launch_scale_by(h->V, h->V, len, h->flag + 1, 0, s);
+    launch_init_cycle(h->st, m, sc + sd_handle::S_B2, h->flag, s, sc + sd_handle::S_VSC);
     step(0);
     const long long k = t_launch_count - l0 + 1;
     {

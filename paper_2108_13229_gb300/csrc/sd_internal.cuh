@@ -198,7 +198,7 @@ template <typename T>
 void launch_setup_coef(const double* Kp, int n, int cx, int P, double mu, double alpha, int lat, int xdir, int b0,
                        int b1, int nx, int iw, T* w, T* rg, T* Tx, T* Ty, cudaStream_t s);
 template <typename T>
-void launch_convert(const double* src, T* dst, long long len, cudaStream_t s);
+void launch_convert(const double* src, T* dst, long long len, cudaStream_t s, const double* rs = nullptr);
 // top faces (row n) of the preconditioner's Darcy coefficients TyR: h^2 / d_i,
 // d_i the diagonal of the v_Gamma row of floor face iw + i (Eq. (5)), the
 // local Schur complement of the interface velocity eliminated through B'_1
@@ -372,16 +372,19 @@ int launch_wave_D(const Coef<float>& c, const float* x_in, const float* b, float
 //  entry: zpf = schur * r_pf + cmass * eP (eP: pressure-Laplacian solve, may be
 //  null); rV = T(r_v - B zpf - B'_1 z_pm) (B omitted: use_B == 0; B'_1 only with
 //  use_B1, reading the z_pm already in z)
+//  rs (entry, mid, bgs_pff and launch_convert; null: 1): the device scale of
+//  r, which is read as rs[0] r (the Krylov basis vector kept unnormalised)
 template <typename T>
 void launch_precond_entry(const Coef<double>& c, const double* r, double* z, double schur, const T* eP, double cmass,
-                          int use_B, int use_B1, T* rV, cudaStream_t s);
+                          int use_B, int use_B1, T* rV, cudaStream_t s, const double* rs = nullptr);
 //  mid: z_v = double(eV); rD = T(r_pm - C'_1 z_v) (C'_1 omitted: use_C == 0; rD null: not written)
 template <typename T>
 void launch_precond_mid(const Coef<double>& c, const double* r, double* z, const T* eV, int use_C, T* rD,
-                        cudaStream_t s);
+                        cudaStream_t s, const double* rs = nullptr);
 //  block Gauss-Seidel with identity on p_ff: z_pf = r_pf - C z_v
 template <typename T>
-void launch_precond_bgs_pff(const Coef<double>& c, const double* r, double* z, const T* eV, cudaStream_t s);
+void launch_precond_bgs_pff(const Coef<double>& c, const double* r, double* z, const T* eV, cudaStream_t s,
+                            const double* rs = nullptr);
 //  exit: z_pm = double(eD)
 template <typename T>
 void launch_precond_exit(const Coef<double>& c, double* z, const T* eD, cudaStream_t s);
@@ -394,11 +397,15 @@ int reduce_blocks(long long len);
 void launch_mdot(const double* V, long long vstride, int k, const double* w, long long len, double* partial,
                  int ps, int nblk, const double* cond, cudaStream_t s);
 // w -= sum_i coef[i] V_i, then partial dots of V_i . w (mode 1) or w . w (mode 2)
+//   qs (may be null): scales of the V_i (kept unnormalised), folded into the coefficients
 void launch_mupdate(const double* V, long long vstride, int k, const double* coef, double* w, long long len,
-                    double* partial, int ps, int nblk, int mode, const double* cond, cudaStream_t s);
+                    double* partial, int ps, int nblk, int mode, const double* cond, cudaStream_t s,
+                    const double* qs = nullptr);
 // out[i] = sum_b partial[i * ps + b], fixed order; cond (may be null): nothing
 // when cond[0] == 0
-void launch_reduce(const double* partial, int nblk, int k, int ps, double* out, const double* cond, cudaStream_t s);
+//   qs (may be null): out[i] is multiplied by qs[i] (scales of unnormalised basis vectors)
+void launch_reduce(const double* partial, int nblk, int k, int ps, double* out, const double* cond, cudaStream_t s,
+                   const double* qs = nullptr);
 // out[0] = sum_b partial[b] (= w'.w', the first Gram-Schmidt pass's projected
 // w) and the re-orthogonalisation decision reo[0] = 1 when w'.w' < eta2
 // (sum_{i < k1} h1[i]^2 + w'.w'), the right side being ||w||^2 before the
@@ -421,13 +428,15 @@ void launch_axpy_multi(double* x, const double* Z, long long zstride, const doub
 //   the new column is hcol1 + hcol2 and its sub-diagonal sqrt(nrm2b) if reo is
 //   null or reo[0] != 0 (second Gram-Schmidt pass done), else hcol1 and
 //   sqrt(nrm2a) (hcol2 and nrm2b are then not read);
-//   flag[5] = j + 1, the basis vectors of the cycle so far
+//   flag[5] = j + 1, the basis vectors of the cycle so far; vsc (may be null):
+//   vsc[j + 1] = flag[1] = 1 / h_{j+1,j}, the scale of the new basis vector
 void launch_givens(double* st, int j, int m, const double* hcol1, const double* hcol2, const double* nrm2a,
-                   const double* nrm2b, const double* reo, double* flag, cudaStream_t s);
+                   const double* nrm2b, const double* reo, double* flag, cudaStream_t s, double* vsc = nullptr);
 void launch_backsolve(double* st, int k, int m, double* y, const double* kdev, cudaStream_t s);
 // lockstep batches: out[z * count + t] = instance z's src[t]
 void launch_gather_inst(const double* src, int count, double* out, cudaStream_t s);
-void launch_init_cycle(double* st, int m, const double* beta2, double* flag, cudaStream_t s);
+//   vsc (may be null): vsc[0] = 1 / beta, the scale of the cycle's first basis vector
+void launch_init_cycle(double* st, int m, const double* beta2, double* flag, cudaStream_t s, double* vsc = nullptr);
 
 // device-side loop control of a whole FGMRES solve replayed as one graph
 // (sd_krylov.cu).  ctl[C_TOL] tolerance on ||r||, ctl[C_BN] ||b||, the

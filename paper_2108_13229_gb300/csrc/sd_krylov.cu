@@ -117,13 +117,15 @@ void launch_mdot(const double* V, long long vstride, int k, const double* w, lon
   launch_k(k_mdot, dim3(nblk), dim3(KT), 0, s, V, vstride, k, w, len, partial, ps, cond);
 }
 
-// w -= sum_q coef_q V_q, then partials (as k_mdot) of
+// w -= sum_q coef_q qs_q V_q (qs null: 1; the scales of basis vectors kept
+// unnormalised), then partials (as k_mdot) of
 //   mode 1: V_q . w, q < k (second Gram-Schmidt pass),
 //   mode 2: w . w (norm of the new basis vector).
 __global__ void __launch_bounds__(KT) k_mupdate(const double* __restrict__ V, long long vs, int k,
                                                 const double* __restrict__ coef, double* __restrict__ w,
                                                 long long len, double* __restrict__ partial, int ps, int mode,
-                                                const double* __restrict__ cond, Bat bt) {
+                                                const double* __restrict__ cond, const double* __restrict__ qs,
+                                                Bat bt) {
   griddep_wait();
   long long o;
   if (!bat_enter(bt, o)) return;
@@ -133,11 +135,13 @@ __global__ void __launch_bounds__(KT) k_mupdate(const double* __restrict__ V, lo
     w = bsh(w, o);
     partial = bsh(partial, o);
     cond = bsh(cond, o);
+    qs = bsh(qs, o);
   }
   if (cond && cond[0] == 0.0) return;
   __shared__ double cf[KMAX_REG];
   __shared__ double red[KMAX_REG][KT];
-  if (threadIdx.x < KMAX_REG) cf[threadIdx.x] = threadIdx.x < k ? coef[threadIdx.x] : 0.0;
+  if (threadIdx.x < KMAX_REG)
+    cf[threadIdx.x] = threadIdx.x < k ? (qs ? coef[threadIdx.x] * qs[threadIdx.x] : coef[threadIdx.x]) : 0.0;
   __syncthreads();
   const long long base = (long long)blockIdx.x * KT * KE + threadIdx.x;
   double we[KE];
@@ -190,21 +194,24 @@ __global__ void __launch_bounds__(KT) k_mupdate(const double* __restrict__ V, lo
 }
 
 void launch_mupdate(const double* V, long long vstride, int k, const double* coef, double* w, long long len,
-                    double* partial, int ps, int nblk, int mode, const double* cond, cudaStream_t s) {
+                    double* partial, int ps, int nblk, int mode, const double* cond, cudaStream_t s,
+                    const double* qs) {
   SD_COUNT(1);
-  launch_k(k_mupdate, dim3(nblk), dim3(KT), 0, s, V, vstride, k, coef, w, len, partial, ps, mode, cond);
+  launch_k(k_mupdate, dim3(nblk), dim3(KT), 0, s, V, vstride, k, coef, w, len, partial, ps, mode, cond, qs);
 }
 
-// out[q] = sum_b partial[q * ps + b], q < k, one block per q in a fixed-order
-// tree; cond (may be null): nothing when cond[0] == 0 (a skipped pass).
+// out[q] = sum_b partial[q * ps + b] (times qs[q] unless qs is null: the
+// scale of basis vector q, kept unnormalised), q < k, one block per q in a
+// fixed-order tree; cond (may be null): nothing when cond[0] == 0 (a skipped
+// pass).
 // With reo (k = 1, the norm w'.w' of the first pass's projected w): the
 // re-orthogonalisation decision (Daniel-Gragg-Kaufman-Stewart), reo[0] = 1
 // when w'.w' < eta2 ||w||^2, else 0, where ||w||^2 = sum_{i < k1} h1_i^2 +
 // w'.w' (Pythagoras over the orthonormal basis: w = sum_i h1_i V_i + w'), so
 // no separate norm of w before the projection is formed.
 __global__ void k_reduce(const double* __restrict__ partial, int nblk, int k, int ps, double* __restrict__ out,
-                         const double* __restrict__ cond, const double* __restrict__ h1, int k1, double eta2,
-                         double* __restrict__ reo, Bat bt) {
+                         const double* __restrict__ cond, const double* __restrict__ qs, const double* __restrict__ h1,
+                         int k1, double eta2, double* __restrict__ reo, Bat bt) {
   griddep_wait();
   long long o;
   if (!bat_enter(bt, o)) return;
@@ -212,6 +219,7 @@ __global__ void k_reduce(const double* __restrict__ partial, int nblk, int k, in
     partial = bsh(partial, o);
     out = bsh(out, o);
     cond = bsh(cond, o);
+    qs = bsh(qs, o);
     h1 = bsh(h1, o);
     reo = bsh(reo, o);
   }
@@ -230,7 +238,7 @@ __global__ void k_reduce(const double* __restrict__ partial, int nblk, int k, in
     double t = 0.0;
 #pragma unroll
     for (int w = 0; w < RT / 32; ++w) t += sm[w];
-    out[q] = t;
+    out[q] = qs ? t * qs[q] : t;
     if (reo) {
       double nw2 = 0.0;
       for (int i = 0; i < k1; ++i) nw2 = fma(h1[i], h1[i], nw2);
@@ -240,16 +248,18 @@ __global__ void k_reduce(const double* __restrict__ partial, int nblk, int k, in
   }
 }
 
-void launch_reduce(const double* partial, int nblk, int k, int ps, double* out, const double* cond, cudaStream_t s) {
+void launch_reduce(const double* partial, int nblk, int k, int ps, double* out, const double* cond, cudaStream_t s,
+                   const double* qs) {
   SD_COUNT(1);
-  launch_k(k_reduce, dim3(k), dim3(RT), 0, s, partial, nblk, k, ps, out, cond, (const double*)nullptr, 0, 0.0,
+  launch_k(k_reduce, dim3(k), dim3(RT), 0, s, partial, nblk, k, ps, out, cond, qs, (const double*)nullptr, 0, 0.0,
            (double*)nullptr);
 }
 
 void launch_reduce_decide(const double* partial, int nblk, double* out, const double* h1, int k1, double eta2,
                           double* reo, cudaStream_t s) {
   SD_COUNT(1);
-  launch_k(k_reduce, dim3(1), dim3(RT), 0, s, partial, nblk, 1, nblk, out, (const double*)nullptr, h1, k1, eta2, reo);
+  launch_k(k_reduce, dim3(1), dim3(RT), 0, s, partial, nblk, 1, nblk, out, (const double*)nullptr,
+           (const double*)nullptr, h1, k1, eta2, reo);
 }
 
 void launch_dot(const double* a, const double* b, long long len, double* partial, int nblk, double* out,
@@ -338,13 +348,14 @@ void launch_axpy_multi(double* x, const double* Z, long long zstride, const doub
 // cs[m], sn[m], g[m+1].  flag[0] = |g_{j+1}| (residual estimate),
 // flag[1] = 1 / h_{j+1,j} (scale of the next basis vector), flag[2] = 1 on
 // NaN/Inf, flag[3] = 1 on breakdown (h_{j+1,j} == 0).
-__global__ void k_init_cycle(double* st, int m, const double* beta2, double* flag, Bat bt) {
+__global__ void k_init_cycle(double* st, int m, const double* beta2, double* flag, double* vsc, Bat bt) {
   griddep_wait();
   long long o;
   if (!bat_enter(bt, o)) return;
   st = bsh(st, o);
   beta2 = bsh(beta2, o);
   flag = bsh(flag, o);
+  vsc = bsh(vsc, o);
   if (threadIdx.x != 0) return;
   double* g = st + (m + 1) * m + 2 * m;
   const double beta = sqrt(beta2[0]);
@@ -355,15 +366,16 @@ __global__ void k_init_cycle(double* st, int m, const double* beta2, double* fla
   flag[2] = isfinite(beta) ? 0.0 : 1.0;
   flag[3] = 0.0;
   flag[5] = 0.0;
+  if (vsc) vsc[0] = flag[1];
 }
 
-void launch_init_cycle(double* st, int m, const double* beta2, double* flag, cudaStream_t s) {
+void launch_init_cycle(double* st, int m, const double* beta2, double* flag, cudaStream_t s, double* vsc) {
   SD_COUNT(1);
-  launch_k(k_init_cycle, dim3(1), dim3(32), 0, s, st, m, beta2, flag);
+  launch_k(k_init_cycle, dim3(1), dim3(32), 0, s, st, m, beta2, flag, vsc);
 }
 
 __global__ void k_givens(double* st, int j, int m, const double* h1, const double* h2, const double* nrm2a,
-                         const double* nrm2b, const double* reo, double* flag, Bat bt) {
+                         const double* nrm2b, const double* reo, double* flag, double* vsc, Bat bt) {
   griddep_wait();
   long long o;
   if (!bat_enter(bt, o)) return;
@@ -376,6 +388,7 @@ __global__ void k_givens(double* st, int j, int m, const double* h1, const doubl
     nrm2b = bsh(nrm2b, o);
     reo = bsh(reo, o);
     flag = bsh(flag, o);
+    vsc = bsh(vsc, o);
   }
   const bool second = reo == nullptr || reo[0] != 0.0;
   const double* nrm2 = second ? nrm2b : nrm2a;
@@ -408,12 +421,13 @@ __global__ void k_givens(double* st, int j, int m, const double* h1, const doubl
   flag[3] = hn > 0.0 ? 0.0 : 1.0;
   flag[4] = second ? 1.0 : 0.0;
   flag[5] = (double)(j + 1);
+  if (vsc) vsc[j + 1] = flag[1];
 }
 
 void launch_givens(double* st, int j, int m, const double* hcol1, const double* hcol2, const double* nrm2a,
-                   const double* nrm2b, const double* reo, double* flag, cudaStream_t s) {
+                   const double* nrm2b, const double* reo, double* flag, cudaStream_t s, double* vsc) {
   SD_COUNT(1);
-  launch_k(k_givens, dim3(1), dim3(32), 0, s, st, j, m, hcol1, hcol2, nrm2a, nrm2b, reo, flag);
+  launch_k(k_givens, dim3(1), dim3(32), 0, s, st, j, m, hcol1, hcol2, nrm2a, nrm2b, reo, flag, vsc);
 }
 
 // Polynomial extrapolation in time over the known levels: the history shifts

@@ -1792,10 +1792,14 @@ int launch_coarse_cycle(const CoarseCycle<T>& q, cudaStream_t s) {
 // Block upper-triangular Stokes part (Sec. 4, zero block replaced by the
 // Schur approximation S^ = h^2/(2 mu) I, or by I): z_pf = schur * r_pf,
 // then the velocity rhs r_v - B z_pf for the V-block multigrid.
+// rs (may be null: 1) in these glue kernels: the scale of r, the Krylov
+// basis vector kept unnormalised (r is used as rs[0] r, formed in FP64 before
+// the conversion, so the multigrid sees the same values as from a normalised
+// vector).
 template <typename T>
 __global__ void k_precond_entry(Coef<double> c, const double* __restrict__ r, double* __restrict__ z, T schur,
                                 const T* __restrict__ eP, T cmass, T hT, int useB, int useB1, T* __restrict__ rV,
-                                Bat bt) {
+                                const double* __restrict__ rs, Bat bt) {
   griddep_wait();
   long long o;
   if (!bat_enter(bt, o)) return;
@@ -1805,7 +1809,9 @@ __global__ void k_precond_entry(Coef<double> c, const double* __restrict__ r, do
     z = bsh(z, o);
     eP = bsh(eP, o);
     rV = bsh(rV, o);
+    rs = bsh(rs, o);
   }
+  const double sr = rs ? rs[0] : 1.0;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int n = c.n, nx = c.nx, P = c.P;
@@ -1816,7 +1822,7 @@ __global__ void k_precond_entry(Coef<double> c, const double* __restrict__ r, do
   // west and south neighbours (staged in shared memory: each FP64 value is
   // converted once)
   const T ts = schur, tm = cmass;
-  auto zp = [&](long long kc) -> T { return ts * (T)rpf[kc] + (eP ? tm * eP[kc] : T(0)); };
+  auto zp = [&](long long kc) -> T { return ts * (T)(rpf[kc] * sr) + (eP ? tm * eP[kc] : T(0)); };
   __shared__ T sz[BY + 1][BX + 1];
   const int i0 = blockIdx.x * blockDim.x - 1, j0 = blockIdx.y * blockDim.y - 1;
   for (int p = threadIdx.y * blockDim.x + threadIdx.x; p < (BX + 1) * (BY + 1); p += BX * BY) {
@@ -1830,7 +1836,7 @@ __global__ void k_precond_entry(Coef<double> c, const double* __restrict__ r, do
   if (i < nx && j < n) z[(long long)(2 * n + 1) * P + (long long)j * P + i] = (double)zc;
   if (j < n) {
     const long long k = (long long)j * P + i;
-    T val = (T)r[k];
+    T val = (T)(r[k] * sr);
     if (useB && i > 0 && i < nx) val -= h * (zc - sz[lj][li - 1]);
     else if (useB && c.lat) val -= i == 0 ? h * zc : -h * sz[lj][li - 1];  // traction side
     rV[k] = val;
@@ -1838,7 +1844,7 @@ __global__ void k_precond_entry(Coef<double> c, const double* __restrict__ r, do
   if (i < nx) {
     const long long kv = (long long)j * P + i;
     const long long k = (long long)n * P + kv;
-    T val = (T)r[k];
+    T val = (T)(r[k] * sr);
     const bool iface = j == 0 && on_gamma(c, i);  // (a floor face beside it is a Dirichlet row)
     if (useB && j < n && (j > 0 || iface)) {
       if (j > 0) val -= h * (zc - sz[lj - 1][li]);
@@ -1852,15 +1858,16 @@ __global__ void k_precond_entry(Coef<double> c, const double* __restrict__ r, do
 
 template <typename T>
 void launch_precond_entry(const Coef<double>& c, const double* r, double* z, double schur, const T* eP, double cmass,
-                          int use_B, int use_B1, T* rV, cudaStream_t s) {
+                          int use_B, int use_B1, T* rV, cudaStream_t s, const double* rs) {
   SD_COUNT(1);
   launch_k(k_precond_entry<T>, dim3(grid2(c.nx + 1, c.n + 1)), dim3(dim3(BX, BY)), 0, s, c, r, z, (T)schur, eP,
-           (T)cmass, (T)c.h, use_B, use_B1, rV);
+           (T)cmass, (T)c.h, use_B, use_B1, rV, rs);
 }
 
 template <typename T>
 __global__ void k_precond_mid(Coef<double> c, const double* __restrict__ r, double* __restrict__ z,
-                              const T* __restrict__ eV, int useC, T* __restrict__ rD, Bat bt) {
+                              const T* __restrict__ eV, int useC, T* __restrict__ rD, const double* __restrict__ rs,
+                              Bat bt) {
   griddep_wait();
   long long o;
   if (!bat_enter(bt, o)) return;
@@ -1870,6 +1877,7 @@ __global__ void k_precond_mid(Coef<double> c, const double* __restrict__ r, doub
     z = bsh(z, o);
     eV = bsh(eV, o);
     rD = bsh(rD, o);
+    rs = bsh(rs, o);
   }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -1885,7 +1893,7 @@ __global__ void k_precond_mid(Coef<double> c, const double* __restrict__ r, doub
   }
   if (rD && i < n && j < n) {
     const long long kc = (long long)j * P + i;
-    T val = (T)r[(long long)(3 * n + 1) * P + kc];
+    T val = (T)(r[(long long)(3 * n + 1) * P + kc] * (rs ? rs[0] : 1.0));
     if (useC && j == n - 1) val -= (T)c.h * eV[(long long)n * P + c.iw + i];
     rD[kc] = val;
   }
@@ -1893,9 +1901,9 @@ __global__ void k_precond_mid(Coef<double> c, const double* __restrict__ r, doub
 
 template <typename T>
 void launch_precond_mid(const Coef<double>& c, const double* r, double* z, const T* eV, int use_C, T* rD,
-                        cudaStream_t s) {
+                        cudaStream_t s, const double* rs) {
   SD_COUNT(1);
-  launch_k(k_precond_mid<T>, dim3(grid2(c.nx + 1, c.n + 1)), dim3(dim3(BX, BY)), 0, s, c, r, z, eV, use_C, rD);
+  launch_k(k_precond_mid<T>, dim3(grid2(c.nx + 1, c.n + 1)), dim3(dim3(BX, BY)), 0, s, c, r, z, eV, use_C, rD, rs);
 }
 
 template <typename T>
@@ -1924,7 +1932,7 @@ void launch_precond_exit(const Coef<double>& c, double* z, const T* eD, cudaStre
 // gives z_pf = r_pf - C z_v (C: the continuity rows of Eq. (2)).
 template <typename T>
 __global__ void k_precond_bgs_pff(Coef<double> c, const double* __restrict__ r, double* __restrict__ z,
-                                  const T* __restrict__ eV, Bat bt) {
+                                  const T* __restrict__ eV, const double* __restrict__ rs, Bat bt) {
   griddep_wait();
   long long o;
   if (!bat_enter(bt, o)) return;
@@ -1933,6 +1941,7 @@ __global__ void k_precond_bgs_pff(Coef<double> c, const double* __restrict__ r, 
     r = bsh(r, o);
     z = bsh(z, o);
     eV = bsh(eV, o);
+    rs = bsh(rs, o);
   }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -1946,13 +1955,14 @@ __global__ void k_precond_bgs_pff(Coef<double> c, const double* __restrict__ r, 
   if (c.lat || i >= 1) s -= (double)u[kc];
   if (j + 1 <= n - 1) s += (double)v[kc + P];
   const long long kp = (long long)(2 * n + 1) * P + kc;
-  z[kp] = r[kp] - c.h * s;
+  z[kp] = r[kp] * (rs ? rs[0] : 1.0) - c.h * s;
 }
 
 template <typename T>
-void launch_precond_bgs_pff(const Coef<double>& c, const double* r, double* z, const T* eV, cudaStream_t s) {
+void launch_precond_bgs_pff(const Coef<double>& c, const double* r, double* z, const T* eV, cudaStream_t s,
+                            const double* rs) {
   SD_COUNT(1);
-  launch_k(k_precond_bgs_pff<T>, dim3(grid2(c.nx, c.n)), dim3(dim3(BX, BY)), 0, s, c, r, z, eV);
+  launch_k(k_precond_bgs_pff<T>, dim3(grid2(c.nx, c.n)), dim3(dim3(BX, BY)), 0, s, c, r, z, eV, rs);
 }
 
 // ------------------------------------------------------------------ setup
@@ -2086,26 +2096,29 @@ void launch_darcy_schur_top(double* TyR, const double* w, const double* rg, int 
 }
 
 template <typename T>
-__global__ void k_convert(const double* __restrict__ a, T* __restrict__ b, long long len, Bat bt) {
+__global__ void k_convert(const double* __restrict__ a, T* __restrict__ b, long long len,
+                          const double* __restrict__ rs, Bat bt) {
   griddep_wait();
   long long o;
   if (!bat_enter(bt, o)) return;
   if (bt.off) {
     a = bsh(a, o);
     b = bsh(b, o);
+    rs = bsh(rs, o);
   }
+  const double sr = rs ? rs[0] : 1.0;  // the scale of a (as in the glue kernels)
   // 32-bit indices (a vector has fewer than 2^31 entries); the conversion
   // itself runs on the FP64 pipe
   const int n = (int)len;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) b[k] = (T)a[k];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) b[k] = (T)(a[k] * sr);
 }
 template <typename T>
-void launch_convert(const double* src, T* dst, long long len, cudaStream_t s) {
+void launch_convert(const double* src, T* dst, long long len, cudaStream_t s, const double* rs) {
   SD_COUNT(1);
   long long nb = (len + 255) / 256;
   if (nb > 4096) nb = 4096;
   if (nb < 1) nb = 1;
-  launch_k(k_convert<T>, dim3((int)nb), dim3(256), 0, s, src, dst, len);
+  launch_k(k_convert<T>, dim3((int)nb), dim3(256), 0, s, src, dst, len, rs);
 }
 
 // ------------------------------------------------- manufactured solution
@@ -2446,7 +2459,7 @@ void launch_unpack(const Geom& g, const double* padded, double* dense, cudaStrea
 #define SD_INST(T)                                                                                               \
   template void launch_setup_coef<T>(const double*, int, int, int, double, double, int, int, int, int, int, int, \
                                      T*, T*, T*, T*, cudaStream_t);                                                \
-  template void launch_convert<T>(const double*, T*, long long, cudaStream_t);                                   \
+  template void launch_convert<T>(const double*, T*, long long, cudaStream_t, const double*);                                   \
   template void launch_cheb_V<T>(const Coef<T>&, const T*, const T*, T*, T*, T, T, const T*, int, long long, cudaStream_t); \
   template void launch_cheb_D<T>(const Coef<T>&, const T*, const T*, T*, T*, T, T, const T*, int, long long, cudaStream_t); \
   template void launch_resid_V<T>(const Coef<T>&, const T*, const T*, T*, int, int, long long, cudaStream_t);    \
@@ -2456,10 +2469,10 @@ void launch_unpack(const Geom& g, const double* padded, double* dense, cudaStrea
   template void launch_prolong_V<T>(int, int, T*, int, int, int, int, const T*, int, cudaStream_t);               \
   template void launch_prolong_D<T>(int, int, int, T*, int, int, const T*, cudaStream_t);                         \
   template void launch_resid_restrict_D<T>(const Coef<T>&, const T*, const T*, int, int, T*, cudaStream_t);                              \
-  template void launch_precond_entry<T>(const Coef<double>&, const double*, double*, double, const T*, double, int, int, T*, cudaStream_t); \
-  template void launch_precond_mid<T>(const Coef<double>&, const double*, double*, const T*, int, T*, cudaStream_t); \
+  template void launch_precond_entry<T>(const Coef<double>&, const double*, double*, double, const T*, double, int, int, T*, cudaStream_t, const double*); \
+  template void launch_precond_mid<T>(const Coef<double>&, const double*, double*, const T*, int, T*, cudaStream_t, const double*); \
   template void launch_precond_exit<T>(const Coef<double>&, double*, const T*, cudaStream_t);                     \
-  template void launch_precond_bgs_pff<T>(const Coef<double>&, const double*, double*, const T*, cudaStream_t);
+  template void launch_precond_bgs_pff<T>(const Coef<double>&, const double*, double*, const T*, cudaStream_t, const double*);
 SD_INST(float)
 SD_INST(double)
 template int launch_coarse_cycle<float>(const CoarseCycle<float>&, cudaStream_t);

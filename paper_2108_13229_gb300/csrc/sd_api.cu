@@ -171,6 +171,17 @@ struct sd_handle {
   double *stage = nullptr, *x = nullptr, *xm = nullptr, *b = nullptr, *B0 = nullptr, *B1 = nullptr;
   double* xmm = nullptr;  // x^{n-2} (extrapolate >= 2)
   double* x3 = nullptr;   // x^{n-3} (extrapolate 3)
+  // the operator applied to the solved states, Y[i] = A x^{n-i} (i < ydepth =
+  // extrapolate + 1; whole-system coupling only): the step's first residual
+  // b - A x^0 then comes from their extrapolation (k_yhist, k_resid_hist)
+  // instead of an FP64 operator application.  Every whole-system residual
+  // launch stores its A x in Y[0], so a step's solve leaves A x^n there;
+  // ylev: the valid entries Y[0 .. ylev-1] between steps (a user solve,
+  // which also writes Y[0], clears them; sd_set_state and sd_set_history
+  // recompute them with the operator's own arithmetic, so a resumed run is
+  // bitwise the uninterrupted one).
+  double* Y[4] = {nullptr, nullptr, nullptr, nullptr};
+  int ydepth = 0, ylev = 0;
   double *V = nullptr, *Z = nullptr, *partial = nullptr, *scal = nullptr, *st = nullptr, *flag = nullptr;
   // partitioned coupling: subdomain right-hand side and the IQN-ILS state
   double* bsub = nullptr;
@@ -198,7 +209,7 @@ struct sd_handle {
   // S_VSC + j: the scale of basis vector j of the whole-system solve, which
   // keeps its basis vectors unnormalised (arnoldi_orth)
   static const int S_H1 = 0, S_H2 = 32, S_N2 = 64, S_B2 = 65, S_BN = 66, S_N2B = 67, S_REO = 68, S_BLK = 69,
-                   S_Y = 96, S_CTL = 128, S_VSC = 200;
+                   S_Y = 96, S_CTL = 128, S_VSC = 200, S_RH = 240;
 };
 
 namespace {
@@ -272,6 +283,10 @@ void plan_all(sd_handle* h) {
   h->xm = a.take<double>(len);
   if (h->opt.extrapolate >= 2) h->xmm = a.take<double>(len);
   if (h->opt.extrapolate >= 3) h->x3 = a.take<double>(len);
+  if (h->opt.coupling != SD_PARTITIONED) {
+    h->ydepth = h->opt.extrapolate + 1;
+    for (int i = 0; i < h->ydepth; ++i) h->Y[i] = a.take<double>(len);
+  }
   h->b = a.take<double>(len);
   h->B0 = a.take<double>(len);
   h->B1 = a.take<double>(len);
@@ -1105,7 +1120,8 @@ void resid_norms(sd_handle* h, int mode, const double* x, const double* b, bool 
   double* sc = h->scal;
   if (mode == MODE_MONO) {
     launch_resid_norms(coef64(h, 0), x, b, h->V, h->partial, sc, sd_handle::S_BLK, sd_handle::S_B2,
-                       sd_handle::S_BN, with_b ? 1 : 0, h->s);
+                       sd_handle::S_BN, with_b ? 1 : 0, h->s, with_b && h->ydepth ? sd_handle::S_RH : -1,
+                       h->ydepth ? h->Y[0] : nullptr);
     return;
   }
   const Range rg = mode_range(h, mode);
@@ -1687,10 +1703,20 @@ int step_rhs(sd_handle* h, cudaStream_t s) {
   const double cm = h->g.h * h->g.h / h->dt;
   const double tn = h->t + h->dt;
   const int lat = h->opt.bc != SD_BC_MMS;
-  if (h->opt.extrapolate && h->have_prev) {
+  const bool extra = h->opt.extrapolate && h->have_prev;
+  const int order = extra ? std::max(0, std::min(h->opt.extrapolate, h->levels - 1)) : 0;
+  if (h->ydepth) {
+    // the first residual is formed from the operator history when it reaches
+    // back as far as the extrapolation; the history shifts either way
+    if (h->ylev > 0)
+      launch_yhist(h->Y, h->ydepth, h->V, h->g.len, order, h->ylev >= order + 1 ? 1 : 0, h->scal + sd_handle::S_RH,
+                   s);
+    else
+      CK(cudaMemsetAsync(h->scal + sd_handle::S_RH, 0, sizeof(double), s));
+  }
+  if (extra) {
     // extrapolate over the solved levels only, up to the option's order; the
     // history shifts, and x_m then holds x^n, the mass-term source
-    const int order = std::max(0, std::min(h->opt.extrapolate, h->levels - 1));
     launch_extrapolate(h->x, h->xm, h->xmm, h->x3, h->g.len, order, s);
     launch_rhs(h->g, lat, cm, h->B0, h->B1, data_scale(h, tn), h->xm, h->b, h->x, s);
   } else {
@@ -2288,6 +2314,8 @@ int step_lockstep(sd_handle* const* hs, int count, int nsteps, sd_step_info* con
     std::memset(si.data(), 0, sizeof(sd_step_info) * count);
     const int rc = fgmres_lockstep(L, si);
     if (rc != SD_OK) return rc;
+    for (int i = 0; i < count; ++i)
+      if (hs[i]->ydepth) hs[i]->ylev = std::min(hs[i]->ylev + 1, hs[i]->ydepth);
     if (t_bat_misuse) {
       snprintf(g_errmsg, sizeof(g_errmsg), "a kernel without batch support was launched in a lockstep batch");
       return SD_E_STATE;
@@ -2453,6 +2481,10 @@ int step_graph_batch(const std::vector<std::vector<sd_handle*>>& groups, const s
     CK(cudaEventSynchronize(E.ev[1]));
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, E.ev[0], E.ev[1]));
+    for (int g = 0; g < G; ++g)
+      if (on[g])
+        for (sd_handle* h : groups[g])
+          if (h->ydepth) h->ylev = std::min(h->ylev + 1, h->ydepth);
     for (int g = 0; g < G; ++g) {
       if (!on[g]) continue;
       Lockstep& L = *Ls[g];
@@ -2574,6 +2606,7 @@ int sd_step(sd_handle* h, int32_t nsteps, sd_step_info* info) {
     std::memset(&si, 0, sizeof(si));
     const int rc = h->opt.coupling == SD_PARTITIONED ? step_partitioned(h, &si) : fgmres(h, h->b, h->x, &si);
     if (rc == SD_E_CUDA || rc == SD_E_NOMEM) return rc;
+    if (h->ydepth) h->ylev = std::min(h->ylev + 1, h->ydepth);  // the solve left A x^n in Y[0]
     CK(cudaEventRecord(h->e1, h->s));
     CK(cudaEventSynchronize(h->e1));
     finish_block_residuals(h, &si);
@@ -2629,9 +2662,19 @@ int sd_set_state(sd_handle* h, double t, int64_t step, const double* x, const do
   CK(cudaStreamSynchronize(h->s));
   h->have_prev = false;
   h->levels = 1;
+  // the operator history of the given states, by the operator's own arithmetic
+  h->ylev = 0;
+  if (h->ydepth) {
+    launch_apply_full(coef64(h, 0), h->x, nullptr, h->Y[0], h->s);
+    h->ylev = 1;
+  }
   if (xprev) {
     CKR(copy_in_dense(h, xprev, dof_of(h)));
     launch_pack(h->g, h->stage, h->xm, h->s);
+    if (h->ydepth >= 2) {
+      launch_apply_full(coef64(h, 0), h->xm, nullptr, h->Y[1], h->s);
+      h->ylev = 2;
+    }
     CK(cudaStreamSynchronize(h->s));
     h->have_prev = true;
     h->levels = 2;
@@ -2657,6 +2700,10 @@ int sd_set_history(sd_handle* h, const double* xprev2) {
   if (h->opt.extrapolate < 2 || !h->have_prev || h->levels < 2) return SD_E_STATE;
   CKR(copy_in_dense(h, xprev2, dof_of(h)));
   launch_pack(h->g, h->stage, h->xmm, h->s);
+  if (h->ydepth >= 3 && h->ylev >= 2) {
+    launch_apply_full(coef64(h, 0), h->xmm, nullptr, h->Y[2], h->s);
+    h->ylev = 3;
+  }
   CK(cudaStreamSynchronize(h->s));
   h->levels = 3;
   return SD_OK;
@@ -2697,6 +2744,7 @@ int sd_solve(sd_handle* h, const double* b, double* x, sd_step_info* info) {
   std::lock_guard<std::mutex> lk(h->mtx);
   t_pdl = h->opt.pdl;
   const long long nd = dof_of(h);
+  h->ylev = 0;  // its residuals overwrite the newest operator-history entry
   // b and the iterate use the handle's b and a separate padded copy of x
   CKR(copy_in_dense(h, b, nd));
   launch_pack(h->g, h->stage, h->b, h->s);

@@ -210,9 +210,14 @@ void launch_darcy_schur_top(double* TyR, const double* w, const double* rg, int 
 void launch_apply_full(const Coef<double>& c, const double* x, const double* b, double* y, cudaStream_t s);
 // r = b - A x together with its norms: sc[blk + 0..2] = ||r||^2 over the
 // velocity, continuity and Darcy rows, sc[b2] = ||r||^2, and with with_b
-// sc[bn] = ||b||^2 (partial: 4 * resid_norms_blocks(n) doubles of scratch)
+// sc[bn] = ||b||^2 (partial: 4 * resid_norms_blocks(n) doubles of scratch).
+// rh >= 0 (with with_b): when the device flag sc[rh] is set (launch_yhist),
+// r holds A x already and the residual is b - r instead, with the same norms;
+// the flag is cleared afterwards.  yo (may be null): A x is stored there too,
+// formed by the operator's own arithmetic (as launch_apply_full's y = A x).
 void launch_resid_norms(const Coef<double>& c, const double* x, const double* b, double* r, double* partial,
-                        double* sc, int blk, int b2, int bn, int with_b, cudaStream_t s);
+                        double* sc, int blk, int b2, int bn, int with_b, cudaStream_t s, int rh = -1,
+                        double* yo = nullptr);
 long long resid_norms_blocks(int nx, int n);
 // y = A x together with the block partials of the first Gram-Schmidt pass's
 // dot products of the Arnoldi step: partial[q * nblk + blk] for V_q . y, q <
@@ -412,6 +417,11 @@ void launch_reduce(const double* partial, int nblk, int k, int ps, double* out, 
 // projection (Pythagoras over the orthonormal basis), else 0
 void launch_reduce_decide(const double* partial, int nblk, double* out, const double* h1, int k1, double eta2,
                           double* reo, cudaStream_t s);
+// the operator history of the solved states, Y[i] = A x^{n-i} (depth 1..4
+// entries): with use, r <- A x^0, the extrapolation of the given order (as
+// launch_extrapolate's); then Y[i+1] <- Y[i]; rh[0] = use
+void launch_yhist(double* const* Y, int depth, double* r, long long len, int order, int use, double* rh,
+                  cudaStream_t s);
 // history shift (x3 <- x_mm, x_mm <- x_m, x_m <- x; x3 may be null) and the
 // extrapolation of the given order (1: linear, 2: quadratic, 3: cubic)
 void launch_extrapolate(double* x, double* xm, double* xmm, double* x3, long long len, int order, cudaStream_t s);

@@ -455,6 +455,40 @@ void launch_extrapolate(double* x, double* xm, double* xmm, double* x3, long lon
   launch_k(k_extrapolate, dim3((int)(nb < 152 * 16 ? nb : 152 * 16)), dim3(RT), 0, s, x, xm, xmm, x3, len, order);
 }
 
+// The operator applied to the extrapolated initial guess, from the history of
+// the operator applied to the solved states (the extrapolation is a linear
+// combination, so A x^0 is the same combination of the A x^{n-i}): Y0 =
+// A x^n (stored by the last solve's residual), Y1 = A x^{n-1}, ... (Y1..Y3
+// may be null, the depth the handle keeps).  With use != 0, r = A x^0 by the
+// extrapolation of the given order, the same arithmetic as k_extrapolate's
+// on the states; then the history shifts (Y1 <- Y0, ...; Y0 receives the
+// step's own A x).  rh[0] = use: the step's first residual is b - r
+// (k_resid_hist) instead of an operator application.
+__global__ void k_yhist(double* __restrict__ Y0, double* __restrict__ Y1, double* __restrict__ Y2,
+                        double* __restrict__ Y3, double* __restrict__ r, long long len, int order, int use,
+                        double* __restrict__ rh) {
+  griddep_wait();
+  if (blockIdx.x == 0 && threadIdx.x == 0) rh[0] = use ? 1.0 : 0.0;
+  const int n = (int)len;  // 32-bit indices: fewer than 2^31 entries
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const double t = Y0[e], m = Y1 ? Y1[e] : 0.0, mm = Y2 ? Y2[e] : 0.0, m3 = Y3 ? Y3[e] : 0.0;
+    if (use)
+      r[e] = order >= 3 ? 4.0 * (t + mm) - 6.0 * m - m3 : order == 2 ? 3.0 * (t - m) + mm
+                                                      : order == 1 ? 2.0 * t - m : t;
+    if (Y3) Y3[e] = mm;
+    if (Y2) Y2[e] = m;
+    if (Y1) Y1[e] = t;
+  }
+}
+
+void launch_yhist(double* const* Y, int depth, double* r, long long len, int order, int use, double* rh,
+                  cudaStream_t s) {
+  SD_COUNT(1);
+  const long long nb = (len + RT - 1) / RT;
+  launch_k(k_yhist, dim3((int)(nb < 152 * 16 ? nb : 152 * 16)), dim3(RT), 0, s, Y[0], depth > 1 ? Y[1] : nullptr,
+           depth > 2 ? Y[2] : nullptr, depth > 3 ? Y[3] : nullptr, r, len, order, use, rh);
+}
+
 __global__ void k_backsolve(const double* st, int k, int m, double* y, const double* kdev, Bat bt) {
   griddep_wait();
   long long o;

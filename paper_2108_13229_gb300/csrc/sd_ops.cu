@@ -45,10 +45,16 @@ static inline dim3 grid2R(int nx, int ny, int R) { return dim3((nx + BX - 1) / B
 // partial[q * nblocks + block]: with ND > 0 the dot products of y with the
 // Krylov basis vectors V_q = V + q vs, q < ND (the first Gram-Schmidt pass of
 // the Arnoldi step); with PS the residual's norms.
+// skip (may be null): the launch returns at once when skip[0] != 0 (the
+// step's first residual formed from the operator history, k_resid_hist).
+// yo (YO: the residual form): A x itself is stored there too, formed by the
+// operator's own arithmetic (the residual is then b - A x).
 struct ApplySide {
   const double* V = nullptr;
   long long vs = 0;
   double* partial = nullptr;
+  const double* skip = nullptr;
+  double* yo = nullptr;
 };
 
 // dacc[q] += V_q[idx] * a, q < ND (one instantiation per count, as a
@@ -69,18 +75,33 @@ __device__ __forceinline__ void side_dots(const ApplySide& sd, long long idx, do
 // entry costs one FP64 instruction (the Darcy diagonal adds three).  The
 // caller guarantees 2 <= i <= nx-2 and 1 <= j <= n-2, and with DARCY (the
 // porous medium's rows at the same cell) i <= n-2.
-template <bool RES, int PS, bool DARCY, int ND>
+// YO (with RES): every row is formed as A x, stored in sd.yo, and the
+// residual is b - A x (the chain from b would give other roundings of A x).
+template <bool RES, int PS, bool DARCY, int ND, bool YO = false>
 __device__ __forceinline__ void apply_cell_interior(const Coef<double>& c, const double* __restrict__ u,
                                                     const double* __restrict__ v, const double* __restrict__ pf,
                                                     const double* __restrict__ pm, const double* __restrict__ b,
                                                     double* __restrict__ y, long long kc, long long nv,
                                                     long long npf, long long npm, double* acc,
                                                     const ApplySide& sd, double* dacc) {
+  constexpr bool CH = RES && !YO;  // the chain starts from b
   const int P = c.P;
-  const double sg = RES ? -1.0 : 1.0;
+  const double sg = CH ? -1.0 : 1.0;
   const double kd = sg * c.d6, k2 = sg * c.m2, k1 = sg * c.m1, km = sg * c.mu, kh = sg * c.h;
+  // the row's value a at index idx: y (and for YO, yo and the residual)
+  auto emit = [&](long long idx, double a, int q) {
+    double r = a;
+    if constexpr (YO) {
+      sd.yo[idx] = a;
+      r = b[idx] - a;
+    }
+    y[idx] = r;
+    side_dots<ND>(sd, idx, r, dacc);
+    if (PS) acc[q] = fma(r, r, acc[q]);
+    if (PS == 2) acc[3] = fma(b[idx], b[idx], acc[3]);
+  };
   {  // u face: d6 u + m2 (uW + uE) + m1 (uN + vN + uS + vSW) + mu (vNW + vS) + h (pf - pfW)
-    double a = RES ? fma(kd, u[kc], b[kc]) : kd * u[kc];
+    double a = CH ? fma(kd, u[kc], b[kc]) : kd * u[kc];
     a = fma(k2, u[kc - 1], a);
     a = fma(k2, u[kc + 1], a);
     a = fma(k1, u[kc + P], a);
@@ -91,13 +112,10 @@ __device__ __forceinline__ void apply_cell_interior(const Coef<double>& c, const
     a = fma(k1, v[kc - 1], a);
     a = fma(kh, pf[kc], a);
     a = fma(-kh, pf[kc - 1], a);
-    y[kc] = a;
-    side_dots<ND>(sd, kc, a, dacc);
-    if (PS) acc[0] = fma(a, a, acc[0]);
-    if (PS == 2) acc[3] = fma(b[kc], b[kc], acc[3]);
+    emit(kc, a, 0);
   }
   {  // v face: d6 v + m2 (vS + vN) + m1 (vE + uE + vW + uWS) + mu (uES + uW) + h (pf - pfS)
-    double a = RES ? fma(kd, v[kc], b[nv + kc]) : kd * v[kc];
+    double a = CH ? fma(kd, v[kc], b[nv + kc]) : kd * v[kc];
     a = fma(k2, v[kc - P], a);
     a = fma(k2, v[kc + P], a);
     a = fma(k1, v[kc + 1], a);
@@ -108,40 +126,31 @@ __device__ __forceinline__ void apply_cell_interior(const Coef<double>& c, const
     a = fma(k1, u[kc - P], a);
     a = fma(kh, pf[kc], a);
     a = fma(-kh, pf[kc - P], a);
-    y[nv + kc] = a;
-    side_dots<ND>(sd, nv + kc, a, dacc);
-    if (PS) acc[0] = fma(a, a, acc[0]);
-    if (PS == 2) acc[3] = fma(b[nv + kc], b[nv + kc], acc[3]);
+    emit(nv + kc, a, 0);
   }
   {  // continuity: h (uE - uW + vN - vS)
-    double a = RES ? fma(kh, u[kc + 1], b[npf + kc]) : kh * u[kc + 1];
+    double a = CH ? fma(kh, u[kc + 1], b[npf + kc]) : kh * u[kc + 1];
     a = fma(-kh, u[kc], a);
     a = fma(kh, v[kc + P], a);
     a = fma(-kh, v[kc], a);
-    y[npf + kc] = a;
-    side_dots<ND>(sd, npf + kc, a, dacc);
-    if (PS) acc[1] = fma(a, a, acc[1]);
-    if (PS == 2) acc[3] = fma(b[npf + kc], b[npf + kc], acc[3]);
+    emit(npf + kc, a, 1);
   }
   if (DARCY) {  // Darcy: (tw + te + ts + tn) p - tw pW - te pE - ts pS - tn pN
     const double tw = c.Tx[kc], te = c.Tx[kc + 1], ts = c.Ty[kc], tn = c.Ty[kc + P];
     const double kg = sg * ((tw + te) + (ts + tn));
-    double a = RES ? fma(kg, pm[kc], b[npm + kc]) : kg * pm[kc];
+    double a = CH ? fma(kg, pm[kc], b[npm + kc]) : kg * pm[kc];
     a = fma(-sg * tw, pm[kc - 1], a);
     a = fma(-sg * te, pm[kc + 1], a);
     a = fma(-sg * ts, pm[kc - P], a);
     a = fma(-sg * tn, pm[kc + P], a);
-    y[npm + kc] = a;
-    side_dots<ND>(sd, npm + kc, a, dacc);
-    if (PS) acc[2] = fma(a, a, acc[2]);
-    if (PS == 2) acc[3] = fma(b[npm + kc], b[npm + kc], acc[3]);
+    emit(npm + kc, a, 2);
   }
 }
 
 // The operator's rows of this thread (i, j0 .. j0+R-1).  PS (with RES):
 // acc[0..2] += the squared residuals of the velocity, continuity and Darcy
 // rows; PS 2: also acc[3] += the squared right-hand side of every row.
-template <int R, int FF, bool RES, int PS, int ND>
+template <int R, int FF, bool RES, int PS, int ND, bool YO = false>
 __device__ __forceinline__ void apply_body(const Coef<double>& c, const double* __restrict__ x,
                                            const double* __restrict__ b, double* __restrict__ y, double* acc,
                                            const ApplySide& sd, double* dacc) {
@@ -163,16 +172,16 @@ __device__ __forceinline__ void apply_body(const Coef<double>& c, const double* 
     const long long nv = (long long)n * P, npf = (long long)(2 * n + 1) * P, npm = (long long)(3 * n + 1) * P;
 #pragma unroll
     for (int rr = 0; rr < R; ++rr)
-      apply_cell_interior<RES, PS, true, ND>(c, x, x + nv, x + npf, x + npm, b, y, (long long)(j0 + rr) * P + i, nv,
-                                             npf, npm, acc, sd, dacc);
+      apply_cell_interior<RES, PS, true, ND, YO>(c, x, x + nv, x + npf, x + npm, b, y, (long long)(j0 + rr) * P + i,
+                                                 nv, npf, npm, acc, sd, dacc);
     return;
   }
   if (FF == 0 && ff_in && bi >= n) {
     const long long nv = (long long)n * P, npf = (long long)(2 * n + 1) * P, npm = (long long)(3 * n + 1) * P;
 #pragma unroll
     for (int rr = 0; rr < R; ++rr)
-      apply_cell_interior<RES, PS, false, ND>(c, x, x + nv, x + npf, x + npm, b, y, (long long)(j0 + rr) * P + i,
-                                              nv, npf, npm, acc, sd, dacc);
+      apply_cell_interior<RES, PS, false, ND, YO>(c, x, x + nv, x + npf, x + npm, b, y, (long long)(j0 + rr) * P + i,
+                                                  nv, npf, npm, acc, sd, dacc);
     return;
   }
   if (FF != 0 && ff_in && c.iw == 0) {
@@ -240,6 +249,7 @@ __device__ __forceinline__ void apply_body(const Coef<double>& c, const double* 
       {
         const double r_ = b ? b[k] - val : val;
         y[k] = r_;
+        if constexpr (YO) sd.yo[k] = val;
         side_dots<ND>(sd, k, r_, dacc);
         if (PS) acc[0] = fma(r_, r_, acc[0]);
         if (PS == 2) acc[3] = fma(b[k], b[k], acc[3]);
@@ -262,6 +272,7 @@ __device__ __forceinline__ void apply_body(const Coef<double>& c, const double* 
       {
         const double r_ = b ? b[k] - val : val;
         y[k] = r_;
+        if constexpr (YO) sd.yo[k] = val;
         side_dots<ND>(sd, k, r_, dacc);
         if (PS) acc[0] = fma(r_, r_, acc[0]);
         if (PS == 2) acc[3] = fma(b[k], b[k], acc[3]);
@@ -280,6 +291,7 @@ __device__ __forceinline__ void apply_body(const Coef<double>& c, const double* 
         {
           const double r_ = b ? b[kp] - val : val;
           y[kp] = r_;
+          if constexpr (YO) sd.yo[kp] = val;
           side_dots<ND>(sd, kp, r_, dacc);
           if (PS) acc[1] = fma(r_, r_, acc[1]);
           if (PS == 2) acc[3] = fma(b[kp], b[kp], acc[3]);
@@ -296,6 +308,7 @@ __device__ __forceinline__ void apply_body(const Coef<double>& c, const double* 
       {
         const double r_ = b ? b[km] - val : val;
         y[km] = r_;
+        if constexpr (YO) sd.yo[km] = val;
         side_dots<ND>(sd, km, r_, dacc);
         if (PS) acc[2] = fma(r_, r_, acc[2]);
         if (PS == 2) acc[3] = fma(b[km], b[km], acc[3]);
@@ -310,7 +323,7 @@ __device__ __forceinline__ void apply_body(const Coef<double>& c, const double* 
 // part, so the block sums its values through shared memory with one warp per
 // quantity (eight serial adds per lane, then five butterfly rounds) rather
 // than a butterfly in every warp.
-template <int R, int FF, bool RES, int PS = 0, int ND = 0>
+template <int R, int FF, bool RES, int PS = 0, int ND = 0, bool YO = false>
 __global__ void __launch_bounds__(BX * BY, (PS || ND) ? 3 : 4)
     k_apply_full(Coef<double> c, const double* __restrict__ x, const double* __restrict__ b, double* __restrict__ y,
                  ApplySide sd, Bat bt) {
@@ -324,12 +337,15 @@ __global__ void __launch_bounds__(BX * BY, (PS || ND) ? 3 : 4)
     y = bsh(y, o);
     sd.V = bsh(sd.V, o);
     sd.partial = bsh(sd.partial, o);
+    sd.skip = bsh(sd.skip, o);
+    sd.yo = bsh(sd.yo, o);
   }
+  if (sd.skip && sd.skip[0] != 0.0) return;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   double dacc[ND > 0 ? ND : 1];
 #pragma unroll
   for (int q = 0; q < (ND > 0 ? ND : 1); ++q) dacc[q] = 0.0;
-  apply_body<R, FF, RES, PS, ND>(c, x, b, y, acc, sd, dacc);
+  apply_body<R, FF, RES, PS, ND, YO>(c, x, b, y, acc, sd, dacc);
   if constexpr (PS > 0 || ND > 0) {
     constexpr int NQ = PS == 2 ? 4 : PS == 1 ? 3 : ND;
     __shared__ double red[NQ][BX * BY];
@@ -360,7 +376,7 @@ __global__ void __launch_bounds__(BX * BY, (PS || ND) ? 3 : 4)
 // loaded at once, then one warp per quantity).
 __global__ void __launch_bounds__(256) k_reduce_resid(const double* __restrict__ partial, int nbk,
                                                       double* __restrict__ sc, int blk, int b2, int bn, int with_b,
-                                                      Bat bt) {
+                                                      int rh, Bat bt) {
   griddep_wait();
   long long o;
   if (!bat_enter(bt, o)) return;
@@ -397,25 +413,107 @@ __global__ void __launch_bounds__(256) k_reduce_resid(const double* __restrict__
     sc[blk + 2] = tot[2];
     sc[b2] = (tot[0] + tot[1]) + tot[2];
     if (with_b) sc[bn] = tot[3];
+    if (rh >= 0) sc[rh] = 0.0;  // the history flag serves one residual
   }
 }
 
+// The step's first residual from the operator history (k_yhist): r = b - r,
+// r holding A x^0 on entry (also stored in yo), with the norms of
+// k_apply_full<.., PS 2> in its partial layout (the same grid and rows per
+// thread, so k_reduce_resid sums whichever of the two ran); nothing unless
+// run[0] != 0.  The Dirichlet faces' identity rows take A x^0 = x^0 from x
+// itself, as the operator does: the right-hand side has put the new boundary
+// data into x^0 there, which the extrapolated history does not know.
+template <int R>
+__global__ void __launch_bounds__(BX * BY) k_resid_hist(Coef<double> c, const double* __restrict__ x,
+                                                        const double* __restrict__ b, double* __restrict__ r,
+                                                        double* __restrict__ yo, double* __restrict__ partial,
+                                                        const double* __restrict__ run, Bat bt) {
+  griddep_wait();
+  long long o;
+  if (!bat_enter(bt, o)) return;
+  if (bt.off) {
+    x = bsh(x, o);
+    b = bsh(b, o);
+    r = bsh(r, o);
+    yo = bsh(yo, o);
+    partial = bsh(partial, o);
+    run = bsh(run, o);
+  }
+  if (run[0] == 0.0) return;
+  const int n = c.n, nx = c.nx, P = c.P;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j0 = (blockIdx.y * blockDim.y + threadIdx.y) * R;
+  const long long nv = (long long)n * P, npf = (long long)(2 * n + 1) * P, npm = (long long)(3 * n + 1) * P;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  auto put = [&](long long k, int q, bool ident) {
+    const double ax = ident ? x[k] : r[k], bk = b[k], rk = bk - ax;
+    yo[k] = ax;  // the newest entry of the history (a step solved by this residual alone keeps it)
+    r[k] = rk;
+    acc[q] = fma(rk, rk, acc[q]);
+    acc[3] = fma(bk, bk, acc[3]);
+  };
+  if (i <= nx) {
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) {
+      const int j = j0 + rr;
+      if (j > n) break;
+      const long long kc = (long long)j * P + i;
+      if (j < n) put(kc, 0, (i == 0 || i == nx) && !c.lat);                    // u face
+      if (i < nx) put(nv + kc, 0, j == n || (j == 0 && !on_gamma(c, i)));     // v face
+      if (i < nx && j < n) put(npf + kc, 1, false);                            // continuity
+      if (i < n && j < n) put(npm + kc, 2, false);                             // Darcy
+    }
+  }
+  __shared__ double red[4][BX * BY];
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) red[q][t] = acc[q];
+  __syncthreads();
+  const int wp = t >> 5, lane = t & 31;
+  if (wp < 4) {
+    const double* rq = red[wp] + lane * (BX * BY / 32);
+    double v = rq[0];
+#pragma unroll
+    for (int e = 1; e < BX * BY / 32; ++e) v += rq[e];
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    if (lane == 0) {
+      const long long nbk = (long long)gridDim.x * gridDim.y;
+      partial[wp * nbk + (long long)blockIdx.y * gridDim.x + blockIdx.x] = v;
+    }
+  }
+}
+
+template <int R, bool YO>
+static void resid_go(const dim3& g, cudaStream_t s, const Coef<double>& c, const double* x, const double* b,
+                     double* r, const ApplySide& sd, int with_b) {
+  if (with_b) launch_k(k_apply_full<R, 0, true, 2, 0, YO>, g, dim3(BX, BY), 0, s, c, x, b, r, sd);
+  else launch_k(k_apply_full<R, 0, true, 1, 0, YO>, g, dim3(BX, BY), 0, s, c, x, b, r, sd);
+}
+
 void launch_resid_norms(const Coef<double>& c, const double* x, const double* b, double* r, double* partial,
-                        double* sc, int blk, int b2, int bn, int with_b, cudaStream_t s) {
-  SD_COUNT(2);
+                        double* sc, int blk, int b2, int bn, int with_b, cudaStream_t s, int rh, double* yo) {
+  SD_COUNT(rh >= 0 ? 3 : 2);
   const int R = rows_apply(c.n);
   const dim3 g = grid2R(c.nx + 1, c.n + 1, R);
   ApplySide sd;
   sd.partial = partial;
+  sd.skip = rh >= 0 ? sc + rh : nullptr;
+  sd.yo = yo;
+  if (rh >= 0) {
+    if (R == 4) launch_k(k_resid_hist<4>, g, dim3(BX, BY), 0, s, c, x, b, r, yo, partial, (const double*)(sc + rh));
+    else launch_k(k_resid_hist<1>, g, dim3(BX, BY), 0, s, c, x, b, r, yo, partial, (const double*)(sc + rh));
+  }
   if (R == 4) {
-    if (with_b) launch_k(k_apply_full<4, 0, true, 2>, g, dim3(BX, BY), 0, s, c, x, b, r, sd);
-    else launch_k(k_apply_full<4, 0, true, 1>, g, dim3(BX, BY), 0, s, c, x, b, r, sd);
+    if (yo) resid_go<4, true>(g, s, c, x, b, r, sd, with_b);
+    else resid_go<4, false>(g, s, c, x, b, r, sd, with_b);
   } else {
-    if (with_b) launch_k(k_apply_full<1, 0, true, 2>, g, dim3(BX, BY), 0, s, c, x, b, r, sd);
-    else launch_k(k_apply_full<1, 0, true, 1>, g, dim3(BX, BY), 0, s, c, x, b, r, sd);
+    if (yo) resid_go<1, true>(g, s, c, x, b, r, sd, with_b);
+    else resid_go<1, false>(g, s, c, x, b, r, sd, with_b);
   }
   launch_k(k_reduce_resid, dim3(1), dim3(256), 0, s, (const double*)partial, (int)(g.x * g.y), sc, blk, b2, bn,
-           with_b);
+           with_b, rh);
 }
 
 // blocks of the operator's launch (partial sums per quantity of launch_resid_norms)

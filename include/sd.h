@@ -354,7 +354,12 @@ int sd_get_fields(sd_handle *h, double *u, double *v, double *p_ff, double *p_pm
  * x^{n-2}, is also needed (sd_get_history / sd_set_history), else the first
  * resumed step extrapolates linearly (same tolerance, other bits).
  * With extrapolate 3 the first resumed step is quadratic (x^{n-3} is not
- * carried), so that run is reproduced to the tolerance, not bitwise. */
+ * carried), so that run is reproduced to the tolerance, not bitwise.
+ * A step's first residual is formed from the operator applied to these
+ * levels, which sd_set_state and sd_set_history recompute (one operator
+ * application per level given); a step whose first residual already met
+ * the tolerance keeps that residual's extrapolated operator value instead,
+ * so a run resumed right after such a step agrees to rounding only. */
 int sd_get_state(sd_handle *h, double *t, int64_t *step, double *x, double *xprev);
 int sd_set_state(sd_handle *h, double t, int64_t step, const double *x, const double *xprev);
 

@@ -1539,12 +1539,15 @@ __global__ void __launch_bounds__(NT, NT > TLT ? 2 : (TLY <= 8 ? 8 : 4))
   }
 }
 
-// Levels whose grid has at most two tiles per SM (the GPU is otherwise idle
-// there) run 4-row tiles with 1024 threads instead of 256: a thread then
-// takes a quarter of the points per step, which shortens the latency chain
-// of the launch; every point's arithmetic is unchanged.
+// Launches with at most two tiles per SM in all (the GPU is otherwise idle
+// there; a lockstep batch counts every instance's tiles) run 4-row tiles with
+// 1024 threads instead of 256: a thread then takes a quarter of the points
+// per step, which shortens the latency chain of the launch; every point's
+// arithmetic is unchanged.
 static const int TLT_SMALL = 1024;
-static inline bool small_grid(const dim3& g) { return (long long)g.x * g.y <= 2 * 152; }
+static inline bool small_grid(const dim3& g) {
+  return (long long)g.x * g.y * (t_bat.off ? t_bat_n : 1) <= 2 * 152;
+}
 
 template <typename T, int NS, int TLY, bool RR>
 void tile_D_go(const dim3& g, cudaStream_t s, const Coef<T>& c, const T* x_in, const T* b, T* x_out,

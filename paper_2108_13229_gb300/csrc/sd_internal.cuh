@@ -31,6 +31,10 @@ namespace sdk {
 // touches global memory.  (An explicit early trigger for the next grid was
 // measured and gave no gain.)
 extern thread_local int t_pdl;
+// Set by host threads that run instances side by side on their own streams
+// (sd_solve_batch without lockstep): a launch of one instance then does not
+// have the GPU to itself, which the tile shape of small levels assumes.
+extern thread_local int t_conc;
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // Lockstep batches (sd_solve_batch): instances whose buffers have identical

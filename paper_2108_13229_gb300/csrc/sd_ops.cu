@@ -1546,6 +1546,7 @@ __global__ void __launch_bounds__(NT, NT > TLT ? 2 : (TLY <= 8 ? 8 : 4))
 // arithmetic is unchanged.
 static const int TLT_SMALL = 1024;
 static inline bool small_grid(const dim3& g) {
+  if (t_conc) return false;  // other instances' launches share the GPU
   return (long long)g.x * g.y * (t_bat.off ? t_bat_n : 1) <= 2 * 152;
 }
 

@@ -24,6 +24,10 @@
 #include <tuple>
 #include <vector>
 
+namespace sdk {
+thread_local int t_conc = 0;  // see sd_internal.cuh
+}  // namespace sdk
+
 namespace {
 
 using clk = std::chrono::steady_clock;
@@ -343,6 +347,7 @@ int sd_solve_batch_ex(sd_handle* const* hs, int32_t count, const int32_t* nsteps
   std::vector<int> rcs(ni, SD_OK);
   auto body = [&]() {
     cudaSetDevice(dev);
+    sdk::t_conc = nt > 1 ? 1 : 0;  // the workers' runs share the GPU
     for (;;) {
       const int w = next.fetch_add(1);
       if (w >= ni) return;

@@ -448,7 +448,8 @@ def bench_ours(args, ws, rank, local):
             "dtype": "f64 outer / f32 multigrid", "data": "synthetic",
             "config": {"workload": workload_desc(n, steps), "n": n, "dof": dof, "precision": "mixed",
                        "parallelism": "replicas only" if ws > 1 else "single instance",
-                       "l2": "working set ~2.4 GB per instance, larger than L2 (no flush needed)"},
+                       "l2": "working set %.1f GB per instance (sd_memory_estimate), larger than the 129 MB L2 "
+                             "(no flush needed)" % (sd.sd_memory_estimate(n, sd.sd_options_default()) / 1e9)},
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "iters_per_step": iters, "max_relres": relres, "gpu_launches": launches,
             "launches_per_step": launches / steps, "clocks": clocks}
